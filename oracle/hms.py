@@ -1,0 +1,251 @@
+"""Oracle O2: the hierarchical master-slave iteration, step by step (test infrastructure only).
+
+Follows Secs. 2.1-2.2 and the flowchart of Sec. 3 (Fig. 3) with the readings
+listed below; every step is a plain loop or a library primitive (sparse
+matrix product, LAPACK banded Cholesky), in FP64, with no fusion.
+
+One iteration, from the current displacement u (u = 0 at the start):
+
+1. r = p - K u on the free DOFs; R1 = ||r||_1 / ||p||_1 (Eq. 19).  Stop when
+   R1 < tol.
+2. For every set I, from the same u: the displacement-controlled relaxation
+   of Eq. 12 with the outer displacements held, written as the increment
+   delta_I = u^RD - u^old = (k^Inner_I)^-1 r_I (Eq. 13).  k^Inner_I is K
+   restricted to the free DOFs of set I (Eq. 11: "the same components as the
+   global matrix"), factored once (end of Sec. 2.2).
+3. The q = 9 incremental modes of every set on its free DOFs: translations
+   (Eq. 9), constant gradients (Eq. 10), delta and its two gradient-weighted
+   copies (Eqs. 13-14), with xi = x - x^(I), eta = y - y^(I).
+4. The upper-level matrix K_aa = V^T K V (Eq. 6) and force P = V^T r (Eq. 7).
+5. The upper-level system K_aa a = P (Eq. 8), by a Jacobi-scaled Cholesky that
+   drops degenerate modes (``coarse_solve``).
+6. u <- u + V a (Eq. 3).
+
+Readings (the paper is silent on these):
+
+* the representing node (x^(I), y^(I)) of Eq. 10 is the centroid of the set's
+  nodes; the span of the modes, hence the iterate, does not depend on it;
+* sets are rectangular node tiles of sx x sy nodes in a row-major set grid,
+  the last tile of a row or column takes the remainder;
+* q = 9 (the displacement-controlled modes only); the force-controlled modes
+  10-12 of Eqs. 15-18 are not part of this iteration;
+* a mode whose diagonal entry of K_aa is <= 1e-300 (identically zero on the
+  set's free DOFs) or whose scaled Cholesky pivot is <= 1e-14 (dependent on
+  earlier modes) gets a = 0, in the fixed order (set, mode).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from .direct import to_lower_band
+from .truss import Truss
+
+NMODES = 9
+DROP_DIAG = 1e-300
+DROP_PIVOT = 1e-14
+
+
+@dataclasses.dataclass
+class SetGrid:
+    """Rectangular node tiles: set (Ix, Iy) holds nodes i in [Ix*sx, ...),
+    j in [Iy*sy, ...); set index I = Iy * Mx + Ix."""
+    nx: int
+    ny: int
+    sx: int
+    sy: int
+
+    @property
+    def Mx(self):
+        return -(-self.nx // self.sx)
+
+    @property
+    def My(self):
+        return -(-self.ny // self.sy)
+
+    @property
+    def M(self):
+        return self.Mx * self.My
+
+    def node_set(self):
+        """Set index of every node, array [ny, nx]."""
+        j, i = np.meshgrid(np.arange(self.ny), np.arange(self.nx), indexing="ij")
+        return (j // self.sy) * self.Mx + (i // self.sx)
+
+
+def rep_points(truss: Truss, grid: SetGrid):
+    """Representing node of every set: the centroid of its nodes."""
+    ns = grid.node_set().reshape(-1)
+    cnt = np.bincount(ns, minlength=grid.M).astype(np.float64)
+    xc = np.bincount(ns, weights=truss.x.reshape(-1), minlength=grid.M) / cnt
+    yc = np.bincount(ns, weights=truss.y.reshape(-1), minlength=grid.M) / cnt
+    return xc, yc
+
+
+class LocalFactors:
+    """k^Inner of every set, factored once (end of Sec. 2.2)."""
+
+    def __init__(self, truss: Truss, grid: SetGrid):
+        ns = grid.node_set().reshape(-1)
+        dof_set = np.repeat(ns, 2)
+        self.dofs = []
+        self.factors = []
+        K = truss.K.tocsr()
+        for I in range(grid.M):
+            d = np.flatnonzero((dof_set == I) & truss.free)
+            self.dofs.append(d)
+            if d.size == 0:
+                self.factors.append(None)
+                continue
+            kin = K[d][:, d]
+            self.factors.append(sla.cholesky_banded(to_lower_band(kin), lower=True))
+
+    def relax(self, r: np.ndarray) -> np.ndarray:
+        """delta with delta_I = (k^Inner_I)^-1 r_I on every set (Eqs. 12-13)."""
+        delta = np.zeros_like(r)
+        for d, cb in zip(self.dofs, self.factors):
+            if cb is not None:
+                delta[d] = sla.cho_solve_banded((cb, True), r[d])
+        return delta
+
+
+def modes(truss: Truss, grid: SetGrid, delta: np.ndarray, rep=None,
+          mode_mask: int = 0x1FF) -> sp.csc_matrix:
+    """Incremental modes V (2N x 9M, column I*9 + m = mode m+1 of set I).
+
+    Eq. 9 (translations), Eq. 10 (constant gradients), Eq. 13 (delta) and
+    Eq. 14 (xi*delta, eta*delta); every mode is zero outside its set and on
+    constrained DOFs.  Bit m of ``mode_mask`` keeps mode m+1.
+    """
+    xc, yc = rep_points(truss, grid) if rep is None else rep
+    ns = grid.node_set().reshape(-1)
+    xi = truss.x.reshape(-1) - xc[ns]
+    eta = truss.y.reshape(-1) - yc[ns]
+    nn = ns.size
+    one, zero = np.ones(nn), np.zeros(nn)
+    dx, dy = delta[0::2], delta[1::2]
+    fields = [  # (x component, y component) per node
+        (one, zero), (zero, one),
+        (xi, zero), (eta, zero), (zero, xi), (zero, eta),
+        (dx, dy), (xi * dx, xi * dy), (eta * dx, eta * dy),
+    ]
+    free = truss.free
+    rows, cols, vals = [], [], []
+    node = np.arange(nn)
+    for m, (fx, fy) in enumerate(fields):
+        if not (mode_mask >> m) & 1:
+            continue
+        for c, f in ((0, fx), (1, fy)):
+            dof = 2 * node + c
+            keep = free[dof] & (f != 0)
+            rows.append(dof[keep]); cols.append(ns[keep] * NMODES + m); vals.append(f[keep])
+    rows = np.concatenate(rows); cols = np.concatenate(cols); vals = np.concatenate(vals)
+    return sp.csc_matrix((vals, (rows, cols)), shape=(truss.ndof, NMODES * grid.M))
+
+
+def coarse_system(truss: Truss, V: sp.spmatrix, r: np.ndarray):
+    """K_aa = V^T K V (Eq. 6) and P = V^T r (Eq. 7), dense FP64."""
+    KV = truss.K @ V
+    Kaa = (V.T @ KV).toarray()
+    P = V.T @ r
+    return Kaa, np.asarray(P).reshape(-1)
+
+
+def coarse_solve(Kaa: np.ndarray, P: np.ndarray, drop_diag=DROP_DIAG, drop_pivot=DROP_PIVOT):
+    """Solve Eq. 8 by a Jacobi-scaled Cholesky that drops degenerate modes.
+
+    With D = diag(K_aa), the matrix D^-1/2 K_aa D^-1/2 (unit diagonal) is
+    factored column by column in index order; a column whose D entry is
+    <= drop_diag, or whose pivot is <= drop_pivot, is removed from the system
+    (its coefficient is 0).  Returns (a, dropped mask).
+    """
+    n = P.size
+    D = np.diag(Kaa).copy()
+    active = D > drop_diag
+    s = np.zeros(n)
+    s[active] = 1.0 / np.sqrt(D[active])
+    A = s[:, None] * Kaa * s[None, :]
+    b = s * P
+    L = np.zeros((n, n))
+    for m in range(n):
+        if not active[m]:
+            continue
+        v = A[m:, m] - L[m:, :m] @ L[m, :m]
+        if v[0] <= drop_pivot:
+            active[m] = False
+            continue
+        d = np.sqrt(v[0])
+        L[m, m] = d
+        L[m + 1:, m] = v[1:] / d
+    y = np.zeros(n)
+    for m in range(n):
+        if active[m]:
+            y[m] = (b[m] - L[m, :m] @ y[:m]) / L[m, m]
+    x = np.zeros(n)
+    for m in range(n - 1, -1, -1):
+        if active[m]:
+            x[m] = (y[m] - L[m + 1:, m] @ x[m + 1:]) / L[m, m]
+    return s * x, ~active
+
+
+@dataclasses.dataclass
+class Result:
+    u: np.ndarray
+    history: list          # per residual evaluation: dict(R1, R2, Pi)
+    iterations: int        # master updates performed (NIR)
+    converged: bool
+    iterates: list         # u after each update (if requested)
+    dropped: list          # dropped-mode masks per update
+
+
+def solve(truss: Truss, grid: SetGrid, p: np.ndarray, tol: float, max_iter: int,
+          u0=None, rep=None, mode_mask: int = 0x1FF, keep_iterates=False,
+          factors: LocalFactors | None = None) -> Result:
+    """The paper's iteration (Fig. 3) from u0 (default 0) until R1 < tol."""
+    free = truss.free
+    p = free * np.asarray(p, dtype=np.float64)
+    u = np.zeros(truss.ndof) if u0 is None else free * np.asarray(u0, dtype=np.float64)
+    p1 = np.abs(p).sum()
+    p2 = np.sqrt(p @ p)
+    lf = factors if factors is not None else LocalFactors(truss, grid)
+    hist, its, drops = [], [], []
+    converged = False
+    t = 0
+    while True:
+        r = truss.residual(p, u)
+        R1 = np.abs(r).sum() / p1 if p1 > 0 else 0.0
+        hist.append(dict(R1=R1, R2=np.sqrt(r @ r) / p2 if p2 > 0 else 0.0,
+                         Pi=-0.5 * (u @ (p + r))))
+        if R1 < tol:
+            converged = True
+            break
+        if t >= max_iter:
+            break
+        delta = lf.relax(r)
+        V = modes(truss, grid, delta, rep, mode_mask)
+        Kaa, P = coarse_system(truss, V, r)
+        a, dropped = coarse_solve(Kaa, P)
+        u = u + V @ a
+        drops.append(dropped)
+        if keep_iterates:
+            its.append(u.copy())
+        t += 1
+    return Result(u, hist, t, converged, its, drops)
+
+
+def relax_eq12(truss: Truss, grid: SetGrid, p: np.ndarray, u_old: np.ndarray, I: int):
+    """u^Inner-RD of set I by Eq. 12 as printed: k^Inner u^RD = p^Inner -
+    k^Outer u^Outer-old (outer = every free DOF outside the set).  Returns the
+    set's free DOFs and u^RD on them."""
+    ns = np.repeat(grid.node_set().reshape(-1), 2)
+    free = truss.free
+    inner = np.flatnonzero((ns == I) & free)
+    outer = np.flatnonzero((ns != I) & free)
+    K = truss.K.tocsr()
+    kin = K[inner][:, inner].toarray()
+    kout = K[inner][:, outer]
+    rhs = np.asarray(p, dtype=np.float64)[inner] - kout @ u_old[outer]
+    return inner, np.linalg.solve(kin, rhs)
