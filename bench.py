@@ -1,0 +1,417 @@
+"""Benchmark: time-to-1e-8 relative residual of the hierarchical master-slave
+solver on the 1024 x 1024 triangle-lattice truss (16 x 16 sets of 64 x 64
+nodes, lognormal(0, 0.3) EA, bottom row clamped, Uniform(-1, 1) loads).
+
+A step is one whole solve from u = 0 until R1 = ||K u - p||_1 / ||p||_1 < 1e-8
+(Eq. 19): every iteration runs the residual, the relaxation of every set, the
+upper-level assembly and solve, all in the library's CUDA kernels.  The plain
+FP64 form is the headline (`value`); the mixed form (FP32 relaxation) runs on
+the same workload and is reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  With --impl reference the timed program is
+the CPU oracle on the host cores (a bounded sample of iterations, scaled by
+the iteration count of the method on this workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "lattice1024_lognormal"
+TOL = 1e-8
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+GOLDEN_FULL = os.path.join(ROOT, "tests", "golden", "lattice1024_lognormal_history.json")
+FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (CUDA cores and tensor cores alike)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def case():
+    from workloads import CASES
+    return CASES["lattice1024_lognormal_fp64"]
+
+
+def peaks():
+    try:
+        with open(MEASURED) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- algorithmic work
+def factor_entries(nb, h):
+    def pad4(n):
+        return (n + 3) // 4 * 4
+
+    linv = pad4(nb * (nb + 1) // 2)
+    boff = 4 * nb + (nb - 4) * nb - (nb - 4) * (nb - 3) // 2 if nb > 4 else nb * nb
+    return h * linv + (h - 1) * pad4(boff)
+
+
+def relax_work(c, fp32):
+    """Per launch of the relaxation kernel: bytes the method must move (the
+    factor read by the forward and the back substitution, r read twice,
+    delta written) and flops (two FMAs per factor entry and pass)."""
+    esz = 4 if fp32 else 8
+    ent = 0
+    nodes = c.nx * c.ny
+    for Iy in range(-(-c.ny // c.sy)):
+        for Ix in range(-(-c.nx // c.sx)):
+            w = min(c.sx, c.nx - Ix * c.sx)
+            h = min(c.sy, c.ny - Iy * c.sy)
+            ent += factor_entries(2 * w, h)
+    bytes_ = 2 * ent * esz + nodes * (32 + (8 if fp32 else 16))
+    flops = 4 * ent
+    return bytes_, flops
+
+
+def residual_work(c, fp32):
+    """Per launch of the update/residual kernel: u read + written, p read,
+    r written, delta read, EA/L of the three owned bars, the support mask."""
+    nodes = c.nx * c.ny
+    return nodes * (16 * 4 + (8 if fp32 else 16) + 24 + 1), nodes * 110
+
+
+def src_sha(name):
+    p = os.path.join(ROOT, "paper_1208_4093_gb300", "csrc", name)
+    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+
+
+def traffic_for(kernel, workload, src):
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+        e = d[kernel]
+        if e.get("workload") == workload and e.get("src_sha") == src_sha(src):
+            return e["bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(iters, workload_seed=0):
+    """Time `iters` oracle iterations on the full workload (setup untimed);
+    returns (seconds per iteration, setup seconds)."""
+    import numpy as np
+    from oracle import hms, truss
+    c = case()
+    t0 = time.perf_counter()
+    tr = truss.Truss(c.nx, c.ny, c.ea_array())
+    g = hms.SetGrid(c.nx, c.ny, c.sx, c.sy)
+    lf = hms.LocalFactors(tr, g)
+    setup = time.perf_counter() - t0
+    p = c.load_array().reshape(-1)
+    t0 = time.perf_counter()
+    hms.solve(tr, g, p, 0.0, iters, factors=lf)
+    dt = time.perf_counter() - t0
+    # solve() evaluates iters + 1 residuals and iters updates: charge per update
+    return dt / iters, setup
+
+
+def nir_golden(tol):
+    try:
+        d = json.load(open(GOLDEN_FULL))
+        return int(d["first_below_1e-8"] if tol == 1e-8 else d["first_below_1e-10"]), "oracle run to 1e-10"
+    except Exception:
+        return None, None
+
+
+def cpu_baseline_subprocess(iters):
+    """The oracle as it stands, one thread, in a child process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample(%d)))" % (ROOT, iters))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    per_it, setup = json.loads(out.stdout.strip().splitlines()[-1])
+    return per_it, setup
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    c = case()
+    import numpy as np
+    from oracle import hms, truss
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    tr = truss.Truss(c.nx, c.ny, c.ea_array())
+    g = hms.SetGrid(c.nx, c.ny, c.sx, c.sy)
+    lf = hms.LocalFactors(tr, g)
+    p = c.load_array().reshape(-1)
+    nir, src = nir_golden(TOL)
+    per = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        hms.solve(tr, g, p, 0.0, 1, factors=lf)
+        if k >= args.warmup:
+            per.append(time.perf_counter() - t0)
+    per_it = statistics.median(per)
+    value = per_it * nir * 1e3 if nir else None
+    line = {"impl": "reference", "metric": f"time to R1 < {TOL:g} (Eq. 19)", "value": value, "unit": "ms",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": value, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": c.nx, "ny": c.ny, "sets": [c.sx, c.sy], "ea": "lognormal(0,0.3)",
+                       "tol": TOL, "iterations": nir, "iterations_source": src},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} single-iteration oracle steps on the full workload "
+                                       f"({per_it:.2f} s each, setup excluded) x {nir} iterations"},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1208_4093_gb300 import capi
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    c = case()
+    ea = c.ea_array()
+    nd = c.dofs
+    p_host = c.load_array().reshape(1, -1)
+    ctx = capi.hms_context_create(local_rank)
+    stream = torch.cuda.ExternalStream(capi.hms_context_stream(ctx), device=dev)
+
+    def make(prec, profile=0, tol=TOL):
+        return capi.hms_problem_create(ctx, c.nx, c.ny, c.sx, c.sy, ea=ea, precision=prec, tol=tol,
+                                       max_iter=5000, profile=profile)
+
+    p_dev = torch.from_numpy(p_host).to(dev)
+    u_dev = torch.empty_like(p_dev)
+    its = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def timed(pr, steps, warmup, clocks=False):
+        for _ in range(warmup):
+            capi.hms_solve(ctx, pr, p_dev, u_dev, iters=its)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        sampler = ClockSampler(local_rank)
+        if clocks:
+            sampler.__enter__()
+            time.sleep(0.3)
+        torch.cuda.synchronize()
+        for k in range(steps):
+            ev[k][0].record(stream)
+            capi.hms_solve(ctx, pr, p_dev, u_dev, iters=its)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        if clocks:
+            sampler.__exit__(None, None, None)
+        if world > 1:
+            torch.distributed.barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, (sampler.summary() if clocks else None)
+
+    result = {}
+    # ---- plain FP64 form (headline) ----
+    pr64 = make(capi.HMS_FP64)
+    setup64 = capi.hms_problem_setup_ms(pr64)
+    ms64, clocks = timed(pr64, args.steps, args.warmup, clocks=True)
+    nit64 = int(its.item())
+    u64 = u_dev.cpu().numpy().copy()
+    # e2e through host buffers (pinned): H2D of the loads and D2H of u inside the timed region
+    p_pin = torch.from_numpy(p_host).pin_memory()
+    u_pin = torch.empty_like(p_pin).pin_memory()
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        capi.hms_solve(ctx, pr64, p_pin, u_pin)
+        if k >= args.warmup:
+            e2e.append((time.perf_counter() - t0) * 1e3)
+    capi.hms_problem_destroy(pr64)
+
+    # ---- mixed form on the same workload ----
+    mixed = None
+    if not args.no_mixed:
+        prm = make(capi.HMS_MIXED)
+        setupm = capi.hms_problem_setup_ms(prm)
+        msm, _ = timed(prm, args.steps, args.warmup)
+        nitm = int(its.item())
+        um = u_dev.cpu().numpy()
+        capi.hms_problem_destroy(prm)
+        mixed = {"value": statistics.median(msm), "unit": "ms", "iterations": nitm, "setup_ms": setupm,
+                 "dtype": "f32 relax / f64 residual+master+norms",
+                 "rel_diff_vs_fp64": float(np.linalg.norm(um - u64) / np.linalg.norm(u64)),
+                 "speedup_vs_fp64": statistics.median(ms64) / statistics.median(msm)}
+
+    # ---- per-kernel CUDA-event times (profile pass, same workload) ----
+    hbm_peak, peak_src = peaks()
+    rooflines = {}
+    for prec, name in ((capi.HMS_FP64, "fp64"), (capi.HMS_MIXED, "mixed")):
+        if name == "mixed" and args.no_mixed:
+            continue
+        prp = make(prec, profile=1)
+        capi.hms_solve(ctx, prp, p_dev, u_dev, iters=its)
+        kt = capi.hms_kernel_times(prp)
+        capi.hms_problem_destroy(prp)
+        fp32 = prec == capi.HMS_MIXED
+        ms, n = kt["relax"]
+        b, fl = relax_work(c, fp32)
+        avg = ms / max(n, 1)
+        if fp32:
+            ach = b / (avg * 1e-3) / 1e9
+            roof = {"kernel": "k_relax<float>", "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                    "unit": "GB/s", "frac": ach / hbm_peak, "peak_source": peak_src}
+        else:
+            ach = fl / (avg * 1e-3) / 1e9
+            roof = {"kernel": "k_relax<double>", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS,
+                    "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
+                    "peak_source": "nominal FP64 rate, 1.25 TFLOP/s",
+                    "hbm_gbs": b / (avg * 1e-3) / 1e9}
+        roof.update({"algorithmic_bytes": b, "algorithmic_flops": fl, "avg_launch_ms": avg, "launches": n,
+                     "traffic": traffic_for(roof["kernel"], WORKLOAD, "relax.cu")})
+        rb, rf = residual_work(c, fp32)
+        rms, rn = kt["update_residual"]
+        roof["update_residual"] = {"avg_launch_ms": rms / max(rn, 1),
+                                   "hbm_gbs": rb / (rms / max(rn, 1) * 1e-3) / 1e9}
+        roof["kernel_ms"] = {k: v[0] for k, v in kt.items()}
+        roof["kernel_launches"] = {k: v[1] for k, v in kt.items()}
+        rooflines[name] = roof
+
+    # kernels launched per solve: graph batches of 16 iterations, each iteration
+    # 7 + 2 * coarse_solves - 1 kernels (4 solves on the FP64 path) + 1 norm kernel
+    batches = math.ceil((nit64 + 1) / 16)
+    per_iter = 7 + 2 * 4 - 1
+    launches = args.steps * (batches * 16 * per_iter + 1)
+
+    ms_med = statistics.median(ms64)
+    if world > 1:
+        t = torch.tensor([max(ms64)], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_med = float(t.item())
+    if rank != 0:
+        capi.hms_context_destroy(ctx)
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            per_it, setup_s = cpu_baseline_subprocess(3)
+            nir = nit64
+            cpu = {"value": per_it * nir * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
+                   "sample": f"3 oracle iterations on the full workload, one thread ({per_it:.2f} s per "
+                             f"iteration, setup {setup_s:.1f} s excluded), scaled by the {nir} iterations "
+                             f"the FP64 method takes here"}
+        except Exception as e:  # the baseline is reported, never the target
+            cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+    line = {
+        "metric": f"time to R1 < {TOL:g} (Eq. 19 1-norm relative residual), plain FP64 form",
+        "value": ms_med, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_med, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": c.nx, "ny": c.ny, "dofs": nd, "sets": [c.sx, c.sy],
+                   "ea": "lognormal(0,0.3)", "loads": "Uniform(-1,1) seed 0", "tol": TOL,
+                   "iterations": nit64, "setup_ms": setup64,
+                   "l2": "working set > L2 (FP64 factors 2.2 GB streamed every iteration); no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "mixed": mixed,
+        "roofline": rooflines.get("fp64"),
+        "roofline_mixed": rooflines.get("mixed"),
+        "cpu_baseline": cpu,
+        "e2e": {"value": statistics.median(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * nd,
+                "d2h_bytes_per_step": 8 * nd},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "dofs_per_s": world * nd / (ms_med * 1e-3),
+    }
+    print(json.dumps(line))
+    capi.hms_context_destroy(ctx)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * hms.h -- C ABI of the GB300 hierarchical master-slave (HMS) truss solver.
+ *
+ * Solves K u = p (Eq. 1 of Xu, Liu, Dong, "Scalable hierarchical parallel
+ * algorithm for the solution of super large-scale sparse linear equations")
+ * for the 2-D triangle-lattice truss of its Sec. 3.1 by the paper's
+ * iteration: matrix-free residual, displacement-controlled local relaxation
+ * of every set (Eqs. 11-14), and the upper-level ("master") correction over
+ * q = 9 incremental modes per set (Eqs. 3-10), stopped by the 1-norm relative
+ * residual of Eq. 19.  Every step runs in CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: nodes (i, j), 0 <= i < nx, 0 <= j < ny, node index n = j*nx + i,
+ *   at x = L (i + (j mod 2)/2), y = L j sqrt(3)/2 (offset rows).  Node (i, j)
+ *   owns up to three bars: E to (i+1, j), NE to (i + (j mod 2), j+1) and NW to
+ *   (i - 1 + (j mod 2), j+1); a bar is a linear rod of axial stiffness EA/L.
+ * Vectors (loads, displacements, residuals, relaxation increments) are
+ *   float64 arrays of 2*nx*ny entries, DOF 2n = x and 2n+1 = y of node n.
+ *   Loads on constrained DOFs are ignored; displacements and residuals are 0
+ *   there.
+ * Sets: rectangular node tiles of set_sx x set_sy nodes, the last tile of a
+ *   row / column takes the remainder; set index I = Iy*Mx + Ix with
+ *   Mx = ceil(nx/set_sx).  Mode m (0-based) of set I is the coarse unknown
+ *   9*I + m: translations x, y (Eq. 9), gradients (xi,0), (eta,0), (0,xi),
+ *   (0,eta) (Eq. 10), delta, xi*delta, eta*delta (Eqs. 13-14), with
+ *   xi = x - x^(I), eta = y - y^(I) and (x^(I), y^(I)) the centroid of the
+ *   set's nodes.
+ * Memory: functions taking `mem_kind` accept either host pointers
+ *   (HMS_MEM_HOST: copied to and from the device inside the call) or device
+ *   pointers on the context's device (HMS_MEM_DEVICE, e.g. torch tensors'
+ *   data_ptr()).  The library copies every input it keeps; outputs go to
+ *   caller-owned buffers.  Calls are ordered on the context's stream and
+ *   return after the results are in the caller's buffers.
+ * Errors: every function returns an hms_status (0 = HMS_OK, negative = error)
+ *   and never throws; hms_last_error() gives a message.  Handles are opaque
+ *   and not thread-safe: use one handle from one thread at a time.
+ */
+#ifndef HMS_H
+#define HMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hms_status;
+#define HMS_OK 0
+#define HMS_ERR_ARG (-1)             /* invalid argument or size */
+#define HMS_ERR_NOT_SPD (-2)         /* non-positive pivot in a local factorisation */
+#define HMS_ERR_NO_CONVERGENCE (-3)  /* max_iter reached; the last iterate is returned */
+#define HMS_ERR_NONFINITE (-4)       /* NaN or Inf in inputs or in a residual norm */
+#define HMS_ERR_OOM (-5)             /* device allocation failed or over budget */
+#define HMS_ERR_TIMEOUT (-6)         /* a bounded device wait gave up */
+#define HMS_ERR_CUDA (-7)            /* any other CUDA runtime error */
+
+#define HMS_MEM_HOST 0
+#define HMS_MEM_DEVICE 1
+
+#define HMS_FP64 0   /* every step in FP64 (the plain form) */
+#define HMS_MIXED 1  /* FP32 local relaxation; FP64 residual, master correction, norms */
+
+typedef struct hms_context hms_context;
+typedef struct hms_problem hms_problem;
+
+/* Problem statement (Sec. 3.1): lattice, bar stiffnesses, supports, sets. */
+typedef struct {
+  int32_t nx, ny;            /* nodes per row, rows (>= 2 each) */
+  double bar_length;         /* L > 0 */
+  const double* ea;          /* host [3][ny][nx]: EA of the E, NE, NW bar owned by
+                                node (i, j) (entries of absent bars ignored), or
+                                NULL for ea_uniform everywhere */
+  double ea_uniform;         /* EA when ea == NULL (> 0) */
+  const uint8_t* fixed;      /* host [ny][nx][2], 1 = constrained DOF (u = 0), or NULL */
+  int32_t fix_bottom_edge;   /* used when fixed == NULL: 1 = clamp row j = 0 */
+  int32_t set_sx, set_sy;    /* set tile in nodes: 1 <= set_sx <= 64, set_sy >= 1 */
+} hms_lattice_desc;
+
+typedef struct {
+  int32_t precision;         /* HMS_FP64 or HMS_MIXED */
+  double tol;                /* stop when R1 = ||K u - p||_1 / ||p||_1 < tol (Eq. 19) */
+  int32_t max_iter;          /* upper-level updates per load vector (>= 0) */
+  int32_t coarse_solves;     /* FP32-factor solves of Eq. 8 per update incl. FP64
+                                refinement steps (1..8); 0 = default (FP64: 4, mixed: 3) */
+  int32_t batch;             /* iterations per CUDA-graph launch; 0 = default (16) */
+  int32_t profile;           /* 1 = time every kernel with CUDA events */
+} hms_options;
+
+/* Context: one device, one CUDA stream.  device = CUDA ordinal. */
+hms_status hms_context_create(int32_t device, hms_context** out);
+void hms_context_destroy(hms_context* ctx);
+/* The context's cudaStream_t (as void*), for callers that time or order work. */
+void* hms_context_stream(hms_context* ctx);
+/* Message of the last error on ctx; with ctx == NULL, of the last failed
+ * hms_context_create.  Valid until the next call on the same handle. */
+const char* hms_last_error(hms_context* ctx);
+
+/* Setup (end of Sec. 2.2: the local matrices of Eq. 12 are constant, so each
+ * set's k^Inner is factored once).  Copies the description, uploads it,
+ * factors every set's k^Inner (block Cholesky, FP64, plus an FP32 copy for
+ * HMS_MIXED) and precomputes the constant translation/gradient part of the
+ * upper-level matrix (Eq. 6).  Returns HMS_ERR_NOT_SPD if a local pivot is
+ * <= 0, HMS_ERR_OOM if device memory runs out. */
+hms_status hms_problem_create(hms_context* ctx, const hms_lattice_desc* d,
+                              const hms_options* o, hms_problem** out);
+void hms_problem_destroy(hms_problem* pr);
+/* Bytes of device memory the problem holds. */
+size_t hms_problem_device_bytes(const hms_problem* pr);
+/* Milliseconds the setup kernels took (CUDA events). */
+double hms_problem_setup_ms(const hms_problem* pr);
+
+/* The whole iteration (Fig. 3) for nrhs load vectors, each from u0 (NULL =
+ * zero): loads [nrhs][2*nx*ny], u0 and u_out likewise.  hist (nullable)
+ * receives per load vector hist_cap rows of (R1, R2, Pi) -- the 1- and
+ * 2-norm relative residuals and the energy of Eq. 2 -- one row per residual
+ * evaluation, iteration 0 first; iters (nullable) receives the number of
+ * upper-level updates per load vector.  Returns HMS_ERR_NO_CONVERGENCE
+ * (with u_out and hist written) if some load vector did not reach tol within
+ * max_iter. */
+hms_status hms_solve(hms_problem* pr, int32_t nrhs, const double* loads, const double* u0,
+                     double* u_out, double* hist, int32_t hist_cap, int32_t* iters,
+                     int32_t mem_kind);
+
+/* Per-kernel CUDA-event time of the last hms_solve with options.profile = 1:
+ * names "update_residual", "relax", "coarse_assemble", "coarse_band",
+ * "coarse_factor", "coarse_residual", "coarse_solve", in that order;
+ * ms_total[k] and launches[k] for k < n (n <= 7).  Returns the count. */
+int32_t hms_kernel_times(const hms_problem* pr, double* ms_total, int64_t* launches, int32_t n);
+
+/* ---- single steps of one iteration (for parity tests and custom drivers) ---- */
+
+/* Step a1 (Eqs. 1, 19, 2): r = p - K u on the free DOFs and the sums
+ * norms[0] = ||r||_1, norms[1] = ||r||_2^2, norms[2] = u.(p + r) (so that
+ * Pi = -norms[2]/2).  p, u, r: [2*nx*ny]. */
+hms_status hms_residual(hms_problem* pr, const double* p, const double* u, double* r,
+                        double* norms, int32_t mem_kind);
+
+/* Steps a2 + a1 (Eq. 3 then Eq. 1): u_out = u + V a with modes built from
+ * delta [2*nx*ny] and coefficients a [9*M] (set-major, 9 per set), then
+ * r = p - K u_out and the sums of hms_residual.  u_out may not alias u. */
+hms_status hms_update_residual(hms_problem* pr, const double* p, const double* u,
+                               const double* delta, const double* a, double* u_out,
+                               double* r, double* norms, int32_t mem_kind);
+
+/* Steps a3 + a4 (Eqs. 12-13 and Eq. 7): delta_I = (k^Inner_I)^-1 r_I on every
+ * set from the setup factors (FP64, or FP32 for HMS_MIXED), and P = V^T r
+ * [9*M] with the modes built from that delta. */
+hms_status hms_relax(hms_problem* pr, const double* r, double* delta, double* P,
+                     int32_t mem_kind);
+
+/* Step a5 (Eq. 6): the upper-level matrix K_aa = V^T K V for the modes built
+ * from delta, written dense [9M][9M] row-major (only for 9M <= 4096). */
+hms_status hms_coarse_matrix(hms_problem* pr, const double* delta, double* Kaa,
+                             int32_t mem_kind);
+
+/* Step a6 (Eq. 8): a = K_aa^-1 P for a dense symmetric Kaa [9M][9M] whose
+ * entries outside the set-grid band are zero, by the Jacobi-scaled Cholesky
+ * that drops modes with diag <= 1e-300 or a negligible pivot (a = 0 for
+ * them); FP32 factor with FP64 refinement (options.coarse_solves solves).
+ * dropped (nullable) receives 1 per dropped mode. */
+hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P, double* a,
+                            int32_t* dropped, int32_t mem_kind);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMS_H */

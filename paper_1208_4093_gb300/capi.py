@@ -1,0 +1,245 @@
+"""Thin Python binding of the HMS C ABI (include/hms.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Arrays are NumPy
+float64 arrays (host memory, HMS_MEM_HOST) or CUDA torch tensors on the
+context's device (HMS_MEM_DEVICE, passed by data_ptr()).  Every step of the
+solver runs in the CUDA library; if the library cannot be loaded the import
+of this module's functions raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HMS_OK = 0
+HMS_ERR_ARG = -1
+HMS_ERR_NOT_SPD = -2
+HMS_ERR_NO_CONVERGENCE = -3
+HMS_ERR_NONFINITE = -4
+HMS_ERR_OOM = -5
+HMS_ERR_TIMEOUT = -6
+HMS_ERR_CUDA = -7
+HMS_MEM_HOST = 0
+HMS_MEM_DEVICE = 1
+HMS_FP64 = 0
+HMS_MIXED = 1
+
+KERNEL_NAMES = ("update_residual", "relax", "coarse_assemble", "coarse_band", "coarse_factor",
+                "coarse_residual", "coarse_solve")
+
+_STATUS_NAMES = {0: "HMS_OK", -1: "HMS_ERR_ARG", -2: "HMS_ERR_NOT_SPD", -3: "HMS_ERR_NO_CONVERGENCE",
+                 -4: "HMS_ERR_NONFINITE", -5: "HMS_ERR_OOM", -6: "HMS_ERR_TIMEOUT", -7: "HMS_ERR_CUDA"}
+
+
+class HmsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class LatticeDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bar_length", ctypes.c_double),
+                ("ea", ctypes.c_void_p), ("ea_uniform", ctypes.c_double), ("fixed", ctypes.c_void_p),
+                ("fix_bottom_edge", ctypes.c_int32), ("set_sx", ctypes.c_int32),
+                ("set_sy", ctypes.c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("coarse_solves", ctypes.c_int32), ("batch", ctypes.c_int32), ("profile", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load lib/libhms.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"HMS CUDA library missing at {path}")
+    L = ctypes.CDLL(path)
+    sig = {
+        "hms_context_create": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(_P)]),
+        "hms_context_destroy": (None, [_P]),
+        "hms_context_stream": (_P, [_P]),
+        "hms_last_error": (ctypes.c_char_p, [_P]),
+        "hms_problem_create": (ctypes.c_int32, [_P, ctypes.POINTER(LatticeDesc), ctypes.POINTER(Options),
+                                                ctypes.POINTER(_P)]),
+        "hms_problem_destroy": (None, [_P]),
+        "hms_problem_device_bytes": (ctypes.c_size_t, [_P]),
+        "hms_problem_setup_ms": (ctypes.c_double, [_P]),
+        "hms_solve": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, ctypes.c_int32]),
+        "hms_kernel_times": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
+        "hms_residual": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32]),
+        "hms_update_residual": (ctypes.c_int32, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32]),
+        "hms_relax": (ctypes.c_int32, [_P, _P, _P, _P, ctypes.c_int32]),
+        "hms_coarse_matrix": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
+        "hms_coarse_solve": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects the library to export."""
+    return ["hms_context_create", "hms_context_destroy", "hms_context_stream", "hms_last_error",
+            "hms_problem_create", "hms_problem_destroy", "hms_problem_device_bytes",
+            "hms_problem_setup_ms", "hms_solve", "hms_kernel_times", "hms_residual",
+            "hms_update_residual", "hms_relax", "hms_coarse_matrix", "hms_coarse_solve"]
+
+
+# ---------------------------------------------------------------- marshalling
+class _Arg:
+    """A pointer argument: NumPy array (host) or CUDA tensor (device)."""
+
+    def __init__(self, x, dtype=np.float64, writable=False):
+        self.keep = None
+        if x is None:
+            self.ptr, self.kind = None, None
+        elif hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+            if not x.is_cuda:
+                x = x.numpy()
+            else:
+                if not x.is_contiguous():
+                    raise ValueError("device tensors must be contiguous")
+                self.ptr, self.kind, self.keep = x.data_ptr(), HMS_MEM_DEVICE, x
+                return
+        if x is not None:
+            a = np.asarray(x)
+            if a.dtype != dtype or not a.flags.c_contiguous or (writable and not a.flags.writeable):
+                if writable:
+                    raise ValueError(f"output array must be C-contiguous {np.dtype(dtype)}")
+                a = np.ascontiguousarray(a, dtype=dtype)
+            self.ptr, self.kind, self.keep = a.ctypes.data, HMS_MEM_HOST, a
+
+
+def _mem_kind(*args):
+    kinds = {a.kind for a in args if a.kind is not None}
+    if len(kinds) > 1:
+        raise ValueError("mix of host arrays and device tensors in one call")
+    return kinds.pop() if kinds else HMS_MEM_HOST
+
+
+def _check(ctx, st, ok=(HMS_OK,)):
+    if st not in ok:
+        msg = lib().hms_last_error(ctx)
+        raise HmsError(st, msg.decode() if msg else "")
+    return st
+
+
+# ---------------------------------------------------------------- entry points
+def hms_context_create(device: int = 0):
+    h = _P()
+    st = lib().hms_context_create(int(device), ctypes.byref(h))
+    if st != HMS_OK:
+        m = lib().hms_last_error(None)
+        raise HmsError(st, f"cannot create a context on device {device}: {m.decode() if m else ''}")
+    return h
+
+
+def hms_context_destroy(ctx):
+    lib().hms_context_destroy(ctx)
+
+
+def hms_context_stream(ctx) -> int:
+    return lib().hms_context_stream(ctx) or 0
+
+
+def hms_last_error(ctx) -> str:
+    m = lib().hms_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def hms_problem_create(ctx, nx, ny, set_sx, set_sy, *, bar_length=1.0, ea=None, ea_uniform=1.0,
+                       fixed=None, fix_bottom_edge=1, precision=HMS_FP64, tol=1e-8, max_iter=1000,
+                       coarse_solves=0, batch=0, profile=0):
+    """ea: host float64 [3, ny, nx] or None; fixed: host uint8 [ny, nx, 2] or None."""
+    ea_a = None if ea is None else np.ascontiguousarray(ea, dtype=np.float64)
+    fx_a = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
+    if ea_a is not None and ea_a.size != 3 * nx * ny:
+        raise ValueError("ea must have 3*nx*ny entries")
+    if fx_a is not None and fx_a.size != 2 * nx * ny:
+        raise ValueError("fixed must have 2*nx*ny entries")
+    d = LatticeDesc(int(nx), int(ny), float(bar_length), None if ea_a is None else ea_a.ctypes.data,
+                    float(ea_uniform), None if fx_a is None else fx_a.ctypes.data, int(fix_bottom_edge),
+                    int(set_sx), int(set_sy))
+    o = Options(int(precision), float(tol), int(max_iter), int(coarse_solves), int(batch), int(profile))
+    h = _P()
+    _check(ctx, lib().hms_problem_create(ctx, ctypes.byref(d), ctypes.byref(o), ctypes.byref(h)))
+    return h
+
+
+def hms_problem_destroy(pr):
+    lib().hms_problem_destroy(pr)
+
+
+def hms_problem_device_bytes(pr) -> int:
+    return int(lib().hms_problem_device_bytes(pr))
+
+
+def hms_problem_setup_ms(pr) -> float:
+    return float(lib().hms_problem_setup_ms(pr))
+
+
+def hms_solve(ctx, pr, loads, u_out, u0=None, hist=None, iters=None, allow_no_convergence=False):
+    """loads, u_out (and u0): [nrhs, 2*nx*ny]; hist: [nrhs, cap, 3]; iters: int32 [nrhs]."""
+    L = _Arg(loads)
+    U = _Arg(u_out, writable=True)
+    U0 = _Arg(u0)
+    H = _Arg(hist, writable=True)
+    It = _Arg(iters, dtype=np.int32, writable=True)
+    kind = _mem_kind(L, U, U0, H, It)
+    nrhs = int(np.prod(loads.shape[:-1])) if len(loads.shape) > 1 else 1
+    cap = 0 if hist is None else int(hist.shape[-2])
+    st = lib().hms_solve(pr, nrhs, L.ptr, U0.ptr, U.ptr, H.ptr, cap, It.ptr, kind)
+    ok = (HMS_OK, HMS_ERR_NO_CONVERGENCE) if allow_no_convergence else (HMS_OK,)
+    return _check(ctx, st, ok)
+
+
+def hms_kernel_times(pr):
+    ms = (ctypes.c_double * 7)()
+    n = (ctypes.c_int64 * 7)()
+    k = lib().hms_kernel_times(pr, ctypes.cast(ms, _P), ctypes.cast(n, _P), 7)
+    return {KERNEL_NAMES[i]: (float(ms[i]), int(n[i])) for i in range(k)}
+
+
+def hms_residual(ctx, pr, p, u, r_out, norms_out):
+    A = [_Arg(p), _Arg(u), _Arg(r_out, writable=True), _Arg(norms_out, writable=True)]
+    _check(ctx, lib().hms_residual(pr, *[a.ptr for a in A], _mem_kind(*A)))
+
+
+def hms_update_residual(ctx, pr, p, u, delta, a, u_out, r_out, norms_out):
+    A = [_Arg(p), _Arg(u), _Arg(delta), _Arg(a), _Arg(u_out, writable=True), _Arg(r_out, writable=True),
+         _Arg(norms_out, writable=True)]
+    _check(ctx, lib().hms_update_residual(pr, *[x.ptr for x in A], _mem_kind(*A)))
+
+
+def hms_relax(ctx, pr, r, delta_out, P_out):
+    A = [_Arg(r), _Arg(delta_out, writable=True), _Arg(P_out, writable=True)]
+    _check(ctx, lib().hms_relax(pr, *[x.ptr for x in A], _mem_kind(*A)))
+
+
+def hms_coarse_matrix(ctx, pr, delta, Kaa_out):
+    A = [_Arg(delta), _Arg(Kaa_out, writable=True)]
+    _check(ctx, lib().hms_coarse_matrix(pr, *[x.ptr for x in A], _mem_kind(*A)))
+
+
+def hms_coarse_solve(ctx, pr, Kaa, P, a_out, dropped_out=None):
+    A = [_Arg(Kaa), _Arg(P), _Arg(a_out, writable=True), _Arg(dropped_out, dtype=np.int32, writable=True)]
+    _check(ctx, lib().hms_coarse_solve(pr, *[x.ptr for x in A], _mem_kind(*A)))

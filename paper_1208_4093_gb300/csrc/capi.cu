@@ -1,0 +1,723 @@
+// C ABI of the HMS truss solver: contexts, problem setup, the iteration loop
+// (Fig. 3 of the paper as a device-resident CUDA graph) and the single steps.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hms.h"
+#include "hms_internal.cuh"
+
+using namespace hms;
+
+struct hms_context {
+  int device = 0;
+  int nsm = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+};
+
+struct hms_problem {
+  hms_context* ctx = nullptr;
+  LatView lv{};
+  int precision = HMS_FP64, nsolve = 4, batch = 16, profile = 0, max_iter = 0;
+  double tol = 1e-8;
+  int n_c = 0, bw = 0;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  // lattice
+  double* kbar = nullptr;
+  uint8_t* fix = nullptr;
+  double2* rep = nullptr;
+  long long* set_off = nullptr;
+  // factors
+  double* f64 = nullptr;
+  float* f32 = nullptr;
+  // iteration state
+  double2* u[2] = {nullptr, nullptr};
+  double2* p = nullptr;
+  double2* r = nullptr;
+  void* delta = nullptr;
+  double* a = nullptr;
+  double* P = nullptr;
+  double* slots_base = nullptr;
+  double* slots_it = nullptr;
+  double* band = nullptr;
+  double* sband = nullptr;   // column + row layouts
+  double* scale = nullptr;
+  double* b = nullptr;
+  double* x = nullptr;
+  double* res = nullptr;
+  float* fband = nullptr;    // column + row layouts
+  float* dinv = nullptr;
+  int* dropped = nullptr;
+  double* partials = nullptr;
+  unsigned* ticket = nullptr;
+  IterCtl* ctl = nullptr;
+  IterCtl* ctl_host = nullptr;  // pinned
+  double* hist = nullptr;
+  int hist_cap = 0;
+  int* err = nullptr;
+  double* norms = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  float setup_ms = 0.f;
+  double ktime[KID_COUNT] = {0};
+  long long klaunch[KID_COUNT] = {0};
+};
+
+namespace {
+
+hms_status fail(hms_context* c, hms_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CKC(ctx, x)                                                                            \
+  do {                                                                                         \
+    cudaError_t e_ = (x);                                                                      \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? HMS_ERR_OOM : HMS_ERR_CUDA,          \
+                  std::string(#x) + ": " + cudaGetErrorString(e_));                            \
+  } while (0)
+
+template <typename T>
+cudaError_t palloc(hms_problem* pr, T** ptr, size_t count) {
+  void* p = nullptr;
+  const size_t bytes = count * sizeof(T);
+  cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  pr->allocs.push_back(p);
+  pr->bytes += bytes;
+  *ptr = (T*)p;
+  return cudaSuccess;
+}
+
+__global__ void k_mask_u(LatView lv, double2* u) {
+  const size_t nn = (size_t)lv.nx * lv.ny;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn; n += (size_t)gridDim.x * blockDim.x) {
+    const unsigned fm = lv.fix[n];
+    if (fm) {
+      double2 v = u[n];
+      if (fm & 1u) v.x = 0.0;
+      if (fm & 2u) v.y = 0.0;
+      u[n] = v;
+    }
+  }
+}
+__global__ void k_d2f(const double* in, float* out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+__global__ void k_f2d(const float* in, double* out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+int grid1d(size_t n) {
+  size_t g = (n + 255) / 256;
+  if (g > 8192) g = 8192;
+  return g < 1 ? 1 : (int)g;
+}
+
+cudaMemcpyKind kind_in(int mem_kind) {
+  return mem_kind == HMS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_out(int mem_kind) {
+  return mem_kind == HMS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+size_t nnodes(const hms_problem* pr) { return (size_t)pr->lv.nx * pr->lv.ny; }
+bool fp32(const hms_problem* pr) { return pr->precision == HMS_MIXED; }
+
+// Launches of one iteration (the body of Fig. 3's loop); k = position in a batch.
+cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t* ev) {
+  const LatView& lv = pr->lv;
+  int ei = 0;
+  auto mark = [&]() {
+    if (ev) cudaEventRecord(ev[ei++], s);
+  };
+  cudaError_t e;
+  mark();
+  e = launch_update_residual(s, lv, pr->u[k & 1], pr->u[(k + 1) & 1], pr->p, pr->delta, fp32(pr), pr->a,
+                             pr->r, pr->partials, pr->ticket, nullptr, pr->ctl, pr->hist, pr->hist_cap,
+                             nullptr);
+  if (e != cudaSuccess) return e;
+  mark();
+  e = launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->ctl, pr->err);
+  if (e != cudaSuccess) return e;
+  mark();
+  e = launch_coarse_slots(s, lv, pr->delta, fp32(pr), false, pr->slots_it, pr->ctl);
+  if (e != cudaSuccess) return e;
+  mark();
+  e = launch_coarse_band_from_slots(s, lv, pr->slots_base, pr->slots_it, pr->band, pr->ctl);
+  if (e != cudaSuccess) return e;
+  e = launch_coarse_scale(s, pr->n_c, pr->bw, pr->band, pr->P, pr->sband, pr->fband, pr->scale, pr->b,
+                          pr->x, pr->dropped, pr->ctl);
+  if (e != cudaSuccess) return e;
+  mark();
+  e = launch_coarse_factor(s, pr->n_c, pr->bw, pr->fband, pr->dinv, pr->dropped, pr->ctl, pr->err);
+  if (e != cudaSuccess) return e;
+  mark();
+  for (int q = 0; q < pr->nsolve; ++q) {
+    if (q > 0) {
+      e = launch_coarse_residual(s, pr->n_c, pr->bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, pr->ctl);
+      if (e != cudaSuccess) return e;
+      mark();
+    }
+    e = launch_coarse_solve(s, pr->n_c, pr->bw, pr->fband, pr->dinv, pr->dropped, q == 0 ? pr->b : pr->res,
+                            pr->x, pr->scale, q == pr->nsolve - 1 ? pr->a : nullptr, pr->ctl);
+    if (e != cudaSuccess) return e;
+    mark();
+  }
+  return cudaSuccess;
+}
+
+// kernel id of the interval between event i and i+1 of launch_iteration
+int interval_kid(int i) {
+  if (i == 0) return KID_UPDATE_RESIDUAL;
+  if (i == 1) return KID_RELAX;
+  if (i == 2) return KID_COARSE_ASSEMBLE;
+  if (i == 3) return KID_COARSE_BAND;
+  if (i == 4) return KID_COARSE_FACTOR;
+  // then: solve, (residual, solve)*
+  return ((i - 5) % 2 == 0) ? KID_COARSE_SOLVE : KID_COARSE_RESIDUAL;
+}
+
+hms_status build_graph(hms_problem* pr) {
+  hms_context* c = pr->ctx;
+  cudaStream_t s = c->stream;
+  cudaGraph_t g = nullptr;
+  CKC(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < pr->batch && e == cudaSuccess; ++k) e = launch_iteration(pr, s, k, nullptr);
+  cudaError_t e2 = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(c, HMS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  CKC(c, e2);
+  e = cudaGraphInstantiate(&pr->graph, g, 0);
+  cudaGraphDestroy(g);
+  CKC(c, e);
+  return HMS_OK;
+}
+
+hms_status check_dev_err(hms_problem* pr) {
+  int herr = 0;
+  CKC(pr->ctx, cudaMemcpyAsync(&herr, pr->err, sizeof(int), cudaMemcpyDeviceToHost, pr->ctx->stream));
+  CKC(pr->ctx, cudaStreamSynchronize(pr->ctx->stream));
+  if (herr & DEVERR_NOT_SPD) return fail(pr->ctx, HMS_ERR_NOT_SPD, "non-positive pivot in a local factorisation");
+  if (herr & DEVERR_TIMEOUT) return fail(pr->ctx, HMS_ERR_TIMEOUT, "a bounded device wait gave up");
+  return HMS_OK;
+}
+
+}  // namespace
+
+namespace hms {
+cudaError_t launch_mask_u(cudaStream_t s, const LatView& lv, double2* u) {
+  k_mask_u<<<grid1d(nnodes_of(lv)), 256, 0, s>>>(lv, u);
+  return cudaGetLastError();
+}
+}  // namespace hms
+
+static std::string g_create_err;  // message of the last failed hms_context_create
+
+extern "C" {
+
+hms_status hms_context_create(int32_t device, hms_context** out) {
+  if (!out) return HMS_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || device < 0 || device >= ndev) {
+    g_create_err = std::string("no CUDA device ") + std::to_string(device) + ": " + cudaGetErrorString(ce);
+    return HMS_ERR_ARG;
+  }
+  hms_context* c = new hms_context();
+  c->device = device;
+  if ((ce = cudaSetDevice(device)) != cudaSuccess) {
+    g_create_err = std::string("cudaSetDevice: ") + cudaGetErrorString(ce);
+    delete c;
+    return HMS_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
+  int maxsm = 0;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = configure_setup(maxsm);
+  if (e == cudaSuccess) e = configure_relax(maxsm);
+  if (e == cudaSuccess) e = configure_coarse_assemble(maxsm);
+  if (e == cudaSuccess) e = configure_coarse_solve(maxsm);
+  if (e != cudaSuccess) {
+    g_create_err = std::string("context setup: ") + cudaGetErrorString(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return HMS_ERR_CUDA;
+  }
+  *out = c;
+  return HMS_OK;
+}
+
+void hms_context_destroy(hms_context* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+void* hms_context_stream(hms_context* c) { return c ? (void*)c->stream : nullptr; }
+const char* hms_last_error(hms_context* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+void hms_problem_destroy(hms_problem* pr) {
+  if (!pr) return;
+  cudaSetDevice(pr->ctx->device);
+  cudaStreamSynchronize(pr->ctx->stream);
+  if (pr->graph) cudaGraphExecDestroy(pr->graph);
+  for (void* p : pr->allocs) cudaFree(p);
+  if (pr->ctl_host) cudaFreeHost(pr->ctl_host);
+  delete pr;
+}
+
+size_t hms_problem_device_bytes(const hms_problem* pr) { return pr ? pr->bytes : 0; }
+double hms_problem_setup_ms(const hms_problem* pr) { return pr ? (double)pr->setup_ms : 0.0; }
+
+hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const hms_options* o,
+                              hms_problem** out) {
+  if (!c || !d || !o || !out) return HMS_ERR_ARG;
+  *out = nullptr;
+  if (d->nx < 2 || d->ny < 2) return fail(c, HMS_ERR_ARG, "nx, ny must be >= 2");
+  if (!(d->bar_length > 0.0) || !std::isfinite(d->bar_length)) return fail(c, HMS_ERR_ARG, "bar_length must be > 0");
+  if (d->set_sx < 1 || d->set_sx > MAX_SX || d->set_sy < 1)
+    return fail(c, HMS_ERR_ARG, "set_sx must be in [1, 64] and set_sy >= 1");
+  if (!d->ea && !(d->ea_uniform > 0.0)) return fail(c, HMS_ERR_ARG, "ea_uniform must be > 0");
+  if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return fail(c, HMS_ERR_ARG, "bad precision");
+  if (!(o->tol >= 0.0) || o->max_iter < 0) return fail(c, HMS_ERR_ARG, "bad tol / max_iter");
+  if (o->coarse_solves < 0 || o->coarse_solves > 8) return fail(c, HMS_ERR_ARG, "coarse_solves must be in 0..8");
+  CKC(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+
+  hms_problem* pr = new hms_problem();
+  pr->ctx = c;
+  LatView& lv = pr->lv;
+  lv.nx = d->nx;
+  lv.ny = d->ny;
+  lv.sx = d->set_sx;
+  lv.sy = d->set_sy;
+  lv.Mx = (d->nx + d->set_sx - 1) / d->set_sx;
+  lv.My = (d->ny + d->set_sy - 1) / d->set_sy;
+  lv.M = lv.Mx * lv.My;
+  lv.L = d->bar_length;
+  lv.k_u = d->ea ? 0.0 : d->ea_uniform / d->bar_length;
+  pr->precision = o->precision;
+  pr->nsolve = o->coarse_solves > 0 ? o->coarse_solves : (o->precision == HMS_FP64 ? 4 : 3);
+  pr->batch = o->batch > 0 ? (o->batch + 1) / 2 * 2 : 16;
+  pr->profile = o->profile;
+  pr->tol = o->tol;
+  pr->max_iter = o->max_iter;
+  pr->n_c = NMODES * lv.M;
+  pr->bw = coarse_bw(lv);
+
+  int maxsm = 0;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (relax_smem_bytes(lv, fp32(pr)) + 2048 > (size_t)maxsm) {
+    delete pr;
+    return fail(c, HMS_ERR_ARG, "set tile too large for the relaxation kernel's shared memory");
+  }
+  if (coarse_factor_smem_bytes(pr->bw) > (size_t)maxsm || (size_t)pr->n_c * 4 > (size_t)maxsm) {
+    delete pr;
+    return fail(c, HMS_ERR_ARG, "set grid too wide for the upper-level band factorisation (Mx <= 19)");
+  }
+  if (coarse_slots_smem(lv) > (size_t)maxsm) {
+    delete pr;
+    return fail(c, HMS_ERR_ARG, "set tile too large for the upper-level assembly");
+  }
+
+  auto bail = [&](cudaError_t e, const char* what) {
+    hms_status st = fail(c, e == cudaErrorMemoryAllocation ? HMS_ERR_OOM : HMS_ERR_CUDA,
+                         std::string(what) + ": " + cudaGetErrorString(e));
+    hms_problem_destroy(pr);
+    return st;
+  };
+#define CKP(x)                          \
+  do {                                  \
+    cudaError_t e_ = (x);               \
+    if (e_ != cudaSuccess) return bail(e_, #x); \
+  } while (0)
+
+  const size_t nn = (size_t)lv.nx * lv.ny;
+  // ---- lattice description ----
+  {
+    std::vector<uint8_t> fm(nn, 0);
+    if (d->fixed) {
+      for (size_t n = 0; n < nn; ++n) fm[n] = (uint8_t)((d->fixed[2 * n] ? 1 : 0) | (d->fixed[2 * n + 1] ? 2 : 0));
+    } else if (d->fix_bottom_edge) {
+      for (int i = 0; i < lv.nx; ++i) fm[i] = 3;
+    }
+    CKP(palloc(pr, &pr->fix, nn));
+    CKP(cudaMemcpy(pr->fix, fm.data(), nn, cudaMemcpyHostToDevice));
+    lv.fix = pr->fix;
+  }
+  if (d->ea) {
+    std::vector<double> kb(3 * nn, 0.0);
+    for (int j = 0; j < lv.ny; ++j)
+      for (int i = 0; i < lv.nx; ++i) {
+        const size_t n = (size_t)j * lv.nx + i;
+        const int off = j & 1;
+        const bool e_ok = i + 1 < lv.nx;
+        const bool ne_ok = j + 1 < lv.ny && i + off < lv.nx;
+        const bool nw_ok = j + 1 < lv.ny && i - 1 + off >= 0;
+        const bool ok[3] = {e_ok, ne_ok, nw_ok};
+        for (int dd = 0; dd < 3; ++dd) {
+          const double ea = d->ea[dd * nn + n];
+          if (ok[dd]) {
+            if (!(ea > 0.0) || !std::isfinite(ea)) {
+              hms_problem_destroy(pr);
+              return fail(c, HMS_ERR_ARG, "EA must be finite and > 0 on every bar");
+            }
+            kb[dd * nn + n] = ea / lv.L;
+          }
+        }
+      }
+    CKP(palloc(pr, &pr->kbar, 3 * nn));
+    CKP(cudaMemcpy(pr->kbar, kb.data(), 3 * nn * sizeof(double), cudaMemcpyHostToDevice));
+    lv.kbar = pr->kbar;
+  }
+  {
+    // representing node of each set: the centroid of its nodes (Eq. 10)
+    std::vector<double2> rp(lv.M);
+    std::vector<long long> so(lv.M + 1, 0);
+    for (int I = 0; I < lv.M; ++I) {
+      const int Ix = I % lv.Mx, Iy = I / lv.Mx;
+      const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
+      const int w = std::min(lv.sx, lv.nx - i0), h = std::min(lv.sy, lv.ny - j0);
+      int nodd = 0;
+      for (int j = j0; j < j0 + h; ++j) nodd += (j & 1);
+      rp[I].x = lv.L * ((double)i0 + 0.5 * (double)(w - 1) + 0.5 * (double)nodd / (double)h);
+      rp[I].y = lv.L * SQ3_2 * ((double)j0 + 0.5 * (double)(h - 1));
+      so[I + 1] = so[I] + set_factor_size(2 * w, h);
+    }
+    CKP(palloc(pr, &pr->rep, lv.M));
+    CKP(cudaMemcpy(pr->rep, rp.data(), lv.M * sizeof(double2), cudaMemcpyHostToDevice));
+    lv.rep = pr->rep;
+    CKP(palloc(pr, &pr->set_off, lv.M + 1));
+    CKP(cudaMemcpy(pr->set_off, so.data(), (lv.M + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+    const size_t fsz = (size_t)so[lv.M];
+    if (fp32(pr)) {
+      CKP(palloc(pr, &pr->f32, fsz));
+      CKP(cudaMemsetAsync(pr->f32, 0, fsz * sizeof(float), s));
+    } else {
+      CKP(palloc(pr, &pr->f64, fsz));
+      CKP(cudaMemsetAsync(pr->f64, 0, fsz * sizeof(double), s));
+    }
+  }
+  // ---- iteration buffers ----
+  CKP(palloc(pr, &pr->u[0], nn));
+  CKP(palloc(pr, &pr->u[1], nn));
+  CKP(palloc(pr, &pr->p, nn));
+  CKP(palloc(pr, &pr->r, nn));
+  if (fp32(pr)) {
+    float2* dl;
+    CKP(palloc(pr, &dl, nn));
+    pr->delta = dl;
+    CKP(cudaMemsetAsync(dl, 0, nn * sizeof(float2), s));
+  } else {
+    double2* dl;
+    CKP(palloc(pr, &dl, nn));
+    pr->delta = dl;
+    CKP(cudaMemsetAsync(dl, 0, nn * sizeof(double2), s));
+  }
+  const int n_c = pr->n_c, bw = pr->bw;
+  const size_t nband = (size_t)n_c * (bw + 1);
+  CKP(palloc(pr, &pr->a, n_c));
+  CKP(palloc(pr, &pr->P, n_c));
+  CKP(palloc(pr, &pr->slots_base, (size_t)lv.M * NSLOTS * SLOT_SIZE));
+  CKP(palloc(pr, &pr->slots_it, (size_t)lv.M * NSLOTS * SLOT_SIZE));
+  CKP(palloc(pr, &pr->band, nband));
+  CKP(palloc(pr, &pr->sband, 2 * nband));
+  CKP(palloc(pr, &pr->scale, n_c));
+  CKP(palloc(pr, &pr->b, n_c));
+  CKP(palloc(pr, &pr->x, n_c));
+  CKP(palloc(pr, &pr->res, n_c));
+  CKP(palloc(pr, &pr->fband, 2 * nband));
+  CKP(palloc(pr, &pr->dinv, (size_t)coarse_dinv_size(n_c)));
+  CKP(palloc(pr, &pr->dropped, n_c));
+  const size_t npart = (size_t)std::max(update_residual_blocks(lv), 1024) * 3;
+  CKP(palloc(pr, &pr->partials, npart));
+  CKP(palloc(pr, &pr->ticket, 1));
+  CKP(cudaMemsetAsync(pr->ticket, 0, sizeof(unsigned), s));
+  CKP(palloc(pr, &pr->ctl, 1));
+  CKP(palloc(pr, &pr->err, 1));
+  CKP(cudaMemsetAsync(pr->err, 0, sizeof(int), s));
+  CKP(palloc(pr, &pr->norms, 4));
+  pr->hist_cap = pr->max_iter + 1;
+  CKP(palloc(pr, &pr->hist, 3 * (size_t)pr->hist_cap));
+  CKP(cudaMallocHost(&pr->ctl_host, sizeof(IterCtl)));
+  CKP(cudaMemsetAsync(pr->a, 0, n_c * sizeof(double), s));
+
+  // ---- setup kernels: local factors (K2f) and the constant part of K_aa ----
+  cudaEvent_t e0, e1;
+  CKP(cudaEventCreate(&e0));
+  CKP(cudaEventCreate(&e1));
+  CKP(cudaEventRecord(e0, s));
+  {
+    const int grid = std::max(1, std::min(lv.M, c->nsm));
+    double* scratch = nullptr;
+    CKP(cudaMalloc(&scratch, (size_t)grid * b_size(MAX_NB) * sizeof(double)));
+    cudaError_t e = launch_set_factor(s, lv, pr->set_off, pr->f64, pr->f32, scratch, grid, pr->err);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    CKP(e);
+  }
+  CKP(launch_coarse_slots(s, lv, pr->delta, fp32(pr), true, pr->slots_base, nullptr));
+  CKP(cudaEventRecord(e1, s));
+  CKP(cudaEventSynchronize(e1));
+  cudaEventElapsedTime(&pr->setup_ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    hms_status st = check_dev_err(pr);
+    if (st != HMS_OK) {
+      hms_problem_destroy(pr);
+      return st;
+    }
+  }
+  if (!pr->profile) {
+    hms_status st = build_graph(pr);
+    if (st != HMS_OK) {
+      hms_problem_destroy(pr);
+      return st;
+    }
+  }
+#undef CKP
+  *out = pr;
+  return HMS_OK;
+}
+
+hms_status hms_solve(hms_problem* pr, int32_t nrhs, const double* loads, const double* u0, double* u_out,
+                     double* hist, int32_t hist_cap, int32_t* iters, int32_t mem_kind) {
+  if (!pr || nrhs < 0 || !loads || !u_out) return HMS_ERR_ARG;
+  if (mem_kind != HMS_MEM_HOST && mem_kind != HMS_MEM_DEVICE) return HMS_ERR_ARG;
+  hms_context* c = pr->ctx;
+  CKC(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const size_t nn = nnodes(pr);
+  const size_t vb = nn * sizeof(double2);
+  hms_status result = HMS_OK;
+  for (int k = 0; k < KID_COUNT; ++k) {
+    pr->ktime[k] = 0.0;
+    pr->klaunch[k] = 0;
+  }
+  std::vector<cudaEvent_t> ev;
+  if (pr->profile) {
+    ev.resize(8 + 2 * pr->nsolve);
+    for (auto& e : ev) CKC(c, cudaEventCreate(&e));
+  }
+  for (int q = 0; q < nrhs; ++q) {
+    CKC(c, cudaMemcpyAsync(pr->p, loads + 2 * nn * q, vb, kind_in(mem_kind), s));
+    if (u0) {
+      CKC(c, cudaMemcpyAsync(pr->u[0], u0 + 2 * nn * q, vb, kind_in(mem_kind), s));
+      CKC(c, launch_mask_u(s, pr->lv, pr->u[0]));
+    } else {
+      CKC(c, cudaMemsetAsync(pr->u[0], 0, vb, s));
+    }
+    IterCtl hc{};
+    hc.max_iter = pr->max_iter;
+    hc.tol = pr->tol;
+    *pr->ctl_host = hc;
+    CKC(c, cudaMemcpyAsync(pr->ctl, pr->ctl_host, sizeof(IterCtl), cudaMemcpyHostToDevice, s));
+    CKC(c, launch_load_norms(s, pr->lv, pr->p, pr->partials, pr->ticket, pr->ctl));
+    const int max_launch = pr->max_iter / pr->batch + 3;
+    if (!pr->profile) {
+      for (int g = 0; g < max_launch; ++g) {
+        CKC(c, cudaGraphLaunch(pr->graph, s));
+        CKC(c, cudaMemcpyAsync(pr->ctl_host, pr->ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, s));
+        CKC(c, cudaStreamSynchronize(s));
+        if (pr->ctl_host->done) break;
+      }
+    } else {
+      for (int it = 0; it <= pr->max_iter + 1; ++it) {
+        CKC(c, launch_iteration(pr, s, it, ev.data()));
+        CKC(c, cudaMemcpyAsync(pr->ctl_host, pr->ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, s));
+        CKC(c, cudaStreamSynchronize(s));
+        const int nev = 6 + 2 * (pr->nsolve - 1);
+        const bool ran_all = !pr->ctl_host->done;
+        for (int i = 0; i + 1 < nev; ++i) {
+          if (i > 0 && !ran_all) break;  // after convergence only K1 did work
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+          pr->ktime[interval_kid(i)] += ms;
+          pr->klaunch[interval_kid(i)] += 1;
+        }
+        if (pr->ctl_host->done) break;
+      }
+    }
+    IterCtl fin = *pr->ctl_host;
+    const double2* ucur = pr->u[fin.t & 1];
+    CKC(c, cudaMemcpyAsync(u_out + 2 * nn * q, ucur, vb, kind_out(mem_kind), s));
+    if (hist && hist_cap > 0) {
+      const int rows = std::min(hist_cap, std::min(fin.t, pr->hist_cap));
+      std::vector<double> h(3 * (size_t)hist_cap, NAN);
+      CKC(c, cudaMemcpyAsync(h.data(), pr->hist, 3 * rows * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CKC(c, cudaStreamSynchronize(s));
+      if (mem_kind == HMS_MEM_DEVICE)
+        CKC(c, cudaMemcpyAsync(hist + 3 * (size_t)hist_cap * q, h.data(), 3 * hist_cap * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+      else
+        std::memcpy(hist + 3 * (size_t)hist_cap * q, h.data(), 3 * hist_cap * sizeof(double));
+    }
+    if (iters) {
+      const int32_t nit = fin.t > 0 ? fin.t - 1 : 0;
+      if (mem_kind == HMS_MEM_DEVICE)
+        CKC(c, cudaMemcpyAsync(iters + q, &nit, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      else
+        iters[q] = nit;
+    }
+    CKC(c, cudaStreamSynchronize(s));
+    {
+      hms_status st = check_dev_err(pr);
+      if (st != HMS_OK) return st;
+    }
+    if (fin.status == 3) result = fail(c, HMS_ERR_NONFINITE, "non-finite residual norm");
+    else if (fin.status != 1 && result == HMS_OK)
+      result = fail(c, HMS_ERR_NO_CONVERGENCE, "max_iter reached before tol");
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return result;
+}
+
+int32_t hms_kernel_times(const hms_problem* pr, double* ms_total, int64_t* launches, int32_t n) {
+  if (!pr) return 0;
+  const int m = std::min((int)KID_COUNT, (int)n);
+  for (int k = 0; k < m; ++k) {
+    if (ms_total) ms_total[k] = pr->ktime[k];
+    if (launches) launches[k] = pr->klaunch[k];
+  }
+  return m;
+}
+
+hms_status hms_residual(hms_problem* pr, const double* p, const double* u, double* r, double* norms,
+                        int32_t mem_kind) {
+  return hms_update_residual(pr, p, u, nullptr, nullptr, (double*)nullptr, r, norms, mem_kind);
+}
+
+hms_status hms_update_residual(hms_problem* pr, const double* p, const double* u, const double* delta,
+                               const double* a, double* u_out, double* r, double* norms, int32_t mem_kind) {
+  if (!pr || !p || !u || !r) return HMS_ERR_ARG;
+  if ((delta == nullptr) != (a == nullptr)) return HMS_ERR_ARG;
+  if (mem_kind != HMS_MEM_HOST && mem_kind != HMS_MEM_DEVICE) return HMS_ERR_ARG;
+  hms_context* c = pr->ctx;
+  CKC(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+  CKC(c, cudaMemcpyAsync(pr->p, p, vb, kind_in(mem_kind), s));
+  CKC(c, cudaMemcpyAsync(pr->u[0], u, vb, kind_in(mem_kind), s));
+  CKC(c, launch_mask_u(s, pr->lv, pr->u[0]));
+  if (delta) {
+    if (fp32(pr)) {
+      CKC(c, cudaMemcpyAsync(pr->r, delta, vb, kind_in(mem_kind), s));  // staging
+      CKC(c, launch_d2f(s, (const double*)pr->r, (float*)pr->delta, 2 * nn));
+    } else {
+      CKC(c, cudaMemcpyAsync(pr->delta, delta, vb, kind_in(mem_kind), s));
+    }
+    CKC(c, cudaMemcpyAsync(pr->a, a, pr->n_c * sizeof(double), kind_in(mem_kind), s));
+  }
+  CKC(c, launch_update_residual(s, pr->lv, pr->u[0], pr->u[1], pr->p, pr->delta, fp32(pr), delta ? pr->a : nullptr,
+                                pr->r, pr->partials, pr->ticket, pr->norms, nullptr, nullptr, 0, nullptr));
+  CKC(c, cudaMemcpyAsync(r, pr->r, vb, kind_out(mem_kind), s));
+  if (u_out) CKC(c, cudaMemcpyAsync(u_out, pr->u[1], vb, kind_out(mem_kind), s));
+  if (norms) CKC(c, cudaMemcpyAsync(norms, pr->norms, 3 * sizeof(double), kind_out(mem_kind), s));
+  CKC(c, cudaStreamSynchronize(s));
+  return HMS_OK;
+}
+
+hms_status hms_relax(hms_problem* pr, const double* r, double* delta, double* P, int32_t mem_kind) {
+  if (!pr || !r || !delta || !P) return HMS_ERR_ARG;
+  if (mem_kind != HMS_MEM_HOST && mem_kind != HMS_MEM_DEVICE) return HMS_ERR_ARG;
+  hms_context* c = pr->ctx;
+  CKC(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+  CKC(c, cudaMemcpyAsync(pr->r, r, vb, kind_in(mem_kind), s));
+  CKC(c, launch_mask_u(s, pr->lv, pr->r));
+  CKC(c, launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, nullptr, pr->err));
+  if (fp32(pr)) {
+    CKC(c, launch_f2d(s, (const float*)pr->delta, (double*)pr->u[1], 2 * nn));
+    CKC(c, cudaMemcpyAsync(delta, pr->u[1], vb, kind_out(mem_kind), s));
+  } else {
+    CKC(c, cudaMemcpyAsync(delta, pr->delta, vb, kind_out(mem_kind), s));
+  }
+  CKC(c, cudaMemcpyAsync(P, pr->P, pr->n_c * sizeof(double), kind_out(mem_kind), s));
+  CKC(c, cudaStreamSynchronize(s));
+  return check_dev_err(pr);
+}
+
+hms_status hms_coarse_matrix(hms_problem* pr, const double* delta, double* Kaa, int32_t mem_kind) {
+  if (!pr || !delta || !Kaa) return HMS_ERR_ARG;
+  if (pr->n_c > 4096) return fail(pr->ctx, HMS_ERR_ARG, "dense K_aa only for 9M <= 4096");
+  hms_context* c = pr->ctx;
+  CKC(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+  if (fp32(pr)) {
+    CKC(c, cudaMemcpyAsync(pr->r, delta, vb, kind_in(mem_kind), s));
+    CKC(c, launch_d2f(s, (const double*)pr->r, (float*)pr->delta, 2 * nn));
+  } else {
+    CKC(c, cudaMemcpyAsync(pr->delta, delta, vb, kind_in(mem_kind), s));
+  }
+  CKC(c, launch_coarse_slots(s, pr->lv, pr->delta, fp32(pr), false, pr->slots_it, nullptr));
+  CKC(c, launch_coarse_band_from_slots(s, pr->lv, pr->slots_base, pr->slots_it, pr->band, nullptr));
+  double* dense = nullptr;
+  const size_t nd = (size_t)pr->n_c * pr->n_c;
+  CKC(c, cudaMallocAsync(&dense, nd * sizeof(double), s));
+  cudaError_t e = launch_coarse_dense_from_band(s, pr->n_c, pr->bw, pr->band, dense);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Kaa, dense, nd * sizeof(double), kind_out(mem_kind), s);
+  cudaFreeAsync(dense, s);
+  CKC(c, e);
+  CKC(c, cudaStreamSynchronize(s));
+  return HMS_OK;
+}
+
+hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P, double* a, int32_t* dropped,
+                            int32_t mem_kind) {
+  if (!pr || !Kaa || !P || !a) return HMS_ERR_ARG;
+  if (pr->n_c > 4096) return fail(pr->ctx, HMS_ERR_ARG, "dense K_aa only for 9M <= 4096");
+  hms_context* c = pr->ctx;
+  CKC(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const int n = pr->n_c, bw = pr->bw;
+  const size_t nd = (size_t)n * n;
+  double* dense = nullptr;
+  CKC(c, cudaMallocAsync(&dense, nd * sizeof(double), s));
+  cudaError_t e = cudaMemcpyAsync(dense, Kaa, nd * sizeof(double), kind_in(mem_kind), s);
+  if (e == cudaSuccess) e = launch_coarse_band_from_dense(s, n, bw, dense, pr->band);
+  cudaFreeAsync(dense, s);
+  CKC(c, e);
+  CKC(c, cudaMemcpyAsync(pr->P, P, n * sizeof(double), kind_in(mem_kind), s));
+  CKC(c, launch_coarse_scale(s, n, bw, pr->band, pr->P, pr->sband, pr->fband, pr->scale, pr->b, pr->x,
+                             pr->dropped, nullptr));
+  CKC(c, launch_coarse_factor(s, n, bw, pr->fband, pr->dinv, pr->dropped, nullptr, pr->err));
+  for (int q = 0; q < pr->nsolve; ++q) {
+    if (q > 0) CKC(c, launch_coarse_residual(s, n, bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, nullptr));
+    CKC(c, launch_coarse_solve(s, n, bw, pr->fband, pr->dinv, pr->dropped, q == 0 ? pr->b : pr->res, pr->x,
+                               pr->scale, q == pr->nsolve - 1 ? pr->a : nullptr, nullptr));
+  }
+  CKC(c, cudaMemcpyAsync(a, pr->a, n * sizeof(double), kind_out(mem_kind), s));
+  if (dropped) CKC(c, cudaMemcpyAsync(dropped, pr->dropped, n * sizeof(int32_t), kind_out(mem_kind), s));
+  CKC(c, cudaStreamSynchronize(s));
+  return HMS_OK;
+}
+
+}  // extern "C"
+
+namespace hms {
+cudaError_t launch_d2f(cudaStream_t s, const double* in, float* out, size_t n) {
+  k_d2f<<<grid1d(n), 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_f2d(cudaStream_t s, const float* in, double* out, size_t n) {
+  k_f2d<<<grid1d(n), 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+}  // namespace hms

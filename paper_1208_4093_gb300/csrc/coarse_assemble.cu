@@ -1,0 +1,465 @@
+// K3: the upper-level matrix K_aa = V^T K V of Eq. 6, and its band storage.
+//
+// K = sum over bars of (EA/L) g g^T with g = e at the owner's DOFs and -e at
+// the other end's, so a bar adds (EA/L) s s^T to K_aa, where s_m = e . (V_m(a)
+// - V_m(b)) over the modes of the (at most two) sets the bar touches.  A bar
+// inside set I touches only I's nine modes; a bar crossing to a neighbour set
+// J touches 18 (I's at the owner a, J's at b with a minus sign).
+//
+// One CTA per set I sums the bars owned by its nodes into six 18 x 18 slots:
+// SELF (bars inside I, upper-left 9 x 9 used) and E, W, N, NE, NW (bars to the
+// neighbour set in that direction; rows/cols 0-8 = I's modes, 9-17 = J's).
+// The translation/gradient entries (modes 1-6) do not depend on delta: they
+// are summed once at setup (FULL = true, delta = 0) into a base copy, and
+// every iteration only the entries that involve modes 7-9 are summed
+// (FULL = false).  For bars inside I with all four DOFs free the translation
+// terms vanish and the gradient terms are constants of the bar direction, so
+// those bars only accumulate e.delta sums per direction; bars touching a
+// constrained DOF use the general 9-term form.  All sums run in a fixed order
+// (per-thread node order, then a fixed-shape tree), so the result is the same
+// on every run.
+#include "hms_internal.cuh"
+
+namespace hms {
+namespace {
+
+constexpr int NT = 256, NW = NT / 32;
+constexpr int NREG = 15;          // 3 directions x 3 delta modes + 6 delta-delta products
+constexpr int NGEN_DELTA = 24;    // (m, l), m in 6..8, l <= m
+constexpr int NGEN_FULL = 45;     // (m, l), l <= m < 9
+constexpr int LSTRIDE = 19;       // k, s[18]
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+template <typename DT>
+__device__ inline double2 ld_delta(const DT* d, size_t n);
+template <>
+__device__ inline double2 ld_delta<double2>(const double2* d, size_t n) { return d[n]; }
+template <>
+__device__ inline double2 ld_delta<float2>(const float2* d, size_t n) {
+  const float2 f = d[n];
+  return make_double2((double)f.x, (double)f.y);
+}
+
+__device__ inline int gen_idx(int m, int l, bool full) {
+  if (full) return m * (m + 1) / 2 + l;
+  return (m == 6 ? 0 : (m == 7 ? 7 : 15)) + l;
+}
+
+// e . V_m at a node, modes m = 0..8 (Eqs. 9, 10, 13, 14), zero on constrained DOFs.
+__device__ inline void mode_proj(double ex, double ey, double xi, double eta, unsigned fm, double2 dl,
+                                 double* s) {
+  const double fx = (fm & 1u) ? 0.0 : 1.0, fy = (fm & 2u) ? 0.0 : 1.0;
+  const double ed = ex * dl.x + ey * dl.y;  // delta is 0 on constrained DOFs
+  s[0] = ex * fx;
+  s[1] = ey * fy;
+  s[2] = ex * xi * fx;
+  s[3] = ex * eta * fx;
+  s[4] = ey * xi * fy;
+  s[5] = ey * eta * fy;
+  s[6] = ed;
+  s[7] = xi * ed;
+  s[8] = eta * ed;
+}
+
+struct ListCaps {
+  int cap[6], off[6], total;
+};
+__host__ __device__ inline ListCaps list_caps(int w, int h) {
+  ListCaps c;
+  c.cap[SLOT_SELF] = 0;
+  c.cap[SLOT_E] = 2 * h;
+  c.cap[SLOT_W] = h;
+  c.cap[SLOT_N] = 2 * w;
+  c.cap[SLOT_NE] = 2;
+  c.cap[SLOT_NW] = 2;
+  int o = 0;
+  for (int k = 0; k < 6; ++k) {
+    c.off[k] = o;
+    o += c.cap[k];
+  }
+  c.total = o;
+  return c;
+}
+
+template <typename DT, bool FULL>
+__global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __restrict__ delta,
+                                                     double* __restrict__ slots, const IterCtl* ctl) {
+  extern __shared__ double lists[];
+  __shared__ double sred[NW * (NREG + NGEN_FULL)];
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  constexpr int NGEN = FULL ? NGEN_FULL : NGEN_DELTA;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int I = blockIdx.x;
+  const int Ix = I % lv.Mx, Iy = I / lv.Mx;
+  const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
+  const int w = min(lv.sx, lv.nx - i0), h = min(lv.sy, lv.ny - j0);
+  const ListCaps LC = list_caps(w, h);
+  double* out = slots + (size_t)I * NSLOTS * SLOT_SIZE;
+
+  for (int q = tid; q < LC.total * LSTRIDE; q += NT) lists[q] = 0.0;
+  for (int q = tid; q < NSLOTS * SLOT_SIZE; q += NT) out[q] = 0.0;
+  __syncthreads();
+
+  const double2 repI = lv.rep[I];
+  const double ed_x[3] = {1.0, 0.5, -0.5};
+  const double ed_y[3] = {0.0, SQ3_2, SQ3_2};
+  double reg[NREG];
+  double gen[NGEN];
+#pragma unroll
+  for (int k = 0; k < NREG; ++k) reg[k] = 0.0;
+#pragma unroll
+  for (int k = 0; k < NGEN; ++k) gen[k] = 0.0;
+
+  for (int q = tid; q < w * h; q += NT) {
+    const int il = q % w, jl = q / w;
+    const int i = i0 + il, j = j0 + jl;
+    const int off = j & 1;
+    const size_t na = (size_t)j * lv.nx + i;
+    const unsigned fa = lv.fix[na];
+    const double2 da = FULL ? make_double2(0.0, 0.0) : ld_delta(delta, na);
+    const double xa = node_x(lv, i, j), ya = node_y(lv, j);
+    for (int d = 0; d < 3; ++d) {
+      const double k = bar_k(lv, i, j, d);
+      if (k == 0.0) continue;
+      const int ib = (d == 0) ? i + 1 : (d == 1 ? i + off : i - 1 + off);
+      const int jb = (d == 0) ? j : j + 1;
+      const size_t nbn = (size_t)jb * lv.nx + ib;
+      const unsigned fb = lv.fix[nbn];
+      const double2 db = FULL ? make_double2(0.0, 0.0) : ld_delta(delta, nbn);
+      const double ex = ed_x[d], ey = ed_y[d];
+      const double xb = node_x(lv, ib, jb), yb = node_y(lv, jb);
+      const int dxs = (ib >= i0 + w) ? 1 : (ib < i0 ? -1 : 0);
+      const int dys = (jb >= j0 + h) ? 1 : 0;
+      if (dxs == 0 && dys == 0) {
+        const double xia = xa - repI.x, etaa = ya - repI.y;
+        const double xib = xb - repI.x, etab = yb - repI.y;
+        if (!FULL && fa == 0u && fb == 0u) {
+          // regular bar: s_0 = s_1 = 0, s_2..s_5 constants of the direction
+          const double ea = ex * da.x + ey * da.y, eb = ex * db.x + ey * db.y;
+          const double s6 = ea - eb;
+          const double s7 = xia * ea - xib * eb;
+          const double s8 = etaa * ea - etab * eb;
+          const double k6 = k * s6, k7 = k * s7, k8 = k * s8;
+          reg[3 * d + 0] += k6;
+          reg[3 * d + 1] += k7;
+          reg[3 * d + 2] += k8;
+          reg[9] = fma(k6, s6, reg[9]);
+          reg[10] = fma(k7, s6, reg[10]);
+          reg[11] = fma(k8, s6, reg[11]);
+          reg[12] = fma(k7, s7, reg[12]);
+          reg[13] = fma(k8, s7, reg[13]);
+          reg[14] = fma(k8, s8, reg[14]);
+        } else {
+          double sa[9], sb[9];
+          mode_proj(ex, ey, xia, etaa, fa, da, sa);
+          mode_proj(ex, ey, xib, etab, fb, db, sb);
+#pragma unroll
+          for (int m = 0; m < 9; ++m) sa[m] -= sb[m];
+          if (FULL) {
+#pragma unroll
+            for (int m = 0; m < 9; ++m)
+#pragma unroll
+              for (int l = 0; l <= m; ++l) gen[m * (m + 1) / 2 + l] = fma(k * sa[m], sa[l], gen[m * (m + 1) / 2 + l]);
+          } else {
+#pragma unroll
+            for (int m = 6; m < 9; ++m)
+#pragma unroll
+              for (int l = 0; l <= m; ++l) {
+                const int g = (m == 6 ? 0 : (m == 7 ? 7 : 15)) + l;
+                gen[g] = fma(k * sa[m], sa[l], gen[g]);
+              }
+          }
+        }
+      } else {
+        int slot, idx;
+        if (dys == 0) {
+          if (dxs > 0) {
+            slot = SLOT_E;
+            idx = 2 * jl + (d == 1 ? 1 : 0);
+          } else {
+            slot = SLOT_W;
+            idx = jl;
+          }
+        } else if (dxs == 0) {
+          slot = SLOT_N;
+          idx = 2 * il + (d == 2 ? 1 : 0);
+        } else if (dxs > 0) {
+          slot = SLOT_NE;
+          idx = (d == 1) ? 0 : 1;
+        } else {
+          slot = SLOT_NW;
+          idx = (d == 2) ? 0 : 1;
+        }
+        const int Jx = Ix + dxs, Jy = Iy + dys;
+        const double2 repJ = lv.rep[Jy * lv.Mx + Jx];
+        double* e = lists + (size_t)(LC.off[slot] + idx) * LSTRIDE;
+        e[0] = k;
+        mode_proj(ex, ey, xa - repI.x, ya - repI.y, fa, da, e + 1);
+        double sb[9];
+        mode_proj(ex, ey, xb - repJ.x, yb - repJ.y, fb, db, sb);
+#pragma unroll
+        for (int m = 0; m < 9; ++m) e[10 + m] = -sb[m];
+      }
+    }
+  }
+
+  // deterministic block sums of the per-thread accumulators
+  constexpr int NACC = NREG + NGEN;
+  double acc[NACC];
+#pragma unroll
+  for (int k = 0; k < NREG; ++k) acc[k] = reg[k];
+#pragma unroll
+  for (int k = 0; k < NGEN; ++k) acc[NREG + k] = gen[k];
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) sred[warp * NACC + k] = v;
+  }
+  __syncthreads();
+  double tot = 0.0;
+  if (tid < NACC)
+    for (int ww = 0; ww < NW; ++ww) tot += sred[ww * NACC + tid];
+  __syncthreads();
+  if (tid < NACC) sred[tid] = tot;  // sred[k] = CTA total of accumulator k
+  __syncthreads();
+
+  // SELF slot (upper-left 9 x 9)
+  if (tid < 81) {
+    const int m = tid / 9, l = tid % 9;
+    const int mm = m > l ? m : l, ll = m > l ? l : m;
+    double v = 0.0;
+    bool have = false;
+    if (FULL) {
+      v = sred[NREG + mm * (mm + 1) / 2 + ll];
+      have = true;
+    } else if (mm >= 6) {
+      v = sred[NREG + gen_idx(mm, ll, false)];
+      const double L = lv.L;
+      // constants s_2..s_5 of a regular bar of direction d: -L e_x^2, -L e_x e_y, -L e_y e_x, -L e_y^2
+      if (ll >= 2 && ll <= 5) {
+        for (int d = 0; d < 3; ++d) {
+          const double ex = ed_x[d], ey = ed_y[d];
+          const double c = (ll == 2) ? -L * ex * ex : (ll == 5 ? -L * ey * ey : -L * ex * ey);
+          v = fma(c, sred[3 * d + (mm - 6)], v);
+        }
+      } else if (ll >= 6) {
+        const int qi = (mm == 6) ? 9 : (mm == 7 ? (ll == 6 ? 10 : 12) : (ll == 6 ? 11 : (ll == 7 ? 13 : 14)));
+        v += sred[qi];
+      }
+      have = true;
+    }
+    if (have) out[SLOT_SELF * SLOT_SIZE + m * SLOT_DIM + l] = v;
+  }
+  // interface slots: sum over each list in index order
+  for (int q = tid; q < 5 * SLOT_SIZE; q += NT) {
+    const int slot = 1 + q / SLOT_SIZE;
+    const int pq = q % SLOT_SIZE;
+    const int p = pq / SLOT_DIM, c = pq % SLOT_DIM;
+    const bool dp = (p % 9) >= 6, dc = (c % 9) >= 6;
+    if (!FULL && !dp && !dc) continue;
+    const double* e = lists + (size_t)LC.off[slot] * LSTRIDE;
+    double v = 0.0;
+    for (int b = 0; b < LC.cap[slot]; ++b, e += LSTRIDE) v = fma(e[0] * e[1 + p], e[1 + c], v);
+    out[slot * SLOT_SIZE + pq] = v;
+  }
+}
+
+// Band (lower, column-major: band[c*(bw+1) + k] = A[c+k][c]) of K_aa from the
+// base (modes 1-6) and per-iteration (modes 7-9) slots.
+__device__ inline double slot_entry(const double* base, const double* it, int I, int slot, int p, int c) {
+  const size_t o = ((size_t)I * NSLOTS + slot) * SLOT_SIZE + (size_t)p * SLOT_DIM + c;
+  return base[o] + it[o];
+}
+
+__global__ void k_band_from_slots(LatView lv, const double* __restrict__ base,
+                                  const double* __restrict__ it, double* __restrict__ band, int bw,
+                                  const IterCtl* ctl) {
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  const int n = NMODES * lv.M;
+  const size_t total = (size_t)n * (bw + 1);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int col = (int)(q / (bw + 1)), k = (int)(q % (bw + 1));
+    const int row = col + k;
+    double v = 0.0;
+    if (row < n) {
+      const int I = col / NMODES, m = col % NMODES;
+      const int J = row / NMODES, l = row % NMODES;
+      const int Ix = I % lv.Mx, Iy = I / lv.Mx, Jx = J % lv.Mx, Jy = J / lv.Mx;
+      if (J == I) {
+        v = slot_entry(base, it, I, SLOT_SELF, l, m);
+        for (int s = SLOT_E; s < NSLOTS; ++s) v += slot_entry(base, it, I, s, l, m);
+        // contributions of neighbours that own bars into I
+        const int kx[5] = {-1, 1, 0, -1, 1};   // owner offset for E, W, N, NE, NW
+        const int ky[5] = {0, 0, -1, -1, -1};
+        for (int s = 0; s < 5; ++s) {
+          const int Kx = Ix + kx[s], Ky = Iy + ky[s];
+          if (Kx < 0 || Kx >= lv.Mx || Ky < 0 || Ky >= lv.My) continue;
+          v += slot_entry(base, it, Ky * lv.Mx + Kx, SLOT_E + s, 9 + l, 9 + m);
+        }
+      } else {
+        const int dx = Jx - Ix, dy = Jy - Iy;
+        if (dy == 0 && dx == 1) {
+          v = slot_entry(base, it, I, SLOT_E, 9 + l, m) + slot_entry(base, it, J, SLOT_W, l, 9 + m);
+        } else if (dy == 1 && dx == 0) {
+          v = slot_entry(base, it, I, SLOT_N, 9 + l, m);
+        } else if (dy == 1 && dx == 1) {
+          v = slot_entry(base, it, I, SLOT_NE, 9 + l, m);
+        } else if (dy == 1 && dx == -1) {
+          v = slot_entry(base, it, I, SLOT_NW, 9 + l, m);
+        }
+      }
+    }
+    band[q] = v;
+  }
+}
+
+__global__ void k_band_from_dense(int n, int bw, const double* __restrict__ dense,
+                                  double* __restrict__ band) {
+  const size_t total = (size_t)n * (bw + 1);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int col = (int)(q / (bw + 1)), k = (int)(q % (bw + 1));
+    const int row = col + k;
+    band[q] = row < n ? dense[(size_t)row * n + col] : 0.0;
+  }
+}
+
+__global__ void k_dense_from_band(int n, int bw, const double* __restrict__ band,
+                                  double* __restrict__ dense) {
+  const size_t total = (size_t)n * n;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(q / n), c = (int)(q % n);
+    const int hi = r > c ? r : c, lo = r > c ? c : r;
+    dense[q] = (hi - lo <= bw) ? band[(size_t)lo * (bw + 1) + (hi - lo)] : 0.0;
+  }
+}
+
+// Jacobi scaling (s_i = D_ii^-1/2; modes with D_ii <= 1e-300 are dropped),
+// right-hand side b = s P, and the solution accumulator x = 0.
+__global__ void k_coarse_diag(int n, int bw, const double* __restrict__ band,
+                              const double* __restrict__ P, double* __restrict__ scale,
+                              double* __restrict__ b, double* __restrict__ x, int* __restrict__ dropped,
+                              const IterCtl* ctl) {
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double D = band[(size_t)i * (bw + 1)];
+    const bool drop = !(D > 1e-300);
+    const double s = drop ? 0.0 : 1.0 / sqrt(D);
+    scale[i] = s;
+    b[i] = s * P[i];
+    x[i] = 0.0;
+    dropped[i] = drop ? 1 : 0;
+  }
+}
+
+// Scaled band in FP64 (column layout for the residual's upper part and row
+// layout for its lower part) and its FP32 copy for the factorisation.
+__global__ void k_coarse_scale_band(int n, int bw, const double* __restrict__ band,
+                                    const double* __restrict__ scale, const int* __restrict__ dropped,
+                                    double* __restrict__ sband, double* __restrict__ sbandR,
+                                    float* __restrict__ fband, const IterCtl* ctl) {
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  const size_t total = (size_t)n * (bw + 1);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int col = (int)(q / (bw + 1)), k = (int)(q % (bw + 1));
+    const int row = col + k;
+    double v = 0.0;
+    if (row < n) {
+      if (k == 0) {
+        v = 1.0;
+      } else if (!dropped[row] && !dropped[col]) {
+        v = scale[row] * band[q] * scale[col];
+      }
+    }
+    sband[q] = v;
+    fband[q] = (float)v;
+    if (row < n) sbandR[(size_t)row * (bw + 1) + k] = v;
+  }
+}
+
+}  // namespace
+
+int coarse_bw(const LatView& lv) {
+  // set I couples to I + Mx + 1 at most (NE neighbour)
+  const int reach = (lv.M > 1) ? (lv.Mx + 1 < lv.M - 1 ? lv.Mx + 1 : lv.M - 1) : 0;
+  return NMODES * (reach + 1) - 1;
+}
+
+size_t coarse_slots_smem(const LatView& lv) {
+  const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
+  const int h = lv.sy < lv.ny ? lv.sy : lv.ny;
+  return (size_t)list_caps(w, h).total * LSTRIDE * sizeof(double);
+}
+
+cudaError_t launch_coarse_slots(cudaStream_t s, const LatView& lv, const void* delta, bool delta_fp32,
+                                bool full, double* slots, const IterCtl* ctl) {
+  const size_t smem = coarse_slots_smem(lv);
+  if (delta_fp32) {
+    if (full) k_coarse_slots<float2, true><<<lv.M, NT, smem, s>>>(lv, (const float2*)delta, slots, ctl);
+    else k_coarse_slots<float2, false><<<lv.M, NT, smem, s>>>(lv, (const float2*)delta, slots, ctl);
+  } else {
+    if (full) k_coarse_slots<double2, true><<<lv.M, NT, smem, s>>>(lv, (const double2*)delta, slots, ctl);
+    else k_coarse_slots<double2, false><<<lv.M, NT, smem, s>>>(lv, (const double2*)delta, slots, ctl);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t configure_coarse_assemble(int max_smem) {
+  cudaError_t e;
+  e = set_max_dynamic_smem(k_coarse_slots<float2, true>, max_smem);
+  if (e != cudaSuccess) return e;
+  e = set_max_dynamic_smem(k_coarse_slots<float2, false>, max_smem);
+  if (e != cudaSuccess) return e;
+  e = set_max_dynamic_smem(k_coarse_slots<double2, true>, max_smem);
+  if (e != cudaSuccess) return e;
+  return set_max_dynamic_smem(k_coarse_slots<double2, false>, max_smem);
+}
+
+static int grid_for(size_t total) {
+  size_t g = (total + 255) / 256;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_coarse_band_from_slots(cudaStream_t s, const LatView& lv, const double* base,
+                                          const double* slots, double* band, const IterCtl* ctl) {
+  const int bw = coarse_bw(lv);
+  const size_t total = (size_t)NMODES * lv.M * (bw + 1);
+  k_band_from_slots<<<grid_for(total), 256, 0, s>>>(lv, base, slots, band, bw, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_band_from_dense(cudaStream_t s, int n, int bw, const double* dense,
+                                          double* band) {
+  k_band_from_dense<<<grid_for((size_t)n * (bw + 1)), 256, 0, s>>>(n, bw, dense, band);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_dense_from_band(cudaStream_t s, int n, int bw, const double* band,
+                                          double* dense) {
+  k_dense_from_band<<<grid_for((size_t)n * n), 256, 0, s>>>(n, bw, band, dense);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_scale(cudaStream_t s, int n, int bw, const double* band, const double* P,
+                                double* sband, float* fband, double* scale, double* b, double* x,
+                                int* dropped, const IterCtl* ctl) {
+  k_coarse_diag<<<grid_for(n), 256, 0, s>>>(n, bw, band, P, scale, b, x, dropped, ctl);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  double* sbandR = sband + (size_t)n * (bw + 1);
+  k_coarse_scale_band<<<grid_for((size_t)n * (bw + 1)), 256, 0, s>>>(n, bw, band, scale, dropped,
+                                                                     sband, sbandR, fband, ctl);
+  return cudaGetLastError();
+}
+
+}  // namespace hms

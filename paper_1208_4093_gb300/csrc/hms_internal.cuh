@@ -1,0 +1,173 @@
+// Internal declarations of the HMS truss solver library (not part of the ABI).
+//
+// Data layout in HBM (all row-major over the node grid, node n = j*nx + i):
+//   u, p, r            double2 [ny][nx]      displacement, load, residual
+//   delta              double2 or float2     relaxation increment (Eq. 13)
+//   kbar               double [3][ny][nx]    EA/L of the E, NE, NW bar owned by
+//                                            node n (0 where the bar is absent);
+//                                            null when EA is uniform
+//   fix                uint8 [ny][nx]        bit 0: x constrained, bit 1: y
+//   rep                double2 [M]           representing point of every set
+//   a, P               double [M][9]         upper-level unknowns / forces
+//   factor             per set, block-bidiagonal Cholesky factor of k^Inner
+//                      (see setup.cu), FP64 or FP32
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hms {
+
+constexpr int NMODES = 9;
+constexpr double SQ3_2 = 0.86602540378443864676;  // sqrt(3)/2
+constexpr int MAX_SX = 64;                           // set width limit (nodes)
+constexpr int MAX_NB = 2 * MAX_SX;                   // DOFs per set row
+
+// slots of the per-set upper-level partial sums (Eq. 6), see coarse.cu
+enum Slot { SLOT_SELF = 0, SLOT_E, SLOT_W, SLOT_N, SLOT_NE, SLOT_NW, NSLOTS };
+constexpr int SLOT_DIM = 18;
+constexpr int SLOT_SIZE = SLOT_DIM * SLOT_DIM;
+
+// device error flags (bit mask in a device int)
+enum DevErr { DEVERR_NOT_SPD = 1, DEVERR_TIMEOUT = 2, DEVERR_NONFINITE = 4, DEVERR_COARSE = 8 };
+
+// Read-only description of the lattice and its set partition, by value.
+struct LatView {
+  int nx, ny, sx, sy, Mx, My, M;
+  double L;        // bar length
+  double k_u;      // EA/L when kbar == nullptr
+  const double* kbar;
+  const uint8_t* fix;
+  const double2* rep;
+};
+
+// Iteration control block in device memory (one per load vector in flight).
+struct IterCtl {
+  int t;           // residual evaluations done (= upper-level updates + 1)
+  int done;        // 1 once converged, out of iterations or failed
+  int status;      // 0 running, 1 converged, 2 max_iter, 3 non-finite
+  int err;         // DevErr bits raised by any kernel
+  int max_iter;
+  int pad;
+  double tol;
+  double p1, p2;   // ||p||_1, ||p||_2 of the current load vector
+};
+
+__host__ __device__ inline size_t nnodes_of(const LatView& lv) { return (size_t)lv.nx * lv.ny; }
+__host__ __device__ inline int set_of(const LatView& lv, int i, int j) {
+  return (j / lv.sy) * lv.Mx + (i / lv.sx);
+}
+__host__ __device__ inline double node_x(const LatView& lv, int i, int j) {
+  return lv.L * ((double)i + 0.5 * (double)(j & 1));
+}
+__host__ __device__ inline double node_y(const LatView& lv, int j) {
+  return lv.L * SQ3_2 * (double)j;
+}
+// EA/L of the bar of direction d (0 E, 1 NE, 2 NW) owned by node (i, j);
+// 0 if the bar or its owner does not exist.
+__device__ inline double bar_k(const LatView& lv, int i, int j, int d) {
+  if (i < 0 || i >= lv.nx || j < 0 || j >= lv.ny) return 0.0;
+  if (lv.kbar) return __ldg(lv.kbar + (size_t)d * lv.nx * lv.ny + (size_t)j * lv.nx + i);
+  // uniform stiffness: existence from the geometry
+  if (d == 0) return (i + 1 < lv.nx) ? lv.k_u : 0.0;
+  if (j + 1 >= lv.ny) return 0.0;
+  int off = j & 1;
+  int ie = (d == 1) ? i + off : i - 1 + off;
+  return (ie >= 0 && ie < lv.nx) ? lv.k_u : 0.0;
+}
+
+// Timing of the kernels of one solve (profile mode).
+enum KernelId {
+  KID_UPDATE_RESIDUAL = 0, KID_RELAX, KID_COARSE_ASSEMBLE, KID_COARSE_BAND, KID_COARSE_FACTOR,
+  KID_COARSE_RESIDUAL, KID_COARSE_SOLVE, KID_COUNT
+};
+
+// ---- per-set factor layout (setup.cu / relax.cu) ----
+// Block row jj of a set of width w has nb = 2w DOFs.  Stored per set, in
+// order: Linv_0, B_1, Linv_1, B_2, ..., Linv_{h-1}, where Linv_j is the
+// inverse of the diagonal Cholesky block (lower triangular, row r holds
+// columns 0..r) and B_j = L_{j,j-1} (row r holds columns lo(r)..nb-1,
+// lo(r) = max(0, r-3)).  Each matrix is padded to a multiple of 4 elements.
+__host__ __device__ inline int b_lo(int r) { return r > 3 ? r - 3 : 0; }
+__host__ __device__ inline long long linv_row_off(int r) { return (long long)r * (r + 1) / 2; }
+__host__ __device__ inline long long b_row_off(int nb, int r) {
+  // sum_{r' < r} (nb - lo(r'))
+  if (r <= 4) return (long long)r * nb;
+  long long m = r - 4;  // rows 4..r-1 hold nb - (r' - 3) entries each
+  return 4LL * nb + m * nb - m * (m + 1) / 2;
+}
+__host__ __device__ inline long long pad4(long long n) { return (n + 3) & ~3LL; }
+__host__ __device__ inline long long linv_size(int nb) { return pad4(linv_row_off(nb)); }
+__host__ __device__ inline long long b_size(int nb) { return pad4(b_row_off(nb, nb)); }
+__host__ __device__ inline long long set_factor_size(int nb, int h) {
+  return (long long)h * linv_size(nb) + (long long)(h - 1) * b_size(nb);
+}
+// element offset of matrix k (0 = Linv_0, 1 = B_1, 2 = Linv_1, ...) within a set
+__host__ __device__ inline long long mat_off(int nb, int k) {
+  return (long long)((k + 1) / 2) * linv_size(nb) + (long long)(k / 2) * b_size(nb);
+}
+
+// ---- launchers (each returns the launch error) ----
+// residual.cu
+cudaError_t launch_update_residual(cudaStream_t s, const LatView& lv, const double2* u_in,
+                                   double2* u_out, const double2* p, const void* delta,
+                                   bool delta_fp32, const double* a, double2* r, double* partials,
+                                   unsigned* ticket, double* norms_out, IterCtl* ctl, double* hist,
+                                   int hist_cap, int* u_cur);
+int update_residual_blocks(const LatView& lv);
+cudaError_t launch_load_norms(cudaStream_t s, const LatView& lv, double2* p, double* partials,
+                              unsigned* ticket, IterCtl* ctl);
+// setup.cu
+cudaError_t launch_set_factor(cudaStream_t s, const LatView& lv, const long long* set_off,
+                              double* f64, float* f32, double* scratch, int grid, int* err);
+// relax.cu
+cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
+                         const double* f64, const float* f32, const double2* r, void* delta,
+                         double* P, const IterCtl* ctl, int* err);
+size_t relax_smem_bytes(const LatView& lv, bool fp32);
+// coarse.cu
+cudaError_t launch_coarse_slots(cudaStream_t s, const LatView& lv, const void* delta, bool delta_fp32,
+                                bool full, double* slots, const IterCtl* ctl);
+int coarse_bw(const LatView& lv);
+cudaError_t launch_coarse_band_from_slots(cudaStream_t s, const LatView& lv, const double* base,
+                                          const double* slots, double* band, const IterCtl* ctl);
+cudaError_t launch_coarse_band_from_dense(cudaStream_t s, int n, int bw, const double* dense,
+                                          double* band);
+cudaError_t launch_coarse_dense_from_band(cudaStream_t s, int n, int bw, const double* band,
+                                          double* dense);
+cudaError_t launch_coarse_scale(cudaStream_t s, int n, int bw, const double* band, const double* P,
+                                double* sband, float* fband, double* scale, double* b,
+                                double* x, int* dropped, const IterCtl* ctl);
+cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, float* fband, float* dinv,
+                                 int* dropped, const IterCtl* ctl, int* err);
+cudaError_t launch_coarse_solve(cudaStream_t s, int n, int bw, const float* fband, const float* dinv,
+                                const int* dropped, const double* res, double* x, const double* scale,
+                                double* a_out, const IterCtl* ctl);
+cudaError_t launch_coarse_residual(cudaStream_t s, int n, int bw, const double* sband, const double* b,
+                                   const double* x, const int* dropped, double* res, const IterCtl* ctl);
+size_t coarse_factor_smem_bytes(int bw);
+int coarse_dinv_size(int n);
+size_t coarse_slots_smem(const LatView& lv);
+// one-time function attributes (max dynamic shared memory), per device
+cudaError_t configure_setup(int max_smem);
+cudaError_t configure_relax(int max_smem);
+cudaError_t configure_coarse_assemble(int max_smem);
+cudaError_t configure_coarse_solve(int max_smem);
+// small utility kernels (capi.cu)
+cudaError_t launch_mask_u(cudaStream_t s, const LatView& lv, double2* u);
+cudaError_t launch_d2f(cudaStream_t s, const double* in, float* out, size_t n);
+cudaError_t launch_f2d(cudaStream_t s, const float* in, double* out, size_t n);
+
+}  // namespace hms
+
+namespace hms {
+// Allows `func` the largest dynamic shared memory the device offers beside
+// its static shared memory.
+template <typename F>
+inline cudaError_t set_max_dynamic_smem(F* func, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)func);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute((const void*)func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+}  // namespace hms

@@ -1,0 +1,282 @@
+// K2: displacement-controlled local relaxation of every set (Eqs. 11-13) and
+// the upper-level force P = V^T r (Eq. 7).
+//
+// Eq. 12 fixes the outer displacements at their old values and solves
+//   k^Inner u^RD = p^Inner - k^Outer u^Outer-old.
+// Subtracting k^Inner u^Inner-old from both sides gives the increment of
+// Eq. 13 directly from the global residual:
+//   k^Inner (u^RD - u^old) = p^Inner - k^Outer u^Outer-old - k^Inner u^Inner-old = r_I,
+// so delta_I = (k^Inner_I)^-1 r_I, all sets from the same u (every set relaxes
+// against its neighbours' old displacements).
+//
+// One CTA per set.  The set's block-bidiagonal factor (setup.cu) is a stream
+// of matrices Linv_0, B_1, Linv_1, ..., consumed in order by the forward
+// substitution and in reverse order by the back substitution:
+//   forward  y_j = Linv_j (r_j - B_j y_{j-1})
+//   backward x_j = Linv_j^T (y_j - B_{j+1}^T x_{j+1})
+// Each matrix is staged in shared memory by a 1-D bulk copy (cp.async.bulk,
+// completion on an mbarrier), double-buffered so the next matrix streams in
+// while the current one is applied.  The solve runs in T = double (FP64
+// path) or T = float (mixed path, FP32 factor).  While x_j = delta is
+// finalised, each thread accumulates its DOF's share of the nine sums of
+// P_I = V_I^T r_I in FP64.
+#include "hms_internal.cuh"
+#include "ptx.cuh"
+
+namespace hms {
+namespace {
+
+constexpr int NT = 256, NW = NT / 32;
+
+__device__ inline double warp_sum_d(double v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+__device__ inline float warp_sum_f(float v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+__device__ inline double wsum(double v) { return warp_sum_d(v); }
+__device__ inline float wsum(float v) { return warp_sum_f(v); }
+
+struct RelaxSmem {
+  size_t slot_elems, y_off, z_off, w_off, x_off, part_off, total_elems;
+};
+
+template <typename T>
+__host__ __device__ inline RelaxSmem relax_layout(int nb, int h) {
+  RelaxSmem L;
+  long long ls = linv_size(nb), bs = b_size(nb);
+  L.slot_elems = (size_t)(ls > bs ? ls : bs);
+  // keep every region 16-byte aligned
+  const size_t a = 16 / sizeof(T);
+  auto up = [a](size_t n) { return (n + a - 1) / a * a; };
+  L.y_off = up(2 * L.slot_elems);
+  L.z_off = up(L.y_off + (size_t)h * nb);
+  L.w_off = up(L.z_off + nb);
+  L.x_off = up(L.w_off + nb);
+  L.part_off = up(L.x_off + nb);
+  L.total_elems = up(L.part_off + (size_t)NW * nb);
+  return L;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __restrict__ set_off,
+                                              const T* __restrict__ fac, const double2* __restrict__ r,
+                                              T* __restrict__ delta, double* __restrict__ P,
+                                              const IterCtl* ctl, int* err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint64_t bars[2];
+  __shared__ double pred[NW * NMODES];
+  __shared__ int abort_flag;
+  if (ctl && *(volatile const int*)&ctl->done) return;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int I = blockIdx.x;
+  const int Ix = I % lv.Mx, Iy = I / lv.Mx;
+  const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
+  const int w = min(lv.sx, lv.nx - i0), h = min(lv.sy, lv.ny - j0);
+  const int nb = 2 * w;
+  const RelaxSmem LY = relax_layout<T>(nb, h);
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* slot[2] = {sm, sm + LY.slot_elems};
+  T* ybuf = sm + LY.y_off;
+  T* zbuf = sm + LY.z_off;
+  T* wbuf = sm + LY.w_off;
+  T* xbuf = sm + LY.x_off;
+  T* part = sm + LY.part_off;
+  const T* fset = fac + set_off[I];
+  const double* rg = reinterpret_cast<const double*>(r);
+  const int nmat = 2 * h - 1;
+  const int nops = 2 * nmat;
+
+  auto mat_of_op = [&](int o) { return o < nmat ? o : 2 * nmat - 1 - o; };
+  auto mat_bytes = [&](int k) {
+    return (uint32_t)(((k & 1) ? b_size(nb) : linv_size(nb)) * sizeof(T));
+  };
+  auto issue = [&](int o) {
+    const int k = mat_of_op(o);
+    uint64_t* bar = &bars[o & 1];
+    const uint32_t bytes = mat_bytes(k);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(slot[o & 1], fset + mat_off(nb, k), bytes, bar);
+  };
+
+  if (tid == 0) {
+    abort_flag = 0;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    issue(0);
+    if (nops > 1) issue(1);
+  }
+  // z = r_0
+  const size_t rowbase0 = 2 * ((size_t)j0 * lv.nx + i0);
+  for (int t = tid; t < nb; t += NT) zbuf[t] = (T)rg[rowbase0 + t];
+
+  double pacc[NMODES];
+#pragma unroll
+  for (int m = 0; m < NMODES; ++m) pacc[m] = 0.0;
+  const double2 rep = lv.rep[I];
+
+  for (int o = 0; o < nops; ++o) {
+    const int k = mat_of_op(o);
+    const bool is_b = (k & 1) != 0;
+    const int j = is_b ? (k + 1) / 2 : k / 2;
+    if (!mbar_wait_bounded(&bars[o & 1], (uint32_t)((o >> 1) & 1))) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    const T* M = slot[o & 1];
+    if (o < nmat) {
+      // ---------------- forward ----------------
+      if (!is_b) {
+        // y_j = Linv_j z
+        T* yj = ybuf + (size_t)j * nb;
+        for (int rr = warp; rr < nb; rr += NW) {
+          const T* row = M + linv_row_off(rr);
+          T acc = 0;
+          for (int c = lane; c <= rr; c += 32) acc = fma(row[c], zbuf[c], acc);
+          acc = wsum(acc);
+          if (lane == 0) yj[rr] = acc;
+        }
+      } else {
+        // z = r_j - B_j y_{j-1}
+        const T* yp = ybuf + (size_t)(j - 1) * nb;
+        const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
+        for (int rr = warp; rr < nb; rr += NW) {
+          const int lo = b_lo(rr);
+          const T* row = M + b_row_off(nb, rr) - lo;
+          T acc = 0;
+          for (int c = lo + lane; c < nb; c += 32) acc = fma(row[c], yp[c], acc);
+          acc = wsum(acc);
+          if (lane == 0) zbuf[rr] = (T)rg[rowbase + rr] - acc;
+        }
+      }
+      __syncthreads();
+    } else {
+      // ---------------- backward ----------------
+      T acc[MAX_NB / 32];
+#pragma unroll
+      for (int q = 0; q < MAX_NB / 32; ++q) acc[q] = 0;
+      if (!is_b) {
+        // x_j = Linv_j^T w  (w = y_{h-1} for the last row)
+        const T* wv = (j == h - 1) ? ybuf + (size_t)j * nb : wbuf;
+        for (int rr = warp; rr < nb; rr += NW) {
+          const T* row = M + linv_row_off(rr);
+          const T v = wv[rr];
+#pragma unroll
+          for (int q = 0; q < MAX_NB / 32; ++q) {
+            const int c = lane + 32 * q;
+            if (c <= rr) acc[q] = fma(row[c], v, acc[q]);
+          }
+        }
+      } else {
+        // w = y_{j-1} - B_j^T x_j
+        for (int rr = warp; rr < nb; rr += NW) {
+          const int lo = b_lo(rr);
+          const T* row = M + b_row_off(nb, rr) - lo;
+          const T v = xbuf[rr];
+#pragma unroll
+          for (int q = 0; q < MAX_NB / 32; ++q) {
+            const int c = lane + 32 * q;
+            if (c >= lo && c < nb) acc[q] = fma(row[c], v, acc[q]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < MAX_NB / 32; ++q) {
+        const int c = lane + 32 * q;
+        if (c < nb) part[warp * nb + c] = acc[q];
+      }
+      __syncthreads();
+      if (!is_b) {
+        const size_t node0 = (size_t)(j0 + j) * lv.nx + i0;
+        const size_t rowbase = 2 * node0;
+        const double y = lv.L * SQ3_2 * (double)(j0 + j) - rep.y;
+        for (int c = tid; c < nb; c += NT) {
+          T s = 0;
+#pragma unroll
+          for (int ww = 0; ww < NW; ++ww) s += part[ww * nb + c];
+          xbuf[c] = s;
+          delta[rowbase + c] = s;
+          // P = V^T r (Eq. 7) for this DOF
+          const int il = c >> 1, comp = c & 1;
+          const double rv = rg[rowbase + c];
+          const double xi = lv.L * ((double)(i0 + il) + 0.5 * (double)((j0 + j) & 1)) - rep.x;
+          const double dr = (double)s * rv;
+          pacc[comp] += rv;
+          pacc[2 + 2 * comp] = fma(xi, rv, pacc[2 + 2 * comp]);
+          pacc[3 + 2 * comp] = fma(y, rv, pacc[3 + 2 * comp]);
+          pacc[6] += dr;
+          pacc[7] = fma(xi, dr, pacc[7]);
+          pacc[8] = fma(y, dr, pacc[8]);
+        }
+      } else {
+        const T* yp = ybuf + (size_t)(j - 1) * nb;
+        for (int c = tid; c < nb; c += NT) {
+          T s = 0;
+#pragma unroll
+          for (int ww = 0; ww < NW; ++ww) s += part[ww * nb + c];
+          wbuf[c] = yp[c] - s;
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0 && o + 2 < nops) issue(o + 2);
+  }
+  if (abort_flag) {
+    // let copies still in flight land before the CTA exits
+    if (tid == 0) {
+      for (int b = 0; b < 2; ++b) mbar_wait_bounded(&bars[b], 0u), mbar_wait_bounded(&bars[b], 1u);
+      atomicOr(err, (int)DEVERR_TIMEOUT);
+    }
+    return;
+  }
+  // deterministic block reduction of the nine P sums
+#pragma unroll
+  for (int m = 0; m < NMODES; ++m) {
+    const double v = warp_sum_d(pacc[m]);
+    if (lane == 0) pred[warp * NMODES + m] = v;
+  }
+  __syncthreads();
+  if (tid < NMODES) {
+    double s = 0.0;
+    for (int ww = 0; ww < NW; ++ww) s += pred[ww * NMODES + tid];
+    P[(size_t)NMODES * I + tid] = s;
+  }
+}
+
+}  // namespace
+
+size_t relax_smem_bytes(const LatView& lv, bool fp32) {
+  const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
+  const int h = lv.sy < lv.ny ? lv.sy : lv.ny;
+  return fp32 ? relax_layout<float>(2 * w, h).total_elems * sizeof(float)
+              : relax_layout<double>(2 * w, h).total_elems * sizeof(double);
+}
+
+cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
+                         const double* f64, const float* f32, const double2* r, void* delta,
+                         double* P, const IterCtl* ctl, int* err) {
+  const bool fp32 = (f32 != nullptr);
+  const size_t smem = relax_smem_bytes(lv, fp32);
+  if (fp32)
+    k_relax<float><<<lv.M, NT, smem, s>>>(lv, set_off, f32, r, (float*)delta, P, ctl, err);
+  else
+    k_relax<double><<<lv.M, NT, smem, s>>>(lv, set_off, f64, r, (double*)delta, P, ctl, err);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_relax(int max_smem) {
+  cudaError_t e = set_max_dynamic_smem(k_relax<float>, max_smem);
+  if (e != cudaSuccess) return e;
+  return set_max_dynamic_smem(k_relax<double>, max_smem);
+}
+
+}  // namespace hms

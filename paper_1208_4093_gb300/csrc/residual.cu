@@ -1,0 +1,263 @@
+// K1: update + matrix-free residual + norms (Eqs. 3, 1, 19, 2).
+//
+// One CTA per 32 x 8 node tile.  The tile and its one-node halo are staged in
+// shared memory; every staged node first gets the upper-level update of
+// Eq. 3, u += V a (translations, gradients and the relaxation modes of the
+// node's own set), so halo nodes see the same updated values their owners
+// write.  Then each node sums the axial forces of its six bars,
+//   (K u)_a = sum_b (EA/L)_ab e_ab e_ab^T (u_a - u_b),
+// and writes r = p - K u on free DOFs (0 on constrained DOFs), the new u, and
+// its share of ||r||_1, ||r||_2^2 and u.(p + r).  The last CTA to finish
+// reduces the per-CTA sums in CTA order (deterministic), turns them into the
+// relative residuals of Eq. 19 and the energy Pi = 1/2 u.K.u - u.p =
+// -1/2 u.(p + r) of Eq. 2, and decides convergence.
+#include "hms_internal.cuh"
+
+namespace hms {
+namespace {
+
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+// Deterministic block sum of N values per thread; result valid in warp 0.
+template <int N>
+__device__ inline void block_sum(double (&v)[N], double* sred) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < N; ++k) sred[warp * N + k] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = warp_sum(lane < nw ? sred[lane * N + k] : 0.0);
+  }
+}
+
+template <typename DT>
+__device__ inline double2 load_delta(const DT* d, size_t n);
+template <>
+__device__ inline double2 load_delta<double2>(const double2* d, size_t n) { return d[n]; }
+template <>
+__device__ inline double2 load_delta<float2>(const float2* d, size_t n) {
+  float2 f = d[n];
+  return make_double2((double)f.x, (double)f.y);
+}
+
+// Eq. 3 at node (i, j): u += sum_m a_m^(I) uhat_m^(I) with the modes of
+// Eqs. 9, 10, 13, 14 (zero on constrained DOFs).
+template <typename DT>
+__device__ inline double2 apply_update(const LatView& lv, double2 v, int i, int j, const DT* delta,
+                                       const double* __restrict__ a) {
+  const size_t n = (size_t)j * lv.nx + i;
+  const int I = set_of(lv, i, j);
+  const double* aI = a + (size_t)NMODES * I;
+  const double2 c = lv.rep[I];
+  const double xi = node_x(lv, i, j) - c.x;
+  const double eta = node_y(lv, j) - c.y;
+  const double2 d = load_delta(delta, n);
+  const unsigned fm = lv.fix[n];
+  const double cd = fma(__ldg(aI + 8), eta, fma(__ldg(aI + 7), xi, __ldg(aI + 6)));
+  if (!(fm & 1u)) v.x += fma(cd, d.x, fma(__ldg(aI + 3), eta, fma(__ldg(aI + 2), xi, __ldg(aI + 0))));
+  if (!(fm & 2u)) v.y += fma(cd, d.y, fma(__ldg(aI + 5), eta, fma(__ldg(aI + 4), xi, __ldg(aI + 1))));
+  return v;
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(NT) k_update_residual(
+    LatView lv, const double2* __restrict__ u_in, double2* __restrict__ u_out,
+    const double2* __restrict__ p, const DT* __restrict__ delta, const double* __restrict__ a,
+    double2* __restrict__ r, double* __restrict__ partials, unsigned* ticket, double* norms_out,
+    IterCtl* ctl, double* hist, int hist_cap) {
+  __shared__ double2 U[TY + 2][TX + 2];
+  __shared__ double sred[32 * 3];
+  __shared__ bool last;
+  int t = 0;
+  if (ctl) {
+    if (*(volatile int*)&ctl->done) return;
+    t = *(volatile int*)&ctl->t;
+  }
+  const bool upd = (a != nullptr) && (t > 0 || ctl == nullptr);
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tid = threadIdx.x;
+
+  for (int idx = tid; idx < (TX + 2) * (TY + 2); idx += NT) {
+    const int lx = idx % (TX + 2), ly = idx / (TX + 2);
+    const int i = i0 + lx - 1, j = j0 + ly - 1;
+    double2 v = make_double2(0.0, 0.0);
+    if (i >= 0 && i < lv.nx && j >= 0 && j < lv.ny) {
+      v = u_in[(size_t)j * lv.nx + i];
+      if (upd) v = apply_update(lv, v, i, j, delta, a);
+    }
+    U[ly][lx] = v;
+  }
+  __syncthreads();
+
+  const int tx = tid % TX, ty = tid / TX;
+  const int i = i0 + tx, j = j0 + ty;
+  double s[3] = {0.0, 0.0, 0.0};
+  if (i < lv.nx && j < lv.ny) {
+    const size_t n = (size_t)j * lv.nx + i;
+    const int lx = tx + 1, ly = ty + 1, off = j & 1;
+    const double2 uc = U[ly][lx];
+    // E-W bars (e = (1, 0))
+    const double kE = bar_k(lv, i, j, 0), kW = bar_k(lv, i - 1, j, 0);
+    double fx = kE * (uc.x - U[ly][lx + 1].x) + kW * (uc.x - U[ly][lx - 1].x);
+    // NE bar of this node and NE bar of the SW neighbour: e = (1/2, sqrt3/2)
+    const double kNE = bar_k(lv, i, j, 1), kSW = bar_k(lv, i - 1 + off, j - 1, 1);
+    const double2 une = U[ly + 1][lx + off], usw = U[ly - 1][lx - 1 + off];
+    const double d1x = kNE * (uc.x - une.x) + kSW * (uc.x - usw.x);
+    const double d1y = kNE * (uc.y - une.y) + kSW * (uc.y - usw.y);
+    const double p1 = fma(SQ3_2, d1y, 0.5 * d1x);
+    // NW bar of this node and NW bar of the SE neighbour: e = (-1/2, sqrt3/2)
+    const double kNW = bar_k(lv, i, j, 2), kSE = bar_k(lv, i + off, j - 1, 2);
+    const double2 unw = U[ly + 1][lx - 1 + off], use = U[ly - 1][lx + off];
+    const double d2x = kNW * (uc.x - unw.x) + kSE * (uc.x - use.x);
+    const double d2y = kNW * (uc.y - unw.y) + kSE * (uc.y - use.y);
+    const double p2 = fma(SQ3_2, d2y, -0.5 * d2x);
+    fx = fma(0.5, p1 - p2, fx);
+    const double fy = SQ3_2 * (p1 + p2);
+    const double2 pn = p[n];
+    const unsigned fm = lv.fix[n];
+    double2 rn;
+    rn.x = (fm & 1u) ? 0.0 : pn.x - fx;
+    rn.y = (fm & 2u) ? 0.0 : pn.y - fy;
+    r[n] = rn;
+    u_out[n] = uc;
+    s[0] = fabs(rn.x) + fabs(rn.y);
+    s[1] = fma(rn.x, rn.x, rn.y * rn.y);
+    s[2] = fma(uc.x, pn.x + rn.x, uc.y * (pn.y + rn.y));
+  }
+  block_sum<3>(s, sred);
+  const unsigned nblocks = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (tid == 0) {
+    partials[3 * (size_t)bid + 0] = s[0];
+    partials[3 * (size_t)bid + 1] = s[1];
+    partials[3 * (size_t)bid + 2] = s[2];
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v[3] = {0.0, 0.0, 0.0};
+  for (unsigned b = tid; b < nblocks; b += NT) {
+    v[0] += __ldcg(partials + 3 * (size_t)b + 0);
+    v[1] += __ldcg(partials + 3 * (size_t)b + 1);
+    v[2] += __ldcg(partials + 3 * (size_t)b + 2);
+  }
+  __syncthreads();
+  block_sum<3>(v, sred);
+  if (tid == 0) {
+    *ticket = 0u;  // ready for the next launch
+    if (norms_out) {
+      norms_out[0] = v[0];
+      norms_out[1] = v[1];
+      norms_out[2] = v[2];
+    }
+    if (ctl) {
+      const double R1 = ctl->p1 > 0.0 ? v[0] / ctl->p1 : 0.0;
+      const double R2 = ctl->p2 > 0.0 ? sqrt(v[1]) / ctl->p2 : 0.0;
+      const double Pi = -0.5 * v[2];
+      if (t < hist_cap && hist) {
+        hist[3 * t + 0] = R1;
+        hist[3 * t + 1] = R2;
+        hist[3 * t + 2] = Pi;
+      }
+      if (!isfinite(R1) || !isfinite(R2) || !isfinite(Pi)) {
+        ctl->status = 3;
+        ctl->err |= DEVERR_NONFINITE;
+        ctl->done = 1;
+      } else if (R1 < ctl->tol) {
+        ctl->status = 1;
+        ctl->done = 1;
+      } else if (t >= ctl->max_iter || ctl->err != 0) {
+        ctl->status = 2;
+        ctl->done = 1;
+      }
+      ctl->t = t + 1;
+    }
+  }
+}
+
+// Masks the loads on constrained DOFs and computes ||p||_1, ||p||_2 into ctl.
+__global__ void __launch_bounds__(256) k_load_norms(LatView lv, double2* __restrict__ p,
+                                                    double* __restrict__ partials, unsigned* ticket,
+                                                    IterCtl* ctl) {
+  __shared__ double sred[32 * 2];
+  __shared__ bool last;
+  const size_t nn = (size_t)lv.nx * lv.ny;
+  double s[2] = {0.0, 0.0};
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < nn;
+       n += (size_t)gridDim.x * blockDim.x) {
+    double2 v = p[n];
+    const unsigned fm = lv.fix[n];
+    if (fm & 1u) v.x = 0.0;
+    if (fm & 2u) v.y = 0.0;
+    p[n] = v;
+    s[0] += fabs(v.x) + fabs(v.y);
+    s[1] += fma(v.x, v.x, v.y * v.y);
+  }
+  block_sum<2>(s, sred);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x + 0] = s[0];
+    partials[2 * blockIdx.x + 1] = s[1];
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v[2] = {0.0, 0.0};
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+    v[0] += __ldcg(partials + 2 * b + 0);
+    v[1] += __ldcg(partials + 2 * b + 1);
+  }
+  __syncthreads();
+  block_sum<2>(v, sred);
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    ctl->p1 = v[0];
+    ctl->p2 = sqrt(v[1]);
+  }
+}
+
+}  // namespace
+
+int update_residual_blocks(const LatView& lv) {
+  return ((lv.nx + TX - 1) / TX) * ((lv.ny + TY - 1) / TY);
+}
+
+cudaError_t launch_update_residual(cudaStream_t s, const LatView& lv, const double2* u_in,
+                                   double2* u_out, const double2* p, const void* delta,
+                                   bool delta_fp32, const double* a, double2* r, double* partials,
+                                   unsigned* ticket, double* norms_out, IterCtl* ctl, double* hist,
+                                   int hist_cap, int* /*u_cur*/) {
+  dim3 grid((lv.nx + TX - 1) / TX, (lv.ny + TY - 1) / TY);
+  if (delta_fp32)
+    k_update_residual<float2><<<grid, NT, 0, s>>>(lv, u_in, u_out, p, (const float2*)delta, a, r,
+                                                  partials, ticket, norms_out, ctl, hist, hist_cap);
+  else
+    k_update_residual<double2><<<grid, NT, 0, s>>>(lv, u_in, u_out, p, (const double2*)delta, a,
+                                                   r, partials, ticket, norms_out, ctl, hist,
+                                                   hist_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_norms(cudaStream_t s, const LatView& lv, double2* p, double* partials,
+                              unsigned* ticket, IterCtl* ctl) {
+  const size_t nn = (size_t)lv.nx * lv.ny;
+  int grid = (int)((nn + 255) / 256);
+  if (grid > 1024) grid = 1024;
+  k_load_norms<<<grid, 256, 0, s>>>(lv, p, partials, ticket, ctl);
+  return cudaGetLastError();
+}
+
+}  // namespace hms
