@@ -29,9 +29,11 @@ Readings (the paper is silent on these):
   the last tile of a row or column takes the remainder;
 * q = 9 (the displacement-controlled modes only); the force-controlled modes
   10-12 of Eqs. 15-18 are not part of this iteration;
-* a mode whose diagonal entry of K_aa is <= 1e-300 (identically zero on the
-  set's free DOFs) or whose scaled Cholesky pivot is <= 1e-14 (dependent on
-  earlier modes) gets a = 0, in the fixed order (set, mode).
+* a mode whose diagonal entry of K_aa is <= 1e-300, or <= 1e-28 times the
+  largest diagonal entry among its set's nine modes (the mode vanishes on the
+  set's free DOFs up to rounding, e.g. eta-modes of a one-row set), or whose
+  scaled Cholesky pivot is <= 1e-14 (dependent on earlier modes) gets a = 0,
+  in the fixed order (set, mode).
 """
 from __future__ import annotations
 
@@ -46,6 +48,7 @@ from .truss import Truss
 
 NMODES = 9
 DROP_DIAG = 1e-300
+DROP_DIAG_REL = 1e-28
 DROP_PIVOT = 1e-14
 
 
@@ -154,17 +157,20 @@ def coarse_system(truss: Truss, V: sp.spmatrix, r: np.ndarray):
     return Kaa, np.asarray(P).reshape(-1)
 
 
-def coarse_solve(Kaa: np.ndarray, P: np.ndarray, drop_diag=DROP_DIAG, drop_pivot=DROP_PIVOT):
+def coarse_solve(Kaa: np.ndarray, P: np.ndarray, drop_diag=DROP_DIAG, drop_pivot=DROP_PIVOT,
+                 group=NMODES, drop_diag_rel=DROP_DIAG_REL):
     """Solve Eq. 8 by a Jacobi-scaled Cholesky that drops degenerate modes.
 
     With D = diag(K_aa), the matrix D^-1/2 K_aa D^-1/2 (unit diagonal) is
     factored column by column in index order; a column whose D entry is
-    <= drop_diag, or whose pivot is <= drop_pivot, is removed from the system
-    (its coefficient is 0).  Returns (a, dropped mask).
+    <= drop_diag or <= drop_diag_rel times the largest D of its group (the
+    nine modes of one set), or whose pivot is <= drop_pivot, is removed from
+    the system (its coefficient is 0).  Returns (a, dropped mask).
     """
     n = P.size
     D = np.diag(Kaa).copy()
-    active = D > drop_diag
+    gmax = np.repeat(D.reshape(-1, group).max(axis=1), group) if n % group == 0 else np.full(n, D.max())
+    active = (D > drop_diag) & (D > drop_diag_rel * gmax)
     s = np.zeros(n)
     s[active] = 1.0 / np.sqrt(D[active])
     A = s[:, None] * Kaa * s[None, :]

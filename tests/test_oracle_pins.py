@@ -249,6 +249,18 @@ def test_coarse_solve_special_cases():
     keep = np.arange(12) != 5
     assert dr2[5] and dr2.sum() == 1 and a2[5] == 0
     assert np.allclose(a2[keep], np.linalg.solve(A[np.ix_(keep, keep)], b[keep]), rtol=1e-12)
+    # a mode that vanishes up to rounding (norm 1e-16 of its set's others) is dropped
+    n9 = 18
+    E = rng.standard_normal((n9, n9))
+    E = E @ E.T + n9 * np.eye(n9)
+    sc = np.ones(n9)
+    sc[13] = 1e-16
+    E = sc[:, None] * E * sc[None, :]
+    be = sc * rng.standard_normal(n9)
+    ae, dre = hms.coarse_solve(E, be)
+    keep13 = np.arange(n9) != 13
+    assert dre[13] and dre.sum() == 1 and ae[13] == 0
+    assert np.allclose(ae[keep13], np.linalg.solve(E[np.ix_(keep13, keep13)], be[keep13]), rtol=1e-10)
     # a mode equal to twice another is dependent: the later one is dropped
     C = np.zeros((13, 13))
     C[:12, :12] = A
