@@ -83,9 +83,12 @@ typedef struct {
   double tol;                /* stop when R1 = ||K u - p||_1 / ||p||_1 < tol (Eq. 19) */
   int32_t max_iter;          /* upper-level updates per load vector (>= 0) */
   int32_t coarse_solves;     /* FP32-factor solves of Eq. 8 per update incl. FP64
-                                refinement steps (1..8); 0 = default (FP64: 4, mixed: 3) */
+                                refinement steps (1..8); 0 = default (FP64: 3, mixed: 2) */
   int32_t batch;             /* iterations per CUDA-graph launch; 0 = default (16) */
   int32_t profile;           /* 1 = time every kernel with CUDA events */
+  int32_t coarse_factor;     /* factor of Eq. 8: 0 = auto (FP64 for one- or two-node-wide
+                                set tiles, else FP32), 1 = FP32 with FP64 refinement,
+                                2 = FP64 */
 } hms_options;
 
 /* Context: one device, one CUDA stream.  device = CUDA ordinal. */

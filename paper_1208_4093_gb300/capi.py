@@ -50,7 +50,8 @@ class LatticeDesc(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
-                ("coarse_solves", ctypes.c_int32), ("batch", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("coarse_solves", ctypes.c_int32), ("batch", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("coarse_factor", ctypes.c_int32)]
 
 
 _lib = None
@@ -168,7 +169,7 @@ def hms_last_error(ctx) -> str:
 
 def hms_problem_create(ctx, nx, ny, set_sx, set_sy, *, bar_length=1.0, ea=None, ea_uniform=1.0,
                        fixed=None, fix_bottom_edge=1, precision=HMS_FP64, tol=1e-8, max_iter=1000,
-                       coarse_solves=0, batch=0, profile=0):
+                       coarse_solves=0, batch=0, profile=0, coarse_factor=0):
     """ea: host float64 [3, ny, nx] or None; fixed: host uint8 [ny, nx, 2] or None."""
     ea_a = None if ea is None else np.ascontiguousarray(ea, dtype=np.float64)
     fx_a = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
@@ -179,7 +180,8 @@ def hms_problem_create(ctx, nx, ny, set_sx, set_sy, *, bar_length=1.0, ea=None, 
     d = LatticeDesc(int(nx), int(ny), float(bar_length), None if ea_a is None else ea_a.ctypes.data,
                     float(ea_uniform), None if fx_a is None else fx_a.ctypes.data, int(fix_bottom_edge),
                     int(set_sx), int(set_sy))
-    o = Options(int(precision), float(tol), int(max_iter), int(coarse_solves), int(batch), int(profile))
+    o = Options(int(precision), float(tol), int(max_iter), int(coarse_solves), int(batch), int(profile),
+                int(coarse_factor))
     h = _P()
     _check(ctx, lib().hms_problem_create(ctx, ctypes.byref(d), ctypes.byref(o), ctypes.byref(h)))
     return h

@@ -23,6 +23,7 @@ struct hms_problem {
   hms_context* ctx = nullptr;
   LatView lv{};
   int precision = HMS_FP64, nsolve = 4, batch = 16, profile = 0, max_iter = 0;
+  bool coarse_fp64 = false;  // factor of the upper-level system in FP64 (else FP32 + FP64 refinement)
   double tol = 1e-8;
   int n_c = 0, bw = 0;
   size_t bytes = 0;
@@ -40,6 +41,7 @@ struct hms_problem {
   double2* p = nullptr;
   double2* r = nullptr;
   void* delta = nullptr;
+  void* yscratch = nullptr;  // forward-substitution vectors of every set
   double* a = nullptr;
   double* P = nullptr;
   double* slots_base = nullptr;
@@ -50,8 +52,9 @@ struct hms_problem {
   double* b = nullptr;
   double* x = nullptr;
   double* res = nullptr;
-  float* fband = nullptr;    // column + row layouts
-  float* dinv = nullptr;
+  void* lcol = nullptr;      // L in column layout (float or double)
+  void* lrow = nullptr;      // scaled band in row layout, then L in row layout
+  void* dinv = nullptr;      // inverted 32 x 32 diagonal blocks of L
   int* dropped = nullptr;
   double* partials = nullptr;
   unsigned* ticket = nullptr;
@@ -145,7 +148,7 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
                              nullptr);
   if (e != cudaSuccess) return e;
   mark();
-  e = launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->ctl, pr->err);
+  e = launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, pr->ctl, pr->err);
   if (e != cudaSuccess) return e;
   mark();
   e = launch_coarse_slots(s, lv, pr->delta, fp32(pr), false, pr->slots_it, pr->ctl);
@@ -153,11 +156,11 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
   mark();
   e = launch_coarse_band_from_slots(s, lv, pr->slots_base, pr->slots_it, pr->band, pr->ctl);
   if (e != cudaSuccess) return e;
-  e = launch_coarse_scale(s, pr->n_c, pr->bw, pr->band, pr->P, pr->sband, pr->fband, pr->scale, pr->b,
-                          pr->x, pr->dropped, pr->ctl);
+  e = launch_coarse_scale(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale,
+                          pr->b, pr->x, pr->dropped, pr->ctl);
   if (e != cudaSuccess) return e;
   mark();
-  e = launch_coarse_factor(s, pr->n_c, pr->bw, pr->fband, pr->dinv, pr->dropped, pr->ctl, pr->err);
+  e = launch_coarse_factor(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped, pr->ctl);
   if (e != cudaSuccess) return e;
   mark();
   for (int q = 0; q < pr->nsolve; ++q) {
@@ -166,8 +169,8 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
       if (e != cudaSuccess) return e;
       mark();
     }
-    e = launch_coarse_solve(s, pr->n_c, pr->bw, pr->fband, pr->dinv, pr->dropped, q == 0 ? pr->b : pr->res,
-                            pr->x, pr->scale, q == pr->nsolve - 1 ? pr->a : nullptr, pr->ctl);
+    e = launch_coarse_solve(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped,
+                            q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->ctl, pr->err);
     if (e != cudaSuccess) return e;
     mark();
   }
@@ -295,6 +298,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return fail(c, HMS_ERR_ARG, "bad precision");
   if (!(o->tol >= 0.0) || o->max_iter < 0) return fail(c, HMS_ERR_ARG, "bad tol / max_iter");
   if (o->coarse_solves < 0 || o->coarse_solves > 8) return fail(c, HMS_ERR_ARG, "coarse_solves must be in 0..8");
+  if (o->coarse_factor < 0 || o->coarse_factor > 2) return fail(c, HMS_ERR_ARG, "coarse_factor must be 0, 1 or 2");
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
 
@@ -311,7 +315,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   lv.L = d->bar_length;
   lv.k_u = d->ea ? 0.0 : d->ea_uniform / d->bar_length;
   pr->precision = o->precision;
-  pr->nsolve = o->coarse_solves > 0 ? o->coarse_solves : (o->precision == HMS_FP64 ? 4 : 3);
+  pr->nsolve = o->coarse_solves > 0 ? o->coarse_solves : (o->precision == HMS_FP64 ? 3 : 2);
   pr->batch = o->batch > 0 ? (o->batch + 1) / 2 * 2 : 16;
   pr->profile = o->profile;
   pr->tol = o->tol;
@@ -325,9 +329,24 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     delete pr;
     return fail(c, HMS_ERR_ARG, "set tile too large for the relaxation kernel's shared memory");
   }
-  if (coarse_factor_smem_bytes(pr->bw) > (size_t)maxsm || (size_t)pr->n_c * 4 > (size_t)maxsm) {
-    delete pr;
-    return fail(c, HMS_ERR_ARG, "set grid too wide for the upper-level band factorisation (Mx <= 19)");
+  {
+    // upper-level factor precision: FP64 for degenerate set shapes (one- or
+    // two-node-wide tiles give ill-conditioned upper-level systems), else FP32
+    // with FP64 refinement
+    const int wmin = std::min(lv.sx, lv.nx - (lv.Mx - 1) * lv.sx);
+    const int hmin = std::min(lv.sy, lv.ny - (lv.My - 1) * lv.sy);
+    const bool degenerate = std::min(wmin, hmin) <= 2;
+    auto fits = [&](bool f64) {
+      return coarse_factor_smem_bytes(pr->bw, f64) + 1024 <= (size_t)maxsm &&
+             coarse_solve_smem_bytes(pr->n_c, pr->bw, f64) + 1024 <= (size_t)maxsm;
+    };
+    if (o->coarse_factor == 2) pr->coarse_fp64 = true;
+    else if (o->coarse_factor == 1) pr->coarse_fp64 = false;
+    else pr->coarse_fp64 = degenerate && fits(true);
+    if (!fits(pr->coarse_fp64)) {
+      delete pr;
+      return fail(c, HMS_ERR_ARG, "set grid too wide for the upper-level band factorisation");
+    }
   }
   if (coarse_slots_smem(lv) > (size_t)maxsm) {
     delete pr;
@@ -428,6 +447,12 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     pr->delta = dl;
     CKP(cudaMemsetAsync(dl, 0, nn * sizeof(double2), s));
   }
+  {
+    const size_t ybytes = (size_t)lv.M * relax_y_stride(lv) * (fp32(pr) ? sizeof(float) : sizeof(double));
+    unsigned char* ys;
+    CKP(palloc(pr, &ys, ybytes));
+    pr->yscratch = ys;
+  }
   const int n_c = pr->n_c, bw = pr->bw;
   const size_t nband = (size_t)n_c * (bw + 1);
   CKP(palloc(pr, &pr->a, n_c));
@@ -440,8 +465,16 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   CKP(palloc(pr, &pr->b, n_c));
   CKP(palloc(pr, &pr->x, n_c));
   CKP(palloc(pr, &pr->res, n_c));
-  CKP(palloc(pr, &pr->fband, 2 * nband));
-  CKP(palloc(pr, &pr->dinv, (size_t)coarse_dinv_size(n_c)));
+  {
+    // 8 bytes per entry (FP64 factor) plus the tail read by rounded-up bulk copies
+    double *lc, *lr, *di;
+    CKP(palloc(pr, &lc, nband + 16));
+    CKP(palloc(pr, &lr, nband + 16));
+    CKP(palloc(pr, &di, (size_t)coarse_dinv_size(n_c)));
+    pr->lcol = lc;
+    pr->lrow = lr;
+    pr->dinv = di;
+  }
   CKP(palloc(pr, &pr->dropped, n_c));
   const size_t npart = (size_t)std::max(update_residual_blocks(lv), 1024) * 3;
   CKP(palloc(pr, &pr->partials, npart));
@@ -541,7 +574,7 @@ hms_status hms_solve(hms_problem* pr, int32_t nrhs, const double* loads, const d
         CKC(c, launch_iteration(pr, s, it, ev.data()));
         CKC(c, cudaMemcpyAsync(pr->ctl_host, pr->ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, s));
         CKC(c, cudaStreamSynchronize(s));
-        const int nev = 6 + 2 * (pr->nsolve - 1);
+        const int nev = 7 + 2 * (pr->nsolve - 1);  // marks recorded by launch_iteration
         const bool ran_all = !pr->ctl_host->done;
         for (int i = 0; i + 1 < nev; ++i) {
           if (i > 0 && !ran_all) break;  // after convergence only K1 did work
@@ -641,7 +674,7 @@ hms_status hms_relax(hms_problem* pr, const double* r, double* delta, double* P,
   const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
   CKC(c, cudaMemcpyAsync(pr->r, r, vb, kind_in(mem_kind), s));
   CKC(c, launch_mask_u(s, pr->lv, pr->r));
-  CKC(c, launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, nullptr, pr->err));
+  CKC(c, launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr, pr->err));
   if (fp32(pr)) {
     CKC(c, launch_f2d(s, (const float*)pr->delta, (double*)pr->u[1], 2 * nn));
     CKC(c, cudaMemcpyAsync(delta, pr->u[1], vb, kind_out(mem_kind), s));
@@ -695,13 +728,13 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
   cudaFreeAsync(dense, s);
   CKC(c, e);
   CKC(c, cudaMemcpyAsync(pr->P, P, n * sizeof(double), kind_in(mem_kind), s));
-  CKC(c, launch_coarse_scale(s, n, bw, pr->band, pr->P, pr->sband, pr->fband, pr->scale, pr->b, pr->x,
-                             pr->dropped, nullptr));
-  CKC(c, launch_coarse_factor(s, n, bw, pr->fband, pr->dinv, pr->dropped, nullptr, pr->err));
+  CKC(c, launch_coarse_scale(s, n, bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale, pr->b,
+                             pr->x, pr->dropped, nullptr));
+  CKC(c, launch_coarse_factor(s, n, bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped, nullptr));
   for (int q = 0; q < pr->nsolve; ++q) {
     if (q > 0) CKC(c, launch_coarse_residual(s, n, bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, nullptr));
-    CKC(c, launch_coarse_solve(s, n, bw, pr->fband, pr->dinv, pr->dropped, q == 0 ? pr->b : pr->res, pr->x,
-                               pr->scale, q == pr->nsolve - 1 ? pr->a : nullptr, nullptr));
+    CKC(c, launch_coarse_solve(s, n, bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped,
+                               q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, nullptr, pr->err));
   }
   CKC(c, cudaMemcpyAsync(a, pr->a, n * sizeof(double), kind_out(mem_kind), s));
   if (dropped) CKC(c, cudaMemcpyAsync(dropped, pr->dropped, n * sizeof(int32_t), kind_out(mem_kind), s));

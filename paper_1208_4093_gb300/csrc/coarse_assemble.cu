@@ -106,8 +106,6 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
   __syncthreads();
 
   const double2 repI = lv.rep[I];
-  const double ed_x[3] = {1.0, 0.5, -0.5};
-  const double ed_y[3] = {0.0, SQ3_2, SQ3_2};
   double reg[NREG];
   double gen[NGEN];
 #pragma unroll
@@ -123,6 +121,7 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
     const unsigned fa = lv.fix[na];
     const double2 da = FULL ? make_double2(0.0, 0.0) : ld_delta(delta, na);
     const double xa = node_x(lv, i, j), ya = node_y(lv, j);
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double k = bar_k(lv, i, j, d);
       if (k == 0.0) continue;
@@ -131,7 +130,7 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
       const size_t nbn = (size_t)jb * lv.nx + ib;
       const unsigned fb = lv.fix[nbn];
       const double2 db = FULL ? make_double2(0.0, 0.0) : ld_delta(delta, nbn);
-      const double ex = ed_x[d], ey = ed_y[d];
+      const double ex = (d == 0) ? 1.0 : (d == 1 ? 0.5 : -0.5), ey = (d == 0) ? 0.0 : SQ3_2;
       const double xb = node_x(lv, ib, jb), yb = node_y(lv, jb);
       const int dxs = (ib >= i0 + w) ? 1 : (ib < i0 ? -1 : 0);
       const int dys = (jb >= j0 + h) ? 1 : 0;
@@ -242,8 +241,9 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
       const double L = lv.L;
       // constants s_2..s_5 of a regular bar of direction d: -L e_x^2, -L e_x e_y, -L e_y e_x, -L e_y^2
       if (ll >= 2 && ll <= 5) {
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
-          const double ex = ed_x[d], ey = ed_y[d];
+          const double ex = (d == 0) ? 1.0 : (d == 1 ? 0.5 : -0.5), ey = (d == 0) ? 0.0 : SQ3_2;
           const double c = (ll == 2) ? -L * ex * ex : (ll == 5 ? -L * ey * ey : -L * ex * ey);
           v = fma(c, sred[3 * d + (mm - 6)], v);
         }
@@ -341,8 +341,9 @@ __global__ void k_dense_from_band(int n, int bw, const double* __restrict__ band
   }
 }
 
-// Jacobi scaling (s_i = D_ii^-1/2; modes with D_ii <= 1e-300 are dropped),
-// right-hand side b = s P, and the solution accumulator x = 0.
+// Jacobi scaling (s_i = D_ii^-1/2), right-hand side b = s P, the solution
+// accumulator x = 0, and the modes that vanish: D_ii <= 1e-300, or <= 1e-28
+// times the largest diagonal of the set's nine modes (zero up to rounding).
 __global__ void k_coarse_diag(int n, int bw, const double* __restrict__ band,
                               const double* __restrict__ P, double* __restrict__ scale,
                               double* __restrict__ b, double* __restrict__ x, int* __restrict__ dropped,
@@ -350,7 +351,10 @@ __global__ void k_coarse_diag(int n, int bw, const double* __restrict__ band,
   if (ctl && *(volatile const int*)&ctl->done) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double D = band[(size_t)i * (bw + 1)];
-    const bool drop = !(D > 1e-300);
+    const int g0 = i - i % NMODES;
+    double dmax = 0.0;
+    for (int m = 0; m < NMODES && g0 + m < n; ++m) dmax = fmax(dmax, band[(size_t)(g0 + m) * (bw + 1)]);
+    const bool drop = !(D > 1e-300) || !(D > 1e-28 * dmax);
     const double s = drop ? 0.0 : 1.0 / sqrt(D);
     scale[i] = s;
     b[i] = s * P[i];
@@ -359,12 +363,63 @@ __global__ void k_coarse_diag(int n, int bw, const double* __restrict__ band,
   }
 }
 
+// Modes that depend on earlier modes of the same set get a = 0.  Sets have
+// disjoint supports, so the columns of V can only be dependent within a set:
+// the Jacobi-scaled 9 x 9 diagonal block of every set is factored in FP64 in
+// mode order, and a mode whose pivot is <= 1e-14 is dropped (the rule of the
+// full upper-level system, decided where FP64 resolves it).
+__global__ void k_coarse_set_drops(int nsets, int bw, const double* __restrict__ band,
+                                   const double* __restrict__ scale, int* __restrict__ dropped,
+                                   const IterCtl* ctl) {
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nsets) return;
+  double A[NMODES][NMODES];
+  bool dr[NMODES];
+#pragma unroll
+  for (int m = 0; m < NMODES; ++m) {
+    dr[m] = dropped[NMODES * I + m] != 0;
+#pragma unroll
+    for (int l = 0; l < NMODES; ++l) {
+      const int lo = l < m ? l : m, hi = l < m ? m : l;
+      const int c = NMODES * I + lo;
+      A[m][l] = scale[NMODES * I + m] * band[(size_t)c * (bw + 1) + (hi - lo)] * scale[NMODES * I + l];
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NMODES; ++m) {
+    if (dr[m]) continue;
+    double piv = A[m][m];
+#pragma unroll
+    for (int k = 0; k < m; ++k) piv -= A[m][k] * A[m][k];
+    if (!(piv > 1e-14)) {
+      dr[m] = true;  // its column of L is zero
+#pragma unroll
+      for (int l = m + 1; l < NMODES; ++l) A[l][m] = 0.0;
+      continue;
+    }
+    const double d = sqrt(piv);
+    A[m][m] = d;
+#pragma unroll
+    for (int l = m + 1; l < NMODES; ++l) {
+      if (dr[l]) continue;
+      double v = A[l][m];
+#pragma unroll
+      for (int k = 0; k < m; ++k) v -= A[l][k] * A[m][k];
+      A[l][m] = v / d;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NMODES; ++m) dropped[NMODES * I + m] = dr[m] ? 1 : 0;
+}
+
 // Scaled band in FP64 (column layout for the residual's upper part and row
-// layout for its lower part) and its FP32 copy for the factorisation.
+// layout for its lower part) and the factor's input in row layout, in T.
+template <typename T>
 __global__ void k_coarse_scale_band(int n, int bw, const double* __restrict__ band,
                                     const double* __restrict__ scale, const int* __restrict__ dropped,
                                     double* __restrict__ sband, double* __restrict__ sbandR,
-                                    float* __restrict__ fband, const IterCtl* ctl) {
+                                    T* __restrict__ frow, double* __restrict__ b, const IterCtl* ctl) {
   if (ctl && *(volatile const int*)&ctl->done) return;
   const size_t total = (size_t)n * (bw + 1);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
@@ -380,8 +435,11 @@ __global__ void k_coarse_scale_band(int n, int bw, const double* __restrict__ ba
       }
     }
     sband[q] = v;
-    fband[q] = (float)v;
-    if (row < n) sbandR[(size_t)row * (bw + 1) + k] = v;
+    if (row < n) {
+      sbandR[(size_t)row * (bw + 1) + k] = v;
+      frow[(size_t)row * (bw + 1) + k] = (T)v;
+    }
+    if (k == 0 && dropped[col]) b[col] = 0.0;
   }
 }
 
@@ -450,15 +508,22 @@ cudaError_t launch_coarse_dense_from_band(cudaStream_t s, int n, int bw, const d
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_scale(cudaStream_t s, int n, int bw, const double* band, const double* P,
-                                double* sband, float* fband, double* scale, double* b, double* x,
-                                int* dropped, const IterCtl* ctl) {
+cudaError_t launch_coarse_scale(cudaStream_t s, int n, int bw, bool fp64, const double* band, const double* P,
+                                double* sband, void* frow, double* scale, double* b, double* x, int* dropped,
+                                const IterCtl* ctl) {
   k_coarse_diag<<<grid_for(n), 256, 0, s>>>(n, bw, band, P, scale, b, x, dropped, ctl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const int nsets = n / NMODES;
+  k_coarse_set_drops<<<(nsets + 127) / 128, 128, 0, s>>>(nsets, bw, band, scale, dropped, ctl);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   double* sbandR = sband + (size_t)n * (bw + 1);
-  k_coarse_scale_band<<<grid_for((size_t)n * (bw + 1)), 256, 0, s>>>(n, bw, band, scale, dropped,
-                                                                     sband, sbandR, fband, ctl);
+  const int g = grid_for((size_t)n * (bw + 1));
+  if (fp64)
+    k_coarse_scale_band<double><<<g, 256, 0, s>>>(n, bw, band, scale, dropped, sband, sbandR, (double*)frow, b, ctl);
+  else
+    k_coarse_scale_band<float><<<g, 256, 0, s>>>(n, bw, band, scale, dropped, sband, sbandR, (float*)frow, b, ctl);
   return cudaGetLastError();
 }
 

@@ -122,8 +122,9 @@ cudaError_t launch_set_factor(cudaStream_t s, const LatView& lv, const long long
 // relax.cu
 cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
                          const double* f64, const float* f32, const double2* r, void* delta,
-                         double* P, const IterCtl* ctl, int* err);
+                         double* P, void* yscratch, const IterCtl* ctl, int* err);
 size_t relax_smem_bytes(const LatView& lv, bool fp32);
+long long relax_y_stride(const LatView& lv);
 // coarse.cu
 cudaError_t launch_coarse_slots(cudaStream_t s, const LatView& lv, const void* delta, bool delta_fp32,
                                 bool full, double* slots, const IterCtl* ctl);
@@ -134,17 +135,18 @@ cudaError_t launch_coarse_band_from_dense(cudaStream_t s, int n, int bw, const d
                                           double* band);
 cudaError_t launch_coarse_dense_from_band(cudaStream_t s, int n, int bw, const double* band,
                                           double* dense);
-cudaError_t launch_coarse_scale(cudaStream_t s, int n, int bw, const double* band, const double* P,
-                                double* sband, float* fband, double* scale, double* b,
-                                double* x, int* dropped, const IterCtl* ctl);
-cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, float* fband, float* dinv,
-                                 int* dropped, const IterCtl* ctl, int* err);
-cudaError_t launch_coarse_solve(cudaStream_t s, int n, int bw, const float* fband, const float* dinv,
-                                const int* dropped, const double* res, double* x, const double* scale,
-                                double* a_out, const IterCtl* ctl);
+cudaError_t launch_coarse_scale(cudaStream_t s, int n, int bw, bool fp64, const double* band, const double* P,
+                                double* sband, void* frow, double* scale, double* b, double* x, int* dropped,
+                                const IterCtl* ctl);
+cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, bool fp64, void* lrow, void* lcol, void* dinv,
+                                 int* dropped, const IterCtl* ctl);
+cudaError_t launch_coarse_solve(cudaStream_t s, int n, int bw, bool fp64, const void* lcol, const void* lrow,
+                                const void* dinv, const int* dropped, const double* res, double* x,
+                                const double* scale, double* a_out, const IterCtl* ctl, int* err);
 cudaError_t launch_coarse_residual(cudaStream_t s, int n, int bw, const double* sband, const double* b,
                                    const double* x, const int* dropped, double* res, const IterCtl* ctl);
-size_t coarse_factor_smem_bytes(int bw);
+size_t coarse_factor_smem_bytes(int bw, bool fp64);
+size_t coarse_solve_smem_bytes(int n, int bw, bool fp64);
 int coarse_dinv_size(int n);
 size_t coarse_slots_smem(const LatView& lv);
 // one-time function attributes (max dynamic shared memory), per device

@@ -41,20 +41,21 @@ __device__ inline float warp_sum_f(float v) {
 __device__ inline double wsum(double v) { return warp_sum_d(v); }
 __device__ inline float wsum(float v) { return warp_sum_f(v); }
 
+constexpr int NSLOT = 3;  // matrices staged in shared memory (two in flight while one is applied)
+
 struct RelaxSmem {
-  size_t slot_elems, y_off, z_off, w_off, x_off, part_off, total_elems;
+  size_t slot_elems, ycur_off, z_off, w_off, x_off, part_off, total_elems;
 };
 
 template <typename T>
-__host__ __device__ inline RelaxSmem relax_layout(int nb, int h) {
+__host__ __device__ inline RelaxSmem relax_layout(int nb) {
   RelaxSmem L;
   long long ls = linv_size(nb), bs = b_size(nb);
   L.slot_elems = (size_t)(ls > bs ? ls : bs);
-  // keep every region 16-byte aligned
-  const size_t a = 16 / sizeof(T);
+  const size_t a = 16 / sizeof(T);  // keep every region 16-byte aligned
   auto up = [a](size_t n) { return (n + a - 1) / a * a; };
-  L.y_off = up(2 * L.slot_elems);
-  L.z_off = up(L.y_off + (size_t)h * nb);
+  L.ycur_off = up(NSLOT * L.slot_elems);
+  L.z_off = up(L.ycur_off + nb);
   L.w_off = up(L.z_off + nb);
   L.x_off = up(L.w_off + nb);
   L.part_off = up(L.x_off + nb);
@@ -66,9 +67,10 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __restrict__ set_off,
                                               const T* __restrict__ fac, const double2* __restrict__ r,
                                               T* __restrict__ delta, double* __restrict__ P,
-                                              const IterCtl* ctl, int* err) {
+                                              T* __restrict__ yglob, long long ystride, const IterCtl* ctl,
+                                              int* err) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ uint64_t bars[2];
+  __shared__ uint64_t bars[NSLOT];
   __shared__ double pred[NW * NMODES];
   __shared__ int abort_flag;
   if (ctl && *(volatile const int*)&ctl->done) return;
@@ -79,43 +81,37 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
   const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
   const int w = min(lv.sx, lv.nx - i0), h = min(lv.sy, lv.ny - j0);
   const int nb = 2 * w;
-  const RelaxSmem LY = relax_layout<T>(nb, h);
+  const RelaxSmem LY = relax_layout<T>(nb);
   T* sm = reinterpret_cast<T*>(smraw);
-  T* slot[2] = {sm, sm + LY.slot_elems};
-  T* ybuf = sm + LY.y_off;
+  T* ycur = sm + LY.ycur_off;  // the latest y_j of the forward pass
   T* zbuf = sm + LY.z_off;
   T* wbuf = sm + LY.w_off;
   T* xbuf = sm + LY.x_off;
   T* part = sm + LY.part_off;
+  T* yg = yglob + (size_t)I * ystride;  // all y_j, read back by the backward pass
   const T* fset = fac + set_off[I];
   const double* rg = reinterpret_cast<const double*>(r);
   const int nmat = 2 * h - 1;
   const int nops = 2 * nmat;
 
   auto mat_of_op = [&](int o) { return o < nmat ? o : 2 * nmat - 1 - o; };
-  auto mat_bytes = [&](int k) {
-    return (uint32_t)(((k & 1) ? b_size(nb) : linv_size(nb)) * sizeof(T));
-  };
   auto issue = [&](int o) {
     const int k = mat_of_op(o);
-    uint64_t* bar = &bars[o & 1];
-    const uint32_t bytes = mat_bytes(k);
+    uint64_t* bar = &bars[o % NSLOT];
+    const uint32_t bytes = (uint32_t)(((k & 1) ? b_size(nb) : linv_size(nb)) * sizeof(T));
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, bytes);
-    bulk_g2s(slot[o & 1], fset + mat_off(nb, k), bytes, bar);
+    bulk_g2s(sm + (size_t)(o % NSLOT) * LY.slot_elems, fset + mat_off(nb, k), bytes, bar);
   };
 
   if (tid == 0) {
     abort_flag = 0;
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int k = 0; k < NSLOT; ++k) mbar_init(&bars[k], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0) {
-    issue(0);
-    if (nops > 1) issue(1);
-  }
+  if (tid == 0)
+    for (int o = 0; o < NSLOT - 1 && o < nops; ++o) issue(o);
   // z = r_0
   const size_t rowbase0 = 2 * ((size_t)j0 * lv.nx + i0);
   for (int t = tid; t < nb; t += NT) zbuf[t] = (T)rg[rowbase0 + t];
@@ -129,36 +125,60 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
     const int k = mat_of_op(o);
     const bool is_b = (k & 1) != 0;
     const int j = is_b ? (k + 1) / 2 : k / 2;
-    if (!mbar_wait_bounded(&bars[o & 1], (uint32_t)((o >> 1) & 1))) abort_flag = 1;
+    if (!mbar_wait_bounded(&bars[o % NSLOT], (uint32_t)((o / NSLOT) & 1))) abort_flag = 1;
     __syncthreads();
     if (abort_flag) break;
-    const T* M = slot[o & 1];
+    // the slot of op o - 1 is free: stream op o + NSLOT - 1 into it
+    if (tid == 0 && o + NSLOT - 1 < nops) issue(o + NSLOT - 1);
+    const T* M = sm + (size_t)(o % NSLOT) * LY.slot_elems;
     if (o < nmat) {
-      // ---------------- forward ----------------
-      if (!is_b) {
-        // y_j = Linv_j z
-        T* yj = ybuf + (size_t)j * nb;
-        for (int rr = warp; rr < nb; rr += NW) {
-          const T* row = M + linv_row_off(rr);
-          T acc = 0;
-          for (int c = lane; c <= rr; c += 32) acc = fma(row[c], zbuf[c], acc);
-          acc = wsum(acc);
-          if (lane == 0) yj[rr] = acc;
+      // ---------------- forward: four rows per warp at a time ----------------
+      const T* vin = is_b ? ycur : zbuf;  // B_j y_{j-1} or Linv_j z
+      T res4[4];
+      for (int rb = warp; rb < nb; rb += 4 * NW) {
+        T acc[4] = {0, 0, 0, 0};
+        int rr[4], lo[4];
+        const T* row[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          rr[q] = rb + q * NW;
+          const int rq = rr[q] < nb ? rr[q] : nb - 1;
+          lo[q] = is_b ? b_lo(rq) : 0;
+          row[q] = is_b ? M + b_row_off(nb, rq) - lo[q] : M + linv_row_off(rq);
         }
-      } else {
-        // z = r_j - B_j y_{j-1}
-        const T* yp = ybuf + (size_t)(j - 1) * nb;
-        const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
-        for (int rr = warp; rr < nb; rr += NW) {
-          const int lo = b_lo(rr);
-          const T* row = M + b_row_off(nb, rr) - lo;
-          T acc = 0;
-          for (int c = lo + lane; c < nb; c += 32) acc = fma(row[c], yp[c], acc);
-          acc = wsum(acc);
-          if (lane == 0) zbuf[rr] = (T)rg[rowbase + rr] - acc;
+        const int cmax = is_b ? nb - 1 : min(rr[3], nb - 1);
+        for (int c = lo[0] + lane; c <= cmax; c += 32) {
+          const T v = vin[c];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const bool in = rr[q] < nb && c >= lo[q] && (is_b || c <= rr[q]);
+            if (in) acc[q] = fma(row[q][c], v, acc[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) res4[q] = wsum(acc[q]);
+        if (lane == 0) {
+          const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (rr[q] >= nb) continue;
+            if (is_b) {
+              zbuf[rr[q]] = (T)rg[rowbase + rr[q]] - res4[q];
+            } else {
+              part[rr[q]] = res4[q];  // y_j, copied to ycur below
+            }
+          }
         }
       }
       __syncthreads();
+      if (!is_b) {
+        for (int c = tid; c < nb; c += NT) {
+          const T v = part[c];
+          ycur[c] = v;
+          yg[(size_t)j * nb + c] = v;
+        }
+        __syncthreads();
+      }
     } else {
       // ---------------- backward ----------------
       T acc[MAX_NB / 32];
@@ -166,7 +186,7 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
       for (int q = 0; q < MAX_NB / 32; ++q) acc[q] = 0;
       if (!is_b) {
         // x_j = Linv_j^T w  (w = y_{h-1} for the last row)
-        const T* wv = (j == h - 1) ? ybuf + (size_t)j * nb : wbuf;
+        const T* wv = (j == h - 1) ? ycur : wbuf;
         for (int rr = warp; rr < nb; rr += NW) {
           const T* row = M + linv_row_off(rr);
           const T v = wv[rr];
@@ -198,7 +218,7 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
       if (!is_b) {
         const size_t node0 = (size_t)(j0 + j) * lv.nx + i0;
         const size_t rowbase = 2 * node0;
-        const double y = lv.L * SQ3_2 * (double)(j0 + j) - rep.y;
+        const double eta = lv.L * SQ3_2 * (double)(j0 + j) - rep.y;
         for (int c = tid; c < nb; c += NT) {
           T s = 0;
 #pragma unroll
@@ -210,15 +230,21 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
           const double rv = rg[rowbase + c];
           const double xi = lv.L * ((double)(i0 + il) + 0.5 * (double)((j0 + j) & 1)) - rep.x;
           const double dr = (double)s * rv;
-          pacc[comp] += rv;
-          pacc[2 + 2 * comp] = fma(xi, rv, pacc[2 + 2 * comp]);
-          pacc[3 + 2 * comp] = fma(y, rv, pacc[3 + 2 * comp]);
+          if (comp == 0) {
+            pacc[0] += rv;
+            pacc[2] = fma(xi, rv, pacc[2]);
+            pacc[3] = fma(eta, rv, pacc[3]);
+          } else {
+            pacc[1] += rv;
+            pacc[4] = fma(xi, rv, pacc[4]);
+            pacc[5] = fma(eta, rv, pacc[5]);
+          }
           pacc[6] += dr;
           pacc[7] = fma(xi, dr, pacc[7]);
-          pacc[8] = fma(y, dr, pacc[8]);
+          pacc[8] = fma(eta, dr, pacc[8]);
         }
       } else {
-        const T* yp = ybuf + (size_t)(j - 1) * nb;
+        const T* yp = yg + (size_t)(j - 1) * nb;
         for (int c = tid; c < nb; c += NT) {
           T s = 0;
 #pragma unroll
@@ -228,12 +254,11 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
       }
       __syncthreads();
     }
-    if (tid == 0 && o + 2 < nops) issue(o + 2);
   }
   if (abort_flag) {
     // let copies still in flight land before the CTA exits
     if (tid == 0) {
-      for (int b = 0; b < 2; ++b) mbar_wait_bounded(&bars[b], 0u), mbar_wait_bounded(&bars[b], 1u);
+      for (int b2 = 0; b2 < NSLOT; ++b2) mbar_wait_bounded(&bars[b2], 0u), mbar_wait_bounded(&bars[b2], 1u);
       atomicOr(err, (int)DEVERR_TIMEOUT);
     }
     return;
@@ -256,20 +281,27 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
 
 size_t relax_smem_bytes(const LatView& lv, bool fp32) {
   const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
+  return fp32 ? relax_layout<float>(2 * w).total_elems * sizeof(float)
+              : relax_layout<double>(2 * w).total_elems * sizeof(double);
+}
+
+long long relax_y_stride(const LatView& lv) {
+  const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
   const int h = lv.sy < lv.ny ? lv.sy : lv.ny;
-  return fp32 ? relax_layout<float>(2 * w, h).total_elems * sizeof(float)
-              : relax_layout<double>(2 * w, h).total_elems * sizeof(double);
+  return 2LL * w * h;
 }
 
 cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
                          const double* f64, const float* f32, const double2* r, void* delta,
-                         double* P, const IterCtl* ctl, int* err) {
+                         double* P, void* yscratch, const IterCtl* ctl, int* err) {
   const bool fp32 = (f32 != nullptr);
   const size_t smem = relax_smem_bytes(lv, fp32);
+  const long long ys = relax_y_stride(lv);
   if (fp32)
-    k_relax<float><<<lv.M, NT, smem, s>>>(lv, set_off, f32, r, (float*)delta, P, ctl, err);
+    k_relax<float><<<lv.M, NT, smem, s>>>(lv, set_off, f32, r, (float*)delta, P, (float*)yscratch, ys, ctl, err);
   else
-    k_relax<double><<<lv.M, NT, smem, s>>>(lv, set_off, f64, r, (double*)delta, P, ctl, err);
+    k_relax<double><<<lv.M, NT, smem, s>>>(lv, set_off, f64, r, (double*)delta, P, (double*)yscratch, ys, ctl,
+                                           err);
   return cudaGetLastError();
 }
 

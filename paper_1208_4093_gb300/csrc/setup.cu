@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* Bprev = scratch + (size_t)blockIdx.x * b_size(MAX_NB);
   __shared__ int bad;
+  __shared__ double diag0[MAX_NB];
 
   for (int I = blockIdx.x; I < lv.M; I += gridDim.x) {
     const int Ix = I % lv.Mx, Iy = I / lv.Mx;
@@ -85,6 +86,8 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
         }
       }
       __syncthreads();
+      for (int k = tid; k < nb; k += NT) diag0[k] = S[pk(k, k)];
+      __syncthreads();
       // 2. Schur update S -= B_j B_j^T  (B_j = L_{j,j-1} from the previous row)
       if (jj > 0) {
         for (int r = warp; r < nb; r += NT / 32) {
@@ -99,11 +102,12 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
         }
         __syncthreads();
       }
-      // 3. Cholesky of S in place
+      // 3. Cholesky of S in place; a pivot below 1e-12 of the DOF's own
+      //    stiffness K_kk means k^Inner is singular to working precision
       for (int k = 0; k < nb; ++k) {
         if (tid == 0) {
           double piv = S[pk(k, k)];
-          if (!(piv > 0.0)) {
+          if (!(piv > 1e-12 * diag0[k])) {
             bad = 1;
             piv = 1.0;
           }
