@@ -1,0 +1,112 @@
+"""Full-size parity on the benchmarked workload: the 1024 x 1024 lattice with
+lognormal(0, 0.3) EA, 16 x 16 sets of 64 x 64 nodes, seed-0 loads, in the
+launch configuration bench.py times.
+
+The expected values are the oracle's own run to R1 < 1e-10 (written by
+tests/golden/make_golden.py --full): its update counts, residual history and
+the displacement at 2000 seeded DOFs after updates 1, 2, 3, 10, 100 and at
+convergence.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from workloads import CASES
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "lattice1024_lognormal_history.json")
+
+
+@pytest.fixture(scope="module")
+def golden():
+    return json.load(open(GOLDEN))
+
+
+@pytest.fixture(scope="module")
+def workload():
+    c = CASES["lattice1024_lognormal_fp64"]
+    return c, c.ea_array(), c.load_array().reshape(1, -1)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b)
+
+
+def test_fp64_full_solve_against_oracle_run(hms_ctx, golden, workload):
+    from paper_1208_4093_gb300 import capi
+    c, ea, p = workload
+    idx = np.array(golden["sample_dofs"])
+    pr = capi.hms_problem_create(hms_ctx, c.nx, c.ny, c.sx, c.sy, ea=ea, precision=capi.HMS_FP64, tol=1e-10,
+                                 max_iter=2000)
+    try:
+        u = np.empty_like(p)
+        hist = np.full((1, 2001, 3), np.nan)
+        its = np.zeros(1, np.int32)
+        capi.hms_solve(hms_ctx, pr, p, u, hist=hist, iters=its)
+        h = np.array(golden["history"])
+        assert abs(int(its[0]) - golden["iterations"]) <= 1
+        r1 = hist[0, :, 0]
+        assert int(np.argmax(r1 < 1e-8)) == golden["first_below_1e-8"]
+        n = min(int(its[0]), golden["iterations"])
+        big = h[:n + 1, 0] > 1e-8
+        assert np.allclose(hist[0, :n + 1][big, :2], h[:n + 1][big, :2], rtol=1e-6)
+        assert np.allclose(hist[0, :n + 1, 2], h[:n + 1, 2], rtol=1e-10)
+        assert rel(u[0, idx], np.array(golden["samples"]["final"])) < 1e-9
+    finally:
+        capi.hms_problem_destroy(pr)
+
+
+@pytest.mark.parametrize("k", ["1", "2", "3", "10", "100"])
+def test_fp64_trajectory_samples(hms_ctx, golden, workload, k):
+    """T1 at full size: the iterate after k updates, at 2000 sampled DOFs."""
+    from paper_1208_4093_gb300 import capi
+    c, ea, p = workload
+    idx = np.array(golden["sample_dofs"])
+    pr = capi.hms_problem_create(hms_ctx, c.nx, c.ny, c.sx, c.sy, ea=ea, precision=capi.HMS_FP64, tol=0.0,
+                                 max_iter=int(k))
+    try:
+        u = np.empty_like(p)
+        capi.hms_solve(hms_ctx, pr, p, u, allow_no_convergence=True)
+        assert rel(u[0, idx], np.array(golden["samples"][k])) < 1e-9
+    finally:
+        capi.hms_problem_destroy(pr)
+
+
+def test_mixed_full_solve_against_oracle_run(hms_ctx, golden, workload):
+    """The mixed path (FP32 relaxation) reaches the same solution within 1e-8."""
+    from paper_1208_4093_gb300 import capi
+    c, ea, p = workload
+    idx = np.array(golden["sample_dofs"])
+    pr = capi.hms_problem_create(hms_ctx, c.nx, c.ny, c.sx, c.sy, ea=ea, precision=capi.HMS_MIXED, tol=1e-10,
+                                 max_iter=3000)
+    try:
+        u = np.empty_like(p)
+        its = np.zeros(1, np.int32)
+        capi.hms_solve(hms_ctx, pr, p, u, iters=its)
+        assert rel(u[0, idx], np.array(golden["samples"]["final"])) < 1e-8
+        # the FP32 relaxation changes the search directions, not the rate
+        assert abs(int(its[0]) - golden["iterations"]) <= 0.05 * golden["iterations"]
+    finally:
+        capi.hms_problem_destroy(pr)
+
+
+def test_residual_of_gpu_solution_by_oracle(hms_ctx, workload):
+    """Property that holds at any size: the oracle's own K (FP64, assembled
+    bar by bar) confirms the GPU's converged displacement meets Eq. 19."""
+    from oracle import truss
+    from paper_1208_4093_gb300 import capi
+    c, ea, p = workload
+    pr = capi.hms_problem_create(hms_ctx, c.nx, c.ny, c.sx, c.sy, ea=ea, precision=capi.HMS_MIXED, tol=1e-8,
+                                 max_iter=3000)
+    try:
+        u = np.empty_like(p)
+        capi.hms_solve(hms_ctx, pr, p, u)
+    finally:
+        capi.hms_problem_destroy(pr)
+    tr = truss.Truss(c.nx, c.ny, ea)
+    pf = tr.free * p[0]
+    r = tr.residual(pf, u[0])
+    assert np.abs(r).sum() / np.abs(pf).sum() < 1e-8
