@@ -66,8 +66,10 @@ __device__ inline double wsum(double v) {
   for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
   return v;
 }
-__device__ inline float tsqrt(float x) { return sqrtf(x); }
-__device__ inline double tsqrt(double x) { return sqrt(x); }
+// 1/sqrt(x): the hardware approximation in FP32 (the factor only needs to be a
+// good preconditioner: FP64 refinement restores the accuracy), exact in FP64
+__device__ inline float trsqrt(float x) { return rsqrtf(x); }
+__device__ inline double trsqrt(double x) { return 1.0 / sqrt(x); }
 
 // Column C of the register-resident Cholesky of an NB x NB diagonal block
 // (lane = row; lanes >= NB hold zero rows).  A dropped column becomes a unit column with a zero row.
@@ -76,8 +78,8 @@ __device__ __forceinline__ void diag_steps(T (&a)[NB], unsigned dmask, int lane,
   if constexpr (C < NB) {
     const T piv = __shfl_sync(0xffffffffu, a[C], C);
     const bool drop = ((dmask >> C) & 1u) != 0 || !(piv > Tau<T>::v);
-    const T d = drop ? T(1) : tsqrt(piv);
-    const T inv = T(1) / d;
+    const T inv = drop ? T(1) : trsqrt(piv);
+    const T d = drop ? T(1) : piv * inv;
     const bool mine = lane == C;
     const T acl = a[C];
     a[C] = mine ? d : (lane > C ? (drop ? T(0) : acl * inv) : acl);
@@ -129,14 +131,17 @@ __device__ __forceinline__ void factor_diag_block(T (&a)[NB], int k, int nbk, in
   if (lane == 0) *dropblk = dout;
   __syncwarp();
   if (lane < nbk) dropped[k + lane] = (dout >> lane) & 1u;
-  // X = L^-1: lane c computes column c
+  // X = L^-1, lane c computes column c column-oriented: once x_q is known it
+  // is subtracted from every later row, so the dependent chain is NB steps long
   T x[NB];
 #pragma unroll
-  for (int r = 0; r < NB; ++r) {
-    T acc = (r == lane) ? T(1) : T(0);
+  for (int r = 0; r < NB; ++r) x[r] = (r == lane) ? T(1) : T(0);
 #pragma unroll
-    for (int q = 0; q < r; ++q) acc = fma(-Ls[r * (NB + 1) + q], x[q], acc);
-    x[r] = (r >= lane) ? acc / Ls[r * (NB + 1) + r] : T(0);
+  for (int q = 0; q < NB; ++q) {
+    const T xq = (q >= lane) ? x[q] / Ls[q * (NB + 1) + q] : T(0);
+    x[q] = xq;
+#pragma unroll
+    for (int r = q + 1; r < NB; ++r) x[r] = fma(-Ls[r * (NB + 1) + q], xq, x[r]);
   }
   if (lane < NB) {
 #pragma unroll
@@ -233,21 +238,25 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
       }
     }
     __syncthreads();
+    // (a2) rank-NB update of the next diagonal block, by all threads
+    const int nbk2 = (K + 1 < nblk) ? min(NB, n - k1) : 0;
+    for (int q = tid; q < NB * NB; q += FTF) {
+      const int l = q / NB, j = q - l * NB;
+      if (l < nbk2 && j <= l && l < np && l - j <= bw) {
+        T v = T(0);
+        for (int c = 0; c < nbk; ++c) v = fma(Pc[c * pstr + l], Pc[c * pstr + j], v);
+        Aw[(size_t)((k1 + l) % W) * ldw + (l - j)] -= v;
+      }
+    }
+    __syncthreads();
     if (warp == 0) {
-      // (b0) look-ahead: update and factor the diagonal block K+1
+      // (b0) look-ahead: factor the diagonal block K+1
       if (K + 1 < nblk) {
-        const int nbk2 = min(NB, n - k1);
         T a[NB];
-        const int row = k1 + lane;
-        const size_t rbase = (size_t)(row % W) * ldw;
+        const size_t rbase = (size_t)((k1 + lane) % W) * ldw;
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-          T v = (lane < nbk2 && j <= lane && lane - j <= bw) ? Aw[rbase + (lane - j)] : T(0);
-          if (lane < nbk2 && lane < np && j <= lane) {  // panel rows beyond the band of block K are zero
-            for (int c = 0; c < nbk; ++c) v = fma(-Pc[c * pstr + lane], Pc[c * pstr + j], v);
-          }
-          a[j] = v;
-        }
+        for (int j = 0; j < NB; ++j)
+          a[j] = (lane < nbk2 && j <= lane && lane - j <= bw) ? Aw[rbase + (lane - j)] : T(0);
         factor_diag_block<T>(a, k1, nbk2, lane, dropped, fs + LY.ls + nxt * NB * (NB + 1),
                              fs + LY.xs + nxt * NB * (NB + 1), dinv, &dropblk[nxt]);
       }
@@ -375,7 +384,7 @@ __global__ void __launch_bounds__(FTS) k_coarse_solve(int n, int bw, const T* __
     if (!mbar_wait_bounded(&bars[o % S], (uint32_t)((o / S) & 1))) abort_flag = 1;
     __syncthreads();
     if (abort_flag) break;
-    if (tid == 0 && o + S - 1 < nops) issue(o + S - 1);
+    if (tid == 32 && o + S - 1 < nops) issue(o + S - 1);
     const T* Lb = ss + ybase + (size_t)(o % S) * stage;
     const T* X = Lb + dinv_off;
     const int r = r0 + warp;
@@ -391,14 +400,16 @@ __global__ void __launch_bounds__(FTS) k_coarse_solve(int n, int bw, const T* __
     }
     if (lane == 0) ts[warp] = (r < r1) ? y[r] - acc : T(0);
     __syncthreads();
-    if (warp == 0 && r0 + lane < r1) {
+    // y (or x) of this block: row w = warp, lanes over the block's columns
+    if (r < r1) {
       T v = T(0);
-      if (fwd) {
-        for (int c = 0; c <= lane; ++c) v = fma(X[lane * NB + c], ts[c], v);
-      } else {
-        for (int c = lane; c < NB; ++c) v = fma(X[c * NB + lane], ts[c], v);
+      if (lane < NB) {
+        const int w = warp, c = lane;
+        v = fwd ? (c <= w ? X[w * NB + c] * ts[c] : T(0)) : (c >= w ? X[c * NB + w] * ts[c] : T(0));
       }
-      y[r0 + lane] = dropped[r0 + lane] ? T(0) : v;
+#pragma unroll
+      for (int m = NB / 2; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+      if (lane == 0) y[r] = dropped[r] ? T(0) : v;
     }
     __syncthreads();
   }
