@@ -132,41 +132,42 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
     if (tid == 0 && o + NSLOT - 1 < nops) issue(o + NSLOT - 1);
     const T* M = sm + (size_t)(o % NSLOT) * LY.slot_elems;
     if (o < nmat) {
-      // ---------------- forward: four rows per warp at a time ----------------
-      const T* vin = is_b ? ycur : zbuf;  // B_j y_{j-1} or Linv_j z
-      T res4[4];
-      for (int rb = warp; rb < nb; rb += 4 * NW) {
-        T acc[4] = {0, 0, 0, 0};
-        int rr[4], lo[4];
-        const T* row[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          rr[q] = rb + q * NW;
-          const int rq = rr[q] < nb ? rr[q] : nb - 1;
-          lo[q] = is_b ? b_lo(rq) : 0;
-          row[q] = is_b ? M + b_row_off(nb, rq) - lo[q] : M + linv_row_off(rq);
-        }
-        const int cmax = is_b ? nb - 1 : min(rr[3], nb - 1);
-        for (int c = lo[0] + lane; c <= cmax; c += 32) {
-          const T v = vin[c];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const bool in = rr[q] < nb && c >= lo[q] && (is_b || c <= rr[q]);
-            if (in) acc[q] = fma(row[q][c], v, acc[q]);
+      // ---------------- forward: a quad of threads per pair of rows ----------------
+      // Rows r and nb-1-r (together nb+1 entries of Linv, about nb+7 of B) go
+      // to one quad; its threads take every fourth column, so a row costs two
+      // shuffles instead of a warp-wide reduction.
+      const T* vin = is_b ? ycur : zbuf;
+      const int npair = (nb + 1) / 2;
+      const int sub = tid & 3;
+      const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
+      for (int base = 0; base < npair; base += NT / 4) {
+        const int pq = base + (tid >> 2);
+        const bool active = pq < npair;
+        const int ra = active ? pq : 0, rb2 = nb - 1 - ra;
+        T acc_a = 0, acc_b = 0;
+        if (active) {
+          {
+            const int lo = is_b ? b_lo(ra) : 0, hi = is_b ? nb - 1 : ra;
+            const T* row = is_b ? M + b_row_off(nb, ra) - lo : M + linv_row_off(ra);
+            for (int c = lo + sub; c <= hi; c += 4) acc_a = fma(row[c], vin[c], acc_a);
+          }
+          if (rb2 != ra) {
+            const int lo = is_b ? b_lo(rb2) : 0, hi = is_b ? nb - 1 : rb2;
+            const T* row = is_b ? M + b_row_off(nb, rb2) - lo : M + linv_row_off(rb2);
+            for (int c = lo + sub; c <= hi; c += 4) acc_b = fma(row[c], vin[c], acc_b);
           }
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) res4[q] = wsum(acc[q]);
-        if (lane == 0) {
-          const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (rr[q] >= nb) continue;
-            if (is_b) {
-              zbuf[rr[q]] = (T)rg[rowbase + rr[q]] - res4[q];
-            } else {
-              part[rr[q]] = res4[q];  // y_j, copied to ycur below
-            }
+        acc_a += __shfl_xor_sync(0xffffffffu, acc_a, 1);
+        acc_b += __shfl_xor_sync(0xffffffffu, acc_b, 1);
+        acc_a += __shfl_xor_sync(0xffffffffu, acc_a, 2);
+        acc_b += __shfl_xor_sync(0xffffffffu, acc_b, 2);
+        if (active && sub == 0) {
+          if (is_b) {
+            zbuf[ra] = (T)rg[rowbase + ra] - acc_a;
+            if (rb2 != ra) zbuf[rb2] = (T)rg[rowbase + rb2] - acc_b;
+          } else {
+            part[ra] = acc_a;  // y_j, copied to ycur below
+            if (rb2 != ra) part[rb2] = acc_b;
           }
         }
       }
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
           const T v = wv[rr];
 #pragma unroll
           for (int q = 0; q < MAX_NB / 32; ++q) {
+            if (32 * q > rr) break;  // warp-uniform: the rest of the row is beyond the diagonal
             const int c = lane + 32 * q;
             if (c <= rr) acc[q] = fma(row[c], v, acc[q]);
           }
@@ -204,6 +206,8 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
           const T v = xbuf[rr];
 #pragma unroll
           for (int q = 0; q < MAX_NB / 32; ++q) {
+            if (32 * q >= nb) break;
+            if (32 * q + 31 < lo) continue;  // warp-uniform: chunk left of the row's profile
             const int c = lane + 32 * q;
             if (c >= lo && c < nb) acc[q] = fma(row[c], v, acc[q]);
           }
