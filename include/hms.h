@@ -82,8 +82,10 @@ typedef struct {
   int32_t precision;         /* HMS_FP64 or HMS_MIXED */
   double tol;                /* stop when R1 = ||K u - p||_1 / ||p||_1 < tol (Eq. 19) */
   int32_t max_iter;          /* upper-level updates per load vector (>= 0) */
-  int32_t coarse_solves;     /* FP32-factor solves of Eq. 8 per update incl. FP64
-                                refinement steps (1..8); 0 = default (FP64: 3, mixed: 2) */
+  int32_t coarse_solves;     /* most solves of Eq. 8 per update with the FP32 factor,
+                                incl. FP64 refinement steps (1..8; refinement stops early
+                                once max|res| <= 1e-14 max|b|); 0 = default (FP64: 5,
+                                mixed: 2) */
   int32_t batch;             /* iterations per CUDA-graph launch; 0 = default (16) */
   int32_t profile;           /* 1 = time every kernel with CUDA events */
   int32_t coarse_factor;     /* factor of Eq. 8: 0 = auto (FP64 for one- or two-node-wide

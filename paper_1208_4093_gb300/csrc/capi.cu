@@ -56,6 +56,7 @@ struct hms_problem {
   void* lrow = nullptr;      // scaled band in row layout, then L in row layout
   void* dinv = nullptr;      // inverted 32 x 32 diagonal blocks of L
   int* dropped = nullptr;
+  unsigned long long* cstat = nullptr;  // refinement state of the upper-level solve
   double* partials = nullptr;
   unsigned* ticket = nullptr;
   IterCtl* ctl = nullptr;
@@ -165,12 +166,13 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
   mark();
   for (int q = 0; q < pr->nsolve; ++q) {
     if (q > 0) {
-      e = launch_coarse_residual(s, pr->n_c, pr->bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, pr->ctl);
+      e = launch_coarse_residual(s, pr->n_c, pr->bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, pr->cstat,
+                                 pr->ctl);
       if (e != cudaSuccess) return e;
       mark();
     }
     e = launch_coarse_solve(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped,
-                            q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->ctl, pr->err);
+                            q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, pr->ctl, pr->err);
     if (e != cudaSuccess) return e;
     mark();
   }
@@ -315,7 +317,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   lv.L = d->bar_length;
   lv.k_u = d->ea ? 0.0 : d->ea_uniform / d->bar_length;
   pr->precision = o->precision;
-  pr->nsolve = o->coarse_solves > 0 ? o->coarse_solves : (o->precision == HMS_FP64 ? 3 : 2);
+  pr->nsolve = o->coarse_solves > 0 ? o->coarse_solves : (o->precision == HMS_FP64 ? 5 : 2);
   pr->batch = o->batch > 0 ? (o->batch + 1) / 2 * 2 : 16;
   pr->profile = o->profile;
   pr->tol = o->tol;
@@ -337,7 +339,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     const int hmin = std::min(lv.sy, lv.ny - (lv.My - 1) * lv.sy);
     const bool degenerate = std::min(wmin, hmin) <= 2;
     auto fits = [&](bool f64) {
-      return coarse_factor_smem_bytes(pr->bw, f64) + 1024 <= (size_t)maxsm &&
+      return coarse_factor_smem_bytes(pr->n_c, pr->bw, f64) + 1024 <= (size_t)maxsm &&
              coarse_solve_smem_bytes(pr->n_c, pr->bw, f64) + 1024 <= (size_t)maxsm;
     };
     if (o->coarse_factor == 2) pr->coarse_fp64 = true;
@@ -476,6 +478,8 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     pr->dinv = di;
   }
   CKP(palloc(pr, &pr->dropped, n_c));
+  CKP(palloc(pr, &pr->cstat, 4));
+  CKP(cudaMemsetAsync(pr->cstat, 0, 4 * sizeof(unsigned long long), s));
   const size_t npart = (size_t)std::max(update_residual_blocks(lv), 1024) * 3;
   CKP(palloc(pr, &pr->partials, npart));
   CKP(palloc(pr, &pr->ticket, 1));
@@ -732,9 +736,10 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
                              pr->x, pr->dropped, nullptr));
   CKC(c, launch_coarse_factor(s, n, bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped, nullptr));
   for (int q = 0; q < pr->nsolve; ++q) {
-    if (q > 0) CKC(c, launch_coarse_residual(s, n, bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, nullptr));
+    if (q > 0)
+      CKC(c, launch_coarse_residual(s, n, bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, pr->cstat, nullptr));
     CKC(c, launch_coarse_solve(s, n, bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped,
-                               q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, nullptr, pr->err));
+                               q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, nullptr, pr->err));
   }
   CKC(c, cudaMemcpyAsync(a, pr->a, n * sizeof(double), kind_out(mem_kind), s));
   if (dropped) CKC(c, cudaMemcpyAsync(dropped, pr->dropped, n * sizeof(int32_t), kind_out(mem_kind), s));

@@ -86,7 +86,12 @@ __host__ __device__ inline ListCaps list_caps(int w, int h) {
   return c;
 }
 
-template <typename DT, bool FULL>
+// AT: arithmetic of the per-bar products of bars inside the set (double on the
+// FP64 path; float on the mixed path, where delta itself is FP32 and the
+// products only approximate K_aa, which leaves the iteration's fixed point
+// unchanged because P uses the FP64 residual).  Per-thread partial sums are
+// promoted to FP64 before the block reduction.
+template <typename DT, bool FULL, typename AT>
 __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __restrict__ delta,
                                                      double* __restrict__ slots, const IterCtl* ctl) {
   extern __shared__ double lists[];
@@ -106,12 +111,12 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
   __syncthreads();
 
   const double2 repI = lv.rep[I];
-  double reg[NREG];
-  double gen[NGEN];
+  AT reg[NREG];
+  AT gen[NGEN];
 #pragma unroll
-  for (int k = 0; k < NREG; ++k) reg[k] = 0.0;
+  for (int k = 0; k < NREG; ++k) reg[k] = AT(0);
 #pragma unroll
-  for (int k = 0; k < NGEN; ++k) gen[k] = 0.0;
+  for (int k = 0; k < NGEN; ++k) gen[k] = AT(0);
 
   for (int q = tid; q < w * h; q += NT) {
     const int il = q % w, jl = q / w;
@@ -139,11 +144,12 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
         const double xib = xb - repI.x, etab = yb - repI.y;
         if (!FULL && fa == 0u && fb == 0u) {
           // regular bar: s_0 = s_1 = 0, s_2..s_5 constants of the direction
-          const double ea = ex * da.x + ey * da.y, eb = ex * db.x + ey * db.y;
-          const double s6 = ea - eb;
-          const double s7 = xia * ea - xib * eb;
-          const double s8 = etaa * ea - etab * eb;
-          const double k6 = k * s6, k7 = k * s7, k8 = k * s8;
+          const AT ea = (AT)ex * (AT)da.x + (AT)ey * (AT)da.y, eb = (AT)ex * (AT)db.x + (AT)ey * (AT)db.y;
+          const AT s6 = ea - eb;
+          const AT s7 = (AT)xia * ea - (AT)xib * eb;
+          const AT s8 = (AT)etaa * ea - (AT)etab * eb;
+          const AT kk = (AT)k;
+          const AT k6 = kk * s6, k7 = kk * s7, k8 = kk * s8;
           reg[3 * d + 0] += k6;
           reg[3 * d + 1] += k7;
           reg[3 * d + 2] += k8;
@@ -163,14 +169,15 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
 #pragma unroll
             for (int m = 0; m < 9; ++m)
 #pragma unroll
-              for (int l = 0; l <= m; ++l) gen[m * (m + 1) / 2 + l] = fma(k * sa[m], sa[l], gen[m * (m + 1) / 2 + l]);
+              for (int l = 0; l <= m; ++l)
+                gen[m * (m + 1) / 2 + l] = fma((AT)(k * sa[m]), (AT)sa[l], gen[m * (m + 1) / 2 + l]);
           } else {
 #pragma unroll
             for (int m = 6; m < 9; ++m)
 #pragma unroll
               for (int l = 0; l <= m; ++l) {
                 const int g = (m == 6 ? 0 : (m == 7 ? 7 : 15)) + l;
-                gen[g] = fma(k * sa[m], sa[l], gen[g]);
+                gen[g] = fma((AT)(k * sa[m]), (AT)sa[l], gen[g]);
               }
           }
         }
@@ -211,9 +218,9 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
   constexpr int NACC = NREG + NGEN;
   double acc[NACC];
 #pragma unroll
-  for (int k = 0; k < NREG; ++k) acc[k] = reg[k];
+  for (int k = 0; k < NREG; ++k) acc[k] = (double)reg[k];
 #pragma unroll
-  for (int k = 0; k < NGEN; ++k) acc[NREG + k] = gen[k];
+  for (int k = 0; k < NGEN; ++k) acc[NREG + k] = (double)gen[k];
 #pragma unroll
   for (int k = 0; k < NACC; ++k) {
     const double v = warp_sum(acc[k]);
@@ -461,24 +468,24 @@ cudaError_t launch_coarse_slots(cudaStream_t s, const LatView& lv, const void* d
                                 bool full, double* slots, const IterCtl* ctl) {
   const size_t smem = coarse_slots_smem(lv);
   if (delta_fp32) {
-    if (full) k_coarse_slots<float2, true><<<lv.M, NT, smem, s>>>(lv, (const float2*)delta, slots, ctl);
-    else k_coarse_slots<float2, false><<<lv.M, NT, smem, s>>>(lv, (const float2*)delta, slots, ctl);
+    if (full) k_coarse_slots<float2, true, double><<<lv.M, NT, smem, s>>>(lv, (const float2*)delta, slots, ctl);
+    else k_coarse_slots<float2, false, float><<<lv.M, NT, smem, s>>>(lv, (const float2*)delta, slots, ctl);
   } else {
-    if (full) k_coarse_slots<double2, true><<<lv.M, NT, smem, s>>>(lv, (const double2*)delta, slots, ctl);
-    else k_coarse_slots<double2, false><<<lv.M, NT, smem, s>>>(lv, (const double2*)delta, slots, ctl);
+    if (full) k_coarse_slots<double2, true, double><<<lv.M, NT, smem, s>>>(lv, (const double2*)delta, slots, ctl);
+    else k_coarse_slots<double2, false, double><<<lv.M, NT, smem, s>>>(lv, (const double2*)delta, slots, ctl);
   }
   return cudaGetLastError();
 }
 
 cudaError_t configure_coarse_assemble(int max_smem) {
   cudaError_t e;
-  e = set_max_dynamic_smem(k_coarse_slots<float2, true>, max_smem);
+  e = set_max_dynamic_smem(k_coarse_slots<float2, true, double>, max_smem);
   if (e != cudaSuccess) return e;
-  e = set_max_dynamic_smem(k_coarse_slots<float2, false>, max_smem);
+  e = set_max_dynamic_smem(k_coarse_slots<float2, false, float>, max_smem);
   if (e != cudaSuccess) return e;
-  e = set_max_dynamic_smem(k_coarse_slots<double2, true>, max_smem);
+  e = set_max_dynamic_smem(k_coarse_slots<double2, true, double>, max_smem);
   if (e != cudaSuccess) return e;
-  return set_max_dynamic_smem(k_coarse_slots<double2, false>, max_smem);
+  return set_max_dynamic_smem(k_coarse_slots<double2, false, double>, max_smem);
 }
 
 static int grid_for(size_t total) {

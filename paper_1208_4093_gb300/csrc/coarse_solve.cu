@@ -19,11 +19,12 @@
 //                    rest of the window, write block K's columns of L and load
 //                    the next band rows, warp 0 updates, factors (registers)
 //                    and inverts the diagonal block K+1.
-//   k_coarse_solve   one CTA of 512 threads: block forward / back substitution,
-//                    16 rows per step (one warp per row), products with the
-//                    inverted diagonal blocks; the rows of L each step needs
-//                    are staged by bulk copies several steps ahead.  Adds the
-//                    correction to the FP64 solution and writes a = D^-1/2 x.
+//   k_coarse_solve   one CTA of 512 threads: right-looking block forward / back
+//                    substitution, 16 rows per step: the inverted diagonal
+//                    block, then the block's contribution to the next bw rows;
+//                    the columns (rows) of L each step needs are staged by bulk
+//                    copies several steps ahead.  Adds the correction to the
+//                    FP64 solution and writes a = D^-1/2 x.
 //   k_coarse_residual many CTAs, FP64: res = b - A x over the band.
 #include "hms_internal.cuh"
 #include "ptx.cuh"
@@ -74,12 +75,14 @@ __device__ inline double trsqrt(double x) { return 1.0 / sqrt(x); }
 // Column C of the register-resident Cholesky of an NB x NB diagonal block
 // (lane = row; lanes >= NB hold zero rows).  A dropped column becomes a unit column with a zero row.
 template <typename T, int C>
-__device__ __forceinline__ void diag_steps(T (&a)[NB], unsigned dmask, int lane, unsigned& dropped_out) {
+__device__ __forceinline__ void diag_steps(T (&a)[NB], unsigned dmask, int lane, unsigned& dropped_out,
+                                           T (&rdiag)[NB]) {
   if constexpr (C < NB) {
     const T piv = __shfl_sync(0xffffffffu, a[C], C);
     const bool drop = ((dmask >> C) & 1u) != 0 || !(piv > Tau<T>::v);
     const T inv = drop ? T(1) : trsqrt(piv);
     const T d = drop ? T(1) : piv * inv;
+    rdiag[C] = inv;  // 1 / L_CC
     const bool mine = lane == C;
     const T acl = a[C];
     a[C] = mine ? d : (lane > C ? (drop ? T(0) : acl * inv) : acl);
@@ -92,8 +95,19 @@ __device__ __forceinline__ void diag_steps(T (&a)[NB], unsigned dmask, int lane,
       a[j] = (lane >= j) ? fma(-lc, ljc, a[j]) : a[j];
     }
     if (drop) dropped_out |= (1u << C);
-    diag_steps<T, C + 1>(a, dmask, lane, dropped_out);
+    diag_steps<T, C + 1>(a, dmask, lane, dropped_out, rdiag);
   }
+}
+
+// four consecutive elements from 16-byte-aligned shared memory
+__device__ inline void ld4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+}
+__device__ inline void ld4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
 }
 
 template <typename T>
@@ -115,22 +129,29 @@ __host__ __device__ inline FactorLayout<T> factor_layout(int bw) {
   L.total = L.xs + 2 * NB * (NB + 1);
   return L;
 }
+// extra shared memory of the factor after the T-typed part: the drop flags
+// (int per unknown) and the trailing update's 4 x 4 tile pairs (ti, tj)
+__host__ __device__ inline int factor_tile_pairs(int bw) {
+  const int t4 = (bw + 3) / 4;
+  return t4 * (t4 + 1) / 2;
+}
 
 // Warp 0: factor the diagonal block starting at row k (nbk rows) held in a[],
 // write L to Ls, X = L^-1 to Xs and dinv, and the drop decisions.
 template <typename T>
-__device__ __forceinline__ void factor_diag_block(T (&a)[NB], int k, int nbk, int lane, int* __restrict__ dropped,
-                                                  T* Ls, T* Xs, T* __restrict__ dinv, unsigned* dropblk) {
-  const unsigned dmask = __ballot_sync(0xffffffffu, lane >= nbk || dropped[k + lane] != 0);
+__device__ __forceinline__ void factor_diag_block(T (&a)[NB], int k, int nbk, int lane, int* sdrop, T* Ls, T* Xs,
+                                                  T* __restrict__ dinv, unsigned* dropblk) {
+  const unsigned dmask = __ballot_sync(0xffffffffu, lane >= nbk || sdrop[k + lane] != 0);
   unsigned dout = 0;
-  diag_steps<T, 0>(a, dmask, lane, dout);
+  T rdiag[NB];
+  diag_steps<T, 0>(a, dmask, lane, dout, rdiag);
   if (lane < NB) {
 #pragma unroll
     for (int j = 0; j < NB; ++j) Ls[lane * (NB + 1) + j] = (j <= lane) ? a[j] : T(0);
   }
   if (lane == 0) *dropblk = dout;
   __syncwarp();
-  if (lane < nbk) dropped[k + lane] = (dout >> lane) & 1u;
+  if (lane < nbk) sdrop[k + lane] = (dout >> lane) & 1u;
   // X = L^-1, lane c computes column c column-oriented: once x_q is known it
   // is subtracted from every later row, so the dependent chain is NB steps long
   T x[NB];
@@ -138,7 +159,7 @@ __device__ __forceinline__ void factor_diag_block(T (&a)[NB], int k, int nbk, in
   for (int r = 0; r < NB; ++r) x[r] = (r == lane) ? T(1) : T(0);
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
-    const T xq = (q >= lane) ? x[q] / Ls[q * (NB + 1) + q] : T(0);
+    const T xq = (q >= lane) ? x[q] * rdiag[q] : T(0);
     x[q] = xq;
 #pragma unroll
     for (int r = q + 1; r < NB; ++r) x[r] = fma(-Ls[r * (NB + 1) + q], xq, x[r]);
@@ -166,9 +187,20 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
   const int W = LY.W, ldw = LY.ldw, pstr = LY.pstr;
   T* Aw = fs + LY.aw;
   T* Pc = fs + LY.pc;
+  int* sdrop = reinterpret_cast<int*>(fs + LY.total);
+  unsigned short* tpair = reinterpret_cast<unsigned short*>(sdrop + n);
   __shared__ unsigned dropblk[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nblk = (n + NB - 1) / NB;
+  const int npairs_max = factor_tile_pairs(bw);
+  for (int i = tid; i < n; i += FTF) sdrop[i] = dropped[i];
+  for (int q = tid; q < npairs_max; q += FTF) {
+    int ti = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+    while (ti * (ti + 1) / 2 > q) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= q) ++ti;
+    tpair[2 * q] = (unsigned short)ti;
+    tpair[2 * q + 1] = (unsigned short)(q - ti * (ti + 1) / 2);
+  }
 
   // window rows [0, min(n, W))
   for (int q = tid; q < min(n, W) * ldw; q += FTF) {
@@ -183,7 +215,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
 #pragma unroll
     for (int j = 0; j < NB; ++j)
       a[j] = (lane < nbk && j <= lane && lane - j <= bw) ? Aw[(size_t)lane * ldw + (lane - j)] : T(0);
-    factor_diag_block<T>(a, 0, nbk, lane, dropped, fs + LY.ls, fs + LY.xs, dinv, &dropblk[0]);
+    factor_diag_block<T>(a, 0, nbk, lane, sdrop, fs + LY.ls, fs + LY.xs, dinv, &dropblk[0]);
   }
   __syncthreads();
 
@@ -194,6 +226,8 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
     const T* Ls = fs + LY.ls + cur * NB * (NB + 1);
     const T* Xs = fs + LY.xs + cur * NB * (NB + 1);
     const unsigned dblk = dropblk[cur];
+    const int slot_k1 = k1 % W;  // window slot of row k1; row k1 + d sits at slot_k1 + d (mod W)
+    auto slot = [&](int i) { const int v = slot_k1 + (i - k1); return v >= W ? v - W : v; };
     // (a) panel P[i][c] = sum_{c' <= c} A[i][k0 + c'] X[c][c'], i in [k1, rend); 4 x 4 tiles
     {
       const int nrq = (np + 3) / 4;
@@ -205,7 +239,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
         for (int u = 0; u < 4; ++u) {
           il[u] = 4 * rq + u;
           const int i = k1 + (il[u] < np ? il[u] : np - 1);
-          rowoff[u] = (i % W) * ldw + (i - k0);
+          rowoff[u] = slot(i) * ldw + (i - k0);
         }
         T acc[4][4];
 #pragma unroll
@@ -213,6 +247,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
         const int cmax = min(4 * cq + 3, nbk - 1);
+#pragma unroll 4
         for (int cp = 0; cp <= cmax; ++cp) {
           T av[4], xv[4];
 #pragma unroll
@@ -245,7 +280,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
       if (l < nbk2 && j <= l && l < np && l - j <= bw) {
         T v = T(0);
         for (int c = 0; c < nbk; ++c) v = fma(Pc[c * pstr + l], Pc[c * pstr + j], v);
-        Aw[(size_t)((k1 + l) % W) * ldw + (l - j)] -= v;
+        Aw[(size_t)slot(k1 + l) * ldw + (l - j)] -= v;
       }
     }
     __syncthreads();
@@ -253,39 +288,48 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
       // (b0) look-ahead: factor the diagonal block K+1
       if (K + 1 < nblk) {
         T a[NB];
-        const size_t rbase = (size_t)((k1 + lane) % W) * ldw;
+        const size_t rbase = (size_t)slot(min(k1 + lane, n - 1)) * ldw;
 #pragma unroll
         for (int j = 0; j < NB; ++j)
           a[j] = (lane < nbk2 && j <= lane && lane - j <= bw) ? Aw[rbase + (lane - j)] : T(0);
-        factor_diag_block<T>(a, k1, nbk2, lane, dropped, fs + LY.ls + nxt * NB * (NB + 1),
+        factor_diag_block<T>(a, k1, nbk2, lane, sdrop, fs + LY.ls + nxt * NB * (NB + 1),
                              fs + LY.xs + nxt * NB * (NB + 1), dinv, &dropblk[nxt]);
       }
     } else {
       const int t2 = tid - 32, nt2 = FTF - 32;
+      // band rows [k0 + W, k1 + W) enter the window at the end of this step:
+      // load them now, store them after the update (latency hidden)
+      const int er0 = k0 + W, er1 = min(k1 + W, n);
+      T pre[2][7];  // at most 2 entering rows per warp (NB rows over 15 warps), ldw <= 224
+      {
+        int e = 0;
+        for (int i = er0 + warp - 1; i < er1 && e < 2; i += FTF / 32 - 1, ++e) {
+          const T* src = lrow + (size_t)i * ldw;
+#pragma unroll
+          for (int u = 0; u < 7; ++u) {
+            const int kk = lane + 32 * u;
+            pre[e][u] = (kk < ldw && kk <= i) ? src[kk] : T(0);
+          }
+        }
+      }
       // (b1) trailing update of the window except the next diagonal block
       {
         const int T4 = (np + 3) / 4;
         const int first = (NB / 4) * (NB / 4 + 1) / 2;  // tile pairs inside rows [k1, k1 + NB)
         const int npairs = T4 * (T4 + 1) / 2;
         for (int q = first + t2; q < npairs; q += nt2) {
-          int ti = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-          while (ti * (ti + 1) / 2 > q) --ti;
-          while ((ti + 1) * (ti + 2) / 2 <= q) ++ti;
-          const int tj = q - ti * (ti + 1) / 2;
-          if (ti < NB / 4) continue;
+          const int ti = tpair[2 * q], tj = tpair[2 * q + 1];
           T acc[4][4];
 #pragma unroll
           for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+#pragma unroll 4
           for (int c = 0; c < nbk; ++c) {
             const T* pc = Pc + c * pstr;
             T ri[4], rj[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              ri[u] = pc[4 * ti + u];
-              rj[u] = pc[4 * tj + u];
-            }
+            ld4(pc + 4 * ti, ri);
+            ld4(pc + 4 * tj, rj);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -295,7 +339,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
           for (int u = 0; u < 4; ++u) {
             const int i = k1 + 4 * ti + u;
             if (i >= rend) continue;
-            const size_t rb = (size_t)(i % W) * ldw;
+            const size_t rb = (size_t)slot(i) * ldw;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
               const int j = k1 + 4 * tj + v;
@@ -304,56 +348,88 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
           }
         }
       }
-      // (b2) columns [k0, k1) of L to global, both layouts
-      for (int q = t2; q < nbk * ldw; q += nt2) {
-        const int cl = q / ldw, kk = q - (q / ldw) * ldw;
-        const int c = k0 + cl, i = c + kk;
-        T v = T(0);
-        if (i < n) {
-          if (i < k1) v = Ls[(i - k0) * (NB + 1) + cl];
-          else if (i < rend) v = Pc[cl * pstr + (i - k1)];
+      // (b2) columns [k0, k1) of L to global, both layouts (warp per column)
+      for (int cl = warp - 1; cl < nbk; cl += FTF / 32 - 1) {
+        const int c = k0 + cl;
+        for (int kk = lane; kk < ldw; kk += 32) {
+          const int i = c + kk;
+          T v = T(0);
+          if (i < n) {
+            if (i < k1) v = Ls[(i - k0) * (NB + 1) + cl];
+            else if (i < rend) v = Pc[cl * pstr + (i - k1)];
+          }
+          lcol[(size_t)c * ldw + kk] = v;
+          if (i < n) lrow[(size_t)i * ldw + kk] = v;
         }
-        lcol[(size_t)c * ldw + kk] = v;
-        if (i < n) lrow[(size_t)i * ldw + kk] = v;
       }
-      // (b3) band rows [k0 + W, k1 + W) enter the window (slots of rows [k0, k1))
-      const int r0 = k0 + W, r1 = min(k1 + W, n);
-      for (int q = t2; q < (r1 > r0 ? r1 - r0 : 0) * ldw; q += nt2) {
-        const int i = r0 + q / ldw, kk = q - (q / ldw) * ldw;
-        Aw[(size_t)(i % W) * ldw + kk] = (kk <= i) ? lrow[(size_t)i * ldw + kk] : T(0);
+      // (b3) the prefetched rows enter the window (slots of rows [k0, k1))
+      {
+        int e = 0;
+        for (int i = er0 + warp - 1; i < er1 && e < 2; i += FTF / 32 - 1, ++e) {
+          T* dst = Aw + (size_t)(i % W) * ldw;
+#pragma unroll
+          for (int u = 0; u < 7; ++u) {
+            const int kk = lane + 32 * u;
+            if (kk < ldw) dst[kk] = pre[e][u];
+          }
+        }
       }
     }
     __syncthreads();
   }
+  for (int i = tid; i < n; i += FTF) dropped[i] = sdrop[i];
 }
 
 // One solve with the factor, added to the FP64 solution x; writes a = s x.
+// Right-looking substitution: step K applies the inverted diagonal block to
+// block K's right-hand side (final by then), then subtracts block K's
+// contribution from the next bw rows (forward: columns of L, backward: rows of
+// L), so the chain from one block to the next is two short phases.
 template <typename T>
 __host__ __device__ inline int solve_stage_elems(int bw) {
   return ((NB * (bw + 1) + 3) / 4) * 4 + NB * NB;
 }
 
+// cstat[0]: bits of max |b| (set by the first solve), cstat[1]: bits of the
+// last residual's max |res| (k_coarse_residual), cstat[2]: 1 once refinement
+// has converged (max |res| <= 1e-14 max |b|); later solves then return at once.
 template <typename T>
 __global__ void __launch_bounds__(FTS) k_coarse_solve(int n, int bw, const T* __restrict__ lcol,
                                                       const T* __restrict__ lrow, const T* __restrict__ dinv,
                                                       const int* __restrict__ dropped, const double* __restrict__ res,
                                                       double* __restrict__ x, const double* __restrict__ scale,
-                                                      double* __restrict__ a_out, const IterCtl* ctl, int* err) {
+                                                      double* __restrict__ a_out, unsigned long long* cstat, int first,
+                                                      const IterCtl* ctl, int* err) {
   if (ctl && *(volatile const int*)&ctl->done) return;
+  __shared__ int skip;
+  if (threadIdx.x == 0) {
+    if (first) {
+      skip = 0;
+    } else {
+      const double bmax = __longlong_as_double((long long)cstat[0]);
+      const double rmax = __longlong_as_double((long long)cstat[1]);
+      skip = (cstat[2] != 0ull) || !(rmax > 1e-14 * bmax);
+      if (skip) cstat[2] = 1ull;
+    }
+  }
+  __syncthreads();
+  if (skip) return;
   constexpr int S = Stages<T>::v;
   extern __shared__ __align__(16) unsigned char ssraw[];
   T* ss = reinterpret_cast<T*>(ssraw);
   __shared__ uint64_t bars[S];
-  __shared__ T ts[NB];
   __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ldw = bw + 1;
   const int nblk = (n + NB - 1) / NB;
   const int nops = 2 * nblk;
   const int stage = solve_stage_elems<T>(bw);
-  const int ybase = (n + 3) / 4 * 4;
-  T* y = ss;
+  const int n4 = (n + 3) / 4 * 4;
+  T* tv = ss;       // running right-hand side
+  T* yv = ss + n4;  // y, then x
+  const int sbase = 2 * n4;
   const int dinv_off = stage - NB * NB;
+  int* sdrop = reinterpret_cast<int*>(ss + sbase + (size_t)S * stage);
 
   auto issue = [&](int o) {
     const bool fwd = o < nblk;
@@ -362,10 +438,10 @@ __global__ void __launch_bounds__(FTS) k_coarse_solve(int n, int bw, const T* __
     const uint32_t rb = (uint32_t)((((size_t)rows * ldw * sizeof(T)) + 15) / 16 * 16);
     const uint32_t db = NB * NB * sizeof(T);
     uint64_t* bar = &bars[o % S];
-    T* dst = ss + ybase + (size_t)(o % S) * stage;
+    T* dst = ss + sbase + (size_t)(o % S) * stage;
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, rb + db);
-    bulk_g2s(dst, (fwd ? lrow : lcol) + (size_t)K * NB * ldw, rb, bar);
+    bulk_g2s(dst, (fwd ? lcol : lrow) + (size_t)K * NB * ldw, rb, bar);
     bulk_g2s(dst + dinv_off, dinv + (size_t)K * NB * NB, db, bar);
   };
   if (tid == 0) {
@@ -373,43 +449,89 @@ __global__ void __launch_bounds__(FTS) k_coarse_solve(int n, int bw, const T* __
     for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
     fence_mbar_init();
   }
-  for (int i = tid; i < n; i += FTS) y[i] = dropped[i] ? T(0) : (T)res[i];
+  __shared__ double bred[FTS / 32];
+  double bm = 0.0;
+  for (int i = tid; i < n; i += FTS) {
+    const int d = dropped[i];
+    sdrop[i] = d;
+    tv[i] = d ? T(0) : (T)res[i];
+    if (first && !d) bm = fmax(bm, fabs(res[i]));
+  }
+  if (first) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, m));
+    if (lane == 0) bred[warp] = bm;
+  }
   __syncthreads();
+  if (first && tid == 0) {
+    double v = 0.0;
+    for (int k = 0; k < FTS / 32; ++k) v = fmax(v, bred[k]);
+    cstat[0] = (unsigned long long)__double_as_longlong(v);
+    cstat[2] = 0ull;
+  }
+  if (tid == 0) cstat[1] = 0ull;  // the next residual accumulates its max here
   if (tid == 0)
     for (int o = 0; o < S - 1 && o < nops; ++o) issue(o);
   for (int o = 0; o < nops; ++o) {
     const bool fwd = o < nblk;
     const int K = fwd ? o : nops - 1 - o;
-    const int r0 = K * NB, r1 = min(r0 + NB, n);
+    const int r0 = K * NB, r1 = min(r0 + NB, n), nr = r1 - r0;
+    if (o == nblk) {
+      // the backward pass starts from y
+      for (int i = tid; i < n; i += FTS) tv[i] = yv[i];
+      __syncthreads();
+    }
     if (!mbar_wait_bounded(&bars[o % S], (uint32_t)((o / S) & 1))) abort_flag = 1;
     __syncthreads();
     if (abort_flag) break;
     if (tid == 32 && o + S - 1 < nops) issue(o + S - 1);
-    const T* Lb = ss + ybase + (size_t)(o % S) * stage;
+    const T* Lb = ss + sbase + (size_t)(o % S) * stage;  // rows of lcol (forward) / lrow (backward) of block K
     const T* X = Lb + dinv_off;
-    const int r = r0 + warp;
-    T acc = T(0);
-    if (r < r1) {
-      const T* lr = Lb + (size_t)warp * ldw;
-      if (fwd) {
-        for (int kk = r - r0 + 1 + lane; kk <= bw && kk <= r; kk += 32) acc = fma(lr[kk], y[r - kk], acc);
-      } else {
-        for (int kk = r1 - r + lane; kk <= bw && r + kk < n; kk += 32) acc = fma(lr[kk], y[r + kk], acc);
-      }
-      acc = wsum(acc);
-    }
-    if (lane == 0) ts[warp] = (r < r1) ? y[r] - acc : T(0);
-    __syncthreads();
-    // y (or x) of this block: row w = warp, lanes over the block's columns
-    if (r < r1) {
+    // (1) block K: y_K = X t_K (forward), x_K = X^T t_K (backward); warp w = row
+    if (warp < nr) {
+      const int w = warp, c = lane;
       T v = T(0);
-      if (lane < NB) {
-        const int w = warp, c = lane;
-        v = fwd ? (c <= w ? X[w * NB + c] * ts[c] : T(0)) : (c >= w ? X[c * NB + w] * ts[c] : T(0));
-      }
+      if (c < nr) v = fwd ? (c <= w ? X[w * NB + c] * tv[r0 + c] : T(0)) : (c >= w ? X[c * NB + w] * tv[r0 + c] : T(0));
 #pragma unroll
       for (int m = NB / 2; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-      if (lane == 0) y[r] = dropped[r] ? T(0) : v;
+      if (lane == 0) yv[r0 + w] = sdrop[r0 + w] ? T(0) : v;
+    }
+    __syncthreads();
+    // (2) subtract block K's contribution from the next bw rows; the block's
+    // values sit in registers and two chains share the NB products
+    T yb[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) yb[c] = (c < nr) ? yv[r0 + c] : T(0);
+    if (fwd) {
+      // t_i -= sum_k L[i][k] y_k,  i in [r1, r1 + bw), L[i][k] = lcol[k][i - k]
+      const int iend = min(n, r1 + bw);
+      for (int i = r1 + tid; i < iend; i += FTS) {
+        T acc0 = T(0), acc1 = T(0);
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          const int d = i - (r0 + c);
+          if (c < nr && d <= bw) {
+            const T t = Lb[(size_t)c * ldw + d] * yb[c];
+            if (c & 1) acc1 += t; else acc0 += t;
+          }
+        }
+        tv[i] -= acc0 + acc1;
+      }
+    } else {
+      // t_i -= sum_k L[k][i] x_k,  i in [r0 - bw, r0), L[k][i] = lrow[k][k - i]
+      const int ibeg = max(0, r0 - bw);
+      for (int i = ibeg + tid; i < r0; i += FTS) {
+        T acc0 = T(0), acc1 = T(0);
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          const int d = r0 + c - i;
+          if (c < nr && d <= bw) {
+            const T t = Lb[(size_t)c * ldw + d] * yb[c];
+            if (c & 1) acc1 += t; else acc0 += t;
+          }
+        }
+        tv[i] -= acc0 + acc1;
+      }
     }
     __syncthreads();
   }
@@ -421,7 +543,7 @@ __global__ void __launch_bounds__(FTS) k_coarse_solve(int n, int bw, const T* __
     return;
   }
   for (int i = tid; i < n; i += FTS) {
-    const double xi = dropped[i] ? 0.0 : x[i] + (double)y[i];
+    const double xi = sdrop[i] ? 0.0 : x[i] + (double)yv[i];
     x[i] = xi;
     a_out[i] = scale[i] * xi;
   }
@@ -437,8 +559,9 @@ __device__ inline double warp_sum_d(double v) {
 __global__ void k_coarse_residual(int n, int bw, const double* __restrict__ sband,
                                   const double* __restrict__ sbandR, const double* __restrict__ b,
                                   const double* __restrict__ x, const int* __restrict__ dropped,
-                                  double* __restrict__ res, const IterCtl* ctl) {
+                                  double* __restrict__ res, unsigned long long* cstat, const IterCtl* ctl) {
   if (ctl && *(volatile const int*)&ctl->done) return;
+  if (*(volatile unsigned long long*)&cstat[2]) return;
   const int lane = threadIdx.x & 31;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (row >= n) return;
@@ -451,7 +574,12 @@ __global__ void k_coarse_residual(int n, int bw, const double* __restrict__ sban
     if (kk >= 1 && row - kk >= 0) acc = fma(lo[kk], x[row - kk], acc);
   }
   acc = warp_sum_d(acc);
-  if (lane == 0) res[row] = dropped[row] ? 0.0 : b[row] - acc;
+  if (lane == 0) {
+    const double rv = dropped[row] ? 0.0 : b[row] - acc;
+    res[row] = rv;
+    // max |res| by the order of non-negative doubles' bit patterns
+    atomicMax(&cstat[1], (unsigned long long)__double_as_longlong(fabs(rv)));
+  }
 }
 
 }  // namespace
@@ -464,19 +592,25 @@ cudaError_t configure_coarse_solve(int max_smem) {
   return set_max_dynamic_smem(k_coarse_solve<double>, max_smem);
 }
 
-size_t coarse_factor_smem_bytes(int bw, bool fp64) {
-  return fp64 ? factor_layout<double>(bw).total * sizeof(double) : factor_layout<float>(bw).total * sizeof(float);
+size_t coarse_factor_smem_bytes(int n, int bw, bool fp64) {
+  if (bw + 1 > 7 * 32) return (size_t)1 << 30;  // beyond the row prefetch of the window slide
+  const size_t typed =
+      fp64 ? factor_layout<double>(bw).total * sizeof(double) : factor_layout<float>(bw).total * sizeof(float);
+  return typed + (size_t)n * sizeof(int) + (size_t)factor_tile_pairs(bw) * 2 * sizeof(unsigned short);
 }
 size_t coarse_solve_smem_bytes(int n, int bw, bool fp64) {
+  const size_t flags = (size_t)n * sizeof(int);
   if (fp64)
-    return (((size_t)n + 3) / 4 * 4 + (size_t)Stages<double>::v * solve_stage_elems<double>(bw)) * sizeof(double);
-  return (((size_t)n + 3) / 4 * 4 + (size_t)Stages<float>::v * solve_stage_elems<float>(bw)) * sizeof(float);
+    return (2 * (((size_t)n + 3) / 4 * 4) + (size_t)Stages<double>::v * solve_stage_elems<double>(bw)) * sizeof(double) +
+           flags;
+  return (2 * (((size_t)n + 3) / 4 * 4) + (size_t)Stages<float>::v * solve_stage_elems<float>(bw)) * sizeof(float) +
+         flags;
 }
 int coarse_dinv_size(int n) { return ((n + NB - 1) / NB) * NB * NB; }
 
 cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, bool fp64, void* lrow, void* lcol, void* dinv,
                                  int* dropped, const IterCtl* ctl) {
-  const size_t smem = coarse_factor_smem_bytes(bw, fp64);
+  const size_t smem = coarse_factor_smem_bytes(n, bw, fp64);
   if (fp64)
     k_coarse_factor<double><<<1, FTF, smem, s>>>(n, bw, (double*)lrow, (double*)lcol, (double*)dinv, dropped, ctl);
   else
@@ -486,23 +620,26 @@ cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, bool fp64, void*
 
 cudaError_t launch_coarse_solve(cudaStream_t s, int n, int bw, bool fp64, const void* lcol, const void* lrow,
                                 const void* dinv, const int* dropped, const double* res, double* x,
-                                const double* scale, double* a_out, const IterCtl* ctl, int* err) {
+                                const double* scale, double* a_out, unsigned long long* cstat, bool first,
+                                const IterCtl* ctl, int* err) {
   const size_t smem = coarse_solve_smem_bytes(n, bw, fp64);
   if (fp64)
     k_coarse_solve<double><<<1, FTS, smem, s>>>(n, bw, (const double*)lcol, (const double*)lrow,
-                                                (const double*)dinv, dropped, res, x, scale, a_out, ctl, err);
+                                                (const double*)dinv, dropped, res, x, scale, a_out, cstat,
+                                                first ? 1 : 0, ctl, err);
   else
     k_coarse_solve<float><<<1, FTS, smem, s>>>(n, bw, (const float*)lcol, (const float*)lrow, (const float*)dinv,
-                                               dropped, res, x, scale, a_out, ctl, err);
+                                               dropped, res, x, scale, a_out, cstat, first ? 1 : 0, ctl, err);
   return cudaGetLastError();
 }
 
 cudaError_t launch_coarse_residual(cudaStream_t s, int n, int bw, const double* sband, const double* b,
-                                   const double* x, const int* dropped, double* res, const IterCtl* ctl) {
+                                   const double* x, const int* dropped, double* res, unsigned long long* cstat,
+                                   const IterCtl* ctl) {
   const double* sbandR = sband + (size_t)n * (bw + 1);
   const int threads = 256;
   const int blocks = (int)(((size_t)n * 32 + threads - 1) / threads);
-  k_coarse_residual<<<blocks, threads, 0, s>>>(n, bw, sband, sbandR, b, x, dropped, res, ctl);
+  k_coarse_residual<<<blocks, threads, 0, s>>>(n, bw, sband, sbandR, b, x, dropped, res, cstat, ctl);
   return cudaGetLastError();
 }
 

@@ -142,10 +142,12 @@ cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, bool fp64, void*
                                  int* dropped, const IterCtl* ctl);
 cudaError_t launch_coarse_solve(cudaStream_t s, int n, int bw, bool fp64, const void* lcol, const void* lrow,
                                 const void* dinv, const int* dropped, const double* res, double* x,
-                                const double* scale, double* a_out, const IterCtl* ctl, int* err);
+                                const double* scale, double* a_out, unsigned long long* cstat, bool first,
+                                const IterCtl* ctl, int* err);
 cudaError_t launch_coarse_residual(cudaStream_t s, int n, int bw, const double* sband, const double* b,
-                                   const double* x, const int* dropped, double* res, const IterCtl* ctl);
-size_t coarse_factor_smem_bytes(int bw, bool fp64);
+                                   const double* x, const int* dropped, double* res, unsigned long long* cstat,
+                                   const IterCtl* ctl);
+size_t coarse_factor_smem_bytes(int n, int bw, bool fp64);
 size_t coarse_solve_smem_bytes(int n, int bw, bool fp64);
 int coarse_dinv_size(int n);
 size_t coarse_slots_smem(const LatView& lv);

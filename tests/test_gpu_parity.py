@@ -141,7 +141,9 @@ def test_coarse_matrix_step(problem):
     capi.hms_coarse_matrix(ctx, pr, delta, Kaa)
     d_used = f32(delta) if prec == 1 else delta
     Ko, _ = hms.coarse_system(tr, hms.modes(tr, g, d_used), r)
-    assert np.abs(Kaa - Ko).max() < 1e-12 * np.abs(Ko).max()
+    # FP64 path: rounding level.  Mixed path: the delta-mode products of bars
+    # inside a set run in FP32 (FP64 sums across threads), ~1e-7 per product
+    assert np.abs(Kaa - Ko).max() < (1e-5 if prec == 1 else 1e-12) * np.abs(Ko).max()
     assert np.array_equal(Kaa, Kaa.T)
 
 
