@@ -168,6 +168,51 @@ hms_status hms_coarse_matrix(hms_problem* pr, const double* delta, double* Kaa,
 hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P, double* a,
                             int32_t* dropped, int32_t mem_kind);
 
+/* ---- allocation-free residual (no counterpart in the paper) ---- */
+
+/* Node tiles of 32 x 8 per CTA; the static scratch of
+ * hms_residual_noalloc holds the per-CTA sums of at most this many tiles,
+ * ceil(nx/32) * ceil(ny/8) (3 doubles each: 384 KiB of device memory). */
+#define HMS_RESIDUAL_NOALLOC_MAX_TILES 16384
+
+/* The result of hms_residual (Eqs. 1, 19, 2) -- r = p - K u on the free DOFs
+ * and norms[0] = ||r||_1, norms[1] = ||r||_2^2, norms[2] = u.(p + r) -- for
+ * device-resident vectors, without allocating device memory and without
+ * touching the problem's own buffers.  This is a library service, not a step
+ * the paper describes.
+ *
+ * Who needs it: callers that must not allocate while the device is busy --
+ * cudaFree (and, with a full pool, cudaMalloc) synchronises the whole device,
+ * which stalls work the caller has in flight on other streams; callers whose
+ * device memory is fully committed (e.g. the factors of many problems
+ * filling HBM), where an allocation could fail with out-of-memory at an
+ * arbitrary point; and callers checking a solution between other solves of
+ * the same problem, whose buffers hms_residual would overwrite.
+ *
+ * p, u, r: DEVICE pointers on the context's device (device or managed memory),
+ * 2*nx*ny doubles each, 16-byte aligned; r may not alias p or u.  Constrained
+ * DOFs of u are read as 0 (u itself is not modified).  norms: device pointer
+ * to 3 doubles, 8-byte aligned, or NULL.  The kernel runs on the context's
+ * stream; the call returns after it completed (a stream synchronisation,
+ * which allocates nothing).
+ *
+ * Scratch: a static device array of HMS_RESIDUAL_NOALLOC_MAX_TILES * 3
+ * doubles plus a completion counter, part of the library's device image.
+ * The first call on each device looks up their addresses
+ * (cudaGetSymbolAddress, with the device made current) and caches them; make
+ * that first call before beginning any stream capture on the device.  The
+ * counter must be 0 when a kernel starts; it is 0 at load and every kernel
+ * resets it when it completes.  Calls that run at the same time on one
+ * device -- from two threads, two contexts or two problems -- share the
+ * scratch and race: serialise them.
+ *
+ * Errors: HMS_ERR_ARG for a NULL problem/vector, host or foreign-device
+ * pointers, misalignment, r aliasing p or u, or a lattice of more than
+ * HMS_RESIDUAL_NOALLOC_MAX_TILES tiles (use hms_residual there);
+ * HMS_ERR_CUDA if the scratch lookup or the launch fails. */
+hms_status hms_residual_noalloc(hms_problem* pr, const double* p, const double* u, double* r,
+                                double* norms);
+
 #ifdef __cplusplus
 }
 #endif

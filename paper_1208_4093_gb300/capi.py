@@ -88,6 +88,7 @@ def lib():
         "hms_relax": (ctypes.c_int32, [_P, _P, _P, _P, ctypes.c_int32]),
         "hms_coarse_matrix": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
         "hms_coarse_solve": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32]),
+        "hms_residual_noalloc": (ctypes.c_int32, [_P, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -102,7 +103,8 @@ def exported_symbols():
     return ["hms_context_create", "hms_context_destroy", "hms_context_stream", "hms_last_error",
             "hms_problem_create", "hms_problem_destroy", "hms_problem_device_bytes",
             "hms_problem_setup_ms", "hms_solve", "hms_kernel_times", "hms_residual",
-            "hms_update_residual", "hms_relax", "hms_coarse_matrix", "hms_coarse_solve"]
+            "hms_update_residual", "hms_relax", "hms_coarse_matrix", "hms_coarse_solve",
+            "hms_residual_noalloc"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -224,6 +226,16 @@ def hms_kernel_times(pr):
 def hms_residual(ctx, pr, p, u, r_out, norms_out):
     A = [_Arg(p), _Arg(u), _Arg(r_out, writable=True), _Arg(norms_out, writable=True)]
     _check(ctx, lib().hms_residual(pr, *[a.ptr for a in A], _mem_kind(*A)))
+
+
+def hms_residual_noalloc(ctx, pr, p, u, r_out, norms_out=None):
+    """CUDA tensors only (float64, contiguous): r_out = p - K u and the three sums
+    of hms_residual, with no device allocation inside the call.  Inputs must be
+    complete before the call (e.g. torch.cuda.synchronize())."""
+    A = [_Arg(p), _Arg(u), _Arg(r_out, writable=True), _Arg(norms_out, writable=True)]
+    if any(a.kind != HMS_MEM_DEVICE for a in A if a.ptr is not None):
+        raise ValueError("hms_residual_noalloc takes CUDA tensors only")
+    _check(ctx, lib().hms_residual_noalloc(pr, *[a.ptr for a in A]))
 
 
 def hms_update_residual(ctx, pr, p, u, delta, a, u_out, r_out, norms_out):

@@ -747,6 +747,47 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
   return HMS_OK;
 }
 
+namespace {
+// 1 if ptr is device or managed memory of `device`, with the given alignment
+bool device_ptr_ok(const void* ptr, int device, size_t align) {
+  if (!ptr || ((uintptr_t)ptr % align) != 0) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == device;
+}
+}  // namespace
+
+hms_status hms_residual_noalloc(hms_problem* pr, const double* p, const double* u, double* r, double* norms) {
+  if (!pr) return HMS_ERR_ARG;
+  hms_context* c = pr->ctx;
+  if (!p || !u || !r) return fail(c, HMS_ERR_ARG, "hms_residual_noalloc: p, u and r are required");
+  if ((const void*)r == (const void*)p || (const void*)r == (const void*)u)
+    return fail(c, HMS_ERR_ARG, "hms_residual_noalloc: r may not alias p or u");
+  const int tiles = residual_noalloc_tiles(pr->lv);
+  if (tiles > HMS_RESIDUAL_NOALLOC_MAX_TILES)
+    return fail(c, HMS_ERR_ARG,
+                "hms_residual_noalloc: the lattice needs " + std::to_string(tiles) +
+                    " tiles of 32 x 8 nodes, the static scratch holds " +
+                    std::to_string(HMS_RESIDUAL_NOALLOC_MAX_TILES) + "; use hms_residual");
+  CKC(c, cudaSetDevice(c->device));
+  if (!device_ptr_ok(p, c->device, 16) || !device_ptr_ok(u, c->device, 16) || !device_ptr_ok(r, c->device, 16))
+    return fail(c, HMS_ERR_ARG, "hms_residual_noalloc: p, u, r must be 16-byte aligned device memory of the "
+                                "context's device");
+  if (norms && !device_ptr_ok(norms, c->device, 8))
+    return fail(c, HMS_ERR_ARG, "hms_residual_noalloc: norms must be 8-byte aligned device memory or NULL");
+  double* partials = nullptr;
+  unsigned* ticket = nullptr;
+  CKC(c, residual_noalloc_scratch(c->device, &partials, &ticket));
+  CKC(c, launch_residual_noalloc(c->stream, pr->lv, (const double2*)u, (const double2*)p, (double2*)r, partials,
+                                 ticket, norms));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  return HMS_OK;
+}
+
 }  // extern "C"
 
 namespace hms {

@@ -116,6 +116,11 @@ cudaError_t launch_update_residual(cudaStream_t s, const LatView& lv, const doub
 int update_residual_blocks(const LatView& lv);
 cudaError_t launch_load_norms(cudaStream_t s, const LatView& lv, double2* p, double* partials,
                               unsigned* ticket, IterCtl* ctl);
+// residual_noalloc.cu
+int residual_noalloc_tiles(const LatView& lv);
+cudaError_t residual_noalloc_scratch(int device, double** partials, unsigned** ticket);
+cudaError_t launch_residual_noalloc(cudaStream_t s, const LatView& lv, const double2* u, const double2* p,
+                                    double2* r, double* partials, unsigned* ticket, double* norms_out);
 // setup.cu
 cudaError_t launch_set_factor(cudaStream_t s, const LatView& lv, const long long* set_off,
                               double* f64, float* f32, double* scratch, int grid, int* err);
