@@ -21,6 +21,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -44,6 +45,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--ncu-case", choices=["fp64", "mixed"], default=None,
+                    help="only run --ncu-iters updates of the workload once (for ncu captures); no JSON line")
+    ap.add_argument("--ncu-iters", type=int, default=1)
     return ap.parse_args()
 
 
@@ -101,13 +105,16 @@ def src_sha(name):
 
 
 def traffic_for(kernel, workload, src):
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum of one
+    ncu capture) from the TRAFFIC lines of the committed kernel summary, or
+    None if the kernel's source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "kernels_lattice1024_lognormal.md")
     try:
-        d = json.load(open(p))
-        e = d[kernel]
-        if e.get("workload") == workload and e.get("src_sha") == src_sha(src):
-            return e["bytes_per_launch"]
-    except Exception:
+        for line in open(p):
+            m = re.match(r"TRAFFIC (\S+) workload=(\S+) src_sha=(\S+) bytes_per_launch=(\d+)", line.strip())
+            if m and m.group(1) == kernel and m.group(2) == workload and m.group(3) == src_sha(src):
+                return int(m.group(4))
+    except OSError:
         pass
     return None
 
@@ -228,6 +235,25 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- profiling run
+def run_ncu_case(args):
+    """Setup plus --ncu-iters updates of the bench workload, untimed: the
+    command the committed ncu summaries were captured with."""
+    import numpy as np
+    from paper_1208_4093_gb300 import capi
+    c = case()
+    ctx = capi.hms_context_create(0)
+    prec = capi.HMS_FP64 if args.ncu_case == "fp64" else capi.HMS_MIXED
+    pr = capi.hms_problem_create(ctx, c.nx, c.ny, c.sx, c.sy, ea=c.ea_array(), precision=prec, tol=0.0,
+                                 max_iter=args.ncu_iters)
+    p = c.load_array().reshape(1, -1)
+    u = np.empty_like(p)
+    capi.hms_solve(ctx, pr, p, u, allow_no_convergence=True)
+    capi.hms_problem_destroy(pr)
+    capi.hms_context_destroy(ctx)
+    print(f"{args.ncu_case}: {args.ncu_iters} updates done")
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -342,9 +368,10 @@ def run_ours(args, rank, world, local_rank):
         rooflines[name] = roof
 
     # kernels launched per solve: graph batches of 16 iterations, each iteration
-    # 7 + 2 * coarse_solves - 1 kernels (4 solves on the FP64 path) + 1 norm kernel
+    # 8 kernels + coarse_solves solves + (coarse_solves - 1) refinement
+    # residuals (5 solves on the FP64 path), plus 1 load-norm kernel per solve
     batches = math.ceil((nit64 + 1) / 16)
-    per_iter = 7 + 2 * 4 - 1
+    per_iter = 8 + 5 + 4
     launches = args.steps * (batches * 16 * per_iter + 1)
 
     ms_med = statistics.median(ms64)
@@ -403,7 +430,9 @@ def main():
             torch.cuda.set_device(local_rank)
         dist.init_process_group(backend)
     try:
-        if args.impl == "reference":
+        if args.ncu_case:
+            run_ncu_case(args)
+        elif args.impl == "reference":
             run_reference(args, rank, world)
         else:
             run_ours(args, rank, world, local_rank)
