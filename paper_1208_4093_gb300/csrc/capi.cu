@@ -417,7 +417,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
       for (int j = j0; j < j0 + h; ++j) nodd += (j & 1);
       rp[I].x = lv.L * ((double)i0 + 0.5 * (double)(w - 1) + 0.5 * (double)nodd / (double)h);
       rp[I].y = lv.L * SQ3_2 * ((double)j0 + 0.5 * (double)(h - 1));
-      so[I + 1] = so[I] + set_factor_size(2 * w, h);
+      so[I + 1] = so[I] + set_factor_stride(2 * w, h);
     }
     CKP(palloc(pr, &pr->rep, lv.M));
     CKP(cudaMemcpy(pr->rep, rp.data(), lv.M * sizeof(double2), cudaMemcpyHostToDevice));

@@ -105,6 +105,21 @@ __host__ __device__ inline long long set_factor_size(int nb, int h) {
 __host__ __device__ inline long long mat_off(int nb, int k) {
   return (long long)((k + 1) / 2) * linv_size(nb) + (long long)(k / 2) * b_size(nb);
 }
+// After these, a second copy of the same matrices stored by columns, read by
+// the back substitution (offset set_factor_size + mat_off, same sizes):
+//   Linv_j^T: row c holds Linv_j[r][c] for r = c..nb-1
+//   B_j^T:    row c holds B_j[r][c] for r = 0..bt_hi(c), bt_hi(c) = min(nb-1, c+3)
+__host__ __device__ inline long long lt_row_off(int nb, int c) {
+  return (long long)c * nb - (long long)c * (c - 1) / 2;
+}
+__host__ __device__ inline int bt_hi(int nb, int c) { return c + 3 < nb - 1 ? c + 3 : nb - 1; }
+__host__ __device__ inline long long bt_row_off(int nb, int c) {
+  // sum_{c' < c} min(nb, c' + 4)
+  const long long K = nb > 4 ? nb - 4 : 0;  // rows c' < K hold c' + 4 < nb entries
+  if (c <= K) return (long long)c * (c - 1) / 2 + 4LL * c;
+  return K * (K - 1) / 2 + 4 * K + (long long)(c - K) * nb;
+}
+__host__ __device__ inline long long set_factor_stride(int nb, int h) { return 2 * set_factor_size(nb, h); }
 
 // ---- launchers (each returns the launch error) ----
 // residual.cu

@@ -11,15 +11,20 @@
 //
 // One CTA per set.  The set's block-bidiagonal factor (setup.cu) is a stream
 // of matrices Linv_0, B_1, Linv_1, ..., consumed in order by the forward
-// substitution and in reverse order by the back substitution:
+// substitution and, from the copy stored by columns, in reverse order by the
+// back substitution:
 //   forward  y_j = Linv_j (r_j - B_j y_{j-1})
 //   backward x_j = Linv_j^T (y_j - B_{j+1}^T x_{j+1})
-// Each matrix is staged in shared memory by a 1-D bulk copy (cp.async.bulk,
-// completion on an mbarrier), double-buffered so the next matrix streams in
-// while the current one is applied.  The solve runs in T = double (FP64
-// path) or T = float (mixed path, FP32 factor).  While x_j = delta is
-// finalised, each thread accumulates its DOF's share of the nine sums of
-// P_I = V_I^T r_I in FP64.
+// so both passes are products of packed rows with a vector.  Each matrix is
+// staged in shared memory by a 1-D bulk copy (cp.async.bulk, completion on an
+// mbarrier), three slots deep so two matrices stream in while one is applied.
+// Rows r and nb-1-r of a matrix go to a group of G threads as one combined
+// index range of almost constant length (nb+1 for the triangles, about nb+7
+// for the B blocks), so every lane of a warp runs the same number of FMAs.
+// The solve runs in T = double (FP64 path, G = 2: the FP64 pipe is the bound,
+// so the fewest reduction adds) or T = float (mixed path, FP32 factor, G = 4).
+// While x_j = delta is finalised, each thread accumulates its DOF's share of
+// the nine sums of P_I = V_I^T r_I in FP64.
 #include "hms_internal.cuh"
 #include "ptx.cuh"
 
@@ -33,18 +38,17 @@ __device__ inline double warp_sum_d(double v) {
   for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
   return v;
 }
-__device__ inline float warp_sum_f(float v) {
-#pragma unroll
-  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-  return v;
-}
-__device__ inline double wsum(double v) { return warp_sum_d(v); }
-__device__ inline float wsum(float v) { return warp_sum_f(v); }
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+__device__ inline double2 make_vec2(double x, double y) { return make_double2(x, y); }
+__device__ inline float2 make_vec2(float x, float y) { return make_float2(x, y); }
 
 constexpr int NSLOT = 3;  // matrices staged in shared memory (two in flight while one is applied)
 
 struct RelaxSmem {
-  size_t slot_elems, ycur_off, z_off, w_off, x_off, part_off, total_elems;
+  size_t slot_elems, ycur_off, z_off, w_off, x_off, total_elems;
 };
 
 template <typename T>
@@ -58,9 +62,88 @@ __host__ __device__ inline RelaxSmem relax_layout(int nb) {
   L.z_off = up(L.ycur_off + nb);
   L.w_off = up(L.z_off + nb);
   L.x_off = up(L.w_off + nb);
-  L.part_off = up(L.x_off + nb);
-  L.total_elems = up(L.part_off + (size_t)NW * nb);
+  L.total_elems = up(L.x_off + nb);
   return L;
+}
+
+// Dot products of rows ra and rb (ra < rb) of a packed matrix M with v.  Row
+// x holds v-indices lo_x .. lo_x + len_x - 1, stored from M + off_x.  The G
+// threads of a group (g = 0..G-1) walk the combined index t = 0..lenA+lenB-1
+// with stride G, in CH interleaved chains of FMAs.  Returns the row sums in
+// every thread of the group.
+template <typename T, int G, int CH>
+__device__ inline void pair_dot(const T* __restrict__ pA, int loA, int lenA, const T* __restrict__ pB, int loB,
+                                int lenB, const T* __restrict__ v, int g, T& outA, T& outB) {
+  const int len = lenA + lenB;
+  T a[CH], b[CH];
+#pragma unroll
+  for (int q = 0; q < CH; ++q) a[q] = b[q] = T(0);
+  auto step = [&](int tt, T& ca, T& cb) {
+    const bool inA = tt < lenA;
+    const T* mp = inA ? pA + tt : pB + (tt - lenA);
+    const T* vp = inA ? v + (loA + tt) : v + (loB + tt - lenA);
+    T c = inA ? ca : cb;
+    c = fma(*mp, *vp, c);
+    if (inA) ca = c; else cb = c;
+  };
+  int t = g;
+  for (; t + (CH - 1) * G < len; t += CH * G) {
+#pragma unroll
+    for (int q = 0; q < CH; ++q) step(t + q * G, a[q], b[q]);
+  }
+#pragma unroll
+  for (int q = 0; q + 1 < CH; ++q)
+    if (t + q * G < len) step(t + q * G, a[q], b[q]);
+  T sa = a[0], sb = b[0];
+#pragma unroll
+  for (int q = 1; q < CH; ++q) sa += a[q], sb += b[q];
+#pragma unroll
+  for (int m = 1; m < G; m <<= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, m);
+    sb += __shfl_xor_sync(0xffffffffu, sb, m);
+  }
+  outA = sa;
+  outB = sb;
+}
+
+// The four kinds of matrix rows: lowest v-index, entry count and storage offset.
+enum RowKind { ROW_LINV = 0, ROW_B, ROW_LT, ROW_BT };
+template <int K>
+__device__ inline void row_shape(int nb, int r, int& lo, int& len, long long& off) {
+  if (K == ROW_LINV) {
+    lo = 0; len = r + 1; off = linv_row_off(r);
+  } else if (K == ROW_B) {
+    lo = b_lo(r); len = nb - lo; off = b_row_off(nb, r);
+  } else if (K == ROW_LT) {
+    lo = r; len = nb - r; off = lt_row_off(nb, r);
+  } else {
+    lo = 0; len = bt_hi(nb, r) + 1; off = bt_row_off(nb, r);
+  }
+}
+
+// out(r) for every row r of the matrix: groups of G threads take the row
+// pairs (r, nb-1-r); the group's first thread calls out(r, sum) per row.
+template <typename T, int G, int CH, int K, class Out>
+__device__ inline void rows_times(const T* M, const T* v, int nb, Out out) {
+  const int npair = nb / 2;  // nb = 2w is even
+  const int g = threadIdx.x % G;
+  for (int base = 0; base < npair; base += NT / G) {
+    const int pq = base + (int)threadIdx.x / G;
+    if (base + (int)(threadIdx.x & ~31u) / G >= npair) break;  // the whole warp is past the last pair
+    const bool active = pq < npair;
+    const int ra = active ? pq : 0, rb = nb - 1 - ra;
+    int loA, lenA, loB, lenB;
+    long long offA, offB;
+    row_shape<K>(nb, ra, loA, lenA, offA);
+    row_shape<K>(nb, rb, loB, lenB, offB);
+    if (!active) lenA = lenB = 0;
+    T sa, sb;
+    pair_dot<T, G, CH>(M + offA, loA, lenA, M + offB, loB, lenB, v, g, sa, sb);
+    if (active && g == 0) {
+      out(ra, sa);
+      out(rb, sb);
+    }
+  }
 }
 
 template <typename T>
@@ -75,6 +158,7 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
   __shared__ int abort_flag;
   if (ctl && *(volatile const int*)&ctl->done) return;
 
+  using T2 = typename Vec2<T>::type;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int I = blockIdx.x;
   const int Ix = I % lv.Mx, Iy = I / lv.Mx;
@@ -87,9 +171,9 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
   T* zbuf = sm + LY.z_off;
   T* wbuf = sm + LY.w_off;
   T* xbuf = sm + LY.x_off;
-  T* part = sm + LY.part_off;
   T* yg = yglob + (size_t)I * ystride;  // all y_j, read back by the backward pass
   const T* fset = fac + set_off[I];
+  const T* fset_t = fset + set_factor_size(nb, h);  // the copy stored by columns
   const double* rg = reinterpret_cast<const double*>(r);
   const int nmat = 2 * h - 1;
   const int nops = 2 * nmat;
@@ -101,7 +185,7 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
     const uint32_t bytes = (uint32_t)(((k & 1) ? b_size(nb) : linv_size(nb)) * sizeof(T));
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, bytes);
-    bulk_g2s(sm + (size_t)(o % NSLOT) * LY.slot_elems, fset + mat_off(nb, k), bytes, bar);
+    bulk_g2s(sm + (size_t)(o % NSLOT) * LY.slot_elems, (o < nmat ? fset : fset_t) + mat_off(nb, k), bytes, bar);
   };
 
   if (tid == 0) {
@@ -120,6 +204,9 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
 #pragma unroll
   for (int m = 0; m < NMODES; ++m) pacc[m] = 0.0;
   const double2 rep = lv.rep[I];
+  // xi of node tid of the set on even and odd lattice rows (Eq. 10)
+  const double xi_even = fma(lv.L, (double)(i0 + tid), -rep.x);
+  const double xi_odd = fma(lv.L, (double)(i0 + tid) + 0.5, -rep.x);
 
   for (int o = 0; o < nops; ++o) {
     const int k = mat_of_op(o);
@@ -131,130 +218,56 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
     // the slot of op o - 1 is free: stream op o + NSLOT - 1 into it
     if (tid == 0 && o + NSLOT - 1 < nops) issue(o + NSLOT - 1);
     const T* M = sm + (size_t)(o % NSLOT) * LY.slot_elems;
+    // 4 threads per row pair keep two warps per SMSP issuing; FP64 FMAs are
+    // slow enough that one chain per thread has no stall, FP32 ones want two
+    constexpr int G = 4, CH = sizeof(T) == 8 ? 1 : 2;
     if (o < nmat) {
-      // ---------------- forward: a quad of threads per pair of rows ----------------
-      // Rows r and nb-1-r (together nb+1 entries of Linv, about nb+7 of B) go
-      // to one quad; its threads take every fourth column, so a row costs two
-      // shuffles instead of a warp-wide reduction.
-      const T* vin = is_b ? ycur : zbuf;
-      const int npair = (nb + 1) / 2;
-      const int sub = tid & 3;
+      // ---------------- forward ----------------
       const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
-      for (int base = 0; base < npair; base += NT / 4) {
-        const int pq = base + (tid >> 2);
-        const bool active = pq < npair;
-        const int ra = active ? pq : 0, rb2 = nb - 1 - ra;
-        T acc_a = 0, acc_b = 0;
-        if (active) {
-          {
-            const int lo = is_b ? b_lo(ra) : 0, hi = is_b ? nb - 1 : ra;
-            const T* row = is_b ? M + b_row_off(nb, ra) - lo : M + linv_row_off(ra);
-            for (int c = lo + sub; c <= hi; c += 4) acc_a = fma(row[c], vin[c], acc_a);
-          }
-          if (rb2 != ra) {
-            const int lo = is_b ? b_lo(rb2) : 0, hi = is_b ? nb - 1 : rb2;
-            const T* row = is_b ? M + b_row_off(nb, rb2) - lo : M + linv_row_off(rb2);
-            for (int c = lo + sub; c <= hi; c += 4) acc_b = fma(row[c], vin[c], acc_b);
-          }
-        }
-        acc_a += __shfl_xor_sync(0xffffffffu, acc_a, 1);
-        acc_b += __shfl_xor_sync(0xffffffffu, acc_b, 1);
-        acc_a += __shfl_xor_sync(0xffffffffu, acc_a, 2);
-        acc_b += __shfl_xor_sync(0xffffffffu, acc_b, 2);
-        if (active && sub == 0) {
-          if (is_b) {
-            zbuf[ra] = (T)rg[rowbase + ra] - acc_a;
-            if (rb2 != ra) zbuf[rb2] = (T)rg[rowbase + rb2] - acc_b;
-          } else {
-            part[ra] = acc_a;  // y_j, copied to ycur below
-            if (rb2 != ra) part[rb2] = acc_b;
-          }
-        }
+      if (is_b) {
+        // z = r_j - B_j y_{j-1}
+        rows_times<T, G, CH, ROW_B>(M, ycur, nb, [&](int row, T s) { zbuf[row] = (T)rg[rowbase + row] - s; });
+      } else {
+        // y_j = Linv_j z
+        T* yj = yg + (size_t)j * nb;
+        rows_times<T, G, CH, ROW_LINV>(M, zbuf, nb, [&](int row, T s) {
+          ycur[row] = s;
+          yj[row] = s;
+        });
       }
       __syncthreads();
-      if (!is_b) {
-        for (int c = tid; c < nb; c += NT) {
-          const T v = part[c];
-          ycur[c] = v;
-          yg[(size_t)j * nb + c] = v;
-        }
-        __syncthreads();
-      }
     } else {
       // ---------------- backward ----------------
-      T acc[MAX_NB / 32];
-#pragma unroll
-      for (int q = 0; q < MAX_NB / 32; ++q) acc[q] = 0;
       if (!is_b) {
         // x_j = Linv_j^T w  (w = y_{h-1} for the last row)
         const T* wv = (j == h - 1) ? ycur : wbuf;
-        for (int rr = warp; rr < nb; rr += NW) {
-          const T* row = M + linv_row_off(rr);
-          const T v = wv[rr];
-#pragma unroll
-          for (int q = 0; q < MAX_NB / 32; ++q) {
-            if (32 * q > rr) break;  // warp-uniform: the rest of the row is beyond the diagonal
-            const int c = lane + 32 * q;
-            if (c <= rr) acc[q] = fma(row[c], v, acc[q]);
-          }
-        }
-      } else {
-        // w = y_{j-1} - B_j^T x_j
-        for (int rr = warp; rr < nb; rr += NW) {
-          const int lo = b_lo(rr);
-          const T* row = M + b_row_off(nb, rr) - lo;
-          const T v = xbuf[rr];
-#pragma unroll
-          for (int q = 0; q < MAX_NB / 32; ++q) {
-            if (32 * q >= nb) break;
-            if (32 * q + 31 < lo) continue;  // warp-uniform: chunk left of the row's profile
-            const int c = lane + 32 * q;
-            if (c >= lo && c < nb) acc[q] = fma(row[c], v, acc[q]);
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < MAX_NB / 32; ++q) {
-        const int c = lane + 32 * q;
-        if (c < nb) part[warp * nb + c] = acc[q];
-      }
-      __syncthreads();
-      if (!is_b) {
+        rows_times<T, G, CH, ROW_LT>(M, wv, nb, [&](int row, T s) { xbuf[row] = s; });
+        __syncthreads();
         const size_t node0 = (size_t)(j0 + j) * lv.nx + i0;
-        const size_t rowbase = 2 * node0;
-        const double eta = lv.L * SQ3_2 * (double)(j0 + j) - rep.y;
-        for (int c = tid; c < nb; c += NT) {
-          T s = 0;
-#pragma unroll
-          for (int ww = 0; ww < NW; ++ww) s += part[ww * nb + c];
-          xbuf[c] = s;
-          delta[rowbase + c] = s;
-          // P = V^T r (Eq. 7) for this DOF
-          const int il = c >> 1, comp = c & 1;
-          const double rv = rg[rowbase + c];
-          const double xi = lv.L * ((double)(i0 + il) + 0.5 * (double)((j0 + j) & 1)) - rep.x;
-          const double dr = (double)s * rv;
-          if (comp == 0) {
-            pacc[0] += rv;
-            pacc[2] = fma(xi, rv, pacc[2]);
-            pacc[3] = fma(eta, rv, pacc[3]);
-          } else {
-            pacc[1] += rv;
-            pacc[4] = fma(xi, rv, pacc[4]);
-            pacc[5] = fma(eta, rv, pacc[5]);
-          }
+        const double eta = fma(lv.L * SQ3_2, (double)(j0 + j), -rep.y);
+        const bool odd = ((j0 + j) & 1) != 0;
+        if (tid < w) {
+          // delta and P = V^T r (Eq. 7) for the two DOFs of node tid
+          const T sx = xbuf[2 * tid], sy = xbuf[2 * tid + 1];
+          T2* d2 = reinterpret_cast<T2*>(delta);
+          d2[node0 + tid] = make_vec2(sx, sy);
+          const double2 rv = r[node0 + tid];
+          const double xi = odd ? xi_odd : xi_even;
+          const double dr = fma((double)sx, rv.x, (double)sy * rv.y);
+          pacc[0] += rv.x;
+          pacc[1] += rv.y;
+          pacc[2] = fma(xi, rv.x, pacc[2]);
+          pacc[3] = fma(eta, rv.x, pacc[3]);
+          pacc[4] = fma(xi, rv.y, pacc[4]);
+          pacc[5] = fma(eta, rv.y, pacc[5]);
           pacc[6] += dr;
           pacc[7] = fma(xi, dr, pacc[7]);
           pacc[8] = fma(eta, dr, pacc[8]);
         }
       } else {
+        // w = y_{j-1} - B_j^T x_j
         const T* yp = yg + (size_t)(j - 1) * nb;
-        for (int c = tid; c < nb; c += NT) {
-          T s = 0;
-#pragma unroll
-          for (int ww = 0; ww < NW; ++ww) s += part[ww * nb + c];
-          wbuf[c] = yp[c] - s;
-        }
+        rows_times<T, G, CH, ROW_BT>(M, xbuf, nb, [&](int row, T s) { wbuf[row] = yp[row] - s; });
       }
       __syncthreads();
     }

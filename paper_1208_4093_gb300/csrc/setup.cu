@@ -12,7 +12,8 @@
 // Cholesky factor is block bidiagonal: L_jj (dense lower) and
 // B_j = L_{j,j-1}, whose row r is zero left of column r - 3 (the band of
 // k^Inner reaches 2w + 3 DOFs back).  Stored per set: Linv_j = L_jj^-1 and
-// B_j, so the solves of relax.cu are matrix-vector products only.
+// B_j, so the solves of relax.cu are matrix-vector products only, and a
+// second copy of both stored by columns for the back substitution.
 //
 // One CTA per set (grid-stride over sets), FP64 throughout; the FP32 copy for
 // the mixed path is rounded from the FP64 factor.
@@ -57,6 +58,7 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
     double* S = sm;          // packed lower nb x nb
     double* Li = sm + npk;   // packed lower nb x nb
     const long long base = set_off[I];
+    const long long tr_base = set_factor_size(nb, h);  // the column-stored copy
     if (tid == 0) bad = 0;
 
     for (int jj = 0; jj < h; ++jj) {
@@ -132,18 +134,27 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
         }
       }
       __syncthreads();
-      // 5. store Linv_j
+      // 5. store Linv_j, and Linv_j^T by rows (= Linv_j by columns)
       {
         const long long o = base + mat_off(nb, 2 * jj);
         for (long long q = tid; q < npk; q += NT) {
           if (f64) f64[o + q] = Li[q];
           if (f32) f32[o + q] = (float)Li[q];
         }
+        const long long ot = base + tr_base + mat_off(nb, 2 * jj);
+        for (int c = warp; c < nb; c += NT / 32)
+          for (int r = c + lane; r < nb; r += 32) {
+            const long long q = ot + lt_row_off(nb, c) + (r - c);
+            const double v = Li[pk(r, c)];
+            if (f64) f64[q] = v;
+            if (f32) f32[q] = (float)v;
+          }
       }
       // 6. B_{j+1} = K_{j+1,j} Linv_j^T
       if (jj + 1 < h) {
         const int ja = j + 1, offa = ja & 1;
         const long long o = base + mat_off(nb, 2 * jj + 1);
+        const long long ot = base + tr_base + mat_off(nb, 2 * jj + 1);
         for (int r = warp; r < nb; r += NT / 32)
           for (int c = b_lo(r) + lane; c < nb; c += 32) {
           const long long q = b_row_off(nb, r) + (c - b_lo(r));
@@ -169,8 +180,8 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
             }
           }
           Bprev[q] = acc;
-          if (f64) f64[o + q] = acc;
-          if (f32) f32[o + q] = (float)acc;
+          if (f64) f64[o + q] = acc, f64[ot + bt_row_off(nb, c) + r] = acc;
+          if (f32) f32[o + q] = (float)acc, f32[ot + bt_row_off(nb, c) + r] = (float)acc;
         }
       }
       __syncthreads();
