@@ -90,7 +90,8 @@ typedef struct {
   int32_t profile;           /* 1 = time every kernel with CUDA events */
   int32_t coarse_factor;     /* factor of Eq. 8: 0 = auto (FP64 for one- or two-node-wide
                                 set tiles, else FP32), 1 = FP32 with FP64 refinement,
-                                2 = FP64 */
+                                2 = FP64, 3 = FP32 solved in 16-row steps only (without
+                                the inverted 64 x 64 diagonal blocks used otherwise) */
 } hms_options;
 
 /* Context: one device, one CUDA stream.  device = CUDA ordinal. */

@@ -54,7 +54,9 @@ struct hms_problem {
   double* res = nullptr;
   void* lcol = nullptr;      // L in column layout (float or double)
   void* lrow = nullptr;      // scaled band in row layout, then L in row layout
-  void* dinv = nullptr;      // inverted 32 x 32 diagonal blocks of L
+  void* dinv = nullptr;      // inverted 16 x 16 diagonal blocks of L
+  float* xinv = nullptr;     // per 64-row block of the FP32 L: inverted diagonal block and band neighbours
+  int big_stages = 0;        // pipeline depth of the 64-row block solve, 0 = 16-row solve
   int* dropped = nullptr;
   unsigned long long* cstat = nullptr;  // refinement state of the upper-level solve
   double* partials = nullptr;
@@ -163,6 +165,10 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
   mark();
   e = launch_coarse_factor(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped, pr->ctl);
   if (e != cudaSuccess) return e;
+  if (pr->big_stages > 0) {
+    e = launch_coarse_blockinv(s, pr->n_c, pr->bw, pr->lcol, pr->lrow, pr->xinv, pr->ctl);
+    if (e != cudaSuccess) return e;
+  }
   mark();
   for (int q = 0; q < pr->nsolve; ++q) {
     if (q > 0) {
@@ -171,8 +177,14 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
       if (e != cudaSuccess) return e;
       mark();
     }
-    e = launch_coarse_solve(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped,
-                            q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, pr->ctl, pr->err);
+    if (pr->big_stages > 0)
+      e = launch_coarse_solve_big(s, pr->big_stages, pr->n_c, pr->bw, pr->lcol, pr->lrow, pr->xinv, pr->dropped,
+                                  q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, pr->ctl,
+                                  pr->err);
+    else
+      e = launch_coarse_solve(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped,
+                              q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, pr->ctl,
+                              pr->err);
     if (e != cudaSuccess) return e;
     mark();
   }
@@ -300,7 +312,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return fail(c, HMS_ERR_ARG, "bad precision");
   if (!(o->tol >= 0.0) || o->max_iter < 0) return fail(c, HMS_ERR_ARG, "bad tol / max_iter");
   if (o->coarse_solves < 0 || o->coarse_solves > 8) return fail(c, HMS_ERR_ARG, "coarse_solves must be in 0..8");
-  if (o->coarse_factor < 0 || o->coarse_factor > 2) return fail(c, HMS_ERR_ARG, "coarse_factor must be 0, 1 or 2");
+  if (o->coarse_factor < 0 || o->coarse_factor > 3) return fail(c, HMS_ERR_ARG, "coarse_factor must be in 0..3");
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
 
@@ -343,12 +355,15 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
              coarse_solve_smem_bytes(pr->n_c, pr->bw, f64) + 1024 <= (size_t)maxsm;
     };
     if (o->coarse_factor == 2) pr->coarse_fp64 = true;
-    else if (o->coarse_factor == 1) pr->coarse_fp64 = false;
+    else if (o->coarse_factor == 1 || o->coarse_factor == 3) pr->coarse_fp64 = false;
     else pr->coarse_fp64 = degenerate && fits(true);
     if (!fits(pr->coarse_fp64)) {
       delete pr;
       return fail(c, HMS_ERR_ARG, "set grid too wide for the upper-level band factorisation");
     }
+    // FP32 factor: solve by 64-row blocks with inverted diagonal blocks when
+    // that fits in shared memory (coarse_factor = 3 keeps the 16-row solve)
+    pr->big_stages = (pr->coarse_fp64 || o->coarse_factor == 3) ? 0 : coarse_big_stages(pr->n_c, pr->bw, maxsm);
   }
   if (coarse_slots_smem(lv) > (size_t)maxsm) {
     delete pr;
@@ -477,6 +492,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     pr->lrow = lr;
     pr->dinv = di;
   }
+  if (pr->big_stages > 0) CKP(palloc(pr, &pr->xinv, coarse_xinv_elems(n_c, pr->bw)));
   CKP(palloc(pr, &pr->dropped, n_c));
   CKP(palloc(pr, &pr->cstat, 4));
   CKP(cudaMemsetAsync(pr->cstat, 0, 4 * sizeof(unsigned long long), s));
@@ -735,11 +751,18 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
   CKC(c, launch_coarse_scale(s, n, bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale, pr->b,
                              pr->x, pr->dropped, nullptr));
   CKC(c, launch_coarse_factor(s, n, bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped, nullptr));
+  if (pr->big_stages > 0) CKC(c, launch_coarse_blockinv(s, n, bw, pr->lcol, pr->lrow, pr->xinv, nullptr));
   for (int q = 0; q < pr->nsolve; ++q) {
     if (q > 0)
       CKC(c, launch_coarse_residual(s, n, bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, pr->cstat, nullptr));
-    CKC(c, launch_coarse_solve(s, n, bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped,
-                               q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, nullptr, pr->err));
+    if (pr->big_stages > 0)
+      CKC(c, launch_coarse_solve_big(s, pr->big_stages, n, bw, pr->lcol, pr->lrow, pr->xinv, pr->dropped,
+                                     q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, nullptr,
+                                     pr->err));
+    else
+      CKC(c, launch_coarse_solve(s, n, bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped,
+                                 q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, nullptr,
+                                 pr->err));
   }
   CKC(c, cudaMemcpyAsync(a, pr->a, n * sizeof(double), kind_out(mem_kind), s));
   if (dropped) CKC(c, cudaMemcpyAsync(dropped, pr->dropped, n * sizeof(int32_t), kind_out(mem_kind), s));

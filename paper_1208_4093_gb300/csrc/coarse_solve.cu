@@ -25,6 +25,11 @@
 //                    the columns (rows) of L each step needs are staged by bulk
 //                    copies several steps ahead.  Adds the correction to the
 //                    FP64 solution and writes a = D^-1/2 x.
+//   k_coarse_blockinv / k_coarse_solve_big  (FP32 factor, when it fits in
+//                    shared memory): the inverses of the 64 x 64 diagonal
+//                    blocks of L are formed once per factor (one CTA per
+//                    block), and each solve then takes n/64 block steps of a
+//                    dense 64 x 64 product and a one-thread-per-row update.
 //   k_coarse_residual many CTAs, FP64: res = b - A x over the band.
 #include "hms_internal.cuh"
 #include "ptx.cuh"
@@ -57,16 +62,6 @@ struct Stages<double> {
   static constexpr int v = 2;
 };
 
-__device__ inline float wsum(float v) {
-#pragma unroll
-  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-  return v;
-}
-__device__ inline double wsum(double v) {
-#pragma unroll
-  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-  return v;
-}
 // 1/sqrt(x): the hardware approximation in FP32 (the factor only needs to be a
 // good preconditioner: FP64 refinement restores the accuracy), exact in FP64
 __device__ inline float trsqrt(float x) { return rsqrtf(x); }
@@ -549,6 +544,293 @@ __global__ void __launch_bounds__(FTS) k_coarse_solve(int n, int bw, const T* __
   }
 }
 
+// ---- solves with inverted 64 x 64 diagonal blocks (FP32 factor) ----
+constexpr int NBB = 64;   // rows per block of the block substitution
+constexpr int LDX = 72;   // row stride of the stored block inverses (conflict-free row reads)
+constexpr int LDR = 68;   // row stride of the stored band neighbours (conflict-free 16-byte row reads)
+constexpr int FTB = 512;  // threads of the block-substitution CTA
+
+// Per NBB-row block K of the FP32 factor, stored one after another:
+//   X_K   = L_KK^-1                         NBB x LDX, lower
+//   X_K^T                                   NBB x LDX, upper
+//   R_K[q][c] = L[r1 + q][r0 + c]           bw x LDR, the band rows below the block
+//   U_K[q][c] = L[r0 + c][r0 - bw + q]      bw x LDR, the band columns left of the block
+// (r0 = K NBB, r1 = min(r0 + NBB, n); zero outside the band and the matrix).
+__host__ __device__ inline size_t blk_elems(int bw) { return 2 * (size_t)NBB * LDX + 2 * (size_t)bw * LDR; }
+
+// The per-block matrices above from the FP32 factor (row and column layouts);
+// rows of X past n are identity rows.  Per block, one CTA of 256 threads
+// inverts the diagonal block and three more copy a third of R_K and U_K each.
+__global__ void __launch_bounds__(256) k_coarse_blockinv(int n, int bw, const float* __restrict__ lcol,
+                                                         const float* __restrict__ lrow, float* __restrict__ xinv,
+                                                         const IterCtl* ctl) {
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  __shared__ float Ls[NBB][NBB + 1];
+  __shared__ float Xs[NBB][NBB + 1];
+  const int tid = threadIdx.x;
+  const int K = blockIdx.x, r0 = K * NBB, nr = min(NBB, n - r0);
+  const int ldw = bw + 1;
+  float* X = xinv + (size_t)K * blk_elems(bw);
+  float* XT = X + NBB * LDX;
+  float* R = XT + NBB * LDX;
+  float* U = R + (size_t)bw * LDR;
+  if (blockIdx.y > 0) {
+    // R_K and U_K, a third of their rows per CTA
+    const int r1 = r0 + nr;
+    const int part = (bw + gridDim.y - 2) / (gridDim.y - 1);
+    const int qa = (blockIdx.y - 1) * part, qb = min(bw, qa + part);
+#pragma unroll 4
+    for (int idx = qa * LDR + tid; idx < qb * LDR; idx += blockDim.x) {
+      const int q = idx / LDR, c = idx % LDR;
+      float rv = 0.f, uv = 0.f;
+      if (c < nr) {
+        const int i = r1 + q, k = r0 + c;  // R: L[i][k], i > k, from the row layout (coalesced over c)
+        if (i < n && i - k <= bw) rv = lrow[(size_t)i * ldw + (i - k)];
+        const int iu = r0 - bw + q;        // U: L[k][iu], k > iu, from the column layout (coalesced over c)
+        if (iu >= 0 && k - iu <= bw) uv = lcol[(size_t)iu * ldw + (k - iu)];
+      }
+      R[idx] = rv;
+      U[idx] = uv;
+    }
+    return;
+  }
+#pragma unroll 8
+  for (int idx = tid; idx < NBB * NBB; idx += blockDim.x) {
+    const int r = idx / NBB, c = idx % NBB;
+    float v = 0.f;
+    if (r < nr && c <= r && r - c <= bw) v = lrow[(size_t)(r0 + r) * ldw + (r - c)];  // coalesced over c
+    if (r >= nr && r == c) v = 1.f;
+    Ls[r][c] = v;
+  }
+  __syncthreads();
+  // X = L^-1 by 16 x 16 blocks: the four diagonal blocks by column
+  // substitution (64 threads, one column each), then block rows i = 1..3:
+  //   X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj   for all j < i at once
+  constexpr int B = 16;
+  if (tid < NBB) {
+    const int b = tid / B, c = tid % B, o = b * B;
+    for (int r = 0; r < B; ++r) {
+      float acc = (r == c) ? 1.f : 0.f;
+#pragma unroll
+      for (int k = 0; k < B; ++k)
+        if (k >= c && k < r) acc = fmaf(-Ls[o + r][o + k], Xs[o + k][o + c], acc);
+      Xs[o + r][o + c] = r < c ? 0.f : acc / Ls[o + r][o + r];
+    }
+  }
+  __syncthreads();
+  __shared__ float Ts[3][B][B + 1];
+  const int rr = tid / B, cc = tid % B;
+  for (int i = 1; i < NBB / B; ++i) {
+    for (int j = 0; j < i; ++j) {
+      float acc = 0.f;
+      for (int k = j; k < i; ++k) {
+#pragma unroll
+        for (int m = 0; m < B; ++m) acc = fmaf(Ls[i * B + rr][k * B + m], Xs[k * B + m][j * B + cc], acc);
+      }
+      Ts[j][rr][cc] = acc;
+    }
+    __syncthreads();
+    for (int j = 0; j < i; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int m = 0; m < B; ++m) acc = fmaf(Xs[i * B + rr][i * B + m], Ts[j][m][cc], acc);
+      Xs[i * B + rr][j * B + cc] = -acc;
+    }
+    __syncthreads();
+  }
+  // the zero upper blocks
+  for (int idx = tid; idx < NBB * NBB; idx += blockDim.x) {
+    const int r = idx / NBB, c = idx % NBB;
+    if (c / B > r / B) Xs[r][c] = 0.f;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < NBB * LDX; idx += blockDim.x) {
+    const int r = idx / LDX, c = idx % LDX;
+    X[idx] = c < NBB ? Xs[r][c] : 0.f;
+    XT[idx] = c < NBB ? Xs[c][r] : 0.f;
+  }
+}
+
+__host__ __device__ inline int big_stage_elems(int bw) { return bw * LDR + NBB * LDX; }
+
+// Block forward / back substitution with the FP32 factor, NBB rows per step:
+//   forward   y_K = X_K t_K,     t_i -= sum_c R_K[i - r1][c] y_c        (the next bw rows)
+//   backward  x_K = X_K^T t_K,   t_i -= sum_c U_K[i - r0 + bw][c] x_c   (the previous bw rows)
+// then x += y in FP64 and a = D^-1/2 x; the same refinement control as
+// k_coarse_solve.  Each step's R_K (U_K) and X_K (X_K^T) are staged by bulk
+// copies S - 1 steps ahead.
+template <int S>
+__global__ void __launch_bounds__(FTB) k_coarse_solve_big(int n, int bw, const float* __restrict__ xinv,
+                                                          const int* __restrict__ dropped,
+                                                          const double* __restrict__ res, double* __restrict__ x,
+                                                          const double* __restrict__ scale,
+                                                          double* __restrict__ a_out, unsigned long long* cstat,
+                                                          int first, const IterCtl* ctl, int* err) {
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  __shared__ int skip;
+  if (threadIdx.x == 0) {
+    if (first) {
+      skip = 0;
+    } else {
+      const double bmax = __longlong_as_double((long long)cstat[0]);
+      const double rmax = __longlong_as_double((long long)cstat[1]);
+      skip = (cstat[2] != 0ull) || !(rmax > 1e-14 * bmax);
+      if (skip) cstat[2] = 1ull;
+    }
+  }
+  __syncthreads();
+  if (skip) return;
+  extern __shared__ __align__(16) unsigned char ssraw[];
+  float* ss = reinterpret_cast<float*>(ssraw);
+  __shared__ uint64_t bars[S];
+  __shared__ int abort_flag;
+  __shared__ double bred[FTB / 32];
+  __shared__ float hpart[512];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nblk = (n + NBB - 1) / NBB;
+  const int nops = 2 * nblk;
+  const int stage = big_stage_elems(bw);
+  const int xoff = stage - NBB * LDX;
+  const int n4 = (n + 3) / 4 * 4;
+  float* tv = ss;       // running right-hand side
+  float* yv = ss + n4;  // y, then x
+  const int sbase = 2 * n4 + NBB;  // yv keeps NBB spare entries for the vector loads of the last block
+  int* sdrop = reinterpret_cast<int*>(ss + sbase + (size_t)S * stage);
+
+  auto issue = [&](int o) {
+    const bool fwd = o < nblk;
+    const int K = fwd ? o : nops - 1 - o;
+    const uint32_t rb = (uint32_t)((size_t)bw * LDR * sizeof(float));
+    const uint32_t xb = NBB * LDX * sizeof(float);
+    uint64_t* bar = &bars[o % S];
+    float* dst = ss + sbase + (size_t)(o % S) * stage;
+    const float* blk = xinv + (size_t)K * blk_elems(bw);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, rb + xb);
+    bulk_g2s(dst, blk + 2 * NBB * LDX + (fwd ? 0 : (size_t)bw * LDR), rb, bar);
+    bulk_g2s(dst + xoff, blk + (fwd ? 0 : NBB * LDX), xb, bar);
+  };
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+    fence_mbar_init();
+  }
+  double bm = 0.0;
+  for (int i = tid; i < n; i += FTB) {
+    const int d = dropped[i];
+    sdrop[i] = d;
+    tv[i] = d ? 0.f : (float)res[i];
+    if (first && !d) bm = fmax(bm, fabs(res[i]));
+  }
+  for (int i = n + tid; i < n4 + NBB; i += FTB) yv[i] = 0.f;
+  if (first) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, m));
+    if (lane == 0) bred[warp] = bm;
+  }
+  __syncthreads();
+  if (first && tid == 0) {
+    double v = 0.0;
+    for (int k = 0; k < FTB / 32; ++k) v = fmax(v, bred[k]);
+    cstat[0] = (unsigned long long)__double_as_longlong(v);
+    cstat[2] = 0ull;
+  }
+  if (tid == 0) cstat[1] = 0ull;  // the next residual accumulates its max here
+  if (tid == 0)
+    for (int o = 0; o < S - 1 && o < nops; ++o) issue(o);
+  for (int o = 0; o < nops; ++o) {
+    const bool fwd = o < nblk;
+    const int K = fwd ? o : nops - 1 - o;
+    const int r0 = K * NBB, r1 = min(r0 + NBB, n), nr = r1 - r0;
+    if (o == nblk) {
+      for (int i = tid; i < n; i += FTB) tv[i] = yv[i];
+      __syncthreads();
+    }
+    if (!mbar_wait_bounded(&bars[o % S], (uint32_t)((o / S) & 1))) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) break;
+    if (tid == 32 && o + S - 1 < nops) issue(o + S - 1);
+    const float* Lb = ss + sbase + (size_t)(o % S) * stage;
+    const float* M = Lb + xoff;  // X_K (forward) or X_K^T (backward), rows of LDX
+    // (1) 8 threads per row: y_w = sum_c M[w][c] t_c (M is zero outside its triangle)
+    {
+      const int w = tid >> 3, p = tid & 7;
+      const float* mr = M + w * LDX;
+      float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < NBB / 8; k += 2) {
+        const int c0 = p + 8 * k, c1 = c0 + 8;
+        const float m0 = mr[c0], m1 = mr[c1];
+        const float t0 = c0 < nr ? tv[r0 + c0] : 0.f;
+        const float t1 = c1 < nr ? tv[r0 + c1] : 0.f;
+        v0 = fmaf(m0, t0, v0);
+        v1 = fmaf(m1, t1, v1);
+      }
+      float v = v0 + v1;
+      v += __shfl_xor_sync(0xffffffffu, v, 4);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      if (w < nr && p == 0) yv[r0 + w] = sdrop[r0 + w] ? 0.f : v;
+    }
+    __syncthreads();
+    // (2) the band rows next to the block, t_i -= sum_c B[q][c] y_c with
+    // B = R_K (rows i = r1 + q) or U_K (rows i = r0 - bw + q): threads
+    // h*256 + q take row q and the columns [32h, 32h + 32) by 16-byte loads;
+    // the two halves meet in shared memory.
+    {
+      const int qlo = fwd ? 0 : max(0, bw - r0);
+      const int qhi = fwd ? min(bw, n - r1) : bw;
+      const int ioff = fwd ? r1 : r0 - bw;  // i = ioff + q
+      const int h = tid >> 8, q0 = tid & 255;
+      const int cbase = 32 * h;
+      float yb[32];
+#pragma unroll
+      for (int c4 = 0; c4 < 32; c4 += 4) {
+        const float4 y4 = *reinterpret_cast<const float4*>(yv + r0 + cbase + c4);
+        yb[c4] = y4.x, yb[c4 + 1] = y4.y, yb[c4 + 2] = y4.z, yb[c4 + 3] = y4.w;
+      }
+      for (int qb = qlo; qb < qhi; qb += 256) {
+        const int q = qb + q0;
+        const int i = ioff + q;
+        float acc0 = 0.f, acc1 = 0.f;
+        if (q < qhi) {
+          const float* br = Lb + (size_t)q * LDR + cbase;
+#pragma unroll
+          for (int c4 = 0; c4 < 32; c4 += 4) {
+            const float4 l4 = *reinterpret_cast<const float4*>(br + c4);
+            acc0 = fmaf(l4.x, yb[c4], acc0);
+            acc1 = fmaf(l4.y, yb[c4 + 1], acc1);
+            acc0 = fmaf(l4.z, yb[c4 + 2], acc0);
+            acc1 = fmaf(l4.w, yb[c4 + 3], acc1);
+          }
+        }
+        const float part = acc0 + acc1;
+        hpart[h * 256 + q0] = part;
+        __syncthreads();
+        if (h == 0 && q < qhi) tv[i] -= hpart[q0] + hpart[256 + q0];
+        if (qb + 256 < qhi) __syncthreads();
+      }
+    }
+  }
+  if (abort_flag) {
+    if (tid == 0) {
+      for (int b2 = 0; b2 < S; ++b2) mbar_wait_bounded(&bars[b2], 0u), mbar_wait_bounded(&bars[b2], 1u);
+      if (err) atomicOr(err, (int)DEVERR_TIMEOUT);
+    }
+    return;
+  }
+  for (int i = tid; i < n; i += FTB) {
+    const double xi = sdrop[i] ? 0.0 : x[i] + (double)yv[i];
+    x[i] = xi;
+    a_out[i] = scale[i] * xi;
+  }
+}
+
+size_t big_solve_smem_bytes(int n, int bw, int S) {
+  const size_t n4 = ((size_t)n + 3) / 4 * 4;
+  return (2 * n4 + NBB + (size_t)S * big_stage_elems(bw)) * sizeof(float) + (size_t)n * sizeof(int);
+}
+
 __device__ inline double warp_sum_d(double v) {
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
@@ -589,6 +871,8 @@ cudaError_t configure_coarse_solve(int max_smem) {
   if ((e = set_max_dynamic_smem(k_coarse_factor<float>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_coarse_factor<double>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_coarse_solve<float>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_coarse_solve_big<2>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_coarse_solve_big<3>, max_smem)) != cudaSuccess) return e;
   return set_max_dynamic_smem(k_coarse_solve<double>, max_smem);
 }
 
@@ -607,6 +891,34 @@ size_t coarse_solve_smem_bytes(int n, int bw, bool fp64) {
          flags;
 }
 int coarse_dinv_size(int n) { return ((n + NB - 1) / NB) * NB * NB; }
+size_t coarse_xinv_elems(int n, int bw) { return (size_t)((n + NBB - 1) / NBB) * blk_elems(bw); }
+
+int coarse_big_stages(int n, int bw, int max_smem) {
+  for (int S = 3; S >= 2; --S)
+    if (big_solve_smem_bytes(n, bw, S) + 4096 <= (size_t)max_smem) return S;
+  return 0;
+}
+
+cudaError_t launch_coarse_blockinv(cudaStream_t s, int n, int bw, const void* lcol, const void* lrow, float* xinv,
+                                   const IterCtl* ctl) {
+  k_coarse_blockinv<<<dim3((n + NBB - 1) / NBB, 4), 256, 0, s>>>(n, bw, (const float*)lcol, (const float*)lrow, xinv,
+                                                                 ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve_big(cudaStream_t s, int stages, int n, int bw, const void* lcol, const void* lrow,
+                                    const float* xinv, const int* dropped, const double* res, double* x,
+                                    const double* scale, double* a_out, unsigned long long* cstat, bool first,
+                                    const IterCtl* ctl, int* err) {
+  const size_t smem = big_solve_smem_bytes(n, bw, stages);
+  if (stages >= 3)
+    k_coarse_solve_big<3><<<1, FTB, smem, s>>>(n, bw, xinv, dropped, res, x, scale, a_out, cstat, first ? 1 : 0,
+                                               ctl, err);
+  else
+    k_coarse_solve_big<2><<<1, FTB, smem, s>>>(n, bw, xinv, dropped, res, x, scale, a_out, cstat, first ? 1 : 0,
+                                               ctl, err);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, bool fp64, void* lrow, void* lcol, void* dinv,
                                  int* dropped, const IterCtl* ctl) {

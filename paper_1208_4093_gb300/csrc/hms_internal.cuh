@@ -164,6 +164,14 @@ cudaError_t launch_coarse_solve(cudaStream_t s, int n, int bw, bool fp64, const 
                                 const void* dinv, const int* dropped, const double* res, double* x,
                                 const double* scale, double* a_out, unsigned long long* cstat, bool first,
                                 const IterCtl* ctl, int* err);
+size_t coarse_xinv_elems(int n, int bw);
+int coarse_big_stages(int n, int bw, int max_smem);
+cudaError_t launch_coarse_blockinv(cudaStream_t s, int n, int bw, const void* lcol, const void* lrow, float* xinv,
+                                   const IterCtl* ctl);
+cudaError_t launch_coarse_solve_big(cudaStream_t s, int stages, int n, int bw, const void* lcol, const void* lrow,
+                                    const float* xinv, const int* dropped, const double* res, double* x,
+                                    const double* scale, double* a_out, unsigned long long* cstat, bool first,
+                                    const IterCtl* ctl, int* err);
 cudaError_t launch_coarse_residual(cudaStream_t s, int n, int bw, const double* sband, const double* b,
                                    const double* x, const int* dropped, double* res, unsigned long long* cstat,
                                    const IterCtl* ctl);

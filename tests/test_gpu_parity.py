@@ -183,6 +183,30 @@ def test_coarse_solve_step(problem):
         assert rel(a, ao) < tol
 
 
+@pytest.mark.parametrize("cf", [1, 3], ids=["blocks64", "rows16"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[3]], ids=lambda c: c[0])
+def test_coarse_solve_both_substitutions(hms_ctx, case, cf):
+    """The FP32 factor's two substitutions (inverted 64 x 64 diagonal blocks,
+    or 16-row steps) give the oracle's update V a and full solve."""
+    from paper_1208_4093_gb300 import capi
+    tr, g, p, pr = setup_case(hms_ctx, case, 0, coarse_factor=cf)
+    try:
+        u = tr.free * np.random.default_rng(9).standard_normal(tr.ndof)
+        r = tr.residual(tr.free * p, u)
+        delta = hms.LocalFactors(tr, g).relax(r)
+        V = hms.modes(tr, g, delta)
+        Ko, Po = hms.coarse_system(tr, V, r)
+        a = np.empty(9 * g.M)
+        capi.hms_coarse_solve(hms_ctx, pr, Ko, Po, a)
+        ao, _ = hms.coarse_solve(Ko, Po)
+        assert rel(V @ a, V @ ao) < 1e-11
+        out = np.empty((1, tr.ndof))
+        capi.hms_solve(hms_ctx, pr, p.reshape(1, -1), out)
+        assert rel(out[0], direct.cholesky_solve(tr, tr.free * p)) < 1e-9
+    finally:
+        capi.hms_problem_destroy(pr)
+
+
 def test_one_iteration_from_any_state(problem):
     """T1 per step: one GPU update from u equals one oracle update from u."""
     from paper_1208_4093_gb300 import capi
