@@ -23,8 +23,8 @@
 // for the B blocks), so every lane of a warp runs the same number of FMAs.
 // The solve runs in T = double (FP64 path, G = 2: the FP64 pipe is the bound,
 // so the fewest reduction adds) or T = float (mixed path, FP32 factor, G = 4).
-// While x_j = delta is finalised, each thread accumulates its DOF's share of
-// the nine sums of P_I = V_I^T r_I in FP64.
+// After the back substitution the nine sums of P_I = V_I^T r_I are formed in
+// FP64 from r and the delta just written, node by node.
 #include "hms_internal.cuh"
 #include "ptx.cuh"
 
@@ -42,8 +42,6 @@ __device__ inline double warp_sum_d(double v) {
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
-__device__ inline double2 make_vec2(double x, double y) { return make_double2(x, y); }
-__device__ inline float2 make_vec2(float x, float y) { return make_float2(x, y); }
 
 constexpr int NSLOT = 3;  // matrices staged in shared memory (two in flight while one is applied)
 
@@ -69,11 +67,11 @@ __host__ __device__ inline RelaxSmem relax_layout(int nb) {
 // Dot products of rows ra and rb (ra < rb) of a packed matrix M with v.  Row
 // x holds v-indices lo_x .. lo_x + len_x - 1, stored from M + off_x.  The G
 // threads of a group (g = 0..G-1) walk the combined index t = 0..lenA+lenB-1
-// with stride G, in CH interleaved chains of FMAs.  Returns the row sums in
-// every thread of the group.
+// with stride G, in CH interleaved chains of FMAs.  Returns the sum of row A
+// in the group's even threads and of row B in its odd threads.
 template <typename T, int G, int CH>
 __device__ inline void pair_dot(const T* __restrict__ pA, int loA, int lenA, const T* __restrict__ pB, int loB,
-                                int lenB, const T* __restrict__ v, int g, T& outA, T& outB) {
+                                int lenB, const T* __restrict__ v, int g, T& out) {
   const int len = lenA + lenB;
   T a[CH], b[CH];
 #pragma unroll
@@ -97,13 +95,14 @@ __device__ inline void pair_dot(const T* __restrict__ pA, int loA, int lenA, con
   T sa = a[0], sb = b[0];
 #pragma unroll
   for (int q = 1; q < CH; ++q) sa += a[q], sb += b[q];
+  // joint reduction over the group: after the first exchange even threads
+  // hold partial sums of row A and odd threads of row B
+  const bool odd = (g & 1) != 0;
+  T s = odd ? sb : sa;
+  s += __shfl_xor_sync(0xffffffffu, odd ? sa : sb, 1);
 #pragma unroll
-  for (int m = 1; m < G; m <<= 1) {
-    sa += __shfl_xor_sync(0xffffffffu, sa, m);
-    sb += __shfl_xor_sync(0xffffffffu, sb, m);
-  }
-  outA = sa;
-  outB = sb;
+  for (int m = 2; m < G; m <<= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  out = s;  // row A in threads g = 0, 2, ..., row B in g = 1, 3, ...
 }
 
 // The four kinds of matrix rows: lowest v-index, entry count and storage offset.
@@ -121,10 +120,12 @@ __device__ inline void row_shape(int nb, int r, int& lo, int& len, long long& of
   }
 }
 
-// out(r) for every row r of the matrix: groups of G threads take the row
-// pairs (r, nb-1-r); the group's first thread calls out(r, sum) per row.
-template <typename T, int G, int CH, int K, class Out>
-__device__ inline void rows_times(const T* M, const T* v, int nb, Out out) {
+// out(r, sum, pre) for every row r of the matrix: groups of G threads take
+// the row pairs (r, nb-1-r); thread 0 of a group handles row r and thread 1
+// row nb-1-r.  pre = fetch(r) is loaded before the products so that its
+// latency hides behind them.
+template <typename T, int G, int CH, int K, class Fetch, class Out>
+__device__ inline void rows_times(const T* M, const T* v, int nb, Fetch fetch, Out out) {
   const int npair = nb / 2;  // nb = 2w is even
   const int g = threadIdx.x % G;
   for (int base = 0; base < npair; base += NT / G) {
@@ -137,12 +138,12 @@ __device__ inline void rows_times(const T* M, const T* v, int nb, Out out) {
     row_shape<K>(nb, ra, loA, lenA, offA);
     row_shape<K>(nb, rb, loB, lenB, offB);
     if (!active) lenA = lenB = 0;
-    T sa, sb;
-    pair_dot<T, G, CH>(M + offA, loA, lenA, M + offB, loB, lenB, v, g, sa, sb);
-    if (active && g == 0) {
-      out(ra, sa);
-      out(rb, sb);
-    }
+    const int myrow = (g & 1) ? rb : ra;
+    const bool mine = active && g < 2;
+    const T pre = mine ? fetch(myrow) : T(0);
+    T s;
+    pair_dot<T, G, CH>(M + offA, loA, lenA, M + offB, loB, lenB, v, g, s);
+    if (mine) out(myrow, s, pre);
   }
 }
 
@@ -204,9 +205,6 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
 #pragma unroll
   for (int m = 0; m < NMODES; ++m) pacc[m] = 0.0;
   const double2 rep = lv.rep[I];
-  // xi of node tid of the set on even and odd lattice rows (Eq. 10)
-  const double xi_even = fma(lv.L, (double)(i0 + tid), -rep.x);
-  const double xi_odd = fma(lv.L, (double)(i0 + tid) + 0.5, -rep.x);
 
   for (int o = 0; o < nops; ++o) {
     const int k = mat_of_op(o);
@@ -226,14 +224,18 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
       const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
       if (is_b) {
         // z = r_j - B_j y_{j-1}
-        rows_times<T, G, CH, ROW_B>(M, ycur, nb, [&](int row, T s) { zbuf[row] = (T)rg[rowbase + row] - s; });
+        rows_times<T, G, CH, ROW_B>(
+            M, ycur, nb, [&](int row) { return (T)rg[rowbase + row]; },
+            [&](int row, T s, T pre) { zbuf[row] = pre - s; });
       } else {
         // y_j = Linv_j z
         T* yj = yg + (size_t)j * nb;
-        rows_times<T, G, CH, ROW_LINV>(M, zbuf, nb, [&](int row, T s) {
-          ycur[row] = s;
-          yj[row] = s;
-        });
+        rows_times<T, G, CH, ROW_LINV>(
+            M, zbuf, nb, [](int) { return T(0); },
+            [&](int row, T s, T) {
+              ycur[row] = s;
+              yj[row] = s;
+            });
       }
       __syncthreads();
     } else {
@@ -241,33 +243,18 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
       if (!is_b) {
         // x_j = Linv_j^T w  (w = y_{h-1} for the last row)
         const T* wv = (j == h - 1) ? ycur : wbuf;
-        rows_times<T, G, CH, ROW_LT>(M, wv, nb, [&](int row, T s) { xbuf[row] = s; });
-        __syncthreads();
-        const size_t node0 = (size_t)(j0 + j) * lv.nx + i0;
-        const double eta = fma(lv.L * SQ3_2, (double)(j0 + j), -rep.y);
-        const bool odd = ((j0 + j) & 1) != 0;
-        if (tid < w) {
-          // delta and P = V^T r (Eq. 7) for the two DOFs of node tid
-          const T sx = xbuf[2 * tid], sy = xbuf[2 * tid + 1];
-          T2* d2 = reinterpret_cast<T2*>(delta);
-          d2[node0 + tid] = make_vec2(sx, sy);
-          const double2 rv = r[node0 + tid];
-          const double xi = odd ? xi_odd : xi_even;
-          const double dr = fma((double)sx, rv.x, (double)sy * rv.y);
-          pacc[0] += rv.x;
-          pacc[1] += rv.y;
-          pacc[2] = fma(xi, rv.x, pacc[2]);
-          pacc[3] = fma(eta, rv.x, pacc[3]);
-          pacc[4] = fma(xi, rv.y, pacc[4]);
-          pacc[5] = fma(eta, rv.y, pacc[5]);
-          pacc[6] += dr;
-          pacc[7] = fma(xi, dr, pacc[7]);
-          pacc[8] = fma(eta, dr, pacc[8]);
-        }
+        const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
+        rows_times<T, G, CH, ROW_LT>(
+            M, wv, nb, [](int) { return T(0); },
+            [&](int row, T s, T) {
+              xbuf[row] = s;
+              delta[rowbase + row] = s;
+            });
       } else {
         // w = y_{j-1} - B_j^T x_j
         const T* yp = yg + (size_t)(j - 1) * nb;
-        rows_times<T, G, CH, ROW_BT>(M, xbuf, nb, [&](int row, T s) { wbuf[row] = yp[row] - s; });
+        rows_times<T, G, CH, ROW_BT>(
+            M, xbuf, nb, [&](int row) { return yp[row]; }, [&](int row, T s, T pre) { wbuf[row] = pre - s; });
       }
       __syncthreads();
     }
@@ -279,6 +266,30 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
       atomicOr(err, (int)DEVERR_TIMEOUT);
     }
     return;
+  }
+  // P = V^T r (Eq. 7) from r and the delta just written, node by node
+  __syncthreads();
+  {
+    const T2* d2 = reinterpret_cast<const T2*>(delta);
+    for (int node = tid; node < w * h; node += NT) {
+      const int jj = node / w, il = node - jj * w;
+      const int j = j0 + jj;
+      const size_t nidx = (size_t)j * lv.nx + i0 + il;
+      const double2 rv = r[nidx];
+      const T2 dv = d2[nidx];
+      const double xi = fma(lv.L, (double)(i0 + il) + 0.5 * (double)(j & 1), -rep.x);
+      const double eta = fma(lv.L * SQ3_2, (double)j, -rep.y);
+      const double dr = fma((double)dv.x, rv.x, (double)dv.y * rv.y);
+      pacc[0] += rv.x;
+      pacc[1] += rv.y;
+      pacc[2] = fma(xi, rv.x, pacc[2]);
+      pacc[3] = fma(eta, rv.x, pacc[3]);
+      pacc[4] = fma(xi, rv.y, pacc[4]);
+      pacc[5] = fma(eta, rv.y, pacc[5]);
+      pacc[6] += dr;
+      pacc[7] = fma(xi, dr, pacc[7]);
+      pacc[8] = fma(eta, dr, pacc[8]);
+    }
   }
   // deterministic block reduction of the nine P sums
 #pragma unroll
