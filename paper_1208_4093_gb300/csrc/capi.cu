@@ -163,7 +163,8 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
                           pr->b, pr->x, pr->dropped, pr->ctl);
   if (e != cudaSuccess) return e;
   mark();
-  e = launch_coarse_factor(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped, pr->ctl);
+  e = launch_coarse_factor(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped,
+                           pr->big_stages == 0, pr->ctl);
   if (e != cudaSuccess) return e;
   if (pr->big_stages > 0) {
     e = launch_coarse_blockinv(s, pr->n_c, pr->bw, pr->lcol, pr->lrow, pr->xinv, pr->ctl);
@@ -750,7 +751,8 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
   CKC(c, cudaMemcpyAsync(pr->P, P, n * sizeof(double), kind_in(mem_kind), s));
   CKC(c, launch_coarse_scale(s, n, bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale, pr->b,
                              pr->x, pr->dropped, nullptr));
-  CKC(c, launch_coarse_factor(s, n, bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped, nullptr));
+  CKC(c, launch_coarse_factor(s, n, bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped,
+                              pr->big_stages == 0, nullptr));
   if (pr->big_stages > 0) CKC(c, launch_coarse_blockinv(s, n, bw, pr->lcol, pr->lrow, pr->xinv, nullptr));
   for (int q = 0; q < pr->nsolve; ++q) {
     if (q > 0)

@@ -170,11 +170,12 @@ __device__ __forceinline__ void factor_diag_block(T (&a)[NB], int k, int nbk, in
 }
 
 // lrow: input = scaled band in row layout [i][kk] = A[i][i-kk]; output = L in
-// row layout.  lcol: output = L in column layout [c][kk] = L[c+kk][c].
+// row layout if write_lrow (the 16-row substitution reads it).  lcol: output
+// = L in column layout [c][kk] = L[c+kk][c].
 template <typename T>
 __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __restrict__ lrow, T* __restrict__ lcol,
                                                           T* __restrict__ dinv, int* __restrict__ dropped,
-                                                          const IterCtl* ctl) {
+                                                          int write_lrow, const IterCtl* ctl) {
   if (ctl && *(volatile const int*)&ctl->done) return;
   extern __shared__ __align__(16) unsigned char fsraw[];
   T* fs = reinterpret_cast<T*>(fsraw);
@@ -241,9 +242,10 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
         for (int u = 0; u < 4; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-        const int cmax = min(4 * cq + 3, nbk - 1);
-#pragma unroll 4
-        for (int cp = 0; cp <= cmax; ++cp) {
+        // X is zero above its diagonal: run all NB columns (unrolled by 8:
+        // fully unrolled, the kernel's 128 registers spill)
+#pragma unroll 8
+        for (int cp = 0; cp < NB; ++cp) {
           T av[4], xv[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -319,8 +321,9 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
           for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-#pragma unroll 4
-          for (int c = 0; c < nbk; ++c) {
+          // columns of Pc past nbk are zero (a short last block): always NB
+#pragma unroll
+          for (int c = 0; c < NB; ++c) {
             const T* pc = Pc + c * pstr;
             T ri[4], rj[4];
             ld4(pc + 4 * ti, ri);
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
             else if (i < rend) v = Pc[cl * pstr + (i - k1)];
           }
           lcol[(size_t)c * ldw + kk] = v;
-          if (i < n) lrow[(size_t)i * ldw + kk] = v;
+          if (write_lrow && i < n) lrow[(size_t)i * ldw + kk] = v;
         }
       }
       // (b3) the prefetched rows enter the window (slots of rows [k0, k1))
@@ -584,9 +587,9 @@ __global__ void __launch_bounds__(256) k_coarse_blockinv(int n, int bw, const fl
       const int q = idx / LDR, c = idx % LDR;
       float rv = 0.f, uv = 0.f;
       if (c < nr) {
-        const int i = r1 + q, k = r0 + c;  // R: L[i][k], i > k, from the row layout (coalesced over c)
-        if (i < n && i - k <= bw) rv = lrow[(size_t)i * ldw + (i - k)];
-        const int iu = r0 - bw + q;        // U: L[k][iu], k > iu, from the column layout (coalesced over c)
+        const int i = r1 + q, k = r0 + c;  // R: L[i][k], i > k
+        if (i < n && i - k <= bw) rv = lcol[(size_t)k * ldw + (i - k)];
+        const int iu = r0 - bw + q;        // U: L[k][iu], k > iu (coalesced over c)
         if (iu >= 0 && k - iu <= bw) uv = lcol[(size_t)iu * ldw + (k - iu)];
       }
       R[idx] = rv;
@@ -598,7 +601,7 @@ __global__ void __launch_bounds__(256) k_coarse_blockinv(int n, int bw, const fl
   for (int idx = tid; idx < NBB * NBB; idx += blockDim.x) {
     const int r = idx / NBB, c = idx % NBB;
     float v = 0.f;
-    if (r < nr && c <= r && r - c <= bw) v = lrow[(size_t)(r0 + r) * ldw + (r - c)];  // coalesced over c
+    if (r < nr && c <= r && r - c <= bw) v = lcol[(size_t)(r0 + c) * ldw + (r - c)];
     if (r >= nr && r == c) v = 1.f;
     Ls[r][c] = v;
   }
@@ -921,12 +924,14 @@ cudaError_t launch_coarse_solve_big(cudaStream_t s, int stages, int n, int bw, c
 }
 
 cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, bool fp64, void* lrow, void* lcol, void* dinv,
-                                 int* dropped, const IterCtl* ctl) {
+                                 int* dropped, bool write_lrow, const IterCtl* ctl) {
   const size_t smem = coarse_factor_smem_bytes(n, bw, fp64);
   if (fp64)
-    k_coarse_factor<double><<<1, FTF, smem, s>>>(n, bw, (double*)lrow, (double*)lcol, (double*)dinv, dropped, ctl);
+    k_coarse_factor<double><<<1, FTF, smem, s>>>(n, bw, (double*)lrow, (double*)lcol, (double*)dinv, dropped,
+                                                 write_lrow ? 1 : 0, ctl);
   else
-    k_coarse_factor<float><<<1, FTF, smem, s>>>(n, bw, (float*)lrow, (float*)lcol, (float*)dinv, dropped, ctl);
+    k_coarse_factor<float><<<1, FTF, smem, s>>>(n, bw, (float*)lrow, (float*)lcol, (float*)dinv, dropped,
+                                                write_lrow ? 1 : 0, ctl);
   return cudaGetLastError();
 }
 

@@ -159,7 +159,7 @@ cudaError_t launch_coarse_scale(cudaStream_t s, int n, int bw, bool fp64, const 
                                 double* sband, void* frow, double* scale, double* b, double* x, int* dropped,
                                 const IterCtl* ctl);
 cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, bool fp64, void* lrow, void* lcol, void* dinv,
-                                 int* dropped, const IterCtl* ctl);
+                                 int* dropped, bool write_lrow, const IterCtl* ctl);
 cudaError_t launch_coarse_solve(cudaStream_t s, int n, int bw, bool fp64, const void* lcol, const void* lrow,
                                 const void* dinv, const int* dropped, const double* res, double* x,
                                 const double* scale, double* a_out, unsigned long long* cstat, bool first,
