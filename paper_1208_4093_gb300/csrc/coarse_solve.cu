@@ -15,10 +15,10 @@
 //   k_coarse_factor  one CTA of 512 threads: right-looking band Cholesky in
 //                    16-column blocks over a window of bw + 16 band rows held in
 //                    shared memory (circular row-band storage).  Look-ahead:
-//                    while warps 1-15 apply block K's rank-16 update to the
-//                    rest of the window, write block K's columns of L and load
-//                    the next band rows, warp 0 updates, factors (registers)
-//                    and inverts the diagonal block K+1.
+//                    while 12 warps apply block K's rank-16 update to the rest
+//                    of the window and load the next band rows, and warps 4,
+//                    8, 12 write block K's columns of L, warp 0 factors
+//                    (registers) and inverts the diagonal block K+1.
 //   k_coarse_solve   one CTA of 512 threads: right-looking block forward / back
 //                    substitution, 16 rows per step: the inverted diagonal
 //                    block, then the block's contribution to the next bw rows;
@@ -81,13 +81,16 @@ __device__ __forceinline__ void diag_steps(T (&a)[NB], unsigned dmask, int lane,
     const bool mine = lane == C;
     const T acl = a[C];
     a[C] = mine ? d : (lane > C ? (drop ? T(0) : acl * inv) : acl);
+    if (drop) {  // warp-uniform and rare: the dropped row becomes zero
 #pragma unroll
-    for (int j = 0; j < C; ++j) a[j] = (mine && drop) ? T(0) : a[j];
+      for (int j = 0; j < C; ++j) a[j] = mine ? T(0) : a[j];
+    }
     const T lc = a[C];
+    // entries above the diagonal (lane < j) are never read: update them too
 #pragma unroll
     for (int j = C + 1; j < NB; ++j) {
       const T ljc = __shfl_sync(0xffffffffu, lc, j);
-      a[j] = (lane >= j) ? fma(-lc, ljc, a[j]) : a[j];
+      a[j] = fma(-lc, ljc, a[j]);
     }
     if (drop) dropped_out |= (1u << C);
     diag_steps<T, C + 1>(a, dmask, lane, dropped_out, rdiag);
@@ -104,21 +107,39 @@ __device__ inline void ld4(const double* p, double (&v)[4]) {
   const double2 b = *reinterpret_cast<const double2*>(p + 2);
   v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
 }
+__device__ inline void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ inline void st4(double* p, double a, double b, double c, double d) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(c, d);
+}
 
 template <typename T>
 struct FactorLayout {
-  int W, ldw, pstr;
+  int W, ldw, lda, pstr;
   size_t aw, pc, ls, xs, total;
 };
+// The window holds band rows [k0, k0 + W) in circular row slots; row i keeps
+// its entry of column j at position j mod lda.  lda >= bw + 4 is a multiple
+// of 4 with lda / 4 odd, so the four entries (i, j..j+3), j = 0 mod 4, are one
+// aligned 16-byte word, and such words of consecutive rows fall in different
+// bank groups; positions outside the row's band [i - bw, i] are never read.
+__host__ __device__ inline int window_lda(int bw) {
+  int m = (bw + 4 + 3) / 4;
+  if ((m & 1) == 0) ++m;
+  return 4 * m;
+}
 template <typename T>
 __host__ __device__ inline FactorLayout<T> factor_layout(int bw) {
   FactorLayout<T> L;
   // rows [k0, k0 + W) cover block K's band rows and the next diagonal block
   L.W = (bw > NB ? bw : NB) + NB;
   L.ldw = bw + 1;
+  L.lda = window_lda(bw);
   L.pstr = ((bw + 3) / 4) * 4 + 4;
   L.aw = 0;
-  L.pc = ((size_t)L.W * L.ldw + 3) / 4 * 4;
+  L.pc = ((size_t)L.W * L.lda + 3) / 4 * 4;
   L.ls = L.pc + (size_t)NB * L.pstr;  // 2 buffers of NB x (NB+1)
   L.xs = L.ls + 2 * NB * (NB + 1);    // 2 buffers of NB x (NB+1)
   L.total = L.xs + 2 * NB * (NB + 1);
@@ -180,7 +201,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
   extern __shared__ __align__(16) unsigned char fsraw[];
   T* fs = reinterpret_cast<T*>(fsraw);
   const FactorLayout<T> LY = factor_layout<T>(bw);
-  const int W = LY.W, ldw = LY.ldw, pstr = LY.pstr;
+  const int W = LY.W, ldw = LY.ldw, lda = LY.lda, pstr = LY.pstr;
   T* Aw = fs + LY.aw;
   T* Pc = fs + LY.pc;
   int* sdrop = reinterpret_cast<int*>(fs + LY.total);
@@ -201,7 +222,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
   // window rows [0, min(n, W))
   for (int q = tid; q < min(n, W) * ldw; q += FTF) {
     const int i = q / ldw, kk = q - (q / ldw) * ldw;
-    Aw[(size_t)(i % W) * ldw + kk] = (kk <= i) ? lrow[(size_t)i * ldw + kk] : T(0);
+    if (kk <= i) Aw[(size_t)(i % W) * lda + (i - kk) % lda] = lrow[(size_t)i * ldw + kk];
   }
   __syncthreads();
   // diagonal block 0
@@ -210,7 +231,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
     const int nbk = min(NB, n);
 #pragma unroll
     for (int j = 0; j < NB; ++j)
-      a[j] = (lane < nbk && j <= lane && lane - j <= bw) ? Aw[(size_t)lane * ldw + (lane - j)] : T(0);
+      a[j] = (lane < nbk && j <= lane && lane - j <= bw) ? Aw[(size_t)lane * lda + j] : T(0);
     factor_diag_block<T>(a, 0, nbk, lane, sdrop, fs + LY.ls, fs + LY.xs, dinv, &dropblk[0]);
   }
   __syncthreads();
@@ -224,7 +245,10 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
     const unsigned dblk = dropblk[cur];
     const int slot_k1 = k1 % W;  // window slot of row k1; row k1 + d sits at slot_k1 + d (mod W)
     auto slot = [&](int i) { const int v = slot_k1 + (i - k1); return v >= W ? v - W : v; };
-    // (a) panel P[i][c] = sum_{c' <= c} A[i][k0 + c'] X[c][c'], i in [k1, rend); 4 x 4 tiles
+    // (a) panel P[i][c] = sum_{c' <= c} A[i][k0 + c'] X[c][c'], i in [k1, rend);
+    // tiles of 4 rows (interleaved by nrq, so that neighbouring threads read
+    // neighbouring rows) x 4 columns
+    const int ck0 = k0 % lda;  // position of column k0 in a window row
     {
       const int nrq = (np + 3) / 4;
       for (int q = tid; q < nrq * (NB / 4); q += FTF) {
@@ -233,9 +257,9 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
         int il[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          il[u] = 4 * rq + u;
+          il[u] = rq + u * nrq;
           const int i = k1 + (il[u] < np ? il[u] : np - 1);
-          rowoff[u] = slot(i) * ldw + (i - k0);
+          rowoff[u] = slot(i) * lda;
         }
         T acc[4][4];
 #pragma unroll
@@ -250,7 +274,8 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int kk = k1 + il[u] - k0 - cp;  // i - (k0 + cp)
-            av[u] = (il[u] < np && kk <= bw) ? Aw[rowoff[u] - cp] : T(0);
+            const int pos = ck0 + cp;
+            av[u] = (il[u] < np && kk <= bw) ? Aw[rowoff[u] + (pos >= lda ? pos - lda : pos)] : T(0);
           }
 #pragma unroll
           for (int v = 0; v < 4; ++v) xv[v] = Xs[(4 * cq + v) * (NB + 1) + cp];
@@ -277,7 +302,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
       if (l < nbk2 && j <= l && l < np && l - j <= bw) {
         T v = T(0);
         for (int c = 0; c < nbk; ++c) v = fma(Pc[c * pstr + l], Pc[c * pstr + j], v);
-        Aw[(size_t)slot(k1 + l) * ldw + (l - j)] -= v;
+        Aw[(size_t)slot(k1 + l) * lda + (k1 + j) % lda] -= v;
       }
     }
     __syncthreads();
@@ -285,30 +310,43 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
       // (b0) look-ahead: factor the diagonal block K+1
       if (K + 1 < nblk) {
         T a[NB];
-        const size_t rbase = (size_t)slot(min(k1 + lane, n - 1)) * ldw;
+        const size_t rbase = (size_t)slot(min(k1 + lane, n - 1)) * lda;
+        const int ck1 = k1 % lda;
 #pragma unroll
-        for (int j = 0; j < NB; ++j)
-          a[j] = (lane < nbk2 && j <= lane && lane - j <= bw) ? Aw[rbase + (lane - j)] : T(0);
+        for (int j = 0; j < NB; ++j) {
+          const int pos = ck1 + j;
+          a[j] = (lane < nbk2 && j <= lane && lane - j <= bw) ? Aw[rbase + (pos >= lda ? pos - lda : pos)] : T(0);
+        }
         factor_diag_block<T>(a, k1, nbk2, lane, sdrop, fs + LY.ls + nxt * NB * (NB + 1),
                              fs + LY.xs + nxt * NB * (NB + 1), dinv, &dropblk[nxt]);
       }
-    } else {
-      const int t2 = tid - 32, nt2 = FTF - 32;
-      // band rows [k0 + W, k1 + W) enter the window at the end of this step:
-      // load them now, store them after the update (latency hidden)
+    } else if ((warp & 3) == 0) {
+      // warps 4, 8, 12 share warp 0's scheduler, so they take only light
+      // work that does not wait on the update: band rows [k0 + W, k1 + W)
+      // enter the window in the slots of rows [k0, k1), which nothing reads
+      // in this phase
       const int er0 = k0 + W, er1 = min(k1 + W, n);
-      T pre[2][7];  // at most 2 entering rows per warp (NB rows over 15 warps), ldw <= 224
-      {
-        int e = 0;
-        for (int i = er0 + warp - 1; i < er1 && e < 2; i += FTF / 32 - 1, ++e) {
-          const T* src = lrow + (size_t)i * ldw;
+      for (int i = er0 + (warp >> 2) - 1; i < er1; i += FTF / 128 - 1) {
+        const T* src = lrow + (size_t)i * ldw;
+        T* dst = Aw + (size_t)(i % W) * lda;
+        const int ci = i % lda;  // position of column i; column i - kk wraps at most once (kk < ldw <= lda)
+        T v[7];  // ldw <= 224: all loads first, then the stores
 #pragma unroll
-          for (int u = 0; u < 7; ++u) {
-            const int kk = lane + 32 * u;
-            pre[e][u] = (kk < ldw && kk <= i) ? src[kk] : T(0);
-          }
+        for (int u = 0; u < 7; ++u) {
+          const int kk = lane + 32 * u;
+          v[u] = (kk < ldw && kk <= i) ? src[kk] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 7; ++u) {
+          const int kk = lane + 32 * u;
+          const int pos = ci - kk;
+          if (kk < ldw && kk <= i) dst[pos < 0 ? pos + lda : pos] = v[u];
         }
       }
+    } else {
+      // the other 12 warps: trailing update, then block K's columns of L
+      const int wi = warp - 1 - (warp >> 2), nwi = FTF / 32 - FTF / 128;
+      const int t2 = wi * 32 + lane, nt2 = nwi * 32;
       // (b1) trailing update of the window except the next diagonal block
       {
         const int T4 = (np + 3) / 4;
@@ -333,42 +371,40 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
 #pragma unroll
               for (int v = 0; v < 4; ++v) acc[u][v] = fma(ri[u], rj[v], acc[u][v]);
           }
+          // (i, k1 + 4 tj .. + 3) is one aligned 16-byte word of row i; in a
+          // diagonal tile the entries right of the diagonal land on unused
+          // positions of the row
+          const int pj = (k1 + 4 * tj) % lda;
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int i = k1 + 4 * ti + u;
             if (i >= rend) continue;
-            const size_t rb = (size_t)slot(i) * ldw;
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              const int j = k1 + 4 * tj + v;
-              if (j <= i) Aw[rb + (i - j)] -= acc[u][v];
-            }
+            T* w4 = Aw + (size_t)slot(i) * lda + pj;
+            T old[4];
+            ld4(w4, old);
+            st4(w4, old[0] - acc[u][0], old[1] - acc[u][1], old[2] - acc[u][2], old[3] - acc[u][3]);
           }
         }
       }
-      // (b2) columns [k0, k1) of L to global, both layouts (warp per column)
-      for (int cl = warp - 1; cl < nbk; cl += FTF / 32 - 1) {
+      // (b2) columns [k0, k1) of L to global (and the row layout if asked)
+      for (int cl = wi; cl < nbk; cl += nwi) {
         const int c = k0 + cl;
-        for (int kk = lane; kk < ldw; kk += 32) {
-          const int i = c + kk;
-          T v = T(0);
-          if (i < n) {
-            if (i < k1) v = Ls[(i - k0) * (NB + 1) + cl];
-            else if (i < rend) v = Pc[cl * pstr + (i - k1)];
-          }
-          lcol[(size_t)c * ldw + kk] = v;
-          if (write_lrow && i < n) lrow[(size_t)i * ldw + kk] = v;
-        }
-      }
-      // (b3) the prefetched rows enter the window (slots of rows [k0, k1))
-      {
-        int e = 0;
-        for (int i = er0 + warp - 1; i < er1 && e < 2; i += FTF / 32 - 1, ++e) {
-          T* dst = Aw + (size_t)(i % W) * ldw;
+        T v[7];  // ldw <= 224: all loads first, then the stores
 #pragma unroll
-          for (int u = 0; u < 7; ++u) {
-            const int kk = lane + 32 * u;
-            if (kk < ldw) dst[kk] = pre[e][u];
+        for (int u = 0; u < 7; ++u) {
+          const int kk = lane + 32 * u, i = c + kk;
+          v[u] = T(0);
+          if (kk < ldw && i < n) {
+            if (i < k1) v[u] = Ls[(i - k0) * (NB + 1) + cl];
+            else if (i < rend) v[u] = Pc[cl * pstr + (i - k1)];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 7; ++u) {
+          const int kk = lane + 32 * u, i = c + kk;
+          if (kk < ldw) {
+            lcol[(size_t)c * ldw + kk] = v[u];
+            if (write_lrow && i < n) lrow[(size_t)i * ldw + kk] = v[u];
           }
         }
       }
