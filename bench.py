@@ -34,7 +34,12 @@ WORKLOAD = "lattice1024_lognormal"
 TOL = 1e-8
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 GOLDEN_FULL = os.path.join(ROOT, "tests", "golden", "lattice1024_lognormal_history.json")
-FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (CUDA cores and tensor cores alike)
+FP64_LANES_PER_SM_CLK = 2  # DFMA lanes per SM per clock on GB300 (ncu: sm__sass_thread_inst_executed_op_dfma peak)
+
+
+def fp64_peak_gflops(n_sm, sm_mhz):
+    """FP64 roofline from the unit counts and the clock: SMs x DFMA lanes x 2 flops x clock."""
+    return n_sm * FP64_LANES_PER_SM_CLK * 2 * sm_mhz * 1e-3
 
 
 def parse():
@@ -353,9 +358,13 @@ def run_ours(args, rank, world, local_rank):
                     "unit": "GB/s", "frac": ach / hbm_peak, "peak_source": peak_src}
         else:
             ach = fl / (avg * 1e-3) / 1e9
-            roof = {"kernel": "k_relax<double>", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS,
-                    "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
-                    "peak_source": "nominal FP64 rate, 1.25 TFLOP/s",
+            n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+            mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+            pk = fp64_peak_gflops(n_sm, mhz)
+            roof = {"kernel": "k_relax<double>", "bound": "alu", "achieved": ach, "peak": pk,
+                    "unit": "GFLOP/s", "frac": ach / pk,
+                    "peak_source": f"FP64 units: {n_sm} SMs x {FP64_LANES_PER_SM_CLK} DFMA lanes/clock x 2 flops x "
+                                   f"{mhz:.0f} MHz",
                     "hbm_gbs": b / (avg * 1e-3) / 1e9}
         roof.update({"algorithmic_bytes": b, "algorithmic_flops": fl, "avg_launch_ms": avg, "launches": n,
                      "traffic": traffic_for(roof["kernel"], WORKLOAD, "relax.cu")})

@@ -157,15 +157,19 @@ hms_status hms_relax(hms_problem* pr, const double* r, double* delta, double* P,
                      int32_t mem_kind);
 
 /* Step a5 (Eq. 6): the upper-level matrix K_aa = V^T K V for the modes built
- * from delta, written dense [9M][9M] row-major (only for 9M <= 4096). */
+ * from delta, written dense [9M][9M] row-major (only for 9M <= 4096).  For
+ * HMS_MIXED problems delta is rounded to FP32 (as the relaxation leaves it)
+ * and the per-iteration bar products are formed in FP32, summed in FP64. */
 hms_status hms_coarse_matrix(hms_problem* pr, const double* delta, double* Kaa,
                              int32_t mem_kind);
 
 /* Step a6 (Eq. 8): a = K_aa^-1 P for a dense symmetric Kaa [9M][9M] whose
  * entries outside the set-grid band are zero, by the Jacobi-scaled Cholesky
- * that drops modes with diag <= 1e-300 or a negligible pivot (a = 0 for
- * them); FP32 factor with FP64 refinement (options.coarse_solves solves).
- * dropped (nullable) receives 1 per dropped mode. */
+ * that drops a mode (a = 0) whose diagonal is <= 1e-300 or <= 1e-28 times the
+ * largest diagonal of its set's nine modes, or which depends on earlier modes
+ * of its set (FP64 test per set); FP32 factor with FP64 refinement (at most
+ * options.coarse_solves solves, fewer once converged) unless the problem uses
+ * the FP64 factor.  dropped (nullable) receives 1 per dropped mode. */
 hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P, double* a,
                             int32_t* dropped, int32_t mem_kind);
 
