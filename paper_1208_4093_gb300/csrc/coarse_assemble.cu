@@ -27,7 +27,7 @@ constexpr int NT = 256, NW = NT / 32;
 constexpr int NREG = 15;          // 3 directions x 3 delta modes + 6 delta-delta products
 constexpr int NGEN_DELTA = 24;    // (m, l), m in 6..8, l <= m
 constexpr int NGEN_FULL = 45;     // (m, l), l <= m < 9
-constexpr int LSTRIDE = 19;       // k, s[18]
+constexpr int LSTRIDE = 36;       // s[18], (EA/L) s[18]
 
 __device__ inline double warp_sum(double v) {
 #pragma unroll
@@ -111,6 +111,10 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
   __syncthreads();
 
   const double2 repI = lv.rep[I];
+  // set-relative coordinates of the regular-bar path in AT: xi = L (il + off/2) + c0x,
+  // eta = L sqrt3/2 jl + c0y; the far end of a bar of direction d adds (L e_x, L e_y)
+  const AT c0x = (AT)fma(lv.L, (double)i0, -repI.x), c0y = (AT)fma(lv.L * SQ3_2, (double)j0, -repI.y);
+  const AT LA = (AT)lv.L, LyA = (AT)(lv.L * SQ3_2);
   AT reg[NREG];
   AT gen[NGEN];
 #pragma unroll
@@ -124,8 +128,8 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
     const int off = j & 1;
     const size_t na = (size_t)j * lv.nx + i;
     const unsigned fa = lv.fix[na];
-    const double2 da = FULL ? make_double2(0.0, 0.0) : ld_delta(delta, na);
-    const double xa = node_x(lv, i, j), ya = node_y(lv, j);
+    const DT dra = FULL ? DT{} : delta[na];
+    const AT xiaA = fma(LA, (AT)il + (off ? AT(0.5) : AT(0)), c0x), etaaA = fma(LyA, (AT)jl, c0y);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double k = bar_k(lv, i, j, d);
@@ -134,20 +138,27 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
       const int jb = (d == 0) ? j : j + 1;
       const size_t nbn = (size_t)jb * lv.nx + ib;
       const unsigned fb = lv.fix[nbn];
-      const double2 db = FULL ? make_double2(0.0, 0.0) : ld_delta(delta, nbn);
       const double ex = (d == 0) ? 1.0 : (d == 1 ? 0.5 : -0.5), ey = (d == 0) ? 0.0 : SQ3_2;
-      const double xb = node_x(lv, ib, jb), yb = node_y(lv, jb);
       const int dxs = (ib >= i0 + w) ? 1 : (ib < i0 ? -1 : 0);
       const int dys = (jb >= j0 + h) ? 1 : 0;
+      // FP64 node data of the general and interface paths (not of regular bars)
+      auto fp64_ends = [&](double2& da, double2& db, double& xa, double& ya, double& xb, double& yb) {
+        da = FULL ? make_double2(0.0, 0.0) : ld_delta(delta, na);
+        db = FULL ? make_double2(0.0, 0.0) : ld_delta(delta, nbn);
+        xa = node_x(lv, i, j), ya = node_y(lv, j);
+        xb = node_x(lv, ib, jb), yb = node_y(lv, jb);
+      };
       if (dxs == 0 && dys == 0) {
-        const double xia = xa - repI.x, etaa = ya - repI.y;
-        const double xib = xb - repI.x, etab = yb - repI.y;
         if (!FULL && fa == 0u && fb == 0u) {
-          // regular bar: s_0 = s_1 = 0, s_2..s_5 constants of the direction
-          const AT ea = (AT)ex * (AT)da.x + (AT)ey * (AT)da.y, eb = (AT)ex * (AT)db.x + (AT)ey * (AT)db.y;
+          // regular bar: s_0 = s_1 = 0, s_2..s_5 constants of the direction;
+          // everything in AT from the raw delta
+          const DT drb = delta[nbn];
+          const AT exA = (AT)ex, eyA = (AT)ey;
+          const AT ea = fma(eyA, (AT)dra.y, exA * (AT)dra.x), eb = fma(eyA, (AT)drb.y, exA * (AT)drb.x);
+          const AT xibA = fma(LA, exA, xiaA), etabA = (d == 0) ? etaaA : etaaA + LyA;
           const AT s6 = ea - eb;
-          const AT s7 = (AT)xia * ea - (AT)xib * eb;
-          const AT s8 = (AT)etaa * ea - (AT)etab * eb;
+          const AT s7 = fma(xiaA, ea, -(xibA * eb));
+          const AT s8 = fma(etaaA, ea, -(etabA * eb));
           const AT kk = (AT)k;
           const AT k6 = kk * s6, k7 = kk * s7, k8 = kk * s8;
           reg[3 * d + 0] += k6;
@@ -160,6 +171,11 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
           reg[13] = fma(k8, s7, reg[13]);
           reg[14] = fma(k8, s8, reg[14]);
         } else {
+          double2 da, db;
+          double xa, ya, xb, yb;
+          fp64_ends(da, db, xa, ya, xb, yb);
+          const double xia = xa - repI.x, etaa = ya - repI.y;
+          const double xib = xb - repI.x, etab = yb - repI.y;
           double sa[9], sb[9];
           mode_proj(ex, ey, xia, etaa, fa, da, sa);
           mode_proj(ex, ey, xib, etab, fb, db, sb);
@@ -201,15 +217,22 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
           slot = SLOT_NW;
           idx = (d == 2) ? 0 : 1;
         }
+        double2 da, db;
+        double xa, ya, xb, yb;
+        fp64_ends(da, db, xa, ya, xb, yb);
         const int Jx = Ix + dxs, Jy = Iy + dys;
         const double2 repJ = lv.rep[Jy * lv.Mx + Jx];
         double* e = lists + (size_t)(LC.off[slot] + idx) * LSTRIDE;
-        e[0] = k;
-        mode_proj(ex, ey, xa - repI.x, ya - repI.y, fa, da, e + 1);
-        double sb[9];
+        double sa[9], sb[9];
+        mode_proj(ex, ey, xa - repI.x, ya - repI.y, fa, da, sa);
         mode_proj(ex, ey, xb - repJ.x, yb - repJ.y, fb, db, sb);
 #pragma unroll
-        for (int m = 0; m < 9; ++m) e[10 + m] = -sb[m];
+        for (int m = 0; m < 9; ++m) {
+          e[m] = sa[m];
+          e[9 + m] = -sb[m];
+          e[18 + m] = k * sa[m];
+          e[27 + m] = -(k * sb[m]);
+        }
       }
     }
   }
@@ -262,17 +285,21 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
     }
     if (have) out[SLOT_SELF * SLOT_SIZE + m * SLOT_DIM + l] = v;
   }
-  // interface slots: sum over each list in index order
-  for (int q = tid; q < 5 * SLOT_SIZE; q += NT) {
-    const int slot = 1 + q / SLOT_SIZE;
-    const int pq = q % SLOT_SIZE;
-    const int p = pq / SLOT_DIM, c = pq % SLOT_DIM;
+  // interface slots: sum over each list in index order; each slot is
+  // symmetric (a sum of (EA/L) s s^T), so only p <= c is summed
+  constexpr int NUP = SLOT_DIM * (SLOT_DIM + 1) / 2;
+  for (int q = tid; q < 5 * NUP; q += NT) {
+    const int slot = 1 + q / NUP;
+    int r = q % NUP, p = 0;
+    while (r >= SLOT_DIM - p) r -= SLOT_DIM - p, ++p;
+    const int c = p + r;
     const bool dp = (p % 9) >= 6, dc = (c % 9) >= 6;
     if (!FULL && !dp && !dc) continue;
     const double* e = lists + (size_t)LC.off[slot] * LSTRIDE;
     double v = 0.0;
-    for (int b = 0; b < LC.cap[slot]; ++b, e += LSTRIDE) v = fma(e[0] * e[1 + p], e[1 + c], v);
-    out[slot * SLOT_SIZE + pq] = v;
+    for (int b = 0; b < LC.cap[slot]; ++b, e += LSTRIDE) v = fma(e[18 + p], e[c], v);
+    out[slot * SLOT_SIZE + p * SLOT_DIM + c] = v;
+    out[slot * SLOT_SIZE + c * SLOT_DIM + p] = v;
   }
 }
 
