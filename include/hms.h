@@ -129,6 +129,22 @@ hms_status hms_solve(hms_problem* pr, int32_t nrhs, const double* loads, const d
                      double* u_out, double* hist, int32_t hist_cap, int32_t* iters,
                      int32_t mem_kind);
 
+/* Many independent problems of one context solved together (batched uneven
+ * lattices; the paper solves one lattice at a time).  Problem i solves its
+ * nrhs[i] load vectors loads[i] ([nrhs[i]][2*nx_i*ny_i]) from u0 = 0 into
+ * u_out[i] (same shape), one after another, exactly as hms_solve would; the
+ * problems run concurrently: every round launches each active problem's CUDA
+ * graph (options.batch updates) on one of up to 64 streams of the context,
+ * then the host reads every problem's convergence flag and starts its next
+ * load vector where one finished.  iters (nullable) receives the update
+ * counts, problem by problem and load vector by load vector.  The problems
+ * must belong to c, appear once, and not use options.profile.  Returns the
+ * first device error, else HMS_ERR_NONFINITE / HMS_ERR_NO_CONVERGENCE if a
+ * load vector ended that way (all results still written), else HMS_OK. */
+hms_status hms_solve_batch(hms_context* c, int32_t count, hms_problem* const* problems,
+                           const int32_t* nrhs, const double* const* loads, double* const* u_out,
+                           int32_t* iters, int32_t mem_kind);
+
 /* Per-kernel CUDA-event time of the last hms_solve with options.profile = 1:
  * names "update_residual", "relax", "coarse_assemble", "coarse_band",
  * "coarse_factor", "coarse_residual", "coarse_solve", in that order;

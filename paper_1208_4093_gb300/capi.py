@@ -89,6 +89,7 @@ def lib():
         "hms_coarse_matrix": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
         "hms_coarse_solve": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32]),
         "hms_residual_noalloc": (ctypes.c_int32, [_P, _P, _P, _P, _P]),
+        "hms_solve_batch": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -104,7 +105,7 @@ def exported_symbols():
             "hms_problem_create", "hms_problem_destroy", "hms_problem_device_bytes",
             "hms_problem_setup_ms", "hms_solve", "hms_kernel_times", "hms_residual",
             "hms_update_residual", "hms_relax", "hms_coarse_matrix", "hms_coarse_solve",
-            "hms_residual_noalloc"]
+            "hms_residual_noalloc", "hms_solve_batch"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -214,6 +215,22 @@ def hms_solve(ctx, pr, loads, u_out, u0=None, hist=None, iters=None, allow_no_co
     st = lib().hms_solve(pr, nrhs, L.ptr, U0.ptr, U.ptr, H.ptr, cap, It.ptr, kind)
     ok = (HMS_OK, HMS_ERR_NO_CONVERGENCE) if allow_no_convergence else (HMS_OK,)
     return _check(ctx, st, ok)
+
+
+def hms_solve_batch(ctx, problems, loads, u_out, iters=None, allow_no_convergence=False):
+    """problems: list of handles; loads[i], u_out[i]: arrays [nrhs_i, 2*nx_i*ny_i]
+    (all NumPy, or all CUDA tensors); iters: int32 array of sum(nrhs_i) or None."""
+    n = len(problems)
+    L = [_Arg(x) for x in loads]
+    U = [_Arg(x, writable=True) for x in u_out]
+    I = _Arg(iters, dtype=np.int32, writable=True)
+    mk = _mem_kind(*L, *U, I)
+    nrhs = (ctypes.c_int32 * max(n, 1))(*[int(x.shape[0]) if len(x.shape) > 1 else 1 for x in loads])
+    pp = (_P * max(n, 1))(*[ctypes.cast(pr, _P) for pr in problems])
+    lp = (_P * max(n, 1))(*[a.ptr for a in L])
+    up = (_P * max(n, 1))(*[a.ptr for a in U])
+    ok = (HMS_OK, HMS_ERR_NO_CONVERGENCE) if allow_no_convergence else (HMS_OK,)
+    return _check(ctx, lib().hms_solve_batch(ctx, n, pp, nrhs, lp, up, I.ptr, mk), ok=ok)
 
 
 def hms_kernel_times(pr):

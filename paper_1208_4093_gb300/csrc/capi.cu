@@ -16,6 +16,7 @@ struct hms_context {
   int device = 0;
   int nsm = 0;
   cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> pool;  // streams of hms_solve_batch, created on first use
   std::string err;
 };
 
@@ -282,6 +283,7 @@ void hms_context_destroy(hms_context* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamDestroy(c->stream);
+  for (cudaStream_t s : c->pool) cudaStreamDestroy(s);
   delete c;
 }
 
@@ -649,6 +651,107 @@ int32_t hms_kernel_times(const hms_problem* pr, double* ms_total, int64_t* launc
     if (launches) launches[k] = pr->klaunch[k];
   }
   return m;
+}
+
+hms_status hms_solve_batch(hms_context* c, int32_t count, hms_problem* const* problems, const int32_t* nrhs,
+                           const double* const* loads, double* const* u_out, int32_t* iters, int32_t mem_kind) {
+  if (!c) return HMS_ERR_ARG;
+  if (count < 0 || (count > 0 && (!problems || !nrhs || !loads || !u_out)))
+    return fail(c, HMS_ERR_ARG, "hms_solve_batch: count < 0 or missing arrays");
+  if (mem_kind != HMS_MEM_HOST && mem_kind != HMS_MEM_DEVICE) return fail(c, HMS_ERR_ARG, "bad mem_kind");
+  {
+    std::vector<const hms_problem*> seen(problems, problems + count);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+      return fail(c, HMS_ERR_ARG, "hms_solve_batch: a problem appears twice");
+  }
+  for (int i = 0; i < count; ++i) {
+    const hms_problem* pr = problems[i];
+    if (!pr || pr->ctx != c) return fail(c, HMS_ERR_ARG, "hms_solve_batch: problem of another context");
+    if (nrhs[i] < 0 || (nrhs[i] > 0 && (!loads[i] || !u_out[i])))
+      return fail(c, HMS_ERR_ARG, "hms_solve_batch: bad nrhs / loads / u_out");
+    if (pr->profile) return fail(c, HMS_ERR_ARG, "hms_solve_batch: profile-mode problems run alone");
+  }
+  CKC(c, cudaSetDevice(c->device));
+  const int nstreams = std::max(1, std::min(count, 64));
+  while ((int)c->pool.size() < nstreams) {
+    cudaStream_t s = nullptr;
+    CKC(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    c->pool.push_back(s);
+  }
+  std::vector<long long> ioff(count + 1, 0);
+  for (int i = 0; i < count; ++i) ioff[i + 1] = ioff[i] + nrhs[i];
+  std::vector<int32_t> its((size_t)ioff[count], 0);
+  std::vector<int> q(count, 0), launches(count, 0), status(count, 1);
+  std::vector<char> active(count, 0);
+  auto stream_of = [&](int i) { return c->pool[i % nstreams]; };
+  // load vector q[i] of problem i: loads in, u = 0, iteration control reset, ||p|| (as hms_solve)
+  auto start = [&](int i) -> cudaError_t {
+    hms_problem* pr = problems[i];
+    cudaStream_t s = stream_of(i);
+    const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+    cudaError_t e = cudaMemcpyAsync(pr->p, loads[i] + 2 * nn * q[i], vb, kind_in(mem_kind), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pr->u[0], 0, vb, s);
+    IterCtl hc{};
+    hc.max_iter = pr->max_iter;
+    hc.tol = pr->tol;
+    *pr->ctl_host = hc;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pr->ctl, pr->ctl_host, sizeof(IterCtl), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_load_norms(s, pr->lv, pr->p, pr->partials, pr->ticket, pr->ctl);
+    launches[i] = 0;
+    active[i] = 1;
+    return e;
+  };
+  for (int i = 0; i < count; ++i)
+    if (nrhs[i] > 0) CKC(c, start(i));
+  bool any = true;
+  while (any) {
+    // one graph launch (batch iterations) per active problem, each on its stream
+    for (int i = 0; i < count; ++i) {
+      if (!active[i]) continue;
+      hms_problem* pr = problems[i];
+      CKC(c, cudaGraphLaunch(pr->graph, stream_of(i)));
+      CKC(c, cudaMemcpyAsync(pr->ctl_host, pr->ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, stream_of(i)));
+      ++launches[i];
+    }
+    for (int k = 0; k < nstreams; ++k) CKC(c, cudaStreamSynchronize(c->pool[k]));
+    any = false;
+    for (int i = 0; i < count; ++i) {
+      if (!active[i]) continue;
+      hms_problem* pr = problems[i];
+      const IterCtl fin = *pr->ctl_host;
+      if (!fin.done && launches[i] < pr->max_iter / pr->batch + 3) {
+        any = true;
+        continue;
+      }
+      const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+      CKC(c, cudaMemcpyAsync(u_out[i] + 2 * nn * q[i], pr->u[fin.t & 1], vb, kind_out(mem_kind), stream_of(i)));
+      its[(size_t)(ioff[i] + q[i])] = fin.t > 0 ? fin.t - 1 : 0;
+      if (fin.status == 3) status[i] = 3;
+      else if (fin.status != 1 && status[i] == 1) status[i] = 2;
+      if (++q[i] < nrhs[i]) {
+        CKC(c, start(i));
+        any = true;
+      } else {
+        active[i] = 0;
+      }
+    }
+  }
+  for (int k = 0; k < nstreams; ++k) CKC(c, cudaStreamSynchronize(c->pool[k]));
+  if (iters && ioff[count] > 0) {
+    if (mem_kind == HMS_MEM_DEVICE)
+      CKC(c, cudaMemcpy(iters, its.data(), its.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    else
+      std::memcpy(iters, its.data(), its.size() * sizeof(int32_t));
+  }
+  hms_status result = HMS_OK;
+  for (int i = 0; i < count; ++i) {
+    const hms_status st = check_dev_err(problems[i]);
+    if (st != HMS_OK) return st;
+    if (status[i] == 3 && result == HMS_OK) result = fail(c, HMS_ERR_NONFINITE, "non-finite residual norm");
+    if (status[i] == 2 && result == HMS_OK) result = fail(c, HMS_ERR_NO_CONVERGENCE, "max_iter reached before tol");
+  }
+  return result;
 }
 
 hms_status hms_residual(hms_problem* pr, const double* p, const double* u, double* r, double* norms,

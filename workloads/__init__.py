@@ -38,6 +38,7 @@ _MASK32 = np.uint64(0xFFFFFFFF)
 # stream tags (the fourth counter word), one per kind of draw
 TAG_LOAD = 0x4C4F4144  # "LOAD"
 TAG_EA = 0x45414541    # "EAEA"
+TAG_BATCH = 0x42415443  # "BATC"
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):
@@ -161,3 +162,40 @@ CASES = {
     "lattice22361_mixed": LatticeCase(
         "lattice22361_mixed", 22361, 22361, 64, 64, "uniform", 1e-10, "mixed"),
 }
+
+
+@dataclasses.dataclass(frozen=True)
+class BatchLattice:
+    """One lattice of a batch: size, load-vector count and its load seed."""
+    nx: int
+    ny: int
+    nrhs: int
+    seed: int
+
+    def load_array(self):
+        """[nrhs, 2*nx*ny] loads, load vector r from counter rhs = r."""
+        return np.stack([loads(self.nx, self.ny, self.seed, r).reshape(-1) for r in range(self.nrhs)])
+
+
+def batched_lattices(count: int = 256, seed: int = 7, side_min: int = 32, side_max: int = 512,
+                     aspect_max: float = 4.0, nrhs_max: int = 8):
+    """Independent lattices of uneven shape: lattice k draws counter
+    (k, 0, 0, TAG_BATCH) under key (seed, 2); the long side is log-uniform in
+    [side_min, side_max] (word 0), the aspect ratio Uniform[1, aspect_max]
+    (word 1), the short side max(2, round(long / aspect)), the orientation a
+    coin flip (word 2) and the load-vector count 1 + floor(nrhs_max u)
+    (word 3).  Lattice k's loads use seed 1000 + k."""
+    k = np.arange(count, dtype=np.uint64)
+    w0, w1, w2, w3 = philox4x32_10(k.astype(np.uint32), np.zeros(count, np.uint32), np.uint32(0),
+                                   np.uint32(TAG_BATCH), seed & 0xFFFFFFFF, ((seed >> 32) + 2) & 0xFFFFFFFF)
+    lo, hi = math.log(side_min), math.log(side_max)
+    longs = np.rint(np.exp(lo + (hi - lo) * uniform01(w0))).astype(int)
+    aspect = 1.0 + (aspect_max - 1.0) * uniform01(w1)
+    shorts = np.maximum(2, np.rint(longs / aspect).astype(int))
+    flip = uniform01(w2) < 0.5
+    nrhs = 1 + np.minimum(nrhs_max - 1, np.floor(nrhs_max * uniform01(w3)).astype(int))
+    out = []
+    for i in range(count):
+        nx, ny = (int(longs[i]), int(shorts[i])) if flip[i] else (int(shorts[i]), int(longs[i]))
+        out.append(BatchLattice(nx, ny, int(nrhs[i]), 1000 + i))
+    return out
