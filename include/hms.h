@@ -234,6 +234,46 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
 hms_status hms_residual_noalloc(hms_problem* pr, const double* p, const double* u, double* r,
                                 double* norms);
 
+/* ---- serving (no counterpart in the paper) ---- */
+
+/* Device bytes hms_problem_create would allocate for (d, o), counted
+ * allocation by allocation as the library makes them, including the scratch
+ * held while the set factors are computed; 0 if the problem would be
+ * rejected (bad arguments, set tile or set grid too large). */
+size_t hms_problem_estimate_bytes(hms_context* c, const hms_lattice_desc* d, const hms_options* o);
+
+/* A request server on one context: requests (lattice, options, nrhs load
+ * vectors) are queued and admitted in arrival order while the sum of the
+ * admitted requests' device bytes stays within hbm_budget_bytes (and at most
+ * max_active run at once); every hms_server_step advances all admitted
+ * requests together by one CUDA-graph round (options.batch updates), each on
+ * its own stream, so requests that arrive while others run join them at the
+ * next step (continuous batching).  A request solves its load vectors one
+ * after another exactly as hms_solve would; its problem is destroyed, and its
+ * memory returned to the budget, when the last one is done.  A server is not
+ * thread-safe; other work on the same context must not run during a step. */
+typedef struct hms_server hms_server;
+hms_status hms_server_create(hms_context* c, uint64_t hbm_budget_bytes, int32_t max_active,
+                             hms_server** out);
+void hms_server_destroy(hms_server* s);
+/* Queue a request; d, its ea / fixed arrays (host) and the nrhs load vectors
+ * loads [nrhs][2*nx*ny] (host) are copied.  *id receives its id.  A request
+ * whose problem would be rejected gives HMS_ERR_ARG, one larger than the
+ * whole budget HMS_ERR_OOM. */
+hms_status hms_server_submit(hms_server* s, const hms_lattice_desc* d, const hms_options* o,
+                             int32_t nrhs, const double* loads, int64_t* id);
+/* One scheduling round: admit what fits, advance every admitted request,
+ * retire the finished ones.  done_ids [cap] receives the ids finished in
+ * this round (*n_done of them; only the first cap are written); n_active,
+ * n_queued, bytes_in_use (nullable) the state after the round. */
+hms_status hms_server_step(hms_server* s, int64_t* done_ids, int32_t cap, int32_t* n_done,
+                           int32_t* n_active, int32_t* n_queued, uint64_t* bytes_in_use);
+/* Results of a finished request, then forgotten: u_out [nrhs][2*nx*ny] (host,
+ * nullable), iters [nrhs] (host, nullable).  Returns the request's status
+ * (HMS_OK, HMS_ERR_NO_CONVERGENCE, HMS_ERR_NONFINITE, or the error that kept
+ * it from being set up, in which case nothing is written to u_out). */
+hms_status hms_server_take(hms_server* s, int64_t id, double* u_out, int32_t* iters);
+
 #ifdef __cplusplus
 }
 #endif

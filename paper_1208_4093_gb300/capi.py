@@ -90,6 +90,13 @@ def lib():
         "hms_coarse_solve": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32]),
         "hms_residual_noalloc": (ctypes.c_int32, [_P, _P, _P, _P, _P]),
         "hms_solve_batch": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32]),
+        "hms_problem_estimate_bytes": (ctypes.c_size_t, [_P, ctypes.POINTER(LatticeDesc), ctypes.POINTER(Options)]),
+        "hms_server_create": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(_P)]),
+        "hms_server_destroy": (None, [_P]),
+        "hms_server_submit": (ctypes.c_int32, [_P, ctypes.POINTER(LatticeDesc), ctypes.POINTER(Options), ctypes.c_int32,
+                                               _P, ctypes.POINTER(ctypes.c_int64)]),
+        "hms_server_step": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, _P]),
+        "hms_server_take": (ctypes.c_int32, [_P, ctypes.c_int64, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -105,7 +112,8 @@ def exported_symbols():
             "hms_problem_create", "hms_problem_destroy", "hms_problem_device_bytes",
             "hms_problem_setup_ms", "hms_solve", "hms_kernel_times", "hms_residual",
             "hms_update_residual", "hms_relax", "hms_coarse_matrix", "hms_coarse_solve",
-            "hms_residual_noalloc", "hms_solve_batch"]
+            "hms_residual_noalloc", "hms_solve_batch", "hms_problem_estimate_bytes", "hms_server_create",
+            "hms_server_destroy", "hms_server_submit", "hms_server_step", "hms_server_take"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -170,10 +178,9 @@ def hms_last_error(ctx) -> str:
     return m.decode() if m else ""
 
 
-def hms_problem_create(ctx, nx, ny, set_sx, set_sy, *, bar_length=1.0, ea=None, ea_uniform=1.0,
-                       fixed=None, fix_bottom_edge=1, precision=HMS_FP64, tol=1e-8, max_iter=1000,
-                       coarse_solves=0, batch=0, profile=0, coarse_factor=0):
-    """ea: host float64 [3, ny, nx] or None; fixed: host uint8 [ny, nx, 2] or None."""
+def _desc_opts(nx, ny, set_sx, set_sy, bar_length=1.0, ea=None, ea_uniform=1.0, fixed=None, fix_bottom_edge=1,
+               precision=HMS_FP64, tol=1e-8, max_iter=1000, coarse_solves=0, batch=0, profile=0, coarse_factor=0):
+    """LatticeDesc and Options structs (plus the arrays they point to, kept alive by the caller)."""
     ea_a = None if ea is None else np.ascontiguousarray(ea, dtype=np.float64)
     fx_a = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
     if ea_a is not None and ea_a.size != 3 * nx * ny:
@@ -185,9 +192,22 @@ def hms_problem_create(ctx, nx, ny, set_sx, set_sy, *, bar_length=1.0, ea=None, 
                     int(set_sx), int(set_sy))
     o = Options(int(precision), float(tol), int(max_iter), int(coarse_solves), int(batch), int(profile),
                 int(coarse_factor))
+    return d, o, (ea_a, fx_a)
+
+
+def hms_problem_create(ctx, nx, ny, set_sx, set_sy, **kw):
+    """kw: bar_length, ea (host float64 [3, ny, nx]), ea_uniform, fixed (host uint8
+    [ny, nx, 2]), fix_bottom_edge, precision, tol, max_iter, coarse_solves, batch,
+    profile, coarse_factor."""
+    d, o, keep = _desc_opts(nx, ny, set_sx, set_sy, **kw)
     h = _P()
     _check(ctx, lib().hms_problem_create(ctx, ctypes.byref(d), ctypes.byref(o), ctypes.byref(h)))
     return h
+
+
+def hms_problem_estimate_bytes(ctx, nx, ny, set_sx, set_sy, **kw) -> int:
+    d, o, keep = _desc_opts(nx, ny, set_sx, set_sy, **kw)
+    return int(lib().hms_problem_estimate_bytes(ctx, ctypes.byref(d), ctypes.byref(o)))
 
 
 def hms_problem_destroy(pr):
@@ -231,6 +251,45 @@ def hms_solve_batch(ctx, problems, loads, u_out, iters=None, allow_no_convergenc
     up = (_P * max(n, 1))(*[a.ptr for a in U])
     ok = (HMS_OK, HMS_ERR_NO_CONVERGENCE) if allow_no_convergence else (HMS_OK,)
     return _check(ctx, lib().hms_solve_batch(ctx, n, pp, nrhs, lp, up, I.ptr, mk), ok=ok)
+
+
+def hms_server_create(ctx, hbm_budget_bytes, max_active=256):
+    h = _P()
+    _check(ctx, lib().hms_server_create(ctx, int(hbm_budget_bytes), int(max_active), ctypes.byref(h)))
+    return h
+
+
+def hms_server_destroy(srv):
+    lib().hms_server_destroy(srv)
+
+
+def hms_server_submit(ctx, srv, nx, ny, set_sx, set_sy, loads, **kw) -> int:
+    """loads: host float64 [nrhs, 2*nx*ny]; kw as hms_problem_create.  Returns the id."""
+    d, o, keep = _desc_opts(nx, ny, set_sx, set_sy, **kw)
+    a = np.ascontiguousarray(loads, dtype=np.float64).reshape(-1, 2 * int(nx) * int(ny))
+    rid = ctypes.c_int64()
+    _check(ctx, lib().hms_server_submit(srv, ctypes.byref(d), ctypes.byref(o), int(a.shape[0]), a.ctypes.data,
+                                        ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def hms_server_step(ctx, srv, cap=4096):
+    """One round; returns (finished ids, n_active, n_queued, bytes_in_use)."""
+    ids = (ctypes.c_int64 * cap)()
+    nd, na, nq = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    used = ctypes.c_uint64()
+    _check(ctx, lib().hms_server_step(srv, ids, int(cap), ctypes.byref(nd), ctypes.byref(na), ctypes.byref(nq),
+                                      ctypes.byref(used)))
+    return [int(ids[k]) for k in range(min(nd.value, cap))], na.value, nq.value, int(used.value)
+
+
+def hms_server_take(ctx, srv, rid, u_out=None, iters=None):
+    """Copies the results of a finished request; returns its status code."""
+    U = _Arg(u_out, writable=True)
+    I = _Arg(iters, dtype=np.int32, writable=True)
+    if U.kind == HMS_MEM_DEVICE or I.kind == HMS_MEM_DEVICE:
+        raise ValueError("hms_server_take writes host arrays")
+    return int(lib().hms_server_take(srv, int(rid), U.ptr, I.ptr))
 
 
 def hms_kernel_times(pr):

@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/hms.h"
@@ -232,6 +234,29 @@ hms_status check_dev_err(hms_problem* pr) {
   return HMS_OK;
 }
 
+// Upper-level factor precision and substitution of a problem whose lv, n_c,
+// bw and precision are set: FP64 for degenerate set shapes (one- or
+// two-node-wide tiles give ill-conditioned upper-level systems), else FP32
+// with FP64 refinement, solved by 64-row blocks with inverted diagonal blocks
+// when that fits in shared memory (coarse_factor = 3 keeps the 16-row
+// solve).  False if the band does not fit one CTA's shared memory.
+bool choose_coarse(hms_problem* pr, const hms_options* o, int maxsm) {
+  const LatView& lv = pr->lv;
+  const int wmin = std::min(lv.sx, lv.nx - (lv.Mx - 1) * lv.sx);
+  const int hmin = std::min(lv.sy, lv.ny - (lv.My - 1) * lv.sy);
+  const bool degenerate = std::min(wmin, hmin) <= 2;
+  auto fits = [&](bool f64) {
+    return coarse_factor_smem_bytes(pr->n_c, pr->bw, f64) + 1024 <= (size_t)maxsm &&
+           coarse_solve_smem_bytes(pr->n_c, pr->bw, f64) + 1024 <= (size_t)maxsm;
+  };
+  if (o->coarse_factor == 2) pr->coarse_fp64 = true;
+  else if (o->coarse_factor == 1 || o->coarse_factor == 3) pr->coarse_fp64 = false;
+  else pr->coarse_fp64 = degenerate && fits(true);
+  if (!fits(pr->coarse_fp64)) return false;
+  pr->big_stages = (pr->coarse_fp64 || o->coarse_factor == 3) ? 0 : coarse_big_stages(pr->n_c, pr->bw, maxsm);
+  return true;
+}
+
 }  // namespace
 
 namespace hms {
@@ -346,27 +371,9 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     delete pr;
     return fail(c, HMS_ERR_ARG, "set tile too large for the relaxation kernel's shared memory");
   }
-  {
-    // upper-level factor precision: FP64 for degenerate set shapes (one- or
-    // two-node-wide tiles give ill-conditioned upper-level systems), else FP32
-    // with FP64 refinement
-    const int wmin = std::min(lv.sx, lv.nx - (lv.Mx - 1) * lv.sx);
-    const int hmin = std::min(lv.sy, lv.ny - (lv.My - 1) * lv.sy);
-    const bool degenerate = std::min(wmin, hmin) <= 2;
-    auto fits = [&](bool f64) {
-      return coarse_factor_smem_bytes(pr->n_c, pr->bw, f64) + 1024 <= (size_t)maxsm &&
-             coarse_solve_smem_bytes(pr->n_c, pr->bw, f64) + 1024 <= (size_t)maxsm;
-    };
-    if (o->coarse_factor == 2) pr->coarse_fp64 = true;
-    else if (o->coarse_factor == 1 || o->coarse_factor == 3) pr->coarse_fp64 = false;
-    else pr->coarse_fp64 = degenerate && fits(true);
-    if (!fits(pr->coarse_fp64)) {
-      delete pr;
-      return fail(c, HMS_ERR_ARG, "set grid too wide for the upper-level band factorisation");
-    }
-    // FP32 factor: solve by 64-row blocks with inverted diagonal blocks when
-    // that fits in shared memory (coarse_factor = 3 keeps the 16-row solve)
-    pr->big_stages = (pr->coarse_fp64 || o->coarse_factor == 3) ? 0 : coarse_big_stages(pr->n_c, pr->bw, maxsm);
+  if (!choose_coarse(pr, o, maxsm)) {
+    delete pr;
+    return fail(c, HMS_ERR_ARG, "set grid too wide for the upper-level band factorisation");
   }
   if (coarse_slots_smem(lv) > (size_t)maxsm) {
     delete pr;
@@ -914,6 +921,256 @@ hms_status hms_residual_noalloc(hms_problem* pr, const double* p, const double* 
                                  ticket, norms));
   CKC(c, cudaStreamSynchronize(c->stream));
   return HMS_OK;
+}
+
+// Device bytes hms_problem_create would allocate for (d, o), following its
+// allocations one by one (plus the set-factor scratch it holds during setup);
+// 0 if the problem would be rejected.
+size_t hms_problem_estimate_bytes(hms_context* c, const hms_lattice_desc* d, const hms_options* o) {
+  if (!c || !d || !o || d->nx < 2 || d->ny < 2 || d->set_sx < 1 || d->set_sx > MAX_SX || d->set_sy < 1) return 0;
+  if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return 0;
+  hms_problem pr;
+  LatView& lv = pr.lv;
+  lv.nx = d->nx;
+  lv.ny = d->ny;
+  lv.sx = d->set_sx;
+  lv.sy = d->set_sy;
+  lv.Mx = (d->nx + d->set_sx - 1) / d->set_sx;
+  lv.My = (d->ny + d->set_sy - 1) / d->set_sy;
+  lv.M = lv.Mx * lv.My;
+  pr.precision = o->precision;
+  pr.n_c = NMODES * lv.M;
+  pr.bw = coarse_bw(lv);
+  int maxsm = 0;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (relax_smem_bytes(lv, fp32(&pr)) + 2048 > (size_t)maxsm || !choose_coarse(&pr, o, maxsm) ||
+      coarse_slots_smem(lv) > (size_t)maxsm)
+    return 0;
+  const size_t nn = (size_t)lv.nx * lv.ny, M = (size_t)lv.M, n_c = (size_t)pr.n_c;
+  const size_t esz = fp32(&pr) ? 4 : 8;
+  const size_t nband = n_c * (pr.bw + 1);
+  size_t fac = 0;
+  for (int I = 0; I < lv.M; ++I) {
+    const int w = std::min(lv.sx, lv.nx - (I % lv.Mx) * lv.sx), h = std::min(lv.sy, lv.ny - (I / lv.Mx) * lv.sy);
+    fac += (size_t)set_factor_stride(2 * w, h);
+  }
+  size_t b = nn + (d->ea ? 3 * nn * 8 : 0) + M * 16 + (M + 1) * 8 + fac * esz;
+  b += 4 * nn * 16 + nn * 2 * esz + M * (size_t)relax_y_stride(lv) * esz;
+  b += 2 * n_c * 8 + 2 * M * NSLOTS * SLOT_SIZE * 8 + 3 * nband * 8 + 4 * n_c * 8;
+  b += 2 * (nband + 16) * 8 + (size_t)coarse_dinv_size(pr.n_c) * 8;
+  if (pr.big_stages > 0) b += coarse_xinv_elems(pr.n_c, pr.bw) * 4;
+  b += n_c * 4 + 32 + (size_t)std::max(update_residual_blocks(lv), 1024) * 3 * 8 + 4 + sizeof(IterCtl) + 4 + 32;
+  b += 3 * ((size_t)o->max_iter + 1) * 8;
+  b += (size_t)std::max(1, std::min(lv.M, c->nsm)) * b_size(MAX_NB) * 8;  // setup scratch
+  return b;
+}
+
+// ---------------------------------------------------------------- serving
+// Requests (a lattice, options and nrhs load vectors) are queued, admitted in
+// arrival order while their estimated bytes fit the budget, and advanced
+// together one CUDA-graph round per step, each on a stream of the context's
+// pool; a request's problem is destroyed (its memory returned) as soon as its
+// last load vector is done.
+struct hms_server {
+  struct Req {
+    int64_t id = 0;
+    hms_lattice_desc d{};
+    hms_options o{};
+    std::vector<double> ea;
+    std::vector<uint8_t> fixed;
+    int nrhs = 0;
+    double* loads = nullptr;  // pinned, [nrhs][2 nn]
+    double* u = nullptr;      // pinned, [nrhs][2 nn]
+    std::vector<int32_t> iters;
+    hms_problem* pr = nullptr;
+    uint64_t bytes = 0;
+    int q = 0, launches = 0, slot = 0;
+    bool ran = false;  // admitted and solved (u holds results)
+    hms_status status = HMS_OK;
+  };
+  hms_context* ctx = nullptr;
+  uint64_t budget = 0, used = 0;
+  int max_active = 0, next_slot = 0;
+  int64_t next_id = 1;
+  std::deque<Req*> queue;
+  std::vector<Req*> active;
+  std::unordered_map<int64_t, Req*> done;
+};
+
+namespace {
+void free_req(hms_server::Req* r) {
+  if (r->pr) hms_problem_destroy(r->pr);
+  if (r->loads) cudaFreeHost(r->loads);
+  if (r->u) cudaFreeHost(r->u);
+  delete r;
+}
+cudaStream_t req_stream(hms_server* s, const hms_server::Req* r) { return s->ctx->pool[r->slot]; }
+// load vector r->q of a request: in, u = 0, iteration control reset, ||p||
+cudaError_t req_start(hms_server* s, hms_server::Req* r) {
+  hms_problem* pr = r->pr;
+  cudaStream_t st = req_stream(s, r);
+  const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+  cudaError_t e = cudaMemcpyAsync(pr->p, r->loads + 2 * nn * r->q, vb, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pr->u[0], 0, vb, st);
+  IterCtl hc{};
+  hc.max_iter = pr->max_iter;
+  hc.tol = pr->tol;
+  *pr->ctl_host = hc;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pr->ctl, pr->ctl_host, sizeof(IterCtl), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_load_norms(st, pr->lv, pr->p, pr->partials, pr->ticket, pr->ctl);
+  r->launches = 0;
+  return e;
+}
+}  // namespace
+
+hms_status hms_server_create(hms_context* c, uint64_t hbm_budget_bytes, int32_t max_active, hms_server** out) {
+  if (!c || !out || hbm_budget_bytes == 0 || max_active < 1) return HMS_ERR_ARG;
+  CKC(c, cudaSetDevice(c->device));
+  while ((int)c->pool.size() < 64) {
+    cudaStream_t s = nullptr;
+    CKC(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    c->pool.push_back(s);
+  }
+  hms_server* s = new hms_server();
+  s->ctx = c;
+  s->budget = hbm_budget_bytes;
+  s->max_active = max_active;
+  *out = s;
+  return HMS_OK;
+}
+
+void hms_server_destroy(hms_server* s) {
+  if (!s) return;
+  cudaSetDevice(s->ctx->device);
+  for (auto& st : s->ctx->pool) cudaStreamSynchronize(st);
+  for (auto* r : s->queue) free_req(r);
+  for (auto* r : s->active) free_req(r);
+  for (auto& kv : s->done) free_req(kv.second);
+  delete s;
+}
+
+hms_status hms_server_submit(hms_server* s, const hms_lattice_desc* d, const hms_options* o, int32_t nrhs,
+                             const double* loads, int64_t* id) {
+  if (!s || !d || !o || nrhs < 1 || !loads || !id) return HMS_ERR_ARG;
+  hms_context* c = s->ctx;
+  if (o->profile) return fail(c, HMS_ERR_ARG, "hms_server_submit: profile mode is not served");
+  const uint64_t est = hms_problem_estimate_bytes(c, d, o);
+  if (est == 0) return fail(c, HMS_ERR_ARG, "hms_server_submit: the problem would be rejected (lattice / sets / options)");
+  if (est > s->budget)
+    return fail(c, HMS_ERR_OOM, "hms_server_submit: the request needs " + std::to_string(est) +
+                                    " bytes, more than the whole budget of " + std::to_string(s->budget));
+  auto* r = new hms_server::Req();
+  r->d = *d;
+  r->o = *o;
+  const size_t nn = (size_t)d->nx * d->ny;
+  if (d->ea) {
+    r->ea.assign(d->ea, d->ea + 3 * nn);
+    r->d.ea = r->ea.data();
+  }
+  if (d->fixed) {
+    r->fixed.assign(d->fixed, d->fixed + 2 * nn);
+    r->d.fixed = r->fixed.data();
+  }
+  r->nrhs = nrhs;
+  r->bytes = est;
+  r->iters.assign(nrhs, 0);
+  const size_t vb = (size_t)nrhs * 2 * nn * sizeof(double);
+  if (cudaMallocHost(&r->loads, vb) != cudaSuccess || cudaMallocHost(&r->u, vb) != cudaSuccess) {
+    cudaGetLastError();
+    free_req(r);
+    return fail(c, HMS_ERR_OOM, "hms_server_submit: pinned host buffers");
+  }
+  std::memcpy(r->loads, loads, vb);
+  r->id = s->next_id++;
+  s->queue.push_back(r);
+  *id = r->id;
+  return HMS_OK;
+}
+
+hms_status hms_server_step(hms_server* s, int64_t* done_ids, int32_t cap, int32_t* n_done, int32_t* n_active,
+                           int32_t* n_queued, uint64_t* bytes_in_use) {
+  if (!s || (cap > 0 && !done_ids) || !n_done) return HMS_ERR_ARG;
+  hms_context* c = s->ctx;
+  CKC(c, cudaSetDevice(c->device));
+  *n_done = 0;
+  auto report = [&](int64_t id) {
+    if (*n_done < cap) done_ids[*n_done] = id;
+    ++*n_done;
+  };
+  // 1. admission in arrival order while the estimate fits the budget
+  while (!s->queue.empty() && (int)s->active.size() < s->max_active) {
+    hms_server::Req* r = s->queue.front();
+    if (s->used + r->bytes > s->budget) break;
+    s->queue.pop_front();
+    hms_status st = hms_problem_create(c, &r->d, &r->o, &r->pr);
+    if (st != HMS_OK) {
+      r->pr = nullptr;
+      r->status = st;
+      s->done[r->id] = r;
+      report(r->id);
+      continue;
+    }
+    r->bytes = std::max<uint64_t>(r->bytes, r->pr->bytes);
+    s->used += r->bytes;
+    r->ran = true;
+    r->slot = s->next_slot++ % (int)c->pool.size();
+    CKC(c, req_start(s, r));
+    s->active.push_back(r);
+  }
+  // 2. one round of every active request
+  for (auto* r : s->active) {
+    CKC(c, cudaGraphLaunch(r->pr->graph, req_stream(s, r)));
+    CKC(c, cudaMemcpyAsync(r->pr->ctl_host, r->pr->ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, req_stream(s, r)));
+    ++r->launches;
+  }
+  for (auto& st : c->pool) CKC(c, cudaStreamSynchronize(st));
+  // 3. finished load vectors: result out, next one in, or retire the request
+  std::vector<hms_server::Req*> keep;
+  for (auto* r : s->active) {
+    hms_problem* pr = r->pr;
+    const IterCtl fin = *pr->ctl_host;
+    if (!fin.done && r->launches < pr->max_iter / pr->batch + 3) {
+      keep.push_back(r);
+      continue;
+    }
+    const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+    CKC(c, cudaMemcpyAsync(r->u + 2 * nn * r->q, pr->u[fin.t & 1], vb, cudaMemcpyDeviceToHost, req_stream(s, r)));
+    r->iters[r->q] = fin.t > 0 ? fin.t - 1 : 0;
+    if (fin.status == 3 && r->status == HMS_OK) r->status = HMS_ERR_NONFINITE;
+    else if (fin.status != 1 && r->status == HMS_OK) r->status = HMS_ERR_NO_CONVERGENCE;
+    if (++r->q < r->nrhs) {
+      CKC(c, req_start(s, r));
+      keep.push_back(r);
+      continue;
+    }
+    CKC(c, cudaStreamSynchronize(req_stream(s, r)));
+    const hms_status de = check_dev_err(pr);
+    if (de != HMS_OK) r->status = de;
+    hms_problem_destroy(pr);
+    r->pr = nullptr;
+    s->used -= r->bytes;
+    s->done[r->id] = r;
+    report(r->id);
+  }
+  s->active.swap(keep);
+  if (n_active) *n_active = (int32_t)s->active.size();
+  if (n_queued) *n_queued = (int32_t)s->queue.size();
+  if (bytes_in_use) *bytes_in_use = s->used;
+  return HMS_OK;
+}
+
+hms_status hms_server_take(hms_server* s, int64_t id, double* u_out, int32_t* iters) {
+  if (!s) return HMS_ERR_ARG;
+  auto it = s->done.find(id);
+  if (it == s->done.end()) return fail(s->ctx, HMS_ERR_ARG, "hms_server_take: no finished request with this id");
+  hms_server::Req* r = it->second;
+  const size_t nn = (size_t)r->d.nx * r->d.ny;
+  if (u_out && r->ran) std::memcpy(u_out, r->u, (size_t)r->nrhs * 2 * nn * sizeof(double));
+  if (iters) std::memcpy(iters, r->iters.data(), r->nrhs * sizeof(int32_t));
+  const hms_status st = r->status;
+  s->done.erase(it);
+  free_req(r);
+  return st;
 }
 
 }  // extern "C"
