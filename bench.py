@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--ncu-case", choices=["fp64", "mixed"], default=None,
                     help="only run --ncu-iters updates of the workload once (for ncu captures); no JSON line")
     ap.add_argument("--ncu-iters", type=int, default=1)
+    ap.add_argument("--batched", action="store_true",
+                    help="time the batched uneven-lattice workload instead (separate JSON line)")
+    ap.add_argument("--batched-count", type=int, default=256)
+    ap.add_argument("--serve", type=int, default=0, metavar="N",
+                    help="serve N requests of the serving workload instead (separate JSON line)")
     return ap.parse_args()
 
 
@@ -259,6 +264,121 @@ def run_ncu_case(args):
     print(f"{args.ncu_case}: {args.ncu_iters} updates done")
 
 
+# ---------------------------------------------------------------- batched lattices
+def run_batched(args):
+    """256 independent lattices (log-uniform sides 32..512, aspect up to 4,
+    1-8 load vectors, 32 x 32-node sets, EA = 1, mixed precision, R1 < 1e-8):
+    hms_solve_batch against the same problems solved one after another."""
+    import numpy as np
+    import torch
+    from paper_1208_4093_gb300 import capi
+    from workloads import batched_lattices
+    dev = torch.device("cuda", 0)
+    lats = batched_lattices(args.batched_count)
+    ctx = capi.hms_context_create(0)
+    t0 = time.perf_counter()
+    prs = [capi.hms_problem_create(ctx, l.nx, l.ny, 32, 32, precision=capi.HMS_MIXED, tol=TOL, max_iter=5000)
+           for l in lats]
+    setup_s = time.perf_counter() - t0
+    loads = [torch.from_numpy(l.load_array()).to(dev) for l in lats]
+    outs = [torch.empty_like(x) for x in loads]
+    nrhs = sum(l.nrhs for l in lats)
+    its = torch.zeros(nrhs, dtype=torch.int32, device=dev)
+    dofrhs = sum(2 * l.nx * l.ny * l.nrhs for l in lats)
+    torch.cuda.synchronize()
+    for _ in range(max(args.warmup, 1)):
+        capi.hms_solve_batch(ctx, prs, loads, outs, iters=its)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        capi.hms_solve_batch(ctx, prs, loads, outs, iters=its)
+        torch.cuda.synchronize()
+        ms.append((time.perf_counter() - t0) * 1e3)
+    ub = [o.cpu().numpy() for o in outs]
+    # the same problems one after another (one pass)
+    t0 = time.perf_counter()
+    for pr, x, o in zip(prs, loads, outs):
+        capi.hms_solve(ctx, pr, x, o)
+    torch.cuda.synchronize()
+    seq_ms = (time.perf_counter() - t0) * 1e3
+    same = all(np.array_equal(a, o.cpu().numpy()) for a, o in zip(ub, outs))
+    it = its.cpu().numpy()
+    for pr in prs:
+        capi.hms_problem_destroy(pr)
+    capi.hms_context_destroy(ctx)
+    med = statistics.median(ms)
+    print(json.dumps({
+        "metric": "batched uneven lattices: DOF x load vectors solved per second (mixed, R1 < 1e-8)",
+        "value": dofrhs / (med * 1e-3), "unit": "DOF/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 1), "ms_per_step": med, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 relax / f64 residual+master+norms", "data": "synthetic",
+        "config": {"workload": f"batched_lattices_{len(lats)}", "lattices": len(lats), "load_vectors": nrhs,
+                   "dof_x_rhs": dofrhs, "sides": "log-uniform [32, 512]", "aspect": "Uniform[1, 4]",
+                   "sets": [32, 32], "ea": 1.0, "tol": TOL, "setup_s": setup_s,
+                   "updates_median": float(np.median(it)), "updates_max": int(it.max())},
+        "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / med, "same_as_sequential": same}))
+
+
+# ---------------------------------------------------------------- serving
+def run_serve(args):
+    """Requests arrive by a Poisson process (mean 200 per second) with
+    log-uniform sides in [64, 2048] (width capped at 1152), 1-16 load vectors,
+    lognormal(0, 0.3) EA, 64 x 64-node sets, mixed precision, R1 < 1e-8; the
+    server admits them under a 150 GB budget and advances all admitted ones
+    together.  Latency = completion time - arrival time."""
+    import numpy as np
+    from paper_1208_4093_gb300 import capi
+    from workloads import serving_requests
+    reqs = serving_requests(args.serve)
+    data = [(r.ea_array(), r.load_array()) for r in reqs]  # generated before the clock starts
+    budget = 150 << 30
+    ctx = capi.hms_context_create(0)
+    srv = capi.hms_server_create(ctx, budget, max_active=256)
+    rid_of, arrival, done_t, peak_bytes, steps, rejected = {}, {}, {}, 0, 0, []
+    t0 = time.perf_counter()
+    nxt = 0
+    while len(done_t) + len(rejected) < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt].arrival <= now:
+            r = reqs[nxt]
+            ea, ld = data[nxt]
+            try:
+                rid = capi.hms_server_submit(ctx, srv, r.nx, r.ny, 64, 64, ld, ea=ea, precision=capi.HMS_MIXED,
+                                             tol=TOL, max_iter=5000)
+                rid_of[rid] = nxt
+                arrival[rid] = r.arrival
+            except capi.HmsError:
+                rejected.append(nxt)
+            nxt += 1
+        ids, na, nq, used = capi.hms_server_step(ctx, srv)
+        steps += 1
+        peak_bytes = max(peak_bytes, used)
+        t_now = time.perf_counter() - t0
+        for rid in ids:
+            done_t[rid] = t_now
+        if na == 0 and nq == 0 and nxt < len(reqs):
+            time.sleep(max(0.0, reqs[nxt].arrival - (time.perf_counter() - t0)))
+    makespan = time.perf_counter() - t0
+    status = [capi.hms_server_take(ctx, srv, rid) for rid in list(done_t)]
+    capi.hms_server_destroy(srv)
+    capi.hms_context_destroy(ctx)
+    lat = np.array([done_t[rid] - arrival[rid] for rid in done_t]) * 1e3
+    dofrhs = sum(2 * r.nx * r.ny * r.nrhs for k, r in enumerate(reqs) if k not in rejected)
+    print(json.dumps({
+        "metric": "serving: p50 / p99 request latency and DOF x load vectors per second (mixed, R1 < 1e-8)",
+        "value": float(np.percentile(lat, 50)), "unit": "ms (p50 latency)", "n_gpus": 1, "steps": steps,
+        "warmup": 0, "ms_per_step": makespan * 1e3 / max(steps, 1), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 relax / f64 residual+master+norms", "data": "synthetic",
+        "config": {"workload": f"serving_{len(reqs)}", "requests": len(reqs), "arrival_rate_per_s": 200.0,
+                   "sides": "log-uniform [64, 2048], width capped at 1152", "nrhs": "1-16",
+                   "ea": "lognormal(0,0.3)", "sets": [64, 64], "tol": TOL, "hbm_budget_bytes": budget},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "makespan_s": makespan, "dof_x_rhs": dofrhs,
+        "dof_per_s": dofrhs / makespan, "peak_bytes_in_use": peak_bytes,
+        "statuses_ok": int(sum(1 for s in status if s == capi.HMS_OK)), "rejected": len(rejected)}))
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -442,6 +562,10 @@ def main():
     try:
         if args.ncu_case:
             run_ncu_case(args)
+        elif args.batched:
+            run_batched(args)
+        elif args.serve:
+            run_serve(args)
         elif args.impl == "reference":
             run_reference(args, rank, world)
         else:

@@ -39,6 +39,7 @@ _MASK32 = np.uint64(0xFFFFFFFF)
 TAG_LOAD = 0x4C4F4144  # "LOAD"
 TAG_EA = 0x45414541    # "EAEA"
 TAG_BATCH = 0x42415443  # "BATC"
+TAG_SERVE = 0x53525645  # "SRVE"
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):
@@ -198,4 +199,44 @@ def batched_lattices(count: int = 256, seed: int = 7, side_min: int = 32, side_m
     for i in range(count):
         nx, ny = (int(longs[i]), int(shorts[i])) if flip[i] else (int(shorts[i]), int(longs[i]))
         out.append(BatchLattice(nx, ny, int(nrhs[i]), 1000 + i))
+    return out
+
+
+@dataclasses.dataclass(frozen=True)
+class ServeRequest:
+    """One request of the serving workload: arrival time (s), lattice, loads."""
+    arrival: float
+    nx: int
+    ny: int
+    nrhs: int
+    seed: int
+
+    def ea_array(self):
+        return ea_lognormal(self.nx, self.ny, self.seed + 1)
+
+    def load_array(self):
+        return np.stack([loads(self.nx, self.ny, self.seed, r).reshape(-1) for r in range(self.nrhs)])
+
+
+def serving_requests(count: int = 64, seed: int = 5, rate: float = 200.0, side_min: int = 64,
+                     side_max: int = 2048, width_max: int = 1152, nrhs_max: int = 16):
+    """Poisson arrivals (mean rate per second) of lattice solves: request k
+    draws counter (k, 0, 0, TAG_SERVE) under key (seed, 3): the gap to the
+    previous arrival is exponential (word 0), both sides are log-uniform in
+    [side_min, side_max] (words 1, 2), the load-vector count is
+    1 + floor(nrhs_max u) (word 3).  The width (nodes per row) is the smaller
+    side, capped at width_max; request k's loads use seed 2000 + k."""
+    k = np.arange(count, dtype=np.uint64)
+    w0, w1, w2, w3 = philox4x32_10(k.astype(np.uint32), np.zeros(count, np.uint32), np.uint32(0),
+                                   np.uint32(TAG_SERVE), seed & 0xFFFFFFFF, ((seed >> 32) + 3) & 0xFFFFFFFF)
+    gaps = -np.log(uniform01(w0)) / rate
+    t = np.cumsum(gaps) - gaps[0]
+    lo, hi = math.log(side_min), math.log(side_max)
+    a = np.rint(np.exp(lo + (hi - lo) * uniform01(w1))).astype(int)
+    b = np.rint(np.exp(lo + (hi - lo) * uniform01(w2))).astype(int)
+    nrhs = 1 + np.minimum(nrhs_max - 1, np.floor(nrhs_max * uniform01(w3)).astype(int))
+    out = []
+    for i in range(count):
+        nx, ny = min(a[i], b[i], width_max), max(a[i], b[i])
+        out.append(ServeRequest(float(t[i]), int(nx), int(ny), int(nrhs[i]), 2000 + i))
     return out
