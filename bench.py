@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--batched-count", type=int, default=256)
     ap.add_argument("--serve", type=int, default=0, metavar="N",
                     help="serve N requests of the serving workload instead (separate JSON line)")
+    ap.add_argument("--serve-max-active", type=int, default=4,
+                    help="requests running at once (the rest wait in arrival order)")
     return ap.parse_args()
 
 
@@ -334,7 +336,7 @@ def run_serve(args):
     data = [(r.ea_array(), r.load_array()) for r in reqs]  # generated before the clock starts
     budget = 150 << 30
     ctx = capi.hms_context_create(0)
-    srv = capi.hms_server_create(ctx, budget, max_active=256)
+    srv = capi.hms_server_create(ctx, budget, max_active=args.serve_max_active)
     rid_of, arrival, done_t, peak_bytes, steps, rejected = {}, {}, {}, 0, 0, []
     t0 = time.perf_counter()
     nxt = 0
@@ -372,7 +374,8 @@ def run_serve(args):
         "vs_baseline": None, "dtype": "f32 relax / f64 residual+master+norms", "data": "synthetic",
         "config": {"workload": f"serving_{len(reqs)}", "requests": len(reqs), "arrival_rate_per_s": 200.0,
                    "sides": "log-uniform [64, 2048], width capped at 1152", "nrhs": "1-16",
-                   "ea": "lognormal(0,0.3)", "sets": [64, 64], "tol": TOL, "hbm_budget_bytes": budget},
+                   "ea": "lognormal(0,0.3)", "sets": [64, 64], "tol": TOL, "hbm_budget_bytes": budget,
+                   "max_active_requests": args.serve_max_active},
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "makespan_s": makespan, "dof_x_rhs": dofrhs,
         "dof_per_s": dofrhs / makespan, "peak_bytes_in_use": peak_bytes,

@@ -112,6 +112,13 @@ const char* hms_last_error(hms_context* ctx);
 hms_status hms_problem_create(hms_context* ctx, const hms_lattice_desc* d,
                               const hms_options* o, hms_problem** out);
 void hms_problem_destroy(hms_problem* pr);
+/* A problem that shares src's read-only setup -- lattice description, set
+ * factors, constant part of K_aa -- and has its own iteration state, so that
+ * it can solve other load vectors at the same time as src (e.g. in one
+ * hms_solve_batch call).  The shared buffers are freed with the last of src
+ * and its clones; hms_problem_device_bytes of a clone counts its own buffers
+ * only.  Results equal those of src on the same loads. */
+hms_status hms_problem_clone(hms_problem* src, hms_problem** out);
 /* Bytes of device memory the problem holds. */
 size_t hms_problem_device_bytes(const hms_problem* pr);
 /* Milliseconds the setup kernels took (CUDA events). */
@@ -248,10 +255,14 @@ size_t hms_problem_estimate_bytes(hms_context* c, const hms_lattice_desc* d, con
  * max_active run at once); every hms_server_step advances all admitted
  * requests together by one CUDA-graph round (options.batch updates), each on
  * its own stream, so requests that arrive while others run join them at the
- * next step (continuous batching).  A request solves its load vectors one
- * after another exactly as hms_solve would; its problem is destroyed, and its
- * memory returned to the budget, when the last one is done.  A server is not
- * thread-safe; other work on the same context must not run during a step. */
+ * next step (continuous batching).  A request runs one problem instance per
+ * load vector (the problem and nrhs - 1 clones sharing its set factors,
+ * see hms_problem_clone), so its load vectors are solved at the same time,
+ * each exactly as hms_solve would; the instances are destroyed, and the
+ * memory returned to the budget, when the last load vector is done.  A
+ * request is admitted with shared + nrhs x instance + setup-scratch bytes.
+ * A server is not thread-safe; other work on the same context must not run
+ * while requests are active. */
 typedef struct hms_server hms_server;
 hms_status hms_server_create(hms_context* c, uint64_t hbm_budget_bytes, int32_t max_active,
                              hms_server** out);
@@ -262,10 +273,13 @@ void hms_server_destroy(hms_server* s);
  * whole budget HMS_ERR_OOM. */
 hms_status hms_server_submit(hms_server* s, const hms_lattice_desc* d, const hms_options* o,
                              int32_t nrhs, const double* loads, int64_t* id);
-/* One scheduling round: admit what fits, advance every admitted request,
- * retire the finished ones.  done_ids [cap] receives the ids finished in
- * this round (*n_done of them; only the first cap are written); n_active,
- * n_queued, bytes_in_use (nullable) the state after the round. */
+/* One scheduling pass, asynchronous: admit what fits; for every instance
+ * whose previous round has ended, take its finished load vector out or queue
+ * its next round (instances run at their own pace); retire the requests whose
+ * load vectors are all done.  Blocks only when no instance could move, until
+ * the oldest queued round ends.  done_ids [cap] receives the ids finished in
+ * this pass (*n_done of them; only the first cap are written); n_active,
+ * n_queued, bytes_in_use (nullable) the state after the pass. */
 hms_status hms_server_step(hms_server* s, int64_t* done_ids, int32_t cap, int32_t* n_done,
                            int32_t* n_active, int32_t* n_queued, uint64_t* bytes_in_use);
 /* Results of a finished request, then forgotten: u_out [nrhs][2*nx*ny] (host,

@@ -97,6 +97,7 @@ def lib():
                                                _P, ctypes.POINTER(ctypes.c_int64)]),
         "hms_server_step": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, _P]),
         "hms_server_take": (ctypes.c_int32, [_P, ctypes.c_int64, _P, _P]),
+        "hms_problem_clone": (ctypes.c_int32, [_P, ctypes.POINTER(_P)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -113,7 +114,7 @@ def exported_symbols():
             "hms_problem_setup_ms", "hms_solve", "hms_kernel_times", "hms_residual",
             "hms_update_residual", "hms_relax", "hms_coarse_matrix", "hms_coarse_solve",
             "hms_residual_noalloc", "hms_solve_batch", "hms_problem_estimate_bytes", "hms_server_create",
-            "hms_server_destroy", "hms_server_submit", "hms_server_step", "hms_server_take"]
+            "hms_server_destroy", "hms_server_submit", "hms_server_step", "hms_server_take", "hms_problem_clone"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -202,6 +203,12 @@ def hms_problem_create(ctx, nx, ny, set_sx, set_sy, **kw):
     d, o, keep = _desc_opts(nx, ny, set_sx, set_sy, **kw)
     h = _P()
     _check(ctx, lib().hms_problem_create(ctx, ctypes.byref(d), ctypes.byref(o), ctypes.byref(h)))
+    return h
+
+
+def hms_problem_clone(ctx, pr):
+    h = _P()
+    _check(ctx, lib().hms_problem_clone(pr, ctypes.byref(h)))
     return h
 
 

@@ -22,8 +22,17 @@ struct hms_context {
   std::string err;
 };
 
+// Buffers that stay read-only after setup (lattice description, set
+// factors, constant part of K_aa), shared by a problem and its clones and
+// freed with the last of them.
+struct SharedSetup {
+  int refs = 1;
+  std::vector<void*> allocs;
+};
+
 struct hms_problem {
   hms_context* ctx = nullptr;
+  SharedSetup* shared = nullptr;
   LatView lv{};
   int precision = HMS_FP64, nsolve = 4, batch = 16, profile = 0, max_iter = 0;
   bool coarse_fp64 = false;  // factor of the upper-level system in FP64 (else FP32 + FP64 refinement)
@@ -98,6 +107,20 @@ cudaError_t palloc(hms_problem* pr, T** ptr, size_t count) {
   cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 16);
   if (e != cudaSuccess) return e;
   pr->allocs.push_back(p);
+  pr->bytes += bytes;
+  *ptr = (T*)p;
+  return cudaSuccess;
+}
+
+// allocation of a shared (read-only after setup) buffer; counted in the
+// owner's bytes
+template <typename T>
+cudaError_t salloc(hms_problem* pr, T** ptr, size_t count) {
+  void* p = nullptr;
+  const size_t bytes = count * sizeof(T);
+  cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  pr->shared->allocs.push_back(p);
   pr->bytes += bytes;
   *ptr = (T*)p;
   return cudaSuccess;
@@ -322,11 +345,138 @@ void hms_problem_destroy(hms_problem* pr) {
   if (pr->graph) cudaGraphExecDestroy(pr->graph);
   for (void* p : pr->allocs) cudaFree(p);
   if (pr->ctl_host) cudaFreeHost(pr->ctl_host);
+  if (pr->shared && --pr->shared->refs == 0) {
+    for (void* p : pr->shared->allocs) cudaFree(p);
+    delete pr->shared;
+  }
   delete pr;
+}
+
+static cudaError_t alloc_instance(hms_problem* pr);
+
+hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
+  if (!src || !out) return HMS_ERR_ARG;
+  *out = nullptr;
+  hms_context* c = src->ctx;
+  CKC(c, cudaSetDevice(c->device));
+  hms_problem* pr = new hms_problem();
+  pr->ctx = c;
+  pr->shared = src->shared;
+  ++src->shared->refs;
+  pr->lv = src->lv;
+  pr->precision = src->precision;
+  pr->nsolve = src->nsolve;
+  pr->batch = src->batch;
+  pr->profile = src->profile;
+  pr->max_iter = src->max_iter;
+  pr->coarse_fp64 = src->coarse_fp64;
+  pr->tol = src->tol;
+  pr->n_c = src->n_c;
+  pr->bw = src->bw;
+  pr->big_stages = src->big_stages;
+  pr->kbar = src->kbar;
+  pr->fix = src->fix;
+  pr->rep = src->rep;
+  pr->set_off = src->set_off;
+  pr->f64 = src->f64;
+  pr->f32 = src->f32;
+  pr->slots_base = src->slots_base;
+  cudaError_t e = alloc_instance(pr);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    const hms_status st = fail(c, e == cudaErrorMemoryAllocation ? HMS_ERR_OOM : HMS_ERR_CUDA,
+                               std::string("hms_problem_clone: ") + cudaGetErrorString(e));
+    hms_problem_destroy(pr);
+    return st;
+  }
+  if (!pr->profile) {
+    const hms_status st = build_graph(pr);
+    if (st != HMS_OK) {
+      hms_problem_destroy(pr);
+      return st;
+    }
+  }
+  *out = pr;
+  return HMS_OK;
 }
 
 size_t hms_problem_device_bytes(const hms_problem* pr) { return pr ? pr->bytes : 0; }
 double hms_problem_setup_ms(const hms_problem* pr) { return pr ? (double)pr->setup_ms : 0.0; }
+
+// The per-instance buffers of a problem whose configuration (lv, n_c, bw,
+// precision, coarse choice, max_iter) is set: iteration state, upper-level
+// system and control block.
+static cudaError_t alloc_instance(hms_problem* pr) {
+#define CKI(x)                        \
+  do {                                \
+    cudaError_t e_ = (x);             \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+  const LatView& lv = pr->lv;
+  cudaStream_t s = pr->ctx->stream;
+  const size_t nn = (size_t)lv.nx * lv.ny;
+  CKI(palloc(pr, &pr->u[0], nn));
+  CKI(palloc(pr, &pr->u[1], nn));
+  CKI(palloc(pr, &pr->p, nn));
+  CKI(palloc(pr, &pr->r, nn));
+  if (fp32(pr)) {
+    float2* dl;
+    CKI(palloc(pr, &dl, nn));
+    pr->delta = dl;
+    CKI(cudaMemsetAsync(dl, 0, nn * sizeof(float2), s));
+  } else {
+    double2* dl;
+    CKI(palloc(pr, &dl, nn));
+    pr->delta = dl;
+    CKI(cudaMemsetAsync(dl, 0, nn * sizeof(double2), s));
+  }
+  {
+    const size_t ybytes = (size_t)lv.M * relax_y_stride(lv) * (fp32(pr) ? sizeof(float) : sizeof(double));
+    unsigned char* ys;
+    CKI(palloc(pr, &ys, ybytes));
+    pr->yscratch = ys;
+  }
+  const int n_c = pr->n_c, bw = pr->bw;
+  const size_t nband = (size_t)n_c * (bw + 1);
+  CKI(palloc(pr, &pr->a, n_c));
+  CKI(palloc(pr, &pr->P, n_c));
+  CKI(palloc(pr, &pr->slots_it, (size_t)lv.M * NSLOTS * SLOT_SIZE));
+  CKI(palloc(pr, &pr->band, nband));
+  CKI(palloc(pr, &pr->sband, 2 * nband));
+  CKI(palloc(pr, &pr->scale, n_c));
+  CKI(palloc(pr, &pr->b, n_c));
+  CKI(palloc(pr, &pr->x, n_c));
+  CKI(palloc(pr, &pr->res, n_c));
+  {
+    // 8 bytes per entry (FP64 factor) plus the tail read by rounded-up bulk copies
+    double *lc, *lr, *di;
+    CKI(palloc(pr, &lc, nband + 16));
+    CKI(palloc(pr, &lr, nband + 16));
+    CKI(palloc(pr, &di, (size_t)coarse_dinv_size(n_c)));
+    pr->lcol = lc;
+    pr->lrow = lr;
+    pr->dinv = di;
+  }
+  if (pr->big_stages > 0) CKI(palloc(pr, &pr->xinv, coarse_xinv_elems(n_c, pr->bw)));
+  CKI(palloc(pr, &pr->dropped, n_c));
+  CKI(palloc(pr, &pr->cstat, 4));
+  CKI(cudaMemsetAsync(pr->cstat, 0, 4 * sizeof(unsigned long long), s));
+  const size_t npart = (size_t)std::max(update_residual_blocks(lv), 1024) * 3;
+  CKI(palloc(pr, &pr->partials, npart));
+  CKI(palloc(pr, &pr->ticket, 1));
+  CKI(cudaMemsetAsync(pr->ticket, 0, sizeof(unsigned), s));
+  CKI(palloc(pr, &pr->ctl, 1));
+  CKI(palloc(pr, &pr->err, 1));
+  CKI(cudaMemsetAsync(pr->err, 0, sizeof(int), s));
+  CKI(palloc(pr, &pr->norms, 4));
+  pr->hist_cap = pr->max_iter + 1;
+  CKI(palloc(pr, &pr->hist, 3 * (size_t)pr->hist_cap));
+  CKI(cudaMallocHost(&pr->ctl_host, sizeof(IterCtl)));
+  CKI(cudaMemsetAsync(pr->a, 0, n_c * sizeof(double), s));
+
+#undef CKI
+  return cudaSuccess;
+}
 
 hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const hms_options* o,
                               hms_problem** out) {
@@ -346,6 +496,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
 
   hms_problem* pr = new hms_problem();
   pr->ctx = c;
+  pr->shared = new SharedSetup();
   LatView& lv = pr->lv;
   lv.nx = d->nx;
   lv.ny = d->ny;
@@ -401,7 +552,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     } else if (d->fix_bottom_edge) {
       for (int i = 0; i < lv.nx; ++i) fm[i] = 3;
     }
-    CKP(palloc(pr, &pr->fix, nn));
+    CKP(salloc(pr, &pr->fix, nn));
     CKP(cudaMemcpy(pr->fix, fm.data(), nn, cudaMemcpyHostToDevice));
     lv.fix = pr->fix;
   }
@@ -426,7 +577,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
           }
         }
       }
-    CKP(palloc(pr, &pr->kbar, 3 * nn));
+    CKP(salloc(pr, &pr->kbar, 3 * nn));
     CKP(cudaMemcpy(pr->kbar, kb.data(), 3 * nn * sizeof(double), cudaMemcpyHostToDevice));
     lv.kbar = pr->kbar;
   }
@@ -444,80 +595,23 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
       rp[I].y = lv.L * SQ3_2 * ((double)j0 + 0.5 * (double)(h - 1));
       so[I + 1] = so[I] + set_factor_stride(2 * w, h);
     }
-    CKP(palloc(pr, &pr->rep, lv.M));
+    CKP(salloc(pr, &pr->rep, lv.M));
     CKP(cudaMemcpy(pr->rep, rp.data(), lv.M * sizeof(double2), cudaMemcpyHostToDevice));
     lv.rep = pr->rep;
-    CKP(palloc(pr, &pr->set_off, lv.M + 1));
+    CKP(salloc(pr, &pr->set_off, lv.M + 1));
     CKP(cudaMemcpy(pr->set_off, so.data(), (lv.M + 1) * sizeof(long long), cudaMemcpyHostToDevice));
     const size_t fsz = (size_t)so[lv.M];
     if (fp32(pr)) {
-      CKP(palloc(pr, &pr->f32, fsz));
+      CKP(salloc(pr, &pr->f32, fsz));
       CKP(cudaMemsetAsync(pr->f32, 0, fsz * sizeof(float), s));
     } else {
-      CKP(palloc(pr, &pr->f64, fsz));
+      CKP(salloc(pr, &pr->f64, fsz));
       CKP(cudaMemsetAsync(pr->f64, 0, fsz * sizeof(double), s));
     }
   }
   // ---- iteration buffers ----
-  CKP(palloc(pr, &pr->u[0], nn));
-  CKP(palloc(pr, &pr->u[1], nn));
-  CKP(palloc(pr, &pr->p, nn));
-  CKP(palloc(pr, &pr->r, nn));
-  if (fp32(pr)) {
-    float2* dl;
-    CKP(palloc(pr, &dl, nn));
-    pr->delta = dl;
-    CKP(cudaMemsetAsync(dl, 0, nn * sizeof(float2), s));
-  } else {
-    double2* dl;
-    CKP(palloc(pr, &dl, nn));
-    pr->delta = dl;
-    CKP(cudaMemsetAsync(dl, 0, nn * sizeof(double2), s));
-  }
-  {
-    const size_t ybytes = (size_t)lv.M * relax_y_stride(lv) * (fp32(pr) ? sizeof(float) : sizeof(double));
-    unsigned char* ys;
-    CKP(palloc(pr, &ys, ybytes));
-    pr->yscratch = ys;
-  }
-  const int n_c = pr->n_c, bw = pr->bw;
-  const size_t nband = (size_t)n_c * (bw + 1);
-  CKP(palloc(pr, &pr->a, n_c));
-  CKP(palloc(pr, &pr->P, n_c));
-  CKP(palloc(pr, &pr->slots_base, (size_t)lv.M * NSLOTS * SLOT_SIZE));
-  CKP(palloc(pr, &pr->slots_it, (size_t)lv.M * NSLOTS * SLOT_SIZE));
-  CKP(palloc(pr, &pr->band, nband));
-  CKP(palloc(pr, &pr->sband, 2 * nband));
-  CKP(palloc(pr, &pr->scale, n_c));
-  CKP(palloc(pr, &pr->b, n_c));
-  CKP(palloc(pr, &pr->x, n_c));
-  CKP(palloc(pr, &pr->res, n_c));
-  {
-    // 8 bytes per entry (FP64 factor) plus the tail read by rounded-up bulk copies
-    double *lc, *lr, *di;
-    CKP(palloc(pr, &lc, nband + 16));
-    CKP(palloc(pr, &lr, nband + 16));
-    CKP(palloc(pr, &di, (size_t)coarse_dinv_size(n_c)));
-    pr->lcol = lc;
-    pr->lrow = lr;
-    pr->dinv = di;
-  }
-  if (pr->big_stages > 0) CKP(palloc(pr, &pr->xinv, coarse_xinv_elems(n_c, pr->bw)));
-  CKP(palloc(pr, &pr->dropped, n_c));
-  CKP(palloc(pr, &pr->cstat, 4));
-  CKP(cudaMemsetAsync(pr->cstat, 0, 4 * sizeof(unsigned long long), s));
-  const size_t npart = (size_t)std::max(update_residual_blocks(lv), 1024) * 3;
-  CKP(palloc(pr, &pr->partials, npart));
-  CKP(palloc(pr, &pr->ticket, 1));
-  CKP(cudaMemsetAsync(pr->ticket, 0, sizeof(unsigned), s));
-  CKP(palloc(pr, &pr->ctl, 1));
-  CKP(palloc(pr, &pr->err, 1));
-  CKP(cudaMemsetAsync(pr->err, 0, sizeof(int), s));
-  CKP(palloc(pr, &pr->norms, 4));
-  pr->hist_cap = pr->max_iter + 1;
-  CKP(palloc(pr, &pr->hist, 3 * (size_t)pr->hist_cap));
-  CKP(cudaMallocHost(&pr->ctl_host, sizeof(IterCtl)));
-  CKP(cudaMemsetAsync(pr->a, 0, n_c * sizeof(double), s));
+  CKP(salloc(pr, &pr->slots_base, (size_t)lv.M * NSLOTS * SLOT_SIZE));
+  CKP(alloc_instance(pr));
 
   // ---- setup kernels: local factors (K2f) and the constant part of K_aa ----
   cudaEvent_t e0, e1;
@@ -923,12 +1017,15 @@ hms_status hms_residual_noalloc(hms_problem* pr, const double* p, const double* 
   return HMS_OK;
 }
 
-// Device bytes hms_problem_create would allocate for (d, o), following its
-// allocations one by one (plus the set-factor scratch it holds during setup);
-// 0 if the problem would be rejected.
-size_t hms_problem_estimate_bytes(hms_context* c, const hms_lattice_desc* d, const hms_options* o) {
-  if (!c || !d || !o || d->nx < 2 || d->ny < 2 || d->set_sx < 1 || d->set_sx > MAX_SX || d->set_sy < 1) return 0;
-  if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return 0;
+namespace {
+// Device bytes of a problem for (d, o), following hms_problem_create's
+// allocations one by one: the shared setup buffers, one instance's buffers
+// and the scratch held while the set factors are computed.  False if the
+// problem would be rejected.
+bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options* o, size_t* shared, size_t* inst,
+                    size_t* scratch) {
+  if (!c || !d || !o || d->nx < 2 || d->ny < 2 || d->set_sx < 1 || d->set_sx > MAX_SX || d->set_sy < 1) return false;
+  if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return false;
   hms_problem pr;
   LatView& lv = pr.lv;
   lv.nx = d->nx;
@@ -945,7 +1042,7 @@ size_t hms_problem_estimate_bytes(hms_context* c, const hms_lattice_desc* d, con
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   if (relax_smem_bytes(lv, fp32(&pr)) + 2048 > (size_t)maxsm || !choose_coarse(&pr, o, maxsm) ||
       coarse_slots_smem(lv) > (size_t)maxsm)
-    return 0;
+    return false;
   const size_t nn = (size_t)lv.nx * lv.ny, M = (size_t)lv.M, n_c = (size_t)pr.n_c;
   const size_t esz = fp32(&pr) ? 4 : 8;
   const size_t nband = n_c * (pr.bw + 1);
@@ -954,23 +1051,35 @@ size_t hms_problem_estimate_bytes(hms_context* c, const hms_lattice_desc* d, con
     const int w = std::min(lv.sx, lv.nx - (I % lv.Mx) * lv.sx), h = std::min(lv.sy, lv.ny - (I / lv.Mx) * lv.sy);
     fac += (size_t)set_factor_stride(2 * w, h);
   }
-  size_t b = nn + (d->ea ? 3 * nn * 8 : 0) + M * 16 + (M + 1) * 8 + fac * esz;
-  b += 4 * nn * 16 + nn * 2 * esz + M * (size_t)relax_y_stride(lv) * esz;
-  b += 2 * n_c * 8 + 2 * M * NSLOTS * SLOT_SIZE * 8 + 3 * nband * 8 + 4 * n_c * 8;
+  *shared = nn + (d->ea ? 3 * nn * 8 : 0) + M * 16 + (M + 1) * 8 + fac * esz + M * NSLOTS * SLOT_SIZE * 8;
+  size_t b = 4 * nn * 16 + nn * 2 * esz + M * (size_t)relax_y_stride(lv) * esz;
+  b += 2 * n_c * 8 + M * NSLOTS * SLOT_SIZE * 8 + 3 * nband * 8 + 4 * n_c * 8;
   b += 2 * (nband + 16) * 8 + (size_t)coarse_dinv_size(pr.n_c) * 8;
   if (pr.big_stages > 0) b += coarse_xinv_elems(pr.n_c, pr.bw) * 4;
   b += n_c * 4 + 32 + (size_t)std::max(update_residual_blocks(lv), 1024) * 3 * 8 + 4 + sizeof(IterCtl) + 4 + 32;
   b += 3 * ((size_t)o->max_iter + 1) * 8;
-  b += (size_t)std::max(1, std::min(lv.M, c->nsm)) * b_size(MAX_NB) * 8;  // setup scratch
-  return b;
+  *inst = b;
+  *scratch = (size_t)std::max(1, std::min(lv.M, c->nsm)) * b_size(MAX_NB) * 8;
+  return true;
+}
+}  // namespace
+
+// Device bytes hms_problem_create would allocate for (d, o) (plus the
+// set-factor scratch it holds during setup); 0 if it would be rejected.
+size_t hms_problem_estimate_bytes(hms_context* c, const hms_lattice_desc* d, const hms_options* o) {
+  size_t sh = 0, in = 0, sc = 0;
+  if (!estimate_parts(c, d, o, &sh, &in, &sc)) return 0;
+  return sh + in + sc;
 }
 
 // ---------------------------------------------------------------- serving
 // Requests (a lattice, options and nrhs load vectors) are queued, admitted in
 // arrival order while their estimated bytes fit the budget, and advanced
-// together one CUDA-graph round per step, each on a stream of the context's
-// pool; a request's problem is destroyed (its memory returned) as soon as its
-// last load vector is done.
+// together one CUDA-graph round per step.  A request runs one problem
+// instance per load vector (the problem and nrhs - 1 clones sharing its set
+// factors), each on a stream of the context's pool, so its load vectors are
+// solved at the same time; its instances are destroyed, and the memory
+// returned, when the last load vector is done.
 struct hms_server {
   struct Req {
     int64_t id = 0;
@@ -982,9 +1091,13 @@ struct hms_server {
     double* loads = nullptr;  // pinned, [nrhs][2 nn]
     double* u = nullptr;      // pinned, [nrhs][2 nn]
     std::vector<int32_t> iters;
-    hms_problem* pr = nullptr;
+    std::vector<hms_problem*> inst;  // instance q solves load vector q
+    std::vector<int> launches;
+    std::vector<char> running;       // load vector q not finished yet
+    std::vector<char> inflight;      // a round of instance q is queued (ev[q] marks its end)
+    std::vector<cudaEvent_t> ev;
     uint64_t bytes = 0;
-    int q = 0, launches = 0, slot = 0;
+    int slot = 0;
     bool ran = false;  // admitted and solved (u holds results)
     hms_status status = HMS_OK;
   };
@@ -998,19 +1111,29 @@ struct hms_server {
 };
 
 namespace {
+void free_instances(hms_server::Req* r) {
+  for (size_t k = r->inst.size(); k-- > 0;)
+    if (r->inst[k]) hms_problem_destroy(r->inst[k]);
+  r->inst.clear();
+  for (cudaEvent_t e : r->ev)
+    if (e) cudaEventDestroy(e);
+  r->ev.clear();
+}
 void free_req(hms_server::Req* r) {
-  if (r->pr) hms_problem_destroy(r->pr);
+  free_instances(r);
   if (r->loads) cudaFreeHost(r->loads);
   if (r->u) cudaFreeHost(r->u);
   delete r;
 }
-cudaStream_t req_stream(hms_server* s, const hms_server::Req* r) { return s->ctx->pool[r->slot]; }
-// load vector r->q of a request: in, u = 0, iteration control reset, ||p||
-cudaError_t req_start(hms_server* s, hms_server::Req* r) {
-  hms_problem* pr = r->pr;
-  cudaStream_t st = req_stream(s, r);
+cudaStream_t inst_stream(hms_server* s, const hms_server::Req* r, int q) {
+  return s->ctx->pool[(r->slot + q) % s->ctx->pool.size()];
+}
+// load vector q of a request on instance q: in, u = 0, iteration control reset, ||p||
+cudaError_t inst_start(hms_server* s, hms_server::Req* r, int q) {
+  hms_problem* pr = r->inst[q];
+  cudaStream_t st = inst_stream(s, r, q);
   const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
-  cudaError_t e = cudaMemcpyAsync(pr->p, r->loads + 2 * nn * r->q, vb, cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(pr->p, r->loads + 2 * nn * q, vb, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(pr->u[0], 0, vb, st);
   IterCtl hc{};
   hc.max_iter = pr->max_iter;
@@ -1018,7 +1141,8 @@ cudaError_t req_start(hms_server* s, hms_server::Req* r) {
   *pr->ctl_host = hc;
   if (e == cudaSuccess) e = cudaMemcpyAsync(pr->ctl, pr->ctl_host, sizeof(IterCtl), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = launch_load_norms(st, pr->lv, pr->p, pr->partials, pr->ticket, pr->ctl);
-  r->launches = 0;
+  r->launches[q] = 0;
+  r->running[q] = 1;
   return e;
 }
 }  // namespace
@@ -1054,8 +1178,10 @@ hms_status hms_server_submit(hms_server* s, const hms_lattice_desc* d, const hms
   if (!s || !d || !o || nrhs < 1 || !loads || !id) return HMS_ERR_ARG;
   hms_context* c = s->ctx;
   if (o->profile) return fail(c, HMS_ERR_ARG, "hms_server_submit: profile mode is not served");
-  const uint64_t est = hms_problem_estimate_bytes(c, d, o);
-  if (est == 0) return fail(c, HMS_ERR_ARG, "hms_server_submit: the problem would be rejected (lattice / sets / options)");
+  size_t sh = 0, in = 0, sc = 0;
+  if (!estimate_parts(c, d, o, &sh, &in, &sc))
+    return fail(c, HMS_ERR_ARG, "hms_server_submit: the problem would be rejected (lattice / sets / options)");
+  const uint64_t est = sh + (uint64_t)nrhs * in + sc;
   if (est > s->budget)
     return fail(c, HMS_ERR_OOM, "hms_server_submit: the request needs " + std::to_string(est) +
                                     " bytes, more than the whole budget of " + std::to_string(s->budget));
@@ -1074,6 +1200,9 @@ hms_status hms_server_submit(hms_server* s, const hms_lattice_desc* d, const hms
   r->nrhs = nrhs;
   r->bytes = est;
   r->iters.assign(nrhs, 0);
+  r->launches.assign(nrhs, 0);
+  r->running.assign(nrhs, 0);
+  r->inflight.assign(nrhs, 0);
   const size_t vb = (size_t)nrhs * 2 * nn * sizeof(double);
   if (cudaMallocHost(&r->loads, vb) != cudaSuccess || cudaMallocHost(&r->u, vb) != cudaSuccess) {
     cudaGetLastError();
@@ -1097,60 +1226,107 @@ hms_status hms_server_step(hms_server* s, int64_t* done_ids, int32_t cap, int32_
     if (*n_done < cap) done_ids[*n_done] = id;
     ++*n_done;
   };
+  auto retire = [&](hms_server::Req* r, hms_status st) {
+    r->status = st;
+    free_instances(r);
+    s->done[r->id] = r;
+    report(r->id);
+  };
   // 1. admission in arrival order while the estimate fits the budget
   while (!s->queue.empty() && (int)s->active.size() < s->max_active) {
     hms_server::Req* r = s->queue.front();
     if (s->used + r->bytes > s->budget) break;
     s->queue.pop_front();
-    hms_status st = hms_problem_create(c, &r->d, &r->o, &r->pr);
+    hms_problem* base = nullptr;
+    hms_status st = hms_problem_create(c, &r->d, &r->o, &base);
     if (st != HMS_OK) {
-      r->pr = nullptr;
-      r->status = st;
-      s->done[r->id] = r;
-      report(r->id);
+      retire(r, st);
       continue;
     }
-    r->bytes = std::max<uint64_t>(r->bytes, r->pr->bytes);
+    r->inst.push_back(base);
+    for (int q = 1; q < r->nrhs && st == HMS_OK; ++q) {
+      hms_problem* cl = nullptr;
+      st = hms_problem_clone(base, &cl);
+      if (st == HMS_OK) r->inst.push_back(cl);
+    }
+    if (st != HMS_OK) {
+      retire(r, st);
+      continue;
+    }
     s->used += r->bytes;
     r->ran = true;
-    r->slot = s->next_slot++ % (int)c->pool.size();
-    CKC(c, req_start(s, r));
+    r->slot = s->next_slot;
+    s->next_slot = (s->next_slot + r->nrhs) % (int)c->pool.size();
+    r->ev.assign(r->nrhs, nullptr);
+    for (int q = 0; q < r->nrhs; ++q) {
+      CKC(c, cudaEventCreateWithFlags(&r->ev[q], cudaEventDisableTiming));
+      CKC(c, inst_start(s, r, q));
+    }
     s->active.push_back(r);
   }
-  // 2. one round of every active request
-  for (auto* r : s->active) {
-    CKC(c, cudaGraphLaunch(r->pr->graph, req_stream(s, r)));
-    CKC(c, cudaMemcpyAsync(r->pr->ctl_host, r->pr->ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, req_stream(s, r)));
-    ++r->launches;
+  // 2. every instance whose last round has ended: finished load vector out,
+  // else the next round; instances run at their own pace, the host waits
+  // only when none can move
+  bool moved = false;
+  for (int pass = 0; pass < 2 && !moved; ++pass) {
+    for (auto* r : s->active)
+      for (int q = 0; q < r->nrhs; ++q) {
+        if (!r->running[q]) continue;
+        hms_problem* pr = r->inst[q];
+        cudaStream_t st = inst_stream(s, r, q);
+        if (r->inflight[q]) {
+          const cudaError_t qe = cudaEventQuery(r->ev[q]);
+          if (qe == cudaErrorNotReady) continue;
+          CKC(c, qe);
+          r->inflight[q] = 0;
+          const IterCtl fin = *pr->ctl_host;
+          if (fin.done || r->launches[q] >= pr->max_iter / pr->batch + 3) {
+            const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+            CKC(c, cudaMemcpyAsync(r->u + 2 * nn * q, pr->u[fin.t & 1], vb, cudaMemcpyDeviceToHost, st));
+            r->iters[q] = fin.t > 0 ? fin.t - 1 : 0;
+            if (fin.status == 3 && r->status == HMS_OK) r->status = HMS_ERR_NONFINITE;
+            else if (fin.status != 1 && r->status == HMS_OK) r->status = HMS_ERR_NO_CONVERGENCE;
+            r->running[q] = 0;
+            moved = true;
+            continue;
+          }
+        }
+        CKC(c, cudaGraphLaunch(pr->graph, st));
+        CKC(c, cudaMemcpyAsync(pr->ctl_host, pr->ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
+        CKC(c, cudaEventRecord(r->ev[q], st));
+        r->inflight[q] = 1;
+        ++r->launches[q];
+        moved = true;
+      }
+    if (!moved) {
+      // nothing could move: wait for the oldest round still queued
+      for (auto* r : s->active) {
+        for (int q = 0; q < r->nrhs && !moved; ++q)
+          if (r->inflight[q]) {
+            CKC(c, cudaEventSynchronize(r->ev[q]));
+            moved = true;
+          }
+        if (moved) break;
+      }
+      moved = false;
+    }
   }
-  for (auto& st : c->pool) CKC(c, cudaStreamSynchronize(st));
-  // 3. finished load vectors: result out, next one in, or retire the request
+  // 3. retire the requests whose load vectors are all done
   std::vector<hms_server::Req*> keep;
   for (auto* r : s->active) {
-    hms_problem* pr = r->pr;
-    const IterCtl fin = *pr->ctl_host;
-    if (!fin.done && r->launches < pr->max_iter / pr->batch + 3) {
+    bool all = true;
+    for (int q = 0; q < r->nrhs; ++q) all = all && !r->running[q];
+    if (!all) {
       keep.push_back(r);
       continue;
     }
-    const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
-    CKC(c, cudaMemcpyAsync(r->u + 2 * nn * r->q, pr->u[fin.t & 1], vb, cudaMemcpyDeviceToHost, req_stream(s, r)));
-    r->iters[r->q] = fin.t > 0 ? fin.t - 1 : 0;
-    if (fin.status == 3 && r->status == HMS_OK) r->status = HMS_ERR_NONFINITE;
-    else if (fin.status != 1 && r->status == HMS_OK) r->status = HMS_ERR_NO_CONVERGENCE;
-    if (++r->q < r->nrhs) {
-      CKC(c, req_start(s, r));
-      keep.push_back(r);
-      continue;
+    for (int q = 0; q < r->nrhs; ++q) CKC(c, cudaStreamSynchronize(inst_stream(s, r, q)));
+    for (auto* pr : r->inst) {
+      const hms_status de = check_dev_err(pr);
+      if (de != HMS_OK) r->status = de;
     }
-    CKC(c, cudaStreamSynchronize(req_stream(s, r)));
-    const hms_status de = check_dev_err(pr);
-    if (de != HMS_OK) r->status = de;
-    hms_problem_destroy(pr);
-    r->pr = nullptr;
     s->used -= r->bytes;
-    s->done[r->id] = r;
-    report(r->id);
+    retire(r, r->status);
   }
   s->active.swap(keep);
   if (n_active) *n_active = (int32_t)s->active.size();

@@ -102,7 +102,8 @@ def test_budget_admission_and_rejections(hms_ctx):
     for k, r in enumerate(REQS):
         nx, ny, sx, sy, kw, _ = req_args(k, r)
         sizes.append(capi.hms_problem_estimate_bytes(hms_ctx, nx, ny, sx, sy, **kw))
-    budget = max(sizes) + min(sizes) // 2  # at most one large request at a time
+    # a request holds its shared setup plus one instance per load vector (<= 3 here)
+    budget = 3 * max(sizes)
     srv = capi.hms_server_create(hms_ctx, budget, max_active=8)
     try:
         nx, ny, sx, sy, kw, p = req_args(0, REQS[0])
@@ -132,3 +133,29 @@ def test_budget_admission_and_rejections(hms_ctx):
             assert capi.hms_server_take(hms_ctx, srv, rid) == capi.HMS_OK
     finally:
         capi.hms_server_destroy(srv)
+
+
+def test_clone_shares_setup_and_outlives_its_source(hms_ctx):
+    from paper_1208_4093_gb300 import capi
+    nx, ny, sx, sy, kw, p = req_args(0, REQS[0])
+    pr = capi.hms_problem_create(hms_ctx, nx, ny, sx, sy, **kw)
+    cl = capi.hms_problem_clone(hms_ctx, pr)
+    try:
+        assert capi.hms_problem_device_bytes(cl) < capi.hms_problem_device_bytes(pr)
+        a, b = np.empty_like(p), np.empty_like(p)
+        capi.hms_solve(hms_ctx, pr, p, a)
+        capi.hms_solve(hms_ctx, cl, p, b)
+        assert np.array_equal(a, b)
+        # both at once, one load vector each
+        c0, c1 = np.empty_like(p[:1]), np.empty_like(p[1:2])
+        capi.hms_solve_batch(hms_ctx, [pr, cl], [p[:1], p[1:2]], [c0, c1])
+        assert np.array_equal(c0, a[:1]) and np.array_equal(c1, a[1:2])
+        capi.hms_problem_destroy(pr)
+        pr = None
+        d = np.empty_like(p)
+        capi.hms_solve(hms_ctx, cl, p, d)  # the shared factors live on with the clone
+        assert np.array_equal(d, a)
+    finally:
+        if pr is not None:
+            capi.hms_problem_destroy(pr)
+        capi.hms_problem_destroy(cl)
