@@ -270,7 +270,8 @@ def run_ncu_case(args):
 def run_batched(args):
     """256 independent lattices (log-uniform sides 32..512, aspect up to 4,
     1-8 load vectors, 32 x 32-node sets, EA = 1, mixed precision, R1 < 1e-8):
-    hms_solve_batch against the same problems solved one after another."""
+    hms_solve_batch over one instance per load vector (clones share a
+    lattice's set factors) against the lattices solved one after another."""
     import numpy as np
     import torch
     from paper_1208_4093_gb300 import capi
@@ -287,17 +288,31 @@ def run_batched(args):
     nrhs = sum(l.nrhs for l in lats)
     its = torch.zeros(nrhs, dtype=torch.int32, device=dev)
     dofrhs = sum(2 * l.nx * l.ny * l.nrhs for l in lats)
+    # one instance per load vector: the lattice's problem and nrhs - 1 clones sharing its set factors
+    inst, inst_loads, inst_outs, clones = [], [], [], []
+    for pr, l, x, o in zip(prs, lats, loads, outs):
+        for q in range(l.nrhs):
+            if q == 0:
+                h = pr
+            else:
+                h = capi.hms_problem_clone(ctx, pr)
+                clones.append(h)
+            inst.append(h)
+            inst_loads.append(x[q:q + 1])
+            inst_outs.append(o[q:q + 1])
     torch.cuda.synchronize()
     for _ in range(max(args.warmup, 1)):
-        capi.hms_solve_batch(ctx, prs, loads, outs, iters=its)
+        capi.hms_solve_batch(ctx, inst, inst_loads, inst_outs, iters=its)
     torch.cuda.synchronize()
     ms = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        capi.hms_solve_batch(ctx, prs, loads, outs, iters=its)
+        capi.hms_solve_batch(ctx, inst, inst_loads, inst_outs, iters=its)
         torch.cuda.synchronize()
         ms.append((time.perf_counter() - t0) * 1e3)
     ub = [o.cpu().numpy() for o in outs]
+    for h in clones:
+        capi.hms_problem_destroy(h)
     # the same problems one after another (one pass)
     t0 = time.perf_counter()
     for pr, x, o in zip(prs, loads, outs):

@@ -140,10 +140,12 @@ hms_status hms_solve(hms_problem* pr, int32_t nrhs, const double* loads, const d
  * lattices; the paper solves one lattice at a time).  Problem i solves its
  * nrhs[i] load vectors loads[i] ([nrhs[i]][2*nx_i*ny_i]) from u0 = 0 into
  * u_out[i] (same shape), one after another, exactly as hms_solve would; the
- * problems run concurrently: every round launches each active problem's CUDA
- * graph (options.batch updates) on one of up to 64 streams of the context,
- * then the host reads every problem's convergence flag and starts its next
- * load vector where one finished.  iters (nullable) receives the update
+ * problems run concurrently, each on one of up to 64 streams of the context
+ * and at its own pace: whenever a problem's last CUDA-graph round
+ * (options.batch updates) has ended, the host reads its convergence flag and
+ * queues its next round, or takes the load vector out and starts the next
+ * one.  Clones (hms_problem_clone) let one lattice's load vectors run at the
+ * same time.  iters (nullable) receives the update
  * counts, problem by problem and load vector by load vector.  The problems
  * must belong to c, appear once, and not use options.profile.  Returns the
  * first device error, else HMS_ERR_NONFINITE / HMS_ERR_NO_CONVERGENCE if a

@@ -803,40 +803,66 @@ hms_status hms_solve_batch(hms_context* c, int32_t count, hms_problem* const* pr
     active[i] = 1;
     return e;
   };
+  // every problem moves at its own pace: when its last round has ended (its
+  // event), its load vector is taken out or its next round is queued; the host
+  // blocks only when no problem can move
+  std::vector<cudaEvent_t> ev(count, nullptr);
+  std::vector<char> inflight(count, 0);
+  struct EvGuard {
+    std::vector<cudaEvent_t>& e;
+    ~EvGuard() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } guard{ev};
+  int live = 0;
   for (int i = 0; i < count; ++i)
-    if (nrhs[i] > 0) CKC(c, start(i));
-  bool any = true;
-  while (any) {
-    // one graph launch (batch iterations) per active problem, each on its stream
+    if (nrhs[i] > 0) {
+      CKC(c, cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+      CKC(c, start(i));
+      ++live;
+    }
+  while (live > 0) {
+    bool moved = false;
     for (int i = 0; i < count; ++i) {
       if (!active[i]) continue;
       hms_problem* pr = problems[i];
-      CKC(c, cudaGraphLaunch(pr->graph, stream_of(i)));
-      CKC(c, cudaMemcpyAsync(pr->ctl_host, pr->ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, stream_of(i)));
+      cudaStream_t st = stream_of(i);
+      if (inflight[i]) {
+        const cudaError_t qe = cudaEventQuery(ev[i]);
+        if (qe == cudaErrorNotReady) continue;
+        CKC(c, qe);
+        inflight[i] = 0;
+        const IterCtl fin = *pr->ctl_host;
+        if (fin.done || launches[i] >= pr->max_iter / pr->batch + 3) {
+          const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+          CKC(c, cudaMemcpyAsync(u_out[i] + 2 * nn * q[i], pr->u[fin.t & 1], vb, kind_out(mem_kind), st));
+          its[(size_t)(ioff[i] + q[i])] = fin.t > 0 ? fin.t - 1 : 0;
+          if (fin.status == 3) status[i] = 3;
+          else if (fin.status != 1 && status[i] == 1) status[i] = 2;
+          moved = true;
+          if (++q[i] < nrhs[i]) {
+            CKC(c, start(i));
+          } else {
+            active[i] = 0;
+            --live;
+            continue;
+          }
+        }
+      }
+      CKC(c, cudaGraphLaunch(pr->graph, st));
+      CKC(c, cudaMemcpyAsync(pr->ctl_host, pr->ctl, sizeof(IterCtl), cudaMemcpyDeviceToHost, st));
+      CKC(c, cudaEventRecord(ev[i], st));
+      inflight[i] = 1;
       ++launches[i];
+      moved = true;
     }
-    for (int k = 0; k < nstreams; ++k) CKC(c, cudaStreamSynchronize(c->pool[k]));
-    any = false;
-    for (int i = 0; i < count; ++i) {
-      if (!active[i]) continue;
-      hms_problem* pr = problems[i];
-      const IterCtl fin = *pr->ctl_host;
-      if (!fin.done && launches[i] < pr->max_iter / pr->batch + 3) {
-        any = true;
-        continue;
-      }
-      const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
-      CKC(c, cudaMemcpyAsync(u_out[i] + 2 * nn * q[i], pr->u[fin.t & 1], vb, kind_out(mem_kind), stream_of(i)));
-      its[(size_t)(ioff[i] + q[i])] = fin.t > 0 ? fin.t - 1 : 0;
-      if (fin.status == 3) status[i] = 3;
-      else if (fin.status != 1 && status[i] == 1) status[i] = 2;
-      if (++q[i] < nrhs[i]) {
-        CKC(c, start(i));
-        any = true;
-      } else {
-        active[i] = 0;
-      }
-    }
+    if (!moved)
+      for (int i = 0; i < count; ++i)
+        if (inflight[i]) {
+          CKC(c, cudaEventSynchronize(ev[i]));
+          break;
+        }
   }
   for (int k = 0; k < nstreams; ++k) CKC(c, cudaStreamSynchronize(c->pool[k]));
   if (iters && ioff[count] > 0) {
