@@ -131,6 +131,16 @@ def traffic_for(kernel, workload, src):
     return None
 
 
+def max_over_ranks(x, device="cpu"):
+    """The largest of x over all ranks of the default process group (the
+    slowest replica sets the job's time)."""
+    import torch
+    import torch.distributed as dist
+    v = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -524,9 +534,7 @@ def run_ours(args, rank, world, local_rank):
 
     ms_med = statistics.median(ms64)
     if world > 1:
-        t = torch.tensor([max(ms64)], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_med = float(t.item())
+        ms_med = max_over_ranks(max(ms64), dev)
     if rank != 0:
         capi.hms_context_destroy(ctx)
         return
