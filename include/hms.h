@@ -89,9 +89,12 @@ typedef struct {
   int32_t batch;             /* iterations per CUDA-graph launch; 0 = default (16) */
   int32_t profile;           /* 1 = time every kernel with CUDA events */
   int32_t coarse_factor;     /* factor of Eq. 8: 0 = auto (FP64 for one- or two-node-wide
-                                set tiles, else FP32), 1 = FP32 with FP64 refinement,
-                                2 = FP64, 3 = FP32 solved in 16-row steps only (without
-                                the inverted 64 x 64 diagonal blocks used otherwise) */
+                                set tiles, else FP32 with FP64 refinement, factored on one
+                                SM, or on a cluster of 4 SMs when the band is too wide for
+                                one, and solved by 64-row blocks with inverted diagonal
+                                blocks where they fit), 1 = FP32 on a cluster of 4 SMs,
+                                2 = FP64, 3 = FP32 on one SM solved in 16-row steps,
+                                4 = FP32 on one SM */
 } hms_options;
 
 /* Context: one device, one CUDA stream.  device = CUDA ordinal. */

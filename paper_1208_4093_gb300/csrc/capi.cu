@@ -69,6 +69,7 @@ struct hms_problem {
   void* dinv = nullptr;      // inverted 16 x 16 diagonal blocks of L
   float* xinv = nullptr;     // per 64-row block of the FP32 L: inverted diagonal block and band neighbours
   int big_stages = 0;        // pipeline depth of the 64-row block solve, 0 = 16-row solve
+  bool cluster_factor = false;  // FP32 factor on a cluster of 4 CTAs (with the block solve)
   int* dropped = nullptr;
   unsigned long long* cstat = nullptr;  // refinement state of the upper-level solve
   double* partials = nullptr;
@@ -189,8 +190,10 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
                           pr->b, pr->x, pr->dropped, pr->ctl);
   if (e != cudaSuccess) return e;
   mark();
-  e = launch_coarse_factor(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped,
-                           pr->big_stages == 0, pr->ctl);
+  e = pr->cluster_factor
+          ? launch_coarse_factor_cl(s, pr->n_c, pr->bw, pr->lrow, pr->lcol, pr->dinv, pr->dropped, pr->ctl)
+          : launch_coarse_factor(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped,
+                                 pr->big_stages == 0, pr->ctl);
   if (e != cudaSuccess) return e;
   if (pr->big_stages > 0) {
     e = launch_coarse_blockinv(s, pr->n_c, pr->bw, pr->lcol, pr->lrow, pr->xinv, pr->ctl);
@@ -272,11 +275,30 @@ bool choose_coarse(hms_problem* pr, const hms_options* o, int maxsm) {
     return coarse_factor_smem_bytes(pr->n_c, pr->bw, f64) + 1024 <= (size_t)maxsm &&
            coarse_solve_smem_bytes(pr->n_c, pr->bw, f64) + 1024 <= (size_t)maxsm;
   };
+  const int big = coarse_big_stages(pr->n_c, pr->bw, maxsm);
+  const bool cl_fits = big > 0 && coarse_factor_cl_smem_bytes(pr->n_c, pr->bw) + 4096 <= (size_t)maxsm;
   if (o->coarse_factor == 2) pr->coarse_fp64 = true;
-  else if (o->coarse_factor == 1 || o->coarse_factor == 3) pr->coarse_fp64 = false;
+  else if (o->coarse_factor == 1 || o->coarse_factor == 3 || o->coarse_factor == 4) pr->coarse_fp64 = false;
   else pr->coarse_fp64 = degenerate && fits(true);
-  if (!fits(pr->coarse_fp64)) return false;
-  pr->big_stages = (pr->coarse_fp64 || o->coarse_factor == 3) ? 0 : coarse_big_stages(pr->n_c, pr->bw, maxsm);
+  if (pr->coarse_fp64) {
+    if (!fits(true)) return false;
+    pr->big_stages = 0;
+    pr->cluster_factor = false;
+    return true;
+  }
+  // FP32: one SM where the window fits (the block solve unless coarse_factor
+  // = 3), else, or with coarse_factor = 1, a cluster of SMs with the block solve
+  const bool one_fits = fits(false);
+  if (o->coarse_factor == 3) {
+    if (!one_fits) return false;
+    pr->big_stages = 0;
+    pr->cluster_factor = false;
+    return true;
+  }
+  if (o->coarse_factor == 4) pr->cluster_factor = false;
+  else pr->cluster_factor = cl_fits && (o->coarse_factor == 1 || !one_fits);
+  if (!pr->cluster_factor && !one_fits) return false;
+  pr->big_stages = big;
   return true;
 }
 
@@ -317,6 +339,7 @@ hms_status hms_context_create(int32_t device, hms_context** out) {
   if (e == cudaSuccess) e = configure_relax(maxsm);
   if (e == cudaSuccess) e = configure_coarse_assemble(maxsm);
   if (e == cudaSuccess) e = configure_coarse_solve(maxsm);
+  if (e == cudaSuccess) e = configure_coarse_factor_cl(maxsm);
   if (e != cudaSuccess) {
     g_create_err = std::string("context setup: ") + cudaGetErrorString(e);
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -374,6 +397,7 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
   pr->n_c = src->n_c;
   pr->bw = src->bw;
   pr->big_stages = src->big_stages;
+  pr->cluster_factor = src->cluster_factor;
   pr->kbar = src->kbar;
   pr->fix = src->fix;
   pr->rep = src->rep;
@@ -490,7 +514,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return fail(c, HMS_ERR_ARG, "bad precision");
   if (!(o->tol >= 0.0) || o->max_iter < 0) return fail(c, HMS_ERR_ARG, "bad tol / max_iter");
   if (o->coarse_solves < 0 || o->coarse_solves > 8) return fail(c, HMS_ERR_ARG, "coarse_solves must be in 0..8");
-  if (o->coarse_factor < 0 || o->coarse_factor > 3) return fail(c, HMS_ERR_ARG, "coarse_factor must be in 0..3");
+  if (o->coarse_factor < 0 || o->coarse_factor > 4) return fail(c, HMS_ERR_ARG, "coarse_factor must be in 0..4");
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
 
@@ -981,8 +1005,11 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
   CKC(c, cudaMemcpyAsync(pr->P, P, n * sizeof(double), kind_in(mem_kind), s));
   CKC(c, launch_coarse_scale(s, n, bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale, pr->b,
                              pr->x, pr->dropped, nullptr));
-  CKC(c, launch_coarse_factor(s, n, bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped,
-                              pr->big_stages == 0, nullptr));
+  if (pr->cluster_factor)
+    CKC(c, launch_coarse_factor_cl(s, n, bw, pr->lrow, pr->lcol, pr->dinv, pr->dropped, nullptr));
+  else
+    CKC(c, launch_coarse_factor(s, n, bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped,
+                                pr->big_stages == 0, nullptr));
   if (pr->big_stages > 0) CKC(c, launch_coarse_blockinv(s, n, bw, pr->lcol, pr->lrow, pr->xinv, nullptr));
   for (int q = 0; q < pr->nsolve; ++q) {
     if (q > 0)

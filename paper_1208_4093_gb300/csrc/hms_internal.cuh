@@ -184,6 +184,11 @@ cudaError_t configure_setup(int max_smem);
 cudaError_t configure_relax(int max_smem);
 cudaError_t configure_coarse_assemble(int max_smem);
 cudaError_t configure_coarse_solve(int max_smem);
+// coarse_factor_cluster.cu
+size_t coarse_factor_cl_smem_bytes(int n, int bw);
+cudaError_t configure_coarse_factor_cl(int max_smem);
+cudaError_t launch_coarse_factor_cl(cudaStream_t s, int n, int bw, const void* lrow, void* lcol, void* dinv,
+                                    int* dropped, const IterCtl* ctl);
 // small utility kernels (capi.cu)
 cudaError_t launch_mask_u(cudaStream_t s, const LatView& lv, double2* u);
 cudaError_t launch_d2f(cudaStream_t s, const double* in, float* out, size_t n);

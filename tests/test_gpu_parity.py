@@ -183,11 +183,12 @@ def test_coarse_solve_step(problem):
         assert rel(a, ao) < tol
 
 
-@pytest.mark.parametrize("cf", [1, 3], ids=["blocks64", "rows16"])
+@pytest.mark.parametrize("cf", [1, 3, 4], ids=["cluster", "rows16", "onesm_blocks64"])
 @pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[3]], ids=lambda c: c[0])
 def test_coarse_solve_both_substitutions(hms_ctx, case, cf):
-    """The FP32 factor's two substitutions (inverted 64 x 64 diagonal blocks,
-    or 16-row steps) give the oracle's update V a and full solve."""
+    """The FP32 factor on a cluster of SMs or on one SM, and its two
+    substitutions (inverted 64 x 64 diagonal blocks, or 16-row steps), give the
+    oracle's update V a and full solve."""
     from paper_1208_4093_gb300 import capi
     tr, g, p, pr = setup_case(hms_ctx, case, 0, coarse_factor=cf)
     try:
@@ -373,3 +374,23 @@ def test_bad_arguments_rejected(hms_ctx, kw):
         capi.hms_problem_create(hms_ctx, nx, 8, kw.get("sx", 4), kw.get("sy", 4), ea=ea,
                                 precision=kw.get("prec", 0))
     assert ei.value.status == capi.HMS_ERR_ARG
+
+
+def test_wide_set_grid_needs_the_cluster_factor(hms_ctx):
+    """24 sets across give bw = 9 * 26 - 1 = 233: one SM's window cannot hold
+    the band, the factor on a cluster of SMs can, and the solve matches the
+    direct solution."""
+    from paper_1208_4093_gb300 import capi
+    nx, ny, sx, sy = 96, 8, 4, 4
+    with pytest.raises(capi.HmsError) as e:
+        capi.hms_problem_create(hms_ctx, nx, ny, sx, sy, coarse_factor=4)
+    assert e.value.status == capi.HMS_ERR_ARG
+    tr = truss.Truss(nx, ny)
+    p = loads(nx, ny, 21).reshape(-1)
+    pr = capi.hms_problem_create(hms_ctx, nx, ny, sx, sy, precision=capi.HMS_FP64, tol=1e-11, max_iter=20000)
+    try:
+        u = np.empty((1, tr.ndof))
+        capi.hms_solve(hms_ctx, pr, p.reshape(1, -1), u)
+        assert rel(u[0], direct.cholesky_solve(tr, tr.free * p)) < 1e-9
+    finally:
+        capi.hms_problem_destroy(pr)
