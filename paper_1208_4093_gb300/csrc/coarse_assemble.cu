@@ -28,6 +28,7 @@ constexpr int NREG = 15;          // 3 directions x 3 delta modes + 6 delta-delt
 constexpr int NGEN_DELTA = 24;    // (m, l), m in 6..8, l <= m
 constexpr int NGEN_FULL = 45;     // (m, l), l <= m < 9
 constexpr int LSTRIDE = 36;       // s[18], (EA/L) s[18]
+constexpr int RED_CHUNK = NW;     // accumulators per shared-memory reduction pass
 
 __device__ inline double warp_sum(double v) {
 #pragma unroll
@@ -95,7 +96,6 @@ template <typename DT, bool FULL, typename AT>
 __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __restrict__ delta,
                                                      double* __restrict__ slots, const IterCtl* ctl) {
   extern __shared__ double lists[];
-  __shared__ double sred[NW * (NREG + NGEN_FULL)];
   if (ctl && *(volatile const int*)&ctl->done) return;
   constexpr int NGEN = FULL ? NGEN_FULL : NGEN_DELTA;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -237,25 +237,31 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
     }
   }
 
-  // deterministic block sums of the per-thread accumulators
+  // deterministic block sums of the per-thread accumulators, eight at a time
+  // through shared memory: warp a adds accumulator a of the CTA's threads
+  // lane by lane in thread order, then a shuffle tree finishes it
   constexpr int NACC = NREG + NGEN;
-  double acc[NACC];
+  double* red = lists + (size_t)LC.total * LSTRIDE;  // RED_CHUNK x NT
+  double* tot = red + RED_CHUNK * NT;                 // NACC CTA totals
 #pragma unroll
-  for (int k = 0; k < NREG; ++k) acc[k] = (double)reg[k];
+  for (int c0 = 0; c0 < NACC; c0 += RED_CHUNK) {
 #pragma unroll
-  for (int k = 0; k < NGEN; ++k) acc[NREG + k] = (double)gen[k];
+    for (int q = 0; q < RED_CHUNK; ++q) {
+      const int k = c0 + q;
+      if (k < NREG) red[q * NT + tid] = (double)reg[k];
+      else if (k < NACC) red[q * NT + tid] = (double)gen[k - NREG];
+    }
+    __syncthreads();
+    if (c0 + warp < NACC) {
+      const double* q = red + warp * NT + lane;
+      double v = q[0];
 #pragma unroll
-  for (int k = 0; k < NACC; ++k) {
-    const double v = warp_sum(acc[k]);
-    if (lane == 0) sred[warp * NACC + k] = v;
+      for (int ww = 1; ww < NW; ++ww) v += q[32 * ww];
+      v = warp_sum(v);
+      if (lane == 0) tot[c0 + warp] = v;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  double tot = 0.0;
-  if (tid < NACC)
-    for (int ww = 0; ww < NW; ++ww) tot += sred[ww * NACC + tid];
-  __syncthreads();
-  if (tid < NACC) sred[tid] = tot;  // sred[k] = CTA total of accumulator k
-  __syncthreads();
 
   // SELF slot (upper-left 9 x 9)
   if (tid < 81) {
@@ -264,10 +270,10 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
     double v = 0.0;
     bool have = false;
     if (FULL) {
-      v = sred[NREG + mm * (mm + 1) / 2 + ll];
+      v = tot[NREG + mm * (mm + 1) / 2 + ll];
       have = true;
     } else if (mm >= 6) {
-      v = sred[NREG + gen_idx(mm, ll, false)];
+      v = tot[NREG + gen_idx(mm, ll, false)];
       const double L = lv.L;
       // constants s_2..s_5 of a regular bar of direction d: -L e_x^2, -L e_x e_y, -L e_y e_x, -L e_y^2
       if (ll >= 2 && ll <= 5) {
@@ -275,11 +281,11 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
         for (int d = 0; d < 3; ++d) {
           const double ex = (d == 0) ? 1.0 : (d == 1 ? 0.5 : -0.5), ey = (d == 0) ? 0.0 : SQ3_2;
           const double c = (ll == 2) ? -L * ex * ex : (ll == 5 ? -L * ey * ey : -L * ex * ey);
-          v = fma(c, sred[3 * d + (mm - 6)], v);
+          v = fma(c, tot[3 * d + (mm - 6)], v);
         }
       } else if (ll >= 6) {
         const int qi = (mm == 6) ? 9 : (mm == 7 ? (ll == 6 ? 10 : 12) : (ll == 6 ? 11 : (ll == 7 ? 13 : 14)));
-        v += sred[qi];
+        v += tot[qi];
       }
       have = true;
     }
@@ -488,7 +494,8 @@ int coarse_bw(const LatView& lv) {
 size_t coarse_slots_smem(const LatView& lv) {
   const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
   const int h = lv.sy < lv.ny ? lv.sy : lv.ny;
-  return (size_t)list_caps(w, h).total * LSTRIDE * sizeof(double);
+  // interface lists, then the reduction buffer and the CTA totals
+  return ((size_t)list_caps(w, h).total * LSTRIDE + RED_CHUNK * NT + NREG + NGEN_FULL) * sizeof(double);
 }
 
 cudaError_t launch_coarse_slots(cudaStream_t s, const LatView& lv, const void* delta, bool delta_fp32,

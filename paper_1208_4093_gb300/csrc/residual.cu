@@ -24,20 +24,30 @@ __device__ inline double warp_sum(double v) {
   return v;
 }
 
-// Deterministic block sum of N values per thread; result valid in warp 0.
+// Deterministic block sum of N values per thread over the NT threads of a
+// CTA; the sums land in v of thread 0.  The values go through shared memory:
+// warp k adds value k of the eight warps lane by lane in warp order, then a
+// shuffle tree finishes it.  That is 12 FP64 adds in N warps instead of a
+// shuffle tree in every warp.  sred holds N * (NT + 1) doubles.
 template <int N>
 __device__ inline void block_sum(double (&v)[N], double* sred) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  static_assert(N <= NT / 32, "one warp per value");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-  for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < N; ++k) sred[warp * N + k] = v[k];
+  for (int k = 0; k < N; ++k) sred[k * NT + tid] = v[k];
   __syncthreads();
-  if (warp == 0) {
+  if (warp < N) {
+    const double* c = sred + warp * NT + lane;
+    double t = c[0];
 #pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = warp_sum(lane < nw ? sred[lane * N + k] : 0.0);
+    for (int w = 1; w < NT / 32; ++w) t += c[32 * w];
+    t = warp_sum(t);
+    if (lane == 0) sred[N * NT + warp] = t;
   }
+  __syncthreads();
+  if (tid == 0)
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = sred[N * NT + k];
 }
 
 template <typename DT>
@@ -76,7 +86,7 @@ __global__ void __launch_bounds__(NT) k_update_residual(
     double2* __restrict__ r, double* __restrict__ partials, unsigned* ticket, double* norms_out,
     IterCtl* ctl, double* hist, int hist_cap) {
   __shared__ double2 U[TY + 2][TX + 2];
-  __shared__ double sred[32 * 3];
+  __shared__ double sred[3 * (NT + 1)];
   __shared__ bool last;
   int t = 0;
   if (ctl) {
@@ -188,10 +198,10 @@ __global__ void __launch_bounds__(NT) k_update_residual(
 }
 
 // Masks the loads on constrained DOFs and computes ||p||_1, ||p||_2 into ctl.
-__global__ void __launch_bounds__(256) k_load_norms(LatView lv, double2* __restrict__ p,
+__global__ void __launch_bounds__(NT) k_load_norms(LatView lv, double2* __restrict__ p,
                                                     double* __restrict__ partials, unsigned* ticket,
                                                     IterCtl* ctl) {
-  __shared__ double sred[32 * 2];
+  __shared__ double sred[2 * (NT + 1)];
   __shared__ bool last;
   const size_t nn = (size_t)lv.nx * lv.ny;
   double s[2] = {0.0, 0.0};
@@ -256,7 +266,7 @@ cudaError_t launch_load_norms(cudaStream_t s, const LatView& lv, double2* p, dou
   const size_t nn = (size_t)lv.nx * lv.ny;
   int grid = (int)((nn + 255) / 256);
   if (grid > 1024) grid = 1024;
-  k_load_norms<<<grid, 256, 0, s>>>(lv, p, partials, ticket, ctl);
+  k_load_norms<<<grid, NT, 0, s>>>(lv, p, partials, ticket, ctl);
   return cudaGetLastError();
 }
 
