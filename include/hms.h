@@ -89,12 +89,15 @@ typedef struct {
   int32_t batch;             /* iterations per CUDA-graph launch; 0 = default (16) */
   int32_t profile;           /* 1 = time every kernel with CUDA events */
   int32_t coarse_factor;     /* factor of Eq. 8: 0 = auto (FP64 for one- or two-node-wide
-                                set tiles, else FP32 with FP64 refinement, factored on one
-                                SM, or on a cluster of 4 SMs when the band is too wide for
-                                one, and solved by 64-row blocks with inverted diagonal
+                                set tiles, else FP32 with FP64 refinement: two-sided on two
+                                SMs when the system is at least three bands long, else on
+                                one SM, or on a cluster of 4 SMs when the band is too wide
+                                for one; solved by 64-row blocks with inverted diagonal
                                 blocks where they fit), 1 = FP32 on a cluster of 4 SMs,
                                 2 = FP64, 3 = FP32 on one SM solved in 16-row steps,
-                                4 = FP32 on one SM */
+                                4 = FP32 on one SM, 5 = FP32 two-sided: top and bottom
+                                segments eliminated at once on two SMs, then the
+                                separator between them */
 } hms_options;
 
 /* Context: one device, one CUDA stream.  device = CUDA ordinal. */

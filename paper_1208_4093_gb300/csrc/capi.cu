@@ -70,6 +70,8 @@ struct hms_problem {
   float* xinv = nullptr;     // per 64-row block of the FP32 L: inverted diagonal block and band neighbours
   int big_stages = 0;        // pipeline depth of the 64-row block solve, 0 = 16-row solve
   bool cluster_factor = false;  // FP32 factor on a cluster of 4 CTAs (with the block solve)
+  bool two_sided = false;       // FP32 two-sided factor and solve on two SMs
+  TwoSided ts;
   int* dropped = nullptr;
   unsigned long long* cstat = nullptr;  // refinement state of the upper-level solve
   double* partials = nullptr;
@@ -164,6 +166,30 @@ cudaMemcpyKind kind_out(int mem_kind) {
 size_t nnodes(const hms_problem* pr) { return (size_t)pr->lv.nx * pr->lv.ny; }
 bool fp32(const hms_problem* pr) { return pr->precision == HMS_MIXED; }
 
+// The factor of Eq. 8 (after the scaled band is built) and its per-block
+// matrices, by the configured variant.
+cudaError_t launch_factor_stage(hms_problem* pr, cudaStream_t s, const IterCtl* ctl) {
+  if (pr->two_sided) return launch_coarse_factor_2s(s, pr->n_c, pr->bw, pr->ts, pr->sband, pr->dropped, ctl);
+  cudaError_t e = pr->cluster_factor
+                      ? launch_coarse_factor_cl(s, pr->n_c, pr->bw, pr->lrow, pr->lcol, pr->dinv, pr->dropped, ctl)
+                      : launch_coarse_factor(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv,
+                                             pr->dropped, pr->big_stages == 0, ctl);
+  if (e != cudaSuccess || pr->big_stages == 0) return e;
+  return launch_coarse_blockinv(s, pr->n_c, pr->bw, pr->lcol, pr->lrow, pr->xinv, ctl);
+}
+// Solve q (0: of b, then of the refinement residual) with the factor.
+cudaError_t launch_solve_stage(hms_problem* pr, cudaStream_t s, int q, const IterCtl* ctl) {
+  const double* rhs = q == 0 ? pr->b : pr->res;
+  if (pr->two_sided)
+    return launch_coarse_solve_2s(s, pr->n_c, pr->ts, rhs, pr->x, pr->scale, pr->a, pr->dropped, pr->cstat, q == 0,
+                                  ctl, pr->err);
+  if (pr->big_stages > 0)
+    return launch_coarse_solve_big(s, pr->big_stages, pr->n_c, pr->bw, pr->lcol, pr->lrow, pr->xinv, pr->dropped,
+                                   rhs, pr->x, pr->scale, pr->a, pr->cstat, q == 0, ctl, pr->err);
+  return launch_coarse_solve(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped, rhs,
+                             pr->x, pr->scale, pr->a, pr->cstat, q == 0, ctl, pr->err);
+}
+
 // Launches of one iteration (the body of Fig. 3's loop); k = position in a batch.
 cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t* ev) {
   const LatView& lv = pr->lv;
@@ -190,15 +216,8 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
                           pr->b, pr->x, pr->dropped, pr->ctl);
   if (e != cudaSuccess) return e;
   mark();
-  e = pr->cluster_factor
-          ? launch_coarse_factor_cl(s, pr->n_c, pr->bw, pr->lrow, pr->lcol, pr->dinv, pr->dropped, pr->ctl)
-          : launch_coarse_factor(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped,
-                                 pr->big_stages == 0, pr->ctl);
+  e = launch_factor_stage(pr, s, pr->ctl);
   if (e != cudaSuccess) return e;
-  if (pr->big_stages > 0) {
-    e = launch_coarse_blockinv(s, pr->n_c, pr->bw, pr->lcol, pr->lrow, pr->xinv, pr->ctl);
-    if (e != cudaSuccess) return e;
-  }
   mark();
   for (int q = 0; q < pr->nsolve; ++q) {
     if (q > 0) {
@@ -207,14 +226,7 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
       if (e != cudaSuccess) return e;
       mark();
     }
-    if (pr->big_stages > 0)
-      e = launch_coarse_solve_big(s, pr->big_stages, pr->n_c, pr->bw, pr->lcol, pr->lrow, pr->xinv, pr->dropped,
-                                  q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, pr->ctl,
-                                  pr->err);
-    else
-      e = launch_coarse_solve(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped,
-                              q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, pr->ctl,
-                              pr->err);
+    e = launch_solve_stage(pr, s, q, pr->ctl);
     if (e != cudaSuccess) return e;
     mark();
   }
@@ -263,8 +275,9 @@ hms_status check_dev_err(hms_problem* pr) {
 // Upper-level factor precision and substitution of a problem whose lv, n_c,
 // bw and precision are set: FP64 for degenerate set shapes (one- or
 // two-node-wide tiles give ill-conditioned upper-level systems), else FP32
-// with FP64 refinement, solved by 64-row blocks with inverted diagonal blocks
-// when that fits in shared memory (coarse_factor = 3 keeps the 16-row
+// with FP64 refinement: two-sided on two SMs for long systems (auto or
+// coarse_factor = 5), else solved by 64-row blocks with inverted diagonal
+// blocks when that fits in shared memory (coarse_factor = 3 keeps the 16-row
 // solve).  False if the band does not fit one CTA's shared memory.
 bool choose_coarse(hms_problem* pr, const hms_options* o, int maxsm) {
   const LatView& lv = pr->lv;
@@ -278,7 +291,7 @@ bool choose_coarse(hms_problem* pr, const hms_options* o, int maxsm) {
   const int big = coarse_big_stages(pr->n_c, pr->bw, maxsm);
   const bool cl_fits = big > 0 && coarse_factor_cl_smem_bytes(pr->n_c, pr->bw) + 4096 <= (size_t)maxsm;
   if (o->coarse_factor == 2) pr->coarse_fp64 = true;
-  else if (o->coarse_factor == 1 || o->coarse_factor == 3 || o->coarse_factor == 4) pr->coarse_fp64 = false;
+  else if (o->coarse_factor == 1 || o->coarse_factor >= 3) pr->coarse_fp64 = false;
   else pr->coarse_fp64 = degenerate && fits(true);
   if (pr->coarse_fp64) {
     if (!fits(true)) return false;
@@ -294,6 +307,30 @@ bool choose_coarse(hms_problem* pr, const hms_options* o, int maxsm) {
     pr->big_stages = 0;
     pr->cluster_factor = false;
     return true;
+  }
+  // two-sided: where the split exists and both CTAs' shared memory fits; by
+  // default only for systems at least three bands long (a shorter chain
+  // gains less than the separator's extra factor costs)
+  pr->two_sided = false;
+  if (o->coarse_factor == 0 || o->coarse_factor == 5) {
+    int m0, m1, s;
+    if (coarse_two_sided_split(pr->n_c, pr->bw, &m0, &m1, &s) &&
+        (o->coarse_factor == 5 || pr->n_c >= 3 * (pr->bw + 1)) &&
+        coarse_two_sided_factor_smem(m0, m1, s) + 1024 <= (size_t)maxsm) {
+      const int st = coarse_two_sided_stages(m0, m1, s, maxsm);
+      if (st > 0) {
+        pr->two_sided = true;
+        pr->cluster_factor = false;
+        pr->big_stages = 0;
+        pr->ts = TwoSided();
+        pr->ts.m[0] = m0;
+        pr->ts.m[1] = m1;
+        pr->ts.s = s;
+        pr->ts.stages = st;
+        return true;
+      }
+    }
+    if (o->coarse_factor == 5) return false;
   }
   if (o->coarse_factor == 4) pr->cluster_factor = false;
   else pr->cluster_factor = cl_fits && (o->coarse_factor == 1 || !one_fits);
@@ -398,6 +435,12 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
   pr->bw = src->bw;
   pr->big_stages = src->big_stages;
   pr->cluster_factor = src->cluster_factor;
+  pr->two_sided = src->two_sided;
+  pr->ts = TwoSided();
+  pr->ts.m[0] = src->ts.m[0];
+  pr->ts.m[1] = src->ts.m[1];
+  pr->ts.s = src->ts.s;
+  pr->ts.stages = src->ts.stages;
   pr->kbar = src->kbar;
   pr->fix = src->fix;
   pr->rep = src->rep;
@@ -482,6 +525,18 @@ static cudaError_t alloc_instance(hms_problem* pr) {
     pr->dinv = di;
   }
   if (pr->big_stages > 0) CKI(palloc(pr, &pr->xinv, coarse_xinv_elems(n_c, pr->bw)));
+  if (pr->two_sided) {
+    for (int k = 0; k < 2; ++k) {
+      const TwoSidedSizes z = coarse_two_sided_sizes(pr->ts.m[k], pr->ts.s);
+      CKI(palloc(pr, &pr->ts.lin[k], z.lin));
+      CKI(palloc(pr, &pr->ts.lcol[k], z.lcol));
+      CKI(palloc(pr, &pr->ts.dinv[k], z.dinv));
+      CKI(palloc(pr, &pr->ts.dropped[k], z.dropped));
+      CKI(palloc(pr, &pr->ts.delta[k], z.delta));
+      CKI(palloc(pr, &pr->ts.srow[k], z.srow));
+      CKI(palloc(pr, &pr->ts.xinv[k], z.xinv));
+    }
+  }
   CKI(palloc(pr, &pr->dropped, n_c));
   CKI(palloc(pr, &pr->cstat, 4));
   CKI(cudaMemsetAsync(pr->cstat, 0, 4 * sizeof(unsigned long long), s));
@@ -514,7 +569,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return fail(c, HMS_ERR_ARG, "bad precision");
   if (!(o->tol >= 0.0) || o->max_iter < 0) return fail(c, HMS_ERR_ARG, "bad tol / max_iter");
   if (o->coarse_solves < 0 || o->coarse_solves > 8) return fail(c, HMS_ERR_ARG, "coarse_solves must be in 0..8");
-  if (o->coarse_factor < 0 || o->coarse_factor > 4) return fail(c, HMS_ERR_ARG, "coarse_factor must be in 0..4");
+  if (o->coarse_factor < 0 || o->coarse_factor > 5) return fail(c, HMS_ERR_ARG, "coarse_factor must be in 0..5");
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
 
@@ -1005,23 +1060,11 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
   CKC(c, cudaMemcpyAsync(pr->P, P, n * sizeof(double), kind_in(mem_kind), s));
   CKC(c, launch_coarse_scale(s, n, bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale, pr->b,
                              pr->x, pr->dropped, nullptr));
-  if (pr->cluster_factor)
-    CKC(c, launch_coarse_factor_cl(s, n, bw, pr->lrow, pr->lcol, pr->dinv, pr->dropped, nullptr));
-  else
-    CKC(c, launch_coarse_factor(s, n, bw, pr->coarse_fp64, pr->lrow, pr->lcol, pr->dinv, pr->dropped,
-                                pr->big_stages == 0, nullptr));
-  if (pr->big_stages > 0) CKC(c, launch_coarse_blockinv(s, n, bw, pr->lcol, pr->lrow, pr->xinv, nullptr));
+  CKC(c, launch_factor_stage(pr, s, nullptr));
   for (int q = 0; q < pr->nsolve; ++q) {
     if (q > 0)
       CKC(c, launch_coarse_residual(s, n, bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, pr->cstat, nullptr));
-    if (pr->big_stages > 0)
-      CKC(c, launch_coarse_solve_big(s, pr->big_stages, n, bw, pr->lcol, pr->lrow, pr->xinv, pr->dropped,
-                                     q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, nullptr,
-                                     pr->err));
-    else
-      CKC(c, launch_coarse_solve(s, n, bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped,
-                                 q == 0 ? pr->b : pr->res, pr->x, pr->scale, pr->a, pr->cstat, q == 0, nullptr,
-                                 pr->err));
+    CKC(c, launch_solve_stage(pr, s, q, nullptr));
   }
   CKC(c, cudaMemcpyAsync(a, pr->a, n * sizeof(double), kind_out(mem_kind), s));
   if (dropped) CKC(c, cudaMemcpyAsync(dropped, pr->dropped, n * sizeof(int32_t), kind_out(mem_kind), s));
@@ -1109,6 +1152,11 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
   b += 2 * n_c * 8 + M * NSLOTS * SLOT_SIZE * 8 + 3 * nband * 8 + 4 * n_c * 8;
   b += 2 * (nband + 16) * 8 + (size_t)coarse_dinv_size(pr.n_c) * 8;
   if (pr.big_stages > 0) b += coarse_xinv_elems(pr.n_c, pr.bw) * 4;
+  if (pr.two_sided)
+    for (int k = 0; k < 2; ++k) {
+      const TwoSidedSizes z = coarse_two_sided_sizes(pr.ts.m[k], pr.ts.s);
+      b += (z.lin + z.lcol + z.dinv + z.dropped + z.delta + z.srow + z.xinv) * 4;
+    }
   b += n_c * 4 + 32 + (size_t)std::max(update_residual_blocks(lv), 1024) * 3 * 8 + 4 + sizeof(IterCtl) + 4 + 32;
   b += 3 * ((size_t)o->max_iter + 1) * 8;
   *inst = b;

@@ -31,6 +31,8 @@
 //                    block), and each solve then takes n/64 block steps of a
 //                    dense 64 x 64 product and a one-thread-per-row update.
 //   k_coarse_residual many CTAs, FP64: res = b - A x over the band.
+#include <cooperative_groups.h>
+
 #include "coarse_common.cuh"
 #include "hms_internal.cuh"
 #include "ptx.cuh"
@@ -39,6 +41,7 @@ namespace hms {
 namespace {
 
 using namespace coarse;
+namespace cg = cooperative_groups;
 constexpr int FTF = 512;   // threads of the factor CTA
 constexpr int FTS = 32 * NB;  // threads of the solve CTA (one warp per row of a block)
 
@@ -83,11 +86,17 @@ __host__ __device__ inline int factor_tile_pairs(int bw) {
 // lrow: input = scaled band in row layout [i][kk] = A[i][i-kk]; output = L in
 // row layout if write_lrow (the 16-row substitution reads it).  lcol: output
 // = L in column layout [c][kk] = L[c+kk][c].
+//
+// Only the first npiv rows are pivots (npiv = n: the whole factor; else a
+// multiple of 4).  Columns [0, npiv) of L are written with all their band
+// rows, and rows [npiv, n) end with the Schur complement of the pivots,
+// A - L L^T.  If schur is set, the part of it the pivots changed is written
+// out as a dense s x s lower triangle: schur[i s + j] = (A - S)[npiv + i][npiv
+// + j] for j <= i < min(bw, s), else 0.
 template <typename T>
-__global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __restrict__ lrow, T* __restrict__ lcol,
-                                                          T* __restrict__ dinv, int* __restrict__ dropped,
-                                                          int write_lrow, const IterCtl* ctl) {
-  if (ctl && *(volatile const int*)&ctl->done) return;
+__device__ __forceinline__ void factor_run(int n, int npiv, int bw, T* __restrict__ lrow, T* __restrict__ lcol,
+                                           T* __restrict__ dinv, int* __restrict__ dropped, int write_lrow,
+                                           T* __restrict__ schur, int s) {
   extern __shared__ __align__(16) unsigned char fsraw[];
   T* fs = reinterpret_cast<T*>(fsraw);
   const FactorLayout<T> LY = factor_layout<T>(bw);
@@ -98,9 +107,12 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
   unsigned short* tpair = reinterpret_cast<unsigned short*>(sdrop + n);
   __shared__ unsigned dropblk[2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nblk = (n + NB - 1) / NB;
+  const int nblk = (npiv + NB - 1) / NB;
   const int npairs_max = factor_tile_pairs(bw);
-  for (int i = tid; i < n; i += FTF) sdrop[i] = dropped[i];
+  // lrow and dropped may have been written earlier in the same kernel (the
+  // two-sided factor's second part): coherent loads (__ldcg), never the
+  // read-only path
+  for (int i = tid; i < n; i += FTF) sdrop[i] = __ldcg(dropped + i);
   for (int q = tid; q < npairs_max; q += FTF) {
     int ti = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
     while (ti * (ti + 1) / 2 > q) --ti;
@@ -112,13 +124,13 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
   // window rows [0, min(n, W))
   for (int q = tid; q < min(n, W) * ldw; q += FTF) {
     const int i = q / ldw, kk = q - (q / ldw) * ldw;
-    if (kk <= i) Aw[(size_t)(i % W) * lda + (i - kk) % lda] = lrow[(size_t)i * ldw + kk];
+    if (kk <= i) Aw[(size_t)(i % W) * lda + (i - kk) % lda] = __ldcg(lrow + (size_t)i * ldw + kk);
   }
   __syncthreads();
   // diagonal block 0
   if (warp == 0) {
     T a[NB];
-    const int nbk = min(NB, n);
+    const int nbk = min(NB, npiv);
 #pragma unroll
     for (int j = 0; j < NB; ++j)
       a[j] = (lane < nbk && j <= lane && lane - j <= bw) ? Aw[(size_t)lane * lda + j] : T(0);
@@ -128,7 +140,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
 
   for (int K = 0; K < nblk; ++K) {
     const int cur = K & 1, nxt = cur ^ 1;
-    const int k0 = K * NB, k1 = min(k0 + NB, n), nbk = k1 - k0;
+    const int k0 = K * NB, k1 = min(k0 + NB, npiv), nbk = k1 - k0;
     const int rend = min(n, k1 + bw), np = rend - k1;
     const T* Ls = fs + LY.ls + cur * NB * (NB + 1);
     const T* Xs = fs + LY.xs + cur * NB * (NB + 1);
@@ -185,11 +197,13 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
       }
     }
     __syncthreads();
-    // (a2) rank-NB update of the next diagonal block, by all threads
-    const int nbk2 = (K + 1 < nblk) ? min(NB, n - k1) : 0;
+    // (a2) rank-NB update of the next diagonal block, by all threads (its
+    // rows past npiv are not pivots but are updated all the same)
+    const int nbu = min(NB, n - k1);
+    const int nbk2 = (K + 1 < nblk) ? min(NB, npiv - k1) : 0;
     for (int q = tid; q < NB * NB; q += FTF) {
       const int l = q / NB, j = q - l * NB;
-      if (l < nbk2 && j <= l && l < np && l - j <= bw) {
+      if (l < nbu && j <= l && l < np && l - j <= bw) {
         T v = T(0);
         for (int c = 0; c < nbk; ++c) v = fma(Pc[c * pstr + l], Pc[c * pstr + j], v);
         Aw[(size_t)slot(k1 + l) * lda + (k1 + j) % lda] -= v;
@@ -224,7 +238,7 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
 #pragma unroll
         for (int u = 0; u < 7; ++u) {
           const int kk = lane + 32 * u;
-          v[u] = (kk < ldw && kk <= i) ? src[kk] : T(0);
+          v[u] = (kk < ldw && kk <= i) ? __ldcg(src + kk) : T(0);
         }
 #pragma unroll
         for (int u = 0; u < 7; ++u) {
@@ -301,7 +315,26 @@ __global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __re
     }
     __syncthreads();
   }
+  if (schur) {
+    // rows [npiv, npiv + bw) are still in the window: slot i mod W
+    for (int q = tid; q < s * s; q += FTF) {
+      const int i = q / s, j = q - (q / s) * s;
+      const int gi = npiv + i, gj = npiv + j;
+      T v = T(0);
+      if (j <= i && i < bw && gi < n)
+        v = __ldcg(lrow + (size_t)gi * ldw + (gi - gj)) - Aw[(size_t)(gi % W) * lda + gj % lda];
+      schur[q] = v;
+    }
+  }
   for (int i = tid; i < n; i += FTF) dropped[i] = sdrop[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FTF, 1) k_coarse_factor(int n, int bw, T* __restrict__ lrow, T* __restrict__ lcol,
+                                                          T* __restrict__ dinv, int* __restrict__ dropped,
+                                                          int write_lrow, const IterCtl* ctl) {
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  factor_run<T>(n, n, bw, lrow, lcol, dinv, dropped, write_lrow, nullptr, 0);
 }
 
 // One solve with the factor, added to the FP64 solution x; writes a = s x.
@@ -490,24 +523,22 @@ __host__ __device__ inline size_t blk_elems(int bw) { return 2 * (size_t)NBB * L
 // The per-block matrices above from the FP32 factor (row and column layouts);
 // rows of X past n are identity rows.  Per block, one CTA of 256 threads
 // inverts the diagonal block and three more copy a third of R_K and U_K each.
-__global__ void __launch_bounds__(256) k_coarse_blockinv(int n, int bw, const float* __restrict__ lcol,
-                                                         const float* __restrict__ lrow, float* __restrict__ xinv,
-                                                         const IterCtl* ctl) {
-  if (ctl && *(volatile const int*)&ctl->done) return;
+// Block [r0, r0 + nr) of an n-row factor: part 0 inverts the diagonal block,
+// parts 1 .. nparts - 1 copy a share of R_K and U_K each.
+__device__ __forceinline__ void blockinv_run(int n, int bw, int r0, int nr, const float* __restrict__ lcol,
+                                             float* __restrict__ X, int part_id, int nparts) {
   __shared__ float Ls[NBB][NBB + 1];
   __shared__ float Xs[NBB][NBB + 1];
   const int tid = threadIdx.x;
-  const int K = blockIdx.x, r0 = K * NBB, nr = min(NBB, n - r0);
   const int ldw = bw + 1;
-  float* X = xinv + (size_t)K * blk_elems(bw);
   float* XT = X + NBB * LDX;
   float* R = XT + NBB * LDX;
   float* U = R + (size_t)bw * LDR;
-  if (blockIdx.y > 0) {
-    // R_K and U_K, a third of their rows per CTA
+  if (part_id > 0) {
+    // R_K and U_K, a share of their rows per CTA
     const int r1 = r0 + nr;
-    const int part = (bw + gridDim.y - 2) / (gridDim.y - 1);
-    const int qa = (blockIdx.y - 1) * part, qb = min(bw, qa + part);
+    const int part = (bw + nparts - 2) / (nparts - 1);
+    const int qa = (part_id - 1) * part, qb = min(bw, qa + part);
 #pragma unroll 4
     for (int idx = qa * LDR + tid; idx < qb * LDR; idx += blockDim.x) {
       const int q = idx / LDR, c = idx % LDR;
@@ -580,7 +611,78 @@ __global__ void __launch_bounds__(256) k_coarse_blockinv(int n, int bw, const fl
   }
 }
 
+__global__ void __launch_bounds__(256) k_coarse_blockinv(int n, int bw, const float* __restrict__ lcol,
+                                                         float* __restrict__ xinv, const IterCtl* ctl) {
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  const int K = blockIdx.x, r0 = K * NBB;
+  blockinv_run(n, bw, r0, min(NBB, n - r0), lcol, xinv + (size_t)K * blk_elems(bw), blockIdx.y, gridDim.y);
+}
+
 __host__ __device__ inline int big_stage_elems(int bw) { return bw * LDR + NBB * LDX; }
+
+// One step of the block substitution on the vectors tv (running right-hand
+// side) and yv (solution) in shared memory, block rows [r0, r1), nr = r1 - r0.
+// (1) 8 threads per row: y_w = sum_c M[w][c] t_c (M is zero outside its triangle)
+__device__ __forceinline__ void bsolve_diag(const float* M, const float* tv, float* yv, const int* sdrop, int r0,
+                                            int nr, int tid) {
+  const int w = tid >> 3, p = tid & 7;
+  const float* mr = M + w * LDX;
+  float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+  for (int k = 0; k < NBB / 8; k += 2) {
+    const int c0 = p + 8 * k, c1 = c0 + 8;
+    const float m0 = mr[c0], m1 = mr[c1];
+    const float t0 = c0 < nr ? tv[r0 + c0] : 0.f;
+    const float t1 = c1 < nr ? tv[r0 + c1] : 0.f;
+    v0 = fmaf(m0, t0, v0);
+    v1 = fmaf(m1, t1, v1);
+  }
+  float v = v0 + v1;
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  if (w < nr && p == 0) yv[r0 + w] = sdrop[r0 + w] ? 0.f : v;
+}
+// (2) the band rows next to the block, t_i -= sum_c B[q][c] y_c with B = R_K
+// (rows i = r1 + q, forward) or U_K (rows i = r0 - bw + q, backward): threads
+// h*256 + q take row q and the columns [32h, 32h + 32) by 16-byte loads (r0 is
+// a multiple of 4; y past the block is finite and meets zero columns of B);
+// the two halves meet in shared memory.
+__device__ __forceinline__ void bsolve_band(const float* Lb, const float* yv, float* tv, float* hpart, bool fwd,
+                                            int r0, int r1, int n, int bw, int tid) {
+  const int qlo = fwd ? 0 : max(0, bw - r0);
+  const int qhi = fwd ? min(bw, n - r1) : bw;
+  const int ioff = fwd ? r1 : r0 - bw;  // i = ioff + q
+  const int h = tid >> 8, q0 = tid & 255;
+  const int cbase = 32 * h;
+  float yb[32];
+#pragma unroll
+  for (int c4 = 0; c4 < 32; c4 += 4) {
+    const float4 y4 = *reinterpret_cast<const float4*>(yv + r0 + cbase + c4);
+    yb[c4] = y4.x, yb[c4 + 1] = y4.y, yb[c4 + 2] = y4.z, yb[c4 + 3] = y4.w;
+  }
+  for (int qb = qlo; qb < qhi; qb += 256) {
+    const int q = qb + q0;
+    const int i = ioff + q;
+    float acc0 = 0.f, acc1 = 0.f;
+    if (q < qhi) {
+      const float* br = Lb + (size_t)q * LDR + cbase;
+#pragma unroll
+      for (int c4 = 0; c4 < 32; c4 += 4) {
+        const float4 l4 = *reinterpret_cast<const float4*>(br + c4);
+        acc0 = fmaf(l4.x, yb[c4], acc0);
+        acc1 = fmaf(l4.y, yb[c4 + 1], acc1);
+        acc0 = fmaf(l4.z, yb[c4 + 2], acc0);
+        acc1 = fmaf(l4.w, yb[c4 + 3], acc1);
+      }
+    }
+    const float part = acc0 + acc1;
+    hpart[h * 256 + q0] = part;
+    __syncthreads();
+    if (h == 0 && q < qhi) tv[i] -= hpart[q0] + hpart[256 + q0];
+    if (qb + 256 < qhi) __syncthreads();
+  }
+}
 
 // Block forward / back substitution with the FP32 factor, NBB rows per step:
 //   forward   y_K = X_K t_K,     t_i -= sum_c R_K[i - r1][c] y_c        (the next bw rows)
@@ -681,65 +783,9 @@ __global__ void __launch_bounds__(FTB) k_coarse_solve_big(int n, int bw, const f
     if (tid == 32 && o + S - 1 < nops) issue(o + S - 1);
     const float* Lb = ss + sbase + (size_t)(o % S) * stage;
     const float* M = Lb + xoff;  // X_K (forward) or X_K^T (backward), rows of LDX
-    // (1) 8 threads per row: y_w = sum_c M[w][c] t_c (M is zero outside its triangle)
-    {
-      const int w = tid >> 3, p = tid & 7;
-      const float* mr = M + w * LDX;
-      float v0 = 0.f, v1 = 0.f;
-#pragma unroll
-      for (int k = 0; k < NBB / 8; k += 2) {
-        const int c0 = p + 8 * k, c1 = c0 + 8;
-        const float m0 = mr[c0], m1 = mr[c1];
-        const float t0 = c0 < nr ? tv[r0 + c0] : 0.f;
-        const float t1 = c1 < nr ? tv[r0 + c1] : 0.f;
-        v0 = fmaf(m0, t0, v0);
-        v1 = fmaf(m1, t1, v1);
-      }
-      float v = v0 + v1;
-      v += __shfl_xor_sync(0xffffffffu, v, 4);
-      v += __shfl_xor_sync(0xffffffffu, v, 2);
-      v += __shfl_xor_sync(0xffffffffu, v, 1);
-      if (w < nr && p == 0) yv[r0 + w] = sdrop[r0 + w] ? 0.f : v;
-    }
+    bsolve_diag(M, tv, yv, sdrop, r0, nr, tid);
     __syncthreads();
-    // (2) the band rows next to the block, t_i -= sum_c B[q][c] y_c with
-    // B = R_K (rows i = r1 + q) or U_K (rows i = r0 - bw + q): threads
-    // h*256 + q take row q and the columns [32h, 32h + 32) by 16-byte loads;
-    // the two halves meet in shared memory.
-    {
-      const int qlo = fwd ? 0 : max(0, bw - r0);
-      const int qhi = fwd ? min(bw, n - r1) : bw;
-      const int ioff = fwd ? r1 : r0 - bw;  // i = ioff + q
-      const int h = tid >> 8, q0 = tid & 255;
-      const int cbase = 32 * h;
-      float yb[32];
-#pragma unroll
-      for (int c4 = 0; c4 < 32; c4 += 4) {
-        const float4 y4 = *reinterpret_cast<const float4*>(yv + r0 + cbase + c4);
-        yb[c4] = y4.x, yb[c4 + 1] = y4.y, yb[c4 + 2] = y4.z, yb[c4 + 3] = y4.w;
-      }
-      for (int qb = qlo; qb < qhi; qb += 256) {
-        const int q = qb + q0;
-        const int i = ioff + q;
-        float acc0 = 0.f, acc1 = 0.f;
-        if (q < qhi) {
-          const float* br = Lb + (size_t)q * LDR + cbase;
-#pragma unroll
-          for (int c4 = 0; c4 < 32; c4 += 4) {
-            const float4 l4 = *reinterpret_cast<const float4*>(br + c4);
-            acc0 = fmaf(l4.x, yb[c4], acc0);
-            acc1 = fmaf(l4.y, yb[c4 + 1], acc1);
-            acc0 = fmaf(l4.z, yb[c4 + 2], acc0);
-            acc1 = fmaf(l4.w, yb[c4 + 3], acc1);
-          }
-        }
-        const float part = acc0 + acc1;
-        hpart[h * 256 + q0] = part;
-        __syncthreads();
-        if (h == 0 && q < qhi) tv[i] -= hpart[q0] + hpart[256 + q0];
-        if (qb + 256 < qhi) __syncthreads();
-      }
-    }
+    bsolve_band(Lb, yv, tv, hpart, fwd, r0, r1, n, bw, tid);
   }
   if (abort_flag) {
     if (tid == 0) {
@@ -752,6 +798,287 @@ __global__ void __launch_bounds__(FTB) k_coarse_solve_big(int n, int bw, const f
     const double xi = sdrop[i] ? 0.0 : x[i] + (double)yv[i];
     x[i] = xi;
     a_out[i] = scale[i] * xi;
+  }
+}
+
+// ---- two-sided factor and solve (FP32): two SMs, a cluster of 2 CTAs ----
+//
+// The n unknowns split as [0, m0) (top), the separator [m0, m0 + s) and
+// [m0 + s, n) (bottom, m1 rows), with s > bw, so top and bottom do not
+// couple.  Side 0 works in the natural order on top + separator, side 1 in
+// reversed order (row i of its frame = row n - 1 - i) on bottom + separator;
+// each side's frame is a band matrix of bws = s - 1 >= bw (a reversed
+// symmetric band matrix is one).  Eliminating a side's segment leaves its
+// Schur contribution in the separator block; with both contributions,
+//   S = A_MM - L_MT L_MT^T - L_MB L_MB^T,
+// each side factors S in its own frame and holds the Cholesky factor of
+// [[A_SS, A_SM], [A_MS, S + L_MS L_MS^T]], which with the other side's
+// segment contribution is the factor of A in the order (T, B, M).  The chain
+// of dependent pivots is max(m0, m1) + s instead of n.
+struct FactorSide {
+  float* lin;     // (m + s) x (bws + 1) row band of the side's frame: [i][kk] = A[i][i - kk]
+  float* lcol;    // L of the side's frame, column layout [c][kk] = L[c + kk][c]
+  float* dinv;    // scratch: inverted 16 x 16 diagonal blocks
+  int* dropped;   // m + s drop flags of the side's frame
+  float* delta;   // s x s, lower: the segment's change of the separator block
+  float* srow;    // s x (bws + 1): S in the side's frame, row band
+  int m;          // rows of the segment
+};
+
+// Both sides' row bands and drop flags from the scaled FP64 band (column layout).
+__global__ void k_side_bands(int n, int bw, int bws, int s, int m0, int m1, const double* __restrict__ sband,
+                             const int* __restrict__ dropped, float* __restrict__ lin0, float* __restrict__ lin1,
+                             int* __restrict__ d0, int* __restrict__ d1, const IterCtl* ctl) {
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  const int ldw = bws + 1, ld = bw + 1;
+  const size_t t0 = (size_t)(m0 + s) * ldw, t1 = (size_t)(m1 + s) * ldw;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < t0 + t1; q += (size_t)gridDim.x * blockDim.x) {
+    const bool side1 = q >= t0;
+    const size_t ql = side1 ? q - t0 : q;
+    const int i = (int)(ql / ldw), kk = (int)(ql % ldw);
+    float v = 0.f;
+    if (!side1) {
+      // A[i][i - kk] = column i - kk, offset kk
+      if (kk <= bw && kk <= i) v = (float)sband[(size_t)(i - kk) * ld + kk];
+      lin0[ql] = v;
+      if (kk == 0) d0[i] = dropped[i];
+    } else {
+      // A'[i][i - kk] = A[n - 1 - i][n - 1 - i + kk] = column n - 1 - i, offset kk
+      const int c = n - 1 - i;
+      if (kk <= bw && c + kk < n) v = (float)sband[(size_t)c * ld + kk];
+      lin1[ql] = v;
+      if (kk == 0) d1[i] = dropped[c];
+    }
+  }
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FTF, 1)
+    k_coarse_factor_2s(int s, int bws, FactorSide f0, FactorSide f1, const IterCtl* ctl) {
+  if (ctl && *(volatile const int*)&ctl->done) return;  // the same for both CTAs
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const FactorSide me = rank ? f1 : f0, ot = rank ? f0 : f1;
+  const int ldw = bws + 1;
+  // the segment; its change of the separator block to me.delta
+  factor_run<float>(me.m + s, me.m, bws, me.lin, me.lcol, me.dinv, me.dropped, 0, me.delta, s);
+  __threadfence();
+  cl.sync();
+  // S in this side's frame; separator row i here is row s - 1 - i of the other frame
+  for (int q = threadIdx.x; q < s * ldw; q += FTF) {
+    const int i = q / ldw, kk = q - (q / ldw) * ldw, j = i - kk;
+    float v = 0.f;
+    if (j >= 0)
+      v = me.lin[(size_t)(me.m + i) * ldw + kk] - __ldcg(me.delta + (size_t)i * s + j) -
+          __ldcg(ot.delta + (size_t)(s - 1 - j) * s + (s - 1 - i));
+    me.srow[q] = v;
+  }
+  __syncthreads();
+  factor_run<float>(s, s, bws, me.srow, me.lcol + (size_t)me.m * ldw, me.dinv + (size_t)((me.m + NB - 1) / NB) * NB * NB,
+                    me.dropped + me.m, 0, nullptr, 0);
+}
+
+// Block partition of a side: 64-row blocks over the segment [0, m) (the last
+// one possibly short), then over the separator [m, m + s).
+__host__ __device__ inline void side_block(int K, int m, int s, int& r0, int& r1) {
+  const int nbT = (m + NBB - 1) / NBB;
+  if (K < nbT) {
+    r0 = K * NBB;
+    r1 = min(r0 + NBB, m);
+  } else {
+    r0 = m + (K - nbT) * NBB;
+    r1 = min(r0 + NBB, m + s);
+  }
+}
+__host__ __device__ inline int side_blocks(int m, int s) { return (m + NBB - 1) / NBB + (s + NBB - 1) / NBB; }
+
+__global__ void __launch_bounds__(256) k_coarse_blockinv_2s(int s, int bws, const float* __restrict__ lcol0,
+                                                            const float* __restrict__ lcol1, float* __restrict__ x0,
+                                                            float* __restrict__ x1, int m0, int m1,
+                                                            const IterCtl* ctl) {
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  const int nb0 = side_blocks(m0, s);
+  const bool side1 = (int)blockIdx.x >= nb0;
+  const int K = side1 ? blockIdx.x - nb0 : blockIdx.x;
+  const int m = side1 ? m1 : m0;
+  int r0, r1;
+  side_block(K, m, s, r0, r1);
+  blockinv_run(m + s, bws, r0, r1 - r0, side1 ? lcol1 : lcol0,
+               (side1 ? x1 : x0) + (size_t)K * blk_elems(bws), blockIdx.y, gridDim.y);
+}
+
+struct SolveSide {
+  const float* xinv;    // per-block matrices of the side's factor
+  const int* dropped;   // drop flags of the side's frame
+  int m;                // rows of the segment
+};
+
+// The block substitution of k_coarse_solve_big on each side's frame.  After
+// the forward steps over its segment, each side's separator rows hold b_M
+// minus its own segment's contribution; the two sides exchange them through
+// distributed shared memory (b_M - both contributions), then go on through
+// the separator and back.  Side 0 writes the top and the separator, side 1
+// the bottom.
+template <int S>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FTB)
+    k_coarse_solve_2s(int n, int s, int bws, SolveSide s0, SolveSide s1, const double* __restrict__ res,
+                      double* __restrict__ x, const double* __restrict__ scale, double* __restrict__ a_out,
+                      int* __restrict__ dropped_out, unsigned long long* cstat, int first, const IterCtl* ctl,
+                      int* err) {
+  if (ctl && *(volatile const int*)&ctl->done) return;  // the same for both CTAs
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const SolveSide sd = rank ? s1 : s0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int skip;
+  if (tid == 0) {
+    if (first) {
+      skip = 0;
+    } else {
+      const double bmax = __longlong_as_double((long long)cstat[0]);
+      const double rmax = __longlong_as_double((long long)cstat[1]);
+      skip = (cstat[2] != 0ull) || !(rmax > 1e-14 * bmax);
+    }
+  }
+  cl.sync();  // both CTAs have read cstat
+  if (skip) {
+    if (rank == 0 && tid == 0) cstat[2] = 1ull;
+    return;
+  }
+  if (rank == 0 && tid == 0) cstat[1] = 0ull;  // the next residual accumulates its max here
+  extern __shared__ __align__(16) unsigned char ssraw[];
+  float* ss = reinterpret_cast<float*>(ssraw);
+  __shared__ uint64_t bars[S];
+  __shared__ int abort_flag;
+  __shared__ double bred[FTB / 32];
+  __shared__ double bm_cta;
+  __shared__ float hpart[512];
+  const int m = sd.m, nside = m + s;
+  const int nbT = (m + NBB - 1) / NBB;
+  const int nblk = side_blocks(m, s);
+  const int nops = 2 * nblk;
+  const int stage = big_stage_elems(bws);
+  const int xoff = stage - NBB * LDX;
+  const int n4 = (nside + 3) / 4 * 4;
+  float* tv = ss;
+  float* yv = ss + n4;
+  const int sbase = 2 * n4 + NBB;
+  int* sdrop = reinterpret_cast<int*>(ss + sbase + (size_t)S * stage);
+  auto orig = [&](int i) { return rank ? n - 1 - i : i; };
+
+  auto issue = [&](int o) {
+    const bool fwd = o < nblk;
+    const int K = fwd ? o : nops - 1 - o;
+    const uint32_t rb = (uint32_t)((size_t)bws * LDR * sizeof(float));
+    const uint32_t xb = NBB * LDX * sizeof(float);
+    uint64_t* bar = &bars[o % S];
+    float* dst = ss + sbase + (size_t)(o % S) * stage;
+    const float* blk = sd.xinv + (size_t)K * blk_elems(bws);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, rb + xb);
+    bulk_g2s(dst, blk + 2 * NBB * LDX + (fwd ? 0 : (size_t)bws * LDR), rb, bar);
+    bulk_g2s(dst + xoff, blk + (fwd ? 0 : NBB * LDX), xb, bar);
+  };
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+    fence_mbar_init();
+  }
+  // the rows this side writes: top and separator (side 0), bottom (side 1)
+  const int nown = rank ? m : nside;
+  double bm = 0.0;
+  for (int i = tid; i < nside; i += FTB) {
+    const int d = sd.dropped[i];
+    const double bi = res[orig(i)];
+    sdrop[i] = d;
+    tv[i] = d ? 0.f : (float)bi;
+    if (first && !d && i < nown) bm = fmax(bm, fabs(bi));
+  }
+  for (int i = tid; i < n4 + NBB; i += FTB) yv[i] = 0.f;
+#pragma unroll
+  for (int k = 16; k > 0; k >>= 1) bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, k));
+  if (lane == 0) bred[warp] = bm;
+  __syncthreads();
+  if (tid == 0) {
+    double v = 0.0;
+    for (int k = 0; k < FTB / 32; ++k) v = fmax(v, bred[k]);
+    bm_cta = v;
+  }
+  if (tid == 0)
+    for (int o = 0; o < S - 1 && o < nops; ++o) issue(o);
+  for (int o = 0; o < nops; ++o) {
+    const bool fwd = o < nblk;
+    const int K = fwd ? o : nops - 1 - o;
+    int r0, r1;
+    side_block(K, m, s, r0, r1);
+    const int nr = r1 - r0;
+    if (o == nbT) {
+      // exchange of the separator rows; both CTAs come here, aborted or not
+      __syncthreads();
+      cl.sync();
+      // the other CTA's layout: tv at 0, its drop flags after its own vectors
+      const int mo = rank ? s0.m : s1.m;
+      const int on4 = (mo + s + 3) / 4 * 4;
+      const float* otv = cl.map_shared_rank(tv, rank ^ 1);
+      const int* osd = reinterpret_cast<const int*>(otv + 2 * on4 + NBB + (size_t)S * stage);
+      float ov[4] = {0.f, 0.f, 0.f, 0.f};
+      bool od[4] = {false, false, false, false};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = tid + u * FTB;
+        if (i < s) {
+          ov[u] = otv[mo + s - 1 - i];
+          od[u] = osd[mo + s - 1 - i] != 0;
+        }
+      }
+      double obm = 0.0;
+      if (tid == 0) obm = *cl.map_shared_rank(&bm_cta, rank ^ 1);
+      cl.sync();  // no reads of the other CTA's shared memory after this
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = tid + u * FTB;
+        // the other side started this row from b (0 if it dropped the row)
+        if (i < s && !sdrop[m + i]) tv[m + i] += ov[u] - (od[u] ? 0.f : (float)res[orig(m + i)]);
+      }
+      if (first && rank == 0 && tid == 0) {
+        cstat[0] = (unsigned long long)__double_as_longlong(fmax(bm_cta, obm));
+        cstat[2] = 0ull;
+      }
+      __syncthreads();
+    }
+    if (abort_flag) {
+      if (o >= nbT) break;
+      continue;
+    }
+    if (o == nblk) {
+      for (int i = tid; i < nside; i += FTB) tv[i] = yv[i];
+      __syncthreads();
+    }
+    if (!mbar_wait_bounded(&bars[o % S], (uint32_t)((o / S) & 1))) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) {
+      if (o >= nbT) break;
+      continue;
+    }
+    if (tid == 32 && o + S - 1 < nops) issue(o + S - 1);
+    const float* Lb = ss + sbase + (size_t)(o % S) * stage;
+    const float* Mx = Lb + xoff;
+    bsolve_diag(Mx, tv, yv, sdrop, r0, nr, tid);
+    __syncthreads();
+    bsolve_band(Lb, yv, tv, hpart, fwd, r0, r1, nside, bws, tid);
+  }
+  if (abort_flag) {
+    if (tid == 0) {
+      for (int b2 = 0; b2 < S; ++b2) mbar_wait_bounded(&bars[b2], 0u), mbar_wait_bounded(&bars[b2], 1u);
+      if (err) atomicOr(err, (int)DEVERR_TIMEOUT);
+    }
+    return;
+  }
+  for (int i = tid; i < nown; i += FTB) {
+    const int g = orig(i);
+    const double xi = sdrop[i] ? 0.0 : x[g] + (double)yv[i];
+    x[g] = xi;
+    a_out[g] = scale[g] * xi;
+    if (first) dropped_out[g] = sdrop[i];
   }
 }
 
@@ -797,6 +1124,9 @@ __global__ void k_coarse_residual(int n, int bw, const double* __restrict__ sban
 
 cudaError_t configure_coarse_solve(int max_smem) {
   cudaError_t e;
+  if ((e = set_max_dynamic_smem(k_coarse_factor_2s, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_coarse_solve_2s<2>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_coarse_solve_2s<3>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_coarse_factor<float>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_coarse_factor<double>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_coarse_solve<float>, max_smem)) != cudaSuccess) return e;
@@ -830,8 +1160,8 @@ int coarse_big_stages(int n, int bw, int max_smem) {
 
 cudaError_t launch_coarse_blockinv(cudaStream_t s, int n, int bw, const void* lcol, const void* lrow, float* xinv,
                                    const IterCtl* ctl) {
-  k_coarse_blockinv<<<dim3((n + NBB - 1) / NBB, 4), 256, 0, s>>>(n, bw, (const float*)lcol, (const float*)lrow, xinv,
-                                                                 ctl);
+  (void)lrow;
+  k_coarse_blockinv<<<dim3((n + NBB - 1) / NBB, 4), 256, 0, s>>>(n, bw, (const float*)lcol, xinv, ctl);
   return cudaGetLastError();
 }
 
@@ -883,6 +1213,69 @@ cudaError_t launch_coarse_residual(cudaStream_t s, int n, int bw, const double* 
   const int threads = 256;
   const int blocks = (int)(((size_t)n * 32 + threads - 1) / threads);
   k_coarse_residual<<<blocks, threads, 0, s>>>(n, bw, sband, sbandR, b, x, dropped, res, cstat, ctl);
+  return cudaGetLastError();
+}
+
+// Split for the two-sided factor: s = bw + 1 .. bw + 4 separator rows, both
+// segments multiples of 4 rows (the factor's 16-byte words) and at least one
+// 64-row block.
+bool coarse_two_sided_split(int n, int bw, int* m0, int* m1, int* s) {
+  const int s0 = bw + 1, rem = n - s0;
+  if (rem < 2 * NBB) return false;
+  const int a = (rem / 2) / 4 * 4, b = (rem - a) / 4 * 4;
+  *m0 = a;
+  *m1 = b;
+  *s = n - a - b;
+  return a >= NBB && b >= NBB && *s <= 7 * 32;  // the window's row loads take ldw <= 224
+}
+TwoSidedSizes coarse_two_sided_sizes(int m, int s) {
+  const int bws = s - 1;
+  TwoSidedSizes z;
+  z.lin = (size_t)(m + s) * (bws + 1) + 16;
+  z.lcol = (size_t)(m + s) * (bws + 1) + 16;
+  z.dinv = (size_t)((m + NB - 1) / NB + (s + NB - 1) / NB) * NB * NB;
+  z.dropped = (size_t)(m + s);
+  z.delta = (size_t)s * s;
+  z.srow = (size_t)s * (bws + 1);
+  z.xinv = (size_t)side_blocks(m, s) * blk_elems(bws);
+  return z;
+}
+size_t coarse_two_sided_factor_smem(int m0, int m1, int s) {
+  return coarse_factor_smem_bytes((m0 > m1 ? m0 : m1) + s, s - 1, false);
+}
+int coarse_two_sided_stages(int m0, int m1, int s, int max_smem) {
+  return coarse_big_stages((m0 > m1 ? m0 : m1) + s, s - 1, max_smem);
+}
+cudaError_t launch_coarse_factor_2s(cudaStream_t st, int n, int bw, const TwoSided& t, const double* sband,
+                                    const int* dropped, const IterCtl* ctl) {
+  const int s = t.s, bws = s - 1;
+  {
+    const size_t total = (size_t)(t.m[0] + t.m[1] + 2 * s) * (bws + 1);
+    const int g = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    k_side_bands<<<g, 256, 0, st>>>(n, bw, bws, s, t.m[0], t.m[1], sband, dropped, t.lin[0], t.lin[1],
+                                    t.dropped[0], t.dropped[1], ctl);
+  }
+  FactorSide f[2];
+  for (int k = 0; k < 2; ++k)
+    f[k] = FactorSide{t.lin[k], t.lcol[k], t.dinv[k], t.dropped[k], t.delta[k], t.srow[k], t.m[k]};
+  k_coarse_factor_2s<<<2, FTF, coarse_two_sided_factor_smem(t.m[0], t.m[1], s), st>>>(s, bws, f[0], f[1], ctl);
+  const int nb = side_blocks(t.m[0], s) + side_blocks(t.m[1], s);
+  k_coarse_blockinv_2s<<<dim3(nb, 4), 256, 0, st>>>(s, bws, t.lcol[0], t.lcol[1], t.xinv[0], t.xinv[1], t.m[0],
+                                                    t.m[1], ctl);
+  return cudaGetLastError();
+}
+cudaError_t launch_coarse_solve_2s(cudaStream_t st, int n, const TwoSided& t, const double* res, double* x,
+                                   const double* scale, double* a_out, int* dropped_out, unsigned long long* cstat,
+                                   bool first, const IterCtl* ctl, int* err) {
+  const int s = t.s, bws = s - 1;
+  const SolveSide a{t.xinv[0], t.dropped[0], t.m[0]}, b{t.xinv[1], t.dropped[1], t.m[1]};
+  const size_t smem = big_solve_smem_bytes((t.m[0] > t.m[1] ? t.m[0] : t.m[1]) + s, bws, t.stages);
+  if (t.stages >= 3)
+    k_coarse_solve_2s<3><<<2, FTB, smem, st>>>(n, s, bws, a, b, res, x, scale, a_out, dropped_out, cstat,
+                                               first ? 1 : 0, ctl, err);
+  else
+    k_coarse_solve_2s<2><<<2, FTB, smem, st>>>(n, s, bws, a, b, res, x, scale, a_out, dropped_out, cstat,
+                                               first ? 1 : 0, ctl, err);
   return cudaGetLastError();
 }
 

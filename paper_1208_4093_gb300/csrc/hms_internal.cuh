@@ -175,6 +175,34 @@ cudaError_t launch_coarse_solve_big(cudaStream_t s, int stages, int n, int bw, c
 cudaError_t launch_coarse_residual(cudaStream_t s, int n, int bw, const double* sband, const double* b,
                                    const double* x, const int* dropped, double* res, unsigned long long* cstat,
                                    const IterCtl* ctl);
+// two-sided FP32 factor and solve (coarse_solve.cu): top [0, m[0]), separator
+// [m[0], m[0] + s), bottom (m[1] rows, reversed frame); per side its row band,
+// factor, drop flags, separator buffers and 64-row block matrices
+struct TwoSided {
+  int m[2] = {0, 0};
+  int s = 0;
+  int stages = 0;
+  float* lin[2] = {nullptr, nullptr};
+  float* lcol[2] = {nullptr, nullptr};
+  float* dinv[2] = {nullptr, nullptr};
+  int* dropped[2] = {nullptr, nullptr};
+  float* delta[2] = {nullptr, nullptr};
+  float* srow[2] = {nullptr, nullptr};
+  float* xinv[2] = {nullptr, nullptr};
+};
+bool coarse_two_sided_split(int n, int bw, int* m0, int* m1, int* s);
+// element counts of one side's buffers (float, except dropped: int)
+struct TwoSidedSizes {
+  size_t lin, lcol, dinv, dropped, delta, srow, xinv;
+};
+TwoSidedSizes coarse_two_sided_sizes(int m, int s);
+size_t coarse_two_sided_factor_smem(int m0, int m1, int s);
+int coarse_two_sided_stages(int m0, int m1, int s, int max_smem);
+cudaError_t launch_coarse_factor_2s(cudaStream_t st, int n, int bw, const TwoSided& t, const double* sband,
+                                    const int* dropped, const IterCtl* ctl);
+cudaError_t launch_coarse_solve_2s(cudaStream_t st, int n, const TwoSided& t, const double* res, double* x,
+                                   const double* scale, double* a_out, int* dropped_out, unsigned long long* cstat,
+                                   bool first, const IterCtl* ctl, int* err);
 size_t coarse_factor_smem_bytes(int n, int bw, bool fp64);
 size_t coarse_solve_smem_bytes(int n, int bw, bool fp64);
 int coarse_dinv_size(int n);

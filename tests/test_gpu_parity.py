@@ -208,6 +208,58 @@ def test_coarse_solve_both_substitutions(hms_ctx, case, cf):
         capi.hms_problem_destroy(pr)
 
 
+# set grids whose upper-level system is long enough to split: separator s =
+# bw + 1 (33 x 90), bw + 4 (50 x 70), and a longer one (64 x 128)
+TWO_SIDED = [
+    ("split_s_bw1", 33, 90, 7, 6, True, None),
+    ("split_s_bw4", 50, 70, 10, 7, False, None),
+    ("split_long", 64, 128, 8, 8, True, None),
+]
+
+
+@pytest.mark.parametrize("case", TWO_SIDED + [CASES[1]], ids=lambda c: c[0])
+def test_two_sided_factor(hms_ctx, case):
+    """The FP32 factor of Eq. 8 split into top and bottom segments eliminated
+    on two SMs and the separator between them: the update V a and the full
+    solve match the oracle, and the result equals the one-SM factor's within
+    the FP64 refinement's accuracy."""
+    from paper_1208_4093_gb300 import capi
+    tr, g, p, pr = setup_case(hms_ctx, case, 0, coarse_factor=5)
+    pr1 = setup_case(hms_ctx, case, 0, coarse_factor=4)[3]
+    try:
+        rng = np.random.default_rng(19)
+        for _ in range(2):
+            u = tr.free * rng.standard_normal(tr.ndof)
+            r = tr.residual(tr.free * p, u)
+            delta = hms.LocalFactors(tr, g).relax(r)
+            V = hms.modes(tr, g, delta)
+            Ko, Po = hms.coarse_system(tr, V, r)
+            a = np.empty(9 * g.M)
+            a1 = np.empty(9 * g.M)
+            dr = np.zeros(9 * g.M, np.int32)
+            capi.hms_coarse_solve(hms_ctx, pr, Ko, Po, a, dropped_out=dr)
+            capi.hms_coarse_solve(hms_ctx, pr1, Ko, Po, a1)
+            ao, dro = hms.coarse_solve(Ko, Po)
+            assert rel(V @ a, V @ ao) < 1e-11
+            assert rel(V @ a, V @ a1) < 1e-11
+            assert np.array_equal(dr != 0, np.asarray(dro, bool))
+        out = np.empty((1, tr.ndof))
+        capi.hms_solve(hms_ctx, pr, p.reshape(1, -1), out)
+        assert rel(out[0], direct.cholesky_solve(tr, tr.free * p)) < 1e-9
+    finally:
+        capi.hms_problem_destroy(pr)
+        capi.hms_problem_destroy(pr1)
+
+
+def test_two_sided_needs_a_long_system(hms_ctx):
+    """coarse_factor = 5 is refused where the system is shorter than two 64-row
+    segments plus a separator (4 x 4 sets: n = 144, bw = 53)."""
+    from paper_1208_4093_gb300 import capi
+    with pytest.raises(capi.HmsError) as e:
+        setup_case(hms_ctx, CASES[0], 0, coarse_factor=5)
+    assert e.value.status == capi.HMS_ERR_ARG
+
+
 def test_one_iteration_from_any_state(problem):
     """T1 per step: one GPU update from u equals one oracle update from u."""
     from paper_1208_4093_gb300 import capi
