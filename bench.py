@@ -525,11 +525,12 @@ def run_ours(args, rank, world, local_rank):
         rooflines[name] = roof
 
     # kernels launched per solve: graph batches of 16 iterations, each iteration
-    # 9 kernels (residual, relaxation, assembly, band, diagonal, set drops,
-    # scaling, factor, block inverses) + coarse_solves solves + (coarse_solves - 1)
-    # refinement residuals (5 solves on the FP64 path), plus 1 load-norm kernel
+    # 10 kernels (residual, relaxation, assembly, band, diagonal, set drops,
+    # scaling, the two sides' bands, two-sided factor, block inverses) +
+    # coarse_solves solves + (coarse_solves - 1) refinement residuals (5 solves
+    # on the FP64 path), plus 1 load-norm kernel
     batches = math.ceil((nit64 + 1) / 16)
-    per_iter = 9 + 5 + 4
+    per_iter = 10 + 5 + 4
     launches = args.steps * (batches * 16 * per_iter + 1)
 
     ms_med = statistics.median(ms64)

@@ -98,6 +98,11 @@ typedef struct {
                                 4 = FP32 on one SM, 5 = FP32 two-sided: top and bottom
                                 segments eliminated at once on two SMs, then the
                                 separator between them */
+  int32_t relax_threads;     /* CTA size of the relaxation (Eqs. 11-13): 64, 128 or 256, or
+                                0 = autotuned: the first problem of a set-tile shape and
+                                precision on a context times each size on its own factors
+                                and the context keeps the fastest for that shape.  Results
+                                are bitwise the same for every size */
 } hms_options;
 
 /* Context: one device, one CUDA stream.  device = CUDA ordinal. */
@@ -129,6 +134,8 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out);
 size_t hms_problem_device_bytes(const hms_problem* pr);
 /* Milliseconds the setup kernels took (CUDA events). */
 double hms_problem_setup_ms(const hms_problem* pr);
+/* CTA size the relaxation of pr runs with (relax_threads, or the autotuned choice). */
+int32_t hms_problem_relax_threads(const hms_problem* pr);
 
 /* The whole iteration (Fig. 3) for nrhs load vectors, each from u0 (NULL =
  * zero): loads [nrhs][2*nx*ny], u0 and u_out likewise.  hist (nullable)

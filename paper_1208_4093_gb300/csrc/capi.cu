@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -20,6 +22,8 @@ struct hms_context {
   cudaStream_t stream = nullptr;
   std::vector<cudaStream_t> pool;  // streams of hms_solve_batch, created on first use
   std::string err;
+  // relaxation CTA size picked by timing, per (set width, set height, precision)
+  std::map<std::tuple<int, int, int>, int> relax_tuned;
 };
 
 // Buffers that stay read-only after setup (lattice description, set
@@ -37,6 +41,7 @@ struct hms_problem {
   int precision = HMS_FP64, nsolve = 4, batch = 16, profile = 0, max_iter = 0;
   bool coarse_fp64 = false;  // factor of the upper-level system in FP64 (else FP32 + FP64 refinement)
   double tol = 1e-8;
+  int relax_threads = 256;   // CTA size of the relaxation
   int n_c = 0, bw = 0;
   size_t bytes = 0;
   std::vector<void*> allocs;
@@ -204,7 +209,8 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
                              nullptr);
   if (e != cudaSuccess) return e;
   mark();
-  e = launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, pr->ctl, pr->err);
+  e = launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, pr->ctl, pr->err,
+                   pr->relax_threads);
   if (e != cudaSuccess) return e;
   mark();
   e = launch_coarse_slots(s, lv, pr->delta, fp32(pr), false, pr->slots_it, pr->ctl);
@@ -435,6 +441,7 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
   pr->bw = src->bw;
   pr->big_stages = src->big_stages;
   pr->cluster_factor = src->cluster_factor;
+  pr->relax_threads = src->relax_threads;
   pr->two_sided = src->two_sided;
   pr->ts = TwoSided();
   pr->ts.m[0] = src->ts.m[0];
@@ -468,6 +475,7 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
 }
 
 size_t hms_problem_device_bytes(const hms_problem* pr) { return pr ? pr->bytes : 0; }
+int32_t hms_problem_relax_threads(const hms_problem* pr) { return pr ? pr->relax_threads : 0; }
 double hms_problem_setup_ms(const hms_problem* pr) { return pr ? (double)pr->setup_ms : 0.0; }
 
 // The per-instance buffers of a problem whose configuration (lv, n_c, bw,
@@ -557,6 +565,56 @@ static cudaError_t alloc_instance(hms_problem* pr) {
   return cudaSuccess;
 }
 
+// Relaxation CTA size by timing: the first problem of a (set width, set
+// height, precision) on a context times one warm-up and three timed launches
+// of each size on its own factors (r = 0; the kernel's time does not depend
+// on the values) and the context keeps the fastest for that shape.  The sizes
+// give bitwise the same results, so the choice only changes the time.
+static cudaError_t autotune_relax(hms_problem* pr) {
+  hms_context* c = pr->ctx;
+  const LatView& lv = pr->lv;
+  const auto key = std::make_tuple(std::min(lv.sx, lv.nx), std::min(lv.sy, lv.ny), pr->precision);
+  const auto it = c->relax_tuned.find(key);
+  if (it != c->relax_tuned.end()) {
+    pr->relax_threads = it->second;
+    return cudaSuccess;
+  }
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaMemsetAsync(pr->r, 0, nnodes(pr) * sizeof(double2), s);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  float best = 0.f;
+  int best_nt = 256;
+  for (int nt : {64, 128, 256}) {
+    auto run = [&]() {
+      return launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr,
+                          pr->err, nt);
+    };
+    if ((e = run()) != cudaSuccess) break;
+    if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = run();
+    if (e != cudaSuccess || (e = cudaEventRecord(e1, s)) != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (nt == 64 || ms < best) {
+      best = ms;
+      best_nt = nt;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  pr->relax_threads = best_nt;
+  c->relax_tuned[key] = best_nt;
+  return cudaSuccess;
+}
+
 hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const hms_options* o,
                               hms_problem** out) {
   if (!c || !d || !o || !out) return HMS_ERR_ARG;
@@ -570,6 +628,8 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (!(o->tol >= 0.0) || o->max_iter < 0) return fail(c, HMS_ERR_ARG, "bad tol / max_iter");
   if (o->coarse_solves < 0 || o->coarse_solves > 8) return fail(c, HMS_ERR_ARG, "coarse_solves must be in 0..8");
   if (o->coarse_factor < 0 || o->coarse_factor > 5) return fail(c, HMS_ERR_ARG, "coarse_factor must be in 0..5");
+  if (o->relax_threads != 0 && o->relax_threads != 64 && o->relax_threads != 128 && o->relax_threads != 256)
+    return fail(c, HMS_ERR_ARG, "relax_threads must be 0, 64, 128 or 256");
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
 
@@ -719,6 +779,8 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
       return st;
     }
   }
+  if (o->relax_threads != 0) pr->relax_threads = o->relax_threads;
+  else CKP(autotune_relax(pr));
   if (!pr->profile) {
     hms_status st = build_graph(pr);
     if (st != HMS_OK) {
@@ -1004,7 +1066,8 @@ hms_status hms_relax(hms_problem* pr, const double* r, double* delta, double* P,
   const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
   CKC(c, cudaMemcpyAsync(pr->r, r, vb, kind_in(mem_kind), s));
   CKC(c, launch_mask_u(s, pr->lv, pr->r));
-  CKC(c, launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr, pr->err));
+  CKC(c, launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr, pr->err,
+                      pr->relax_threads));
   if (fp32(pr)) {
     CKC(c, launch_f2d(s, (const float*)pr->delta, (double*)pr->u[1], 2 * nn));
     CKC(c, cudaMemcpyAsync(delta, pr->u[1], vb, kind_out(mem_kind), s));

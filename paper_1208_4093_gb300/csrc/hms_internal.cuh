@@ -142,7 +142,7 @@ cudaError_t launch_set_factor(cudaStream_t s, const LatView& lv, const long long
 // relax.cu
 cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
                          const double* f64, const float* f32, const double2* r, void* delta,
-                         double* P, void* yscratch, const IterCtl* ctl, int* err);
+                         double* P, void* yscratch, const IterCtl* ctl, int* err, int threads);
 size_t relax_smem_bytes(const LatView& lv, bool fp32);
 long long relax_y_stride(const LatView& lv);
 // coarse.cu

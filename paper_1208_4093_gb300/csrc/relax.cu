@@ -21,17 +21,26 @@
 // Rows r and nb-1-r of a matrix go to a group of G threads as one combined
 // index range of almost constant length (nb+1 for the triangles, about nb+7
 // for the B blocks), so every lane of a warp runs the same number of FMAs.
-// The solve runs in T = double (FP64 path, G = 2: the FP64 pipe is the bound,
-// so the fewest reduction adds) or T = float (mixed path, FP32 factor, G = 4).
-// After the back substitution the nine sums of P_I = V_I^T r_I are formed in
-// FP64 from r and the delta just written, node by node.
+// The solve runs in T = double (FP64 path) or T = float (mixed path, FP32
+// factor), with G = 4 threads per row pair either way.  After the back
+// substitution the nine sums of P_I = V_I^T r_I are formed in FP64 from r and
+// the delta just written, node by node.
+//
+// The CTA size NT (64, 128 or 256 threads) is a launch choice: NT / G row
+// pairs are worked on at once, so 32 x 32-node sets (32 pairs) fill a CTA of
+// 128 threads and 64 x 64-node sets one of 256.  Every row's sum and every P
+// sum is formed in the same order whatever NT is (the P sums over 256 virtual
+// lanes), so the results are bitwise the same for every NT, and the problem
+// setup may pick NT by timing (relax_threads = 0).
+#include <type_traits>
+
 #include "hms_internal.cuh"
 #include "ptx.cuh"
 
 namespace hms {
 namespace {
 
-constexpr int NT = 256, NW = NT / 32;
+constexpr int VL = 256;  // virtual lanes of the P sums (8 virtual warps)
 
 __device__ inline double warp_sum_d(double v) {
 #pragma unroll
@@ -124,7 +133,7 @@ __device__ inline void row_shape(int nb, int r, int& lo, int& len, long long& of
 // the row pairs (r, nb-1-r); thread 0 of a group handles row r and thread 1
 // row nb-1-r.  pre = fetch(r) is loaded before the products so that its
 // latency hides behind them.
-template <typename T, int G, int CH, int K, class Fetch, class Out>
+template <int NT, typename T, int G, int CH, int K, class Fetch, class Out>
 __device__ inline void rows_times(const T* M, const T* v, int nb, Fetch fetch, Out out) {
   const int npair = nb / 2;  // nb = 2w is even
   const int g = threadIdx.x % G;
@@ -147,7 +156,7 @@ __device__ inline void rows_times(const T* M, const T* v, int nb, Fetch fetch, O
   }
 }
 
-template <typename T>
+template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __restrict__ set_off,
                                               const T* __restrict__ fac, const double2* __restrict__ r,
                                               T* __restrict__ delta, double* __restrict__ P,
@@ -155,12 +164,12 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
                                               int* err) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ uint64_t bars[NSLOT];
-  __shared__ double pred[NW * NMODES];
+  __shared__ double pred[(VL / 32) * NMODES];
   __shared__ int abort_flag;
   if (ctl && *(volatile const int*)&ctl->done) return;
 
   using T2 = typename Vec2<T>::type;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int I = blockIdx.x;
   const int Ix = I % lv.Mx, Iy = I / lv.Mx;
   const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
@@ -201,9 +210,6 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
   const size_t rowbase0 = 2 * ((size_t)j0 * lv.nx + i0);
   for (int t = tid; t < nb; t += NT) zbuf[t] = (T)rg[rowbase0 + t];
 
-  double pacc[NMODES];
-#pragma unroll
-  for (int m = 0; m < NMODES; ++m) pacc[m] = 0.0;
   const double2 rep = lv.rep[I];
 
   for (int o = 0; o < nops; ++o) {
@@ -224,13 +230,13 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
       const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
       if (is_b) {
         // z = r_j - B_j y_{j-1}
-        rows_times<T, G, CH, ROW_B>(
+        rows_times<NT, T, G, CH, ROW_B>(
             M, ycur, nb, [&](int row) { return (T)rg[rowbase + row]; },
             [&](int row, T s, T pre) { zbuf[row] = pre - s; });
       } else {
         // y_j = Linv_j z
         T* yj = yg + (size_t)j * nb;
-        rows_times<T, G, CH, ROW_LINV>(
+        rows_times<NT, T, G, CH, ROW_LINV>(
             M, zbuf, nb, [](int) { return T(0); },
             [&](int row, T s, T) {
               ycur[row] = s;
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
         // x_j = Linv_j^T w  (w = y_{h-1} for the last row)
         const T* wv = (j == h - 1) ? ycur : wbuf;
         const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
-        rows_times<T, G, CH, ROW_LT>(
+        rows_times<NT, T, G, CH, ROW_LT>(
             M, wv, nb, [](int) { return T(0); },
             [&](int row, T s, T) {
               xbuf[row] = s;
@@ -253,7 +259,7 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
       } else {
         // w = y_{j-1} - B_j^T x_j
         const T* yp = yg + (size_t)(j - 1) * nb;
-        rows_times<T, G, CH, ROW_BT>(
+        rows_times<NT, T, G, CH, ROW_BT>(
             M, xbuf, nb, [&](int row) { return yp[row]; }, [&](int row, T s, T pre) { wbuf[row] = pre - s; });
       }
       __syncthreads();
@@ -267,11 +273,18 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
     }
     return;
   }
-  // P = V^T r (Eq. 7) from r and the delta just written, node by node
+  // P = V^T r (Eq. 7) from r and the delta just written, node by node:
+  // virtual lane v sums nodes v, v + VL, ...; each virtual warp's 32 lanes go
+  // through one shuffle tree, and the 8 virtual warps are added in order
   __syncthreads();
-  {
-    const T2* d2 = reinterpret_cast<const T2*>(delta);
-    for (int node = tid; node < w * h; node += NT) {
+  const T2* d2 = reinterpret_cast<const T2*>(delta);
+  for (int vbase = 0; vbase < VL; vbase += NT) {
+    const int v = vbase + tid;
+    if (v >= VL) break;  // whole warps (VL is a multiple of 32)
+    double pacc[NMODES];
+#pragma unroll
+    for (int m = 0; m < NMODES; ++m) pacc[m] = 0.0;
+    for (int node = v; node < w * h; node += VL) {
       const int jj = node / w, il = node - jj * w;
       const int j = j0 + jj;
       const size_t nidx = (size_t)j * lv.nx + i0 + il;
@@ -290,18 +303,17 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
       pacc[7] = fma(xi, dr, pacc[7]);
       pacc[8] = fma(eta, dr, pacc[8]);
     }
-  }
-  // deterministic block reduction of the nine P sums
 #pragma unroll
-  for (int m = 0; m < NMODES; ++m) {
-    const double v = warp_sum_d(pacc[m]);
-    if (lane == 0) pred[warp * NMODES + m] = v;
+    for (int m = 0; m < NMODES; ++m) {
+      const double sm2 = warp_sum_d(pacc[m]);
+      if (lane == 0) pred[(v >> 5) * NMODES + m] = sm2;
+    }
   }
   __syncthreads();
   if (tid < NMODES) {
-    double s = 0.0;
-    for (int ww = 0; ww < NW; ++ww) s += pred[ww * NMODES + tid];
-    P[(size_t)NMODES * I + tid] = s;
+    double sum = 0.0;
+    for (int ww = 0; ww < VL / 32; ++ww) sum += pred[ww * NMODES + tid];
+    P[(size_t)NMODES * I + tid] = sum;
   }
 }
 
@@ -321,22 +333,34 @@ long long relax_y_stride(const LatView& lv) {
 
 cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
                          const double* f64, const float* f32, const double2* r, void* delta,
-                         double* P, void* yscratch, const IterCtl* ctl, int* err) {
+                         double* P, void* yscratch, const IterCtl* ctl, int* err, int threads) {
   const bool fp32 = (f32 != nullptr);
   const size_t smem = relax_smem_bytes(lv, fp32);
   const long long ys = relax_y_stride(lv);
-  if (fp32)
-    k_relax<float><<<lv.M, NT, smem, s>>>(lv, set_off, f32, r, (float*)delta, P, (float*)yscratch, ys, ctl, err);
-  else
-    k_relax<double><<<lv.M, NT, smem, s>>>(lv, set_off, f64, r, (double*)delta, P, (double*)yscratch, ys, ctl,
-                                           err);
+  auto go = [&](auto nt) {
+    constexpr int NT = decltype(nt)::value;
+    if (fp32)
+      k_relax<float, NT><<<lv.M, NT, smem, s>>>(lv, set_off, f32, r, (float*)delta, P, (float*)yscratch, ys, ctl,
+                                                err);
+    else
+      k_relax<double, NT><<<lv.M, NT, smem, s>>>(lv, set_off, f64, r, (double*)delta, P, (double*)yscratch, ys,
+                                                 ctl, err);
+  };
+  if (threads == 64) go(std::integral_constant<int, 64>());
+  else if (threads == 128) go(std::integral_constant<int, 128>());
+  else if (threads == 256) go(std::integral_constant<int, 256>());
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 cudaError_t configure_relax(int max_smem) {
-  cudaError_t e = set_max_dynamic_smem(k_relax<float>, max_smem);
-  if (e != cudaSuccess) return e;
-  return set_max_dynamic_smem(k_relax<double>, max_smem);
+  cudaError_t e;
+  if ((e = set_max_dynamic_smem(k_relax<float, 64>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_relax<float, 128>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_relax<float, 256>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_relax<double, 64>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_relax<double, 128>, max_smem)) != cudaSuccess) return e;
+  return set_max_dynamic_smem(k_relax<double, 256>, max_smem);
 }
 
 }  // namespace hms
