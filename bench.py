@@ -290,8 +290,10 @@ def run_batched(args):
     lats = batched_lattices(args.batched_count)
     ctx = capi.hms_context_create(0)
     t0 = time.perf_counter()
-    prs = [capi.hms_problem_create(ctx, l.nx, l.ny, 32, 32, precision=capi.HMS_MIXED, tol=TOL, max_iter=5000)
-           for l in lats]
+    # the one-SM upper-level factor for every lattice: the lockstep engine runs
+    # them all with one launch per step
+    prs = [capi.hms_problem_create(ctx, l.nx, l.ny, 32, 32, precision=capi.HMS_MIXED, tol=TOL, max_iter=5000,
+                                   coarse_factor=4) for l in lats]
     setup_s = time.perf_counter() - t0
     loads = [torch.from_numpy(l.load_array()).to(dev) for l in lats]
     outs = [torch.empty_like(x) for x in loads]
@@ -321,6 +323,15 @@ def run_batched(args):
         torch.cuda.synchronize()
         ms.append((time.perf_counter() - t0) * 1e3)
     ub = [o.cpu().numpy() for o in outs]
+    # the same batch with one CUDA-graph round per problem on a pool of streams
+    capi.hms_context_set_batch_mode(ctx, capi.HMS_BATCH_STREAMS)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    capi.hms_solve_batch(ctx, inst, inst_loads, inst_outs, iters=its)
+    torch.cuda.synchronize()
+    streams_ms = (time.perf_counter() - t0) * 1e3
+    same_streams = all(np.array_equal(a, o.cpu().numpy()) for a, o in zip(ub, outs))
+    capi.hms_context_set_batch_mode(ctx, capi.HMS_BATCH_AUTO)
     for h in clones:
         capi.hms_problem_destroy(h)
     # the same problems one after another (one pass)
@@ -344,6 +355,8 @@ def run_batched(args):
                    "dof_x_rhs": dofrhs, "sides": "log-uniform [32, 512]", "aspect": "Uniform[1, 4]",
                    "sets": [32, 32], "ea": 1.0, "tol": TOL, "setup_s": setup_s,
                    "updates_median": float(np.median(it)), "updates_max": int(it.max())},
+        "engine": "lockstep: one launch per step over every running problem's work items, 16 updates per graph",
+        "streams_engine_ms": streams_ms, "same_as_streams_engine": same_streams,
         "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / med, "same_as_sequential": same}))
 
 

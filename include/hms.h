@@ -152,20 +152,35 @@ hms_status hms_solve(hms_problem* pr, int32_t nrhs, const double* loads, const d
 /* Many independent problems of one context solved together (batched uneven
  * lattices; the paper solves one lattice at a time).  Problem i solves its
  * nrhs[i] load vectors loads[i] ([nrhs[i]][2*nx_i*ny_i]) from u0 = 0 into
- * u_out[i] (same shape), one after another, exactly as hms_solve would; the
- * problems run concurrently, each on one of up to 64 streams of the context
- * and at its own pace: whenever a problem's last CUDA-graph round
- * (options.batch updates) has ended, the host reads its convergence flag and
- * queues its next round, or takes the load vector out and starts the next
- * one.  Clones (hms_problem_clone) let one lattice's load vectors run at the
- * same time.  iters (nullable) receives the update
- * counts, problem by problem and load vector by load vector.  The problems
- * must belong to c, appear once, and not use options.profile.  Returns the
- * first device error, else HMS_ERR_NONFINITE / HMS_ERR_NO_CONVERGENCE if a
- * load vector ended that way (all results still written), else HMS_OK. */
+ * u_out[i] (same shape), one after another, exactly as hms_solve would
+ * (bitwise the same results).  Two engines (hms_context_set_batch_mode):
+ *  - lockstep (default where it applies): every step of an update is one
+ *    launch over a work list of (problem, tile) items of all running
+ *    problems; 16 updates of all of them are one CUDA graph launch; after
+ *    each, the host reads every problem's convergence flag (one gathered
+ *    copy), takes finished load vectors out and starts the next ones, and
+ *    rebuilds the work lists when the set of running problems has changed.
+ *    It applies when all problems share precision and coarse_solves and use
+ *    the FP32 one-SM factor with the 64-row block solve (coarse_factor = 4,
+ *    or auto where that is its choice);
+ *  - streams: each problem runs its own graph rounds on one of up to 64
+ *    streams of the context at its own pace.
+ * Clones (hms_problem_clone) let one lattice's load vectors run at the same
+ * time.  iters (nullable) receives the update counts, problem by problem and
+ * load vector by load vector.  The problems must belong to c, appear once,
+ * and not use options.profile.  Returns the first device error, else
+ * HMS_ERR_NONFINITE / HMS_ERR_NO_CONVERGENCE if a load vector ended that way
+ * (all results still written), else HMS_OK. */
 hms_status hms_solve_batch(hms_context* c, int32_t count, hms_problem* const* problems,
                            const int32_t* nrhs, const double* const* loads, double* const* u_out,
                            int32_t* iters, int32_t mem_kind);
+/* Engine of hms_solve_batch on c: HMS_BATCH_AUTO (lockstep where it applies,
+ * else streams; the default), HMS_BATCH_STREAMS, HMS_BATCH_LOCKSTEP (fails
+ * with HMS_ERR_ARG where it does not apply). */
+#define HMS_BATCH_AUTO 0
+#define HMS_BATCH_STREAMS 1
+#define HMS_BATCH_LOCKSTEP 2
+hms_status hms_context_set_batch_mode(hms_context* c, int32_t mode);
 
 /* Per-kernel CUDA-event time of the last hms_solve with options.profile = 1:
  * names "update_residual", "relax", "coarse_assemble", "coarse_band",

@@ -27,6 +27,9 @@ HMS_MEM_HOST = 0
 HMS_MEM_DEVICE = 1
 HMS_FP64 = 0
 HMS_MIXED = 1
+HMS_BATCH_AUTO = 0
+HMS_BATCH_STREAMS = 1
+HMS_BATCH_LOCKSTEP = 2
 
 KERNEL_NAMES = ("update_residual", "relax", "coarse_assemble", "coarse_band", "coarse_factor",
                 "coarse_residual", "coarse_solve")
@@ -91,6 +94,7 @@ def lib():
         "hms_coarse_solve": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32]),
         "hms_residual_noalloc": (ctypes.c_int32, [_P, _P, _P, _P, _P]),
         "hms_solve_batch": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_int32]),
+        "hms_context_set_batch_mode": (ctypes.c_int32, [_P, ctypes.c_int32]),
         "hms_problem_estimate_bytes": (ctypes.c_size_t, [_P, ctypes.POINTER(LatticeDesc), ctypes.POINTER(Options)]),
         "hms_server_create": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(_P)]),
         "hms_server_destroy": (None, [_P]),
@@ -116,7 +120,7 @@ def exported_symbols():
             "hms_update_residual", "hms_relax", "hms_coarse_matrix", "hms_coarse_solve",
             "hms_residual_noalloc", "hms_solve_batch", "hms_problem_estimate_bytes", "hms_server_create",
             "hms_server_destroy", "hms_server_submit", "hms_server_step", "hms_server_take", "hms_problem_clone",
-            "hms_problem_relax_threads"]
+            "hms_problem_relax_threads", "hms_context_set_batch_mode"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -249,6 +253,10 @@ def hms_solve(ctx, pr, loads, u_out, u0=None, hist=None, iters=None, allow_no_co
     st = lib().hms_solve(pr, nrhs, L.ptr, U0.ptr, U.ptr, H.ptr, cap, It.ptr, kind)
     ok = (HMS_OK, HMS_ERR_NO_CONVERGENCE) if allow_no_convergence else (HMS_OK,)
     return _check(ctx, st, ok)
+
+
+def hms_context_set_batch_mode(ctx, mode):
+    _check(ctx, lib().hms_context_set_batch_mode(ctx, int(mode)))
 
 
 def hms_solve_batch(ctx, problems, loads, u_out, iters=None, allow_no_convergence=False):

@@ -24,6 +24,7 @@ struct hms_context {
   std::string err;
   // relaxation CTA size picked by timing, per (set width, set height, precision)
   std::map<std::tuple<int, int, int>, int> relax_tuned;
+  int batch_mode = HMS_BATCH_AUTO;
 };
 
 // Buffers that stay read-only after setup (lattice description, set
@@ -895,8 +896,48 @@ int32_t hms_kernel_times(const hms_problem* pr, double* ms_total, int64_t* launc
   return m;
 }
 
+static hms_status solve_batch_streams(hms_context* c, int32_t count, hms_problem* const* problems,
+                                      const int32_t* nrhs, const double* const* loads, double* const* u_out,
+                                      int32_t* iters, int32_t mem_kind);
+static hms_status solve_batch_lockstep(hms_context* c, int32_t count, hms_problem* const* problems,
+                                       const int32_t* nrhs, const double* const* loads, double* const* u_out,
+                                       int32_t* iters, int32_t mem_kind);
+
+hms_status hms_context_set_batch_mode(hms_context* c, int32_t mode) {
+  if (!c || mode < HMS_BATCH_AUTO || mode > HMS_BATCH_LOCKSTEP) return HMS_ERR_ARG;
+  c->batch_mode = mode;
+  return HMS_OK;
+}
+
+// Whether the lockstep engine can run these problems together.
+static bool lockstep_applies(int32_t count, hms_problem* const* problems) {
+  for (int i = 0; i < count; ++i) {
+    const hms_problem* pr = problems[i];
+    if (!pr || pr->profile || pr->coarse_fp64 || pr->cluster_factor || pr->two_sided || pr->big_stages <= 0)
+      return false;
+    if (pr->precision != problems[0]->precision || pr->nsolve != problems[0]->nsolve) return false;
+  }
+  return true;
+}
+
 hms_status hms_solve_batch(hms_context* c, int32_t count, hms_problem* const* problems, const int32_t* nrhs,
                            const double* const* loads, double* const* u_out, int32_t* iters, int32_t mem_kind) {
+  if (!c) return HMS_ERR_ARG;
+  if (count > 0 && problems && c->batch_mode != HMS_BATCH_STREAMS) {
+    bool ok = true;
+    for (int i = 0; i < count && ok; ++i) ok = problems[i] && problems[i]->ctx == c;
+    if (ok && lockstep_applies(count, problems))
+      return solve_batch_lockstep(c, count, problems, nrhs, loads, u_out, iters, mem_kind);
+    if (c->batch_mode == HMS_BATCH_LOCKSTEP)
+      return fail(c, HMS_ERR_ARG, "hms_solve_batch: lockstep needs one precision, one coarse_solves and the "
+                                  "one-SM FP32 factor with the block solve for every problem");
+  }
+  return solve_batch_streams(c, count, problems, nrhs, loads, u_out, iters, mem_kind);
+}
+
+static hms_status solve_batch_streams(hms_context* c, int32_t count, hms_problem* const* problems,
+                                      const int32_t* nrhs, const double* const* loads, double* const* u_out,
+                                      int32_t* iters, int32_t mem_kind) {
   if (!c) return HMS_ERR_ARG;
   if (count < 0 || (count > 0 && (!problems || !nrhs || !loads || !u_out)))
     return fail(c, HMS_ERR_ARG, "hms_solve_batch: count < 0 or missing arrays");
@@ -1015,6 +1056,274 @@ hms_status hms_solve_batch(hms_context* c, int32_t count, hms_problem* const* pr
   hms_status result = HMS_OK;
   for (int i = 0; i < count; ++i) {
     const hms_status st = check_dev_err(problems[i]);
+    if (st != HMS_OK) return st;
+    if (status[i] == 3 && result == HMS_OK) result = fail(c, HMS_ERR_NONFINITE, "non-finite residual norm");
+    if (status[i] == 2 && result == HMS_OK) result = fail(c, HMS_ERR_NO_CONVERGENCE, "max_iter reached before tol");
+  }
+  return result;
+}
+
+// ---- lockstep batches ----
+
+// The convergence state of the running problems of a lockstep batch, gathered
+// into one array for one device-to-host copy per round.
+__global__ void k_gather_ctl(const BatchProb* __restrict__ P, const int* __restrict__ which, int n,
+                             IterCtl* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = *P[which[i]].ctl;
+}
+
+static BatchProb batch_prob_of(const hms_problem* pr) {
+  BatchProb q{};
+  q.lv = pr->lv;
+  q.u[0] = pr->u[0];
+  q.u[1] = pr->u[1];
+  q.p = pr->p;
+  q.r = pr->r;
+  q.delta = pr->delta;
+  q.a = pr->a;
+  q.P = pr->P;
+  q.partials = pr->partials;
+  q.ticket = pr->ticket;
+  q.ctl = pr->ctl;
+  q.hist = pr->hist;
+  q.hist_cap = pr->hist_cap;
+  q.err = pr->err;
+  q.set_off = pr->set_off;
+  q.f64 = pr->f64;
+  q.f32 = pr->f32;
+  q.yscratch = pr->yscratch;
+  q.slots_base = pr->slots_base;
+  q.slots_it = pr->slots_it;
+  q.band = pr->band;
+  q.sband = pr->sband;
+  q.scale = pr->scale;
+  q.b = pr->b;
+  q.x = pr->x;
+  q.res = pr->res;
+  q.lrow = (float*)pr->lrow;
+  q.lcol = (float*)pr->lcol;
+  q.dinv = (float*)pr->dinv;
+  q.xinv = pr->xinv;
+  q.dropped = pr->dropped;
+  q.cstat = pr->cstat;
+  q.n_c = pr->n_c;
+  q.bw = pr->bw;
+  return q;
+}
+
+// Work lists of the batched launches for the running problems, one after
+// another in one array; off[k] .. off[k + 1] is kernel k's list.
+enum BatchList { BL_K1 = 0, BL_SETS, BL_BAND, BL_DIAG, BL_DROPS, BL_SCALE, BL_ONE, BL_BLOCKINV, BL_CRES, BL_COUNT };
+
+static void build_lists(const std::vector<hms_problem*>& probs, const std::vector<int>& run,
+                        std::vector<BatchItem>& items, int off[BL_COUNT + 1]) {
+  items.clear();
+  for (int k = 0; k < BL_COUNT; ++k) {
+    off[k] = (int)items.size();
+    for (int i : run) {
+      const hms_problem* pr = probs[i];
+      const LatView& lv = pr->lv;
+      auto grid = [&](int g) {
+        for (int b = 0; b < g; ++b) items.push_back(BatchItem{i, b, 0, g, 1});
+      };
+      switch (k) {
+        case BL_K1: {
+          const int gx = update_residual_grid_x(lv), gy = update_residual_grid_y(lv);
+          for (int by = 0; by < gy; ++by)
+            for (int bx = 0; bx < gx; ++bx) items.push_back(BatchItem{i, bx, by, gx, gy});
+          break;
+        }
+        case BL_SETS: grid(lv.M); break;
+        case BL_BAND: grid(coarse_grid_for((size_t)pr->n_c * (pr->bw + 1))); break;
+        case BL_DIAG: grid(coarse_grid_for((size_t)pr->n_c)); break;
+        case BL_DROPS: grid(set_drops_blocks(lv.M)); break;
+        case BL_SCALE: grid(coarse_grid_for((size_t)pr->n_c * (pr->bw + 1))); break;
+        case BL_ONE: items.push_back(BatchItem{i, 0, 0, 1, 1}); break;
+        case BL_BLOCKINV: {
+          const int nb = (pr->n_c + 63) / 64;
+          for (int K = 0; K < nb; ++K)
+            for (int part = 0; part < 4; ++part) items.push_back(BatchItem{i, K, part, nb, 4});
+          break;
+        }
+        case BL_CRES: grid(coarse_residual_blocks(pr->n_c)); break;
+      }
+    }
+  }
+  off[BL_COUNT] = (int)items.size();
+}
+
+static hms_status solve_batch_lockstep(hms_context* c, int32_t count, hms_problem* const* problems,
+                                       const int32_t* nrhs, const double* const* loads, double* const* u_out,
+                                       int32_t* iters, int32_t mem_kind) {
+  if (count < 0 || (count > 0 && (!problems || !nrhs || !loads || !u_out)))
+    return fail(c, HMS_ERR_ARG, "hms_solve_batch: count < 0 or missing arrays");
+  if (mem_kind != HMS_MEM_HOST && mem_kind != HMS_MEM_DEVICE) return fail(c, HMS_ERR_ARG, "bad mem_kind");
+  {
+    std::vector<const hms_problem*> seen(problems, problems + count);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+      return fail(c, HMS_ERR_ARG, "hms_solve_batch: a problem appears twice");
+  }
+  for (int i = 0; i < count; ++i)
+    if (nrhs[i] < 0 || (nrhs[i] > 0 && (!loads[i] || !u_out[i])))
+      return fail(c, HMS_ERR_ARG, "hms_solve_batch: bad nrhs / loads / u_out");
+  CKC(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  std::vector<hms_problem*> probs(problems, problems + count);
+  const bool f32 = fp32(probs[0]);
+  const int nsolve = probs[0]->nsolve;
+  // one launch shape for all: the relaxation CTA size gives the same bits at
+  // any size; the block solve's pipeline depth does not change its arithmetic
+  const int rthreads = probs[0]->relax_threads;
+  int stages = 3;
+  size_t sm_relax = 0, sm_slots = 0, sm_factor = 0, sm_solve = 0;
+  for (hms_problem* pr : probs) stages = std::min(stages, pr->big_stages);
+  for (hms_problem* pr : probs) {
+    sm_relax = std::max(sm_relax, relax_smem_bytes(pr->lv, f32));
+    sm_slots = std::max(sm_slots, coarse_slots_smem(pr->lv));
+    sm_factor = std::max(sm_factor, coarse_factor_smem_bytes(pr->n_c, pr->bw, false));
+    sm_solve = std::max(sm_solve, big_solve_smem_bytes(pr->n_c, pr->bw, stages));
+  }
+  // device copies of the problems' buffers, the running set and the work lists
+  struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() {
+      if (p) cudaFree(p);
+    }
+  } dprob, dwhich, ditems, dctl;
+  std::vector<BatchProb> hp(count);
+  for (int i = 0; i < count; ++i) hp[i] = batch_prob_of(probs[i]);
+  CKC(c, cudaMalloc(&dprob.p, std::max<size_t>(1, count) * sizeof(BatchProb)));
+  CKC(c, cudaMalloc(&dwhich.p, std::max<size_t>(1, count) * sizeof(int)));
+  CKC(c, cudaMalloc(&dctl.p, std::max<size_t>(1, count) * sizeof(IterCtl)));
+  CKC(c, cudaMemcpyAsync(dprob.p, hp.data(), count * sizeof(BatchProb), cudaMemcpyHostToDevice, s));
+  IterCtl* hctl = nullptr;
+  CKC(c, cudaMallocHost(&hctl, std::max<size_t>(1, count) * sizeof(IterCtl)));
+  struct HostFree {
+    IterCtl* p;
+    ~HostFree() { cudaFreeHost(p); }
+  } hctl_guard{hctl};
+  const BatchProb* P = (const BatchProb*)dprob.p;
+
+  std::vector<long long> ioff(count + 1, 0);
+  for (int i = 0; i < count; ++i) ioff[i + 1] = ioff[i] + nrhs[i];
+  std::vector<int32_t> its((size_t)ioff[count], 0);
+  std::vector<int> q(count, 0), launches(count, 0), status(count, 1);
+  auto start = [&](int i) -> cudaError_t {
+    hms_problem* pr = probs[i];
+    const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+    cudaError_t e = cudaMemcpyAsync(pr->p, loads[i] + 2 * nn * q[i], vb, kind_in(mem_kind), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pr->u[0], 0, vb, s);
+    IterCtl hc{};
+    hc.max_iter = pr->max_iter;
+    hc.tol = pr->tol;
+    *pr->ctl_host = hc;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pr->ctl, pr->ctl_host, sizeof(IterCtl), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_load_norms(s, pr->lv, pr->p, pr->partials, pr->ticket, pr->ctl);
+    launches[i] = 0;
+    return e;
+  };
+  std::vector<int> run;
+  for (int i = 0; i < count; ++i)
+    if (nrhs[i] > 0) {
+      CKC(c, start(i));
+      run.push_back(i);
+    }
+  std::vector<BatchItem> items;
+  int off[BL_COUNT + 1];
+  size_t items_cap = 0;
+  cudaGraphExec_t exec = nullptr;
+  struct ExecGuard {
+    cudaGraphExec_t& e;
+    ~ExecGuard() {
+      if (e) cudaGraphExecDestroy(e);
+    }
+  } exec_guard{exec};
+  bool rebuild = true;
+  while (!run.empty()) {
+    if (rebuild) {
+      build_lists(probs, run, items, off);
+      if (items.size() > items_cap) {
+        if (ditems.p) cudaFree(ditems.p);
+        ditems.p = nullptr;
+        items_cap = items.size();
+        CKC(c, cudaMalloc(&ditems.p, items_cap * sizeof(BatchItem)));
+      }
+      CKC(c, cudaMemcpyAsync(ditems.p, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s));
+      CKC(c, cudaMemcpyAsync(dwhich.p, run.data(), run.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      const BatchItem* I = (const BatchItem*)ditems.p;
+      auto L = [&](int k) { return I + off[k]; };
+      auto N = [&](int k) { return off[k + 1] - off[k]; };
+      if (exec) {
+        cudaGraphExecDestroy(exec);
+        exec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      CKC(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (int k = 0; k < 16 && e == cudaSuccess; ++k) {
+        e = launch_batch_update_residual(s, f32, P, L(BL_K1), N(BL_K1), k);
+        if (e == cudaSuccess) e = launch_batch_relax(s, f32, rthreads, sm_relax, P, L(BL_SETS), N(BL_SETS));
+        if (e == cudaSuccess) e = launch_batch_slots(s, f32, sm_slots, P, L(BL_SETS), N(BL_SETS));
+        if (e == cudaSuccess) e = launch_batch_band(s, P, L(BL_BAND), N(BL_BAND));
+        if (e == cudaSuccess) e = launch_batch_diag(s, P, L(BL_DIAG), N(BL_DIAG));
+        if (e == cudaSuccess) e = launch_batch_set_drops(s, P, L(BL_DROPS), N(BL_DROPS));
+        if (e == cudaSuccess) e = launch_batch_scale_band(s, P, L(BL_SCALE), N(BL_SCALE));
+        if (e == cudaSuccess) e = launch_batch_factor(s, sm_factor, P, L(BL_ONE), N(BL_ONE));
+        if (e == cudaSuccess) e = launch_batch_blockinv(s, P, L(BL_BLOCKINV), N(BL_BLOCKINV));
+        for (int qq = 0; qq < nsolve && e == cudaSuccess; ++qq) {
+          if (qq > 0) e = launch_batch_coarse_residual(s, P, L(BL_CRES), N(BL_CRES));
+          if (e == cudaSuccess) e = launch_batch_solve(s, stages, sm_solve, P, L(BL_ONE), N(BL_ONE), qq == 0);
+        }
+      }
+      const cudaError_t ee = cudaStreamEndCapture(s, &g);
+      if (e == cudaSuccess) e = ee;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      CKC(c, e);
+      rebuild = false;
+    }
+    CKC(c, cudaGraphLaunch(exec, s));
+    const int nr = (int)run.size();
+    k_gather_ctl<<<(nr + 127) / 128, 128, 0, s>>>(P, (const int*)dwhich.p, nr, (IterCtl*)dctl.p);
+    CKC(c, cudaGetLastError());
+    CKC(c, cudaMemcpyAsync(hctl, dctl.p, nr * sizeof(IterCtl), cudaMemcpyDeviceToHost, s));
+    CKC(c, cudaStreamSynchronize(s));
+    std::vector<int> next;
+    for (int r = 0; r < nr; ++r) {
+      const int i = run[r];
+      hms_problem* pr = probs[i];
+      ++launches[i];
+      const IterCtl fin = hctl[r];
+      if (fin.done || launches[i] >= pr->max_iter / pr->batch + 3) {
+        const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+        CKC(c, cudaMemcpyAsync(u_out[i] + 2 * nn * q[i], pr->u[fin.t & 1], vb, kind_out(mem_kind), s));
+        its[(size_t)(ioff[i] + q[i])] = fin.t > 0 ? fin.t - 1 : 0;
+        if (fin.status == 3) status[i] = 3;
+        else if (fin.status != 1 && status[i] == 1) status[i] = 2;
+        if (++q[i] < nrhs[i]) {
+          CKC(c, start(i));
+          next.push_back(i);
+        } else {
+          rebuild = true;
+        }
+      } else {
+        next.push_back(i);
+      }
+    }
+    run.swap(next);
+  }
+  CKC(c, cudaStreamSynchronize(s));
+  if (iters && ioff[count] > 0) {
+    if (mem_kind == HMS_MEM_DEVICE)
+      CKC(c, cudaMemcpy(iters, its.data(), its.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    else
+      std::memcpy(iters, its.data(), its.size() * sizeof(int32_t));
+  }
+  hms_status result = HMS_OK;
+  for (int i = 0; i < count; ++i) {
+    const hms_status st = check_dev_err(probs[i]);
     if (st != HMS_OK) return st;
     if (status[i] == 3 && result == HMS_OK) result = fail(c, HMS_ERR_NONFINITE, "non-finite residual norm");
     if (status[i] == 2 && result == HMS_OK) result = fail(c, HMS_ERR_NO_CONVERGENCE, "max_iter reached before tol");

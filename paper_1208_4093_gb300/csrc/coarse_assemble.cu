@@ -92,14 +92,14 @@ __host__ __device__ inline ListCaps list_caps(int w, int h) {
 // products only approximate K_aa, which leaves the iteration's fixed point
 // unchanged because P uses the FP64 residual).  Per-thread partial sums are
 // promoted to FP64 before the block reduction.
+// The kernel body for set I.
 template <typename DT, bool FULL, typename AT>
-__global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __restrict__ delta,
-                                                     double* __restrict__ slots, const IterCtl* ctl) {
+__device__ __forceinline__ void slots_body(const LatView lv, const DT* __restrict__ delta, double* __restrict__ slots,
+                                           const IterCtl* ctl, int I) {
   extern __shared__ double lists[];
   if (ctl && *(volatile const int*)&ctl->done) return;
   constexpr int NGEN = FULL ? NGEN_FULL : NGEN_DELTA;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int I = blockIdx.x;
   const int Ix = I % lv.Mx, Iy = I / lv.Mx;
   const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
   const int w = min(lv.sx, lv.nx - i0), h = min(lv.sy, lv.ny - j0);
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const double k = bar_k(lv, i, j, d);
-      if (k == 0.0) continue;
+      if (__double_as_longlong(k) == 0) continue;  // no bar (bar_k returns +0.0; EA > 0): an integer test
       const int ib = (d == 0) ? i + 1 : (d == 1 ? i + off : i - 1 + off);
       const int jb = (d == 0) ? j : j + 1;
       const size_t nbn = (size_t)jb * lv.nx + ib;
@@ -197,42 +197,80 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
               }
           }
         }
-      } else {
-        int slot, idx;
-        if (dys == 0) {
-          if (dxs > 0) {
-            slot = SLOT_E;
-            idx = 2 * jl + (d == 1 ? 1 : 0);
-          } else {
-            slot = SLOT_W;
-            idx = jl;
-          }
-        } else if (dxs == 0) {
-          slot = SLOT_N;
-          idx = 2 * il + (d == 2 ? 1 : 0);
-        } else if (dxs > 0) {
-          slot = SLOT_NE;
-          idx = (d == 1) ? 0 : 1;
+      }
+      // else an interface bar: the pass below
+    }
+  }
+
+  // Interface bars (the far end in a neighbour set), apart from the node loop
+  // so that whole warps take their FP64 work (in the node loop one lane of a
+  // warp would, while the FP64 pipe spends a warp instruction's full time):
+  // the right column's E and NE bars, the left column's NW bars, the top
+  // row's NE and NW bars.  Each list entry is written by one item; the sums
+  // over the lists below are unchanged.
+  for (int t = tid; t < 3 * h + 2 * w; t += NT) {
+    int il, jl, d;
+    if (t < 2 * h) {
+      il = w - 1, jl = t >> 1, d = t & 1;
+    } else if (t < 3 * h) {
+      il = 0, jl = t - 2 * h, d = 2;
+    } else {
+      const int u = t - 3 * h;
+      il = u >> 1, jl = h - 1, d = 1 + (u & 1);
+      if ((d == 1 && il == w - 1) || (d == 2 && il == 0)) continue;  // in the column groups
+    }
+    const int i = i0 + il, j = j0 + jl, off = j & 1;
+    const double k = bar_k(lv, i, j, d);
+    if (__double_as_longlong(k) == 0) continue;
+    const int ib = (d == 0) ? i + 1 : (d == 1 ? i + off : i - 1 + off);
+    const int jb = (d == 0) ? j : j + 1;
+    const int dxs = (ib >= i0 + w) ? 1 : (ib < i0 ? -1 : 0);
+    const int dys = (jb >= j0 + h) ? 1 : 0;
+    if (dxs == 0 && dys == 0) continue;  // an inner bar (node loop)
+    const size_t na = (size_t)j * lv.nx + i, nbn = (size_t)jb * lv.nx + ib;
+    const unsigned fa = lv.fix[na], fb = lv.fix[nbn];
+    const double ex = (d == 0) ? 1.0 : (d == 1 ? 0.5 : -0.5), ey = (d == 0) ? 0.0 : SQ3_2;
+    auto fp64_ends = [&](double2& da, double2& db, double& xa, double& ya, double& xb, double& yb) {
+      da = FULL ? make_double2(0.0, 0.0) : ld_delta(delta, na);
+      db = FULL ? make_double2(0.0, 0.0) : ld_delta(delta, nbn);
+      xa = node_x(lv, i, j), ya = node_y(lv, j);
+      xb = node_x(lv, ib, jb), yb = node_y(lv, jb);
+    };
+    {
+      int slot, idx;
+      if (dys == 0) {
+        if (dxs > 0) {
+          slot = SLOT_E;
+          idx = 2 * jl + (d == 1 ? 1 : 0);
         } else {
-          slot = SLOT_NW;
-          idx = (d == 2) ? 0 : 1;
+          slot = SLOT_W;
+          idx = jl;
         }
-        double2 da, db;
-        double xa, ya, xb, yb;
-        fp64_ends(da, db, xa, ya, xb, yb);
-        const int Jx = Ix + dxs, Jy = Iy + dys;
-        const double2 repJ = lv.rep[Jy * lv.Mx + Jx];
-        double* e = lists + (size_t)(LC.off[slot] + idx) * LSTRIDE;
-        double sa[9], sb[9];
-        mode_proj(ex, ey, xa - repI.x, ya - repI.y, fa, da, sa);
-        mode_proj(ex, ey, xb - repJ.x, yb - repJ.y, fb, db, sb);
+      } else if (dxs == 0) {
+        slot = SLOT_N;
+        idx = 2 * il + (d == 2 ? 1 : 0);
+      } else if (dxs > 0) {
+        slot = SLOT_NE;
+        idx = (d == 1) ? 0 : 1;
+      } else {
+        slot = SLOT_NW;
+        idx = (d == 2) ? 0 : 1;
+      }
+      double2 da, db;
+      double xa, ya, xb, yb;
+      fp64_ends(da, db, xa, ya, xb, yb);
+      const int Jx = Ix + dxs, Jy = Iy + dys;
+      const double2 repJ = lv.rep[Jy * lv.Mx + Jx];
+      double* e = lists + (size_t)(LC.off[slot] + idx) * LSTRIDE;
+      double sa[9], sb[9];
+      mode_proj(ex, ey, xa - repI.x, ya - repI.y, fa, da, sa);
+      mode_proj(ex, ey, xb - repJ.x, yb - repJ.y, fb, db, sb);
 #pragma unroll
-        for (int m = 0; m < 9; ++m) {
-          e[m] = sa[m];
-          e[9 + m] = -sb[m];
-          e[18 + m] = k * sa[m];
-          e[27 + m] = -(k * sb[m]);
-        }
+      for (int m = 0; m < 9; ++m) {
+        e[m] = sa[m];
+        e[9 + m] = -sb[m];
+        e[18 + m] = k * sa[m];
+        e[27 + m] = -(k * sb[m]);
       }
     }
   }
@@ -309,6 +347,21 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
   }
 }
 
+template <typename DT, bool FULL, typename AT>
+__global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __restrict__ delta,
+                                                     double* __restrict__ slots, const IterCtl* ctl) {
+  slots_body<DT, FULL, AT>(lv, delta, slots, ctl, blockIdx.x);
+}
+
+// Batched (per-iteration pass, FULL = false): the sets of every problem.
+template <typename DT, typename AT>
+__global__ void __launch_bounds__(NT) kb_coarse_slots(const BatchProb* __restrict__ P,
+                                                      const BatchItem* __restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  const BatchProb& q = P[it.prob];
+  slots_body<DT, false, AT>(q.lv, (const DT*)q.delta, q.slots_it, q.ctl, it.bx);
+}
+
 // Band (lower, column-major: band[c*(bw+1) + k] = A[c+k][c]) of K_aa from the
 // base (modes 1-6) and per-iteration (modes 7-9) slots.
 __device__ inline double slot_entry(const double* base, const double* it, int I, int slot, int p, int c) {
@@ -316,14 +369,14 @@ __device__ inline double slot_entry(const double* base, const double* it, int I,
   return base[o] + it[o];
 }
 
-__global__ void k_band_from_slots(LatView lv, const double* __restrict__ base,
-                                  const double* __restrict__ it, double* __restrict__ band, int bw,
-                                  const IterCtl* ctl) {
+__device__ __forceinline__ void band_from_slots_body(const LatView lv, const double* __restrict__ base,
+                                                     const double* __restrict__ it, double* __restrict__ band,
+                                                     int bw, const IterCtl* ctl, int bx, int gx) {
   if (ctl && *(volatile const int*)&ctl->done) return;
   const int n = NMODES * lv.M;
   const size_t total = (size_t)n * (bw + 1);
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
-       q += (size_t)gridDim.x * blockDim.x) {
+  for (size_t q = bx * (size_t)blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gx * blockDim.x) {
     const int col = (int)(q / (bw + 1)), k = (int)(q % (bw + 1));
     const int row = col + k;
     double v = 0.0;
@@ -359,6 +412,17 @@ __global__ void k_band_from_slots(LatView lv, const double* __restrict__ base,
   }
 }
 
+__global__ void k_band_from_slots(LatView lv, const double* __restrict__ base,
+                                  const double* __restrict__ it, double* __restrict__ band, int bw,
+                                  const IterCtl* ctl) {
+  band_from_slots_body(lv, base, it, band, bw, ctl, blockIdx.x, gridDim.x);
+}
+__global__ void kb_band_from_slots(const BatchProb* __restrict__ P, const BatchItem* __restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  const BatchProb& q = P[it.prob];
+  band_from_slots_body(q.lv, q.slots_base, q.slots_it, q.band, q.bw, q.ctl, it.bx, it.gx);
+}
+
 __global__ void k_band_from_dense(int n, int bw, const double* __restrict__ dense,
                                   double* __restrict__ band) {
   const size_t total = (size_t)n * (bw + 1);
@@ -384,12 +448,12 @@ __global__ void k_dense_from_band(int n, int bw, const double* __restrict__ band
 // Jacobi scaling (s_i = D_ii^-1/2), right-hand side b = s P, the solution
 // accumulator x = 0, and the modes that vanish: D_ii <= 1e-300, or <= 1e-28
 // times the largest diagonal of the set's nine modes (zero up to rounding).
-__global__ void k_coarse_diag(int n, int bw, const double* __restrict__ band,
-                              const double* __restrict__ P, double* __restrict__ scale,
-                              double* __restrict__ b, double* __restrict__ x, int* __restrict__ dropped,
-                              const IterCtl* ctl) {
+__device__ __forceinline__ void coarse_diag_body(int n, int bw, const double* __restrict__ band,
+                                                 const double* __restrict__ P, double* __restrict__ scale,
+                                                 double* __restrict__ b, double* __restrict__ x,
+                                                 int* __restrict__ dropped, const IterCtl* ctl, int bx, int gx) {
   if (ctl && *(volatile const int*)&ctl->done) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = bx * blockDim.x + threadIdx.x; i < n; i += gx * blockDim.x) {
     const double D = band[(size_t)i * (bw + 1)];
     const int g0 = i - i % NMODES;
     double dmax = 0.0;
@@ -403,16 +467,28 @@ __global__ void k_coarse_diag(int n, int bw, const double* __restrict__ band,
   }
 }
 
+__global__ void k_coarse_diag(int n, int bw, const double* __restrict__ band,
+                              const double* __restrict__ P, double* __restrict__ scale,
+                              double* __restrict__ b, double* __restrict__ x, int* __restrict__ dropped,
+                              const IterCtl* ctl) {
+  coarse_diag_body(n, bw, band, P, scale, b, x, dropped, ctl, blockIdx.x, gridDim.x);
+}
+__global__ void kb_coarse_diag(const BatchProb* __restrict__ Pb, const BatchItem* __restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  const BatchProb& q = Pb[it.prob];
+  coarse_diag_body(q.n_c, q.bw, q.band, q.P, q.scale, q.b, q.x, q.dropped, q.ctl, it.bx, it.gx);
+}
+
 // Modes that depend on earlier modes of the same set get a = 0.  Sets have
 // disjoint supports, so the columns of V can only be dependent within a set:
 // the Jacobi-scaled 9 x 9 diagonal block of every set is factored in FP64 in
 // mode order, and a mode whose pivot is <= 1e-14 is dropped (the rule of the
 // full upper-level system, decided where FP64 resolves it).
-__global__ void k_coarse_set_drops(int nsets, int bw, const double* __restrict__ band,
-                                   const double* __restrict__ scale, int* __restrict__ dropped,
-                                   const IterCtl* ctl) {
+__device__ __forceinline__ void set_drops_body(int nsets, int bw, const double* __restrict__ band,
+                                               const double* __restrict__ scale, int* __restrict__ dropped,
+                                               const IterCtl* ctl, int bx, int gx) {
   if (ctl && *(volatile const int*)&ctl->done) return;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = bx * blockDim.x + threadIdx.x;
   if (I >= nsets) return;
   double A[NMODES][NMODES];
   bool dr[NMODES];
@@ -453,17 +529,29 @@ __global__ void k_coarse_set_drops(int nsets, int bw, const double* __restrict__
   for (int m = 0; m < NMODES; ++m) dropped[NMODES * I + m] = dr[m] ? 1 : 0;
 }
 
+__global__ void k_coarse_set_drops(int nsets, int bw, const double* __restrict__ band,
+                                   const double* __restrict__ scale, int* __restrict__ dropped,
+                                   const IterCtl* ctl) {
+  set_drops_body(nsets, bw, band, scale, dropped, ctl, blockIdx.x, gridDim.x);
+}
+__global__ void kb_coarse_set_drops(const BatchProb* __restrict__ P, const BatchItem* __restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  const BatchProb& q = P[it.prob];
+  set_drops_body(q.lv.M, q.bw, q.band, q.scale, q.dropped, q.ctl, it.bx, it.gx);
+}
+
 // Scaled band in FP64 (column layout for the residual's upper part and row
 // layout for its lower part) and the factor's input in row layout, in T.
 template <typename T>
-__global__ void k_coarse_scale_band(int n, int bw, const double* __restrict__ band,
-                                    const double* __restrict__ scale, const int* __restrict__ dropped,
-                                    double* __restrict__ sband, double* __restrict__ sbandR,
-                                    T* __restrict__ frow, double* __restrict__ b, const IterCtl* ctl) {
+__device__ __forceinline__ void scale_band_body(int n, int bw, const double* __restrict__ band,
+                                                const double* __restrict__ scale, const int* __restrict__ dropped,
+                                                double* __restrict__ sband, double* __restrict__ sbandR,
+                                                T* __restrict__ frow, double* __restrict__ b, const IterCtl* ctl,
+                                                int bx, int gx) {
   if (ctl && *(volatile const int*)&ctl->done) return;
   const size_t total = (size_t)n * (bw + 1);
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
-       q += (size_t)gridDim.x * blockDim.x) {
+  for (size_t q = bx * (size_t)blockDim.x + threadIdx.x; q < total;
+       q += (size_t)gx * blockDim.x) {
     const int col = (int)(q / (bw + 1)), k = (int)(q % (bw + 1));
     const int row = col + k;
     double v = 0.0;
@@ -481,6 +569,21 @@ __global__ void k_coarse_scale_band(int n, int bw, const double* __restrict__ ba
     }
     if (k == 0 && dropped[col]) b[col] = 0.0;
   }
+}
+
+template <typename T>
+__global__ void k_coarse_scale_band(int n, int bw, const double* __restrict__ band,
+                                    const double* __restrict__ scale, const int* __restrict__ dropped,
+                                    double* __restrict__ sband, double* __restrict__ sbandR,
+                                    T* __restrict__ frow, double* __restrict__ b, const IterCtl* ctl) {
+  scale_band_body<T>(n, bw, band, scale, dropped, sband, sbandR, frow, b, ctl, blockIdx.x, gridDim.x);
+}
+// Batched: the FP32 factor's input (the batched path factors in FP32).
+__global__ void kb_coarse_scale_band(const BatchProb* __restrict__ P, const BatchItem* __restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  const BatchProb& q = P[it.prob];
+  scale_band_body<float>(q.n_c, q.bw, q.band, q.scale, q.dropped, q.sband, q.sband + (size_t)q.n_c * (q.bw + 1),
+                         q.lrow, q.b, q.ctl, it.bx, it.gx);
 }
 
 }  // namespace
@@ -519,7 +622,11 @@ cudaError_t configure_coarse_assemble(int max_smem) {
   if (e != cudaSuccess) return e;
   e = set_max_dynamic_smem(k_coarse_slots<double2, true, double>, max_smem);
   if (e != cudaSuccess) return e;
-  return set_max_dynamic_smem(k_coarse_slots<double2, false, double>, max_smem);
+  e = set_max_dynamic_smem(k_coarse_slots<double2, false, double>, max_smem);
+  if (e != cudaSuccess) return e;
+  e = set_max_dynamic_smem(kb_coarse_slots<float2, float>, max_smem);
+  if (e != cudaSuccess) return e;
+  return set_max_dynamic_smem(kb_coarse_slots<double2, double>, max_smem);
 }
 
 static int grid_for(size_t total) {
@@ -527,6 +634,37 @@ static int grid_for(size_t total) {
   if (g > 4096) g = 4096;
   if (g < 1) g = 1;
   return (int)g;
+}
+
+int coarse_grid_for(size_t n) { return grid_for(n); }
+int set_drops_blocks(int nsets) { return (nsets + 127) / 128; }
+
+cudaError_t launch_batch_slots(cudaStream_t s, bool fp32, size_t smem, const BatchProb* P, const BatchItem* it,
+                               int n) {
+  if (n <= 0) return cudaSuccess;
+  if (fp32) kb_coarse_slots<float2, float><<<n, NT, smem, s>>>(P, it);
+  else kb_coarse_slots<double2, double><<<n, NT, smem, s>>>(P, it);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_band(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n) {
+  if (n <= 0) return cudaSuccess;
+  kb_band_from_slots<<<n, 256, 0, s>>>(P, it);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_diag(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n) {
+  if (n <= 0) return cudaSuccess;
+  kb_coarse_diag<<<n, 256, 0, s>>>(P, it);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_set_drops(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n) {
+  if (n <= 0) return cudaSuccess;
+  kb_coarse_set_drops<<<n, 128, 0, s>>>(P, it);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_scale_band(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n) {
+  if (n <= 0) return cudaSuccess;
+  kb_coarse_scale_band<<<n, 256, 0, s>>>(P, it);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_coarse_band_from_slots(cudaStream_t s, const LatView& lv, const double* base,

@@ -618,6 +618,24 @@ __global__ void __launch_bounds__(256) k_coarse_blockinv(int n, int bw, const fl
   blockinv_run(n, bw, r0, min(NBB, n - r0), lcol, xinv + (size_t)K * blk_elems(bw), blockIdx.y, gridDim.y);
 }
 
+// Batched: one CTA per problem (FP32 band factor on one SM), and the block
+// inverses of every problem (item = block K, part).
+__global__ void __launch_bounds__(FTF, 1) kb_coarse_factor(const BatchProb* __restrict__ P,
+                                                           const BatchItem* __restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  const BatchProb& q = P[it.prob];
+  if (q.ctl && *(volatile const int*)&q.ctl->done) return;
+  factor_run<float>(q.n_c, q.n_c, q.bw, q.lrow, q.lcol, q.dinv, q.dropped, 0, nullptr, 0);
+}
+__global__ void __launch_bounds__(256) kb_coarse_blockinv(const BatchProb* __restrict__ P,
+                                                          const BatchItem* __restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  const BatchProb& q = P[it.prob];
+  if (q.ctl && *(volatile const int*)&q.ctl->done) return;
+  const int r0 = it.bx * NBB;
+  blockinv_run(q.n_c, q.bw, r0, min(NBB, q.n_c - r0), q.lcol, q.xinv + (size_t)it.bx * blk_elems(q.bw), it.by, it.gy);
+}
+
 __host__ __device__ inline int big_stage_elems(int bw) { return bw * LDR + NBB * LDX; }
 
 // One step of the block substitution on the vectors tv (running right-hand
@@ -691,12 +709,11 @@ __device__ __forceinline__ void bsolve_band(const float* Lb, const float* yv, fl
 // k_coarse_solve.  Each step's R_K (U_K) and X_K (X_K^T) are staged by bulk
 // copies S - 1 steps ahead.
 template <int S>
-__global__ void __launch_bounds__(FTB) k_coarse_solve_big(int n, int bw, const float* __restrict__ xinv,
-                                                          const int* __restrict__ dropped,
-                                                          const double* __restrict__ res, double* __restrict__ x,
-                                                          const double* __restrict__ scale,
-                                                          double* __restrict__ a_out, unsigned long long* cstat,
-                                                          int first, const IterCtl* ctl, int* err) {
+__device__ __forceinline__ void solve_big_body(int n, int bw, const float* __restrict__ xinv,
+                                               const int* __restrict__ dropped, const double* __restrict__ res,
+                                               double* __restrict__ x, const double* __restrict__ scale,
+                                               double* __restrict__ a_out, unsigned long long* cstat, int first,
+                                               const IterCtl* ctl, int* err) {
   if (ctl && *(volatile const int*)&ctl->done) return;
   __shared__ int skip;
   if (threadIdx.x == 0) {
@@ -799,6 +816,27 @@ __global__ void __launch_bounds__(FTB) k_coarse_solve_big(int n, int bw, const f
     x[i] = xi;
     a_out[i] = scale[i] * xi;
   }
+}
+
+template <int S>
+__global__ void __launch_bounds__(FTB) k_coarse_solve_big(int n, int bw, const float* __restrict__ xinv,
+                                                          const int* __restrict__ dropped,
+                                                          const double* __restrict__ res, double* __restrict__ x,
+                                                          const double* __restrict__ scale,
+                                                          double* __restrict__ a_out, unsigned long long* cstat,
+                                                          int first, const IterCtl* ctl, int* err) {
+  solve_big_body<S>(n, bw, xinv, dropped, res, x, scale, a_out, cstat, first, ctl, err);
+}
+
+// Batched: one CTA per problem; first = the solve of b, else of the
+// refinement residual.
+template <int S>
+__global__ void __launch_bounds__(FTB) kb_coarse_solve_big(const BatchProb* __restrict__ P,
+                                                           const BatchItem* __restrict__ items, int first) {
+  const BatchItem it = items[blockIdx.x];
+  const BatchProb& q = P[it.prob];
+  solve_big_body<S>(q.n_c, q.bw, q.xinv, q.dropped, first ? q.b : q.res, q.x, q.scale, q.a, q.cstat, first, q.ctl,
+                    q.err);
 }
 
 // ---- two-sided factor and solve (FP32): two SMs, a cluster of 2 CTAs ----
@@ -1082,10 +1120,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FTB)
   }
 }
 
-size_t big_solve_smem_bytes(int n, int bw, int S) {
-  const size_t n4 = ((size_t)n + 3) / 4 * 4;
-  return (2 * n4 + NBB + (size_t)S * big_stage_elems(bw)) * sizeof(float) + (size_t)n * sizeof(int);
-}
 
 __device__ inline double warp_sum_d(double v) {
 #pragma unroll
@@ -1094,14 +1128,15 @@ __device__ inline double warp_sum_d(double v) {
 }
 
 // res = b - A x in FP64 (A symmetric band: column layout sband, row layout sbandR).
-__global__ void k_coarse_residual(int n, int bw, const double* __restrict__ sband,
-                                  const double* __restrict__ sbandR, const double* __restrict__ b,
-                                  const double* __restrict__ x, const int* __restrict__ dropped,
-                                  double* __restrict__ res, unsigned long long* cstat, const IterCtl* ctl) {
+__device__ __forceinline__ void coarse_residual_body(int n, int bw, const double* __restrict__ sband,
+                                                     const double* __restrict__ sbandR, const double* __restrict__ b,
+                                                     const double* __restrict__ x, const int* __restrict__ dropped,
+                                                     double* __restrict__ res, unsigned long long* cstat,
+                                                     const IterCtl* ctl, int bx) {
   if (ctl && *(volatile const int*)&ctl->done) return;
   if (*(volatile unsigned long long*)&cstat[2]) return;
   const int lane = threadIdx.x & 31;
-  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int row = (bx * blockDim.x + threadIdx.x) >> 5;
   if (row >= n) return;
   const int ldw = bw + 1;
   double acc = 0.0;
@@ -1120,11 +1155,32 @@ __global__ void k_coarse_residual(int n, int bw, const double* __restrict__ sban
   }
 }
 
+__global__ void k_coarse_residual(int n, int bw, const double* __restrict__ sband,
+                                  const double* __restrict__ sbandR, const double* __restrict__ b,
+                                  const double* __restrict__ x, const int* __restrict__ dropped,
+                                  double* __restrict__ res, unsigned long long* cstat, const IterCtl* ctl) {
+  coarse_residual_body(n, bw, sband, sbandR, b, x, dropped, res, cstat, ctl, blockIdx.x);
+}
+__global__ void kb_coarse_residual(const BatchProb* __restrict__ P, const BatchItem* __restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  const BatchProb& q = P[it.prob];
+  coarse_residual_body(q.n_c, q.bw, q.sband, q.sband + (size_t)q.n_c * (q.bw + 1), q.b, q.x, q.dropped, q.res,
+                       q.cstat, q.ctl, it.bx);
+}
+
 }  // namespace
+
+size_t big_solve_smem_bytes(int n, int bw, int S) {
+  const size_t n4 = ((size_t)n + 3) / 4 * 4;
+  return (2 * n4 + NBB + (size_t)S * big_stage_elems(bw)) * sizeof(float) + (size_t)n * sizeof(int);
+}
 
 cudaError_t configure_coarse_solve(int max_smem) {
   cudaError_t e;
   if ((e = set_max_dynamic_smem(k_coarse_factor_2s, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(kb_coarse_factor, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(kb_coarse_solve_big<2>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(kb_coarse_solve_big<3>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_coarse_solve_2s<2>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_coarse_solve_2s<3>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_coarse_factor<float>, max_smem)) != cudaSuccess) return e;
@@ -1205,6 +1261,30 @@ cudaError_t launch_coarse_solve(cudaStream_t s, int n, int bw, bool fp64, const 
                                                dropped, res, x, scale, a_out, cstat, first ? 1 : 0, ctl, err);
   return cudaGetLastError();
 }
+
+cudaError_t launch_batch_factor(cudaStream_t s, size_t smem, const BatchProb* P, const BatchItem* it, int n) {
+  if (n <= 0) return cudaSuccess;
+  kb_coarse_factor<<<n, FTF, smem, s>>>(P, it);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_blockinv(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n) {
+  if (n <= 0) return cudaSuccess;
+  kb_coarse_blockinv<<<n, 256, 0, s>>>(P, it);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_solve(cudaStream_t s, int stages, size_t smem, const BatchProb* P, const BatchItem* it,
+                               int n, bool first) {
+  if (n <= 0) return cudaSuccess;
+  if (stages >= 3) kb_coarse_solve_big<3><<<n, FTB, smem, s>>>(P, it, first ? 1 : 0);
+  else kb_coarse_solve_big<2><<<n, FTB, smem, s>>>(P, it, first ? 1 : 0);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_coarse_residual(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n) {
+  if (n <= 0) return cudaSuccess;
+  kb_coarse_residual<<<n, 256, 0, s>>>(P, it);
+  return cudaGetLastError();
+}
+int coarse_residual_blocks(int n) { return (int)(((size_t)n * 32 + 255) / 256); }
 
 cudaError_t launch_coarse_residual(cudaStream_t s, int n, int bw, const double* sband, const double* b,
                                    const double* x, const int* dropped, double* res, unsigned long long* cstat,

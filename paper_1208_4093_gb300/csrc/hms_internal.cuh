@@ -175,6 +175,70 @@ cudaError_t launch_coarse_solve_big(cudaStream_t s, int stages, int n, int bw, c
 cudaError_t launch_coarse_residual(cudaStream_t s, int n, int bw, const double* sband, const double* b,
                                    const double* x, const int* dropped, double* res, unsigned long long* cstat,
                                    const IterCtl* ctl);
+// ---- lockstep batches (batch.cu drives them): one launch per step covers the
+// work items of every problem of a batch.  A problem's per-iteration buffers:
+struct BatchProb {
+  LatView lv;
+  double2* u[2];
+  double2* p;
+  double2* r;
+  void* delta;
+  double* a;
+  double* P;
+  double* partials;
+  unsigned* ticket;
+  IterCtl* ctl;
+  double* hist;
+  int hist_cap;
+  int* err;
+  const long long* set_off;
+  const double* f64;
+  const float* f32;
+  void* yscratch;
+  const double* slots_base;
+  double* slots_it;
+  double* band;
+  double* sband;  // column layout, then row layout
+  double* scale;
+  double* b;
+  double* x;
+  double* res;
+  float* lrow;
+  float* lcol;
+  float* dinv;
+  float* xinv;
+  int* dropped;
+  unsigned long long* cstat;
+  int n_c, bw;
+};
+// One CTA of a batched launch: the problem and the block index (bx, by) of the
+// problem's own launch of that kernel, whose grid is gx x gy.
+struct BatchItem {
+  int prob, bx, by, gx, gy;
+};
+cudaError_t launch_batch_update_residual(cudaStream_t s, bool fp32, const BatchProb* P, const BatchItem* it, int n,
+                                         int k);
+cudaError_t launch_batch_relax(cudaStream_t s, bool fp32, int threads, size_t smem, const BatchProb* P,
+                               const BatchItem* it, int n);
+cudaError_t launch_batch_slots(cudaStream_t s, bool fp32, size_t smem, const BatchProb* P, const BatchItem* it,
+                               int n);
+cudaError_t launch_batch_band(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n);
+cudaError_t launch_batch_diag(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n);
+cudaError_t launch_batch_set_drops(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n);
+cudaError_t launch_batch_scale_band(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n);
+cudaError_t launch_batch_factor(cudaStream_t s, size_t smem, const BatchProb* P, const BatchItem* it, int n);
+cudaError_t launch_batch_blockinv(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n);
+cudaError_t launch_batch_solve(cudaStream_t s, int stages, size_t smem, const BatchProb* P, const BatchItem* it,
+                               int n, bool first);
+cudaError_t launch_batch_coarse_residual(cudaStream_t s, const BatchProb* P, const BatchItem* it, int n);
+// grids of the per-problem launches the batched ones stand for
+int update_residual_grid_x(const LatView& lv);
+int update_residual_grid_y(const LatView& lv);
+int coarse_grid_for(size_t n);   // 256-thread CTAs of a grid-stride kernel over n entries
+int coarse_residual_blocks(int n);
+int set_drops_blocks(int nsets);
+size_t big_solve_smem_bytes(int n, int bw, int S);
+
 // two-sided FP32 factor and solve (coarse_solve.cu): top [0, m[0]), separator
 // [m[0], m[0] + s), bottom (m[1] rows, reversed frame); per side its row band,
 // factor, drop flags, separator buffers and 64-row block matrices

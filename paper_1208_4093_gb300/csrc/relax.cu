@@ -156,12 +156,19 @@ __device__ inline void rows_times(const T* M, const T* v, int nb, Fetch fetch, O
   }
 }
 
+// Entries of one set's slice of the y scratch (the widest, tallest set).
+__host__ __device__ inline long long y_stride(const LatView& lv) {
+  const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
+  const int h = lv.sy < lv.ny ? lv.sy : lv.ny;
+  return 2LL * w * h;
+}
+
+// The kernel body for set I.
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __restrict__ set_off,
-                                              const T* __restrict__ fac, const double2* __restrict__ r,
-                                              T* __restrict__ delta, double* __restrict__ P,
-                                              T* __restrict__ yglob, long long ystride, const IterCtl* ctl,
-                                              int* err) {
+__device__ __forceinline__ void relax_body(const LatView lv, const long long* __restrict__ set_off,
+                                           const T* __restrict__ fac, const double2* __restrict__ r,
+                                           T* __restrict__ delta, double* __restrict__ P, T* __restrict__ yglob,
+                                           long long ystride, const IterCtl* ctl, int* err, int I) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ uint64_t bars[NSLOT];
   __shared__ double pred[(VL / 32) * NMODES];
@@ -170,7 +177,6 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
 
   using T2 = typename Vec2<T>::type;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int I = blockIdx.x;
   const int Ix = I % lv.Mx, Iy = I / lv.Mx;
   const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
   const int w = min(lv.sx, lv.nx - i0), h = min(lv.sy, lv.ny - j0);
@@ -317,6 +323,27 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
   }
 }
 
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __restrict__ set_off,
+                                              const T* __restrict__ fac, const double2* __restrict__ r,
+                                              T* __restrict__ delta, double* __restrict__ P,
+                                              T* __restrict__ yglob, long long ystride, const IterCtl* ctl,
+                                              int* err) {
+  relax_body<T, NT>(lv, set_off, fac, r, delta, P, yglob, ystride, ctl, err, blockIdx.x);
+}
+
+// Batched: the sets of every problem of a batch.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) kb_relax(const BatchProb* __restrict__ Pb, const BatchItem* __restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  const BatchProb& q = Pb[it.prob];
+  const T* fac;
+  if constexpr (sizeof(T) == 4) fac = q.f32;
+  else fac = q.f64;
+  relax_body<T, NT>(q.lv, q.set_off, fac, q.r, (T*)q.delta, q.P, (T*)q.yscratch, y_stride(q.lv), q.ctl, q.err,
+                    it.bx);
+}
+
 }  // namespace
 
 size_t relax_smem_bytes(const LatView& lv, bool fp32) {
@@ -325,11 +352,7 @@ size_t relax_smem_bytes(const LatView& lv, bool fp32) {
               : relax_layout<double>(2 * w).total_elems * sizeof(double);
 }
 
-long long relax_y_stride(const LatView& lv) {
-  const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
-  const int h = lv.sy < lv.ny ? lv.sy : lv.ny;
-  return 2LL * w * h;
-}
+long long relax_y_stride(const LatView& lv) { return y_stride(lv); }
 
 cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
                          const double* f64, const float* f32, const double2* r, void* delta,
@@ -353,8 +376,29 @@ cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set
   return cudaGetLastError();
 }
 
+cudaError_t launch_batch_relax(cudaStream_t s, bool fp32, int threads, size_t smem, const BatchProb* P,
+                               const BatchItem* it, int n) {
+  if (n <= 0) return cudaSuccess;
+  auto go = [&](auto nt) {
+    constexpr int NT = decltype(nt)::value;
+    if (fp32) kb_relax<float, NT><<<n, NT, smem, s>>>(P, it);
+    else kb_relax<double, NT><<<n, NT, smem, s>>>(P, it);
+  };
+  if (threads == 64) go(std::integral_constant<int, 64>());
+  else if (threads == 128) go(std::integral_constant<int, 128>());
+  else if (threads == 256) go(std::integral_constant<int, 256>());
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 cudaError_t configure_relax(int max_smem) {
   cudaError_t e;
+  if ((e = set_max_dynamic_smem(kb_relax<float, 64>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(kb_relax<float, 128>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(kb_relax<float, 256>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(kb_relax<double, 64>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(kb_relax<double, 128>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(kb_relax<double, 256>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_relax<float, 64>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_relax<float, 128>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_relax<float, 256>, max_smem)) != cudaSuccess) return e;

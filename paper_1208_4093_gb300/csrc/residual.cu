@@ -79,12 +79,13 @@ __device__ inline double2 apply_update(const LatView& lv, double2 v, int i, int 
   return v;
 }
 
+// The kernel body for tile (bx, by) of a gx x gy grid (the whole lattice).
 template <typename DT>
-__global__ void __launch_bounds__(NT) k_update_residual(
-    LatView lv, const double2* __restrict__ u_in, double2* __restrict__ u_out,
+__device__ __forceinline__ void update_residual_body(
+    const LatView lv, const double2* __restrict__ u_in, double2* __restrict__ u_out,
     const double2* __restrict__ p, const DT* __restrict__ delta, const double* __restrict__ a,
     double2* __restrict__ r, double* __restrict__ partials, unsigned* ticket, double* norms_out,
-    IterCtl* ctl, double* hist, int hist_cap) {
+    IterCtl* ctl, double* hist, int hist_cap, int bx, int by, int gx, int gy) {
   __shared__ double2 U[TY + 2][TX + 2];
   __shared__ double sred[3 * (NT + 1)];
   __shared__ bool last;
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(NT) k_update_residual(
     t = *(volatile int*)&ctl->t;
   }
   const bool upd = (a != nullptr) && (t > 0 || ctl == nullptr);
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i0 = bx * TX, j0 = by * TY;
   const int tid = threadIdx.x;
 
   for (int idx = tid; idx < (TX + 2) * (TY + 2); idx += NT) {
@@ -145,8 +146,8 @@ __global__ void __launch_bounds__(NT) k_update_residual(
     s[2] = fma(uc.x, pn.x + rn.x, uc.y * (pn.y + rn.y));
   }
   block_sum<3>(s, sred);
-  const unsigned nblocks = gridDim.x * gridDim.y;
-  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const unsigned nblocks = (unsigned)(gx * gy);
+  const unsigned bid = (unsigned)(by * gx + bx);
   if (tid == 0) {
     partials[3 * (size_t)bid + 0] = s[0];
     partials[3 * (size_t)bid + 1] = s[1];
@@ -197,6 +198,27 @@ __global__ void __launch_bounds__(NT) k_update_residual(
   }
 }
 
+template <typename DT>
+__global__ void __launch_bounds__(NT) k_update_residual(
+    LatView lv, const double2* __restrict__ u_in, double2* __restrict__ u_out,
+    const double2* __restrict__ p, const DT* __restrict__ delta, const double* __restrict__ a,
+    double2* __restrict__ r, double* __restrict__ partials, unsigned* ticket, double* norms_out,
+    IterCtl* ctl, double* hist, int hist_cap) {
+  update_residual_body<DT>(lv, u_in, u_out, p, delta, a, r, partials, ticket, norms_out, ctl, hist, hist_cap,
+                           blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+}
+
+// Batched: update k of a CUDA-graph round (u ping-pongs between u[k & 1] and
+// u[(k + 1) & 1]) for the tiles of every problem of a batch.
+template <typename DT>
+__global__ void __launch_bounds__(NT) kb_update_residual(const BatchProb* __restrict__ P,
+                                                         const BatchItem* __restrict__ items, int k) {
+  const BatchItem it = items[blockIdx.x];
+  const BatchProb& q = P[it.prob];
+  update_residual_body<DT>(q.lv, q.u[k & 1], q.u[(k + 1) & 1], q.p, (const DT*)q.delta, q.a, q.r, q.partials,
+                           q.ticket, nullptr, q.ctl, q.hist, q.hist_cap, it.bx, it.by, it.gx, it.gy);
+}
+
 // Masks the loads on constrained DOFs and computes ||p||_1, ||p||_2 into ctl.
 __global__ void __launch_bounds__(NT) k_load_norms(LatView lv, double2* __restrict__ p,
                                                     double* __restrict__ partials, unsigned* ticket,
@@ -243,6 +265,16 @@ __global__ void __launch_bounds__(NT) k_load_norms(LatView lv, double2* __restri
 
 int update_residual_blocks(const LatView& lv) {
   return ((lv.nx + TX - 1) / TX) * ((lv.ny + TY - 1) / TY);
+}
+int update_residual_grid_x(const LatView& lv) { return (lv.nx + TX - 1) / TX; }
+int update_residual_grid_y(const LatView& lv) { return (lv.ny + TY - 1) / TY; }
+
+cudaError_t launch_batch_update_residual(cudaStream_t s, bool fp32, const BatchProb* P, const BatchItem* it, int n,
+                                         int k) {
+  if (n <= 0) return cudaSuccess;
+  if (fp32) kb_update_residual<float2><<<n, NT, 0, s>>>(P, it, k);
+  else kb_update_residual<double2><<<n, NT, 0, s>>>(P, it, k);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_update_residual(cudaStream_t s, const LatView& lv, const double2* u_in,

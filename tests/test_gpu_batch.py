@@ -88,3 +88,60 @@ def test_batch_rejects_duplicates_and_foreign_problems(hms_ctx, batch):
         capi.hms_context_destroy(other)
     # an empty batch is a no-op
     capi.hms_solve_batch(hms_ctx, [], [], [])
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_lockstep_equals_streams_and_solo(hms_ctx, prec):
+    """The lockstep engine (one launch per step over a work list of every
+    running problem's tiles) gives the stream engine's and the solo solves'
+    bits, iteration counts included; lattices finish at different rounds and
+    load vectors restart inside the batch."""
+    from paper_1208_4093_gb300 import capi
+    lats = batched_lattices(count=12, seed=13, side_min=8, side_max=160, nrhs_max=3)
+    prs = [capi.hms_problem_create(hms_ctx, l.nx, l.ny, 32, 32, precision=prec, tol=TOL, max_iter=4000,
+                                   coarse_factor=4) for l in lats]
+    try:
+        loads = [l.load_array() for l in lats]
+        nrhs = sum(l.nrhs for l in lats)
+        res = {}
+        for mode in (capi.HMS_BATCH_LOCKSTEP, capi.HMS_BATCH_STREAMS):
+            capi.hms_context_set_batch_mode(hms_ctx, mode)
+            outs = [np.empty_like(p) for p in loads]
+            its = np.zeros(nrhs, np.int32)
+            capi.hms_solve_batch(hms_ctx, prs, loads, outs, iters=its)
+            res[mode] = (outs, its)
+        capi.hms_context_set_batch_mode(hms_ctx, capi.HMS_BATCH_AUTO)
+        (ol, il), (os_, is_) = res[capi.HMS_BATCH_LOCKSTEP], res[capi.HMS_BATCH_STREAMS]
+        assert np.array_equal(il, is_)
+        k = 0
+        for l, pr, p, a, b in zip(lats, prs, loads, ol, os_):
+            assert np.array_equal(a, b), (l.nx, l.ny)
+            solo = np.empty_like(p)
+            sits = np.zeros(l.nrhs, np.int32)
+            capi.hms_solve(hms_ctx, pr, p, solo, iters=sits)
+            assert np.array_equal(a, solo) and np.array_equal(il[k:k + l.nrhs], sits)
+            k += l.nrhs
+    finally:
+        capi.hms_context_set_batch_mode(hms_ctx, capi.HMS_BATCH_AUTO)
+        for pr in prs:
+            capi.hms_problem_destroy(pr)
+
+
+def test_lockstep_refuses_mixed_precisions(hms_ctx):
+    from paper_1208_4093_gb300 import capi
+    a = capi.hms_problem_create(hms_ctx, 40, 40, 16, 16, precision=0, coarse_factor=4)
+    b = capi.hms_problem_create(hms_ctx, 40, 40, 16, 16, precision=1, coarse_factor=4)
+    try:
+        p = np.zeros((1, 2 * 40 * 40))
+        capi.hms_context_set_batch_mode(hms_ctx, capi.HMS_BATCH_LOCKSTEP)
+        with pytest.raises(capi.HmsError) as e:
+            capi.hms_solve_batch(hms_ctx, [a, b], [p, p], [np.empty_like(p), np.empty_like(p)])
+        assert e.value.status == capi.HMS_ERR_ARG
+        capi.hms_context_set_batch_mode(hms_ctx, capi.HMS_BATCH_AUTO)
+        capi.hms_solve_batch(hms_ctx, [a, b], [p, p], [np.empty_like(p), np.empty_like(p)])  # streams
+        with pytest.raises(capi.HmsError):
+            capi.hms_context_set_batch_mode(hms_ctx, 7)
+    finally:
+        capi.hms_context_set_batch_mode(hms_ctx, capi.HMS_BATCH_AUTO)
+        capi.hms_problem_destroy(a)
+        capi.hms_problem_destroy(b)
