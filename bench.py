@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="time the batched uneven-lattice workload instead (separate JSON line)")
     ap.add_argument("--batched-count", type=int, default=256)
+    ap.add_argument("--nir-sweep", action="store_true",
+                    help="NIR (updates to R1 < 1e-8) versus set size at 8 x 8 sets, and versus the number "
+                         "of 32 x 32-node sets (the shapes of the paper's Tests 2 and 3), FP64, 4 loadings")
     ap.add_argument("--serve", type=int, default=0, metavar="N",
                     help="serve N requests of the serving workload instead (separate JSON line)")
     ap.add_argument("--serve-max-active", type=int, default=4,
@@ -360,6 +363,46 @@ def run_batched(args):
         "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / med, "same_as_sequential": same}))
 
 
+# ---------------------------------------------------------------- NIR sweeps
+def run_nir_sweep(args):
+    """The number of iterations required (NIR, upper-level updates to R1 < 1e-8
+    by Eq. 19) and the time per update, averaged over four random loadings
+    (seeds 0-3), FP64 form, EA = 1, bottom row clamped:
+      test 2 shape: 8 x 8 sets of s x s nodes, s = 8 .. 64 (DOFs per set 128 .. 8192);
+      test 3 shape: 32 x 32-node sets, 2 .. 1024 sets.
+    The paper's own sweeps (Figs. 6-7: up to 980 000 DOFs per set, 2 .. 2000
+    sets) are printed without values, so only the shapes compare."""
+    import numpy as np
+    from paper_1208_4093_gb300 import capi
+    from workloads import loads
+    ctx = capi.hms_context_create(0)
+
+    def nir(nx, ny, sx, sy):
+        pr = capi.hms_problem_create(ctx, nx, ny, sx, sy, precision=capi.HMS_FP64, tol=TOL, max_iter=20000)
+        its, ms = [], []
+        try:
+            for seed in range(4):
+                p = loads(nx, ny, seed).reshape(1, -1)
+                u = np.empty_like(p)
+                it = np.zeros(1, np.int32)
+                t0 = time.perf_counter()
+                capi.hms_solve(ctx, pr, p, u, iters=it)
+                ms.append((time.perf_counter() - t0) * 1e3)
+                its.append(int(it[0]))
+        finally:
+            capi.hms_problem_destroy(pr)
+        return {"nx": nx, "ny": ny, "set": [sx, sy], "sets": -(-nx // sx) * -(-ny // sy),
+                "dofs_per_set": 2 * sx * sy, "dofs": 2 * nx * ny, "nir": its, "nir_mean": float(np.mean(its)),
+                "ms_per_update": float(np.sum(ms) / max(1, np.sum(its)))}
+
+    test2 = [nir(8 * s, 8 * s, s, s) for s in (8, 12, 16, 24, 32, 48, 64)]
+    test3 = [nir(32 * mx, 32 * my, 32, 32) for mx, my in ((1, 2), (2, 2), (2, 4), (4, 4), (4, 8), (8, 8), (8, 16),
+                                                           (16, 16), (16, 32), (20, 50))]
+    capi.hms_context_destroy(ctx)
+    print(json.dumps({"metric": "NIR to R1 < 1e-8 (FP64 form, mean of 4 loadings)", "unit": "updates",
+                      "test2_fixed_sets_8x8": test2, "test3_sets_of_32x32": test3}))
+
+
 # ---------------------------------------------------------------- serving
 def run_serve(args):
     """Requests arrive by a Poisson process (mean 200 per second) with
@@ -604,6 +647,8 @@ def main():
             run_ncu_case(args)
         elif args.batched:
             run_batched(args)
+        elif args.nir_sweep:
+            run_nir_sweep(args)
         elif args.serve:
             run_serve(args)
         elif args.impl == "reference":
