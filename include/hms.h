@@ -103,6 +103,11 @@ typedef struct {
                                 precision on a context times each size on its own factors
                                 and the context keeps the fastest for that shape.  Results
                                 are bitwise the same for every size */
+  int32_t relax_copies;      /* bulk copies per factor matrix in the FP64 relaxation: 1, or
+                                2 (the rows of the outer and of the inner row pairs apart,
+                                half the shared memory per CTA, so two CTAs share an SM;
+                                even set widths >= 6 only), or 0 = with relax_threads = 0
+                                timed together with it, else 1.  Same results either way */
 } hms_options;
 
 /* Context: one device, one CUDA stream.  device = CUDA ordinal. */
@@ -134,8 +139,10 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out);
 size_t hms_problem_device_bytes(const hms_problem* pr);
 /* Milliseconds the setup kernels took (CUDA events). */
 double hms_problem_setup_ms(const hms_problem* pr);
-/* CTA size the relaxation of pr runs with (relax_threads, or the autotuned choice). */
+/* CTA size and copies per matrix the relaxation of pr runs with (the options,
+ * or the autotuned choice). */
 int32_t hms_problem_relax_threads(const hms_problem* pr);
+int32_t hms_problem_relax_copies(const hms_problem* pr);
 
 /* The whole iteration (Fig. 3) for nrhs load vectors, each from u0 (NULL =
  * zero): loads [nrhs][2*nx*ny], u0 and u_out likewise.  hist (nullable)

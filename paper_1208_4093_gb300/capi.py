@@ -54,7 +54,8 @@ class LatticeDesc(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("coarse_solves", ctypes.c_int32), ("batch", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("coarse_factor", ctypes.c_int32), ("relax_threads", ctypes.c_int32)]
+                ("coarse_factor", ctypes.c_int32), ("relax_threads", ctypes.c_int32),
+                ("relax_copies", ctypes.c_int32)]
 
 
 _lib = None
@@ -85,6 +86,7 @@ def lib():
         "hms_problem_device_bytes": (ctypes.c_size_t, [_P]),
         "hms_problem_setup_ms": (ctypes.c_double, [_P]),
         "hms_problem_relax_threads": (ctypes.c_int32, [_P]),
+        "hms_problem_relax_copies": (ctypes.c_int32, [_P]),
         "hms_solve": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, ctypes.c_int32]),
         "hms_kernel_times": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
         "hms_residual": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32]),
@@ -120,7 +122,7 @@ def exported_symbols():
             "hms_update_residual", "hms_relax", "hms_coarse_matrix", "hms_coarse_solve",
             "hms_residual_noalloc", "hms_solve_batch", "hms_problem_estimate_bytes", "hms_server_create",
             "hms_server_destroy", "hms_server_submit", "hms_server_step", "hms_server_take", "hms_problem_clone",
-            "hms_problem_relax_threads", "hms_context_set_batch_mode"]
+            "hms_problem_relax_threads", "hms_context_set_batch_mode", "hms_problem_relax_copies"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -187,7 +189,7 @@ def hms_last_error(ctx) -> str:
 
 def _desc_opts(nx, ny, set_sx, set_sy, bar_length=1.0, ea=None, ea_uniform=1.0, fixed=None, fix_bottom_edge=1,
                precision=HMS_FP64, tol=1e-8, max_iter=1000, coarse_solves=0, batch=0, profile=0, coarse_factor=0,
-               relax_threads=0):
+               relax_threads=0, relax_copies=0):
     """LatticeDesc and Options structs (plus the arrays they point to, kept alive by the caller)."""
     ea_a = None if ea is None else np.ascontiguousarray(ea, dtype=np.float64)
     fx_a = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
@@ -199,14 +201,14 @@ def _desc_opts(nx, ny, set_sx, set_sy, bar_length=1.0, ea=None, ea_uniform=1.0, 
                     float(ea_uniform), None if fx_a is None else fx_a.ctypes.data, int(fix_bottom_edge),
                     int(set_sx), int(set_sy))
     o = Options(int(precision), float(tol), int(max_iter), int(coarse_solves), int(batch), int(profile),
-                int(coarse_factor), int(relax_threads))
+                int(coarse_factor), int(relax_threads), int(relax_copies))
     return d, o, (ea_a, fx_a)
 
 
 def hms_problem_create(ctx, nx, ny, set_sx, set_sy, **kw):
     """kw: bar_length, ea (host float64 [3, ny, nx]), ea_uniform, fixed (host uint8
     [ny, nx, 2]), fix_bottom_edge, precision, tol, max_iter, coarse_solves, batch,
-    profile, coarse_factor, relax_threads."""
+    profile, coarse_factor, relax_threads, relax_copies."""
     d, o, keep = _desc_opts(nx, ny, set_sx, set_sy, **kw)
     h = _P()
     _check(ctx, lib().hms_problem_create(ctx, ctypes.byref(d), ctypes.byref(o), ctypes.byref(h)))
@@ -238,6 +240,10 @@ def hms_problem_setup_ms(pr) -> float:
 
 def hms_problem_relax_threads(pr) -> int:
     return int(lib().hms_problem_relax_threads(pr))
+
+
+def hms_problem_relax_copies(pr) -> int:
+    return int(lib().hms_problem_relax_copies(pr))
 
 
 def hms_solve(ctx, pr, loads, u_out, u0=None, hist=None, iters=None, allow_no_convergence=False):

@@ -43,6 +43,7 @@ struct hms_problem {
   bool coarse_fp64 = false;  // factor of the upper-level system in FP64 (else FP32 + FP64 refinement)
   double tol = 1e-8;
   int relax_threads = 256;   // CTA size of the relaxation
+  int relax_chunks = 1;      // bulk copies per factor matrix in the relaxation (2: half the shared memory)
   int n_c = 0, bw = 0;
   size_t bytes = 0;
   std::vector<void*> allocs;
@@ -211,7 +212,7 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
   if (e != cudaSuccess) return e;
   mark();
   e = launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, pr->ctl, pr->err,
-                   pr->relax_threads);
+                   pr->relax_threads, pr->relax_chunks);
   if (e != cudaSuccess) return e;
   mark();
   e = launch_coarse_slots(s, lv, pr->delta, fp32(pr), false, pr->slots_it, pr->ctl);
@@ -443,6 +444,7 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
   pr->big_stages = src->big_stages;
   pr->cluster_factor = src->cluster_factor;
   pr->relax_threads = src->relax_threads;
+  pr->relax_chunks = src->relax_chunks;
   pr->two_sided = src->two_sided;
   pr->ts = TwoSided();
   pr->ts.m[0] = src->ts.m[0];
@@ -477,6 +479,7 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
 
 size_t hms_problem_device_bytes(const hms_problem* pr) { return pr ? pr->bytes : 0; }
 int32_t hms_problem_relax_threads(const hms_problem* pr) { return pr ? pr->relax_threads : 0; }
+int32_t hms_problem_relax_copies(const hms_problem* pr) { return pr ? pr->relax_chunks : 0; }
 double hms_problem_setup_ms(const hms_problem* pr) { return pr ? (double)pr->setup_ms : 0.0; }
 
 // The per-instance buffers of a problem whose configuration (lv, n_c, bw,
@@ -571,13 +574,14 @@ static cudaError_t alloc_instance(hms_problem* pr) {
 // of each size on its own factors (r = 0; the kernel's time does not depend
 // on the values) and the context keeps the fastest for that shape.  The sizes
 // give bitwise the same results, so the choice only changes the time.
-static cudaError_t autotune_relax(hms_problem* pr) {
+static cudaError_t autotune_relax(hms_problem* pr, int copies) {
   hms_context* c = pr->ctx;
   const LatView& lv = pr->lv;
-  const auto key = std::make_tuple(std::min(lv.sx, lv.nx), std::min(lv.sy, lv.ny), pr->precision);
+  const auto key = std::make_tuple(std::min(lv.sx, lv.nx), std::min(lv.sy, lv.ny), pr->precision * 10 + copies);
   const auto it = c->relax_tuned.find(key);
   if (it != c->relax_tuned.end()) {
-    pr->relax_threads = it->second;
+    pr->relax_threads = it->second / 10;
+    pr->relax_chunks = it->second % 10;
     return cudaSuccess;
   }
   cudaStream_t s = c->stream;
@@ -590,29 +594,35 @@ static cudaError_t autotune_relax(hms_problem* pr) {
     return e;
   }
   float best = 0.f;
-  int best_nt = 256;
-  for (int nt : {64, 128, 256}) {
-    auto run = [&]() {
-      return launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr,
-                          pr->err, nt);
-    };
-    if ((e = run()) != cudaSuccess) break;
-    if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = run();
-    if (e != cudaSuccess || (e = cudaEventRecord(e1, s)) != cudaSuccess) break;
-    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (nt == 64 || ms < best) {
-      best = ms;
-      best_nt = nt;
+  int best_nt = 256, best_nc = 1;
+  bool first = true;
+  const int max_nc = copies != 0 ? copies : (relax_chunks_possible(lv, fp32(pr)) ? 2 : 1);
+  for (int nc = copies != 0 ? copies : 1; nc <= max_nc && e == cudaSuccess; ++nc)
+    for (int nt : {64, 128, 256}) {
+      auto run = [&]() {
+        return launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr,
+                            pr->err, nt, nc);
+      };
+      if ((e = run()) != cudaSuccess) break;
+      if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = run();
+      if (e != cudaSuccess || (e = cudaEventRecord(e1, s)) != cudaSuccess) break;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (first || ms < best) {
+        best = ms;
+        best_nt = nt;
+        best_nc = nc;
+        first = false;
+      }
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return e;
   pr->relax_threads = best_nt;
-  c->relax_tuned[key] = best_nt;
+  pr->relax_chunks = best_nc;
+  c->relax_tuned[key] = best_nt * 10 + best_nc;
   return cudaSuccess;
 }
 
@@ -631,6 +641,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (o->coarse_factor < 0 || o->coarse_factor > 5) return fail(c, HMS_ERR_ARG, "coarse_factor must be in 0..5");
   if (o->relax_threads != 0 && o->relax_threads != 64 && o->relax_threads != 128 && o->relax_threads != 256)
     return fail(c, HMS_ERR_ARG, "relax_threads must be 0, 64, 128 or 256");
+  if (o->relax_copies < 0 || o->relax_copies > 2) return fail(c, HMS_ERR_ARG, "relax_copies must be 0, 1 or 2");
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
 
@@ -780,8 +791,19 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
       return st;
     }
   }
-  if (o->relax_threads != 0) pr->relax_threads = o->relax_threads;
-  else CKP(autotune_relax(pr));
+  if (o->relax_copies == 2 && !relax_chunks_possible(lv, fp32(pr))) {
+    hms_problem_destroy(pr);
+    return fail(c, HMS_ERR_ARG, "relax_copies = 2 needs the FP64 path and even set widths >= 6");
+  }
+  if (o->relax_threads != 0 && o->relax_copies != 0) {
+    pr->relax_threads = o->relax_threads;
+    pr->relax_chunks = o->relax_copies;
+  } else if (o->relax_threads != 0) {
+    pr->relax_threads = o->relax_threads;
+    pr->relax_chunks = 1;
+  } else {
+    CKP(autotune_relax(pr, o->relax_copies));
+  }
   if (!pr->profile) {
     hms_status st = build_graph(pr);
     if (st != HMS_OK) {
@@ -1176,11 +1198,13 @@ static hms_status solve_batch_lockstep(hms_context* c, int32_t count, hms_proble
   // one launch shape for all: the relaxation CTA size gives the same bits at
   // any size; the block solve's pipeline depth does not change its arithmetic
   const int rthreads = probs[0]->relax_threads;
+  int rchunks = 2;
+  for (hms_problem* pr : probs) rchunks = std::min(rchunks, pr->relax_chunks);
   int stages = 3;
   size_t sm_relax = 0, sm_slots = 0, sm_factor = 0, sm_solve = 0;
   for (hms_problem* pr : probs) stages = std::min(stages, pr->big_stages);
   for (hms_problem* pr : probs) {
-    sm_relax = std::max(sm_relax, relax_smem_bytes(pr->lv, f32));
+    sm_relax = std::max(sm_relax, relax_smem_bytes(pr->lv, f32, rchunks));
     sm_slots = std::max(sm_slots, coarse_slots_smem(pr->lv));
     sm_factor = std::max(sm_factor, coarse_factor_smem_bytes(pr->n_c, pr->bw, false));
     sm_solve = std::max(sm_solve, big_solve_smem_bytes(pr->n_c, pr->bw, stages));
@@ -1264,7 +1288,7 @@ static hms_status solve_batch_lockstep(hms_context* c, int32_t count, hms_proble
       cudaError_t e = cudaSuccess;
       for (int k = 0; k < 16 && e == cudaSuccess; ++k) {
         e = launch_batch_update_residual(s, f32, P, L(BL_K1), N(BL_K1), k);
-        if (e == cudaSuccess) e = launch_batch_relax(s, f32, rthreads, sm_relax, P, L(BL_SETS), N(BL_SETS));
+        if (e == cudaSuccess) e = launch_batch_relax(s, f32, rthreads, rchunks, sm_relax, P, L(BL_SETS), N(BL_SETS));
         if (e == cudaSuccess) e = launch_batch_slots(s, f32, sm_slots, P, L(BL_SETS), N(BL_SETS));
         if (e == cudaSuccess) e = launch_batch_band(s, P, L(BL_BAND), N(BL_BAND));
         if (e == cudaSuccess) e = launch_batch_diag(s, P, L(BL_DIAG), N(BL_DIAG));
@@ -1376,7 +1400,7 @@ hms_status hms_relax(hms_problem* pr, const double* r, double* delta, double* P,
   CKC(c, cudaMemcpyAsync(pr->r, r, vb, kind_in(mem_kind), s));
   CKC(c, launch_mask_u(s, pr->lv, pr->r));
   CKC(c, launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr, pr->err,
-                      pr->relax_threads));
+                      pr->relax_threads, pr->relax_chunks));
   if (fp32(pr)) {
     CKC(c, launch_f2d(s, (const float*)pr->delta, (double*)pr->u[1], 2 * nn));
     CKC(c, cudaMemcpyAsync(delta, pr->u[1], vb, kind_out(mem_kind), s));

@@ -175,9 +175,13 @@ __device__ __forceinline__ void factor_run(int n, int npiv, int bw, T* __restric
           T av[4], xv[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
+            // kk = i - (k0 + cp) < 0 only in a short last block followed by
+            // rows that are no pivots (npiv < n): column k0 + cp is then right
+            // of row i's band, a window position never loaded, and X's zero
+            // there must not meet it (0 * NaN)
             const int kk = k1 + il[u] - k0 - cp;  // i - (k0 + cp)
             const int pos = ck0 + cp;
-            av[u] = (il[u] < np && kk <= bw) ? Aw[rowoff[u] + (pos >= lda ? pos - lda : pos)] : T(0);
+            av[u] = (il[u] < np && kk >= 0 && kk <= bw) ? Aw[rowoff[u] + (pos >= lda ? pos - lda : pos)] : T(0);
           }
 #pragma unroll
           for (int v = 0; v < 4; ++v) xv[v] = Xs[(4 * cq + v) * (NB + 1) + cp];
@@ -947,15 +951,19 @@ __global__ void __launch_bounds__(256) k_coarse_blockinv_2s(int s, int bws, cons
 struct SolveSide {
   const float* xinv;    // per-block matrices of the side's factor
   const int* dropped;   // drop flags of the side's frame
+  const float* lcol;    // the side's factor, column layout (side 1: L_MB^T x_M)
   int m;                // rows of the segment
 };
 
 // The block substitution of k_coarse_solve_big on each side's frame.  After
 // the forward steps over its segment, each side's separator rows hold b_M
-// minus its own segment's contribution; the two sides exchange them through
-// distributed shared memory (b_M - both contributions), then go on through
-// the separator and back.  Side 0 writes the top and the separator, side 1
-// the bottom.
+// minus its own segment's contribution; side 0 reads side 1's through
+// distributed shared memory (b_M - both contributions) and solves the
+// separator with its own factor of S, forward and back.  Side 1 then takes
+// x_M from side 0, subtracts L_MB^T x_M from its segment rows and goes back
+// through its segment.  One separator solution serves both sides, so they
+// agree even where the two frames' FP32 factors of S drop different pivots.
+// Side 0 writes the top and the separator, side 1 the bottom.
 template <int S>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FTB)
     k_coarse_solve_2s(int n, int s, int bws, SolveSide s0, SolveSide s1, const double* __restrict__ res,
@@ -1043,12 +1051,37 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FTB)
   }
   if (tid == 0)
     for (int o = 0; o < S - 1 && o < nops; ++o) issue(o);
+  const int oM = 2 * nblk - nbT;  // first backward op over the segment
   for (int o = 0; o < nops; ++o) {
     const bool fwd = o < nblk;
     const int K = fwd ? o : nops - 1 - o;
     int r0, r1;
     side_block(K, m, s, r0, r1);
     const int nr = r1 - r0;
+    if (o == oM) {
+      // side 0 holds x_M; side 1 takes it (both CTAs come here, aborted or not)
+      __syncthreads();
+      cl.sync();
+      if (rank == 1) {
+        const int on4 = (s0.m + s + 3) / 4 * 4;
+        const float* oyv = cl.map_shared_rank(ss, 0) + on4;
+        for (int i = tid; i < s; i += FTB) yv[m + i] = oyv[s0.m + s - 1 - i];
+      }
+      cl.sync();  // no reads of the other CTA's shared memory after this
+      if (rank == 1 && !abort_flag) {
+        // t_i -= sum_{j in M} L[j][i] x_j over the segment's last bws rows, one warp per row
+        const int ldw = bws + 1;
+        for (int i = max(0, m - bws) + warp; i < m; i += FTB / 32) {
+          float acc = 0.f;
+          for (int q = lane; q < s && m + q - i <= bws; q += 32)
+            acc = fmaf(sd.lcol[(size_t)i * ldw + (m + q - i)], yv[m + q], acc);
+#pragma unroll
+          for (int k = 16; k > 0; k >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, k);
+          if (lane == 0) tv[i] -= acc;
+        }
+        __syncthreads();
+      }
+    }
     if (o == nbT) {
       // exchange of the separator rows; both CTAs come here, aborted or not
       __syncthreads();
@@ -1084,7 +1117,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FTB)
       __syncthreads();
     }
     if (abort_flag) {
-      if (o >= nbT) break;
+      if (o >= oM) break;
       continue;
     }
     if (o == nblk) {
@@ -1094,10 +1127,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FTB)
     if (!mbar_wait_bounded(&bars[o % S], (uint32_t)((o / S) & 1))) abort_flag = 1;
     __syncthreads();
     if (abort_flag) {
-      if (o >= nbT) break;
+      if (o >= oM) break;
       continue;
     }
     if (tid == 32 && o + S - 1 < nops) issue(o + S - 1);
+    if (rank == 1 && K >= nbT) continue;  // the separator is side 0's (its copies still pass through)
     const float* Lb = ss + sbase + (size_t)(o % S) * stage;
     const float* Mx = Lb + xoff;
     bsolve_diag(Mx, tv, yv, sdrop, r0, nr, tid);
@@ -1348,7 +1382,7 @@ cudaError_t launch_coarse_solve_2s(cudaStream_t st, int n, const TwoSided& t, co
                                    const double* scale, double* a_out, int* dropped_out, unsigned long long* cstat,
                                    bool first, const IterCtl* ctl, int* err) {
   const int s = t.s, bws = s - 1;
-  const SolveSide a{t.xinv[0], t.dropped[0], t.m[0]}, b{t.xinv[1], t.dropped[1], t.m[1]};
+  const SolveSide a{t.xinv[0], t.dropped[0], t.lcol[0], t.m[0]}, b{t.xinv[1], t.dropped[1], t.lcol[1], t.m[1]};
   const size_t smem = big_solve_smem_bytes((t.m[0] > t.m[1] ? t.m[0] : t.m[1]) + s, bws, t.stages);
   if (t.stages >= 3)
     k_coarse_solve_2s<3><<<2, FTB, smem, st>>>(n, s, bws, a, b, res, x, scale, a_out, dropped_out, cstat,

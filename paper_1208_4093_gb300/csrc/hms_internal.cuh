@@ -142,8 +142,9 @@ cudaError_t launch_set_factor(cudaStream_t s, const LatView& lv, const long long
 // relax.cu
 cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
                          const double* f64, const float* f32, const double2* r, void* delta,
-                         double* P, void* yscratch, const IterCtl* ctl, int* err, int threads);
-size_t relax_smem_bytes(const LatView& lv, bool fp32);
+                         double* P, void* yscratch, const IterCtl* ctl, int* err, int threads, int chunks);
+size_t relax_smem_bytes(const LatView& lv, bool fp32, int chunks = 1);
+bool relax_chunks_possible(const LatView& lv, bool fp32);
 long long relax_y_stride(const LatView& lv);
 // coarse.cu
 cudaError_t launch_coarse_slots(cudaStream_t s, const LatView& lv, const void* delta, bool delta_fp32,
@@ -218,7 +219,7 @@ struct BatchItem {
 };
 cudaError_t launch_batch_update_residual(cudaStream_t s, bool fp32, const BatchProb* P, const BatchItem* it, int n,
                                          int k);
-cudaError_t launch_batch_relax(cudaStream_t s, bool fp32, int threads, size_t smem, const BatchProb* P,
+cudaError_t launch_batch_relax(cudaStream_t s, bool fp32, int threads, int chunks, size_t smem, const BatchProb* P,
                                const BatchItem* it, int n);
 cudaError_t launch_batch_slots(cudaStream_t s, bool fp32, size_t smem, const BatchProb* P, const BatchItem* it,
                                int n);

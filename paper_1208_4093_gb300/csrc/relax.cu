@@ -58,11 +58,60 @@ struct RelaxSmem {
   size_t slot_elems, ycur_off, z_off, w_off, x_off, total_elems;
 };
 
+// Row offsets within a matrix of each kind, and the storage size (padded).
+__host__ __device__ inline long long kind_row_off(int kind, int nb, int r) {
+  switch (kind) {
+    case 0: return linv_row_off(r);
+    case 1: return b_row_off(nb, r);
+    case 2: return lt_row_off(nb, r);
+    default: return bt_row_off(nb, r);
+  }
+}
+__host__ __device__ inline long long kind_size(int kind, int nb) {
+  return (kind == 0 || kind == 2) ? linv_size(nb) : b_size(nb);
+}
+
+// Two copies per matrix (NC = 2): the rows of the pairs (r, nb-1-r) with
+// r < r1 ("outer", rows [0, r1) and [nb-r1, nb)) and those with r >= r1
+// ("inner", rows [r1, nb-r1)), about half the matrix each, so that a CTA
+// needs only half the shared memory per slot.  r1 is the value nearest nb/4
+// at which every kind's row offsets at r1 and nb-r1 start on 16 bytes (the
+// bulk copies' rule); 0 if there is none.
 template <typename T>
+__host__ __device__ inline int chunk_r1(int nb) {
+  const long long a = 16 / sizeof(T);
+  for (int d = 0; d <= 8; ++d)
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      const int r1 = nb / 4 + (sgn ? -d : d);
+      if (r1 < 1 || 2 * r1 >= nb) continue;
+      bool ok = true;
+      for (int kind = 0; kind < 4 && ok; ++kind)
+        ok = kind_row_off(kind, nb, r1) % a == 0 && kind_row_off(kind, nb, nb - r1) % a == 0;
+      if (ok) return r1;
+    }
+  return 0;
+}
+// elements of chunk c (0 outer, 1 inner) of a matrix of the kind
+__host__ __device__ inline long long chunk_elems(int kind, int nb, int r1, int c) {
+  const long long lo = kind_row_off(kind, nb, r1), hi = kind_row_off(kind, nb, nb - r1);
+  return c == 0 ? lo + (kind_size(kind, nb) - hi) : hi - lo;
+}
+
+template <typename T, int NC = 1>
 __host__ __device__ inline RelaxSmem relax_layout(int nb) {
   RelaxSmem L;
   long long ls = linv_size(nb), bs = b_size(nb);
   L.slot_elems = (size_t)(ls > bs ? ls : bs);
+  if (NC == 2) {
+    const int r1 = chunk_r1<T>(nb);
+    long long m = 0;
+    for (int kind = 0; kind < 4; ++kind)
+      for (int c = 0; c < 2; ++c) {
+        const long long e = chunk_elems(kind, nb, r1, c);
+        m = e > m ? e : m;
+      }
+    L.slot_elems = (size_t)m;
+  }
   const size_t a = 16 / sizeof(T);  // keep every region 16-byte aligned
   auto up = [a](size_t n) { return (n + a - 1) / a * a; };
   L.ycur_off = up(NSLOT * L.slot_elems);
@@ -133,19 +182,25 @@ __device__ inline void row_shape(int nb, int r, int& lo, int& len, long long& of
 // the row pairs (r, nb-1-r); thread 0 of a group handles row r and thread 1
 // row nb-1-r.  pre = fetch(r) is loaded before the products so that its
 // latency hides behind them.
+//
+// Only the pairs [pa, pb) are taken; the slot M holds the rows from storage
+// offset base_lo on (rows r < cut) and base_hi on (rows >= cut), i.e. a row's
+// place in M is its storage offset minus its base.
 template <int NT, typename T, int G, int CH, int K, class Fetch, class Out>
-__device__ inline void rows_times(const T* M, const T* v, int nb, Fetch fetch, Out out) {
-  const int npair = nb / 2;  // nb = 2w is even
+__device__ inline void rows_times(const T* M, const T* v, int nb, int pa, int pb, long long base_lo, int cut,
+                                  long long base_hi, Fetch fetch, Out out) {
   const int g = threadIdx.x % G;
-  for (int base = 0; base < npair; base += NT / G) {
+  for (int base = pa; base < pb; base += NT / G) {
     const int pq = base + (int)threadIdx.x / G;
-    if (base + (int)(threadIdx.x & ~31u) / G >= npair) break;  // the whole warp is past the last pair
-    const bool active = pq < npair;
-    const int ra = active ? pq : 0, rb = nb - 1 - ra;
+    if (base + (int)(threadIdx.x & ~31u) / G >= pb) break;  // the whole warp is past the last pair
+    const bool active = pq < pb;
+    const int ra = active ? pq : pa, rb = nb - 1 - ra;
     int loA, lenA, loB, lenB;
     long long offA, offB;
     row_shape<K>(nb, ra, loA, lenA, offA);
     row_shape<K>(nb, rb, loB, lenB, offB);
+    offA -= ra < cut ? base_lo : base_hi;
+    offB -= rb < cut ? base_lo : base_hi;
     if (!active) lenA = lenB = 0;
     const int myrow = (g & 1) ? rb : ra;
     const bool mine = active && g < 2;
@@ -164,7 +219,7 @@ __host__ __device__ inline long long y_stride(const LatView& lv) {
 }
 
 // The kernel body for set I.
-template <typename T, int NT>
+template <typename T, int NT, int NC>
 __device__ __forceinline__ void relax_body(const LatView lv, const long long* __restrict__ set_off,
                                            const T* __restrict__ fac, const double2* __restrict__ r,
                                            T* __restrict__ delta, double* __restrict__ P, T* __restrict__ yglob,
@@ -181,7 +236,8 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
   const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
   const int w = min(lv.sx, lv.nx - i0), h = min(lv.sy, lv.ny - j0);
   const int nb = 2 * w;
-  const RelaxSmem LY = relax_layout<T>(nb);
+  const RelaxSmem LY = relax_layout<T, NC>(nb);
+  const int r1 = NC == 2 ? chunk_r1<T>(nb) : 0;
   T* sm = reinterpret_cast<T*>(smraw);
   T* ycur = sm + LY.ycur_off;  // the latest y_j of the forward pass
   T* zbuf = sm + LY.z_off;
@@ -192,16 +248,54 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
   const T* fset_t = fset + set_factor_size(nb, h);  // the copy stored by columns
   const double* rg = reinterpret_cast<const double*>(r);
   const int nmat = 2 * h - 1;
-  const int nops = 2 * nmat;
+  const int nops = 2 * nmat * NC;  // one op per matrix copy (NC per matrix)
 
-  auto mat_of_op = [&](int o) { return o < nmat ? o : 2 * nmat - 1 - o; };
+  auto mat_of_op = [&](int o) {
+    const int m = o / NC;
+    return m < nmat ? m : 2 * nmat - 1 - m;
+  };
+  auto kind_of_op = [&](int o) {
+    const bool fwd = o / NC < nmat;
+    return (mat_of_op(o) & 1) ? (fwd ? 1 : 3) : (fwd ? 0 : 2);
+  };
   auto issue = [&](int o) {
     const int k = mat_of_op(o);
+    const int kind = kind_of_op(o);
     uint64_t* bar = &bars[o % NSLOT];
-    const uint32_t bytes = (uint32_t)(((k & 1) ? b_size(nb) : linv_size(nb)) * sizeof(T));
+    const T* src = (o / NC < nmat ? fset : fset_t) + mat_off(nb, k);
+    T* dst = sm + (size_t)(o % NSLOT) * LY.slot_elems;
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, bytes);
-    bulk_g2s(sm + (size_t)(o % NSLOT) * LY.slot_elems, (o < nmat ? fset : fset_t) + mat_off(nb, k), bytes, bar);
+    if (NC == 1) {
+      const uint32_t bytes = (uint32_t)(kind_size(kind, nb) * sizeof(T));
+      mbar_arrive_expect_tx(bar, bytes);
+      bulk_g2s(dst, src, bytes, bar);
+    } else {
+      const long long lo = kind_row_off(kind, nb, r1), hi = kind_row_off(kind, nb, nb - r1);
+      if (o % NC == 0) {
+        // outer rows: [0, lo) and [hi, size) one after the other
+        const uint32_t b0 = (uint32_t)(lo * sizeof(T)), b1 = (uint32_t)((kind_size(kind, nb) - hi) * sizeof(T));
+        mbar_arrive_expect_tx(bar, b0 + b1);
+        bulk_g2s(dst, src, b0, bar);
+        bulk_g2s(dst + lo, src + hi, b1, bar);
+      } else {
+        const uint32_t b = (uint32_t)((hi - lo) * sizeof(T));
+        mbar_arrive_expect_tx(bar, b);
+        bulk_g2s(dst, src + lo, b, bar);
+      }
+    }
+  };
+  // pair range and slot bases of op o (see rows_times)
+  int pa = 0, pb = nb / 2, cut = nb;
+  long long base_lo = 0, base_hi = 0;
+  auto chunk_of = [&](int o) {
+    if (NC == 1) return;
+    const int kind = kind_of_op(o);
+    const long long lo = kind_row_off(kind, nb, r1), hi = kind_row_off(kind, nb, nb - r1);
+    if (o % NC == 0) {
+      pa = 0, pb = r1, cut = r1, base_lo = 0, base_hi = hi - lo;
+    } else {
+      pa = r1, pb = nb / 2, cut = nb, base_lo = lo, base_hi = 0;
+    }
   };
 
   if (tid == 0) {
@@ -222,34 +316,36 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
     const int k = mat_of_op(o);
     const bool is_b = (k & 1) != 0;
     const int j = is_b ? (k + 1) / 2 : k / 2;
+    const bool last_copy = (o % NC) == NC - 1;  // the matrix's outputs are complete after it
     if (!mbar_wait_bounded(&bars[o % NSLOT], (uint32_t)((o / NSLOT) & 1))) abort_flag = 1;
     __syncthreads();
     if (abort_flag) break;
     // the slot of op o - 1 is free: stream op o + NSLOT - 1 into it
     if (tid == 0 && o + NSLOT - 1 < nops) issue(o + NSLOT - 1);
     const T* M = sm + (size_t)(o % NSLOT) * LY.slot_elems;
+    chunk_of(o);
     // 4 threads per row pair keep two warps per SMSP issuing; FP64 FMAs are
     // slow enough that one chain per thread has no stall, FP32 ones want two
     constexpr int G = 4, CH = sizeof(T) == 8 ? 1 : 2;
-    if (o < nmat) {
+    if (o / NC < nmat) {
       // ---------------- forward ----------------
       const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
       if (is_b) {
         // z = r_j - B_j y_{j-1}
         rows_times<NT, T, G, CH, ROW_B>(
-            M, ycur, nb, [&](int row) { return (T)rg[rowbase + row]; },
+            M, ycur, nb, pa, pb, base_lo, cut, base_hi, [&](int row) { return (T)rg[rowbase + row]; },
             [&](int row, T s, T pre) { zbuf[row] = pre - s; });
       } else {
         // y_j = Linv_j z
         T* yj = yg + (size_t)j * nb;
         rows_times<NT, T, G, CH, ROW_LINV>(
-            M, zbuf, nb, [](int) { return T(0); },
+            M, zbuf, nb, pa, pb, base_lo, cut, base_hi, [](int) { return T(0); },
             [&](int row, T s, T) {
               ycur[row] = s;
               yj[row] = s;
             });
       }
-      __syncthreads();
+      if (last_copy) __syncthreads();
     } else {
       // ---------------- backward ----------------
       if (!is_b) {
@@ -257,7 +353,7 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
         const T* wv = (j == h - 1) ? ycur : wbuf;
         const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
         rows_times<NT, T, G, CH, ROW_LT>(
-            M, wv, nb, [](int) { return T(0); },
+            M, wv, nb, pa, pb, base_lo, cut, base_hi, [](int) { return T(0); },
             [&](int row, T s, T) {
               xbuf[row] = s;
               delta[rowbase + row] = s;
@@ -266,9 +362,10 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
         // w = y_{j-1} - B_j^T x_j
         const T* yp = yg + (size_t)(j - 1) * nb;
         rows_times<NT, T, G, CH, ROW_BT>(
-            M, xbuf, nb, [&](int row) { return yp[row]; }, [&](int row, T s, T pre) { wbuf[row] = pre - s; });
+            M, xbuf, nb, pa, pb, base_lo, cut, base_hi, [&](int row) { return yp[row]; },
+            [&](int row, T s, T pre) { wbuf[row] = pre - s; });
       }
-      __syncthreads();
+      if (last_copy) __syncthreads();
     }
   }
   if (abort_flag) {
@@ -323,88 +420,114 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
   }
 }
 
-template <typename T, int NT>
+template <typename T, int NT, int NC>
 __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __restrict__ set_off,
                                               const T* __restrict__ fac, const double2* __restrict__ r,
                                               T* __restrict__ delta, double* __restrict__ P,
                                               T* __restrict__ yglob, long long ystride, const IterCtl* ctl,
                                               int* err) {
-  relax_body<T, NT>(lv, set_off, fac, r, delta, P, yglob, ystride, ctl, err, blockIdx.x);
+  relax_body<T, NT, NC>(lv, set_off, fac, r, delta, P, yglob, ystride, ctl, err, blockIdx.x);
 }
 
 // Batched: the sets of every problem of a batch.
-template <typename T, int NT>
+template <typename T, int NT, int NC>
 __global__ void __launch_bounds__(NT) kb_relax(const BatchProb* __restrict__ Pb, const BatchItem* __restrict__ items) {
   const BatchItem it = items[blockIdx.x];
   const BatchProb& q = Pb[it.prob];
   const T* fac;
   if constexpr (sizeof(T) == 4) fac = q.f32;
   else fac = q.f64;
-  relax_body<T, NT>(q.lv, q.set_off, fac, q.r, (T*)q.delta, q.P, (T*)q.yscratch, y_stride(q.lv), q.ctl, q.err,
-                    it.bx);
+  relax_body<T, NT, NC>(q.lv, q.set_off, fac, q.r, (T*)q.delta, q.P, (T*)q.yscratch, y_stride(q.lv), q.ctl,
+                        q.err, it.bx);
 }
 
 }  // namespace
 
-size_t relax_smem_bytes(const LatView& lv, bool fp32) {
+size_t relax_smem_bytes(const LatView& lv, bool fp32, int chunks) {
   const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
+  if (chunks == 2 && !fp32) return relax_layout<double, 2>(2 * w).total_elems * sizeof(double);
   return fp32 ? relax_layout<float>(2 * w).total_elems * sizeof(float)
               : relax_layout<double>(2 * w).total_elems * sizeof(double);
 }
 
+// Two copies per matrix apply to the FP64 relaxation when every set width of
+// the lattice has a split row r1 (the regular width and the ragged last one).
+bool relax_chunks_possible(const LatView& lv, bool fp32) {
+  if (fp32) return false;
+  const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
+  const int wr = lv.nx - (lv.Mx - 1) * lv.sx;  // last column of sets
+  return chunk_r1<double>(2 * w) > 0 && chunk_r1<double>(2 * wr) > 0;
+}
+
 long long relax_y_stride(const LatView& lv) { return y_stride(lv); }
+
+template <int NC, class F>
+static cudaError_t dispatch_nt(int threads, F go) {
+  if (threads == 64) go(std::integral_constant<int, 64>(), std::integral_constant<int, NC>());
+  else if (threads == 128) go(std::integral_constant<int, 128>(), std::integral_constant<int, NC>());
+  else if (threads == 256) go(std::integral_constant<int, 256>(), std::integral_constant<int, NC>());
+  else return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
 
 cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
                          const double* f64, const float* f32, const double2* r, void* delta,
-                         double* P, void* yscratch, const IterCtl* ctl, int* err, int threads) {
+                         double* P, void* yscratch, const IterCtl* ctl, int* err, int threads, int chunks) {
   const bool fp32 = (f32 != nullptr);
-  const size_t smem = relax_smem_bytes(lv, fp32);
+  if (chunks == 2 && !relax_chunks_possible(lv, fp32)) return cudaErrorInvalidValue;
+  const size_t smem = relax_smem_bytes(lv, fp32, chunks);
   const long long ys = relax_y_stride(lv);
-  auto go = [&](auto nt) {
-    constexpr int NT = decltype(nt)::value;
+  auto go = [&](auto nt, auto nc) {
+    constexpr int NT = decltype(nt)::value, NC = decltype(nc)::value;
     if (fp32)
-      k_relax<float, NT><<<lv.M, NT, smem, s>>>(lv, set_off, f32, r, (float*)delta, P, (float*)yscratch, ys, ctl,
-                                                err);
+      k_relax<float, NT, 1><<<lv.M, NT, smem, s>>>(lv, set_off, f32, r, (float*)delta, P, (float*)yscratch, ys, ctl,
+                                                   err);
     else
-      k_relax<double, NT><<<lv.M, NT, smem, s>>>(lv, set_off, f64, r, (double*)delta, P, (double*)yscratch, ys,
-                                                 ctl, err);
+      k_relax<double, NT, NC><<<lv.M, NT, smem, s>>>(lv, set_off, f64, r, (double*)delta, P, (double*)yscratch, ys,
+                                                     ctl, err);
   };
-  if (threads == 64) go(std::integral_constant<int, 64>());
-  else if (threads == 128) go(std::integral_constant<int, 128>());
-  else if (threads == 256) go(std::integral_constant<int, 256>());
-  else return cudaErrorInvalidValue;
+  const cudaError_t e = chunks == 2 ? dispatch_nt<2>(threads, go) : dispatch_nt<1>(threads, go);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_relax(cudaStream_t s, bool fp32, int threads, size_t smem, const BatchProb* P,
+cudaError_t launch_batch_relax(cudaStream_t s, bool fp32, int threads, int chunks, size_t smem, const BatchProb* P,
                                const BatchItem* it, int n) {
   if (n <= 0) return cudaSuccess;
-  auto go = [&](auto nt) {
-    constexpr int NT = decltype(nt)::value;
-    if (fp32) kb_relax<float, NT><<<n, NT, smem, s>>>(P, it);
-    else kb_relax<double, NT><<<n, NT, smem, s>>>(P, it);
+  auto go = [&](auto nt, auto nc) {
+    constexpr int NT = decltype(nt)::value, NC = decltype(nc)::value;
+    if (fp32) kb_relax<float, NT, 1><<<n, NT, smem, s>>>(P, it);
+    else kb_relax<double, NT, NC><<<n, NT, smem, s>>>(P, it);
   };
-  if (threads == 64) go(std::integral_constant<int, 64>());
-  else if (threads == 128) go(std::integral_constant<int, 128>());
-  else if (threads == 256) go(std::integral_constant<int, 256>());
-  else return cudaErrorInvalidValue;
+  const cudaError_t e = chunks == 2 ? dispatch_nt<2>(threads, go) : dispatch_nt<1>(threads, go);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t configure_relax(int max_smem) {
   cudaError_t e;
-  if ((e = set_max_dynamic_smem(kb_relax<float, 64>, max_smem)) != cudaSuccess) return e;
-  if ((e = set_max_dynamic_smem(kb_relax<float, 128>, max_smem)) != cudaSuccess) return e;
-  if ((e = set_max_dynamic_smem(kb_relax<float, 256>, max_smem)) != cudaSuccess) return e;
-  if ((e = set_max_dynamic_smem(kb_relax<double, 64>, max_smem)) != cudaSuccess) return e;
-  if ((e = set_max_dynamic_smem(kb_relax<double, 128>, max_smem)) != cudaSuccess) return e;
-  if ((e = set_max_dynamic_smem(kb_relax<double, 256>, max_smem)) != cudaSuccess) return e;
-  if ((e = set_max_dynamic_smem(k_relax<float, 64>, max_smem)) != cudaSuccess) return e;
-  if ((e = set_max_dynamic_smem(k_relax<float, 128>, max_smem)) != cudaSuccess) return e;
-  if ((e = set_max_dynamic_smem(k_relax<float, 256>, max_smem)) != cudaSuccess) return e;
-  if ((e = set_max_dynamic_smem(k_relax<double, 64>, max_smem)) != cudaSuccess) return e;
-  if ((e = set_max_dynamic_smem(k_relax<double, 128>, max_smem)) != cudaSuccess) return e;
-  return set_max_dynamic_smem(k_relax<double, 256>, max_smem);
+#define HMS_RELAX_ATTR(K)                                                            \
+  if ((e = set_max_dynamic_smem(K, max_smem)) != cudaSuccess) return e;
+  HMS_RELAX_ATTR((k_relax<float, 64, 1>))
+  HMS_RELAX_ATTR((k_relax<float, 128, 1>))
+  HMS_RELAX_ATTR((k_relax<float, 256, 1>))
+  HMS_RELAX_ATTR((k_relax<double, 64, 1>))
+  HMS_RELAX_ATTR((k_relax<double, 128, 1>))
+  HMS_RELAX_ATTR((k_relax<double, 256, 1>))
+  HMS_RELAX_ATTR((k_relax<double, 64, 2>))
+  HMS_RELAX_ATTR((k_relax<double, 128, 2>))
+  HMS_RELAX_ATTR((k_relax<double, 256, 2>))
+  HMS_RELAX_ATTR((kb_relax<float, 64, 1>))
+  HMS_RELAX_ATTR((kb_relax<float, 128, 1>))
+  HMS_RELAX_ATTR((kb_relax<float, 256, 1>))
+  HMS_RELAX_ATTR((kb_relax<double, 64, 1>))
+  HMS_RELAX_ATTR((kb_relax<double, 128, 1>))
+  HMS_RELAX_ATTR((kb_relax<double, 256, 1>))
+  HMS_RELAX_ATTR((kb_relax<double, 64, 2>))
+  HMS_RELAX_ATTR((kb_relax<double, 128, 2>))
+  HMS_RELAX_ATTR((kb_relax<double, 256, 2>))
+#undef HMS_RELAX_ATTR
+  return cudaSuccess;
 }
 
 }  // namespace hms

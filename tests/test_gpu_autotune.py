@@ -1,5 +1,6 @@
-"""Relaxation CTA size: every size gives bitwise the same iteration, and the
-autotuned choice (relax_threads = 0) is one of them, kept per set shape.
+"""Relaxation CTA size and copies per matrix: every size gives bitwise the
+same iteration, and the autotuned choice (relax_threads = 0) is one of them,
+kept per set shape.
 
 The relaxation's row sums are formed by groups of 4 threads whatever the CTA
 size, and its P sums over 256 virtual lanes, so 64-, 128- and 256-thread CTAs
@@ -26,11 +27,20 @@ def test_every_cta_size_gives_the_same_bits(hms_ctx, shape, prec):
     p = loads(nx, ny, 8).reshape(1, -1)
     r = loads(nx, ny, 9).reshape(-1)
     outs, its, rel = [], [], []
-    for nt in (64, 128, 256, 0):
-        pr = capi.hms_problem_create(hms_ctx, nx, ny, sx, sy, relax_threads=nt, **kw)
+    # two copies per matrix: FP64 and even set widths >= 6 (the ragged 6-wide column included)
+    two = prec == 0 and sx % 2 == 0 and (nx - (-(-nx // sx) - 1) * sx) % 2 == 0 and nx - (-(-nx // sx) - 1) * sx >= 6
+    variants = [(64, 1), (128, 1), (256, 1), (0, 0)] + ([(64, 2), (128, 2), (256, 2)] if two else [])
+    if not two:
+        with pytest.raises(capi.HmsError) as e:
+            capi.hms_problem_create(hms_ctx, nx, ny, sx, sy, relax_threads=128, relax_copies=2, **kw)
+        assert e.value.status == capi.HMS_ERR_ARG
+    for nt, nc in variants:
+        pr = capi.hms_problem_create(hms_ctx, nx, ny, sx, sy, relax_threads=nt, relax_copies=nc, **kw)
         try:
             got = capi.hms_problem_relax_threads(pr)
             assert got == nt if nt else got in (64, 128, 256)
+            gc = capi.hms_problem_relax_copies(pr)
+            assert gc == nc if nc else gc in ((1, 2) if two else (1,))
             u = np.empty_like(p)
             it = np.zeros(1, np.int32)
             capi.hms_solve(hms_ctx, pr, p, u, iters=it)
@@ -42,7 +52,7 @@ def test_every_cta_size_gives_the_same_bits(hms_ctx, shape, prec):
             rel.append((d, P))
         finally:
             capi.hms_problem_destroy(pr)
-    for k in range(1, 4):
+    for k in range(1, len(variants)):
         assert np.array_equal(outs[k], outs[0])
         assert its[k] == its[0]
         assert np.array_equal(rel[k][0], rel[0][0]) and np.array_equal(rel[k][1], rel[0][1])

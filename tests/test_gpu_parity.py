@@ -251,6 +251,26 @@ def test_two_sided_factor(hms_ctx, case):
         capi.hms_problem_destroy(pr1)
 
 
+def test_two_sided_short_segment_block_converges(hms_ctx):
+    """8 x 8 sets of 16 x 16 nodes: the bottom segment has 244 pivots, so its
+    last 16-column block is short and rows of the separator follow it.  The
+    panel of that block must not read the window positions right of those
+    rows' band (never loaded: whatever an earlier kernel left in shared
+    memory), which once turned this solve non-finite after ~105 updates."""
+    from paper_1208_4093_gb300 import capi
+    nx = 128
+    tr = truss.Truss(nx, nx)
+    p = loads(nx, nx, 0).reshape(-1)
+    pr = capi.hms_problem_create(hms_ctx, nx, nx, 16, 16, precision=capi.HMS_FP64, tol=1e-10, max_iter=5000,
+                                 coarse_factor=5)
+    try:
+        u = np.empty((1, tr.ndof))
+        capi.hms_solve(hms_ctx, pr, p.reshape(1, -1), u)
+        assert rel(u[0], direct.cholesky_solve(tr, tr.free * p)) < 1e-9
+    finally:
+        capi.hms_problem_destroy(pr)
+
+
 def test_two_sided_needs_a_long_system(hms_ctx):
     """coarse_factor = 5 is refused where the system is shorter than two 64-row
     segments plus a separator (4 x 4 sets: n = 144, bw = 53)."""
