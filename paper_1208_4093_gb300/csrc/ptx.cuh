@@ -19,6 +19,11 @@ __device__ inline void fence_mbar_init() {
 
 // Orders this thread's earlier shared-memory accesses before later async-proxy
 // (bulk copy) accesses of the same memory.
+// Global memory written by generic-proxy stores, then read by a bulk copy
+// (async proxy): the writes must be ordered before the copy by this fence.
+__device__ inline void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 __device__ inline void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

@@ -55,8 +55,12 @@ template <> struct Vec2<float> { using type = float2; };
 constexpr int NSLOT = 3;  // matrices staged in shared memory (two in flight while one is applied)
 
 struct RelaxSmem {
-  size_t slot_elems, ycur_off, z_off, w_off, x_off, total_elems;
+  size_t slot_elems, vec_off, vec_elems, ycur_off, z_off, w_off, x_off, total_elems;
 };
+
+// Row stride of the y scratch: nb rounded up to 4 entries, so that every row
+// starts on 16 bytes (the bulk copies' rule).
+__host__ __device__ inline int y_row(int nb) { return (nb + 3) / 4 * 4; }
 
 // Row offsets within a matrix of each kind, and the storage size (padded).
 __host__ __device__ inline long long kind_row_off(int kind, int nb, int r) {
@@ -114,7 +118,14 @@ __host__ __device__ inline RelaxSmem relax_layout(int nb) {
   }
   const size_t a = 16 / sizeof(T);  // keep every region 16-byte aligned
   auto up = [a](size_t n) { return (n + a - 1) / a * a; };
-  L.ycur_off = up(NSLOT * L.slot_elems);
+  // per slot, the vector a B step reads besides the product: r_j (FP64) in the
+  // forward pass, y_{j-1} in the backward pass; staged with the matrix
+  L.vec_off = up(NSLOT * L.slot_elems);
+  {
+    const size_t rb = (size_t)nb * sizeof(double), yb = (size_t)y_row(nb) * sizeof(T);  // r_j, y_{j-1}
+    L.vec_elems = up(((rb > yb ? rb : yb) + sizeof(T) - 1) / sizeof(T));
+  }
+  L.ycur_off = up(L.vec_off + NSLOT * L.vec_elems);
   L.z_off = up(L.ycur_off + nb);
   L.w_off = up(L.z_off + nb);
   L.x_off = up(L.w_off + nb);
@@ -215,7 +226,7 @@ __device__ inline void rows_times(const T* M, const T* v, int nb, int pa, int pb
 __host__ __device__ inline long long y_stride(const LatView& lv) {
   const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
   const int h = lv.sy < lv.ny ? lv.sy : lv.ny;
-  return 2LL * w * h;
+  return (long long)y_row(2 * w) * h;
 }
 
 // The kernel body for set I.
@@ -258,31 +269,43 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
     const bool fwd = o / NC < nmat;
     return (mat_of_op(o) & 1) ? (fwd ? 1 : 3) : (fwd ? 0 : 2);
   };
+  const int nbr = y_row(nb);
   auto issue = [&](int o) {
     const int k = mat_of_op(o);
     const int kind = kind_of_op(o);
+    const bool fwd = o / NC < nmat;
     uint64_t* bar = &bars[o % NSLOT];
-    const T* src = (o / NC < nmat ? fset : fset_t) + mat_off(nb, k);
+    const T* src = (fwd ? fset : fset_t) + mat_off(nb, k);
     T* dst = sm + (size_t)(o % NSLOT) * LY.slot_elems;
+    // a B step's vector: r_j (forward; 16 bytes per node) or y_{j-1} (backward; rows of nbr entries)
+    const int jv = (k + 1) / 2;
+    const void* vsrc = fwd ? (const void*)(rg + 2 * ((size_t)(j0 + jv) * lv.nx + i0))
+                           : (const void*)(yg + (size_t)(jv - 1) * nbr);
+    const uint32_t vbytes = (k & 1) ? (uint32_t)(fwd ? nb * sizeof(double) : nbr * sizeof(T)) : 0u;
+    T* vdst = sm + LY.vec_off + (size_t)(o % NSLOT) * LY.vec_elems;
     fence_proxy_async_smem();
+    // y_{j-1} was stored by this CTA's threads in the forward pass (ordered
+    // before this thread by the step barriers)
+    if (!fwd && (k & 1)) fence_proxy_async_global();
     if (NC == 1) {
       const uint32_t bytes = (uint32_t)(kind_size(kind, nb) * sizeof(T));
-      mbar_arrive_expect_tx(bar, bytes);
+      mbar_arrive_expect_tx(bar, bytes + vbytes);
       bulk_g2s(dst, src, bytes, bar);
     } else {
       const long long lo = kind_row_off(kind, nb, r1), hi = kind_row_off(kind, nb, nb - r1);
       if (o % NC == 0) {
         // outer rows: [0, lo) and [hi, size) one after the other
         const uint32_t b0 = (uint32_t)(lo * sizeof(T)), b1 = (uint32_t)((kind_size(kind, nb) - hi) * sizeof(T));
-        mbar_arrive_expect_tx(bar, b0 + b1);
+        mbar_arrive_expect_tx(bar, b0 + b1 + vbytes);
         bulk_g2s(dst, src, b0, bar);
         bulk_g2s(dst + lo, src + hi, b1, bar);
       } else {
         const uint32_t b = (uint32_t)((hi - lo) * sizeof(T));
-        mbar_arrive_expect_tx(bar, b);
+        mbar_arrive_expect_tx(bar, b + vbytes);
         bulk_g2s(dst, src + lo, b, bar);
       }
     }
+    if (vbytes) bulk_g2s(vdst, vsrc, vbytes, bar);
   };
   // pair range and slot bases of op o (see rows_times)
   int pa = 0, pb = nb / 2, cut = nb;
@@ -323,21 +346,22 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
     // the slot of op o - 1 is free: stream op o + NSLOT - 1 into it
     if (tid == 0 && o + NSLOT - 1 < nops) issue(o + NSLOT - 1);
     const T* M = sm + (size_t)(o % NSLOT) * LY.slot_elems;
+    const T* vstage = sm + LY.vec_off + (size_t)(o % NSLOT) * LY.vec_elems;
     chunk_of(o);
     // 4 threads per row pair keep two warps per SMSP issuing; FP64 FMAs are
     // slow enough that one chain per thread has no stall, FP32 ones want two
     constexpr int G = 4, CH = sizeof(T) == 8 ? 1 : 2;
     if (o / NC < nmat) {
       // ---------------- forward ----------------
-      const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
       if (is_b) {
-        // z = r_j - B_j y_{j-1}
+        // z = r_j - B_j y_{j-1} (r_j staged with B_j)
+        const double* rj = reinterpret_cast<const double*>(vstage);
         rows_times<NT, T, G, CH, ROW_B>(
-            M, ycur, nb, pa, pb, base_lo, cut, base_hi, [&](int row) { return (T)rg[rowbase + row]; },
+            M, ycur, nb, pa, pb, base_lo, cut, base_hi, [&](int row) { return (T)rj[row]; },
             [&](int row, T s, T pre) { zbuf[row] = pre - s; });
       } else {
         // y_j = Linv_j z
-        T* yj = yg + (size_t)j * nb;
+        T* yj = yg + (size_t)j * nbr;
         rows_times<NT, T, G, CH, ROW_LINV>(
             M, zbuf, nb, pa, pb, base_lo, cut, base_hi, [](int) { return T(0); },
             [&](int row, T s, T) {
@@ -359,8 +383,8 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
               delta[rowbase + row] = s;
             });
       } else {
-        // w = y_{j-1} - B_j^T x_j
-        const T* yp = yg + (size_t)(j - 1) * nb;
+        // w = y_{j-1} - B_j^T x_j (y_{j-1} staged with B_j^T)
+        const T* yp = vstage;
         rows_times<NT, T, G, CH, ROW_BT>(
             M, xbuf, nb, pa, pb, base_lo, cut, base_hi, [&](int row) { return yp[row]; },
             [&](int row, T s, T pre) { wbuf[row] = pre - s; });
