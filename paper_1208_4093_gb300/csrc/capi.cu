@@ -593,30 +593,33 @@ static cudaError_t autotune_relax(hms_problem* pr, int copies) {
     cudaEventDestroy(e0);
     return e;
   }
-  float best = 0.f;
-  int best_nt = 256, best_nc = 1;
-  bool first = true;
+  // candidates, each timed in two rounds (the smaller time counts) after a
+  // warm-up, so that clocks ramping up from idle do not favour later ones
+  std::vector<std::pair<int, int>> cand;
   const int max_nc = copies != 0 ? copies : (relax_chunks_possible(lv, fp32(pr)) ? 2 : 1);
-  for (int nc = copies != 0 ? copies : 1; nc <= max_nc && e == cudaSuccess; ++nc)
-    for (int nt : {64, 128, 256}) {
-      auto run = [&]() {
-        return launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr,
-                            pr->err, nt, nc);
-      };
-      if ((e = run()) != cudaSuccess) break;
+  for (int nc = copies != 0 ? copies : 1; nc <= max_nc; ++nc)
+    for (int nt : {64, 128, 256}) cand.push_back({nt, nc});
+  std::vector<float> tbest(cand.size(), 1e30f);
+  auto run = [&](int nt, int nc) {
+    return launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr,
+                        pr->err, nt, nc);
+  };
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = run(256, 1);
+  for (int round = 0; round < 2 && e == cudaSuccess; ++round)
+    for (size_t i = 0; i < cand.size() && e == cudaSuccess; ++i) {
+      if ((e = run(cand[i].first, cand[i].second)) != cudaSuccess) break;
       if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
-      for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = run();
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = run(cand[i].first, cand[i].second);
       if (e != cudaSuccess || (e = cudaEventRecord(e1, s)) != cudaSuccess) break;
       if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (first || ms < best) {
-        best = ms;
-        best_nt = nt;
-        best_nc = nc;
-        first = false;
-      }
+      tbest[i] = std::min(tbest[i], ms);
     }
+  int best_nt = 256, best_nc = 1;
+  float best = 1e30f;
+  for (size_t i = 0; i < cand.size(); ++i)
+    if (tbest[i] < best) best = tbest[i], best_nt = cand[i].first, best_nc = cand[i].second;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return e;

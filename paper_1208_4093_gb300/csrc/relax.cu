@@ -141,26 +141,52 @@ __host__ __device__ inline RelaxSmem relax_layout(int nb) {
 template <typename T, int G, int CH>
 __device__ inline void pair_dot(const T* __restrict__ pA, int loA, int lenA, const T* __restrict__ pB, int loB,
                                 int lenB, const T* __restrict__ v, int g, T& out) {
+  static_assert(CH == 1 || CH == 2, "one or two chains per thread");
   const int len = lenA + lenB;
   T a[CH], b[CH];
 #pragma unroll
   for (int q = 0; q < CH; ++q) a[q] = b[q] = T(0);
-  auto step = [&](int tt, T& ca, T& cb) {
-    const bool inA = tt < lenA;
-    const T* mp = inA ? pA + tt : pB + (tt - lenA);
-    const T* vp = inA ? v + (loA + tt) : v + (loB + tt - lenA);
-    T c = inA ? ca : cb;
-    c = fma(*mp, *vp, c);
-    if (inA) ca = c; else cb = c;
-  };
-  int t = g;
-  for (; t + (CH - 1) * G < len; t += CH * G) {
-#pragma unroll
-    for (int q = 0; q < CH; ++q) step(t + q * G, a[q], b[q]);
+  // The combined index t (row A's entries, then row B's) is walked from g with
+  // stride G, entry t going to chain ((t - g) / G) mod CH.
+  if constexpr (CH == 1) {
+    // FP64: one walk with the row chosen per entry.  Every lane of a warp then
+    // runs the same number of FMAs (len is nearly the same for every pair),
+    // which matters where a warp's FMA holds the FP64 pipe whatever its
+    // active lanes.
+    for (int t = g; t < len; t += G) {
+      const bool inA = t < lenA;
+      const T* mp = inA ? pA + t : pB + (t - lenA);
+      const T* vp = inA ? v + (loA + t) : v + (loB + t - lenA);
+      T c = inA ? a[0] : b[0];
+      c = fma(*mp, *vp, c);
+      if (inA) a[0] = c;
+      else b[0] = c;
+    }
+  } else {
+    // FP32: row A's part and row B's part as two plain loops (no per-entry
+    // choice of row: the index arithmetic, not the FMAs, bound the one
+    // walk), each entry landing in the same chain and order as in one walk.
+    const T* va = v + loA;
+    int t = g;
+    for (; t + G < lenA; t += 2 * G) {
+      a[0] = fma(pA[t], va[t], a[0]);
+      a[1] = fma(pA[t + G], va[t + G], a[1]);
+    }
+    if (t < lenA) a[0] = fma(pA[t], va[t], a[0]);
+    // row B from the first t >= lenA of this thread's walk; its chain is q0
+    const int t0 = lenA + ((g - lenA) & (G - 1));
+    const int q0 = ((t0 - g) / G) & 1;
+    const T* mb = pB - lenA;  // indexed by the combined t >= lenA
+    const T* vb = v + (loB - lenA);
+    T b0 = T(0), b1 = T(0);  // the chains in walk order: q0, then the other
+    for (t = t0; t + G < len; t += 2 * G) {
+      b0 = fma(mb[t], vb[t], b0);
+      b1 = fma(mb[t + G], vb[t + G], b1);
+    }
+    if (t < len) b0 = fma(mb[t], vb[t], b0);
+    b[0] = q0 ? b1 : b0;
+    b[CH - 1] = q0 ? b0 : b1;
   }
-#pragma unroll
-  for (int q = 0; q + 1 < CH; ++q)
-    if (t + q * G < len) step(t + q * G, a[q], b[q]);
   T sa = a[0], sb = b[0];
 #pragma unroll
   for (int q = 1; q < CH; ++q) sa += a[q], sb += b[q];
