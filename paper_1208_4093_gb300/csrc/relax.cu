@@ -17,21 +17,24 @@
 //   backward x_j = Linv_j^T (y_j - B_{j+1}^T x_{j+1})
 // so both passes are products of packed rows with a vector.  Each matrix is
 // staged in shared memory by a 1-D bulk copy (cp.async.bulk, completion on an
-// mbarrier), three slots deep so two matrices stream in while one is applied.
-// Rows r and nb-1-r of a matrix go to a group of G threads as one combined
-// index range of almost constant length (nb+1 for the triangles, about nb+7
-// for the B blocks), so every lane of a warp runs the same number of FMAs.
-// The solve runs in T = double (FP64 path) or T = float (mixed path, FP32
-// factor), with G = 4 threads per row pair either way.  After the back
+// mbarrier), three slots deep so two matrices stream in while one is applied;
+// a B step's vector (r_j forward, y_{j-1} backward) comes in the same
+// transaction.  Rows r and nb-1-r of a matrix go to a group of G threads as
+// one combined index range of almost constant length (nb+1 for the triangles,
+// about nb+7 for the B blocks), so every lane of a warp runs the same number
+// of FMAs.  The solve runs in T = double (FP64 path) or T = float (mixed path,
+// FP32 factor), with G = 4 threads per row pair either way.  After the back
 // substitution the nine sums of P_I = V_I^T r_I are formed in FP64 from r and
 // the delta just written, node by node.
 //
-// The CTA size NT (64, 128 or 256 threads) is a launch choice: NT / G row
-// pairs are worked on at once, so 32 x 32-node sets (32 pairs) fill a CTA of
-// 128 threads and 64 x 64-node sets one of 256.  Every row's sum and every P
-// sum is formed in the same order whatever NT is (the P sums over 256 virtual
-// lanes), so the results are bitwise the same for every NT, and the problem
-// setup may pick NT by timing (relax_threads = 0).
+// The CTA size NT (64, 128 or 256 threads) and, in FP64, the copies per matrix
+// NC (1, or 2: the outer and the inner row pairs apart, half the shared memory
+// per slot) are launch choices: NT / G row pairs are worked on at once, so 32
+// x 32-node sets (32 pairs) fill a CTA of 128 threads and 64 x 64-node sets
+// one of 256.  Every row's sum and every P sum is formed in the same order
+// whatever NT and NC are (the P sums over 256 virtual lanes), so the results
+// are bitwise the same for every choice, and the problem setup may pick them
+// by timing (relax_threads = 0).
 #include <type_traits>
 
 #include "hms_internal.cuh"
