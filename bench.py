@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "lattice1024_lognormal"
 TOL = 1e-8
+TOL_CONFIG = 1e-10  # the stopping level the 1024^2 lognormal configuration states
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 GOLDEN_FULL = os.path.join(ROOT, "tests", "golden", "lattice1024_lognormal_history.json")
 FP64_LANES_PER_SM_CLK = 2  # DFMA lanes per SM per clock on GB300 (ncu: sm__sass_thread_inst_executed_op_dfma peak)
@@ -50,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-config-eps", action="store_true",
+                    help="skip the solves to the configuration's own R1 < 1e-10")
     ap.add_argument("--ncu-case", choices=["fp64", "mixed"], default=None,
                     help="only run --ncu-iters updates of the workload once (for ncu captures); no JSON line")
     ap.add_argument("--ncu-iters", type=int, default=1)
@@ -561,6 +564,23 @@ def run_ours(args, rank, world, local_rank):
                  "err_vs_oracle_sampled": err_vs_oracle(um),
                  "speedup_vs_fp64": statistics.median(ms64) / statistics.median(msm)}
 
+    # ---- the configuration's own stopping level (R1 < 1e-10), both forms ----
+    # The oracle's stored state is at the same level (its run to 1e-10), so the
+    # sampled error here compares like with like.
+    config_eps = None
+    if not args.no_config_eps:
+        config_eps = {"tol": TOL_CONFIG}
+        for prec, name in ((capi.HMS_FP64, "fp64"), (capi.HMS_MIXED, "mixed")):
+            if name == "mixed" and args.no_mixed:
+                continue
+            pre = make(prec, tol=TOL_CONFIG)
+            mse, _ = timed(pre, 2, 1)
+            config_eps[name] = {"value": statistics.median(mse), "unit": "ms", "iterations": int(its.item()),
+                                "err_vs_oracle_sampled": err_vs_oracle(u_dev.cpu().numpy())}
+            capi.hms_problem_destroy(pre)
+        nor, _ = nir_golden(TOL_CONFIG)
+        config_eps["oracle_iterations"] = nor
+
     # ---- per-kernel CUDA-event times (profile pass, same workload) ----
     hbm_peak, peak_src = peaks()
     rooflines = {}
@@ -637,6 +657,7 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "err_vs_oracle_sampled": err_vs_oracle(u64),
         "mixed": mixed,
+        "config_eps": config_eps,
         "roofline": rooflines.get("fp64"),
         "roofline_mixed": rooflines.get("mixed"),
         "cpu_baseline": cpu,

@@ -27,7 +27,12 @@
 // substitution the nine sums of P_I = V_I^T r_I are formed in FP64 from r and
 // the delta just written, node by node.
 //
-// The CTA size NT (64, 128 or 256 threads) and, in FP64, the copies per matrix
+// The copies are issued by one more warp (the producer, threads NT .. NT+31),
+// which takes no part in the products: issuing a copy (fences, the expected
+// byte count, the copy instructions) would otherwise delay one compute warp,
+// and with it the whole step, at every matrix.
+//
+// The compute CTA size NT (64, 128 or 256 threads) and, in FP64, the copies per matrix
 // NC (1, or 2: the outer and the inner row pairs apart, half the shared memory
 // per slot) are launch choices: NT / G row pairs are worked on at once, so 32
 // x 32-node sets (32 pairs) fill a CTA of 128 threads and 64 x 64-node sets
@@ -272,6 +277,7 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
 
   using T2 = typename Vec2<T>::type;
   const int tid = threadIdx.x, lane = tid & 31;
+  const bool producer = tid >= NT;  // the last warp issues the copies
   const int Ix = I % lv.Mx, Iy = I / lv.Mx;
   const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
   const int w = min(lv.sx, lv.nx - i0), h = min(lv.sy, lv.ny - j0);
@@ -356,11 +362,12 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0)
+  if (tid == NT)
     for (int o = 0; o < NSLOT - 1 && o < nops; ++o) issue(o);
   // z = r_0
   const size_t rowbase0 = 2 * ((size_t)j0 * lv.nx + i0);
-  for (int t = tid; t < nb; t += NT) zbuf[t] = (T)rg[rowbase0 + t];
+  if (!producer)
+    for (int t = tid; t < nb; t += NT) zbuf[t] = (T)rg[rowbase0 + t];
 
   const double2 rep = lv.rep[I];
 
@@ -369,11 +376,15 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
     const bool is_b = (k & 1) != 0;
     const int j = is_b ? (k + 1) / 2 : k / 2;
     const bool last_copy = (o % NC) == NC - 1;  // the matrix's outputs are complete after it
-    if (!mbar_wait_bounded(&bars[o % NSLOT], (uint32_t)((o / NSLOT) & 1))) abort_flag = 1;
+    if (!producer && !mbar_wait_bounded(&bars[o % NSLOT], (uint32_t)((o / NSLOT) & 1))) abort_flag = 1;
     __syncthreads();
     if (abort_flag) break;
     // the slot of op o - 1 is free: stream op o + NSLOT - 1 into it
-    if (tid == 0 && o + NSLOT - 1 < nops) issue(o + NSLOT - 1);
+    if (producer) {
+      if (tid == NT && o + NSLOT - 1 < nops) issue(o + NSLOT - 1);
+      if (last_copy) __syncthreads();
+      continue;
+    }
     const T* M = sm + (size_t)(o % NSLOT) * LY.slot_elems;
     const T* vstage = sm + LY.vec_off + (size_t)(o % NSLOT) * LY.vec_elems;
     chunk_of(o);
@@ -434,7 +445,7 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
   // through one shuffle tree, and the 8 virtual warps are added in order
   __syncthreads();
   const T2* d2 = reinterpret_cast<const T2*>(delta);
-  for (int vbase = 0; vbase < VL; vbase += NT) {
+  for (int vbase = 0; vbase < VL && !producer; vbase += NT) {
     const int v = vbase + tid;
     if (v >= VL) break;  // whole warps (VL is a multiple of 32)
     double pacc[NMODES];
@@ -474,7 +485,7 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
 }
 
 template <typename T, int NT, int NC>
-__global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __restrict__ set_off,
+__global__ void __launch_bounds__(NT + 32) k_relax(LatView lv, const long long* __restrict__ set_off,
                                               const T* __restrict__ fac, const double2* __restrict__ r,
                                               T* __restrict__ delta, double* __restrict__ P,
                                               T* __restrict__ yglob, long long ystride, const IterCtl* ctl,
@@ -484,7 +495,7 @@ __global__ void __launch_bounds__(NT) k_relax(LatView lv, const long long* __res
 
 // Batched: the sets of every problem of a batch.
 template <typename T, int NT, int NC>
-__global__ void __launch_bounds__(NT) kb_relax(const BatchProb* __restrict__ Pb, const BatchItem* __restrict__ items) {
+__global__ void __launch_bounds__(NT + 32) kb_relax(const BatchProb* __restrict__ Pb, const BatchItem* __restrict__ items) {
   const BatchItem it = items[blockIdx.x];
   const BatchProb& q = Pb[it.prob];
   const T* fac;
@@ -533,10 +544,10 @@ cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set
   auto go = [&](auto nt, auto nc) {
     constexpr int NT = decltype(nt)::value, NC = decltype(nc)::value;
     if (fp32)
-      k_relax<float, NT, 1><<<lv.M, NT, smem, s>>>(lv, set_off, f32, r, (float*)delta, P, (float*)yscratch, ys, ctl,
+      k_relax<float, NT, 1><<<lv.M, NT + 32, smem, s>>>(lv, set_off, f32, r, (float*)delta, P, (float*)yscratch, ys, ctl,
                                                    err);
     else
-      k_relax<double, NT, NC><<<lv.M, NT, smem, s>>>(lv, set_off, f64, r, (double*)delta, P, (double*)yscratch, ys,
+      k_relax<double, NT, NC><<<lv.M, NT + 32, smem, s>>>(lv, set_off, f64, r, (double*)delta, P, (double*)yscratch, ys,
                                                      ctl, err);
   };
   const cudaError_t e = chunks == 2 ? dispatch_nt<2>(threads, go) : dispatch_nt<1>(threads, go);
@@ -549,8 +560,8 @@ cudaError_t launch_batch_relax(cudaStream_t s, bool fp32, int threads, int chunk
   if (n <= 0) return cudaSuccess;
   auto go = [&](auto nt, auto nc) {
     constexpr int NT = decltype(nt)::value, NC = decltype(nc)::value;
-    if (fp32) kb_relax<float, NT, 1><<<n, NT, smem, s>>>(P, it);
-    else kb_relax<double, NT, NC><<<n, NT, smem, s>>>(P, it);
+    if (fp32) kb_relax<float, NT, 1><<<n, NT + 32, smem, s>>>(P, it);
+    else kb_relax<double, NT, NC><<<n, NT + 32, smem, s>>>(P, it);
   };
   const cudaError_t e = chunks == 2 ? dispatch_nt<2>(threads, go) : dispatch_nt<1>(threads, go);
   if (e != cudaSuccess) return e;
