@@ -537,6 +537,7 @@ def run_ours(args, rank, world, local_rank):
     setup64 = capi.hms_problem_setup_ms(pr64)
     ms64, clocks = timed(pr64, args.steps, args.warmup, clocks=True)
     nit64 = int(its.item())
+    shape64 = {"threads": capi.hms_problem_relax_threads(pr64), "copies": capi.hms_problem_relax_copies(pr64)}
     u64 = u_dev.cpu().numpy().copy()
     # e2e through host buffers (pinned): H2D of the loads and D2H of u inside the timed region
     p_pin = torch.from_numpy(p_host).pin_memory()
@@ -556,10 +557,11 @@ def run_ours(args, rank, world, local_rank):
         setupm = capi.hms_problem_setup_ms(prm)
         msm, _ = timed(prm, args.steps, args.warmup)
         nitm = int(its.item())
+        shapem = {"threads": capi.hms_problem_relax_threads(prm), "copies": capi.hms_problem_relax_copies(prm)}
         um = u_dev.cpu().numpy()
         capi.hms_problem_destroy(prm)
         mixed = {"value": statistics.median(msm), "unit": "ms", "iterations": nitm, "setup_ms": setupm,
-                 "dtype": "f32 relax / f64 residual+master+norms",
+                 "dtype": "f32 relax / f64 residual+master+norms", "relax_launch": shapem,
                  "rel_diff_vs_fp64": float(np.linalg.norm(um - u64) / np.linalg.norm(u64)),
                  "err_vs_oracle_sampled": err_vs_oracle(um),
                  "speedup_vs_fp64": statistics.median(ms64) / statistics.median(msm)}
@@ -652,7 +654,7 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": c.nx, "ny": c.ny, "dofs": nd, "sets": [c.sx, c.sy],
                    "ea": "lognormal(0,0.3)", "loads": "Uniform(-1,1) seed 0", "tol": TOL,
-                   "iterations": nit64, "setup_ms": setup64,
+                   "iterations": nit64, "setup_ms": setup64, "relax_launch": shape64,
                    "l2": "working set > L2 (FP64 factors 2.2 GB streamed every iteration); no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "err_vs_oracle_sampled": err_vs_oracle(u64),
