@@ -117,6 +117,21 @@ def residual_work(c, fp32):
     return nodes * (16 * 4 + (8 if fp32 else 16) + 24 + 1), nodes * 110
 
 
+# FP64 instructions per node of the update/residual kernel, each one slot of the
+# FP64 pipe whatever its flops: 37 for the six bar forces, r and the three norm
+# terms, plus 17 for the upper-level update u += V a of each staged node (node
+# position, xi and eta, the mode sums; int-to-double conversions not counted),
+# of which a 32 x 8 tile stages (34 x 10) / (32 x 8) = 1.33 per node.
+RESIDUAL_FP64_INSTR_PER_NODE = 37 + 17 * (34 * 10) / (32 * 8)
+
+
+def residual_fp64_frac(c, avg_ms, n_sm, sm_mhz):
+    """Share of the FP64 pipe's instruction slots (SMs x DFMA lanes x clock)
+    the update/residual kernel's FP64 instructions fill."""
+    slots = n_sm * FP64_LANES_PER_SM_CLK * sm_mhz * 1e6 * avg_ms * 1e-3
+    return c.nx * c.ny * RESIDUAL_FP64_INSTR_PER_NODE / slots
+
+
 def src_sha(name):
     p = os.path.join(ROOT, "paper_1208_4093_gb300", "csrc", name)
     return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
@@ -615,8 +630,14 @@ def run_ours(args, rank, world, local_rank):
                      "traffic": traffic_for(roof["kernel"], WORKLOAD, "relax.cu")})
         rb, rf = residual_work(c, fp32)
         rms, rn = kt["update_residual"]
-        roof["update_residual"] = {"avg_launch_ms": rms / max(rn, 1),
-                                   "hbm_gbs": rb / (rms / max(rn, 1) * 1e-3) / 1e9}
+        ravg = rms / max(rn, 1)
+        n_sm1 = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz1 = (clocks or {}).get("sm_max_mhz") or 2070.0
+        roof["update_residual"] = {"avg_launch_ms": ravg, "hbm_gbs": rb / (ravg * 1e-3) / 1e9,
+                                   "hbm_frac": rb / (ravg * 1e-3) / 1e9 / hbm_peak,
+                                   "bound": "alu (FP64 pipe)",
+                                   "fp64_instr_per_node": RESIDUAL_FP64_INSTR_PER_NODE,
+                                   "fp64_frac": residual_fp64_frac(c, ravg, n_sm1, mhz1)}
         roof["kernel_ms"] = {k: v[0] for k, v in kt.items()}
         roof["kernel_launches"] = {k: v[1] for k, v in kt.items()}
         rooflines[name] = roof
