@@ -98,7 +98,8 @@ typedef struct {
                                 4 = FP32 on one SM, 5 = FP32 two-sided: top and bottom
                                 segments eliminated at once on two SMs, then the
                                 separator between them */
-  int32_t relax_threads;     /* CTA size of the relaxation (Eqs. 11-13): 64, 128 or 256, or
+  int32_t relax_threads;     /* compute threads per CTA of the relaxation (Eqs. 11-13; one more
+                                warp issues its copies): 64, 128 or 256, or
                                 0 = autotuned: the first problem of a set-tile shape and
                                 precision on a context times each size on its own factors
                                 and the context keeps the fastest for that shape.  Results
