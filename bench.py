@@ -33,6 +33,13 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "lattice1024_lognormal"
 TOL = 1e-8
 TOL_CONFIG = 1e-10  # the stopping level the 1024^2 lognormal configuration states
+METRIC = f"time to R1 < {TOL:g} (Eq. 19 1-norm relative residual), plain FP64 form"
+
+
+def workload_config(c):
+    """The config keys both arms report for the bench workload."""
+    return {"workload": WORKLOAD, "nx": c.nx, "ny": c.ny, "dofs": c.dofs, "sets": [c.sx, c.sy],
+            "ea": "lognormal(0,0.3)", "loads": "Uniform(-1,1) seed 0", "tol": TOL}
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 GOLDEN_FULL = os.path.join(ROOT, "tests", "golden", "lattice1024_lognormal_history.json")
 FP64_LANES_PER_SM_CLK = 2  # DFMA lanes per SM per clock on GB300 (ncu: sm__sass_thread_inst_executed_op_dfma peak)
@@ -281,12 +288,12 @@ def run_reference(args, rank, world):
             per.append(time.perf_counter() - t0)
     per_it = statistics.median(per)
     value = per_it * nir * 1e3 if nir else None
-    line = {"impl": "reference", "metric": f"time to R1 < {TOL:g} (Eq. 19)", "value": value, "unit": "ms",
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": value, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": c.nx, "ny": c.ny, "sets": [c.sx, c.sy], "ea": "lognormal(0,0.3)",
-                       "tol": TOL, "iterations": nir, "iterations_source": src},
+            "config": dict(workload_config(c), iterations=nir, iterations_source=src,
+                           parallelism="single host thread"),
             "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} single-iteration oracle steps on the full workload "
                                        f"({per_it:.2f} s each, setup excluded) x {nir} iterations"},
@@ -669,12 +676,11 @@ def run_ours(args, rank, world, local_rank):
         except Exception as e:  # the baseline is reported, never the target
             cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
     line = {
-        "metric": f"time to R1 < {TOL:g} (Eq. 19 1-norm relative residual), plain FP64 form",
+        "metric": METRIC,
         "value": ms_med, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_med, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": c.nx, "ny": c.ny, "dofs": nd, "sets": [c.sx, c.sy],
-                   "ea": "lognormal(0,0.3)", "loads": "Uniform(-1,1) seed 0", "tol": TOL,
+        "config": {**workload_config(c),
                    "iterations": nit64, "setup_ms": setup64, "relax_launch": shape64,
                    "l2": "working set > L2 (FP64 factors 2.2 GB streamed every iteration); no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
