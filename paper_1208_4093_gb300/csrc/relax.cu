@@ -17,7 +17,8 @@
 //   backward x_j = Linv_j^T (y_j - B_{j+1}^T x_{j+1})
 // so both passes are products of packed rows with a vector.  Each matrix is
 // staged in shared memory by a 1-D bulk copy (cp.async.bulk, completion on an
-// mbarrier), three slots deep so two matrices stream in while one is applied;
+// mbarrier), three slots deep so two matrices stream in while one is applied
+// (with one copy per matrix a step ends in the only barrier it has);
 // a B step's vector (r_j forward, y_{j-1} backward) comes in the same
 // transaction.  Rows r and nb-1-r of a matrix go to a group of G threads as
 // one combined index range of almost constant length (nb+1 for the triangles,
@@ -368,6 +369,7 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
   const size_t rowbase0 = 2 * ((size_t)j0 * lv.nx + i0);
   if (!producer)
     for (int t = tid; t < nb; t += NT) zbuf[t] = (T)rg[rowbase0 + t];
+  if (NC == 1) __syncthreads();  // z before op 0 reads it (two copies: op 0's own barrier)
 
   const double2 rep = lv.rep[I];
 
@@ -376,13 +378,28 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
     const bool is_b = (k & 1) != 0;
     const int j = is_b ? (k + 1) / 2 : k / 2;
     const bool last_copy = (o % NC) == NC - 1;  // the matrix's outputs are complete after it
-    if (!producer && !mbar_wait_bounded(&bars[o % NSLOT], (uint32_t)((o / NSLOT) & 1))) abort_flag = 1;
-    __syncthreads();
-    if (abort_flag) break;
-    // the slot of op o - 1 is free: stream op o + NSLOT - 1 into it
+    const bool late = !producer && !mbar_wait_bounded(&bars[o % NSLOT], (uint32_t)((o / NSLOT) & 1));
+    if (NC != 1) {
+      // after the first copy of a matrix there is no end-of-op barrier: this
+      // one frees its slot (and decides an abort the same way in every thread)
+      if (late) abort_flag = 1;
+      __syncthreads();
+      if (abort_flag) break;
+    }
+    // The slot of op o - 1 is free (one copy per matrix: since the barrier
+    // that ended op o - 1): stream op o + NSLOT - 1 into it.  With one copy,
+    // a wait that ran out is voted on at the end of the op, so every thread
+    // leaves the loop there together.
     if (producer) {
       if (tid == NT && o + NSLOT - 1 < nops) issue(o + NSLOT - 1);
-      if (last_copy) __syncthreads();
+      if (NC == 1) {
+        if (__syncthreads_or(0)) {
+          abort_flag = 1;
+          break;
+        }
+      } else if (last_copy) {
+        __syncthreads();
+      }
       continue;
     }
     const T* M = sm + (size_t)(o % NSLOT) * LY.slot_elems;
@@ -409,7 +426,6 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
               yj[row] = s;
             });
       }
-      if (last_copy) __syncthreads();
     } else {
       // ---------------- backward ----------------
       if (!is_b) {
@@ -429,7 +445,14 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
             M, xbuf, nb, pa, pb, base_lo, cut, base_hi, [&](int row) { return yp[row]; },
             [&](int row, T s, T pre) { wbuf[row] = pre - s; });
       }
-      if (last_copy) __syncthreads();
+    }
+    if (NC == 1) {
+      if (__syncthreads_or(late)) {
+        abort_flag = 1;
+        break;
+      }
+    } else if (last_copy) {
+      __syncthreads();
     }
   }
   if (abort_flag) {
