@@ -109,6 +109,14 @@ typedef struct {
                                 half the shared memory per CTA, so two CTAs share an SM;
                                 even set widths >= 6 only), or 0 = with relax_threads = 0
                                 timed together with it, else 1.  Same results either way */
+  int32_t relax_overlap;     /* extended relaxation region (Sec. 2.2, the region around a
+                                set in Fig. 1): each set relaxes together with the nodes
+                                within relax_overlap nodes of its tile (clipped to the
+                                lattice), all other DOFs held, and keeps its own nodes' part
+                                of the increment as its mode of Eq. 13.  0 = the set itself.
+                                The grown tile must be at most 64 nodes wide
+                                (min(nx, set_sx + 2 relax_overlap) <= 64); with overlap the
+                                FP64 relaxation uses one copy per matrix */
 } hms_options;
 
 /* Context: one device, one CUDA stream.  device = CUDA ordinal. */

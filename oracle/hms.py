@@ -29,6 +29,9 @@ Readings (the paper is silent on these):
   the last tile of a row or column takes the remainder;
 * q = 9 (the displacement-controlled modes only); the force-controlled modes
   10-12 of Eqs. 15-18 are not part of this iteration;
+* an extended relaxation region (``LocalFactors(overlap=e)``) relaxes the set
+  together with a ring of e nodes around it and keeps the set's part of the
+  increment as its mode;
 * a mode whose diagonal entry of K_aa is <= 1e-300, or <= 1e-28 times the
   largest diagonal entry among its set's nine modes (the mode vanishes on the
   set's free DOFs up to rounding, e.g. eta-modes of a one-row set), or whose
@@ -89,29 +92,52 @@ def rep_points(truss: Truss, grid: SetGrid):
 
 
 class LocalFactors:
-    """k^Inner of every set, factored once (end of Sec. 2.2)."""
+    """k^Inner of every set's relaxation region, factored once (end of Sec. 2.2).
 
-    def __init__(self, truss: Truss, grid: SetGrid):
-        ns = grid.node_set().reshape(-1)
-        dof_set = np.repeat(ns, 2)
-        self.dofs = []
+    With ``overlap`` = e > 0 the relaxation region of set I is extended as
+    Sec. 2.2 allows (the region drawn around Set_I in Fig. 1): the nodes within
+    e nodes of the set's tile in i and in j, clipped to the lattice.  k^Inner is
+    then K restricted to the region's free DOFs, every DOF outside the region is
+    held, and the mode delta_I of Eq. 13 is the region's increment restricted
+    to the set's own DOFs (reading: the sets stay disjoint, so V keeps one block
+    of modes per set).  e = 0 is the set itself.
+    """
+
+    def __init__(self, truss: Truss, grid: SetGrid, overlap: int = 0):
+        if overlap < 0:
+            raise ValueError("overlap must be >= 0")
+        self.overlap = overlap
+        jn, inode = np.meshgrid(np.arange(grid.ny), np.arange(grid.nx), indexing="ij")
+        self.dofs = []     # the set's free DOFs
+        self.region = []   # the region's free DOFs (ascending)
+        self.pos = []      # where the set's DOFs sit in the region's
         self.factors = []
         K = truss.K.tocsr()
         for I in range(grid.M):
-            d = np.flatnonzero((dof_set == I) & truss.free)
+            Ix, Iy = I % grid.Mx, I // grid.Mx
+            i0, j0 = Ix * grid.sx, Iy * grid.sy
+            i1, j1 = min(grid.nx, i0 + grid.sx), min(grid.ny, j0 + grid.sy)
+            in_set = (inode >= i0) & (inode < i1) & (jn >= j0) & (jn < j1)
+            e = overlap
+            in_reg = (inode >= i0 - e) & (inode < i1 + e) & (jn >= j0 - e) & (jn < j1 + e)
+            d = np.flatnonzero(np.repeat(in_set.reshape(-1), 2) & truss.free)
+            dr = np.flatnonzero(np.repeat(in_reg.reshape(-1), 2) & truss.free)
             self.dofs.append(d)
+            self.region.append(dr)
+            self.pos.append(np.searchsorted(dr, d))
             if d.size == 0:
                 self.factors.append(None)
                 continue
-            kin = K[d][:, d]
+            kin = K[dr][:, dr]
             self.factors.append(sla.cholesky_banded(to_lower_band(kin), lower=True))
 
     def relax(self, r: np.ndarray) -> np.ndarray:
-        """delta with delta_I = (k^Inner_I)^-1 r_I on every set (Eqs. 12-13)."""
+        """delta with delta_I = [(k^Inner_R)^-1 r_R] on set I's DOFs, R its
+        relaxation region (Eqs. 12-13; R = I without overlap)."""
         delta = np.zeros_like(r)
-        for d, cb in zip(self.dofs, self.factors):
+        for d, dr, pos, cb in zip(self.dofs, self.region, self.pos, self.factors):
             if cb is not None:
-                delta[d] = sla.cho_solve_banded((cb, True), r[d])
+                delta[d] = sla.cho_solve_banded((cb, True), r[dr])[pos]
         return delta
 
 

@@ -55,7 +55,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("coarse_solves", ctypes.c_int32), ("batch", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("coarse_factor", ctypes.c_int32), ("relax_threads", ctypes.c_int32),
-                ("relax_copies", ctypes.c_int32)]
+                ("relax_copies", ctypes.c_int32), ("relax_overlap", ctypes.c_int32)]
 
 
 _lib = None
@@ -189,7 +189,7 @@ def hms_last_error(ctx) -> str:
 
 def _desc_opts(nx, ny, set_sx, set_sy, bar_length=1.0, ea=None, ea_uniform=1.0, fixed=None, fix_bottom_edge=1,
                precision=HMS_FP64, tol=1e-8, max_iter=1000, coarse_solves=0, batch=0, profile=0, coarse_factor=0,
-               relax_threads=0, relax_copies=0):
+               relax_threads=0, relax_copies=0, relax_overlap=0):
     """LatticeDesc and Options structs (plus the arrays they point to, kept alive by the caller)."""
     ea_a = None if ea is None else np.ascontiguousarray(ea, dtype=np.float64)
     fx_a = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
@@ -201,14 +201,14 @@ def _desc_opts(nx, ny, set_sx, set_sy, bar_length=1.0, ea=None, ea_uniform=1.0, 
                     float(ea_uniform), None if fx_a is None else fx_a.ctypes.data, int(fix_bottom_edge),
                     int(set_sx), int(set_sy))
     o = Options(int(precision), float(tol), int(max_iter), int(coarse_solves), int(batch), int(profile),
-                int(coarse_factor), int(relax_threads), int(relax_copies))
+                int(coarse_factor), int(relax_threads), int(relax_copies), int(relax_overlap))
     return d, o, (ea_a, fx_a)
 
 
 def hms_problem_create(ctx, nx, ny, set_sx, set_sy, **kw):
     """kw: bar_length, ea (host float64 [3, ny, nx]), ea_uniform, fixed (host uint8
     [ny, nx, 2]), fix_bottom_edge, precision, tol, max_iter, coarse_solves, batch,
-    profile, coarse_factor, relax_threads, relax_copies."""
+    profile, coarse_factor, relax_threads, relax_copies, relax_overlap."""
     d, o, keep = _desc_opts(nx, ny, set_sx, set_sy, **kw)
     h = _P()
     _check(ctx, lib().hms_problem_create(ctx, ctypes.byref(d), ctypes.byref(o), ctypes.byref(h)))

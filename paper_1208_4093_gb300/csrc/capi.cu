@@ -645,6 +645,8 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (o->relax_threads != 0 && o->relax_threads != 64 && o->relax_threads != 128 && o->relax_threads != 256)
     return fail(c, HMS_ERR_ARG, "relax_threads must be 0, 64, 128 or 256");
   if (o->relax_copies < 0 || o->relax_copies > 2) return fail(c, HMS_ERR_ARG, "relax_copies must be 0, 1 or 2");
+  if (o->relax_overlap < 0 || std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_SX)
+    return fail(c, HMS_ERR_ARG, "relax_overlap must be >= 0 with min(nx, set_sx + 2 relax_overlap) <= 64");
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
 
@@ -659,6 +661,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   lv.Mx = (d->nx + d->set_sx - 1) / d->set_sx;
   lv.My = (d->ny + d->set_sy - 1) / d->set_sy;
   lv.M = lv.Mx * lv.My;
+  lv.ov = o->relax_overlap;
   lv.L = d->bar_length;
   lv.k_u = d->ea ? 0.0 : d->ea_uniform / d->bar_length;
   pr->precision = o->precision;
@@ -747,7 +750,8 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
       for (int j = j0; j < j0 + h; ++j) nodd += (j & 1);
       rp[I].x = lv.L * ((double)i0 + 0.5 * (double)(w - 1) + 0.5 * (double)nodd / (double)h);
       rp[I].y = lv.L * SQ3_2 * ((double)j0 + 0.5 * (double)(h - 1));
-      so[I + 1] = so[I] + set_factor_stride(2 * w, h);
+      const Region R = relax_region(lv, I);  // the factor is the relaxation region's
+      so[I + 1] = so[I] + set_factor_stride(2 * R.w, R.h);
     }
     CKP(salloc(pr, &pr->rep, lv.M));
     CKP(cudaMemcpy(pr->rep, rp.data(), lv.M * sizeof(double2), cudaMemcpyHostToDevice));
@@ -1521,6 +1525,7 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
                     size_t* scratch) {
   if (!c || !d || !o || d->nx < 2 || d->ny < 2 || d->set_sx < 1 || d->set_sx > MAX_SX || d->set_sy < 1) return false;
   if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return false;
+  if (o->relax_overlap < 0 || std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_SX) return false;
   hms_problem pr;
   LatView& lv = pr.lv;
   lv.nx = d->nx;
@@ -1530,6 +1535,7 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
   lv.Mx = (d->nx + d->set_sx - 1) / d->set_sx;
   lv.My = (d->ny + d->set_sy - 1) / d->set_sy;
   lv.M = lv.Mx * lv.My;
+  lv.ov = o->relax_overlap;
   pr.precision = o->precision;
   pr.n_c = NMODES * lv.M;
   pr.bw = coarse_bw(lv);
@@ -1543,8 +1549,8 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
   const size_t nband = n_c * (pr.bw + 1);
   size_t fac = 0;
   for (int I = 0; I < lv.M; ++I) {
-    const int w = std::min(lv.sx, lv.nx - (I % lv.Mx) * lv.sx), h = std::min(lv.sy, lv.ny - (I / lv.Mx) * lv.sy);
-    fac += (size_t)set_factor_stride(2 * w, h);
+    const Region R = relax_region(lv, I);
+    fac += (size_t)set_factor_stride(2 * R.w, R.h);
   }
   *shared = nn + (d->ea ? 3 * nn * 8 : 0) + M * 16 + (M + 1) * 8 + fac * esz + M * NSLOTS * SLOT_SIZE * 8;
   size_t b = 4 * nn * 16 + nn * 2 * esz + M * (size_t)relax_y_stride(lv) * esz;

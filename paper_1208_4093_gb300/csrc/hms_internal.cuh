@@ -33,6 +33,7 @@ enum DevErr { DEVERR_NOT_SPD = 1, DEVERR_TIMEOUT = 2, DEVERR_NONFINITE = 4, DEVE
 // Read-only description of the lattice and its set partition, by value.
 struct LatView {
   int nx, ny, sx, sy, Mx, My, M;
+  int ov;          // relaxation region: the set's tile grown by ov nodes (Sec. 2.2)
   double L;        // bar length
   double k_u;      // EA/L when kbar == nullptr
   const double* kbar;
@@ -55,6 +56,28 @@ struct IterCtl {
 __host__ __device__ inline size_t nnodes_of(const LatView& lv) { return (size_t)lv.nx * lv.ny; }
 __host__ __device__ inline int set_of(const LatView& lv, int i, int j) {
   return (j / lv.sy) * lv.Mx + (i / lv.sx);
+}
+// Relaxation region of set I: its tile grown by lv.ov nodes in i and j,
+// clipped to the lattice (origin i0, j0; w x h nodes).  ov = 0: the set.
+struct Region {
+  int i0, j0, w, h;
+};
+__host__ __device__ inline Region relax_region(const LatView& lv, int I) {
+  const int si0 = (I % lv.Mx) * lv.sx, sj0 = (I / lv.Mx) * lv.sy;
+  const int si1 = si0 + lv.sx < lv.nx ? si0 + lv.sx : lv.nx, sj1 = sj0 + lv.sy < lv.ny ? sj0 + lv.sy : lv.ny;
+  Region R;
+  R.i0 = si0 - lv.ov > 0 ? si0 - lv.ov : 0;
+  R.j0 = sj0 - lv.ov > 0 ? sj0 - lv.ov : 0;
+  R.w = (si1 + lv.ov < lv.nx ? si1 + lv.ov : lv.nx) - R.i0;
+  R.h = (sj1 + lv.ov < lv.ny ? sj1 + lv.ov : lv.ny) - R.j0;
+  return R;
+}
+// bounds of every region's width and height (scratch and shared-memory sizes)
+__host__ __device__ inline int region_w_max(const LatView& lv) {
+  return lv.sx + 2 * lv.ov < lv.nx ? lv.sx + 2 * lv.ov : lv.nx;
+}
+__host__ __device__ inline int region_h_max(const LatView& lv) {
+  return lv.sy + 2 * lv.ov < lv.ny ? lv.sy + 2 * lv.ov : lv.ny;
 }
 __host__ __device__ inline double node_x(const LatView& lv, int i, int j) {
   return lv.L * ((double)i + 0.5 * (double)(j & 1));

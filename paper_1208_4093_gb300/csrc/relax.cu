@@ -257,11 +257,9 @@ __device__ inline void rows_times(const T* M, const T* v, int nb, int pa, int pb
   }
 }
 
-// Entries of one set's slice of the y scratch (the widest, tallest set).
+// Entries of one set's slice of the y scratch (the widest, tallest relaxation region).
 __host__ __device__ inline long long y_stride(const LatView& lv) {
-  const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
-  const int h = lv.sy < lv.ny ? lv.sy : lv.ny;
-  return (long long)y_row(2 * w) * h;
+  return (long long)y_row(2 * region_w_max(lv)) * region_h_max(lv);
 }
 
 // The kernel body for set I.
@@ -280,9 +278,14 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
   const int tid = threadIdx.x, lane = tid & 31;
   const bool producer = tid >= NT;  // the last warp issues the copies
   const int Ix = I % lv.Mx, Iy = I / lv.Mx;
-  const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
+  const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;  // the set (its P sums)
   const int w = min(lv.sx, lv.nx - i0), h = min(lv.sy, lv.ny - j0);
-  const int nb = 2 * w;
+  // the relaxation region the solve runs on (the set itself without overlap);
+  // delta is kept on the set's own nodes
+  const Region RG = relax_region(lv, I);
+  const int ri0 = RG.i0, rj0 = RG.j0, rh = RG.h;
+  const int nb = 2 * RG.w;
+  const int keep_lo = 2 * (i0 - ri0), keep_hi = keep_lo + 2 * w;  // the set's DOFs within a region row
   const RelaxSmem LY = relax_layout<T, NC>(nb);
   const int r1 = NC == 2 ? chunk_r1<T>(nb) : 0;
   T* sm = reinterpret_cast<T*>(smraw);
@@ -292,9 +295,9 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
   T* xbuf = sm + LY.x_off;
   T* yg = yglob + (size_t)I * ystride;  // all y_j, read back by the backward pass
   const T* fset = fac + set_off[I];
-  const T* fset_t = fset + set_factor_size(nb, h);  // the copy stored by columns
+  const T* fset_t = fset + set_factor_size(nb, rh);  // the copy stored by columns
   const double* rg = reinterpret_cast<const double*>(r);
-  const int nmat = 2 * h - 1;
+  const int nmat = 2 * rh - 1;
   const int nops = 2 * nmat * NC;  // one op per matrix copy (NC per matrix)
 
   auto mat_of_op = [&](int o) {
@@ -315,7 +318,7 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
     T* dst = sm + (size_t)(o % NSLOT) * LY.slot_elems;
     // a B step's vector: r_j (forward; 16 bytes per node) or y_{j-1} (backward; rows of nbr entries)
     const int jv = (k + 1) / 2;
-    const void* vsrc = fwd ? (const void*)(rg + 2 * ((size_t)(j0 + jv) * lv.nx + i0))
+    const void* vsrc = fwd ? (const void*)(rg + 2 * ((size_t)(rj0 + jv) * lv.nx + ri0))
                            : (const void*)(yg + (size_t)(jv - 1) * nbr);
     const uint32_t vbytes = (k & 1) ? (uint32_t)(fwd ? nb * sizeof(double) : nbr * sizeof(T)) : 0u;
     T* vdst = sm + LY.vec_off + (size_t)(o % NSLOT) * LY.vec_elems;
@@ -366,7 +369,7 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
   if (tid == NT)
     for (int o = 0; o < NSLOT - 1 && o < nops; ++o) issue(o);
   // z = r_0
-  const size_t rowbase0 = 2 * ((size_t)j0 * lv.nx + i0);
+  const size_t rowbase0 = 2 * ((size_t)rj0 * lv.nx + ri0);
   if (!producer)
     for (int t = tid; t < nb; t += NT) zbuf[t] = (T)rg[rowbase0 + t];
   if (NC == 1) __syncthreads();  // z before op 0 reads it (two copies: op 0's own barrier)
@@ -430,13 +433,14 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
       // ---------------- backward ----------------
       if (!is_b) {
         // x_j = Linv_j^T w  (w = y_{h-1} for the last row)
-        const T* wv = (j == h - 1) ? ycur : wbuf;
-        const size_t rowbase = 2 * ((size_t)(j0 + j) * lv.nx + i0);
+        const T* wv = (j == rh - 1) ? ycur : wbuf;
+        const size_t rowbase = 2 * ((size_t)(rj0 + j) * lv.nx + ri0);
+        const bool keep_row = rj0 + j >= j0 && rj0 + j < j0 + h;
         rows_times<NT, T, G, CH, ROW_LT>(
             M, wv, nb, pa, pb, base_lo, cut, base_hi, [](int) { return T(0); },
             [&](int row, T s, T) {
               xbuf[row] = s;
-              delta[rowbase + row] = s;
+              if (keep_row && row >= keep_lo && row < keep_hi) delta[rowbase + row] = s;
             });
       } else {
         // w = y_{j-1} - B_j^T x_j (y_{j-1} staged with B_j^T)
@@ -531,7 +535,7 @@ __global__ void __launch_bounds__(NT + 32) kb_relax(const BatchProb* __restrict_
 }  // namespace
 
 size_t relax_smem_bytes(const LatView& lv, bool fp32, int chunks) {
-  const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
+  const int w = region_w_max(lv);
   if (chunks == 2 && !fp32) return relax_layout<double, 2>(2 * w).total_elems * sizeof(double);
   return fp32 ? relax_layout<float>(2 * w).total_elems * sizeof(float)
               : relax_layout<double>(2 * w).total_elems * sizeof(double);
@@ -540,7 +544,7 @@ size_t relax_smem_bytes(const LatView& lv, bool fp32, int chunks) {
 // Two copies per matrix apply to the FP64 relaxation when every set width of
 // the lattice has a split row r1 (the regular width and the ragged last one).
 bool relax_chunks_possible(const LatView& lv, bool fp32) {
-  if (fp32) return false;
+  if (fp32 || lv.ov > 0) return false;  // with overlap the region widths vary: one copy
   const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
   const int wr = lv.nx - (lv.Mx - 1) * lv.sx;  // last column of sets
   return chunk_r1<double>(2 * w) > 0 && chunk_r1<double>(2 * wr) > 0;

@@ -2,8 +2,9 @@
 // Eq. 12 do not change during the iteration, so they are factored in the
 // first iteration and the factors are reused).
 //
-// k^Inner_I is K restricted to the free DOFs of set I (Eq. 11: its entries
-// are those of the global matrix).  Constrained DOFs are kept as identity
+// k^Inner_I is K restricted to the free DOFs of set I's relaxation region
+// (the set, or its tile grown by lv.ov nodes: Sec. 2.2's extended region; Eq.
+// 11: its entries are those of the global matrix).  Constrained DOFs are kept as identity
 // rows/columns so that every set row has the same layout; their right-hand
 // side is always 0, which leaves the free-DOF solution unchanged.
 //
@@ -50,9 +51,9 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
   __shared__ double diag0[MAX_NB];
 
   for (int I = blockIdx.x; I < lv.M; I += gridDim.x) {
-    const int Ix = I % lv.Mx, Iy = I / lv.Mx;
-    const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
-    const int w = min(lv.sx, lv.nx - i0), h = min(lv.sy, lv.ny - j0);
+    // the set's relaxation region (the set itself without overlap)
+    const Region R = relax_region(lv, I);
+    const int i0 = R.i0, j0 = R.j0, w = R.w, h = R.h;
     const int nb = 2 * w;
     const long long npk = pk(nb - 1, nb - 1) + 1;
     double* S = sm;          // packed lower nb x nb
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
 
 cudaError_t launch_set_factor(cudaStream_t s, const LatView& lv, const long long* set_off,
                               double* f64, float* f32, double* scratch, int grid, int* err) {
-  const int nb = 2 * (lv.sx < lv.nx ? lv.sx : lv.nx);
+  const int nb = 2 * region_w_max(lv);
   const size_t smem = 2 * (size_t)((long long)nb * (nb + 1) / 2) * sizeof(double);
   k_set_factor<<<grid, NT, smem, s>>>(lv, set_off, f64, f32, scratch, err);
   return cudaGetLastError();

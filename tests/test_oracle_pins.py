@@ -394,3 +394,57 @@ def test_pins_catch_a_sign_error_in_the_residual(monkeypatch):
     res = hms.solve(tr, g, p, tol=1e-10, max_iter=30)
     u_ref = direct.cholesky_solve(tr, p)
     assert not res.converged or np.linalg.norm(res.u - u_ref) > 1e-3 * np.linalg.norm(u_ref)
+
+
+# ---------------------------------------------------------------- extended relaxation regions
+def region_dofs(tr, g, I, e):
+    """Free DOFs of set I's tile grown by e nodes, from node indices alone."""
+    Ix, Iy = I % g.Mx, I // g.Mx
+    i0, j0 = Ix * g.sx, Iy * g.sy
+    out = []
+    for n in range(tr.nx * tr.ny):
+        i, j = n % tr.nx, n // tr.nx
+        if i0 - e <= i < min(tr.nx, i0 + g.sx) + e and j0 - e <= j < min(tr.ny, j0 + g.sy) + e:
+            out += [2 * n + c for c in range(2) if tr.free[2 * n + c]]
+    return np.array(out)
+
+
+@pytest.mark.parametrize("e", [1, 3])
+def test_overlap_relaxation_solves_the_region(e):
+    """delta_I is the solution of K restricted to the grown region (every other
+    DOF held), taken on the set's own DOFs (Sec. 2.2, the extended region)."""
+    tr = truss.Truss(13, 11, ea_lognormal(13, 11, 5))
+    g = hms.SetGrid(13, 11, 5, 4)
+    p = loads(13, 11, 9, 0).reshape(-1)
+    r = tr.residual(p, np.zeros(tr.ndof))
+    delta = hms.LocalFactors(tr, g, overlap=e).relax(r)
+    K = tr.K.toarray()
+    for I in (0, 4, g.M - 1):
+        dr = region_dofs(tr, g, I, e)
+        ds = region_dofs(tr, g, I, 0)
+        sol = np.linalg.solve(K[np.ix_(dr, dr)], r[dr])
+        want = sol[np.searchsorted(dr, ds)]
+        assert np.allclose(delta[ds], want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+def test_overlap_covering_the_lattice_is_one_direct_update():
+    """Grown over the whole lattice, every set's relaxation is the direct
+    solution on its DOFs, so the modes delta_I add up to it and one update
+    reaches it."""
+    tr = truss.Truss(24, 20)
+    g = hms.SetGrid(24, 20, 8, 8)
+    p = loads(24, 20, 3, 0).reshape(-1)
+    res = hms.solve(tr, g, p, 1e-12, 5, factors=hms.LocalFactors(tr, g, overlap=24))
+    ref = direct.cholesky_solve(tr, tr.free * p)
+    assert res.iterations == 1
+    assert np.linalg.norm(res.u - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_overlap_reduces_iterations():
+    """A larger relaxation region needs fewer updates (Sec. 2.2)."""
+    tr = truss.Truss(24, 20)
+    g = hms.SetGrid(24, 20, 8, 8)
+    p = loads(24, 20, 3, 0).reshape(-1)
+    nir = [hms.solve(tr, g, p, 1e-8, 500, factors=hms.LocalFactors(tr, g, overlap=e)).iterations
+           for e in (0, 1, 4)]
+    assert nir[0] > nir[1] > nir[2]
