@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--nir-sweep", action="store_true",
                     help="NIR (updates to R1 < 1e-8) versus set size at 8 x 8 sets, and versus the number "
                          "of 32 x 32-node sets (the shapes of the paper's Tests 2 and 3), FP64, 4 loadings")
+    ap.add_argument("--overlap-sweep", action="store_true",
+                    help="time to R1 < 1e-8 against the relaxation region's overlap instead (separate JSON line)")
     ap.add_argument("--serve", type=int, default=0, metavar="N",
                     help="serve N requests of the serving workload instead (separate JSON line)")
     ap.add_argument("--serve-max-active", type=int, default=4,
@@ -446,6 +448,52 @@ def run_nir_sweep(args):
                       "test2_fixed_sets_8x8": test2, "test3_sets_of_32x32": test3}))
 
 
+def run_overlap_sweep(args):
+    """Extended relaxation regions (Sec. 2.2): a 512 x 1024-node lognormal
+    lattice with 32 x 32-node sets (16 x 32 sets, the widest set grid the
+    upper-level band factor takes at this set size), each set relaxed over its
+    tile grown by e nodes, e = 0 .. 16; updates to R1 < 1e-8, setup (factoring
+    the regions) and the time of one whole solve after a warm-up solve (CUDA
+    events on the context stream), per form.  A larger region needs fewer
+    updates but each relaxation does more work (Sec. 2.2)."""
+    import numpy as np
+    import torch
+    from paper_1208_4093_gb300 import capi
+    from workloads import ea_lognormal, loads
+    nx, ny = 512, 1024
+    ea = ea_lognormal(nx, ny, 1000)
+    ctx = capi.hms_context_create(0)
+    stream = torch.cuda.ExternalStream(capi.hms_context_stream(ctx), device=torch.device("cuda", 0))
+    p = torch.from_numpy(loads(nx, ny, 0).reshape(1, -1)).cuda()
+    u = torch.empty_like(p)
+    its = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rows = []
+    for prec, name in ((capi.HMS_FP64, "fp64"), (capi.HMS_MIXED, "mixed")):
+        for e in (0, 1, 2, 4, 8, 16):
+            pr = capi.hms_problem_create(ctx, nx, ny, 32, 32, ea=ea, precision=prec, tol=TOL,
+                                         max_iter=5000, relax_overlap=e)
+            try:
+                setup = capi.hms_problem_setup_ms(pr)
+                capi.hms_solve(ctx, pr, p, u, iters=its)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                capi.hms_solve(ctx, pr, p, u, iters=its)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms, nir = a.elapsed_time(b), int(its.item())
+                rows.append({"form": name, "overlap": e, "updates": nir, "ms": ms, "ms_per_update": ms / max(nir, 1),
+                             "setup_ms": setup, "device_bytes": capi.hms_problem_device_bytes(pr)})
+            finally:
+                capi.hms_problem_destroy(pr)
+    capi.hms_context_destroy(ctx)
+    print(json.dumps({"metric": "time to R1 < 1e-8 against the relaxation region's overlap", "unit": "ms",
+                      "config": {"workload": "lattice512x1024_lognormal, 32 x 32-node sets", "nx": nx, "ny": ny,
+                                 "sets": [32, 32], "ea": "lognormal(0,0.3)", "loads": "Uniform(-1,1) seed 0",
+                                 "tol": TOL},
+                      "rows": rows}))
+
+
 # ---------------------------------------------------------------- serving
 def run_serve(args):
     """Requests arrive by a Poisson process (mean 200 per second) with
@@ -719,6 +767,8 @@ def main():
             run_batched(args)
         elif args.nir_sweep:
             run_nir_sweep(args)
+        elif args.overlap_sweep:
+            run_overlap_sweep(args)
         elif args.serve:
             run_serve(args)
         elif args.impl == "reference":

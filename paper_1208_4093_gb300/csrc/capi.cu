@@ -23,7 +23,7 @@ struct hms_context {
   std::vector<cudaStream_t> pool;  // streams of hms_solve_batch, created on first use
   std::string err;
   // relaxation CTA size picked by timing, per (set width, set height, precision)
-  std::map<std::tuple<int, int, int>, int> relax_tuned;
+  std::map<std::tuple<int, int, int, int>, int> relax_tuned;  // (set w, set h, precision, copies, overlap)
   int batch_mode = HMS_BATCH_AUTO;
 };
 
@@ -577,7 +577,9 @@ static cudaError_t alloc_instance(hms_problem* pr) {
 static cudaError_t autotune_relax(hms_problem* pr, int copies) {
   hms_context* c = pr->ctx;
   const LatView& lv = pr->lv;
-  const auto key = std::make_tuple(std::min(lv.sx, lv.nx), std::min(lv.sy, lv.ny), pr->precision * 10 + copies);
+  // the relaxation region's overlap changes the factors' shapes and rules out
+  // two copies per matrix, so it is part of the key
+  const auto key = std::make_tuple(std::min(lv.sx, lv.nx), std::min(lv.sy, lv.ny), pr->precision * 10 + copies, lv.ov);
   const auto it = c->relax_tuned.find(key);
   if (it != c->relax_tuned.end()) {
     pr->relax_threads = it->second / 10;

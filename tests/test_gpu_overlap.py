@@ -155,3 +155,27 @@ def test_overlap_rejections(hms_ctx):
     # the grown tile is clipped to the lattice: 40 nodes wide is fine at any overlap
     pr = capi.hms_problem_create(hms_ctx, 40, 24, 32, 8, relax_overlap=40)
     capi.hms_problem_destroy(pr)
+
+
+def test_overlap_after_the_same_set_shape_without(hms_ctx):
+    """The launch-shape tuner keeps its choice per set shape, precision and
+    overlap: a shape tuned without overlap (where two copies per matrix may
+    win) must not hand that choice to a problem with overlap."""
+    from paper_1208_4093_gb300 import capi
+    nx, ny = 52, 40
+    p = loads(nx, ny, 6).reshape(1, -1)
+    a = capi.hms_problem_create(hms_ctx, nx, ny, 26, 20, tol=1e-10, max_iter=500, relax_copies=2)
+    b = capi.hms_problem_create(hms_ctx, nx, ny, 26, 20, tol=1e-10, max_iter=500)
+    c = capi.hms_problem_create(hms_ctx, nx, ny, 26, 20, tol=1e-10, max_iter=500, relax_overlap=3)
+    try:
+        assert capi.hms_problem_relax_copies(c) == 1
+        ua, uc = np.empty_like(p), np.empty_like(p)
+        capi.hms_solve(hms_ctx, a, p, ua)
+        capi.hms_solve(hms_ctx, c, p, uc)
+        tr = truss.Truss(nx, ny)
+        ref = direct.cholesky_solve(tr, tr.free * p[0])
+        assert rel(uc[0], ref) < 1e-9 and rel(ua[0], ref) < 1e-9
+        assert capi.hms_problem_relax_copies(b) in (1, 2)
+    finally:
+        for q in (a, b, c):
+            capi.hms_problem_destroy(q)
