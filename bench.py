@@ -486,8 +486,35 @@ def run_overlap_sweep(args):
                              "setup_ms": setup, "device_bytes": capi.hms_problem_device_bytes(pr)})
             finally:
                 capi.hms_problem_destroy(pr)
+    # the 1024^2 lognormal workload's own 64 x 64-node sets: regions up to 80
+    # nodes wide, which the mixed path's FP32 factors take
+    from workloads import CASES
+    c = CASES["lattice1024_lognormal_fp64"]
+    p2 = torch.from_numpy(c.load_array().reshape(1, -1)).cuda()
+    u2 = torch.empty_like(p2)
+    rows1024 = []
+    for e in (0, 2, 4, 8):
+        pr = capi.hms_problem_create(ctx, c.nx, c.ny, c.sx, c.sy, ea=c.ea_array(), precision=capi.HMS_MIXED,
+                                     tol=TOL, max_iter=5000, relax_overlap=e)
+        try:
+            setup = capi.hms_problem_setup_ms(pr)
+            capi.hms_solve(ctx, pr, p2, u2, iters=its)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            capi.hms_solve(ctx, pr, p2, u2, iters=its)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms, nir = a.elapsed_time(b), int(its.item())
+            rows1024.append({"form": "mixed", "overlap": e, "updates": nir, "ms": ms,
+                             "ms_per_update": ms / max(nir, 1), "setup_ms": setup,
+                             "device_bytes": capi.hms_problem_device_bytes(pr),
+                             "err_vs_oracle_sampled": err_vs_oracle(u2.cpu().numpy())})
+        finally:
+            capi.hms_problem_destroy(pr)
     capi.hms_context_destroy(ctx)
     print(json.dumps({"metric": "time to R1 < 1e-8 against the relaxation region's overlap", "unit": "ms",
+                      "lattice1024_lognormal_mixed": rows1024,
                       "config": {"workload": "lattice512x1024_lognormal, 32 x 32-node sets", "nx": nx, "ny": ny,
                                  "sets": [32, 32], "ea": "lognormal(0,0.3)", "loads": "Uniform(-1,1) seed 0",
                                  "tol": TOL},

@@ -114,9 +114,10 @@ typedef struct {
                                 within relax_overlap nodes of its tile (clipped to the
                                 lattice), all other DOFs held, and keeps its own nodes' part
                                 of the increment as its mode of Eq. 13.  0 = the set itself.
-                                The grown tile must be at most 64 nodes wide
-                                (min(nx, set_sx + 2 relax_overlap) <= 64); with overlap the
-                                FP64 relaxation uses one copy per matrix */
+                                The grown tile must be at most 80 nodes wide
+                                (min(nx, set_sx + 2 relax_overlap) <= 80), and at most 64 on
+                                the FP64 path (the relaxation kernel's shared memory); with
+                                overlap the FP64 relaxation uses one copy per matrix */
 } hms_options;
 
 /* Context: one device, one CUDA stream.  device = CUDA ordinal. */

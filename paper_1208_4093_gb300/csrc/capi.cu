@@ -647,8 +647,10 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (o->relax_threads != 0 && o->relax_threads != 64 && o->relax_threads != 128 && o->relax_threads != 256)
     return fail(c, HMS_ERR_ARG, "relax_threads must be 0, 64, 128 or 256");
   if (o->relax_copies < 0 || o->relax_copies > 2) return fail(c, HMS_ERR_ARG, "relax_copies must be 0, 1 or 2");
-  if (o->relax_overlap < 0 || std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_SX)
-    return fail(c, HMS_ERR_ARG, "relax_overlap must be >= 0 with min(nx, set_sx + 2 relax_overlap) <= 64");
+  if (o->relax_overlap < 0 || std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_RX)
+    return fail(c, HMS_ERR_ARG, "relax_overlap must be >= 0 with min(nx, set_sx + 2 relax_overlap) <= 80");
+  if (o->precision == HMS_FP64 && std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_SX)
+    return fail(c, HMS_ERR_ARG, "the FP64 relaxation takes regions up to 64 nodes wide");
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
 
@@ -1527,7 +1529,8 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
                     size_t* scratch) {
   if (!c || !d || !o || d->nx < 2 || d->ny < 2 || d->set_sx < 1 || d->set_sx > MAX_SX || d->set_sy < 1) return false;
   if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return false;
-  if (o->relax_overlap < 0 || std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_SX) return false;
+  if (o->relax_overlap < 0 || std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_RX) return false;
+  if (o->precision == HMS_FP64 && std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_SX) return false;
   hms_problem pr;
   LatView& lv = pr.lv;
   lv.nx = d->nx;

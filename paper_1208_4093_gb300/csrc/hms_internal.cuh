@@ -20,7 +20,8 @@ namespace hms {
 constexpr int NMODES = 9;
 constexpr double SQ3_2 = 0.86602540378443864676;  // sqrt(3)/2
 constexpr int MAX_SX = 64;                           // set width limit (nodes)
-constexpr int MAX_NB = 2 * MAX_SX;                   // DOFs per set row
+constexpr int MAX_RX = 80;                           // relaxation region width limit (nodes)
+constexpr int MAX_NB = 2 * MAX_RX;                   // DOFs per region row
 
 // slots of the per-set upper-level partial sums (Eq. 6), see coarse.cu
 enum Slot { SLOT_SELF = 0, SLOT_E, SLOT_W, SLOT_N, SLOT_NE, SLOT_NW, NSLOTS };

@@ -26,6 +26,8 @@ CASES = [
     ("wide_e4", 67, 24, 32, 12, True, 4),
     ("one_row_sets_e2", 16, 9, 8, 1, False, 2),
 ]
+# regions wider than 64 nodes: mixed path only
+WIDE = [("region80_e8", 100, 30, 64, 10, True, 8)]
 PRECS = [0, 1]
 
 
@@ -148,12 +150,16 @@ def test_overlap_launch_shapes_and_batch_agree(hms_ctx):
 
 def test_overlap_rejections(hms_ctx):
     from paper_1208_4093_gb300 import capi
-    for kw in (dict(relax_overlap=-1), dict(relax_overlap=17), dict(relax_overlap=1, relax_copies=2)):
+    for kw in (dict(relax_overlap=-1), dict(relax_overlap=25), dict(relax_overlap=1, relax_copies=2),
+               dict(relax_overlap=17, precision=0)):
         with pytest.raises(capi.HmsError) as e:
             capi.hms_problem_create(hms_ctx, 96, 40, 32, 16, **kw)
         assert e.value.status == capi.HMS_ERR_ARG, kw
     # the grown tile is clipped to the lattice: 40 nodes wide is fine at any overlap
     pr = capi.hms_problem_create(hms_ctx, 40, 24, 32, 8, relax_overlap=40)
+    capi.hms_problem_destroy(pr)
+    # up to 80 nodes on the mixed path (FP32 factors), at most 64 with FP64 ones
+    pr = capi.hms_problem_create(hms_ctx, 96, 40, 32, 16, relax_overlap=24, precision=1)
     capi.hms_problem_destroy(pr)
 
 
@@ -179,3 +185,24 @@ def test_overlap_after_the_same_set_shape_without(hms_ctx):
     finally:
         for q in (a, b, c):
             capi.hms_problem_destroy(q)
+
+
+@pytest.mark.parametrize("case", WIDE, ids=lambda c: c[0])
+def test_overlap_regions_wider_than_64_nodes_mixed(hms_ctx, case):
+    """Regions up to 80 nodes wide on the mixed path: the relaxation step
+    against the oracle and the converged displacement against the direct solve."""
+    from paper_1208_4093_gb300 import capi
+    tr, g, p, pr = make(hms_ctx, case, 1)
+    try:
+        u = tr.free * np.random.default_rng(4).standard_normal(tr.ndof)
+        r = tr.residual(tr.free * p, u)
+        dl, P = np.empty(tr.ndof), np.empty(9 * g.M)
+        capi.hms_relax(hms_ctx, pr, r, dl, P)
+        assert rel(dl, hms.LocalFactors(tr, g, overlap=case[6]).relax(r)) < 2e-5
+        us = np.empty((1, tr.ndof))
+        capi.hms_solve(hms_ctx, pr, p.reshape(1, -1), us)
+        assert rel(us[0], direct.cholesky_solve(tr, tr.free * p)) < 1e-8
+    finally:
+        capi.hms_problem_destroy(pr)
+    with pytest.raises(capi.HmsError):
+        make(hms_ctx, case, 0)

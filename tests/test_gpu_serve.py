@@ -34,8 +34,9 @@ def req_args(k, r):
 
 
 def b_size_max():
-    # pad4 of the entry count of a B block with nb = 128 (rows r hold columns max(0, r-3)..127)
-    nb = 128
+    # pad4 of the entry count of a B block with nb = 160, the widest relaxation
+    # region row (80 nodes; rows r hold columns max(0, r-3)..159)
+    nb = 160
     n = sum(nb - max(0, r - 3) for r in range(nb))
     return (n + 3) // 4 * 4
 
