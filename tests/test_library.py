@@ -48,3 +48,37 @@ def test_no_cpu_fallback_in_binding():
         if f.endswith(".py"):
             src = open(os.path.join(pkg, f)).read()
             assert "oracle" not in re.sub(r'""".*?"""', "", src, flags=re.S), f
+
+
+def header_struct_fields(name):
+    """(C type, field) of a typedef struct in the header, in order."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = {m.group(2): m.group(1) for m in re.finditer(r"typedef struct \{([^{}]*)\}\s*(\w+)\s*;", text)}[name]
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        m = re.match(r"((?:const\s+)?\w+\s*\**)\s*(.*)", decl)
+        ctype = m.group(1).replace(" ", "")
+        for field in m.group(2).split(","):
+            field = field.strip()
+            star = field.startswith("*")
+            out.append((ctype + ("*" if star else ""), field.lstrip("*").strip()))
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("hms_options", "Options"), ("hms_lattice_desc", "LatticeDesc")])
+def test_binding_structs_match_the_header(cname, pyname):
+    """The ctypes structs the binding passes by pointer have the header's
+    fields, in its order and with its sizes (an appended option must reach
+    both sides)."""
+    import ctypes
+    from paper_1208_4093_gb300 import capi
+    want = header_struct_fields(cname)
+    got = getattr(capi, pyname)._fields_
+    assert [n for _, n in want] == [n for n, _ in got]
+    size = {"int32_t": ctypes.c_int32, "double": ctypes.c_double}
+    for (ctype, n), (_, pytype) in zip(want, got):
+        c = ctypes.c_void_p if ctype.endswith("*") else size[ctype]
+        assert ctypes.sizeof(c) == ctypes.sizeof(pytype), n
