@@ -27,8 +27,9 @@ Readings (the paper is silent on these):
   nodes; the span of the modes, hence the iterate, does not depend on it;
 * sets are rectangular node tiles of sx x sy nodes in a row-major set grid,
   the last tile of a row or column takes the remainder;
-* q = 9 (the displacement-controlled modes only); the force-controlled modes
-  10-12 of Eqs. 15-18 are not part of this iteration;
+* q = 9 (the displacement-controlled modes only) by default; ``solve(...,
+  force=ForceFactors(...))`` adds the force-controlled modes 10-12 of Eqs.
+  15-18 (q = 12; the floating-set reading is in ``ForceFactors``);
 * an extended relaxation region (``LocalFactors(overlap=e)``) relaxes the set
   together with a ring of e nodes around it and keeps the set's part of the
   increment as its mode;
@@ -47,9 +48,10 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 from .direct import to_lower_band
-from .truss import Truss
+from .truss import BAR_DIRS, Truss, bar_stiffness, bars
 
 NMODES = 9
+NMODES_RF = 12  # with the force-controlled modes 10-12 of Eqs. 17-18
 DROP_DIAG = 1e-300
 DROP_DIAG_REL = 1e-28
 DROP_PIVOT = 1e-14
@@ -141,13 +143,67 @@ class LocalFactors:
         return delta
 
 
+class ForceFactors:
+    """Force-controlled relaxation of every set (Eqs. 15-17).
+
+    The set is cut free: Delta k of Eq. 15 adds, on the diagonal block of each
+    inner node i, the blocks k_il of K that couple it to nodes l outside the
+    set, so k^Inner + Delta k is the stiffness of the set's own bars on its
+    free DOFs.  Eq. 16's right-hand side minus (k^Inner + Delta k) u^Inner-old
+    is r_I, so the increment of Eq. 17 solves (k^Inner + Delta k) delta^RF = r_I.
+    A set clear of the supports floats: the matrix is singular (rigid motions;
+    also the mechanisms of one-row or one-column sets) and the paper does not
+    say how its solver treated that.  Reading: the minimum-norm solution of the
+    system with r_I projected onto the matrix's range, from a dense
+    eigendecomposition in which eigenvalues <= ZERO times the largest count as
+    zero.
+    """
+    ZERO = 1e-10
+
+    def __init__(self, truss: Truss, grid: SetGrid):
+        ns = grid.node_set().reshape(-1)
+        K = truss.K.tocsr()
+        a, b, d = bars(truss.nx, truss.ny)
+        k = bar_stiffness(truss.nx, truss.ny, truss.ea, truss.L)
+        e = BAR_DIRS[d]
+        cut = ns[a] != ns[b]
+        self.dofs, self.mats, self.eig = [], [], []
+        for I in range(grid.M):
+            dI = np.flatnonzero((np.repeat(ns, 2) == I) & truss.free)
+            loc = {g: q for q, g in enumerate(dI)}
+            kf = K[dI][:, dI].toarray()
+            # Eq. 15: each cut bar's inner end i gets k_il = -(EA/L) e e^T on its diagonal block
+            for t in np.flatnonzero(cut & ((ns[a] == I) | (ns[b] == I))):
+                i = a[t] if ns[a[t]] == I else b[t]
+                for pp in range(2):
+                    for qq in range(2):
+                        gp, gq = 2 * i + pp, 2 * i + qq
+                        if gp in loc and gq in loc:
+                            kf[loc[gp], loc[gq]] -= k[t] * e[t, pp] * e[t, qq]
+            w, Q = np.linalg.eigh(kf) if dI.size else (np.zeros(0), np.zeros((0, 0)))
+            keep = w > self.ZERO * (w.max() if w.size else 0.0)
+            self.dofs.append(dI)
+            self.mats.append(kf)
+            self.eig.append((w[keep], Q[:, keep]))
+
+    def relax(self, r: np.ndarray) -> np.ndarray:
+        """delta^RF with delta^RF_I = (k^Inner_I + Delta k_I)^+ r_I (Eq. 17)."""
+        delta = np.zeros_like(r)
+        for dI, (w, Q) in zip(self.dofs, self.eig):
+            if w.size:
+                delta[dI] = Q @ ((Q.T @ r[dI]) / w)
+        return delta
+
+
 def modes(truss: Truss, grid: SetGrid, delta: np.ndarray, rep=None,
-          mode_mask: int = 0x1FF) -> sp.csc_matrix:
+          mode_mask: int = 0x1FF, delta_rf: np.ndarray | None = None) -> sp.csc_matrix:
     """Incremental modes V (2N x 9M, column I*9 + m = mode m+1 of set I).
 
     Eq. 9 (translations), Eq. 10 (constant gradients), Eq. 13 (delta) and
     Eq. 14 (xi*delta, eta*delta); every mode is zero outside its set and on
-    constrained DOFs.  Bit m of ``mode_mask`` keeps mode m+1.
+    constrained DOFs.  Bit m of ``mode_mask`` keeps mode m+1.  With
+    ``delta_rf`` (the force-controlled increment of Eq. 17) the modes 10-12
+    of Eqs. 17-18 follow: V is 2N x 12M, column I*12 + m.
     """
     xc, yc = rep_points(truss, grid) if rep is None else rep
     ns = grid.node_set().reshape(-1)
@@ -161,6 +217,12 @@ def modes(truss: Truss, grid: SetGrid, delta: np.ndarray, rep=None,
         (xi, zero), (eta, zero), (zero, xi), (zero, eta),
         (dx, dy), (xi * dx, xi * dy), (eta * dx, eta * dy),
     ]
+    nm = NMODES
+    if delta_rf is not None:
+        fx_, fy_ = delta_rf[0::2], delta_rf[1::2]
+        fields += [(fx_, fy_), (xi * fx_, xi * fy_), (eta * fx_, eta * fy_)]
+        nm = NMODES_RF
+        mode_mask |= 0x7 << NMODES
     free = truss.free
     rows, cols, vals = [], [], []
     node = np.arange(nn)
@@ -170,9 +232,9 @@ def modes(truss: Truss, grid: SetGrid, delta: np.ndarray, rep=None,
         for c, f in ((0, fx), (1, fy)):
             dof = 2 * node + c
             keep = free[dof] & (f != 0)
-            rows.append(dof[keep]); cols.append(ns[keep] * NMODES + m); vals.append(f[keep])
+            rows.append(dof[keep]); cols.append(ns[keep] * nm + m); vals.append(f[keep])
     rows = np.concatenate(rows); cols = np.concatenate(cols); vals = np.concatenate(vals)
-    return sp.csc_matrix((vals, (rows, cols)), shape=(truss.ndof, NMODES * grid.M))
+    return sp.csc_matrix((vals, (rows, cols)), shape=(truss.ndof, nm * grid.M))
 
 
 def coarse_system(truss: Truss, V: sp.spmatrix, r: np.ndarray):
@@ -235,8 +297,9 @@ class Result:
 
 def solve(truss: Truss, grid: SetGrid, p: np.ndarray, tol: float, max_iter: int,
           u0=None, rep=None, mode_mask: int = 0x1FF, keep_iterates=False,
-          factors: LocalFactors | None = None) -> Result:
-    """The paper's iteration (Fig. 3) from u0 (default 0) until R1 < tol."""
+          factors: LocalFactors | None = None, force: ForceFactors | None = None) -> Result:
+    """The paper's iteration (Fig. 3) from u0 (default 0) until R1 < tol;
+    with ``force`` the q = 12 modes (force-controlled relaxation too)."""
     free = truss.free
     p = free * np.asarray(p, dtype=np.float64)
     u = np.zeros(truss.ndof) if u0 is None else free * np.asarray(u0, dtype=np.float64)
@@ -257,9 +320,14 @@ def solve(truss: Truss, grid: SetGrid, p: np.ndarray, tol: float, max_iter: int,
         if t >= max_iter:
             break
         delta = lf.relax(r)
-        V = modes(truss, grid, delta, rep, mode_mask)
-        Kaa, P = coarse_system(truss, V, r)
-        a, dropped = coarse_solve(Kaa, P)
+        if force is None:
+            V = modes(truss, grid, delta, rep, mode_mask)
+            Kaa, P = coarse_system(truss, V, r)
+            a, dropped = coarse_solve(Kaa, P)
+        else:
+            V = modes(truss, grid, delta, rep, mode_mask, delta_rf=force.relax(r))
+            Kaa, P = coarse_system(truss, V, r)
+            a, dropped = coarse_solve(Kaa, P, group=NMODES_RF)
         u = u + V @ a
         drops.append(dropped)
         if keep_iterates:

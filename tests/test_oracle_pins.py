@@ -448,3 +448,105 @@ def test_overlap_reduces_iterations():
     nir = [hms.solve(tr, g, p, 1e-8, 500, factors=hms.LocalFactors(tr, g, overlap=e)).iterations
            for e in (0, 1, 4)]
     assert nir[0] > nir[1] > nir[2]
+
+
+# ---------------------------------------------------------------- force-controlled relaxation
+def brute_force_set_K(nx, ny, ea, members):
+    """Dense stiffness of the rods with both ends in ``members`` (a set of node
+    indices), from node coordinates only (as brute_force_K)."""
+    n = nx * ny
+    xy = np.array([(i + 0.5 * (j % 2), j * SQ3 / 2) for j in range(ny) for i in range(nx)])
+    K = np.zeros((2 * n, 2 * n))
+    for a in members:
+        for b in members:
+            if b <= a:
+                continue
+            d = xy[b] - xy[a]
+            if abs(math.hypot(*d) - 1.0) > 1e-9:
+                continue
+            e = d
+            ja, ia = divmod(a, nx)
+            lab = 0 if abs(d[1]) < 1e-12 else (1 if d[0] > 0 else 2)
+            kee = (1.0 if ea is None else ea[lab, ja, ia]) * np.outer(e, e)
+            for (p, q, s) in ((a, a, 1), (b, b, 1), (a, b, -1), (b, a, -1)):
+                K[2 * p:2 * p + 2, 2 * q:2 * q + 2] += s * kee
+    return K
+
+
+def force_problem():
+    nx, ny = 18, 14
+    ea = ea_lognormal(nx, ny, 21)
+    return truss.Truss(nx, ny, ea), hms.SetGrid(nx, ny, 6, 5), ea
+
+
+def test_force_matrix_is_the_stiffness_of_the_sets_own_bars():
+    """k^Inner + Delta k (Eq. 15) = the set cut free: only the rods with both
+    ends in the set act."""
+    tr, g, ea = force_problem()
+    ff = hms.ForceFactors(tr, g)
+    ns = g.node_set().reshape(-1)
+    for I in (0, 4, g.M - 1):
+        members = [int(v) for v in np.flatnonzero(ns == I)]
+        Kb = brute_force_set_K(tr.nx, tr.ny, ea, members)
+        d = ff.dofs[I]
+        assert np.allclose(ff.mats[I], Kb[np.ix_(d, d)], rtol=0, atol=1e-12)
+
+
+def test_floating_set_null_space_is_the_rigid_motions():
+    """A set clear of the supports has exactly the three rigid motions of the
+    plane (two translations, the rotation) as zero modes; one on the clamped
+    row has none."""
+    tr, g, _ = force_problem()
+    ff = hms.ForceFactors(tr, g)
+    ns = g.node_set().reshape(-1)
+    I = g.Mx + 1  # an interior set
+    d = ff.dofs[I]
+    assert d.size - ff.eig[I][0].size == 3
+    nodes = d[0::2] // 2
+    x, y = tr.x.reshape(-1)[nodes], tr.y.reshape(-1)[nodes]
+    R = np.zeros((d.size, 3))
+    R[0::2, 0] = 1.0
+    R[1::2, 1] = 1.0
+    R[0::2, 2], R[1::2, 2] = -y, x
+    assert np.abs(ff.mats[I] @ R).max() < 1e-12
+    assert ff.dofs[0].size == ff.eig[0][0].size  # the bottom-left set touches the clamp
+
+
+def test_force_relaxation_is_the_minimum_norm_solution():
+    """delta^RF_I solves the cut-free system for r_I with its rigid-motion part
+    removed, and has no rigid-motion part itself (reading of the floating set)."""
+    tr, g, _ = force_problem()
+    ff = hms.ForceFactors(tr, g)
+    r = tr.residual(loads(tr.nx, tr.ny, 4, 0).reshape(-1), np.zeros(tr.ndof))
+    delta = ff.relax(r)
+    I = g.Mx + 1
+    d = ff.dofs[I]
+    nodes = d[0::2] // 2
+    x, y = tr.x.reshape(-1)[nodes], tr.y.reshape(-1)[nodes]
+    R = np.zeros((d.size, 3))
+    R[0::2, 0] = 1.0
+    R[1::2, 1] = 1.0
+    R[0::2, 2], R[1::2, 2] = -y, x
+    Qr, _ = np.linalg.qr(R)
+    rI = r[d] - Qr @ (Qr.T @ r[d])
+    assert np.abs(Qr.T @ delta[d]).max() < 1e-10 * np.abs(delta[d]).max()
+    assert np.allclose(ff.mats[I] @ delta[d], rI, rtol=0, atol=1e-10 * np.abs(rI).max())
+
+
+def test_twelve_modes_converge_and_need_fewer_updates():
+    """With the force-controlled modes (q = 12, Eqs. 17-18) the iteration still
+    converges to the direct solution, keeps Galerkin orthogonality (Eq. 5) and
+    needs fewer updates than with q = 9."""
+    tr, g, _ = force_problem()
+    p = loads(tr.nx, tr.ny, 7, 0).reshape(-1)
+    ff = hms.ForceFactors(tr, g)
+    r9 = hms.solve(tr, g, p, 1e-10, 2000)
+    r12 = hms.solve(tr, g, p, 1e-10, 2000, force=ff, keep_iterates=True)
+    ref = direct.cholesky_solve(tr, tr.free * p)
+    assert r12.converged and np.linalg.norm(r12.u - ref) / np.linalg.norm(ref) < 1e-9
+    assert r12.iterations < r9.iterations
+    # Eq. 5 after the first update: V^T r_new = 0 for the twelve modes of that update
+    r0 = tr.residual(tr.free * p, np.zeros(tr.ndof))
+    V = hms.modes(tr, g, hms.LocalFactors(tr, g).relax(r0), delta_rf=ff.relax(r0))
+    r1 = tr.residual(tr.free * p, r12.iterates[0])
+    assert np.abs(V.T @ r1).max() < 1e-9 * np.abs(V.T @ r0).max()
