@@ -7,7 +7,9 @@
 // Eq. 13 directly from the global residual:
 //   k^Inner (u^RD - u^old) = p^Inner - k^Outer u^Outer-old - k^Inner u^Inner-old = r_I,
 // so delta_I = (k^Inner_I)^-1 r_I, all sets from the same u (every set relaxes
-// against its neighbours' old displacements).
+// against its neighbours' old displacements).  With an extended relaxation
+// region (Sec. 2.2; LatView::ov > 0) the same solve runs on the set's tile
+// grown by ov nodes and delta is kept on the set's own nodes.
 //
 // One CTA per set.  The set's block-bidiagonal factor (setup.cu) is a stream
 // of matrices Linv_0, B_1, Linv_1, ..., consumed in order by the forward
