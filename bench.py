@@ -628,7 +628,6 @@ def run_ours(args, rank, world, local_rank):
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms, (sampler.summary() if clocks else None)
 
-    result = {}
     # ---- plain FP64 form (headline) ----
     pr64 = make(capi.HMS_FP64)
     setup64 = capi.hms_problem_setup_ms(pr64)
@@ -710,7 +709,7 @@ def run_ours(args, rank, world, local_rank):
                     "hbm_gbs": b / (avg * 1e-3) / 1e9}
         roof.update({"algorithmic_bytes": b, "algorithmic_flops": fl, "avg_launch_ms": avg, "launches": n,
                      "traffic": traffic_for(roof["kernel"], WORKLOAD, "relax.cu")})
-        rb, rf = residual_work(c, fp32)
+        rb, _ = residual_work(c, fp32)
         rms, rn = kt["update_residual"]
         ravg = rms / max(rn, 1)
         n_sm1 = torch.cuda.get_device_properties(dev).multi_processor_count
