@@ -118,6 +118,15 @@ typedef struct {
                                 (min(nx, set_sx + 2 relax_overlap) <= 80), and at most 64 on
                                 the FP64 path (the relaxation kernel's shared memory); with
                                 overlap the FP64 relaxation uses one copy per matrix */
+  uint32_t mode_mask;        /* incremental modes of every set taking part in the upper-level
+                                correction (Eqs. 3 and 8): bit m keeps mode m+1 (bit 0, 1:
+                                translations of Eq. 9; bits 2-5: gradients of Eq. 10; bit 6:
+                                delta of Eq. 13; bits 7, 8: its gradient-weighted copies of
+                                Eq. 14).  A cleared mode gets a = 0, as a mode the coarse solve
+                                drops.  0 = all nine (0x1FF); bits above 8 must be 0 */
+  int32_t record_history;    /* 1 = keep the (R1, R2, Pi) row of every residual evaluation on
+                                the device for hms_solve's hist output; 0 = record nothing
+                                (no history buffer; hist rows come back as NaN) */
 } hms_options;
 
 /* Context: one device, one CUDA stream.  device = CUDA ordinal. */
@@ -199,6 +208,15 @@ hms_status hms_solve_batch(hms_context* c, int32_t count, hms_problem* const* pr
 #define HMS_BATCH_LOCKSTEP 2
 hms_status hms_context_set_batch_mode(hms_context* c, int32_t mode);
 
+/* Upper-level updates of the last hms_solve call (all its load vectors)
+ * whose FP64 refinement of the Eq. 8 solve used every solve
+ * options.coarse_solves allows while the residual before the last one was
+ * still above 1e-14 max|b|: the update then went on with the refined
+ * solution as it stood.  0 when every update's refinement met the criterion
+ * before its last solve, and always with coarse_solves = 1 (no
+ * refinement). */
+int64_t hms_problem_refine_cap_hits(const hms_problem* pr);
+
 /* Per-kernel CUDA-event time of the last hms_solve with options.profile = 1:
  * names "update_residual", "relax", "coarse_assemble", "coarse_band",
  * "coarse_factor", "coarse_residual", "coarse_solve", in that order;
@@ -212,6 +230,16 @@ int32_t hms_kernel_times(const hms_problem* pr, double* ms_total, int64_t* launc
  * Pi = -norms[2]/2).  p, u, r: [2*nx*ny]. */
 hms_status hms_residual(hms_problem* pr, const double* p, const double* u, double* r,
                         double* norms, int32_t mem_kind);
+
+/* K u at every DOF, the constrained ones included (Eq. 1 read as the nodal
+ * forces the bars exert: (K u)_a = sum over the bars ab at node a of
+ * (EA/L)_ab e_ab e_ab^T (u_a - u_b)).  On a free DOF this is the internal
+ * force that balances the load; on a constrained DOF it is the support
+ * reaction (Sec. 3.1's clamped supports), so that at a converged solution the
+ * reactions and the loads are in equilibrium.  u: [2*nx*ny], read with its
+ * constrained DOFs taken as 0 (u itself is not modified); f_out: [2*nx*ny]
+ * (may not alias u).  HMS_ERR_ARG for NULL pointers or a bad mem_kind. */
+hms_status hms_reactions(hms_problem* pr, const double* u, double* f_out, int32_t mem_kind);
 
 /* Steps a2 + a1 (Eq. 3 then Eq. 1): u_out = u + V a with modes built from
  * delta [2*nx*ny] and coefficients a [9*M] (set-major, 9 per set), then
@@ -243,6 +271,15 @@ hms_status hms_coarse_matrix(hms_problem* pr, const double* delta, double* Kaa,
 hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P, double* a,
                             int32_t* dropped, int32_t mem_kind);
 
+/* For tests of the timeout path: the relaxation kernel's first wait for its
+ * factor copies (of every set) gives up after `spins` tries instead of the
+ * usual bound, so that hms_relax and hms_solve return HMS_ERR_TIMEOUT (0
+ * tries: always).  The kernel then waits, with the usual bound, for the
+ * copies it has in flight, raises the error flag and returns; the context
+ * stays usable.  spins < 0 restores the usual bound.  The problem's CUDA
+ * graph is rebuilt. */
+hms_status hms_problem_set_relax_wait_limit(hms_problem* pr, int32_t spins);
+
 /* ---- allocation-free residual (no counterpart in the paper) ---- */
 
 /* Node tiles of 32 x 8 per CTA; the static scratch of
@@ -250,11 +287,11 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
  * ceil(nx/32) * ceil(ny/8) (3 doubles each: 384 KiB of device memory). */
 #define HMS_RESIDUAL_NOALLOC_MAX_TILES 16384
 
-/* The result of hms_residual (Eqs. 1, 19, 2) -- r = p - K u on the free DOFs
- * and norms[0] = ||r||_1, norms[1] = ||r||_2^2, norms[2] = u.(p + r) -- for
- * device-resident vectors, without allocating device memory and without
- * touching the problem's own buffers.  This is a library service, not a step
- * the paper describes.
+/* No counterpart in the paper: a library service.  It gives what
+ * hms_residual gives -- r = p - K u on the free DOFs (0 on constrained
+ * ones), and norms[0] = the sum of |r|, norms[1] = the sum of r^2, norms[2] =
+ * u.(p + r) -- for vectors the caller already holds on the device, without
+ * allocating device memory and without touching the problem's own buffers.
  *
  * Who needs it: callers that must not allocate while the device is busy --
  * cudaFree (and, with a full pool, cudaMalloc) synchronises the whole device,
@@ -265,24 +302,25 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
  * the same problem, whose buffers hms_residual would overwrite.
  *
  * p, u, r: DEVICE pointers on the context's device (device or managed memory),
- * 2*nx*ny doubles each, 16-byte aligned; r may not alias p or u.  Constrained
- * DOFs of u are read as 0 (u itself is not modified).  norms: device pointer
- * to 3 doubles, 8-byte aligned, or NULL.  The kernel runs on the context's
- * stream; the call returns after it completed (a stream synchronisation,
- * which allocates nothing).
+ * 2*nx*ny doubles each, 16-byte aligned; r may not overlap p or u anywhere.
+ * Constrained DOFs of u are read as 0 (u itself is not modified).  norms:
+ * device pointer to 3 doubles, 8-byte aligned, or NULL.  The kernel runs on
+ * the context's stream; the call returns after it completed (a stream
+ * synchronisation, which allocates nothing).
  *
  * Scratch: a static device array of HMS_RESIDUAL_NOALLOC_MAX_TILES * 3
- * doubles plus a completion counter, part of the library's device image.
- * The first call on each device looks up their addresses
+ * doubles plus a completion counter, part of the library's device image; it
+ * stays allocated on every device that loads the library until the process
+ * exits.  The first call on each device looks up their addresses
  * (cudaGetSymbolAddress, with the device made current) and caches them; make
- * that first call before beginning any stream capture on the device.  The
+ * that first call before any stream capture begins on the device.  The
  * counter must be 0 when a kernel starts; it is 0 at load and every kernel
  * resets it when it completes.  Calls that run at the same time on one
  * device -- from two threads, two contexts or two problems -- share the
  * scratch and race: serialise them.
  *
  * Errors: HMS_ERR_ARG for a NULL problem/vector, host or foreign-device
- * pointers, misalignment, r aliasing p or u, or a lattice of more than
+ * pointers, misalignment, r overlapping p or u, or a lattice of more than
  * HMS_RESIDUAL_NOALLOC_MAX_TILES tiles (use hms_residual there);
  * HMS_ERR_CUDA if the scratch lookup or the launch fails. */
 hms_status hms_residual_noalloc(hms_problem* pr, const double* p, const double* u, double* r,

@@ -55,7 +55,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("coarse_solves", ctypes.c_int32), ("batch", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("coarse_factor", ctypes.c_int32), ("relax_threads", ctypes.c_int32),
-                ("relax_copies", ctypes.c_int32), ("relax_overlap", ctypes.c_int32)]
+                ("relax_copies", ctypes.c_int32), ("relax_overlap", ctypes.c_int32),
+                ("mode_mask", ctypes.c_uint32), ("record_history", ctypes.c_int32)]
 
 
 _lib = None
@@ -105,6 +106,9 @@ def lib():
         "hms_server_step": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, _P, _P, _P]),
         "hms_server_take": (ctypes.c_int32, [_P, ctypes.c_int64, _P, _P]),
         "hms_problem_clone": (ctypes.c_int32, [_P, ctypes.POINTER(_P)]),
+        "hms_reactions": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
+        "hms_problem_refine_cap_hits": (ctypes.c_int64, [_P]),
+        "hms_problem_set_relax_wait_limit": (ctypes.c_int32, [_P, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -122,7 +126,8 @@ def exported_symbols():
             "hms_update_residual", "hms_relax", "hms_coarse_matrix", "hms_coarse_solve",
             "hms_residual_noalloc", "hms_solve_batch", "hms_problem_estimate_bytes", "hms_server_create",
             "hms_server_destroy", "hms_server_submit", "hms_server_step", "hms_server_take", "hms_problem_clone",
-            "hms_problem_relax_threads", "hms_context_set_batch_mode", "hms_problem_relax_copies"]
+            "hms_problem_relax_threads", "hms_context_set_batch_mode", "hms_problem_relax_copies",
+            "hms_reactions", "hms_problem_refine_cap_hits", "hms_problem_set_relax_wait_limit"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -189,7 +194,7 @@ def hms_last_error(ctx) -> str:
 
 def _desc_opts(nx, ny, set_sx, set_sy, bar_length=1.0, ea=None, ea_uniform=1.0, fixed=None, fix_bottom_edge=1,
                precision=HMS_FP64, tol=1e-8, max_iter=1000, coarse_solves=0, batch=0, profile=0, coarse_factor=0,
-               relax_threads=0, relax_copies=0, relax_overlap=0):
+               relax_threads=0, relax_copies=0, relax_overlap=0, mode_mask=0x1FF, record_history=1):
     """LatticeDesc and Options structs (plus the arrays they point to, kept alive by the caller)."""
     ea_a = None if ea is None else np.ascontiguousarray(ea, dtype=np.float64)
     fx_a = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
@@ -201,14 +206,16 @@ def _desc_opts(nx, ny, set_sx, set_sy, bar_length=1.0, ea=None, ea_uniform=1.0, 
                     float(ea_uniform), None if fx_a is None else fx_a.ctypes.data, int(fix_bottom_edge),
                     int(set_sx), int(set_sy))
     o = Options(int(precision), float(tol), int(max_iter), int(coarse_solves), int(batch), int(profile),
-                int(coarse_factor), int(relax_threads), int(relax_copies), int(relax_overlap))
+                int(coarse_factor), int(relax_threads), int(relax_copies), int(relax_overlap), int(mode_mask),
+                int(record_history))
     return d, o, (ea_a, fx_a)
 
 
 def hms_problem_create(ctx, nx, ny, set_sx, set_sy, **kw):
     """kw: bar_length, ea (host float64 [3, ny, nx]), ea_uniform, fixed (host uint8
     [ny, nx, 2]), fix_bottom_edge, precision, tol, max_iter, coarse_solves, batch,
-    profile, coarse_factor, relax_threads, relax_copies, relax_overlap."""
+    profile, coarse_factor, relax_threads, relax_copies, relax_overlap, mode_mask,
+    record_history."""
     d, o, keep = _desc_opts(nx, ny, set_sx, set_sy, **kw)
     h = _P()
     _check(ctx, lib().hms_problem_create(ctx, ctypes.byref(d), ctypes.byref(o), ctypes.byref(h)))
@@ -330,6 +337,20 @@ def hms_kernel_times(pr):
 def hms_residual(ctx, pr, p, u, r_out, norms_out):
     A = [_Arg(p), _Arg(u), _Arg(r_out, writable=True), _Arg(norms_out, writable=True)]
     _check(ctx, lib().hms_residual(pr, *[a.ptr for a in A], _mem_kind(*A)))
+
+
+def hms_reactions(ctx, pr, u, f_out):
+    """f_out = K u at every DOF, constrained ones included (u read as 0 there)."""
+    A = [_Arg(u), _Arg(f_out, writable=True)]
+    _check(ctx, lib().hms_reactions(pr, A[0].ptr, A[1].ptr, _mem_kind(*A)))
+
+
+def hms_problem_refine_cap_hits(pr) -> int:
+    return int(lib().hms_problem_refine_cap_hits(pr))
+
+
+def hms_problem_set_relax_wait_limit(ctx, pr, spins):
+    _check(ctx, lib().hms_problem_set_relax_wait_limit(pr, int(spins)))
 
 
 def hms_residual_noalloc(ctx, pr, p, u, r_out, norms_out=None):

@@ -40,6 +40,10 @@ struct hms_problem {
   SharedSetup* shared = nullptr;
   LatView lv{};
   int precision = HMS_FP64, nsolve = 4, batch = 16, profile = 0, max_iter = 0;
+  unsigned mode_mask = 0x1FFu;  // modes taking part in the upper-level correction
+  bool record_history = true;
+  int relax_wait0 = -1;         // tries of the relaxation's first copy wait (-1: the usual bound)
+  long long refine_cap_hits = 0;  // of the last hms_solve
   bool coarse_fp64 = false;  // factor of the upper-level system in FP64 (else FP32 + FP64 refinement)
   double tol = 1e-8;
   int relax_threads = 256;   // CTA size of the relaxation
@@ -187,14 +191,17 @@ cudaError_t launch_factor_stage(hms_problem* pr, cudaStream_t s, const IterCtl* 
 // Solve q (0: of b, then of the refinement residual) with the factor.
 cudaError_t launch_solve_stage(hms_problem* pr, cudaStream_t s, int q, const IterCtl* ctl) {
   const double* rhs = q == 0 ? pr->b : pr->res;
+  // bit 0: the solve of b; bit 1: the last solve an update allows (the
+  // kernels count the updates whose refinement had not converged before it)
+  const int flags = (q == 0 ? 1 : 0) | (q == pr->nsolve - 1 ? 2 : 0);
   if (pr->two_sided)
-    return launch_coarse_solve_2s(s, pr->n_c, pr->ts, rhs, pr->x, pr->scale, pr->a, pr->dropped, pr->cstat, q == 0,
+    return launch_coarse_solve_2s(s, pr->n_c, pr->ts, rhs, pr->x, pr->scale, pr->a, pr->dropped, pr->cstat, flags,
                                   ctl, pr->err);
   if (pr->big_stages > 0)
     return launch_coarse_solve_big(s, pr->big_stages, pr->n_c, pr->bw, pr->lcol, pr->lrow, pr->xinv, pr->dropped,
-                                   rhs, pr->x, pr->scale, pr->a, pr->cstat, q == 0, ctl, pr->err);
+                                   rhs, pr->x, pr->scale, pr->a, pr->cstat, flags, ctl, pr->err);
   return launch_coarse_solve(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->lcol, pr->lrow, pr->dinv, pr->dropped, rhs,
-                             pr->x, pr->scale, pr->a, pr->cstat, q == 0, ctl, pr->err);
+                             pr->x, pr->scale, pr->a, pr->cstat, flags, ctl, pr->err);
 }
 
 // Launches of one iteration (the body of Fig. 3's loop); k = position in a batch.
@@ -212,7 +219,7 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
   if (e != cudaSuccess) return e;
   mark();
   e = launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, pr->ctl, pr->err,
-                   pr->relax_threads, pr->relax_chunks);
+                   pr->relax_threads, pr->relax_chunks, pr->relax_wait0);
   if (e != cudaSuccess) return e;
   mark();
   e = launch_coarse_slots(s, lv, pr->delta, fp32(pr), false, pr->slots_it, pr->ctl);
@@ -221,7 +228,7 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
   e = launch_coarse_band_from_slots(s, lv, pr->slots_base, pr->slots_it, pr->band, pr->ctl);
   if (e != cudaSuccess) return e;
   e = launch_coarse_scale(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale,
-                          pr->b, pr->x, pr->dropped, pr->ctl);
+                          pr->b, pr->x, pr->dropped, pr->mode_mask, pr->ctl);
   if (e != cudaSuccess) return e;
   mark();
   e = launch_factor_stage(pr, s, pr->ctl);
@@ -275,6 +282,11 @@ hms_status check_dev_err(hms_problem* pr) {
   int herr = 0;
   CKC(pr->ctx, cudaMemcpyAsync(&herr, pr->err, sizeof(int), cudaMemcpyDeviceToHost, pr->ctx->stream));
   CKC(pr->ctx, cudaStreamSynchronize(pr->ctx->stream));
+  if (herr) {
+    // reported once: the next call starts from a clear flag
+    CKC(pr->ctx, cudaMemsetAsync(pr->err, 0, sizeof(int), pr->ctx->stream));
+    CKC(pr->ctx, cudaStreamSynchronize(pr->ctx->stream));
+  }
   if (herr & DEVERR_NOT_SPD) return fail(pr->ctx, HMS_ERR_NOT_SPD, "non-positive pivot in a local factorisation");
   if (herr & DEVERR_TIMEOUT) return fail(pr->ctx, HMS_ERR_TIMEOUT, "a bounded device wait gave up");
   return HMS_OK;
@@ -437,6 +449,9 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
   pr->batch = src->batch;
   pr->profile = src->profile;
   pr->max_iter = src->max_iter;
+  pr->mode_mask = src->mode_mask;
+  pr->record_history = src->record_history;
+  pr->relax_wait0 = src->relax_wait0;
   pr->coarse_fp64 = src->coarse_fp64;
   pr->tol = src->tol;
   pr->n_c = src->n_c;
@@ -560,8 +575,13 @@ static cudaError_t alloc_instance(hms_problem* pr) {
   CKI(palloc(pr, &pr->err, 1));
   CKI(cudaMemsetAsync(pr->err, 0, sizeof(int), s));
   CKI(palloc(pr, &pr->norms, 4));
-  pr->hist_cap = pr->max_iter + 1;
-  CKI(palloc(pr, &pr->hist, 3 * (size_t)pr->hist_cap));
+  if (pr->record_history) {
+    pr->hist_cap = pr->max_iter + 1;
+    CKI(palloc(pr, &pr->hist, 3 * (size_t)pr->hist_cap));
+  } else {
+    pr->hist_cap = 0;
+    pr->hist = nullptr;
+  }
   CKI(cudaMallocHost(&pr->ctl_host, sizeof(IterCtl)));
   CKI(cudaMemsetAsync(pr->a, 0, n_c * sizeof(double), s));
 
@@ -647,10 +667,14 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (o->relax_threads != 0 && o->relax_threads != 64 && o->relax_threads != 128 && o->relax_threads != 256)
     return fail(c, HMS_ERR_ARG, "relax_threads must be 0, 64, 128 or 256");
   if (o->relax_copies < 0 || o->relax_copies > 2) return fail(c, HMS_ERR_ARG, "relax_copies must be 0, 1 or 2");
-  if (o->relax_overlap < 0 || std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_RX)
+  // the region width in 64 bits: set_sx + 2 relax_overlap may exceed INT_MAX
+  const long long rw = std::min((long long)d->nx, (long long)d->set_sx + 2LL * (long long)o->relax_overlap);
+  if (o->relax_overlap < 0 || rw > MAX_RX)
     return fail(c, HMS_ERR_ARG, "relax_overlap must be >= 0 with min(nx, set_sx + 2 relax_overlap) <= 80");
-  if (o->precision == HMS_FP64 && std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_SX)
+  if (o->precision == HMS_FP64 && rw > MAX_SX)
     return fail(c, HMS_ERR_ARG, "the FP64 relaxation takes regions up to 64 nodes wide");
+  if ((o->mode_mask >> NMODES) != 0u) return fail(c, HMS_ERR_ARG, "mode_mask has bits above mode 9");
+  if (o->record_history != 0 && o->record_history != 1) return fail(c, HMS_ERR_ARG, "record_history must be 0 or 1");
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
 
@@ -674,6 +698,8 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   pr->profile = o->profile;
   pr->tol = o->tol;
   pr->max_iter = o->max_iter;
+  pr->mode_mask = o->mode_mask ? o->mode_mask : 0x1FFu;
+  pr->record_history = o->record_history != 0;
   pr->n_c = NMODES * lv.M;
   pr->bw = coarse_bw(lv);
 
@@ -846,6 +872,8 @@ hms_status hms_solve(hms_problem* pr, int32_t nrhs, const double* loads, const d
     ev.resize(8 + 2 * pr->nsolve);
     for (auto& e : ev) CKC(c, cudaEventCreate(&e));
   }
+  pr->refine_cap_hits = 0;
+  CKC(c, cudaMemsetAsync(pr->cstat + 3, 0, sizeof(unsigned long long), s));
   for (int q = 0; q < nrhs; ++q) {
     CKC(c, cudaMemcpyAsync(pr->p, loads + 2 * nn * q, vb, kind_in(mem_kind), s));
     if (u0) {
@@ -916,7 +944,29 @@ hms_status hms_solve(hms_problem* pr, int32_t nrhs, const double* loads, const d
       result = fail(c, HMS_ERR_NO_CONVERGENCE, "max_iter reached before tol");
   }
   for (auto& e : ev) cudaEventDestroy(e);
+  {
+    unsigned long long hits = 0;
+    CKC(c, cudaMemcpyAsync(&hits, pr->cstat + 3, sizeof(hits), cudaMemcpyDeviceToHost, s));
+    CKC(c, cudaStreamSynchronize(s));
+    pr->refine_cap_hits = (long long)hits;
+  }
   return result;
+}
+
+int64_t hms_problem_refine_cap_hits(const hms_problem* pr) { return pr ? (int64_t)pr->refine_cap_hits : 0; }
+
+hms_status hms_problem_set_relax_wait_limit(hms_problem* pr, int32_t spins) {
+  if (!pr) return HMS_ERR_ARG;
+  hms_context* c = pr->ctx;
+  CKC(c, cudaSetDevice(c->device));
+  CKC(c, cudaStreamSynchronize(c->stream));
+  pr->relax_wait0 = spins < 0 ? -1 : spins;
+  if (pr->graph) {
+    CKC(c, cudaGraphExecDestroy(pr->graph));
+    pr->graph = nullptr;
+  }
+  if (!pr->profile) return build_graph(pr);
+  return HMS_OK;
 }
 
 int32_t hms_kernel_times(const hms_problem* pr, double* ms_total, int64_t* launches, int32_t n) {
@@ -1142,6 +1192,7 @@ static BatchProb batch_prob_of(const hms_problem* pr) {
   q.cstat = pr->cstat;
   q.n_c = pr->n_c;
   q.bw = pr->bw;
+  q.mode_mask = pr->mode_mask;
   return q;
 }
 
@@ -1371,6 +1422,22 @@ hms_status hms_residual(hms_problem* pr, const double* p, const double* u, doubl
   return hms_update_residual(pr, p, u, nullptr, nullptr, (double*)nullptr, r, norms, mem_kind);
 }
 
+hms_status hms_reactions(hms_problem* pr, const double* u, double* f_out, int32_t mem_kind) {
+  if (!pr || !u || !f_out) return HMS_ERR_ARG;
+  if (mem_kind != HMS_MEM_HOST && mem_kind != HMS_MEM_DEVICE) return HMS_ERR_ARG;
+  hms_context* c = pr->ctx;
+  const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+  if (mem_kind == HMS_MEM_DEVICE && (const char*)f_out < (const char*)u + vb && (const char*)u < (const char*)f_out + vb)
+    return fail(c, HMS_ERR_ARG, "hms_reactions: f_out may not overlap u");
+  CKC(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  CKC(c, cudaMemcpyAsync(pr->u[0], u, vb, kind_in(mem_kind), s));
+  CKC(c, launch_reactions(s, pr->lv, pr->u[0], pr->r));
+  CKC(c, cudaMemcpyAsync(f_out, pr->r, vb, kind_out(mem_kind), s));
+  CKC(c, cudaStreamSynchronize(s));
+  return HMS_OK;
+}
+
 hms_status hms_update_residual(hms_problem* pr, const double* p, const double* u, const double* delta,
                                const double* a, double* u_out, double* r, double* norms, int32_t mem_kind) {
   if (!pr || !p || !u || !r) return HMS_ERR_ARG;
@@ -1411,7 +1478,7 @@ hms_status hms_relax(hms_problem* pr, const double* r, double* delta, double* P,
   CKC(c, cudaMemcpyAsync(pr->r, r, vb, kind_in(mem_kind), s));
   CKC(c, launch_mask_u(s, pr->lv, pr->r));
   CKC(c, launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr, pr->err,
-                      pr->relax_threads, pr->relax_chunks));
+                      pr->relax_threads, pr->relax_chunks, pr->relax_wait0));
   if (fp32(pr)) {
     CKC(c, launch_f2d(s, (const float*)pr->delta, (double*)pr->u[1], 2 * nn));
     CKC(c, cudaMemcpyAsync(delta, pr->u[1], vb, kind_out(mem_kind), s));
@@ -1466,7 +1533,7 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
   CKC(c, e);
   CKC(c, cudaMemcpyAsync(pr->P, P, n * sizeof(double), kind_in(mem_kind), s));
   CKC(c, launch_coarse_scale(s, n, bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale, pr->b,
-                             pr->x, pr->dropped, nullptr));
+                             pr->x, pr->dropped, pr->mode_mask, nullptr));
   CKC(c, launch_factor_stage(pr, s, nullptr));
   for (int q = 0; q < pr->nsolve; ++q) {
     if (q > 0)
@@ -1497,8 +1564,16 @@ hms_status hms_residual_noalloc(hms_problem* pr, const double* p, const double* 
   if (!pr) return HMS_ERR_ARG;
   hms_context* c = pr->ctx;
   if (!p || !u || !r) return fail(c, HMS_ERR_ARG, "hms_residual_noalloc: p, u and r are required");
-  if ((const void*)r == (const void*)p || (const void*)r == (const void*)u)
-    return fail(c, HMS_ERR_ARG, "hms_residual_noalloc: r may not alias p or u");
+  {
+    // r is written while other CTAs still read p and u (halos): no byte of r
+    // may lie in either
+    const size_t vb = nnodes(pr) * sizeof(double2);
+    auto overlap = [vb](const void* a, const void* b) {
+      const char *x = (const char*)a, *y = (const char*)b;
+      return x < y + vb && y < x + vb;
+    };
+    if (overlap(r, p) || overlap(r, u)) return fail(c, HMS_ERR_ARG, "hms_residual_noalloc: r may not overlap p or u");
+  }
   const int tiles = residual_noalloc_tiles(pr->lv);
   if (tiles > HMS_RESIDUAL_NOALLOC_MAX_TILES)
     return fail(c, HMS_ERR_ARG,
@@ -1529,8 +1604,10 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
                     size_t* scratch) {
   if (!c || !d || !o || d->nx < 2 || d->ny < 2 || d->set_sx < 1 || d->set_sx > MAX_SX || d->set_sy < 1) return false;
   if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return false;
-  if (o->relax_overlap < 0 || std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_RX) return false;
-  if (o->precision == HMS_FP64 && std::min(d->nx, d->set_sx + 2 * o->relax_overlap) > MAX_SX) return false;
+  const long long rw = std::min((long long)d->nx, (long long)d->set_sx + 2LL * (long long)o->relax_overlap);
+  if (o->relax_overlap < 0 || rw > MAX_RX) return false;
+  if (o->precision == HMS_FP64 && rw > MAX_SX) return false;
+  if ((o->mode_mask >> NMODES) != 0u || (o->record_history != 0 && o->record_history != 1)) return false;
   hms_problem pr;
   LatView& lv = pr.lv;
   lv.nx = d->nx;
@@ -1568,7 +1645,7 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
       b += (z.lin + z.lcol + z.dinv + z.dropped + z.delta + z.srow + z.xinv) * 4;
     }
   b += n_c * 4 + 32 + (size_t)std::max(update_residual_blocks(lv), 1024) * 3 * 8 + 4 + sizeof(IterCtl) + 4 + 32;
-  b += 3 * ((size_t)o->max_iter + 1) * 8;
+  if (o->record_history) b += 3 * ((size_t)o->max_iter + 1) * 8;
   *inst = b;
   *scratch = (size_t)std::max(1, std::min(lv.M, c->nsm)) * b_size(MAX_NB) * 8;
   return true;

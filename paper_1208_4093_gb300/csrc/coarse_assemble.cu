@@ -446,19 +446,23 @@ __global__ void k_dense_from_band(int n, int bw, const double* __restrict__ band
 }
 
 // Jacobi scaling (s_i = D_ii^-1/2), right-hand side b = s P, the solution
-// accumulator x = 0, and the modes that vanish: D_ii <= 1e-300, or <= 1e-28
-// times the largest diagonal of the set's nine modes (zero up to rounding).
+// accumulator x = 0, and the modes that take no part: those left out by the
+// mode mask (bit m keeps mode m of every set) and those that vanish, D_ii <=
+// 1e-300 or <= 1e-28 times the largest diagonal of the set's modes that are
+// kept (zero up to rounding).
 __device__ __forceinline__ void coarse_diag_body(int n, int bw, const double* __restrict__ band,
                                                  const double* __restrict__ P, double* __restrict__ scale,
                                                  double* __restrict__ b, double* __restrict__ x,
-                                                 int* __restrict__ dropped, const IterCtl* ctl, int bx, int gx) {
+                                                 int* __restrict__ dropped, unsigned mode_mask, const IterCtl* ctl,
+                                                 int bx, int gx) {
   if (ctl && *(volatile const int*)&ctl->done) return;
   for (int i = bx * blockDim.x + threadIdx.x; i < n; i += gx * blockDim.x) {
     const double D = band[(size_t)i * (bw + 1)];
     const int g0 = i - i % NMODES;
     double dmax = 0.0;
-    for (int m = 0; m < NMODES && g0 + m < n; ++m) dmax = fmax(dmax, band[(size_t)(g0 + m) * (bw + 1)]);
-    const bool drop = !(D > 1e-300) || !(D > 1e-28 * dmax);
+    for (int m = 0; m < NMODES && g0 + m < n; ++m)
+      if ((mode_mask >> m) & 1u) dmax = fmax(dmax, band[(size_t)(g0 + m) * (bw + 1)]);
+    const bool drop = !((mode_mask >> (i % NMODES)) & 1u) || !(D > 1e-300) || !(D > 1e-28 * dmax);
     const double s = drop ? 0.0 : 1.0 / sqrt(D);
     scale[i] = s;
     b[i] = s * P[i];
@@ -470,13 +474,13 @@ __device__ __forceinline__ void coarse_diag_body(int n, int bw, const double* __
 __global__ void k_coarse_diag(int n, int bw, const double* __restrict__ band,
                               const double* __restrict__ P, double* __restrict__ scale,
                               double* __restrict__ b, double* __restrict__ x, int* __restrict__ dropped,
-                              const IterCtl* ctl) {
-  coarse_diag_body(n, bw, band, P, scale, b, x, dropped, ctl, blockIdx.x, gridDim.x);
+                              unsigned mode_mask, const IterCtl* ctl) {
+  coarse_diag_body(n, bw, band, P, scale, b, x, dropped, mode_mask, ctl, blockIdx.x, gridDim.x);
 }
 __global__ void kb_coarse_diag(const BatchProb* __restrict__ Pb, const BatchItem* __restrict__ items) {
   const BatchItem it = items[blockIdx.x];
   const BatchProb& q = Pb[it.prob];
-  coarse_diag_body(q.n_c, q.bw, q.band, q.P, q.scale, q.b, q.x, q.dropped, q.ctl, it.bx, it.gx);
+  coarse_diag_body(q.n_c, q.bw, q.band, q.P, q.scale, q.b, q.x, q.dropped, q.mode_mask, q.ctl, it.bx, it.gx);
 }
 
 // Modes that depend on earlier modes of the same set get a = 0.  Sets have
@@ -689,8 +693,8 @@ cudaError_t launch_coarse_dense_from_band(cudaStream_t s, int n, int bw, const d
 
 cudaError_t launch_coarse_scale(cudaStream_t s, int n, int bw, bool fp64, const double* band, const double* P,
                                 double* sband, void* frow, double* scale, double* b, double* x, int* dropped,
-                                const IterCtl* ctl) {
-  k_coarse_diag<<<grid_for(n), 256, 0, s>>>(n, bw, band, P, scale, b, x, dropped, ctl);
+                                unsigned mode_mask, const IterCtl* ctl) {
+  k_coarse_diag<<<grid_for(n), 256, 0, s>>>(n, bw, band, P, scale, b, x, dropped, mode_mask, ctl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nsets = n / NMODES;

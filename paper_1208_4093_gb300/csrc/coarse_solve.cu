@@ -353,7 +353,9 @@ __host__ __device__ inline int solve_stage_elems(int bw) {
 
 // cstat[0]: bits of max |b| (set by the first solve), cstat[1]: bits of the
 // last residual's max |res| (k_coarse_residual), cstat[2]: 1 once refinement
-// has converged (max |res| <= 1e-14 max |b|); later solves then return at once.
+// has converged (max |res| <= 1e-14 max |b|); later solves then return at once;
+// cstat[3]: updates whose last allowed solve still ran (refinement not
+// converged before it), counted over a whole hms_solve.
 template <typename T>
 __global__ void __launch_bounds__(FTS) k_coarse_solve(int n, int bw, const T* __restrict__ lcol,
                                                       const T* __restrict__ lrow, const T* __restrict__ dinv,
@@ -362,6 +364,9 @@ __global__ void __launch_bounds__(FTS) k_coarse_solve(int n, int bw, const T* __
                                                       double* __restrict__ a_out, unsigned long long* cstat, int first,
                                                       const IterCtl* ctl, int* err) {
   if (ctl && *(volatile const int*)&ctl->done) return;
+  // first: bit 0 = the solve of b, bit 1 = the last solve the update allows
+  const bool last = (first & 2) != 0;
+  first &= 1;
   __shared__ int skip;
   if (threadIdx.x == 0) {
     if (first) {
@@ -371,6 +376,7 @@ __global__ void __launch_bounds__(FTS) k_coarse_solve(int n, int bw, const T* __
       const double rmax = __longlong_as_double((long long)cstat[1]);
       skip = (cstat[2] != 0ull) || !(rmax > 1e-14 * bmax);
       if (skip) cstat[2] = 1ull;
+      else if (last) atomicAdd(&cstat[3], 1ull);  // refinement used every solve it may
     }
   }
   __syncthreads();
@@ -719,6 +725,9 @@ __device__ __forceinline__ void solve_big_body(int n, int bw, const float* __res
                                                double* __restrict__ a_out, unsigned long long* cstat, int first,
                                                const IterCtl* ctl, int* err) {
   if (ctl && *(volatile const int*)&ctl->done) return;
+  // first: bit 0 = the solve of b, bit 1 = the last solve the update allows
+  const bool last = (first & 2) != 0;
+  first &= 1;
   __shared__ int skip;
   if (threadIdx.x == 0) {
     if (first) {
@@ -728,6 +737,7 @@ __device__ __forceinline__ void solve_big_body(int n, int bw, const float* __res
       const double rmax = __longlong_as_double((long long)cstat[1]);
       skip = (cstat[2] != 0ull) || !(rmax > 1e-14 * bmax);
       if (skip) cstat[2] = 1ull;
+      else if (last) atomicAdd(&cstat[3], 1ull);  // refinement used every solve it may
     }
   }
   __syncthreads();
@@ -975,6 +985,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FTB)
   const int rank = (int)cl.block_rank();
   const SolveSide sd = rank ? s1 : s0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // first: bit 0 = the solve of b, bit 1 = the last solve the update allows
+  const bool last = (first & 2) != 0;
+  first &= 1;
   __shared__ int skip;
   if (tid == 0) {
     if (first) {
@@ -983,6 +996,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(FTB)
       const double bmax = __longlong_as_double((long long)cstat[0]);
       const double rmax = __longlong_as_double((long long)cstat[1]);
       skip = (cstat[2] != 0ull) || !(rmax > 1e-14 * bmax);
+      if (!skip && last && rank == 0) atomicAdd(&cstat[3], 1ull);  // refinement used every solve it may
     }
   }
   cl.sync();  // both CTAs have read cstat
@@ -1257,14 +1271,14 @@ cudaError_t launch_coarse_blockinv(cudaStream_t s, int n, int bw, const void* lc
 
 cudaError_t launch_coarse_solve_big(cudaStream_t s, int stages, int n, int bw, const void* lcol, const void* lrow,
                                     const float* xinv, const int* dropped, const double* res, double* x,
-                                    const double* scale, double* a_out, unsigned long long* cstat, bool first,
+                                    const double* scale, double* a_out, unsigned long long* cstat, int flags,
                                     const IterCtl* ctl, int* err) {
   const size_t smem = big_solve_smem_bytes(n, bw, stages);
   if (stages >= 3)
-    k_coarse_solve_big<3><<<1, FTB, smem, s>>>(n, bw, xinv, dropped, res, x, scale, a_out, cstat, first ? 1 : 0,
+    k_coarse_solve_big<3><<<1, FTB, smem, s>>>(n, bw, xinv, dropped, res, x, scale, a_out, cstat, flags,
                                                ctl, err);
   else
-    k_coarse_solve_big<2><<<1, FTB, smem, s>>>(n, bw, xinv, dropped, res, x, scale, a_out, cstat, first ? 1 : 0,
+    k_coarse_solve_big<2><<<1, FTB, smem, s>>>(n, bw, xinv, dropped, res, x, scale, a_out, cstat, flags,
                                                ctl, err);
   return cudaGetLastError();
 }
@@ -1283,16 +1297,16 @@ cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, bool fp64, void*
 
 cudaError_t launch_coarse_solve(cudaStream_t s, int n, int bw, bool fp64, const void* lcol, const void* lrow,
                                 const void* dinv, const int* dropped, const double* res, double* x,
-                                const double* scale, double* a_out, unsigned long long* cstat, bool first,
+                                const double* scale, double* a_out, unsigned long long* cstat, int flags,
                                 const IterCtl* ctl, int* err) {
   const size_t smem = coarse_solve_smem_bytes(n, bw, fp64);
   if (fp64)
     k_coarse_solve<double><<<1, FTS, smem, s>>>(n, bw, (const double*)lcol, (const double*)lrow,
                                                 (const double*)dinv, dropped, res, x, scale, a_out, cstat,
-                                                first ? 1 : 0, ctl, err);
+                                                flags, ctl, err);
   else
     k_coarse_solve<float><<<1, FTS, smem, s>>>(n, bw, (const float*)lcol, (const float*)lrow, (const float*)dinv,
-                                               dropped, res, x, scale, a_out, cstat, first ? 1 : 0, ctl, err);
+                                               dropped, res, x, scale, a_out, cstat, flags, ctl, err);
   return cudaGetLastError();
 }
 
@@ -1380,16 +1394,16 @@ cudaError_t launch_coarse_factor_2s(cudaStream_t st, int n, int bw, const TwoSid
 }
 cudaError_t launch_coarse_solve_2s(cudaStream_t st, int n, const TwoSided& t, const double* res, double* x,
                                    const double* scale, double* a_out, int* dropped_out, unsigned long long* cstat,
-                                   bool first, const IterCtl* ctl, int* err) {
+                                   int flags, const IterCtl* ctl, int* err) {
   const int s = t.s, bws = s - 1;
   const SolveSide a{t.xinv[0], t.dropped[0], t.lcol[0], t.m[0]}, b{t.xinv[1], t.dropped[1], t.lcol[1], t.m[1]};
   const size_t smem = big_solve_smem_bytes((t.m[0] > t.m[1] ? t.m[0] : t.m[1]) + s, bws, t.stages);
   if (t.stages >= 3)
     k_coarse_solve_2s<3><<<2, FTB, smem, st>>>(n, s, bws, a, b, res, x, scale, a_out, dropped_out, cstat,
-                                               first ? 1 : 0, ctl, err);
+                                               flags, ctl, err);
   else
     k_coarse_solve_2s<2><<<2, FTB, smem, st>>>(n, s, bws, a, b, res, x, scale, a_out, dropped_out, cstat,
-                                               first ? 1 : 0, ctl, err);
+                                               flags, ctl, err);
   return cudaGetLastError();
 }
 

@@ -153,6 +153,7 @@ cudaError_t launch_update_residual(cudaStream_t s, const LatView& lv, const doub
                                    unsigned* ticket, double* norms_out, IterCtl* ctl, double* hist,
                                    int hist_cap, int* u_cur);
 int update_residual_blocks(const LatView& lv);
+cudaError_t launch_reactions(cudaStream_t s, const LatView& lv, const double2* u, double2* f);
 cudaError_t launch_load_norms(cudaStream_t s, const LatView& lv, double2* p, double* partials,
                               unsigned* ticket, IterCtl* ctl);
 // residual_noalloc.cu
@@ -166,7 +167,8 @@ cudaError_t launch_set_factor(cudaStream_t s, const LatView& lv, const long long
 // relax.cu
 cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
                          const double* f64, const float* f32, const double2* r, void* delta,
-                         double* P, void* yscratch, const IterCtl* ctl, int* err, int threads, int chunks);
+                         double* P, void* yscratch, const IterCtl* ctl, int* err, int threads, int chunks,
+                         int wait0 = -1);
 size_t relax_smem_bytes(const LatView& lv, bool fp32, int chunks = 1);
 bool relax_chunks_possible(const LatView& lv, bool fp32);
 long long relax_y_stride(const LatView& lv);
@@ -182,12 +184,12 @@ cudaError_t launch_coarse_dense_from_band(cudaStream_t s, int n, int bw, const d
                                           double* dense);
 cudaError_t launch_coarse_scale(cudaStream_t s, int n, int bw, bool fp64, const double* band, const double* P,
                                 double* sband, void* frow, double* scale, double* b, double* x, int* dropped,
-                                const IterCtl* ctl);
+                                unsigned mode_mask, const IterCtl* ctl);
 cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, bool fp64, void* lrow, void* lcol, void* dinv,
                                  int* dropped, bool write_lrow, const IterCtl* ctl);
 cudaError_t launch_coarse_solve(cudaStream_t s, int n, int bw, bool fp64, const void* lcol, const void* lrow,
                                 const void* dinv, const int* dropped, const double* res, double* x,
-                                const double* scale, double* a_out, unsigned long long* cstat, bool first,
+                                const double* scale, double* a_out, unsigned long long* cstat, int flags,
                                 const IterCtl* ctl, int* err);
 size_t coarse_xinv_elems(int n, int bw);
 int coarse_big_stages(int n, int bw, int max_smem);
@@ -195,7 +197,7 @@ cudaError_t launch_coarse_blockinv(cudaStream_t s, int n, int bw, const void* lc
                                    const IterCtl* ctl);
 cudaError_t launch_coarse_solve_big(cudaStream_t s, int stages, int n, int bw, const void* lcol, const void* lrow,
                                     const float* xinv, const int* dropped, const double* res, double* x,
-                                    const double* scale, double* a_out, unsigned long long* cstat, bool first,
+                                    const double* scale, double* a_out, unsigned long long* cstat, int flags,
                                     const IterCtl* ctl, int* err);
 cudaError_t launch_coarse_residual(cudaStream_t s, int n, int bw, const double* sband, const double* b,
                                    const double* x, const int* dropped, double* res, unsigned long long* cstat,
@@ -235,6 +237,7 @@ struct BatchProb {
   int* dropped;
   unsigned long long* cstat;
   int n_c, bw;
+  unsigned mode_mask;
 };
 // One CTA of a batched launch: the problem and the block index (bx, by) of the
 // problem's own launch of that kernel, whose grid is gx x gy.
@@ -291,7 +294,7 @@ cudaError_t launch_coarse_factor_2s(cudaStream_t st, int n, int bw, const TwoSid
                                     const int* dropped, const IterCtl* ctl);
 cudaError_t launch_coarse_solve_2s(cudaStream_t st, int n, const TwoSided& t, const double* res, double* x,
                                    const double* scale, double* a_out, int* dropped_out, unsigned long long* cstat,
-                                   bool first, const IterCtl* ctl, int* err);
+                                   int flags, const IterCtl* ctl, int* err);
 size_t coarse_factor_smem_bytes(int n, int bw, bool fp64);
 size_t coarse_solve_smem_bytes(int n, int bw, bool fp64);
 int coarse_dinv_size(int n);

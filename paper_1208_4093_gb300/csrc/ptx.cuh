@@ -56,9 +56,11 @@ __device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`; false if it gave up.
-__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it)
+// Bounded wait for phase `parity` of `bar`: at most `limit` tries; false if
+// it gave up.
+constexpr uint32_t MBAR_WAIT_TRIES = 1u << 22;
+__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit = MBAR_WAIT_TRIES) {
+  for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

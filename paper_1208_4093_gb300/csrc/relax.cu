@@ -269,7 +269,7 @@ template <typename T, int NT, int NC>
 __device__ __forceinline__ void relax_body(const LatView lv, const long long* __restrict__ set_off,
                                            const T* __restrict__ fac, const double2* __restrict__ r,
                                            T* __restrict__ delta, double* __restrict__ P, T* __restrict__ yglob,
-                                           long long ystride, const IterCtl* ctl, int* err, int I) {
+                                           long long ystride, const IterCtl* ctl, int* err, int I, int wait0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ uint64_t bars[NSLOT];
   __shared__ double pred[(VL / 32) * NMODES];
@@ -311,7 +311,9 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
     return (mat_of_op(o) & 1) ? (fwd ? 1 : 3) : (fwd ? 0 : 2);
   };
   const int nbr = y_row(nb);
+  int issued = 0;  // ops whose copies the producer has issued (producer thread only)
   auto issue = [&](int o) {
+    ++issued;
     const int k = mat_of_op(o);
     const int kind = kind_of_op(o);
     const bool fwd = o / NC < nmat;
@@ -378,12 +380,16 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
 
   const double2 rep = lv.rep[I];
 
+  int o_stop = 0;  // the op at which an abort left the loop
   for (int o = 0; o < nops; ++o) {
+    o_stop = o;
     const int k = mat_of_op(o);
     const bool is_b = (k & 1) != 0;
     const int j = is_b ? (k + 1) / 2 : k / 2;
     const bool last_copy = (o % NC) == NC - 1;  // the matrix's outputs are complete after it
-    const bool late = !producer && !mbar_wait_bounded(&bars[o % NSLOT], (uint32_t)((o / NSLOT) & 1));
+    // the first wait may be given a shorter bound (tests of the timeout path)
+    const uint32_t tries = (o == 0 && wait0 >= 0) ? (uint32_t)wait0 : MBAR_WAIT_TRIES;
+    const bool late = !producer && !mbar_wait_bounded(&bars[o % NSLOT], (uint32_t)((o / NSLOT) & 1), tries);
     if (NC != 1) {
       // after the first copy of a matrix there is no end-of-op barrier: this
       // one frees its slot (and decides an abort the same way in every thread)
@@ -462,9 +468,12 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
     }
   }
   if (abort_flag) {
-    // let copies still in flight land before the CTA exits
-    if (tid == 0) {
-      for (int b2 = 0; b2 < NSLOT; ++b2) mbar_wait_bounded(&bars[b2], 0u), mbar_wait_bounded(&bars[b2], 1u);
+    // Let the copies still in flight land before the CTA exits: every thread
+    // left the loop at op o_stop, whose wait (or an earlier one) gave up, and
+    // the ops before it completed, so the ones in flight are o_stop ..
+    // issued - 1, one per slot.  The producer waits for exactly those phases.
+    if (tid == NT) {
+      for (int k = o_stop; k < issued; ++k) mbar_wait_bounded(&bars[k % NSLOT], (uint32_t)((k / NSLOT) & 1));
       atomicOr(err, (int)DEVERR_TIMEOUT);
     }
     return;
@@ -518,8 +527,8 @@ __global__ void __launch_bounds__(NT + 32) k_relax(LatView lv, const long long* 
                                               const T* __restrict__ fac, const double2* __restrict__ r,
                                               T* __restrict__ delta, double* __restrict__ P,
                                               T* __restrict__ yglob, long long ystride, const IterCtl* ctl,
-                                              int* err) {
-  relax_body<T, NT, NC>(lv, set_off, fac, r, delta, P, yglob, ystride, ctl, err, blockIdx.x);
+                                              int* err, int wait0) {
+  relax_body<T, NT, NC>(lv, set_off, fac, r, delta, P, yglob, ystride, ctl, err, blockIdx.x, wait0);
 }
 
 // Batched: the sets of every problem of a batch.
@@ -531,7 +540,7 @@ __global__ void __launch_bounds__(NT + 32) kb_relax(const BatchProb* __restrict_
   if constexpr (sizeof(T) == 4) fac = q.f32;
   else fac = q.f64;
   relax_body<T, NT, NC>(q.lv, q.set_off, fac, q.r, (T*)q.delta, q.P, (T*)q.yscratch, y_stride(q.lv), q.ctl,
-                        q.err, it.bx);
+                        q.err, it.bx, -1);
 }
 
 }  // namespace
@@ -565,7 +574,8 @@ static cudaError_t dispatch_nt(int threads, F go) {
 
 cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
                          const double* f64, const float* f32, const double2* r, void* delta,
-                         double* P, void* yscratch, const IterCtl* ctl, int* err, int threads, int chunks) {
+                         double* P, void* yscratch, const IterCtl* ctl, int* err, int threads, int chunks,
+                         int wait0) {
   const bool fp32 = (f32 != nullptr);
   if (chunks == 2 && !relax_chunks_possible(lv, fp32)) return cudaErrorInvalidValue;
   const size_t smem = relax_smem_bytes(lv, fp32, chunks);
@@ -574,10 +584,10 @@ cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set
     constexpr int NT = decltype(nt)::value, NC = decltype(nc)::value;
     if (fp32)
       k_relax<float, NT, 1><<<lv.M, NT + 32, smem, s>>>(lv, set_off, f32, r, (float*)delta, P, (float*)yscratch, ys, ctl,
-                                                   err);
+                                                   err, wait0);
     else
       k_relax<double, NT, NC><<<lv.M, NT + 32, smem, s>>>(lv, set_off, f64, r, (double*)delta, P, (double*)yscratch, ys,
-                                                     ctl, err);
+                                                     ctl, err, wait0);
   };
   const cudaError_t e = chunks == 2 ? dispatch_nt<2>(threads, go) : dispatch_nt<1>(threads, go);
   if (e != cudaSuccess) return e;

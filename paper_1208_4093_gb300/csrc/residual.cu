@@ -261,7 +261,57 @@ __global__ void __launch_bounds__(NT) k_load_norms(LatView lv, double2* __restri
   }
 }
 
+// K u at every DOF (constrained ones included): the nodal forces of the bars,
+// with u read as 0 on constrained DOFs.  One CTA per 32 x 8 node tile and its
+// one-node halo in shared memory, the six bars of each node summed as in the
+// residual above.
+__global__ void __launch_bounds__(NT) k_reactions(LatView lv, const double2* __restrict__ u,
+                                                  double2* __restrict__ f) {
+  __shared__ double2 U[TY + 2][TX + 2];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < (TX + 2) * (TY + 2); idx += NT) {
+    const int lx = idx % (TX + 2), ly = idx / (TX + 2);
+    const int i = i0 + lx - 1, j = j0 + ly - 1;
+    double2 v = make_double2(0.0, 0.0);
+    if (i >= 0 && i < lv.nx && j >= 0 && j < lv.ny) {
+      const size_t n = (size_t)j * lv.nx + i;
+      v = u[n];
+      const unsigned fm = lv.fix[n];
+      if (fm & 1u) v.x = 0.0;
+      if (fm & 2u) v.y = 0.0;
+    }
+    U[ly][lx] = v;
+  }
+  __syncthreads();
+  const int tx = tid % TX, ty = tid / TX;
+  const int i = i0 + tx, j = j0 + ty;
+  if (i >= lv.nx || j >= lv.ny) return;
+  const int lx = tx + 1, ly = ty + 1, off = j & 1;
+  const double2 uc = U[ly][lx];
+  const double kE = bar_k(lv, i, j, 0), kW = bar_k(lv, i - 1, j, 0);
+  double fx = kE * (uc.x - U[ly][lx + 1].x) + kW * (uc.x - U[ly][lx - 1].x);
+  const double kNE = bar_k(lv, i, j, 1), kSW = bar_k(lv, i - 1 + off, j - 1, 1);
+  const double2 une = U[ly + 1][lx + off], usw = U[ly - 1][lx - 1 + off];
+  const double d1x = kNE * (uc.x - une.x) + kSW * (uc.x - usw.x);
+  const double d1y = kNE * (uc.y - une.y) + kSW * (uc.y - usw.y);
+  const double p1 = fma(SQ3_2, d1y, 0.5 * d1x);
+  const double kNW = bar_k(lv, i, j, 2), kSE = bar_k(lv, i + off, j - 1, 2);
+  const double2 unw = U[ly + 1][lx - 1 + off], use = U[ly - 1][lx + off];
+  const double d2x = kNW * (uc.x - unw.x) + kSE * (uc.x - use.x);
+  const double d2y = kNW * (uc.y - unw.y) + kSE * (uc.y - use.y);
+  const double p2 = fma(SQ3_2, d2y, -0.5 * d2x);
+  fx = fma(0.5, p1 - p2, fx);
+  f[(size_t)j * lv.nx + i] = make_double2(fx, SQ3_2 * (p1 + p2));
+}
+
 }  // namespace
+
+cudaError_t launch_reactions(cudaStream_t s, const LatView& lv, const double2* u, double2* f) {
+  dim3 grid((lv.nx + TX - 1) / TX, (lv.ny + TY - 1) / TY);
+  k_reactions<<<grid, NT, 0, s>>>(lv, u, f);
+  return cudaGetLastError();
+}
 
 int update_residual_blocks(const LatView& lv) {
   return ((lv.nx + TX - 1) / TX) * ((lv.ny + TY - 1) / TY);

@@ -1,5 +1,6 @@
 """Serving: requests of different sizes admitted under an HBM budget and
-advanced together (continuous batching) give the same result as solo solves.
+advanced together (continuous batching) give the same result as solo solves,
+and every served load vector matches the oracle's direct solve.
 
 Every request runs its own problem, whose kernels are deterministic and share
 no buffers with the others, so each result in the mix must equal its solo
@@ -59,6 +60,7 @@ def test_estimate_equals_allocation_plus_setup_scratch(hms_ctx):
 
 
 def test_serving_matches_solo(hms_ctx):
+    from oracle import direct, truss
     from paper_1208_4093_gb300 import capi
     srv = capi.hms_server_create(hms_ctx, 64 << 30, max_active=64)
     ids = {}
@@ -93,6 +95,13 @@ def test_serving_matches_solo(hms_ctx):
                 capi.hms_problem_destroy(pr)
             assert np.array_equal(u, solo), REQS[k]
             assert np.array_equal(its, sits)
+            # and every served load vector against the direct solve (O1):
+            # 1e-9 for the FP64 path, 1e-8 for the mixed one
+            tr = truss.Truss(nx, ny, kw.get("ea"))
+            bar = 1e-9 if kw["precision"] == capi.HMS_FP64 else 1e-8
+            for q in range(p.shape[0]):
+                us = direct.cholesky_solve(tr, tr.free * p[q])
+                assert np.linalg.norm(u[q] - us) <= bar * np.linalg.norm(us), (REQS[k], q)
     finally:
         capi.hms_server_destroy(srv)
 

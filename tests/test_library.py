@@ -78,7 +78,7 @@ def test_binding_structs_match_the_header(cname, pyname):
     want = header_struct_fields(cname)
     got = getattr(capi, pyname)._fields_
     assert [n for _, n in want] == [n for n, _ in got]
-    size = {"int32_t": ctypes.c_int32, "double": ctypes.c_double}
+    size = {"int32_t": ctypes.c_int32, "uint32_t": ctypes.c_uint32, "double": ctypes.c_double}
     for (ctype, n), (_, pytype) in zip(want, got):
         c = ctypes.c_void_p if ctype.endswith("*") else size[ctype]
         assert ctypes.sizeof(c) == ctypes.sizeof(pytype), n

@@ -144,6 +144,23 @@ def test_direct_matches_dense_solve(nx, ny, lognormal):
     assert np.all(u[~tr.free] == 0)
 
 
+@pytest.mark.parametrize("nx,ny,lognormal", [(9, 7, False), (12, 11, True), (40, 33, True)])
+def test_sparse_direct_matches_banded_and_dense(nx, ny, lognormal):
+    """The sparse direct solve (used where the band no longer fits) against a
+    dense solve and the banded Cholesky, and its residual against K itself."""
+    tr = truss.Truss(nx, ny, ea_lognormal(nx, ny, 13) if lognormal else None)
+    p = tr.free * loads(nx, ny, 4).reshape(-1)
+    u = direct.sparse_solve(tr, p)
+    assert np.all(u[~tr.free] == 0)
+    ub = direct.cholesky_solve(tr, p)
+    assert np.linalg.norm(u - ub) <= 1e-12 * np.linalg.norm(ub)
+    if tr.fdofs.size <= 1000:
+        uf = np.linalg.solve(tr.K_ff().toarray(), p[tr.fdofs])
+        assert np.allclose(u[tr.fdofs], uf, rtol=1e-12, atol=1e-12)
+    r = tr.residual(p, u)
+    assert np.abs(r).sum() <= 1e-13 * np.abs(p).sum()
+
+
 def test_reactions_balance_loads():
     """At the solution the supports carry the applied loads: K u summed over
     the constrained DOFs equals minus the sum of the loads (forces and moment)."""

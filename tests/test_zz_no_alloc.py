@@ -1,11 +1,13 @@
-"""The allocation-free residual entry point against hms_residual.
+"""The allocation-free residual entry point against hms_residual and the oracle.
 
-hms_residual_noalloc computes the same r = p - K u and sums (Eqs. 1, 19, 2)
-as hms_residual, with its per-CTA partial sums and completion counter in
-static device memory.  Two calls in a row must both match hms_residual: the
-second one only does if the first left the counter at zero.  This file is
-named to be collected last, so that it also runs after every other GPU test
-has used the context.
+hms_residual_noalloc is for callers that cannot allocate device memory while
+they call (a busy device where cudaFree would synchronise it, or HBM already
+committed).  It computes the same r = p - K u and sums as hms_residual, with
+its per-CTA partial sums and completion counter in static device memory.  Two
+calls in a row must both match hms_residual: the second one only does if the
+first left the counter at zero.  Both are also checked against the oracle's
+assembled K.  This file is named to be collected last, so that it also runs
+after every other GPU test has used the context.
 """
 import ctypes
 
@@ -52,9 +54,18 @@ def test_two_calls_match_hms_residual(hms_ctx, nx, ny, sx, sy, lognormal):
             outs.append((r.cpu().numpy(), nrm.cpu().numpy()))
         rr, nr = r_ref.cpu().numpy(), n_ref.cpu().numpy()
         scale = np.abs(rr).max()
+        # the oracle: K assembled bar by bar, constrained DOFs of u read as 0
+        from oracle import truss
+        tr = truss.Truss(nx, ny, ea_lognormal(nx, ny, seed=5) if lognormal else None)
+        pn, un = p.cpu().numpy(), u.cpu().numpy()
+        ro = tr.residual(pn, un)
+        uf = tr.free * un
+        no = np.array([np.abs(ro).sum(), ro @ ro, uf @ (tr.free * pn + ro)])
         for r, nrm in outs:
             np.testing.assert_allclose(r, rr, rtol=1e-13, atol=1e-13 * scale)
             np.testing.assert_allclose(nrm, nr, rtol=1e-12)
+            assert np.abs(r - ro).max() <= 1e-13 * np.abs(ro).max()
+            np.testing.assert_allclose(nrm, no, rtol=1e-11)
         # inputs are read in place and left unchanged
         assert torch.equal(p.cpu(), torch.from_numpy(loads(nx, ny, seed=12).reshape(-1)))
     finally:
@@ -77,6 +88,9 @@ def test_rejects_host_misaligned_and_aliased(hms_ctx):
         assert f(pr, host.ctypes.data, u.data_ptr(), r.data_ptr(), None) == capi.HMS_ERR_ARG
         assert f(pr, p.data_ptr() + 8, u.data_ptr(), r.data_ptr(), None) == capi.HMS_ERR_ARG
         assert f(pr, p.data_ptr(), u.data_ptr(), u.data_ptr(), None) == capi.HMS_ERR_ARG
+        # r overlapping u or p at an offset (16-byte aligned, so only the overlap is wrong)
+        assert f(pr, p.data_ptr(), u.data_ptr(), u.data_ptr() + 16, None) == capi.HMS_ERR_ARG
+        assert f(pr, p.data_ptr() + 16, u.data_ptr(), p.data_ptr(), None) == capi.HMS_ERR_ARG
         assert f(pr, p.data_ptr(), u.data_ptr(), r.data_ptr(), r.data_ptr() + 4) == capi.HMS_ERR_ARG
         assert f(pr, None, u.data_ptr(), r.data_ptr(), None) == capi.HMS_ERR_ARG
         with pytest.raises(ValueError):
