@@ -216,23 +216,46 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(iters, workload_seed=0):
-    """Time `iters` oracle iterations on the full workload (setup untimed);
-    returns (seconds per iteration, setup seconds)."""
-    import numpy as np
-    from oracle import hms, truss
+def oracle_update_seconds(tr, g, p, lf, iters):
+    """Seconds per update of the oracle's iteration: `iters` updates (and their
+    iters + 1 residuals) from u = 0, divided by iters.  The one definition both
+    CPU legs use."""
+    from oracle import hms
+    t0 = time.perf_counter()
+    hms.solve(tr, g, p, 0.0, iters, factors=lf)
+    return (time.perf_counter() - t0) / iters
+
+
+def oracle_sample(iters, workers=None):
+    """Time `iters` oracle updates on the full workload, the per-set relaxation
+    spread over `workers` host processes (all cores by default) and the dense
+    algebra on the host BLAS's threads; setup untimed.  Returns (seconds per
+    update, setup seconds, workers)."""
+    from oracle import hms, pool, truss
     c = case()
     t0 = time.perf_counter()
     tr = truss.Truss(c.nx, c.ny, c.ea_array())
     g = hms.SetGrid(c.nx, c.ny, c.sx, c.sy)
+    with pool.PoolFactors(c.nx, c.ny, c.sx, c.sy, ea=c.ea_array(), workers=workers) as lf:
+        setup = time.perf_counter() - t0
+        p = c.load_array().reshape(-1)
+        per = oracle_update_seconds(tr, g, p, lf, iters)
+        return per, setup, lf.workers
+
+
+def oracle_c1_solve():
+    """The oracle's whole solve of the 64 x 64 lattice (16 x 16 sets, EA = 1,
+    seed-0 loads) to R1 < 1e-8, timed end to end after its setup: (ms, updates)."""
+    from oracle import hms, truss
+    from workloads import CASES
+    c = CASES["lattice64_fp64"]
+    tr = truss.Truss(c.nx, c.ny)
+    g = hms.SetGrid(c.nx, c.ny, c.sx, c.sy)
     lf = hms.LocalFactors(tr, g)
-    setup = time.perf_counter() - t0
     p = c.load_array().reshape(-1)
     t0 = time.perf_counter()
-    hms.solve(tr, g, p, 0.0, iters, factors=lf)
-    dt = time.perf_counter() - t0
-    # solve() evaluates iters + 1 residuals and iters updates: charge per update
-    return dt / iters, setup
+    res = hms.solve(tr, g, p, 1e-8, 5000, factors=lf)
+    return (time.perf_counter() - t0) * 1e3, res.iterations
 
 
 def err_vs_oracle(u):
@@ -259,14 +282,35 @@ def nir_golden(tol):
         return None, None
 
 
+def host_cpu():
+    """(model name, logical cores) of this host."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            if k.strip() in ("model name", "Model", "CPU part") and v.strip():
+                model = model or v.strip()
+    except OSError:
+        pass
+    import platform
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+    if model in arm_parts:
+        model = f"{arm_parts[model]} (CPU part {model})"
+    return model or platform.processor() or platform.machine(), os.cpu_count() or 1
+
+
 def cpu_baseline_subprocess(iters):
-    """The oracle as it stands, one thread, in a child process."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    """The oracle as it stands on all host cores, in a child process (which
+    never touches the GPU): seconds per update on the bench workload and the
+    whole 64 x 64 solve."""
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps(bench.oracle_sample(%d)))" % (ROOT, iters))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
-    per_it, setup = json.loads(out.stdout.strip().splitlines()[-1])
-    return per_it, setup
+            "per, setup, w = bench.oracle_sample(%d); c1 = bench.oracle_c1_solve(); "
+            "print(json.dumps([per, setup, w, c1[0], c1[1]]))" % (ROOT, iters))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr.strip().splitlines()[-1] if out.stderr.strip() else "oracle run failed")
+    per, setup, workers, c1_ms, c1_its = json.loads(out.stdout.strip().splitlines()[-1])
+    return per, setup, workers, c1_ms, c1_its
 
 
 # ---------------------------------------------------------------- reference arm
@@ -274,20 +318,19 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     c = case()
-    import numpy as np
-    from oracle import hms, truss
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import hms, pool, truss
     tr = truss.Truss(c.nx, c.ny, c.ea_array())
     g = hms.SetGrid(c.nx, c.ny, c.sx, c.sy)
-    lf = hms.LocalFactors(tr, g)
     p = c.load_array().reshape(-1)
     nir, src = nir_golden(TOL)
+    model, cores = host_cpu()
     per = []
-    for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        hms.solve(tr, g, p, 0.0, 1, factors=lf)
-        if k >= args.warmup:
-            per.append(time.perf_counter() - t0)
+    with pool.PoolFactors(c.nx, c.ny, c.sx, c.sy, ea=c.ea_array()) as lf:
+        workers = lf.workers
+        for k in range(args.warmup + args.steps):
+            t = oracle_update_seconds(tr, g, p, lf, 1)
+            if k >= args.warmup:
+                per.append(t)
     per_it = statistics.median(per)
     value = per_it * nir * 1e3 if nir else None
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms",
@@ -295,10 +338,11 @@ def run_reference(args, rank, world):
             "ms_per_step": value, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(c), iterations=nir, iterations_source=src,
-                           parallelism="single host thread"),
-            "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} single-iteration oracle steps on the full workload "
-                                       f"({per_it:.2f} s each, setup excluded) x {nir} iterations"},
+                           parallelism=f"host: per-set relaxation over {workers} processes, BLAS threads"),
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "cpu": model, "kind": "oracle",
+                             "sample": f"{args.steps} single-update oracle steps on the full workload "
+                                       f"({per_it:.2f} s each, setup excluded) x {nir} updates, the count the "
+                                       f"oracle's own run takes to R1 < {TOL:g}"},
             "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -633,8 +677,18 @@ def run_ours(args, rank, world, local_rank):
     setup64 = capi.hms_problem_setup_ms(pr64)
     ms64, clocks = timed(pr64, args.steps, args.warmup, clocks=True)
     nit64 = int(its.item())
+    cap_hits64 = capi.hms_problem_refine_cap_hits(pr64)
     shape64 = {"threads": capi.hms_problem_relax_threads(pr64), "copies": capi.hms_problem_relax_copies(pr64)}
     u64 = u_dev.cpu().numpy().copy()
+    # the error of the timed solve, against the same lattice solved far past the
+    # metric's tolerance (R1 < 1e-12); tests/test_gpu_fullsize.py compares such
+    # solves with the oracle's direct solve over every DOF
+    prt = make(capi.HMS_FP64, tol=1e-12)
+    capi.hms_solve(ctx, prt, p_dev, u_dev, iters=its)
+    tight_its = int(its.item())
+    u_tight = u_dev.cpu().numpy().copy()
+    capi.hms_problem_destroy(prt)
+    err_tight = float(np.linalg.norm(u64 - u_tight) / np.linalg.norm(u_tight))
     # e2e through host buffers (pinned): H2D of the loads and D2H of u inside the timed region
     p_pin = torch.from_numpy(p_host).pin_memory()
     u_pin = torch.empty_like(p_pin).pin_memory()
@@ -679,8 +733,32 @@ def run_ours(args, rank, world, local_rank):
         nor, _ = nir_golden(TOL_CONFIG)
         config_eps["oracle_iterations"] = nor
 
+    # ---- the 64 x 64 lattice (16 x 16-node sets, EA = 1), FP64, to R1 < 1e-8 ----
+    from workloads import CASES
+    c1 = CASES["lattice64_fp64"]
+    pr1 = capi.hms_problem_create(ctx, c1.nx, c1.ny, c1.sx, c1.sy, precision=capi.HMS_FP64, tol=1e-8,
+                                  max_iter=5000)
+    p1 = torch.from_numpy(c1.load_array().reshape(1, -1)).to(dev)
+    u1 = torch.empty_like(p1)
+    for _ in range(2):
+        capi.hms_solve(ctx, pr1, p1, u1, iters=its)
+    c1_ms = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        capi.hms_solve(ctx, pr1, p1, u1, iters=its)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c1_ms.append(e0.elapsed_time(e1))
+    c1_gpu = {"value": statistics.median(c1_ms), "unit": "ms", "iterations": int(its.item())}
+    capi.hms_problem_destroy(pr1)
+
     # ---- per-kernel CUDA-event times (profile pass, same workload) ----
     hbm_peak, peak_src = peaks()
+    try:
+        fp64_probe = capi.hms_measure_fp64_rate(local_rank)
+    except capi.HmsError:
+        fp64_probe = None
     rooflines = {}
     for prec, name in ((capi.HMS_FP64, "fp64"), (capi.HMS_MIXED, "mixed")):
         if name == "mixed" and args.no_mixed:
@@ -706,8 +784,12 @@ def run_ours(args, rank, world, local_rank):
                     "unit": "GFLOP/s", "frac": ach / pk,
                     "peak_source": f"FP64 units: {n_sm} SMs x {FP64_LANES_PER_SM_CLK} DFMA lanes/clock x 2 flops x "
                                    f"{mhz:.0f} MHz",
-                    "hbm_gbs": b / (avg * 1e-3) / 1e9}
+                    "peak_measured_fma_loop": fp64_probe,
+                    "frac_of_measured_fma_loop": (ach / fp64_probe) if fp64_probe else None,
+                    "hbm_gbs": b / (avg * 1e-3) / 1e9, "hbm_frac": b / (avg * 1e-3) / 1e9 / hbm_peak}
         roof.update({"algorithmic_bytes": b, "algorithmic_flops": fl, "avg_launch_ms": avg, "launches": n,
+                     "avg_launch_ms_source": "profile pass: one solve of the same workload with options.profile "
+                                             "= 1 (CUDA events on the context stream around every kernel)",
                      "traffic": traffic_for(roof["kernel"], WORKLOAD, "relax.cu")})
         rb, _ = residual_work(c, fp32)
         rms, rn = kt["update_residual"]
@@ -741,14 +823,19 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         try:
-            per_it, setup_s = cpu_baseline_subprocess(3)
+            per_it, setup_s, workers, c1_ms_or, c1_its_or = cpu_baseline_subprocess(3)
             nir = nit64
-            cpu = {"value": per_it * nir * 1e3, "unit": "ms", "cores": 1, "kind": "oracle",
-                   "sample": f"3 oracle iterations on the full workload, one thread ({per_it:.2f} s per "
-                             f"iteration, setup {setup_s:.1f} s excluded), scaled by the {nir} iterations "
-                             f"the FP64 method takes here"}
+            model, cores = host_cpu()
+            cpu = {"value": per_it * nir * 1e3, "unit": "ms", "cores": cores, "cpu": model, "kind": "oracle",
+                   "sample": f"3 oracle updates on the full workload ({per_it:.2f} s per update: the per-set "
+                             f"relaxation over {workers} host processes, dense algebra on the host BLAS's "
+                             f"threads; setup {setup_s:.1f} s excluded), times the {nir} updates the FP64 "
+                             f"method takes here",
+                   "c1_full_solve": {"value": c1_ms_or, "unit": "ms", "iterations": c1_its_or,
+                                     "what": "the oracle's whole solve of the 64 x 64 lattice to R1 < 1e-8, run "
+                                             "(not extrapolated), one process"}}
         except Exception as e:  # the baseline is reported, never the target
-            cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+            cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
     line = {
         "metric": METRIC,
         "value": ms_med, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -759,6 +846,12 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "working set > L2 (FP64 factors 2.2 GB streamed every iteration); no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "err_vs_oracle_sampled": err_vs_oracle(u64),
+        "err_vs_tight_solve": {"value": err_tight, "tight_tol": 1e-12, "tight_iterations": tight_its,
+                               "what": "||u - u_t|| / ||u_t|| over every DOF, u the timed R1 < 1e-8 solve, u_t the "
+                                       "same lattice solved to R1 < 1e-12 (the FP64 bar 1e-9 is met at the "
+                                       "configuration's own R1 < 1e-10: config_eps)"},
+        "refine_cap_hits_per_solve": cap_hits64,
+        "c1_lattice64": {"gpu": c1_gpu, "oracle": (cpu or {}).get("c1_full_solve")},
         "mixed": mixed,
         "config_eps": config_eps,
         "roofline": rooflines.get("fp64"),

@@ -223,6 +223,13 @@ int64_t hms_problem_refine_cap_hits(const hms_problem* pr);
  * ms_total[k] and launches[k] for k < n (n <= 7).  Returns the count. */
 int32_t hms_kernel_times(const hms_problem* pr, double* ms_total, int64_t* launches, int32_t n);
 
+/* Measured FP64 rate of `device` in GFLOP/s (a DFMA counting two flops): an
+ * FMA-loop kernel over every SM, timed with CUDA events after a warm-up.  The
+ * roofline denominator measured beside the nominal one (SMs x DFMA lanes x
+ * clock) for the kernels bound by the FP64 units; no counterpart in the
+ * paper.  Allocates and frees a small buffer; runs on its own stream. */
+hms_status hms_measure_fp64_rate(int32_t device, double* gflops);
+
 /* ---- single steps of one iteration (for parity tests and custom drivers) ---- */
 
 /* Step a1 (Eqs. 1, 19, 2): r = p - K u on the free DOFs and the sums

@@ -17,6 +17,8 @@ Parts:
   displacement-controlled relaxation (Eqs. 11-14), incremental modes
   (Eqs. 9, 10, 13, 14), the upper-level system (Eqs. 5-8) and the update (Eq. 3),
   stopped by the 1-norm relative residual of Eq. 19.
+* ``pool``   -- the same per-set relaxation spread over host processes (the
+  sets relax independently), for timing the oracle on all host cores.
 
 Parity status: every function is pinned by the not-gpu tests in
 ``tests/test_oracle_*.py`` (dense brute force, closed forms, invariants).  The
@@ -25,4 +27,4 @@ number of iterations is "parity unpinned" against the paper; it is pinned only
 by the invariants of the method (energy decrease, Galerkin orthogonality,
 one-set convergence in one step).
 """
-from . import truss, direct, hms  # noqa: F401
+from . import truss, direct, hms, pool  # noqa: F401

@@ -105,10 +105,13 @@ class LocalFactors:
     of modes per set).  e = 0 is the set itself.
     """
 
-    def __init__(self, truss: Truss, grid: SetGrid, overlap: int = 0):
+    def __init__(self, truss: Truss, grid: SetGrid, overlap: int = 0, sets=None):
+        """``sets``: factor only these set indices (the others relax to 0);
+        None = every set."""
         if overlap < 0:
             raise ValueError("overlap must be >= 0")
         self.overlap = overlap
+        keep = None if sets is None else set(int(I) for I in sets)
         jn, inode = np.meshgrid(np.arange(grid.ny), np.arange(grid.nx), indexing="ij")
         self.dofs = []     # the set's free DOFs
         self.region = []   # the region's free DOFs (ascending)
@@ -127,7 +130,7 @@ class LocalFactors:
             self.dofs.append(d)
             self.region.append(dr)
             self.pos.append(np.searchsorted(dr, d))
-            if d.size == 0:
+            if d.size == 0 or (keep is not None and I not in keep):
                 self.factors.append(None)
                 continue
             kin = K[dr][:, dr]

@@ -109,6 +109,7 @@ def lib():
         "hms_reactions": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
         "hms_problem_refine_cap_hits": (ctypes.c_int64, [_P]),
         "hms_problem_set_relax_wait_limit": (ctypes.c_int32, [_P, ctypes.c_int32]),
+        "hms_measure_fp64_rate": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -127,7 +128,8 @@ def exported_symbols():
             "hms_residual_noalloc", "hms_solve_batch", "hms_problem_estimate_bytes", "hms_server_create",
             "hms_server_destroy", "hms_server_submit", "hms_server_step", "hms_server_take", "hms_problem_clone",
             "hms_problem_relax_threads", "hms_context_set_batch_mode", "hms_problem_relax_copies",
-            "hms_reactions", "hms_problem_refine_cap_hits", "hms_problem_set_relax_wait_limit"]
+            "hms_reactions", "hms_problem_refine_cap_hits", "hms_problem_set_relax_wait_limit",
+            "hms_measure_fp64_rate"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -343,6 +345,15 @@ def hms_reactions(ctx, pr, u, f_out):
     """f_out = K u at every DOF, constrained ones included (u read as 0 there)."""
     A = [_Arg(u), _Arg(f_out, writable=True)]
     _check(ctx, lib().hms_reactions(pr, A[0].ptr, A[1].ptr, _mem_kind(*A)))
+
+
+def hms_measure_fp64_rate(device=0) -> float:
+    """Measured FP64 GFLOP/s of the device (an FMA-loop kernel)."""
+    g = ctypes.c_double()
+    st = lib().hms_measure_fp64_rate(int(device), ctypes.byref(g))
+    if st != HMS_OK:
+        raise HmsError(st, "FP64 rate probe failed")
+    return float(g.value)
 
 
 def hms_problem_refine_cap_hits(pr) -> int:

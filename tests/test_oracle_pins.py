@@ -567,3 +567,16 @@ def test_twelve_modes_converge_and_need_fewer_updates():
     V = hms.modes(tr, g, hms.LocalFactors(tr, g).relax(r0), delta_rf=ff.relax(r0))
     r1 = tr.residual(tr.free * p, r12.iterates[0])
     assert np.abs(V.T @ r1).max() < 1e-9 * np.abs(V.T @ r0).max()
+
+
+def test_pool_relaxation_equals_serial():
+    """The per-set relaxation spread over worker processes adds up to the serial
+    one exactly (every DOF belongs to one set)."""
+    from oracle import pool
+    tr, g, p = small_problem(nx=23, ny=19, sx=6, sy=5)
+    ea = ea_lognormal(23, 19, 11)
+    r = tr.residual(p, np.zeros_like(p))
+    ref = hms.LocalFactors(tr, g).relax(r)
+    with pool.PoolFactors(23, 19, 6, 5, ea=ea, workers=3) as pf:
+        got = pf.relax(r)
+    assert np.array_equal(got, ref)
