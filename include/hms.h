@@ -97,7 +97,12 @@ typedef struct {
                                 2 = FP64, 3 = FP32 on one SM solved in 16-row steps,
                                 4 = FP32 on one SM, 5 = FP32 two-sided: top and bottom
                                 segments eliminated at once on two SMs, then the
-                                separator between them */
+                                separator between them, 6 = FP32 nested dissection of
+                                the set grid: boxes of sets cut by a middle column or
+                                row of sets, the fronts of one level of the tree
+                                factored at once, one CTA each (set grids of any
+                                width; auto takes it where no band factor fits,
+                                e.g. more than about 22 sets across) */
   int32_t relax_threads;     /* compute threads per CTA of the relaxation (Eqs. 11-13; one more
                                 warp issues its copies): 64, 128 or 256, or
                                 0 = autotuned: the first problem of a set-tile shape and

@@ -83,6 +83,9 @@ struct hms_problem {
   bool cluster_factor = false;  // FP32 factor on a cluster of 4 CTAs (with the block solve)
   bool two_sided = false;       // FP32 two-sided factor and solve on two SMs
   TwoSided ts;
+  bool nd = false;              // nested-dissection factor and solve (coarse_nd.cu)
+  NDPlanHost ndp;
+  NDPlanDev ndd;
   int* dropped = nullptr;
   unsigned long long* cstat = nullptr;  // refinement state of the upper-level solve
   double* partials = nullptr;
@@ -180,6 +183,7 @@ bool fp32(const hms_problem* pr) { return pr->precision == HMS_MIXED; }
 // The factor of Eq. 8 (after the scaled band is built) and its per-block
 // matrices, by the configured variant.
 cudaError_t launch_factor_stage(hms_problem* pr, cudaStream_t s, const IterCtl* ctl) {
+  if (pr->nd) return launch_nd_factor(s, pr->ndp, pr->ndd, (const float*)pr->lrow, pr->bw, pr->dropped, ctl);
   if (pr->two_sided) return launch_coarse_factor_2s(s, pr->n_c, pr->bw, pr->ts, pr->sband, pr->dropped, ctl);
   cudaError_t e = pr->cluster_factor
                       ? launch_coarse_factor_cl(s, pr->n_c, pr->bw, pr->lrow, pr->lcol, pr->dinv, pr->dropped, ctl)
@@ -194,6 +198,9 @@ cudaError_t launch_solve_stage(hms_problem* pr, cudaStream_t s, int q, const Ite
   // bit 0: the solve of b; bit 1: the last solve an update allows (the
   // kernels count the updates whose refinement had not converged before it)
   const int flags = (q == 0 ? 1 : 0) | (q == pr->nsolve - 1 ? 2 : 0);
+  if (pr->nd)
+    return launch_nd_solve(s, pr->n_c, pr->ndp, pr->ndd, rhs, pr->x, pr->scale, pr->a, pr->dropped, pr->cstat, flags,
+                           ctl);
   if (pr->two_sided)
     return launch_coarse_solve_2s(s, pr->n_c, pr->ts, rhs, pr->x, pr->scale, pr->a, pr->dropped, pr->cstat, flags,
                                   ctl, pr->err);
@@ -299,7 +306,7 @@ hms_status check_dev_err(hms_problem* pr) {
 // coarse_factor = 5), else solved by 64-row blocks with inverted diagonal
 // blocks when that fits in shared memory (coarse_factor = 3 keeps the 16-row
 // solve).  False if the band does not fit one CTA's shared memory.
-bool choose_coarse(hms_problem* pr, const hms_options* o, int maxsm) {
+bool choose_band(hms_problem* pr, const hms_options* o, int maxsm) {
   const LatView& lv = pr->lv;
   const int wmin = std::min(lv.sx, lv.nx - (lv.Mx - 1) * lv.sx);
   const int hmin = std::min(lv.sy, lv.ny - (lv.My - 1) * lv.sy);
@@ -359,6 +366,29 @@ bool choose_coarse(hms_problem* pr, const hms_options* o, int maxsm) {
   return true;
 }
 
+// Nested dissection over the set grid (coarse_nd.cu): the plan of fronts, if
+// every front fits the factor kernel's shared memory.
+bool choose_nd(hms_problem* pr, int maxsm) {
+  pr->coarse_fp64 = false;
+  pr->two_sided = false;
+  pr->cluster_factor = false;
+  pr->big_stages = 0;
+  pr->nd = false;
+  if (!nd_plan_build(pr->lv, &pr->ndp) || !nd_plan_smem(&pr->ndp, maxsm)) return false;
+  pr->nd = true;
+  return true;
+}
+
+// The factor of Eq. 8: coarse_factor = 6 is nested dissection; otherwise the
+// band factors of choose_band, and with coarse_factor = 0 nested dissection
+// where no band factor fits (set grids wider than one SM's band window).
+bool choose_coarse(hms_problem* pr, const hms_options* o, int maxsm) {
+  pr->nd = false;
+  if (o->coarse_factor == 6) return choose_nd(pr, maxsm);
+  if (choose_band(pr, o, maxsm)) return true;
+  return o->coarse_factor == 0 && choose_nd(pr, maxsm);
+}
+
 }  // namespace
 
 namespace hms {
@@ -397,6 +427,7 @@ hms_status hms_context_create(int32_t device, hms_context** out) {
   if (e == cudaSuccess) e = configure_coarse_assemble(maxsm);
   if (e == cudaSuccess) e = configure_coarse_solve(maxsm);
   if (e == cudaSuccess) e = configure_coarse_factor_cl(maxsm);
+  if (e == cudaSuccess) e = configure_coarse_nd(maxsm);
   if (e != cudaSuccess) {
     g_create_err = std::string("context setup: ") + cudaGetErrorString(e);
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -461,6 +492,8 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
   pr->relax_threads = src->relax_threads;
   pr->relax_chunks = src->relax_chunks;
   pr->two_sided = src->two_sided;
+  pr->nd = src->nd;
+  pr->ndp = src->ndp;
   pr->ts = TwoSided();
   pr->ts.m[0] = src->ts.m[0];
   pr->ts.m[1] = src->ts.m[1];
@@ -541,7 +574,29 @@ static cudaError_t alloc_instance(hms_problem* pr) {
   CKI(palloc(pr, &pr->b, n_c));
   CKI(palloc(pr, &pr->x, n_c));
   CKI(palloc(pr, &pr->res, n_c));
-  {
+  if (pr->nd) {
+    // the scaled band's FP32 row layout (the fronts' input), the plan and the fronts
+    float* lr;
+    CKI(palloc(pr, &lr, nband + 16));
+    pr->lrow = lr;
+    const NDPlanHost& P = pr->ndp;
+    NDPlanDev& D = pr->ndd;
+    CKI(palloc(pr, &D.nodes, P.nodes.size()));
+    CKI(palloc(pr, &D.sets, P.sets.size()));
+    CKI(palloc(pr, &D.maps, std::max<size_t>(P.maps.size(), 1)));
+    CKI(palloc(pr, &D.lvl_nodes, P.lvl_nodes.size()));
+    CKI(cudaMemcpyAsync(D.nodes, P.nodes.data(), P.nodes.size() * sizeof(NDNode), cudaMemcpyHostToDevice, s));
+    CKI(cudaMemcpyAsync(D.sets, P.sets.data(), P.sets.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (!P.maps.empty())
+      CKI(cudaMemcpyAsync(D.maps, P.maps.data(), P.maps.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CKI(cudaMemcpyAsync(D.lvl_nodes, P.lvl_nodes.data(), P.lvl_nodes.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        s));
+    CKI(palloc(pr, &D.F, P.f_elems));
+    CKI(palloc(pr, &D.W, std::max<size_t>(P.w_elems, 1)));
+    CKI(palloc(pr, &D.y, (size_t)n_c));
+    CKI(palloc(pr, &D.xc, (size_t)n_c));
+    CKI(cudaStreamSynchronize(s));  // the host vectors may change after return (clone copies)
+  } else {
     // 8 bytes per entry (FP64 factor) plus the tail read by rounded-up bulk copies
     double *lc, *lr, *di;
     CKI(palloc(pr, &lc, nband + 16));
@@ -663,7 +718,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (o->precision != HMS_FP64 && o->precision != HMS_MIXED) return fail(c, HMS_ERR_ARG, "bad precision");
   if (!(o->tol >= 0.0) || o->max_iter < 0) return fail(c, HMS_ERR_ARG, "bad tol / max_iter");
   if (o->coarse_solves < 0 || o->coarse_solves > 8) return fail(c, HMS_ERR_ARG, "coarse_solves must be in 0..8");
-  if (o->coarse_factor < 0 || o->coarse_factor > 5) return fail(c, HMS_ERR_ARG, "coarse_factor must be in 0..5");
+  if (o->coarse_factor < 0 || o->coarse_factor > 6) return fail(c, HMS_ERR_ARG, "coarse_factor must be in 0..6");
   if (o->relax_threads != 0 && o->relax_threads != 64 && o->relax_threads != 128 && o->relax_threads != 256)
     return fail(c, HMS_ERR_ARG, "relax_threads must be 0, 64, 128 or 256");
   if (o->relax_copies < 0 || o->relax_copies > 2) return fail(c, HMS_ERR_ARG, "relax_copies must be 0, 1 or 2");
@@ -711,7 +766,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   }
   if (!choose_coarse(pr, o, maxsm)) {
     delete pr;
-    return fail(c, HMS_ERR_ARG, "set grid too wide for the upper-level band factorisation");
+    return fail(c, HMS_ERR_ARG, "set grid too wide for the upper-level factorisations");
   }
   if (coarse_slots_smem(lv) > (size_t)maxsm) {
     delete pr;
@@ -1637,7 +1692,14 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
   *shared = nn + (d->ea ? 3 * nn * 8 : 0) + M * 16 + (M + 1) * 8 + fac * esz + M * NSLOTS * SLOT_SIZE * 8;
   size_t b = 4 * nn * 16 + nn * 2 * esz + M * (size_t)relax_y_stride(lv) * esz;
   b += 2 * n_c * 8 + M * NSLOTS * SLOT_SIZE * 8 + 3 * nband * 8 + 4 * n_c * 8;
-  b += 2 * (nband + 16) * 8 + (size_t)coarse_dinv_size(pr.n_c) * 8;
+  if (pr.nd) {
+    const NDPlanHost& P = pr.ndp;
+    b += (nband + 16) * 4 + P.nodes.size() * sizeof(NDNode) + P.sets.size() * 4 +
+         std::max<size_t>(P.maps.size(), 1) * 4 + P.lvl_nodes.size() * 4 + P.f_elems * 4 +
+         std::max<size_t>(P.w_elems, 1) * 4 + 2 * n_c * 4;
+  } else {
+    b += 2 * (nband + 16) * 8 + (size_t)coarse_dinv_size(pr.n_c) * 8;
+  }
   if (pr.big_stages > 0) b += coarse_xinv_elems(pr.n_c, pr.bw) * 4;
   if (pr.two_sided)
     for (int k = 0; k < 2; ++k) {

@@ -1,0 +1,709 @@
+// K4 by nested dissection: the upper-level solve of Eq. 8 with its work
+// spread over the SMs, for set grids of any width.
+//
+// The band factorisations (coarse_solve.cu) are one dependency chain down the
+// band: n / 16 block steps on one or two SMs, and a band window that must fit
+// in shared memory (set grids up to about 22 sets across).  Here the unknowns
+// are ordered by nested dissection of the set grid instead.  A box of sets is
+// cut by its middle column of sets (or middle row, if it is taller than wide);
+// the two halves share no bar (K_aa couples a set only to its eight
+// neighbours), so they are eliminated independently and the separator last.
+// The recursion stops at boxes of at most 2 x 2 sets.  Every tree node is a
+// dense "front" over its own sets S (the separator, or the whole leaf box)
+// and its boundary B: the sets around its box, which all lie on ancestor
+// separators.  Fronts of one tree level are independent, one CTA each:
+//
+//   factor, leaves first: F = [A_SS A_SB; A_BS 0] + (children's update
+//     matrices, added at their sets' places), then the partial Cholesky
+//     L_SS L_SS^T = F_SS, L_BS = F_BS L_SS^-T, U = F_BB - L_BS L_BS^T in 32-
+//     column panels; U stays in the front for the parent.  The diagonal
+//     32 x 32 blocks of L_SS are stored inverted.
+//   forward solve, leaves first: f = [r_S; 0] + children's update vectors,
+//     y_S = L_SS^-1 f_S block by block, w = f_B - L_BS y_S for the parent.
+//   back substitution, root first: x_S = L_SS^-T (y_S - L_BS^T x_B) with x_B
+//     from the ancestors.
+//
+// The matrix is the Jacobi-scaled one the band path factors (its FP32 row
+// layout, written by k_coarse_scale_band), so modes dropped in FP64 are unit
+// rows already; the factor and solves run in FP32 and the FP64 refinement of
+// Eq. 8 (k_coarse_residual) is the same as for the band factors.  Every sum
+// runs in a fixed order (children in order, rows in order), so results are
+// the same on every run.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "coarse_common.cuh"
+#include "hms_internal.cuh"
+
+namespace hms {
+namespace {
+
+constexpr int NDT = 512;          // threads per front CTA
+constexpr int NDW = NDT / 32;     // warps
+constexpr int PB = 32;            // panel width (pivots per step)
+constexpr float ND_TAU = 1e-6f;   // FP32 pivot below which a mode is dropped (as the band factors)
+
+__device__ inline bool nd_done(const IterCtl* ctl) { return ctl && *(volatile const int*)&ctl->done; }
+
+// global unknown of front position p: set st[p / 9], mode p % 9
+__device__ inline int nd_glob(const int* st, int p) { return st[p / NMODES] * NMODES + p % NMODES; }
+
+// entry (gi, gj) of the scaled matrix from its FP32 row-layout band
+__device__ inline float nd_a(const float* __restrict__ frow, int bw, int gi, int gj) {
+  if (gi < gj) {
+    const int t = gi;
+    gi = gj;
+    gj = t;
+  }
+  const int d = gi - gj;
+  return d <= bw ? frow[(size_t)gi * (bw + 1) + d] : 0.f;
+}
+
+__device__ inline float warp_sum_f(float v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+// ---------------------------------------------------------------- factor
+// Cholesky of a kb x kb diagonal block held by one warp (lane = row, a[c] =
+// entry (lane, c); rows >= kb zero).  A pivot at or below ND_TAU drops its
+// mode: unit diagonal, zero row and column.  Fully unrolled: every index is a
+// compile-time constant, so the block stays in registers.
+__device__ __forceinline__ unsigned nd_diag_factor(float (&a)[PB], int kb, int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
+  unsigned dm = 0u;
+#pragma unroll
+  for (int c = 0; c < PB; ++c) {
+    if (c < kb) {
+      const float piv = __shfl_sync(FULL, a[c], c);
+      const bool drop = !(piv > ND_TAU);
+      const float inv = drop ? 0.f : rsqrtf(piv);
+      const float d = drop ? 1.f : piv * inv;
+      if (lane == c) a[c] = d;
+      else if (lane > c) a[c] = a[c] * inv;
+      if (drop) {
+        dm |= 1u << c;
+#pragma unroll
+        for (int j = 0; j < c; ++j)
+          if (lane == c) a[j] = 0.f;
+      }
+      const float lc = a[c];
+#pragma unroll
+      for (int j = c + 1; j < PB; ++j) {
+        const float ljc = __shfl_sync(FULL, lc, j);
+        if (lane > c) a[j] = fmaf(-lc, ljc, a[j]);
+      }
+    }
+  }
+  return dm;
+}
+
+// Inverse of a lower-triangular kb x kb block held by one warp (lane = row r,
+// a[c] = L[r][c]): by columns, lane j computing x[r] = (inverse)[r][j].
+__device__ __forceinline__ void nd_tri_invert(const float (&a)[PB], float (&x)[PB], int kb, int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
+#pragma unroll
+  for (int r = 0; r < PB; ++r) {
+    if (r < kb) {
+      float sacc = (r == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int t = 0; t < r; ++t) sacc = fmaf(-__shfl_sync(FULL, a[t], r), x[t], sacc);
+      const float lrr = __shfl_sync(FULL, a[r], r);
+      x[r] = (r >= lane) ? sacc / lrr : 0.f;
+    } else {
+      x[r] = 0.f;
+    }
+  }
+}
+
+// The front of one tree node, factored where it is stored: SM = true keeps it
+// in shared memory (packed lower rows, row i from i(i+1)/2) and writes it out
+// at the end; SM = false works on the global copy (row-major, nf x nf) with
+// the panel staged in shared memory.  Per PB-column panel: warp 0 factors the
+// diagonal block and inverts it in registers (the inverse replaces the block:
+// the solves multiply by it); every row below is multiplied by the inverse's
+// transpose (one warp per row); the trailing lower triangle takes the rank-PB
+// update.
+template <bool SM>
+__device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* __restrict__ nodes,
+                                               const int* __restrict__ sets, const int* __restrict__ maps,
+                                               const float* __restrict__ frow, int bw, float* __restrict__ F,
+                                               int* __restrict__ dropped, float* sm, int* gidx, int* cpos,
+                                               float (&Dinv)[PB][PB + 1], unsigned& dmask) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nS = NMODES * nd.ns, nf = NMODES * (nd.ns + nd.nb);
+  float* fg = F + nd.f_off;
+  const int* st = sets + nd.s_off;
+  auto at = [&](int i, int j) -> float& {
+    if constexpr (SM) return sm[(size_t)i * (i + 1) / 2 + j];
+    else return fg[(size_t)i * nf + j];
+  };
+  // the global unknown of every front position
+  for (int p = tid; p < nf; p += NDT) gidx[p] = nd_glob(st, p);
+  __syncthreads();
+
+  // ---- assemble: original entries of the S columns, zero B x B (NU loads in flight per lane) ----
+  constexpr int NU = 4;
+  for (int p = warp; p < nf; p += NDW) {
+    const int gp = gidx[p];
+    for (int q0 = lane; q0 <= p; q0 += 32 * NU) {
+      float v[NU];
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        const int q = q0 + 32 * u;
+        v[u] = (q <= p && q < nS) ? nd_a(frow, bw, gp, gidx[q]) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        const int q = q0 + 32 * u;
+        if (q <= p) at(p, q) = v[u];
+      }
+    }
+  }
+  __syncthreads();
+  // ---- extend-add of the children's update matrices (one child after the other) ----
+  for (int c = 0; c < nd.nchild; ++c) {
+    const NDNode ch = nodes[nd.child[c]];
+    const int nSc = NMODES * ch.ns, nbc = NMODES * ch.nb, nfc = nSc + nbc;
+    const float* U = F + ch.f_off + (size_t)nSc * nfc + nSc;
+    const int* mp = maps + nd.map_off[c];
+    for (int k = tid; k < nbc; k += NDT) cpos[k] = NMODES * mp[k / NMODES] + k % NMODES;
+    __syncthreads();
+    for (int k = warp; k < nbc; k += NDW) {
+      const int pk = cpos[k];
+      const float* Uk = U + (size_t)k * nfc;
+      for (int l0 = lane; l0 <= k; l0 += 32 * NU) {
+        float v[NU];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const int l = l0 + 32 * u;
+          v[u] = l <= k ? Uk[l] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const int l = l0 + 32 * u;
+          if (l <= k) {
+            const int pl = cpos[l];
+            at(pk > pl ? pk : pl, pk > pl ? pl : pk) += v[u];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- partial Cholesky of the first nS columns, PB columns at a time ----
+  float* panel = sm;  // global mode: rows below the diagonal block, [nf - k0 - kb][PB + 1]
+  for (int k0 = 0; k0 < nS; k0 += PB) {
+    const int kb = min(PB, nS - k0);
+    // (a) diagonal block: Cholesky and its inverse in warp 0's registers; the
+    // inverse is stored in the block's place (the solves multiply by it)
+    if (warp == 0) {
+      float a[PB], x[PB];
+#pragma unroll
+      for (int c = 0; c < PB; ++c) a[c] = (lane < kb && c <= lane) ? at(k0 + lane, k0 + c) : 0.f;
+      const unsigned dm = nd_diag_factor(a, kb, lane);
+      nd_tri_invert(a, x, kb, lane);
+#pragma unroll
+      for (int r = 0; r < PB; ++r) Dinv[r][lane] = x[r];
+      __syncwarp();
+      for (int r = 0; r < kb; ++r)
+        if (lane <= r) at(k0 + r, k0 + lane) = Dinv[r][lane];
+      // a dropped mode's earlier L row is zeroed and its flag raised
+      for (int c = 0; c < kb; ++c)
+        if ((dm >> c) & 1u) {
+          for (int j = lane; j < k0; j += 32) at(k0 + c, j) = 0.f;
+          if (lane == 0) dropped[gidx[k0 + c]] = 1;
+        }
+      if (lane == 0) dmask = dm;
+    }
+    __syncthreads();
+    // (b) the panel below: L[i][blk] = F[i][blk] Dinv^T, one warp per row (lane = column)
+    const unsigned dmk = dmask;
+    const int r0 = k0 + kb, m = nf - r0;
+    for (int ii = warp; ii < m; ii += NDW) {
+      const float fv = lane < kb ? at(r0 + ii, k0 + lane) : 0.f;
+      float sacc = 0.f;
+#pragma unroll
+      for (int u = 0; u < PB; ++u) sacc = fmaf(__shfl_sync(0xffffffffu, fv, u), Dinv[lane][u], sacc);
+      if ((dmk >> lane) & 1u) sacc = 0.f;
+      if (lane < kb) {
+        at(r0 + ii, k0 + lane) = sacc;
+        if constexpr (!SM) panel[(size_t)ii * (PB + 1) + lane] = sacc;
+      }
+    }
+    __syncthreads();
+    // (c) trailing update of the lower triangle below the block, 4 x 4 tiles
+    const int T = (m + 3) / 4;
+    const int ntile = T * (T + 1) / 2;
+    for (int t = tid; t < ntile; t += NDT) {
+      int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+      while (ti * (ti + 1) / 2 > t) --ti;
+      while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+      const int tj = t - ti * (ti + 1) / 2;
+      float acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+      for (int u = 0; u < kb; ++u) {
+        float pa[4], pb[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int ia = 4 * ti + a, jb = 4 * tj + a;
+          if constexpr (SM) {
+            pa[a] = ia < m ? at(r0 + ia, k0 + u) : 0.f;
+            pb[a] = jb < m ? at(r0 + jb, k0 + u) : 0.f;
+          } else {
+            pa[a] = ia < m ? panel[(size_t)ia * (PB + 1) + u] : 0.f;
+            pb[a] = jb < m ? panel[(size_t)jb * (PB + 1) + u] : 0.f;
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = 4 * ti + a;
+        if (i >= m) break;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int j = 4 * tj + b;
+          if (j <= i) at(r0 + i, r0 + j) -= acc[a][b];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if constexpr (SM) {
+    // the factored front out to its global copy (the solves and the parent read it there)
+    for (int p = warp; p < nf; p += NDW)
+      for (int q = lane; q <= p; q += 32) fg[(size_t)p * nf + q] = sm[(size_t)p * (p + 1) / 2 + q];
+  }
+}
+
+// One CTA per front of a tree level.  cap = the launch's dynamic shared
+// memory in floats: a front whose packed lower triangle fits is factored in
+// shared memory.
+__global__ void __launch_bounds__(NDT) k_nd_factor(const NDNode* __restrict__ nodes, const int* __restrict__ lvl,
+                                                   int lbeg, const int* __restrict__ sets,
+                                                   const int* __restrict__ maps, const float* __restrict__ frow,
+                                                   int bw, float* __restrict__ F, int* __restrict__ dropped,
+                                                   long long cap, const IterCtl* ctl) {
+  if (nd_done(ctl)) return;
+  extern __shared__ __align__(16) float ndsm[];
+  __shared__ float Dinv[PB][PB + 1];
+  __shared__ unsigned dmask;
+  const NDNode nd = nodes[lvl[lbeg + blockIdx.x]];
+  const long long nf = NMODES * (long long)(nd.ns + nd.nb);
+  // the last 2 nf floats of the region hold the front's unknown indices and a child's positions
+  int* gidx = reinterpret_cast<int*>(ndsm + (cap - 2 * nf));
+  int* cpos = gidx + nf;
+  if (nf * (nf + 1) / 2 + 2 * nf <= cap)
+    nd_factor_body<true>(nd, nodes, sets, maps, frow, bw, F, dropped, ndsm, gidx, cpos, Dinv, dmask);
+  else
+    nd_factor_body<false>(nd, nodes, sets, maps, frow, bw, F, dropped, ndsm, gidx, cpos, Dinv, dmask);
+}
+
+// ---------------------------------------------------------------- solves
+// Begins a solve: q = 0 takes max |b| (non-dropped rows) for the refinement
+// test and clears the converged flag; later solves decide whether refinement
+// has converged (cstat[2] = 1: the level kernels and residuals return at once).
+// flags: bit 0 = the solve of b, bit 1 = the last solve the update allows.
+__global__ void __launch_bounds__(1024) k_nd_solve_begin(int n, const double* __restrict__ rhs,
+                                                         const int* __restrict__ dropped, unsigned long long* cstat,
+                                                         int flags, const IterCtl* ctl) {
+  if (nd_done(ctl)) return;
+  __shared__ double red[32];
+  const int tid = threadIdx.x;
+  if (flags & 1) {
+    double bm = 0.0;
+    for (int i = tid; i < n; i += blockDim.x)
+      if (!dropped[i]) bm = fmax(bm, fabs(rhs[i]));
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, m));
+    if ((tid & 31) == 0) red[tid >> 5] = bm;
+    __syncthreads();
+    if (tid == 0) {
+      double v = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v = fmax(v, red[k]);
+      cstat[0] = (unsigned long long)__double_as_longlong(v);
+      cstat[2] = 0ull;
+      cstat[1] = 0ull;
+    }
+    return;
+  }
+  if (tid == 0) {
+    const double bmax = __longlong_as_double((long long)cstat[0]);
+    const double rmax = __longlong_as_double((long long)cstat[1]);
+    const bool skip = (cstat[2] != 0ull) || !(rmax > 1e-14 * bmax);
+    if (skip) cstat[2] = 1ull;
+    else if (flags & 2) atomicAdd(&cstat[3], 1ull);  // refinement used every solve it may
+    cstat[1] = 0ull;  // the next residual accumulates its max here
+  }
+}
+
+constexpr int RU = 4;     // rows per warp in flight in the forward solve's row products
+constexpr int NDQ = 12;   // columns per lane and pass in the back substitution's first product
+
+// Shared memory of a solve CTA (floats): the front's vector (nf), the warps'
+// partial sums (NDW x nS) and the front's unknown indices (nf ints).  The
+// factor is read where it lies (global, L2-resident): staging it first cost
+// more than the reads themselves, the fronts being small.
+__device__ __host__ inline long long nd_solve_need(long long nS, long long nf) { return nf + NDW * nS + nf; }
+
+__global__ void __launch_bounds__(NDT) k_nd_forward(const NDNode* __restrict__ nodes, const int* __restrict__ lvl,
+                                                    int lbeg, const int* __restrict__ sets,
+                                                    const int* __restrict__ maps, const float* __restrict__ F,
+                                                    float* __restrict__ W, const double* __restrict__ rhs,
+                                                    const int* __restrict__ dropped, float* __restrict__ y,
+                                                    long long cap, const unsigned long long* cstat,
+                                                    const IterCtl* ctl) {
+  if (nd_done(ctl) || *(volatile const unsigned long long*)&cstat[2]) return;
+  extern __shared__ __align__(16) float ndsm[];
+  __shared__ float yb[PB];
+  const NDNode nd = nodes[lvl[lbeg + blockIdx.x]];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nS = NMODES * nd.ns, nf = NMODES * (nd.ns + nd.nb);
+  const float* f = F + nd.f_off;
+  const int* st = sets + nd.s_off;
+  float* fv = ndsm;
+  int* gidx = reinterpret_cast<int*>(ndsm + (cap - nf));
+  const float* Lp = f;
+  const int ld = nf;
+  for (int p = tid; p < nf; p += NDT) gidx[p] = nd_glob(st, p);
+  __syncthreads();
+  for (int p = tid; p < nf; p += NDT) {
+    float v = 0.f;
+    if (p < nS) {
+      const int g = gidx[p];
+      v = dropped[g] ? 0.f : (float)rhs[g];
+    }
+    fv[p] = v;
+  }
+  __syncthreads();
+  for (int c = 0; c < nd.nchild; ++c) {
+    const NDNode ch = nodes[nd.child[c]];
+    const int nbc = NMODES * ch.nb;
+    const int* mp = maps + nd.map_off[c];
+    for (int k = tid; k < nbc; k += NDT) fv[NMODES * mp[k / NMODES] + k % NMODES] += W[ch.w_off + k];
+    __syncthreads();
+  }
+  for (int k0 = 0; k0 < nS; k0 += PB) {
+    const int kb = min(PB, nS - k0);
+    const float fl = lane < kb ? fv[k0 + lane] : 0.f;
+    // y_blk = Dinv f_blk: two rows per warp, lane = column
+    for (int t = warp; t < kb; t += NDW) {
+      const float v = lane <= t ? Lp[(size_t)(k0 + t) * ld + k0 + lane] * fl : 0.f;
+      const float sum = warp_sum_f(v);
+      if (lane == 0) yb[t] = sum;
+    }
+    __syncthreads();
+    const float yl = lane < kb ? yb[lane] : 0.f;
+    if (tid < kb) fv[k0 + tid] = yb[tid];
+    // rows below: f_i -= L[i][blk] y_blk, RU rows per warp at once
+    for (int i0 = k0 + kb + RU * warp; i0 < nf; i0 += RU * NDW) {
+      float v[RU];
+#pragma unroll
+      for (int q = 0; q < RU; ++q) {
+        const int i = i0 + q;
+        v[q] = (i < nf && lane < kb) ? Lp[(size_t)i * ld + k0 + lane] * yl : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < RU; ++q) v[q] = warp_sum_f(v[q]);
+      if (lane < RU && i0 + lane < nf) {
+        float mine = v[0];
+#pragma unroll
+        for (int q = 1; q < RU; ++q) mine = lane == q ? v[q] : mine;
+        fv[i0 + lane] -= mine;
+      }
+    }
+    __syncthreads();
+  }
+  for (int p = tid; p < nf; p += NDT) {
+    if (p < nS) y[gidx[p]] = fv[p];
+    else W[nd.w_off + (p - nS)] = fv[p];
+  }
+}
+
+__global__ void __launch_bounds__(NDT) k_nd_backward(const NDNode* __restrict__ nodes, const int* __restrict__ lvl,
+                                                     int lbeg, const int* __restrict__ sets,
+                                                     const float* __restrict__ F, const float* __restrict__ y,
+                                                     float* __restrict__ xc, const int* __restrict__ dropped,
+                                                     double* __restrict__ x, const double* __restrict__ scale,
+                                                     double* __restrict__ a_out, long long cap,
+                                                     const unsigned long long* cstat, const IterCtl* ctl) {
+  if (nd_done(ctl) || *(volatile const unsigned long long*)&cstat[2]) return;
+  extern __shared__ __align__(16) float ndsm[];
+  __shared__ float xb[PB];
+  const NDNode nd = nodes[lvl[lbeg + blockIdx.x]];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nS = NMODES * nd.ns, nB = NMODES * nd.nb, nf = nS + nB;
+  const float* f = F + nd.f_off;
+  const int* st = sets + nd.s_off;
+  float* tv = ndsm;                 // nS
+  float* xB = ndsm + nS;            // nB: the ancestors' corrections
+  float* part = ndsm + nf;          // NDW x nS partial sums
+  int* gidx = reinterpret_cast<int*>(ndsm + (cap - nf));
+  const float* Lp = f;
+  const int ld = nf;
+  for (int p = tid; p < nf; p += NDT) gidx[p] = nd_glob(st, p);
+  __syncthreads();
+  for (int k = tid; k < nB; k += NDT) xB[k] = xc[gidx[nS + k]];
+  __syncthreads();
+  // t = y_S - L_BS^T x_B: warp w sums the rows k = w, w + NDW, ... (lane: columns
+  // lane + 32 q), then the warps' partial sums are added in warp order
+  for (int jb = 0; nB > 0 && jb < nS; jb += 32 * NDQ) {
+    float acc[NDQ];
+#pragma unroll
+    for (int q = 0; q < NDQ; ++q) acc[q] = 0.f;
+    for (int k = warp; k < nB; k += NDW) {
+      const float xk = xB[k];
+      const float* row = Lp + (size_t)(nS + k) * ld + jb;
+#pragma unroll
+      for (int q = 0; q < NDQ; ++q) {
+        const int j = lane + 32 * q;
+        if (jb + j < nS) acc[q] = fmaf(row[j], xk, acc[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NDQ; ++q) {
+      const int j = jb + lane + 32 * q;
+      if (j < nS) part[warp * nS + j] = acc[q];
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j < nS; j += NDT) {
+    float sacc = y[gidx[j]];
+    if (nB > 0)
+      for (int w = 0; w < NDW; ++w) sacc -= part[w * nS + j];
+    tv[j] = sacc;
+  }
+  __syncthreads();
+  const int nblk = (nS + PB - 1) / PB;
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int k0 = b * PB, kb = min(PB, nS - k0);
+    if (warp == 0) {
+      // x_blk = Dinv^T t_blk: lane c sums rows r >= c of column c
+      float sacc = 0.f;
+#pragma unroll 8
+      for (int r = 0; r < kb; ++r) {
+        const float dv = (lane <= r) ? Lp[(size_t)(k0 + r) * ld + k0 + lane] : 0.f;
+        sacc = fmaf(dv, tv[k0 + r], sacc);
+      }
+      if (lane < kb) xb[lane] = sacc;
+    }
+    __syncthreads();
+    if (tid < kb) tv[k0 + tid] = xb[tid];
+    // earlier columns: t_j -= sum_r L[k0 + r][j] x_r
+    for (int j = tid; j < k0; j += NDT) {
+      float sacc = tv[j];
+#pragma unroll 8
+      for (int r = 0; r < kb; ++r) sacc = fmaf(-Lp[(size_t)(k0 + r) * ld + j], xb[r], sacc);
+      tv[j] = sacc;
+    }
+    __syncthreads();
+  }
+  for (int j = tid; j < nS; j += NDT) {
+    const int g = gidx[j];
+    const float v = dropped[g] ? 0.f : tv[j];
+    xc[g] = v;
+    const double xi = dropped[g] ? 0.0 : x[g] + (double)v;
+    x[g] = xi;
+    a_out[g] = scale[g] * xi;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host plan
+namespace {
+struct HNode {
+  int x0, y0, w, h;
+  std::vector<int> S, B;
+  int child[2] = {-1, -1};
+  int nchild = 0;
+  int height = 0;
+};
+
+int nd_build(std::vector<HNode>& out, int Mx, int My, int x0, int y0, int w, int h) {
+  HNode nd;
+  nd.x0 = x0, nd.y0 = y0, nd.w = w, nd.h = h;
+  int kids[2] = {-1, -1}, nk = 0;
+  if (w <= 2 && h <= 2) {
+    for (int y = y0; y < y0 + h; ++y)
+      for (int x = x0; x < x0 + w; ++x) nd.S.push_back(y * Mx + x);
+  } else if (w >= h) {
+    const int c = x0 + w / 2;
+    for (int y = y0; y < y0 + h; ++y) nd.S.push_back(y * Mx + c);
+    if (c > x0) kids[nk++] = nd_build(out, Mx, My, x0, y0, c - x0, h);
+    if (x0 + w - c - 1 > 0) kids[nk++] = nd_build(out, Mx, My, c + 1, y0, x0 + w - c - 1, h);
+  } else {
+    const int r = y0 + h / 2;
+    for (int x = x0; x < x0 + w; ++x) nd.S.push_back(r * Mx + x);
+    if (r > y0) kids[nk++] = nd_build(out, Mx, My, x0, y0, w, r - y0);
+    if (y0 + h - r - 1 > 0) kids[nk++] = nd_build(out, Mx, My, x0, r + 1, w, y0 + h - r - 1);
+  }
+  // the ring of sets around the box, inside the grid (all on ancestor separators)
+  for (int y = y0 - 1; y <= y0 + h; ++y)
+    for (int x = x0 - 1; x <= x0 + w; ++x) {
+      if (x < 0 || y < 0 || x >= Mx || y >= My) continue;
+      if (x >= x0 && x < x0 + w && y >= y0 && y < y0 + h) continue;
+      nd.B.push_back(y * Mx + x);
+    }
+  std::sort(nd.B.begin(), nd.B.end());
+  nd.nchild = nk;
+  for (int k = 0; k < nk; ++k) {
+    nd.child[k] = kids[k];
+    nd.height = std::max(nd.height, out[kids[k]].height + 1);
+  }
+  out.push_back(nd);
+  return (int)out.size() - 1;
+}
+}  // namespace
+
+bool nd_plan_build(const LatView& lv, NDPlanHost* P) {
+  std::vector<HNode> hn;
+  hn.reserve(4 * (size_t)lv.M + 8);
+  nd_build(hn, lv.Mx, lv.My, 0, 0, lv.Mx, lv.My);
+  const int nn = (int)hn.size();
+  int H = 0;
+  for (const HNode& h : hn) H = std::max(H, h.height);
+  P->nodes.assign(nn, NDNode{});
+  P->sets.clear();
+  P->maps.clear();
+  P->level_begin.assign(H + 2, 0);
+  P->lvl_nodes.clear();
+  P->f_elems = 0;
+  P->w_elems = 0;
+  P->max_front = 0;
+  P->max_level_nodes = 0;
+  // sets of every node, S then B
+  for (int k = 0; k < nn; ++k) {
+    NDNode& d = P->nodes[k];
+    d.ns = (int)hn[k].S.size();
+    d.nb = (int)hn[k].B.size();
+    d.s_off = (int)P->sets.size();
+    P->sets.insert(P->sets.end(), hn[k].S.begin(), hn[k].S.end());
+    P->sets.insert(P->sets.end(), hn[k].B.begin(), hn[k].B.end());
+    const long long nf = (long long)NMODES * (d.ns + d.nb);
+    d.f_off = (long long)P->f_elems;
+    P->f_elems += (size_t)(nf * nf);
+    d.w_off = (long long)P->w_elems;
+    P->w_elems += (size_t)NMODES * d.nb;
+    P->max_front = std::max(P->max_front, (int)nf);
+    d.nchild = hn[k].nchild;
+  }
+  // children's boundary sets -> their place in the parent's front
+  for (int k = 0; k < nn; ++k) {
+    NDNode& d = P->nodes[k];
+    const HNode& h = hn[k];
+    for (int c = 0; c < h.nchild; ++c) {
+      const int ch = h.child[c];
+      d.child[c] = ch;
+      d.map_off[c] = (int)P->maps.size();
+      for (int J : hn[ch].B) {
+        int pos = -1;
+        for (size_t q = 0; q < h.S.size() && pos < 0; ++q)
+          if (h.S[q] == J) pos = (int)q;
+        for (size_t q = 0; q < h.B.size() && pos < 0; ++q)
+          if (h.B[q] == J) pos = (int)(h.S.size() + q);
+        if (pos < 0) return false;  // not reachable for boxes cut by full separators
+        P->maps.push_back(pos);
+      }
+    }
+  }
+  // nodes by height: leaves first
+  std::vector<std::vector<int>> byh(H + 1);
+  for (int k = 0; k < nn; ++k) byh[hn[k].height].push_back(k);
+  for (int h = 0; h <= H; ++h) {
+    P->level_begin[h] = (int)P->lvl_nodes.size();
+    P->lvl_nodes.insert(P->lvl_nodes.end(), byh[h].begin(), byh[h].end());
+    P->max_level_nodes = std::max(P->max_level_nodes, (int)byh[h].size());
+  }
+  P->level_begin[H + 1] = (int)P->lvl_nodes.size();
+  P->nlevels = H + 1;
+  return true;
+}
+
+// Shared memory of the factor launch of a level: per front its packed lower
+// triangle where that fits in `cap` floats, else the global path's panel.
+static long long nd_factor_need(long long nf, long long cap) {
+  const long long packed = nf * (nf + 1) / 2 + 2 * nf;
+  return packed <= cap ? packed : nf * (PB + 1) + 2 * nf;
+}
+
+bool nd_plan_smem(NDPlanHost* P, int max_smem) {
+  // dynamic shared memory of the ND kernels: what the device offers beside
+  // their static shared memory (a few KB)
+  const long long cap = ((long long)max_smem - 8 * 1024) / (long long)sizeof(float);
+  P->level_smem_factor.assign(P->nlevels, 0);
+  P->level_smem_solve.assign(P->nlevels, 0);
+  for (int h = 0; h < P->nlevels; ++h) {
+    long long nfac = 0, nsol = 0;
+    for (int k = P->level_begin[h]; k < P->level_begin[h + 1]; ++k) {
+      const NDNode& d = P->nodes[P->lvl_nodes[k]];
+      const long long nS = (long long)NMODES * d.ns, nf = (long long)NMODES * (d.ns + d.nb);
+      const long long fneed = nd_factor_need(nf, cap);
+      const long long sneed = nd_solve_need(nS, nf);
+      if (fneed > cap || sneed > cap) return false;
+      nfac = std::max(nfac, fneed);
+      nsol = std::max(nsol, sneed);
+    }
+    P->level_smem_factor[h] = (size_t)nfac * sizeof(float);
+    P->level_smem_solve[h] = (size_t)nsol * sizeof(float);
+  }
+  return true;
+}
+
+cudaError_t launch_nd_factor(cudaStream_t s, const NDPlanHost& P, const NDPlanDev& D, const float* frow, int bw,
+                             int* dropped, const IterCtl* ctl) {
+  for (int h = 0; h < P.nlevels; ++h) {
+    const int b = P.level_begin[h], n = P.level_begin[h + 1] - b;
+    if (n <= 0) continue;
+    const size_t smem = P.level_smem_factor[h];
+    k_nd_factor<<<n, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.maps, frow, bw, D.F, dropped,
+                                     (long long)(smem / sizeof(float)), ctl);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_nd_solve(cudaStream_t s, int n, const NDPlanHost& P, const NDPlanDev& D, const double* rhs,
+                            double* x, const double* scale, double* a_out, const int* dropped,
+                            unsigned long long* cstat, int flags, const IterCtl* ctl) {
+  k_nd_solve_begin<<<1, 1024, 0, s>>>(n, rhs, dropped, cstat, flags, ctl);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int h = 0; h < P.nlevels; ++h) {
+    const int b = P.level_begin[h], m = P.level_begin[h + 1] - b;
+    if (m <= 0) continue;
+    const size_t smem = P.level_smem_solve[h];
+    k_nd_forward<<<m, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.maps, D.F, D.W, rhs, dropped, D.y,
+                                      (long long)(smem / sizeof(float)), cstat, ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  for (int h = P.nlevels - 1; h >= 0; --h) {
+    const int b = P.level_begin[h], m = P.level_begin[h + 1] - b;
+    if (m <= 0) continue;
+    const size_t smem = P.level_smem_solve[h];
+    k_nd_backward<<<m, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.F, D.y, D.xc, dropped, x, scale, a_out,
+                                       (long long)(smem / sizeof(float)), cstat, ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t configure_coarse_nd(int max_smem) {
+  cudaError_t e = set_max_dynamic_smem(k_nd_factor, max_smem);
+  if (e != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_nd_forward, max_smem)) != cudaSuccess) return e;
+  return set_max_dynamic_smem(k_nd_backward, max_smem);
+}
+
+}  // namespace hms

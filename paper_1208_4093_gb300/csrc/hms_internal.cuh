@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace hms {
 
 constexpr int NMODES = 9;
@@ -304,6 +306,38 @@ cudaError_t configure_setup(int max_smem);
 cudaError_t configure_relax(int max_smem);
 cudaError_t configure_coarse_assemble(int max_smem);
 cudaError_t configure_coarse_solve(int max_smem);
+// coarse_nd.cu: nested-dissection factor and solve of Eq. 8 over the set grid.
+// A tree node (front): its own sets S and boundary sets B (lists of set
+// indices at s_off: S then B), up to two children whose boundary sets sit at
+// the front positions maps[map_off[c] ...] (in sets, S first), its dense
+// front F (9(ns+nb) squared floats at f_off) and its update vector W
+// (9 nb floats at w_off).
+struct NDNode {
+  int ns, nb, s_off, nchild;
+  int child[2];
+  int map_off[2];
+  long long f_off, w_off;
+};
+struct NDPlanHost {
+  std::vector<NDNode> nodes;
+  std::vector<int> sets, maps, lvl_nodes, level_begin;  // nodes by height: leaves first
+  std::vector<size_t> level_smem_factor, level_smem_solve;  // dynamic shared memory per level's launches
+  int nlevels = 0, max_front = 0, max_level_nodes = 0;
+  size_t f_elems = 0, w_elems = 0;
+};
+struct NDPlanDev {
+  NDNode* nodes = nullptr;
+  int *sets = nullptr, *maps = nullptr, *lvl_nodes = nullptr;
+  float *F = nullptr, *W = nullptr, *y = nullptr, *xc = nullptr;
+};
+bool nd_plan_build(const LatView& lv, NDPlanHost* P);
+bool nd_plan_smem(NDPlanHost* P, int max_smem);  // false if a front is too large
+cudaError_t configure_coarse_nd(int max_smem);
+cudaError_t launch_nd_factor(cudaStream_t s, const NDPlanHost& P, const NDPlanDev& D, const float* frow, int bw,
+                             int* dropped, const IterCtl* ctl);
+cudaError_t launch_nd_solve(cudaStream_t s, int n, const NDPlanHost& P, const NDPlanDev& D, const double* rhs,
+                            double* x, const double* scale, double* a_out, const int* dropped,
+                            unsigned long long* cstat, int flags, const IterCtl* ctl);
 // coarse_factor_cluster.cu
 size_t coarse_factor_cl_smem_bytes(int n, int bw);
 cudaError_t configure_coarse_factor_cl(int max_smem);

@@ -1,0 +1,136 @@
+"""The nested-dissection factor of Eq. 8 (coarse_factor = 6, and the automatic
+choice for set grids too wide for a band factor) against the oracle.
+
+The oracle's coarse solve (``hms.coarse_solve``: Jacobi-scaled Cholesky in
+set order, dropping degenerate modes) and its direct solve of Eq. 1 (O1) are
+the references: the elimination order differs (nested dissection of the set
+grid), but the update V a and the Galerkin condition (Eq. 5) are unique, and
+whole solves must reach u* within the FP64 bar.
+"""
+import numpy as np
+import pytest
+
+from oracle import direct, hms, truss
+from workloads import ea_lognormal, loads
+
+pytestmark = pytest.mark.gpu
+
+# name, nx, ny, sx, sy, lognormal EA
+CASES = [
+    ("grid4x4", 64, 64, 16, 16, False),
+    ("ragged_lognormal", 37, 29, 8, 6, True),
+    ("widest_sets", 67, 24, 64, 12, True),
+    ("tall_grid", 33, 90, 7, 6, True),
+    ("single_set", 12, 10, 12, 10, True),
+    ("one_row_sets", 16, 9, 8, 1, False),
+    ("grid9x11", 50, 70, 6, 7, False),
+]
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    n = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (n if n > 0 else 1.0)
+
+
+def make(ctx, nx, ny, sx, sy, ln, **kw):
+    from paper_1208_4093_gb300 import capi
+    ea = ea_lognormal(nx, ny, 23) if ln else None
+    tr = truss.Truss(nx, ny, ea)
+    g = hms.SetGrid(nx, ny, sx, sy)
+    p = tr.free * loads(nx, ny, 6).reshape(-1)
+    pr = capi.hms_problem_create(ctx, nx, ny, sx, sy, ea=ea, **kw)
+    return tr, g, p, pr
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+def test_nd_coarse_solve_matches_oracle(hms_ctx, case):
+    from paper_1208_4093_gb300 import capi
+    name, nx, ny, sx, sy, ln = case
+    tr, g, p, pr = make(hms_ctx, nx, ny, sx, sy, ln, coarse_factor=6, coarse_solves=6)
+    try:
+        rng = np.random.default_rng(31)
+        for _ in range(2):
+            u = tr.free * rng.standard_normal(tr.ndof)
+            r = tr.residual(p, u)
+            delta = hms.LocalFactors(tr, g).relax(r)
+            V = hms.modes(tr, g, delta)
+            Ko, Po = hms.coarse_system(tr, V, r)
+            a = np.empty(9 * g.M)
+            dr = np.zeros(9 * g.M, np.int32)
+            capi.hms_coarse_solve(hms_ctx, pr, Ko, Po, a, dr)
+            ao, dro = hms.coarse_solve(Ko, Po)
+            assert rel(V @ a, V @ ao) < 1e-10, name
+            gal = (Po - Ko @ a)[dr == 0]
+            assert np.abs(gal).max() <= 1e-10 * np.abs(Po).max(), name
+    finally:
+        capi.hms_problem_destroy(pr)
+
+
+@pytest.mark.parametrize("case", CASES[:4] + CASES[6:], ids=lambda c: c[0])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nd_full_solve_and_trajectory(hms_ctx, case, precision):
+    """Whole solves reach the direct solve; the FP64 iterates follow the
+    oracle's iteration update by update (T1)."""
+    from paper_1208_4093_gb300 import capi
+    name, nx, ny, sx, sy, ln = case
+    tr, g, p, pr = make(hms_ctx, nx, ny, sx, sy, ln, coarse_factor=6, precision=precision, tol=1e-11,
+                        max_iter=3000)
+    try:
+        out = np.empty((1, tr.ndof))
+        capi.hms_solve(hms_ctx, pr, p.reshape(1, -1), out)
+        assert rel(out[0], direct.cholesky_solve(tr, p)) < (1e-9 if precision == 0 else 1e-8), name
+    finally:
+        capi.hms_problem_destroy(pr)
+    if precision == 0:
+        ref = hms.solve(tr, g, p, 0.0, 3, keep_iterates=True).iterates
+        pr = make(hms_ctx, nx, ny, sx, sy, ln, coarse_factor=6, tol=0.0, max_iter=3)[3]
+        try:
+            capi.hms_solve(hms_ctx, pr, p.reshape(1, -1), out, allow_no_convergence=True)
+            assert rel(out[0], ref[-1]) < 1e-9, name
+        finally:
+            capi.hms_problem_destroy(pr)
+
+
+@pytest.mark.parametrize("nx,ny,sx,sy", [(2048, 256, 32, 32), (512, 512, 16, 16), (1600, 96, 16, 24)],
+                         ids=["64x8_sets", "32x32_sets", "100x4_sets"])
+def test_wide_set_grids_accepted_and_exact(hms_ctx, nx, ny, sx, sy):
+    """Set grids far wider than a band window (64, 32 and 100 sets across)
+    are taken by the automatic choice and solved to the direct solution
+    (the oracle's sparse direct solve, O1)."""
+    from paper_1208_4093_gb300 import capi
+    ea = ea_lognormal(nx, ny, 29)
+    tr = truss.Truss(nx, ny, ea)
+    p = tr.free * loads(nx, ny, 8).reshape(-1)
+    ref = direct.sparse_solve(tr, p)
+    for prec, bar in ((0, 1e-9), (1, 1e-8)):
+        pr = capi.hms_problem_create(hms_ctx, nx, ny, sx, sy, ea=ea, precision=prec, tol=1e-11, max_iter=5000)
+        try:
+            out = np.empty((1, tr.ndof))
+            its = np.zeros(1, np.int32)
+            capi.hms_solve(hms_ctx, pr, p.reshape(1, -1), out, iters=its)
+            err = rel(out[0], ref)
+            print(f"{nx}x{ny} sets {sx}x{sy} precision {prec}: {int(its[0])} updates, error {err:.2e}")
+            assert err < bar
+        finally:
+            capi.hms_problem_destroy(pr)
+
+
+def test_nd_equals_band_factor_result(hms_ctx):
+    """Same problem, band (one SM) and nested-dissection factors: the solves
+    agree to the refinement's accuracy and take the same updates."""
+    from paper_1208_4093_gb300 import capi
+    nx, ny = 96, 80
+    p = loads(nx, ny, 4).reshape(1, -1)
+    outs = []
+    for cf in (4, 6):
+        pr = capi.hms_problem_create(hms_ctx, nx, ny, 16, 16, coarse_factor=cf, tol=1e-10, max_iter=2000)
+        try:
+            out = np.empty_like(p)
+            its = np.zeros(1, np.int32)
+            capi.hms_solve(hms_ctx, pr, p, out, iters=its)
+            outs.append((out, int(its[0])))
+        finally:
+            capi.hms_problem_destroy(pr)
+    assert rel(outs[1][0], outs[0][0]) < 1e-11
+    assert abs(outs[1][1] - outs[0][1]) <= 1
