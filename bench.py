@@ -73,8 +73,10 @@ def parse():
                     help="time to R1 < 1e-8 against the relaxation region's overlap instead (separate JSON line)")
     ap.add_argument("--serve", type=int, default=0, metavar="N",
                     help="serve N requests of the serving workload instead (separate JSON line)")
-    ap.add_argument("--serve-max-active", type=int, default=4,
+    ap.add_argument("--serve-max-active", type=int, default=8,
                     help="requests running at once (the rest wait in arrival order)")
+    ap.add_argument("--serve-in-bench", type=int, default=24, metavar="N",
+                    help="requests of the serving workload run after the timed solves (the line's `serve`; 0: none)")
     return ap.parse_args()
 
 
@@ -566,20 +568,20 @@ def run_overlap_sweep(args):
 
 
 # ---------------------------------------------------------------- serving
-def run_serve(args):
+def serve_measure(count, max_active):
     """Requests arrive by a Poisson process (mean 200 per second) with
-    log-uniform sides in [64, 2048] (width capped at 1152), 1-16 load vectors,
-    lognormal(0, 0.3) EA, 64 x 64-node sets, mixed precision, R1 < 1e-8; the
-    server admits them under a 150 GB budget and advances all admitted ones
-    together.  Latency = completion time - arrival time."""
+    log-uniform sides in [64, 2048], 1-16 load vectors, lognormal(0, 0.3) EA,
+    64 x 64-node sets, mixed precision, R1 < 1e-8; the server admits them
+    under a 150 GB budget and advances all admitted ones together.  Latency =
+    completion time - arrival time.  Returns the summary dict."""
     import numpy as np
     from paper_1208_4093_gb300 import capi
     from workloads import serving_requests
-    reqs = serving_requests(args.serve)
+    reqs = serving_requests(count)
     data = [(r.ea_array(), r.load_array()) for r in reqs]  # generated before the clock starts
     budget = 150 << 30
     ctx = capi.hms_context_create(0)
-    srv = capi.hms_server_create(ctx, budget, max_active=args.serve_max_active)
+    srv = capi.hms_server_create(ctx, budget, max_active=max_active)
     rid_of, arrival, done_t, peak_bytes, steps, rejected = {}, {}, {}, 0, 0, []
     t0 = time.perf_counter()
     nxt = 0
@@ -610,19 +612,25 @@ def run_serve(args):
     capi.hms_context_destroy(ctx)
     lat = np.array([done_t[rid] - arrival[rid] for rid in done_t]) * 1e3
     dofrhs = sum(2 * r.nx * r.ny * r.nrhs for k, r in enumerate(reqs) if k not in rejected)
+    return {"requests": len(reqs), "arrival_rate_per_s": 200.0, "arrivals_span_s": reqs[-1].arrival,
+            "sides": "nx, ny log-uniform [64, 2048]", "nrhs": "1-16", "ea": "lognormal(0,0.3)", "sets": [64, 64],
+            "tol": TOL, "dtype": "f32 relax / f64 residual+master+norms", "hbm_budget_bytes": budget,
+            "max_active_requests": max_active, "widest_nx": max(r.nx for r in reqs),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "makespan_s": makespan, "dof_x_rhs": dofrhs,
+            "dof_per_s": dofrhs / makespan, "peak_bytes_in_use": peak_bytes, "scheduler_steps": steps,
+            "statuses_ok": int(sum(1 for s in status if s == capi.HMS_OK)), "rejected": len(rejected)}
+
+
+def run_serve(args):
+    """The serving workload alone (--serve N): one JSON line."""
+    d = serve_measure(args.serve, args.serve_max_active)
     print(json.dumps({
         "metric": "serving: p50 / p99 request latency and DOF x load vectors per second (mixed, R1 < 1e-8)",
-        "value": float(np.percentile(lat, 50)), "unit": "ms (p50 latency)", "n_gpus": 1, "steps": steps,
-        "warmup": 0, "ms_per_step": makespan * 1e3 / max(steps, 1), "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 relax / f64 residual+master+norms", "data": "synthetic",
-        "config": {"workload": f"serving_{len(reqs)}", "requests": len(reqs), "arrival_rate_per_s": 200.0,
-                   "sides": "log-uniform [64, 2048], width capped at 1152", "nrhs": "1-16",
-                   "ea": "lognormal(0,0.3)", "sets": [64, 64], "tol": TOL, "hbm_budget_bytes": budget,
-                   "max_active_requests": args.serve_max_active},
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "mean_ms": float(lat.mean()), "makespan_s": makespan, "dof_x_rhs": dofrhs,
-        "dof_per_s": dofrhs / makespan, "peak_bytes_in_use": peak_bytes,
-        "statuses_ok": int(sum(1 for s in status if s == capi.HMS_OK)), "rejected": len(rejected)}))
+        "value": d["p50_ms"], "unit": "ms (p50 latency)", "n_gpus": 1, "steps": d["scheduler_steps"],
+        "warmup": 0, "ms_per_step": d["makespan_s"] * 1e3 / max(d["scheduler_steps"], 1),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": d["dtype"],
+        "data": "synthetic", "config": {"workload": f"serving_{d['requests']}", **d}}))
 
 
 # ---------------------------------------------------------------- our arm
@@ -814,6 +822,11 @@ def run_ours(args, rank, world, local_rank):
     per_iter = 10 + 5 + 4
     launches = args.steps * (batches * 16 * per_iter + 1)
 
+    # ---- serving (continuous batching under the HBM budget), a bounded run ----
+    serve = None
+    if args.serve_in_bench > 0 and world == 1:
+        serve = serve_measure(args.serve_in_bench, args.serve_max_active)
+
     ms_med = statistics.median(ms64)
     if world > 1:
         ms_med = max_over_ranks(max(ms64), dev)
@@ -859,6 +872,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": {"value": statistics.median(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * nd,
                 "d2h_bytes_per_step": 8 * nd},
+        "serve": serve,
         "gpu_launches": launches,
         "clocks": clocks,
         "dofs_per_s": world * nd / (ms_med * 1e-3),

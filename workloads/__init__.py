@@ -219,13 +219,13 @@ class ServeRequest:
 
 
 def serving_requests(count: int = 64, seed: int = 5, rate: float = 200.0, side_min: int = 64,
-                     side_max: int = 2048, width_max: int = 1152, nrhs_max: int = 16):
+                     side_max: int = 2048, width_max: int | None = None, nrhs_max: int = 16):
     """Poisson arrivals (mean rate per second) of lattice solves: request k
     draws counter (k, 0, 0, TAG_SERVE) under key (seed, 3): the gap to the
-    previous arrival is exponential (word 0), both sides are log-uniform in
-    [side_min, side_max] (words 1, 2), the load-vector count is
-    1 + floor(nrhs_max u) (word 3).  The width (nodes per row) is the smaller
-    side, capped at width_max; request k's loads use seed 2000 + k."""
+    previous arrival is exponential (word 0), the width nx and the height ny
+    are log-uniform in [side_min, side_max] (words 1, 2), the load-vector
+    count is 1 + floor(nrhs_max u) (word 3).  width_max (None: no cap) caps
+    nx; request k's loads use seed 2000 + k."""
     k = np.arange(count, dtype=np.uint64)
     w0, w1, w2, w3 = philox4x32_10(k.astype(np.uint32), np.zeros(count, np.uint32), np.uint32(0),
                                    np.uint32(TAG_SERVE), seed & 0xFFFFFFFF, ((seed >> 32) + 3) & 0xFFFFFFFF)
@@ -237,6 +237,8 @@ def serving_requests(count: int = 64, seed: int = 5, rate: float = 200.0, side_m
     nrhs = 1 + np.minimum(nrhs_max - 1, np.floor(nrhs_max * uniform01(w3)).astype(int))
     out = []
     for i in range(count):
-        nx, ny = min(a[i], b[i], width_max), max(a[i], b[i])
+        nx, ny = int(a[i]), int(b[i])
+        if width_max is not None:
+            nx = min(nx, width_max)
         out.append(ServeRequest(float(t[i]), int(nx), int(ny), int(nrhs[i]), 2000 + i))
     return out
