@@ -127,8 +127,16 @@ typedef struct {
                                 correction (Eqs. 3 and 8): bit m keeps mode m+1 (bit 0, 1:
                                 translations of Eq. 9; bits 2-5: gradients of Eq. 10; bit 6:
                                 delta of Eq. 13; bits 7, 8: its gradient-weighted copies of
-                                Eq. 14).  A cleared mode gets a = 0, as a mode the coarse solve
-                                drops.  0 = all nine (0x1FF); bits above 8 must be 0 */
+                                Eq. 14; bits 9-11: the force-controlled modes of Eqs. 17-18,
+                                delta^RF and its gradient-weighted copies).  A cleared mode
+                                gets a = 0, as a mode the coarse solve drops.  0 = the nine
+                                displacement-controlled modes (0x1FF).  Any of bits 9-11 set
+                                makes q = 12 modes per set: every set also relaxes with the
+                                forces from outside held (the set cut free, Eqs. 15-17; a
+                                floating set's increment is the minimum-norm one), the
+                                coefficient vector a and P hold 12 entries per set, and set
+                                tiles must be at least 2 x 2 nodes with relax_overlap = 0.
+                                Bits above 11 must be 0 */
   int32_t record_history;    /* 1 = keep the (R1, R2, Pi) row of every residual evaluation on
                                 the device for hms_solve's hist output; 0 = record nothing
                                 (no history buffer; hist rows come back as NaN) */
@@ -254,20 +262,32 @@ hms_status hms_residual(hms_problem* pr, const double* p, const double* u, doubl
 hms_status hms_reactions(hms_problem* pr, const double* u, double* f_out, int32_t mem_kind);
 
 /* Steps a2 + a1 (Eq. 3 then Eq. 1): u_out = u + V a with modes built from
- * delta [2*nx*ny] and coefficients a [9*M] (set-major, 9 per set), then
- * r = p - K u_out and the sums of hms_residual.  u_out may not alias u. */
+ * delta [2*nx*ny] (q = 12: [2][2*nx*ny], delta then delta^RF) and
+ * coefficients a [q*M] (set-major, q per set), then r = p - K u_out and the
+ * sums of hms_residual.  u_out may not alias u. */
 hms_status hms_update_residual(hms_problem* pr, const double* p, const double* u,
                                const double* delta, const double* a, double* u_out,
                                double* r, double* norms, int32_t mem_kind);
 
 /* Steps a3 + a4 (Eqs. 12-13 and Eq. 7): delta_I = (k^Inner_I)^-1 r_I on every
  * set from the setup factors (FP64, or FP32 for HMS_MIXED), and P = V^T r
- * [9*M] with the modes built from that delta. */
+ * [q*M] with the modes built from that delta (with q = 12, also from the
+ * force-controlled delta^RF of hms_relax_force). */
 hms_status hms_relax(hms_problem* pr, const double* r, double* delta, double* P,
                      int32_t mem_kind);
 
+/* The force-controlled relaxation (Eqs. 15-17) of a problem with q = 12:
+ * delta^RF_I solves (k^Inner_I + Delta k_I) delta = r_I, the set cut free
+ * (Delta k of Eq. 15 removes the stiffness of the bars to the outer region);
+ * where that matrix is singular (the rigid motions the set's supports leave
+ * free), the minimum-norm solution of the system with r_I projected onto its
+ * range.  r, delta_rf: [2*nx*ny]; delta_rf is 0 on constrained DOFs.
+ * HMS_ERR_ARG for a problem without the force-controlled modes. */
+hms_status hms_relax_force(hms_problem* pr, const double* r, double* delta_rf, int32_t mem_kind);
+
 /* Step a5 (Eq. 6): the upper-level matrix K_aa = V^T K V for the modes built
- * from delta, written dense [9M][9M] row-major (only for 9M <= 4096).  For
+ * from delta (q = 12: [2][2*nx*ny], delta then delta^RF), written dense
+ * [qM][qM] row-major (only for qM <= 4096).  For
  * HMS_MIXED problems delta is rounded to FP32 (as the relaxation leaves it)
  * and the per-iteration bar products are formed in FP32, summed in FP64. */
 hms_status hms_coarse_matrix(hms_problem* pr, const double* delta, double* Kaa,

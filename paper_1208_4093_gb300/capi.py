@@ -110,6 +110,7 @@ def lib():
         "hms_problem_refine_cap_hits": (ctypes.c_int64, [_P]),
         "hms_problem_set_relax_wait_limit": (ctypes.c_int32, [_P, ctypes.c_int32]),
         "hms_measure_fp64_rate": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+        "hms_relax_force": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -129,7 +130,7 @@ def exported_symbols():
             "hms_server_destroy", "hms_server_submit", "hms_server_step", "hms_server_take", "hms_problem_clone",
             "hms_problem_relax_threads", "hms_context_set_batch_mode", "hms_problem_relax_copies",
             "hms_reactions", "hms_problem_refine_cap_hits", "hms_problem_set_relax_wait_limit",
-            "hms_measure_fp64_rate"]
+            "hms_measure_fp64_rate", "hms_relax_force"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -383,6 +384,12 @@ def hms_update_residual(ctx, pr, p, u, delta, a, u_out, r_out, norms_out):
 def hms_relax(ctx, pr, r, delta_out, P_out):
     A = [_Arg(r), _Arg(delta_out, writable=True), _Arg(P_out, writable=True)]
     _check(ctx, lib().hms_relax(pr, *[x.ptr for x in A], _mem_kind(*A)))
+
+
+def hms_relax_force(ctx, pr, r, delta_rf_out):
+    """The force-controlled increment delta^RF of Eq. 17 (problems with mode_mask bits 9-11)."""
+    A = [_Arg(r), _Arg(delta_rf_out, writable=True)]
+    _check(ctx, lib().hms_relax_force(pr, A[0].ptr, A[1].ptr, _mem_kind(*A)))
 
 
 def hms_coarse_matrix(ctx, pr, delta, Kaa_out):

@@ -59,6 +59,14 @@ struct hms_problem {
   // factors
   double* f64 = nullptr;
   float* f32 = nullptr;
+  // force-controlled relaxation (q = 12): cut-free set factors with pinned DOFs,
+  // supports | pins, per-set projection onto the free rigid motions (force.cu)
+  double* f64F = nullptr;
+  float* f32F = nullptr;
+  uint8_t* fixF = nullptr;
+  double* Mforce = nullptr;
+  double2* rproj = nullptr;  // per instance: r projected, 0 at the pins
+  void* delta_rf = nullptr;  // per instance: delta^RF of Eq. 17 (double2 or float2)
   // iteration state
   double2* u[2] = {nullptr, nullptr};
   double2* p = nullptr;
@@ -211,6 +219,19 @@ cudaError_t launch_solve_stage(hms_problem* pr, cudaStream_t s, int q, const Ite
                              pr->x, pr->scale, pr->a, pr->cstat, flags, ctl, pr->err);
 }
 
+// The force-controlled relaxation of every set (Eqs. 15-17, force.cu) after the
+// displacement-controlled one: r projected, the cut-free solve, delta^RF and
+// the upper-level forces of the modes 10-12 (P[12 I + 9 .. 11]).
+cudaError_t launch_force_relax(hms_problem* pr, cudaStream_t s, const IterCtl* ctl) {
+  const LatView& lv = pr->lv;
+  cudaError_t e = launch_force_in(s, lv, pr->r, pr->Mforce, pr->fixF, pr->rproj, ctl);
+  if (e != cudaSuccess) return e;
+  e = launch_relax(s, lv, pr->set_off, pr->f64F, pr->f32F, pr->rproj, pr->delta_rf, nullptr, pr->yscratch, ctl,
+                   pr->err, pr->relax_threads, pr->relax_chunks, pr->relax_wait0);
+  if (e != cudaSuccess) return e;
+  return launch_force_out(s, lv, pr->delta_rf, fp32(pr), pr->Mforce, pr->r, pr->P, ctl);
+}
+
 // Launches of one iteration (the body of Fig. 3's loop); k = position in a batch.
 cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t* ev) {
   const LatView& lv = pr->lv;
@@ -222,20 +243,24 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
   mark();
   e = launch_update_residual(s, lv, pr->u[k & 1], pr->u[(k + 1) & 1], pr->p, pr->delta, fp32(pr), pr->a,
                              pr->r, pr->partials, pr->ticket, nullptr, pr->ctl, pr->hist, pr->hist_cap,
-                             nullptr);
+                             pr->delta_rf);
   if (e != cudaSuccess) return e;
   mark();
   e = launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, pr->ctl, pr->err,
                    pr->relax_threads, pr->relax_chunks, pr->relax_wait0);
   if (e != cudaSuccess) return e;
+  if (lv.q == NMODES_RF) {
+    e = launch_force_relax(pr, s, pr->ctl);
+    if (e != cudaSuccess) return e;
+  }
   mark();
-  e = launch_coarse_slots(s, lv, pr->delta, fp32(pr), false, pr->slots_it, pr->ctl);
+  e = launch_coarse_slots(s, lv, pr->delta, fp32(pr), false, pr->slots_it, pr->ctl, pr->delta_rf);
   if (e != cudaSuccess) return e;
   mark();
   e = launch_coarse_band_from_slots(s, lv, pr->slots_base, pr->slots_it, pr->band, pr->ctl);
   if (e != cudaSuccess) return e;
   e = launch_coarse_scale(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale,
-                          pr->b, pr->x, pr->dropped, pr->mode_mask, pr->ctl);
+                          pr->b, pr->x, pr->dropped, pr->mode_mask, lv.q, pr->ctl);
   if (e != cudaSuccess) return e;
   mark();
   e = launch_factor_stage(pr, s, pr->ctl);
@@ -505,6 +530,10 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
   pr->set_off = src->set_off;
   pr->f64 = src->f64;
   pr->f32 = src->f32;
+  pr->f64F = src->f64F;
+  pr->f32F = src->f32F;
+  pr->fixF = src->fixF;
+  pr->Mforce = src->Mforce;
   pr->slots_base = src->slots_base;
   cudaError_t e = alloc_instance(pr);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -557,6 +586,14 @@ static cudaError_t alloc_instance(hms_problem* pr) {
     pr->delta = dl;
     CKI(cudaMemsetAsync(dl, 0, nn * sizeof(double2), s));
   }
+  if (lv.q == NMODES_RF) {
+    CKI(palloc(pr, &pr->rproj, nn));
+    const size_t eb = fp32(pr) ? sizeof(float2) : sizeof(double2);
+    unsigned char* df;
+    CKI(palloc(pr, &df, nn * eb));
+    pr->delta_rf = df;
+    CKI(cudaMemsetAsync(df, 0, nn * eb, s));
+  }
   {
     const size_t ybytes = (size_t)lv.M * relax_y_stride(lv) * (fp32(pr) ? sizeof(float) : sizeof(double));
     unsigned char* ys;
@@ -567,7 +604,7 @@ static cudaError_t alloc_instance(hms_problem* pr) {
   const size_t nband = (size_t)n_c * (bw + 1);
   CKI(palloc(pr, &pr->a, n_c));
   CKI(palloc(pr, &pr->P, n_c));
-  CKI(palloc(pr, &pr->slots_it, (size_t)lv.M * NSLOTS * SLOT_SIZE));
+  CKI(palloc(pr, &pr->slots_it, (size_t)lv.M * NSLOTS * slot_size(lv.q)));
   CKI(palloc(pr, &pr->band, nband));
   CKI(palloc(pr, &pr->sband, 2 * nband));
   CKI(palloc(pr, &pr->scale, n_c));
@@ -728,8 +765,18 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     return fail(c, HMS_ERR_ARG, "relax_overlap must be >= 0 with min(nx, set_sx + 2 relax_overlap) <= 80");
   if (o->precision == HMS_FP64 && rw > MAX_SX)
     return fail(c, HMS_ERR_ARG, "the FP64 relaxation takes regions up to 64 nodes wide");
-  if ((o->mode_mask >> NMODES) != 0u) return fail(c, HMS_ERR_ARG, "mode_mask has bits above mode 9");
+  if ((o->mode_mask >> NMODES_RF) != 0u) return fail(c, HMS_ERR_ARG, "mode_mask has bits above mode 12");
   if (o->record_history != 0 && o->record_history != 1) return fail(c, HMS_ERR_ARG, "record_history must be 0 or 1");
+  const bool force = (o->mode_mask >> NMODES) != 0u;  // modes 10-12: the force-controlled relaxation
+  if (force) {
+    const int wr = d->nx - ((d->nx + d->set_sx - 1) / d->set_sx - 1) * d->set_sx;
+    const int hr = d->ny - ((d->ny + d->set_sy - 1) / d->set_sy - 1) * d->set_sy;
+    if (std::min(std::min(d->set_sx, d->nx), wr) < 2 || std::min(std::min(d->set_sy, d->ny), hr) < 2)
+      return fail(c, HMS_ERR_ARG, "the force-controlled modes need set tiles of at least 2 x 2 nodes (a cut-free "
+                                  "one-row or one-column set is a mechanism)");
+    if (o->relax_overlap != 0)
+      return fail(c, HMS_ERR_ARG, "the force-controlled modes take no extended relaxation region");
+  }
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
 
@@ -745,6 +792,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   lv.My = (d->ny + d->set_sy - 1) / d->set_sy;
   lv.M = lv.Mx * lv.My;
   lv.ov = o->relax_overlap;
+  lv.q = force ? NMODES_RF : NMODES;
   lv.L = d->bar_length;
   lv.k_u = d->ea ? 0.0 : d->ea_uniform / d->bar_length;
   pr->precision = o->precision;
@@ -755,7 +803,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   pr->max_iter = o->max_iter;
   pr->mode_mask = o->mode_mask ? o->mode_mask : 0x1FFu;
   pr->record_history = o->record_history != 0;
-  pr->n_c = NMODES * lv.M;
+  pr->n_c = lv.q * lv.M;
   pr->bw = coarse_bw(lv);
 
   int maxsm = 0;
@@ -786,6 +834,8 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   } while (0)
 
   const size_t nn = (size_t)lv.nx * lv.ny;
+  std::vector<uint8_t> fix_host;   // the supports (kept for the force-controlled setup)
+  std::vector<double2> rep_host;   // the sets' representing points
   // ---- lattice description ----
   {
     std::vector<uint8_t> fm(nn, 0);
@@ -797,6 +847,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     CKP(salloc(pr, &pr->fix, nn));
     CKP(cudaMemcpy(pr->fix, fm.data(), nn, cudaMemcpyHostToDevice));
     lv.fix = pr->fix;
+    fix_host.swap(fm);
   }
   if (d->ea) {
     std::vector<double> kb(3 * nn, 0.0);
@@ -841,6 +892,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     CKP(salloc(pr, &pr->rep, lv.M));
     CKP(cudaMemcpy(pr->rep, rp.data(), lv.M * sizeof(double2), cudaMemcpyHostToDevice));
     lv.rep = pr->rep;
+    rep_host = rp;
     CKP(salloc(pr, &pr->set_off, lv.M + 1));
     CKP(cudaMemcpy(pr->set_off, so.data(), (lv.M + 1) * sizeof(long long), cudaMemcpyHostToDevice));
     const size_t fsz = (size_t)so[lv.M];
@@ -851,9 +903,29 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
       CKP(salloc(pr, &pr->f64, fsz));
       CKP(cudaMemsetAsync(pr->f64, 0, fsz * sizeof(double), s));
     }
+    if (force) {
+      // the cut-free factors have the same shapes; supports | pins and the projections
+      std::vector<double> Mh;
+      std::vector<uint8_t> fixF;
+      if (!force_set_data(lv, fix_host, rep_host, Mh, fixF)) {
+        hms_problem_destroy(pr);
+        return fail(c, HMS_ERR_ARG, "a set's free rigid motions cannot be pinned at its corner nodes");
+      }
+      if (fp32(pr)) {
+        CKP(salloc(pr, &pr->f32F, fsz));
+        CKP(cudaMemsetAsync(pr->f32F, 0, fsz * sizeof(float), s));
+      } else {
+        CKP(salloc(pr, &pr->f64F, fsz));
+        CKP(cudaMemsetAsync(pr->f64F, 0, fsz * sizeof(double), s));
+      }
+      CKP(salloc(pr, &pr->fixF, nn));
+      CKP(cudaMemcpy(pr->fixF, fixF.data(), nn, cudaMemcpyHostToDevice));
+      CKP(salloc(pr, &pr->Mforce, 9 * (size_t)lv.M));
+      CKP(cudaMemcpy(pr->Mforce, Mh.data(), 9 * (size_t)lv.M * sizeof(double), cudaMemcpyHostToDevice));
+    }
   }
   // ---- iteration buffers ----
-  CKP(salloc(pr, &pr->slots_base, (size_t)lv.M * NSLOTS * SLOT_SIZE));
+  CKP(salloc(pr, &pr->slots_base, (size_t)lv.M * NSLOTS * slot_size(lv.q)));
   CKP(alloc_instance(pr));
 
   // ---- setup kernels: local factors (K2f) and the constant part of K_aa ----
@@ -866,11 +938,16 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     double* scratch = nullptr;
     CKP(cudaMalloc(&scratch, (size_t)grid * b_size(MAX_NB) * sizeof(double)));
     cudaError_t e = launch_set_factor(s, lv, pr->set_off, pr->f64, pr->f32, scratch, grid, pr->err);
+    if (e == cudaSuccess && force) {
+      LatView lvF = lv;  // the cut-free sets with their pinned DOFs marked as constrained
+      lvF.fix = pr->fixF;
+      e = launch_set_factor(s, lvF, pr->set_off, pr->f64F, pr->f32F, scratch, grid, pr->err, true);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(scratch);
     CKP(e);
   }
-  CKP(launch_coarse_slots(s, lv, pr->delta, fp32(pr), true, pr->slots_base, nullptr));
+  CKP(launch_coarse_slots(s, lv, pr->delta, fp32(pr), true, pr->slots_base, nullptr, pr->delta_rf));
   CKP(cudaEventRecord(e1, s));
   CKP(cudaEventSynchronize(e1));
   cudaEventElapsedTime(&pr->setup_ms, e0, e1);
@@ -1051,7 +1128,8 @@ hms_status hms_context_set_batch_mode(hms_context* c, int32_t mode) {
 static bool lockstep_applies(int32_t count, hms_problem* const* problems) {
   for (int i = 0; i < count; ++i) {
     const hms_problem* pr = problems[i];
-    if (!pr || pr->profile || pr->coarse_fp64 || pr->cluster_factor || pr->two_sided || pr->big_stages <= 0)
+    if (!pr || pr->profile || pr->coarse_fp64 || pr->cluster_factor || pr->two_sided || pr->big_stages <= 0 ||
+        pr->lv.q != NMODES)
       return false;
     if (pr->precision != problems[0]->precision || pr->nsolve != problems[0]->nsolve) return false;
   }
@@ -1493,6 +1571,38 @@ hms_status hms_reactions(hms_problem* pr, const double* u, double* f_out, int32_
   return HMS_OK;
 }
 
+// delta (and, with the force-controlled modes, delta^RF after it) from the
+// caller into the problem's buffers, rounded to FP32 on the mixed path.
+static cudaError_t stage_deltas(hms_problem* pr, const double* delta, int32_t mem_kind) {
+  cudaStream_t s = pr->ctx->stream;
+  const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+  const int nf = pr->lv.q == NMODES_RF ? 2 : 1;
+  for (int k = 0; k < nf; ++k) {
+    void* dst = k == 0 ? pr->delta : pr->delta_rf;
+    const double* src = delta + 2 * nn * k;
+    cudaError_t e;
+    if (fp32(pr)) {
+      if ((e = cudaMemcpyAsync(pr->r, src, vb, kind_in(mem_kind), s)) != cudaSuccess) return e;  // staging
+      if ((e = launch_d2f(s, (const double*)pr->r, (float*)dst, 2 * nn)) != cudaSuccess) return e;
+    } else {
+      if ((e = cudaMemcpyAsync(dst, src, vb, kind_in(mem_kind), s)) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// The relaxation increment d (FP64, or FP32 widened) out to the caller.
+static cudaError_t copy_delta_out(hms_problem* pr, const void* d, double* out, int32_t mem_kind) {
+  cudaStream_t s = pr->ctx->stream;
+  const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+  if (fp32(pr)) {
+    cudaError_t e = launch_f2d(s, (const float*)d, (double*)pr->u[1], 2 * nn);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(out, pr->u[1], vb, kind_out(mem_kind), s);
+  }
+  return cudaMemcpyAsync(out, d, vb, kind_out(mem_kind), s);
+}
+
 hms_status hms_update_residual(hms_problem* pr, const double* p, const double* u, const double* delta,
                                const double* a, double* u_out, double* r, double* norms, int32_t mem_kind) {
   if (!pr || !p || !u || !r) return HMS_ERR_ARG;
@@ -1506,16 +1616,11 @@ hms_status hms_update_residual(hms_problem* pr, const double* p, const double* u
   CKC(c, cudaMemcpyAsync(pr->u[0], u, vb, kind_in(mem_kind), s));
   CKC(c, launch_mask_u(s, pr->lv, pr->u[0]));
   if (delta) {
-    if (fp32(pr)) {
-      CKC(c, cudaMemcpyAsync(pr->r, delta, vb, kind_in(mem_kind), s));  // staging
-      CKC(c, launch_d2f(s, (const double*)pr->r, (float*)pr->delta, 2 * nn));
-    } else {
-      CKC(c, cudaMemcpyAsync(pr->delta, delta, vb, kind_in(mem_kind), s));
-    }
+    CKC(c, stage_deltas(pr, delta, mem_kind));
     CKC(c, cudaMemcpyAsync(pr->a, a, pr->n_c * sizeof(double), kind_in(mem_kind), s));
   }
   CKC(c, launch_update_residual(s, pr->lv, pr->u[0], pr->u[1], pr->p, pr->delta, fp32(pr), delta ? pr->a : nullptr,
-                                pr->r, pr->partials, pr->ticket, pr->norms, nullptr, nullptr, 0, nullptr));
+                                pr->r, pr->partials, pr->ticket, pr->norms, nullptr, nullptr, 0, pr->delta_rf));
   CKC(c, cudaMemcpyAsync(r, pr->r, vb, kind_out(mem_kind), s));
   if (u_out) CKC(c, cudaMemcpyAsync(u_out, pr->u[1], vb, kind_out(mem_kind), s));
   if (norms) CKC(c, cudaMemcpyAsync(norms, pr->norms, 3 * sizeof(double), kind_out(mem_kind), s));
@@ -1534,31 +1639,37 @@ hms_status hms_relax(hms_problem* pr, const double* r, double* delta, double* P,
   CKC(c, launch_mask_u(s, pr->lv, pr->r));
   CKC(c, launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr, pr->err,
                       pr->relax_threads, pr->relax_chunks, pr->relax_wait0));
-  if (fp32(pr)) {
-    CKC(c, launch_f2d(s, (const float*)pr->delta, (double*)pr->u[1], 2 * nn));
-    CKC(c, cudaMemcpyAsync(delta, pr->u[1], vb, kind_out(mem_kind), s));
-  } else {
-    CKC(c, cudaMemcpyAsync(delta, pr->delta, vb, kind_out(mem_kind), s));
-  }
+  if (pr->lv.q == NMODES_RF) CKC(c, launch_force_relax(pr, s, nullptr));
+  CKC(c, copy_delta_out(pr, pr->delta, delta, mem_kind));
   CKC(c, cudaMemcpyAsync(P, pr->P, pr->n_c * sizeof(double), kind_out(mem_kind), s));
+  CKC(c, cudaStreamSynchronize(s));
+  return check_dev_err(pr);
+}
+
+hms_status hms_relax_force(hms_problem* pr, const double* r, double* delta_rf, int32_t mem_kind) {
+  if (!pr || !r || !delta_rf) return HMS_ERR_ARG;
+  if (mem_kind != HMS_MEM_HOST && mem_kind != HMS_MEM_DEVICE) return HMS_ERR_ARG;
+  hms_context* c = pr->ctx;
+  if (pr->lv.q != NMODES_RF) return fail(c, HMS_ERR_ARG, "hms_relax_force: the problem has no force-controlled modes");
+  CKC(c, cudaSetDevice(c->device));
+  cudaStream_t s = c->stream;
+  const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
+  CKC(c, cudaMemcpyAsync(pr->r, r, vb, kind_in(mem_kind), s));
+  CKC(c, launch_mask_u(s, pr->lv, pr->r));
+  CKC(c, launch_force_relax(pr, s, nullptr));
+  CKC(c, copy_delta_out(pr, pr->delta_rf, delta_rf, mem_kind));
   CKC(c, cudaStreamSynchronize(s));
   return check_dev_err(pr);
 }
 
 hms_status hms_coarse_matrix(hms_problem* pr, const double* delta, double* Kaa, int32_t mem_kind) {
   if (!pr || !delta || !Kaa) return HMS_ERR_ARG;
-  if (pr->n_c > 4096) return fail(pr->ctx, HMS_ERR_ARG, "dense K_aa only for 9M <= 4096");
+  if (pr->n_c > 4096) return fail(pr->ctx, HMS_ERR_ARG, "dense K_aa only for q M <= 4096");
   hms_context* c = pr->ctx;
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
-  const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
-  if (fp32(pr)) {
-    CKC(c, cudaMemcpyAsync(pr->r, delta, vb, kind_in(mem_kind), s));
-    CKC(c, launch_d2f(s, (const double*)pr->r, (float*)pr->delta, 2 * nn));
-  } else {
-    CKC(c, cudaMemcpyAsync(pr->delta, delta, vb, kind_in(mem_kind), s));
-  }
-  CKC(c, launch_coarse_slots(s, pr->lv, pr->delta, fp32(pr), false, pr->slots_it, nullptr));
+  CKC(c, stage_deltas(pr, delta, mem_kind));
+  CKC(c, launch_coarse_slots(s, pr->lv, pr->delta, fp32(pr), false, pr->slots_it, nullptr, pr->delta_rf));
   CKC(c, launch_coarse_band_from_slots(s, pr->lv, pr->slots_base, pr->slots_it, pr->band, nullptr));
   double* dense = nullptr;
   const size_t nd = (size_t)pr->n_c * pr->n_c;
@@ -1574,7 +1685,7 @@ hms_status hms_coarse_matrix(hms_problem* pr, const double* delta, double* Kaa, 
 hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P, double* a, int32_t* dropped,
                             int32_t mem_kind) {
   if (!pr || !Kaa || !P || !a) return HMS_ERR_ARG;
-  if (pr->n_c > 4096) return fail(pr->ctx, HMS_ERR_ARG, "dense K_aa only for 9M <= 4096");
+  if (pr->n_c > 4096) return fail(pr->ctx, HMS_ERR_ARG, "dense K_aa only for q M <= 4096");
   hms_context* c = pr->ctx;
   CKC(c, cudaSetDevice(c->device));
   cudaStream_t s = c->stream;
@@ -1588,7 +1699,7 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
   CKC(c, e);
   CKC(c, cudaMemcpyAsync(pr->P, P, n * sizeof(double), kind_in(mem_kind), s));
   CKC(c, launch_coarse_scale(s, n, bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale, pr->b,
-                             pr->x, pr->dropped, pr->mode_mask, nullptr));
+                             pr->x, pr->dropped, pr->mode_mask, pr->lv.q, nullptr));
   CKC(c, launch_factor_stage(pr, s, nullptr));
   for (int q = 0; q < pr->nsolve; ++q) {
     if (q > 0)
@@ -1662,7 +1773,15 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
   const long long rw = std::min((long long)d->nx, (long long)d->set_sx + 2LL * (long long)o->relax_overlap);
   if (o->relax_overlap < 0 || rw > MAX_RX) return false;
   if (o->precision == HMS_FP64 && rw > MAX_SX) return false;
-  if ((o->mode_mask >> NMODES) != 0u || (o->record_history != 0 && o->record_history != 1)) return false;
+  if ((o->mode_mask >> NMODES_RF) != 0u || (o->record_history != 0 && o->record_history != 1)) return false;
+  const bool force = (o->mode_mask >> NMODES) != 0u;
+  if (force) {
+    const int wr = d->nx - ((d->nx + d->set_sx - 1) / d->set_sx - 1) * d->set_sx;
+    const int hr = d->ny - ((d->ny + d->set_sy - 1) / d->set_sy - 1) * d->set_sy;
+    if (std::min(std::min(d->set_sx, d->nx), wr) < 2 || std::min(std::min(d->set_sy, d->ny), hr) < 2 ||
+        o->relax_overlap != 0)
+      return false;
+  }
   hms_problem pr;
   LatView& lv = pr.lv;
   lv.nx = d->nx;
@@ -1673,8 +1792,9 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
   lv.My = (d->ny + d->set_sy - 1) / d->set_sy;
   lv.M = lv.Mx * lv.My;
   lv.ov = o->relax_overlap;
+  lv.q = force ? NMODES_RF : NMODES;
   pr.precision = o->precision;
-  pr.n_c = NMODES * lv.M;
+  pr.n_c = lv.q * lv.M;
   pr.bw = coarse_bw(lv);
   int maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
@@ -1689,9 +1809,12 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
     const Region R = relax_region(lv, I);
     fac += (size_t)set_factor_stride(2 * R.w, R.h);
   }
-  *shared = nn + (d->ea ? 3 * nn * 8 : 0) + M * 16 + (M + 1) * 8 + fac * esz + M * NSLOTS * SLOT_SIZE * 8;
+  const size_t ss = (size_t)slot_size(lv.q);
+  *shared = nn + (d->ea ? 3 * nn * 8 : 0) + M * 16 + (M + 1) * 8 + fac * esz + M * NSLOTS * ss * 8;
+  if (force) *shared += fac * esz + nn + 9 * M * 8;  // cut-free factors, supports | pins, projections
   size_t b = 4 * nn * 16 + nn * 2 * esz + M * (size_t)relax_y_stride(lv) * esz;
-  b += 2 * n_c * 8 + M * NSLOTS * SLOT_SIZE * 8 + 3 * nband * 8 + 4 * n_c * 8;
+  if (force) b += nn * 16 + nn * 2 * esz;  // r projected, delta^RF
+  b += 2 * n_c * 8 + M * NSLOTS * ss * 8 + 3 * nband * 8 + 4 * n_c * 8;
   if (pr.nd) {
     const NDPlanHost& P = pr.ndp;
     b += (nband + 16) * 4 + P.nodes.size() * sizeof(NDNode) + P.sets.size() * 4 +

@@ -353,6 +353,192 @@ __global__ void __launch_bounds__(NT) k_coarse_slots(LatView lv, const DT* __res
   slots_body<DT, FULL, AT>(lv, delta, slots, ctl, blockIdx.x);
 }
 
+// ---- q = 12: the force-controlled modes 10-12 of Eqs. 17-18 as well ----
+// The same bar-by-bar sums with every bar on the general path: the mode
+// projections s_0..s_8 of mode_proj and s_9 = e.delta^RF, s_10 = xi s_9,
+// s_11 = eta s_9; slots of 24 x 24 (rows/cols 0-11 = I's modes, 12-23 = J's).
+constexpr int Q12 = NMODES_RF, SD12 = 2 * Q12, SS12 = SD12 * SD12;
+constexpr int LSTRIDE12 = 4 * Q12;      // s_a, -s_b, k s_a, -k s_b
+constexpr int NGEN12_FULL = 21;         // (m, l), l <= m < 6
+constexpr int NGEN12_DELTA = 57;        // (m, l), m in 6..11, l <= m
+
+__device__ inline void mode_proj12(double ex, double ey, double xi, double eta, unsigned fm, double2 dl,
+                                   double2 df, double* s) {
+  mode_proj(ex, ey, xi, eta, fm, dl, s);
+  const double ef = ex * df.x + ey * df.y;  // delta^RF is 0 on constrained DOFs
+  s[9] = ef;
+  s[10] = xi * ef;
+  s[11] = eta * ef;
+}
+__device__ inline int gen12_idx(int m, int l, bool full) {
+  return full ? m * (m + 1) / 2 + l : m * (m + 1) / 2 - 21 + l;
+}
+
+template <typename DT, bool FULL, typename AT>
+__device__ __forceinline__ void slots12_body(const LatView lv, const DT* __restrict__ delta,
+                                             const DT* __restrict__ delta_rf, double* __restrict__ slots,
+                                             const IterCtl* ctl, int I) {
+  extern __shared__ double lists[];
+  if (ctl && *(volatile const int*)&ctl->done) return;
+  constexpr int NGEN = FULL ? NGEN12_FULL : NGEN12_DELTA;
+  constexpr int MLO = FULL ? 0 : 6, MHI = FULL ? 6 : Q12;  // rows m of the sums
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Ix = I % lv.Mx, Iy = I / lv.Mx;
+  const int i0 = Ix * lv.sx, j0 = Iy * lv.sy;
+  const int w = min(lv.sx, lv.nx - i0), h = min(lv.sy, lv.ny - j0);
+  const ListCaps LC = list_caps(w, h);
+  double* out = slots + (size_t)I * NSLOTS * SS12;
+
+  for (int q = tid; q < LC.total * LSTRIDE12; q += NT) lists[q] = 0.0;
+  for (int q = tid; q < NSLOTS * SS12; q += NT) out[q] = 0.0;
+  __syncthreads();
+
+  const double2 repI = lv.rep[I];
+  AT gen[NGEN];
+#pragma unroll
+  for (int k = 0; k < NGEN; ++k) gen[k] = AT(0);
+  auto ld = [&](const DT* p, size_t n) { return FULL ? make_double2(0.0, 0.0) : ld_delta(p, n); };
+
+  for (int q = tid; q < w * h; q += NT) {
+    const int il = q % w, jl = q / w;
+    const int i = i0 + il, j = j0 + jl;
+    const int off = j & 1;
+    const size_t na = (size_t)j * lv.nx + i;
+    const unsigned fa = lv.fix[na];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double k = bar_k(lv, i, j, d);
+      if (__double_as_longlong(k) == 0) continue;
+      const int ib = (d == 0) ? i + 1 : (d == 1 ? i + off : i - 1 + off);
+      const int jb = (d == 0) ? j : j + 1;
+      if (ib >= i0 + w || ib < i0 || jb >= j0 + h) continue;  // interface bar: the pass below
+      const size_t nbn = (size_t)jb * lv.nx + ib;
+      const unsigned fb = lv.fix[nbn];
+      const double ex = (d == 0) ? 1.0 : (d == 1 ? 0.5 : -0.5), ey = (d == 0) ? 0.0 : SQ3_2;
+      double sa[Q12], sb[Q12];
+      mode_proj12(ex, ey, node_x(lv, i, j) - repI.x, node_y(lv, j) - repI.y, fa, ld(delta, na), ld(delta_rf, na),
+                  sa);
+      mode_proj12(ex, ey, node_x(lv, ib, jb) - repI.x, node_y(lv, jb) - repI.y, fb, ld(delta, nbn),
+                  ld(delta_rf, nbn), sb);
+#pragma unroll
+      for (int m = 0; m < Q12; ++m) sa[m] -= sb[m];
+#pragma unroll
+      for (int m = MLO; m < MHI; ++m)
+#pragma unroll
+        for (int l = 0; l <= m; ++l) {
+          const int g = gen12_idx(m, l, FULL);
+          gen[g] = fma((AT)(k * sa[m]), (AT)sa[l], gen[g]);
+        }
+    }
+  }
+
+  // interface bars (the far end in a neighbour set), as in slots_body
+  for (int t = tid; t < 3 * h + 2 * w; t += NT) {
+    int il, jl, d;
+    if (t < 2 * h) {
+      il = w - 1, jl = t >> 1, d = t & 1;
+    } else if (t < 3 * h) {
+      il = 0, jl = t - 2 * h, d = 2;
+    } else {
+      const int u = t - 3 * h;
+      il = u >> 1, jl = h - 1, d = 1 + (u & 1);
+      if ((d == 1 && il == w - 1) || (d == 2 && il == 0)) continue;
+    }
+    const int i = i0 + il, j = j0 + jl, off = j & 1;
+    const double k = bar_k(lv, i, j, d);
+    if (__double_as_longlong(k) == 0) continue;
+    const int ib = (d == 0) ? i + 1 : (d == 1 ? i + off : i - 1 + off);
+    const int jb = (d == 0) ? j : j + 1;
+    const int dxs = (ib >= i0 + w) ? 1 : (ib < i0 ? -1 : 0);
+    const int dys = (jb >= j0 + h) ? 1 : 0;
+    if (dxs == 0 && dys == 0) continue;
+    const size_t na = (size_t)j * lv.nx + i, nbn = (size_t)jb * lv.nx + ib;
+    const unsigned fa = lv.fix[na], fb = lv.fix[nbn];
+    const double ex = (d == 0) ? 1.0 : (d == 1 ? 0.5 : -0.5), ey = (d == 0) ? 0.0 : SQ3_2;
+    int slot, idx;
+    if (dys == 0) {
+      if (dxs > 0) {
+        slot = SLOT_E;
+        idx = 2 * jl + (d == 1 ? 1 : 0);
+      } else {
+        slot = SLOT_W;
+        idx = jl;
+      }
+    } else if (dxs == 0) {
+      slot = SLOT_N;
+      idx = 2 * il + (d == 2 ? 1 : 0);
+    } else if (dxs > 0) {
+      slot = SLOT_NE;
+      idx = (d == 1) ? 0 : 1;
+    } else {
+      slot = SLOT_NW;
+      idx = (d == 2) ? 0 : 1;
+    }
+    const int Jx = Ix + dxs, Jy = Iy + dys;
+    const double2 repJ = lv.rep[Jy * lv.Mx + Jx];
+    double* e = lists + (size_t)(LC.off[slot] + idx) * LSTRIDE12;
+    double sa[Q12], sb[Q12];
+    mode_proj12(ex, ey, node_x(lv, i, j) - repI.x, node_y(lv, j) - repI.y, fa, ld(delta, na), ld(delta_rf, na), sa);
+    mode_proj12(ex, ey, node_x(lv, ib, jb) - repJ.x, node_y(lv, jb) - repJ.y, fb, ld(delta, nbn), ld(delta_rf, nbn),
+                sb);
+#pragma unroll
+    for (int m = 0; m < Q12; ++m) {
+      e[m] = sa[m];
+      e[Q12 + m] = -sb[m];
+      e[2 * Q12 + m] = k * sa[m];
+      e[3 * Q12 + m] = -(k * sb[m]);
+    }
+  }
+
+  // deterministic block sums of the per-thread accumulators, RED_CHUNK at a time
+  double* red = lists + (size_t)LC.total * LSTRIDE12;  // RED_CHUNK x NT
+  double* tot = red + RED_CHUNK * NT;                   // NGEN CTA totals
+#pragma unroll
+  for (int c0 = 0; c0 < NGEN; c0 += RED_CHUNK) {
+#pragma unroll
+    for (int q = 0; q < RED_CHUNK; ++q)
+      if (c0 + q < NGEN) red[q * NT + tid] = (double)gen[c0 + q];
+    __syncthreads();
+    if (c0 + warp < NGEN) {
+      const double* q = red + warp * NT + lane;
+      double v = q[0];
+#pragma unroll
+      for (int ww = 1; ww < NW; ++ww) v += q[32 * ww];
+      v = warp_sum(v);
+      if (lane == 0) tot[c0 + warp] = v;
+    }
+    __syncthreads();
+  }
+  // SELF slot (upper-left 12 x 12): the entries this pass sums
+  if (tid < Q12 * Q12) {
+    const int m = tid / Q12, l = tid % Q12;
+    const int mm = m > l ? m : l, ll = m > l ? l : m;
+    if (mm >= MLO && mm < MHI) out[SLOT_SELF * SS12 + m * SD12 + l] = tot[gen12_idx(mm, ll, FULL)];
+  }
+  // interface slots: sums over each list in index order (symmetric: p <= c)
+  constexpr int NUP = SD12 * (SD12 + 1) / 2;
+  for (int q = tid; q < 5 * NUP; q += NT) {
+    const int slot = 1 + q / NUP;
+    int r = q % NUP, p = 0;
+    while (r >= SD12 - p) r -= SD12 - p, ++p;
+    const int c = p + r;
+    const bool dp = (p % Q12) >= 6, dc = (c % Q12) >= 6;
+    if (FULL ? (dp || dc) : (!dp && !dc)) continue;
+    const double* e = lists + (size_t)LC.off[slot] * LSTRIDE12;
+    double v = 0.0;
+    for (int b = 0; b < LC.cap[slot]; ++b, e += LSTRIDE12) v = fma(e[2 * Q12 + p], e[c], v);
+    out[slot * SS12 + p * SD12 + c] = v;
+    out[slot * SS12 + c * SD12 + p] = v;
+  }
+}
+
+template <typename DT, bool FULL, typename AT>
+__global__ void __launch_bounds__(NT) k_coarse_slots12(LatView lv, const DT* __restrict__ delta,
+                                                       const DT* __restrict__ delta_rf, double* __restrict__ slots,
+                                                       const IterCtl* ctl) {
+  slots12_body<DT, FULL, AT>(lv, delta, delta_rf, slots, ctl, blockIdx.x);
+}
+
 // Batched (per-iteration pass, FULL = false): the sets of every problem.
 template <typename DT, typename AT>
 __global__ void __launch_bounds__(NT) kb_coarse_slots(const BatchProb* __restrict__ P,
@@ -363,9 +549,10 @@ __global__ void __launch_bounds__(NT) kb_coarse_slots(const BatchProb* __restric
 }
 
 // Band (lower, column-major: band[c*(bw+1) + k] = A[c+k][c]) of K_aa from the
-// base (modes 1-6) and per-iteration (modes 7-9) slots.
-__device__ inline double slot_entry(const double* base, const double* it, int I, int slot, int p, int c) {
-  const size_t o = ((size_t)I * NSLOTS + slot) * SLOT_SIZE + (size_t)p * SLOT_DIM + c;
+// base (modes 1-6) and per-iteration (modes 7-q) slots; q modes per set, slots
+// of 2q x 2q.
+__device__ inline double slot_entry(const double* base, const double* it, int q, int I, int slot, int p, int c) {
+  const size_t o = ((size_t)I * NSLOTS + slot) * slot_size(q) + (size_t)p * slot_dim(q) + c;
   return base[o] + it[o];
 }
 
@@ -373,7 +560,8 @@ __device__ __forceinline__ void band_from_slots_body(const LatView lv, const dou
                                                      const double* __restrict__ it, double* __restrict__ band,
                                                      int bw, const IterCtl* ctl, int bx, int gx) {
   if (ctl && *(volatile const int*)&ctl->done) return;
-  const int n = NMODES * lv.M;
+  const int nm = lv.q;
+  const int n = nm * lv.M;
   const size_t total = (size_t)n * (bw + 1);
   for (size_t q = bx * (size_t)blockDim.x + threadIdx.x; q < total;
        q += (size_t)gx * blockDim.x) {
@@ -381,30 +569,30 @@ __device__ __forceinline__ void band_from_slots_body(const LatView lv, const dou
     const int row = col + k;
     double v = 0.0;
     if (row < n) {
-      const int I = col / NMODES, m = col % NMODES;
-      const int J = row / NMODES, l = row % NMODES;
+      const int I = col / nm, m = col % nm;
+      const int J = row / nm, l = row % nm;
       const int Ix = I % lv.Mx, Iy = I / lv.Mx, Jx = J % lv.Mx, Jy = J / lv.Mx;
       if (J == I) {
-        v = slot_entry(base, it, I, SLOT_SELF, l, m);
-        for (int s = SLOT_E; s < NSLOTS; ++s) v += slot_entry(base, it, I, s, l, m);
+        v = slot_entry(base, it, nm, I, SLOT_SELF, l, m);
+        for (int s = SLOT_E; s < NSLOTS; ++s) v += slot_entry(base, it, nm, I, s, l, m);
         // contributions of neighbours that own bars into I
         const int kx[5] = {-1, 1, 0, -1, 1};   // owner offset for E, W, N, NE, NW
         const int ky[5] = {0, 0, -1, -1, -1};
         for (int s = 0; s < 5; ++s) {
           const int Kx = Ix + kx[s], Ky = Iy + ky[s];
           if (Kx < 0 || Kx >= lv.Mx || Ky < 0 || Ky >= lv.My) continue;
-          v += slot_entry(base, it, Ky * lv.Mx + Kx, SLOT_E + s, 9 + l, 9 + m);
+          v += slot_entry(base, it, nm, Ky * lv.Mx + Kx, SLOT_E + s, nm + l, nm + m);
         }
       } else {
         const int dx = Jx - Ix, dy = Jy - Iy;
         if (dy == 0 && dx == 1) {
-          v = slot_entry(base, it, I, SLOT_E, 9 + l, m) + slot_entry(base, it, J, SLOT_W, l, 9 + m);
+          v = slot_entry(base, it, nm, I, SLOT_E, nm + l, m) + slot_entry(base, it, nm, J, SLOT_W, l, nm + m);
         } else if (dy == 1 && dx == 0) {
-          v = slot_entry(base, it, I, SLOT_N, 9 + l, m);
+          v = slot_entry(base, it, nm, I, SLOT_N, nm + l, m);
         } else if (dy == 1 && dx == 1) {
-          v = slot_entry(base, it, I, SLOT_NE, 9 + l, m);
+          v = slot_entry(base, it, nm, I, SLOT_NE, nm + l, m);
         } else if (dy == 1 && dx == -1) {
-          v = slot_entry(base, it, I, SLOT_NW, 9 + l, m);
+          v = slot_entry(base, it, nm, I, SLOT_NW, nm + l, m);
         }
       }
     }
@@ -453,16 +641,16 @@ __global__ void k_dense_from_band(int n, int bw, const double* __restrict__ band
 __device__ __forceinline__ void coarse_diag_body(int n, int bw, const double* __restrict__ band,
                                                  const double* __restrict__ P, double* __restrict__ scale,
                                                  double* __restrict__ b, double* __restrict__ x,
-                                                 int* __restrict__ dropped, unsigned mode_mask, const IterCtl* ctl,
-                                                 int bx, int gx) {
+                                                 int* __restrict__ dropped, unsigned mode_mask, int nm,
+                                                 const IterCtl* ctl, int bx, int gx) {
   if (ctl && *(volatile const int*)&ctl->done) return;
   for (int i = bx * blockDim.x + threadIdx.x; i < n; i += gx * blockDim.x) {
     const double D = band[(size_t)i * (bw + 1)];
-    const int g0 = i - i % NMODES;
+    const int g0 = i - i % nm;
     double dmax = 0.0;
-    for (int m = 0; m < NMODES && g0 + m < n; ++m)
+    for (int m = 0; m < nm && g0 + m < n; ++m)
       if ((mode_mask >> m) & 1u) dmax = fmax(dmax, band[(size_t)(g0 + m) * (bw + 1)]);
-    const bool drop = !((mode_mask >> (i % NMODES)) & 1u) || !(D > 1e-300) || !(D > 1e-28 * dmax);
+    const bool drop = !((mode_mask >> (i % nm)) & 1u) || !(D > 1e-300) || !(D > 1e-28 * dmax);
     const double s = drop ? 0.0 : 1.0 / sqrt(D);
     scale[i] = s;
     b[i] = s * P[i];
@@ -474,13 +662,13 @@ __device__ __forceinline__ void coarse_diag_body(int n, int bw, const double* __
 __global__ void k_coarse_diag(int n, int bw, const double* __restrict__ band,
                               const double* __restrict__ P, double* __restrict__ scale,
                               double* __restrict__ b, double* __restrict__ x, int* __restrict__ dropped,
-                              unsigned mode_mask, const IterCtl* ctl) {
-  coarse_diag_body(n, bw, band, P, scale, b, x, dropped, mode_mask, ctl, blockIdx.x, gridDim.x);
+                              unsigned mode_mask, int nm, const IterCtl* ctl) {
+  coarse_diag_body(n, bw, band, P, scale, b, x, dropped, mode_mask, nm, ctl, blockIdx.x, gridDim.x);
 }
 __global__ void kb_coarse_diag(const BatchProb* __restrict__ Pb, const BatchItem* __restrict__ items) {
   const BatchItem it = items[blockIdx.x];
   const BatchProb& q = Pb[it.prob];
-  coarse_diag_body(q.n_c, q.bw, q.band, q.P, q.scale, q.b, q.x, q.dropped, q.mode_mask, q.ctl, it.bx, it.gx);
+  coarse_diag_body(q.n_c, q.bw, q.band, q.P, q.scale, q.b, q.x, q.dropped, q.mode_mask, NMODES, q.ctl, it.bx, it.gx);
 }
 
 // Modes that depend on earlier modes of the same set get a = 0.  Sets have
@@ -488,12 +676,14 @@ __global__ void kb_coarse_diag(const BatchProb* __restrict__ Pb, const BatchItem
 // the Jacobi-scaled 9 x 9 diagonal block of every set is factored in FP64 in
 // mode order, and a mode whose pivot is <= 1e-14 is dropped (the rule of the
 // full upper-level system, decided where FP64 resolves it).
+template <int Q = NMODES>
 __device__ __forceinline__ void set_drops_body(int nsets, int bw, const double* __restrict__ band,
                                                const double* __restrict__ scale, int* __restrict__ dropped,
                                                const IterCtl* ctl, int bx, int gx) {
   if (ctl && *(volatile const int*)&ctl->done) return;
   const int I = bx * blockDim.x + threadIdx.x;
   if (I >= nsets) return;
+  constexpr int NMODES = Q;  // modes per set (shadows the 9 of the displacement-controlled form)
   double A[NMODES][NMODES];
   bool dr[NMODES];
 #pragma unroll
@@ -533,10 +723,11 @@ __device__ __forceinline__ void set_drops_body(int nsets, int bw, const double* 
   for (int m = 0; m < NMODES; ++m) dropped[NMODES * I + m] = dr[m] ? 1 : 0;
 }
 
+template <int Q>
 __global__ void k_coarse_set_drops(int nsets, int bw, const double* __restrict__ band,
                                    const double* __restrict__ scale, int* __restrict__ dropped,
                                    const IterCtl* ctl) {
-  set_drops_body(nsets, bw, band, scale, dropped, ctl, blockIdx.x, gridDim.x);
+  set_drops_body<Q>(nsets, bw, band, scale, dropped, ctl, blockIdx.x, gridDim.x);
 }
 __global__ void kb_coarse_set_drops(const BatchProb* __restrict__ P, const BatchItem* __restrict__ items) {
   const BatchItem it = items[blockIdx.x];
@@ -595,19 +786,33 @@ __global__ void kb_coarse_scale_band(const BatchProb* __restrict__ P, const Batc
 int coarse_bw(const LatView& lv) {
   // set I couples to I + Mx + 1 at most (NE neighbour)
   const int reach = (lv.M > 1) ? (lv.Mx + 1 < lv.M - 1 ? lv.Mx + 1 : lv.M - 1) : 0;
-  return NMODES * (reach + 1) - 1;
+  return lv.q * (reach + 1) - 1;
 }
 
 size_t coarse_slots_smem(const LatView& lv) {
   const int w = lv.sx < lv.nx ? lv.sx : lv.nx;
   const int h = lv.sy < lv.ny ? lv.sy : lv.ny;
   // interface lists, then the reduction buffer and the CTA totals
+  if (lv.q == NMODES_RF)
+    return ((size_t)list_caps(w, h).total * LSTRIDE12 + RED_CHUNK * NT + NGEN12_DELTA) * sizeof(double);
   return ((size_t)list_caps(w, h).total * LSTRIDE + RED_CHUNK * NT + NREG + NGEN_FULL) * sizeof(double);
 }
 
 cudaError_t launch_coarse_slots(cudaStream_t s, const LatView& lv, const void* delta, bool delta_fp32,
-                                bool full, double* slots, const IterCtl* ctl) {
+                                bool full, double* slots, const IterCtl* ctl, const void* delta_rf) {
   const size_t smem = coarse_slots_smem(lv);
+  if (lv.q == NMODES_RF) {
+    if (delta_fp32) {
+      const float2 *d = (const float2*)delta, *f = (const float2*)delta_rf;
+      if (full) k_coarse_slots12<float2, true, double><<<lv.M, NT, smem, s>>>(lv, d, f, slots, ctl);
+      else k_coarse_slots12<float2, false, float><<<lv.M, NT, smem, s>>>(lv, d, f, slots, ctl);
+    } else {
+      const double2 *d = (const double2*)delta, *f = (const double2*)delta_rf;
+      if (full) k_coarse_slots12<double2, true, double><<<lv.M, NT, smem, s>>>(lv, d, f, slots, ctl);
+      else k_coarse_slots12<double2, false, double><<<lv.M, NT, smem, s>>>(lv, d, f, slots, ctl);
+    }
+    return cudaGetLastError();
+  }
   if (delta_fp32) {
     if (full) k_coarse_slots<float2, true, double><<<lv.M, NT, smem, s>>>(lv, (const float2*)delta, slots, ctl);
     else k_coarse_slots<float2, false, float><<<lv.M, NT, smem, s>>>(lv, (const float2*)delta, slots, ctl);
@@ -620,6 +825,10 @@ cudaError_t launch_coarse_slots(cudaStream_t s, const LatView& lv, const void* d
 
 cudaError_t configure_coarse_assemble(int max_smem) {
   cudaError_t e;
+  if ((e = set_max_dynamic_smem(k_coarse_slots12<float2, true, double>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_coarse_slots12<float2, false, float>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_coarse_slots12<double2, true, double>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_coarse_slots12<double2, false, double>, max_smem)) != cudaSuccess) return e;
   e = set_max_dynamic_smem(k_coarse_slots<float2, true, double>, max_smem);
   if (e != cudaSuccess) return e;
   e = set_max_dynamic_smem(k_coarse_slots<float2, false, float>, max_smem);
@@ -693,12 +902,15 @@ cudaError_t launch_coarse_dense_from_band(cudaStream_t s, int n, int bw, const d
 
 cudaError_t launch_coarse_scale(cudaStream_t s, int n, int bw, bool fp64, const double* band, const double* P,
                                 double* sband, void* frow, double* scale, double* b, double* x, int* dropped,
-                                unsigned mode_mask, const IterCtl* ctl) {
-  k_coarse_diag<<<grid_for(n), 256, 0, s>>>(n, bw, band, P, scale, b, x, dropped, mode_mask, ctl);
+                                unsigned mode_mask, int nm, const IterCtl* ctl) {
+  k_coarse_diag<<<grid_for(n), 256, 0, s>>>(n, bw, band, P, scale, b, x, dropped, mode_mask, nm, ctl);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int nsets = n / NMODES;
-  k_coarse_set_drops<<<(nsets + 127) / 128, 128, 0, s>>>(nsets, bw, band, scale, dropped, ctl);
+  const int nsets = n / nm;
+  if (nm == NMODES_RF)
+    k_coarse_set_drops<NMODES_RF><<<(nsets + 127) / 128, 128, 0, s>>>(nsets, bw, band, scale, dropped, ctl);
+  else
+    k_coarse_set_drops<NMODES><<<(nsets + 127) / 128, 128, 0, s>>>(nsets, bw, band, scale, dropped, ctl);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   double* sbandR = sband + (size_t)n * (bw + 1);

@@ -46,8 +46,8 @@ constexpr float ND_TAU = 1e-6f;   // FP32 pivot below which a mode is dropped (a
 
 __device__ inline bool nd_done(const IterCtl* ctl) { return ctl && *(volatile const int*)&ctl->done; }
 
-// global unknown of front position p: set st[p / 9], mode p % 9
-__device__ inline int nd_glob(const int* st, int p) { return st[p / NMODES] * NMODES + p % NMODES; }
+// global unknown of front position p: set st[p / nm], mode p % nm (nm modes per set)
+__device__ inline int nd_glob(const int* st, int p, int nm) { return st[p / nm] * nm + p % nm; }
 
 // entry (gi, gj) of the scaled matrix from its FP32 row-layout band
 __device__ inline float nd_a(const float* __restrict__ frow, int bw, int gi, int gj) {
@@ -133,7 +133,7 @@ __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* _
                                                int* __restrict__ dropped, float* sm, int* gidx, int* cpos,
                                                float (&Dinv)[PB][PB + 1], unsigned& dmask) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nS = NMODES * nd.ns, nf = NMODES * (nd.ns + nd.nb);
+  const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
   float* fg = F + nd.f_off;
   const int* st = sets + nd.s_off;
   auto at = [&](int i, int j) -> float& {
@@ -141,7 +141,7 @@ __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* _
     else return fg[(size_t)i * nf + j];
   };
   // the global unknown of every front position
-  for (int p = tid; p < nf; p += NDT) gidx[p] = nd_glob(st, p);
+  for (int p = tid; p < nf; p += NDT) gidx[p] = nd_glob(st, p, nm);
   __syncthreads();
 
   // ---- assemble: original entries of the S columns, zero B x B (NU loads in flight per lane) ----
@@ -166,10 +166,10 @@ __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* _
   // ---- extend-add of the children's update matrices (one child after the other) ----
   for (int c = 0; c < nd.nchild; ++c) {
     const NDNode ch = nodes[nd.child[c]];
-    const int nSc = NMODES * ch.ns, nbc = NMODES * ch.nb, nfc = nSc + nbc;
+    const int nSc = nm * ch.ns, nbc = nm * ch.nb, nfc = nSc + nbc;
     const float* U = F + ch.f_off + (size_t)nSc * nfc + nSc;
     const int* mp = maps + nd.map_off[c];
-    for (int k = tid; k < nbc; k += NDT) cpos[k] = NMODES * mp[k / NMODES] + k % NMODES;
+    for (int k = tid; k < nbc; k += NDT) cpos[k] = nm * mp[k / nm] + k % nm;
     __syncthreads();
     for (int k = warp; k < nbc; k += NDW) {
       const int pk = cpos[k];
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(NDT) k_nd_factor(const NDNode* __restrict__ no
   __shared__ float Dinv[PB][PB + 1];
   __shared__ unsigned dmask;
   const NDNode nd = nodes[lvl[lbeg + blockIdx.x]];
-  const long long nf = NMODES * (long long)(nd.ns + nd.nb);
+  const long long nf = nd.nm * (long long)(nd.ns + nd.nb);
   // the last 2 nf floats of the region hold the front's unknown indices and a child's positions
   int* gidx = reinterpret_cast<int*>(ndsm + (cap - 2 * nf));
   int* cpos = gidx + nf;
@@ -368,14 +368,14 @@ __global__ void __launch_bounds__(NDT) k_nd_forward(const NDNode* __restrict__ n
   __shared__ float yb[PB];
   const NDNode nd = nodes[lvl[lbeg + blockIdx.x]];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nS = NMODES * nd.ns, nf = NMODES * (nd.ns + nd.nb);
+  const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
   const float* f = F + nd.f_off;
   const int* st = sets + nd.s_off;
   float* fv = ndsm;
   int* gidx = reinterpret_cast<int*>(ndsm + (cap - nf));
   const float* Lp = f;
   const int ld = nf;
-  for (int p = tid; p < nf; p += NDT) gidx[p] = nd_glob(st, p);
+  for (int p = tid; p < nf; p += NDT) gidx[p] = nd_glob(st, p, nm);
   __syncthreads();
   for (int p = tid; p < nf; p += NDT) {
     float v = 0.f;
@@ -388,9 +388,9 @@ __global__ void __launch_bounds__(NDT) k_nd_forward(const NDNode* __restrict__ n
   __syncthreads();
   for (int c = 0; c < nd.nchild; ++c) {
     const NDNode ch = nodes[nd.child[c]];
-    const int nbc = NMODES * ch.nb;
+    const int nbc = nm * ch.nb;
     const int* mp = maps + nd.map_off[c];
-    for (int k = tid; k < nbc; k += NDT) fv[NMODES * mp[k / NMODES] + k % NMODES] += W[ch.w_off + k];
+    for (int k = tid; k < nbc; k += NDT) fv[nm * mp[k / nm] + k % nm] += W[ch.w_off + k];
     __syncthreads();
   }
   for (int k0 = 0; k0 < nS; k0 += PB) {
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(NDT) k_nd_backward(const NDNode* __restrict__ 
   __shared__ float xb[PB];
   const NDNode nd = nodes[lvl[lbeg + blockIdx.x]];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nS = NMODES * nd.ns, nB = NMODES * nd.nb, nf = nS + nB;
+  const int nm = nd.nm, nS = nm * nd.ns, nB = nm * nd.nb, nf = nS + nB;
   const float* f = F + nd.f_off;
   const int* st = sets + nd.s_off;
   float* tv = ndsm;                 // nS
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(NDT) k_nd_backward(const NDNode* __restrict__ 
   int* gidx = reinterpret_cast<int*>(ndsm + (cap - nf));
   const float* Lp = f;
   const int ld = nf;
-  for (int p = tid; p < nf; p += NDT) gidx[p] = nd_glob(st, p);
+  for (int p = tid; p < nf; p += NDT) gidx[p] = nd_glob(st, p, nm);
   __syncthreads();
   for (int k = tid; k < nB; k += NDT) xB[k] = xc[gidx[nS + k]];
   __syncthreads();
@@ -590,11 +590,12 @@ bool nd_plan_build(const LatView& lv, NDPlanHost* P) {
     d.s_off = (int)P->sets.size();
     P->sets.insert(P->sets.end(), hn[k].S.begin(), hn[k].S.end());
     P->sets.insert(P->sets.end(), hn[k].B.begin(), hn[k].B.end());
-    const long long nf = (long long)NMODES * (d.ns + d.nb);
+    d.nm = lv.q;
+    const long long nf = (long long)d.nm * (d.ns + d.nb);
     d.f_off = (long long)P->f_elems;
     P->f_elems += (size_t)(nf * nf);
     d.w_off = (long long)P->w_elems;
-    P->w_elems += (size_t)NMODES * d.nb;
+    P->w_elems += (size_t)d.nm * d.nb;
     P->max_front = std::max(P->max_front, (int)nf);
     d.nchild = hn[k].nchild;
   }
@@ -647,7 +648,7 @@ bool nd_plan_smem(NDPlanHost* P, int max_smem) {
     long long nfac = 0, nsol = 0;
     for (int k = P->level_begin[h]; k < P->level_begin[h + 1]; ++k) {
       const NDNode& d = P->nodes[P->lvl_nodes[k]];
-      const long long nS = (long long)NMODES * d.ns, nf = (long long)NMODES * (d.ns + d.nb);
+      const long long nS = (long long)d.nm * d.ns, nf = (long long)d.nm * (d.ns + d.nb);
       const long long fneed = nd_factor_need(nf, cap);
       const long long sneed = nd_solve_need(nS, nf);
       if (fneed > cap || sneed > cap) return false;

@@ -19,7 +19,8 @@
 
 namespace hms {
 
-constexpr int NMODES = 9;
+constexpr int NMODES = 9;     // incremental modes per set of the displacement-controlled form
+constexpr int NMODES_RF = 12; // with the force-controlled modes 10-12 (Eqs. 15-18)
 constexpr double SQ3_2 = 0.86602540378443864676;  // sqrt(3)/2
 constexpr int MAX_SX = 64;                           // set width limit (nodes)
 constexpr int MAX_RX = 80;                           // relaxation region width limit (nodes)
@@ -29,6 +30,9 @@ constexpr int MAX_NB = 2 * MAX_RX;                   // DOFs per region row
 enum Slot { SLOT_SELF = 0, SLOT_E, SLOT_W, SLOT_N, SLOT_NE, SLOT_NW, NSLOTS };
 constexpr int SLOT_DIM = 18;
 constexpr int SLOT_SIZE = SLOT_DIM * SLOT_DIM;
+// slot shape for q modes per set (q = 9: SLOT_DIM x SLOT_DIM)
+__host__ __device__ inline int slot_dim(int q) { return 2 * q; }
+__host__ __device__ inline int slot_size(int q) { return 4 * q * q; }
 
 // device error flags (bit mask in a device int)
 enum DevErr { DEVERR_NOT_SPD = 1, DEVERR_TIMEOUT = 2, DEVERR_NONFINITE = 4, DEVERR_COARSE = 8 };
@@ -37,6 +41,7 @@ enum DevErr { DEVERR_NOT_SPD = 1, DEVERR_TIMEOUT = 2, DEVERR_NONFINITE = 4, DEVE
 struct LatView {
   int nx, ny, sx, sy, Mx, My, M;
   int ov;          // relaxation region: the set's tile grown by ov nodes (Sec. 2.2)
+  int q = 9;       // incremental modes per set: 9, or 12 with the force-controlled modes
   double L;        // bar length
   double k_u;      // EA/L when kbar == nullptr
   const double* kbar;
@@ -153,7 +158,7 @@ cudaError_t launch_update_residual(cudaStream_t s, const LatView& lv, const doub
                                    double2* u_out, const double2* p, const void* delta,
                                    bool delta_fp32, const double* a, double2* r, double* partials,
                                    unsigned* ticket, double* norms_out, IterCtl* ctl, double* hist,
-                                   int hist_cap, int* u_cur);
+                                   int hist_cap, const void* delta_rf);
 int update_residual_blocks(const LatView& lv);
 cudaError_t launch_reactions(cudaStream_t s, const LatView& lv, const double2* u, double2* f);
 cudaError_t launch_load_norms(cudaStream_t s, const LatView& lv, double2* p, double* partials,
@@ -163,9 +168,19 @@ int residual_noalloc_tiles(const LatView& lv);
 cudaError_t residual_noalloc_scratch(int device, double** partials, unsigned** ticket);
 cudaError_t launch_residual_noalloc(cudaStream_t s, const LatView& lv, const double2* u, const double2* p,
                                     double2* r, double* partials, unsigned* ticket, double* norms_out);
-// setup.cu
+// setup.cu (cut = true: the set cut free, i.e. k^Inner + Delta k of Eq. 15, only the
+// set's own bars; lv.fix then marks the constrained and the pinned DOFs)
 cudaError_t launch_set_factor(cudaStream_t s, const LatView& lv, const long long* set_off,
-                              double* f64, float* f32, double* scratch, int grid, int* err);
+                              double* f64, float* f32, double* scratch, int grid, int* err, bool cut = false);
+// force.cu: the force-controlled relaxation's projections (Eqs. 16-18).  M: per set the
+// 3 x 3 matrix of the projection onto the rigid motions the set's supports leave free
+// (zero for anchored sets); fixF: supports | pinned DOFs.
+cudaError_t launch_force_in(cudaStream_t s, const LatView& lv, const double2* r, const double* M,
+                            const uint8_t* fixF, double2* rproj, const IterCtl* ctl);
+cudaError_t launch_force_out(cudaStream_t s, const LatView& lv, void* drf, bool fp32, const double* M,
+                             const double2* r, double* P, const IterCtl* ctl);
+bool force_set_data(const LatView& lv, const std::vector<uint8_t>& fix, const std::vector<double2>& rep,
+                    std::vector<double>& M, std::vector<uint8_t>& fixF);
 // relax.cu
 cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set_off,
                          const double* f64, const float* f32, const double2* r, void* delta,
@@ -176,7 +191,7 @@ bool relax_chunks_possible(const LatView& lv, bool fp32);
 long long relax_y_stride(const LatView& lv);
 // coarse.cu
 cudaError_t launch_coarse_slots(cudaStream_t s, const LatView& lv, const void* delta, bool delta_fp32,
-                                bool full, double* slots, const IterCtl* ctl);
+                                bool full, double* slots, const IterCtl* ctl, const void* delta_rf = nullptr);
 int coarse_bw(const LatView& lv);
 cudaError_t launch_coarse_band_from_slots(cudaStream_t s, const LatView& lv, const double* base,
                                           const double* slots, double* band, const IterCtl* ctl);
@@ -186,7 +201,7 @@ cudaError_t launch_coarse_dense_from_band(cudaStream_t s, int n, int bw, const d
                                           double* dense);
 cudaError_t launch_coarse_scale(cudaStream_t s, int n, int bw, bool fp64, const double* band, const double* P,
                                 double* sband, void* frow, double* scale, double* b, double* x, int* dropped,
-                                unsigned mode_mask, const IterCtl* ctl);
+                                unsigned mode_mask, int nm, const IterCtl* ctl);
 cudaError_t launch_coarse_factor(cudaStream_t s, int n, int bw, bool fp64, void* lrow, void* lcol, void* dinv,
                                  int* dropped, bool write_lrow, const IterCtl* ctl);
 cudaError_t launch_coarse_solve(cudaStream_t s, int n, int bw, bool fp64, const void* lcol, const void* lrow,
@@ -316,6 +331,7 @@ struct NDNode {
   int ns, nb, s_off, nchild;
   int child[2];
   int map_off[2];
+  int nm, pad;  // modes per set (9 or 12)
   long long f_off, w_off;
 };
 struct NDPlanHost {

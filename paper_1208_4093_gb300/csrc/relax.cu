@@ -480,7 +480,10 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
   }
   // P = V^T r (Eq. 7) from r and the delta just written, node by node:
   // virtual lane v sums nodes v, v + VL, ...; each virtual warp's 32 lanes go
-  // through one shuffle tree, and the 8 virtual warps are added in order
+  // through one shuffle tree, and the 8 virtual warps are added in order.
+  // Modes 1-9 of set I at P[q I + m] (q = 9, or 12 with the force-controlled
+  // modes); no P (the force-controlled relaxation's solve) with P = nullptr.
+  if (P == nullptr) return;
   __syncthreads();
   const T2* d2 = reinterpret_cast<const T2*>(delta);
   for (int vbase = 0; vbase < VL && !producer; vbase += NT) {
@@ -518,7 +521,7 @@ __device__ __forceinline__ void relax_body(const LatView lv, const long long* __
   if (tid < NMODES) {
     double sum = 0.0;
     for (int ww = 0; ww < VL / 32; ++ww) sum += pred[ww * NMODES + tid];
-    P[(size_t)NMODES * I + tid] = sum;
+    P[(size_t)lv.q * I + tid] = sum;
   }
 }
 

@@ -61,13 +61,14 @@ __device__ inline double2 load_delta<float2>(const float2* d, size_t n) {
 }
 
 // Eq. 3 at node (i, j): u += sum_m a_m^(I) uhat_m^(I) with the modes of
-// Eqs. 9, 10, 13, 14 (zero on constrained DOFs).
-template <typename DT>
+// Eqs. 9, 10, 13, 14 (zero on constrained DOFs), and with RF the force-
+// controlled modes of Eqs. 17-18 (delta^RF and its gradient-weighted copies).
+template <typename DT, bool RF>
 __device__ inline double2 apply_update(const LatView& lv, double2 v, int i, int j, const DT* delta,
-                                       const double* __restrict__ a) {
+                                       const DT* delta_rf, const double* __restrict__ a) {
   const size_t n = (size_t)j * lv.nx + i;
   const int I = set_of(lv, i, j);
-  const double* aI = a + (size_t)NMODES * I;
+  const double* aI = a + (size_t)lv.q * I;
   const double2 c = lv.rep[I];
   const double xi = node_x(lv, i, j) - c.x;
   const double eta = node_y(lv, j) - c.y;
@@ -76,14 +77,21 @@ __device__ inline double2 apply_update(const LatView& lv, double2 v, int i, int 
   const double cd = fma(__ldg(aI + 8), eta, fma(__ldg(aI + 7), xi, __ldg(aI + 6)));
   if (!(fm & 1u)) v.x += fma(cd, d.x, fma(__ldg(aI + 3), eta, fma(__ldg(aI + 2), xi, __ldg(aI + 0))));
   if (!(fm & 2u)) v.y += fma(cd, d.y, fma(__ldg(aI + 5), eta, fma(__ldg(aI + 4), xi, __ldg(aI + 1))));
+  if constexpr (RF) {
+    const double2 f = load_delta(delta_rf, n);
+    const double cf = fma(__ldg(aI + 11), eta, fma(__ldg(aI + 10), xi, __ldg(aI + 9)));
+    if (!(fm & 1u)) v.x = fma(cf, f.x, v.x);
+    if (!(fm & 2u)) v.y = fma(cf, f.y, v.y);
+  }
   return v;
 }
 
 // The kernel body for tile (bx, by) of a gx x gy grid (the whole lattice).
-template <typename DT>
+template <typename DT, bool RF = false>
 __device__ __forceinline__ void update_residual_body(
     const LatView lv, const double2* __restrict__ u_in, double2* __restrict__ u_out,
-    const double2* __restrict__ p, const DT* __restrict__ delta, const double* __restrict__ a,
+    const double2* __restrict__ p, const DT* __restrict__ delta, const DT* __restrict__ delta_rf,
+    const double* __restrict__ a,
     double2* __restrict__ r, double* __restrict__ partials, unsigned* ticket, double* norms_out,
     IterCtl* ctl, double* hist, int hist_cap, int bx, int by, int gx, int gy) {
   __shared__ double2 U[TY + 2][TX + 2];
@@ -104,7 +112,7 @@ __device__ __forceinline__ void update_residual_body(
     double2 v = make_double2(0.0, 0.0);
     if (i >= 0 && i < lv.nx && j >= 0 && j < lv.ny) {
       v = u_in[(size_t)j * lv.nx + i];
-      if (upd) v = apply_update(lv, v, i, j, delta, a);
+      if (upd) v = apply_update<DT, RF>(lv, v, i, j, delta, delta_rf, a);
     }
     U[ly][lx] = v;
   }
@@ -198,14 +206,14 @@ __device__ __forceinline__ void update_residual_body(
   }
 }
 
-template <typename DT>
+template <typename DT, bool RF>
 __global__ void __launch_bounds__(NT) k_update_residual(
     LatView lv, const double2* __restrict__ u_in, double2* __restrict__ u_out,
-    const double2* __restrict__ p, const DT* __restrict__ delta, const double* __restrict__ a,
-    double2* __restrict__ r, double* __restrict__ partials, unsigned* ticket, double* norms_out,
-    IterCtl* ctl, double* hist, int hist_cap) {
-  update_residual_body<DT>(lv, u_in, u_out, p, delta, a, r, partials, ticket, norms_out, ctl, hist, hist_cap,
-                           blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+    const double2* __restrict__ p, const DT* __restrict__ delta, const DT* __restrict__ delta_rf,
+    const double* __restrict__ a, double2* __restrict__ r, double* __restrict__ partials, unsigned* ticket,
+    double* norms_out, IterCtl* ctl, double* hist, int hist_cap) {
+  update_residual_body<DT, RF>(lv, u_in, u_out, p, delta, delta_rf, a, r, partials, ticket, norms_out, ctl, hist,
+                               hist_cap, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
 // Batched: update k of a CUDA-graph round (u ping-pongs between u[k & 1] and
@@ -215,8 +223,8 @@ __global__ void __launch_bounds__(NT) kb_update_residual(const BatchProb* __rest
                                                          const BatchItem* __restrict__ items, int k) {
   const BatchItem it = items[blockIdx.x];
   const BatchProb& q = P[it.prob];
-  update_residual_body<DT>(q.lv, q.u[k & 1], q.u[(k + 1) & 1], q.p, (const DT*)q.delta, q.a, q.r, q.partials,
-                           q.ticket, nullptr, q.ctl, q.hist, q.hist_cap, it.bx, it.by, it.gx, it.gy);
+  update_residual_body<DT>(q.lv, q.u[k & 1], q.u[(k + 1) & 1], q.p, (const DT*)q.delta, nullptr, q.a, q.r,
+                           q.partials, q.ticket, nullptr, q.ctl, q.hist, q.hist_cap, it.bx, it.by, it.gx, it.gy);
 }
 
 // Masks the loads on constrained DOFs and computes ||p||_1, ||p||_2 into ctl.
@@ -331,15 +339,26 @@ cudaError_t launch_update_residual(cudaStream_t s, const LatView& lv, const doub
                                    double2* u_out, const double2* p, const void* delta,
                                    bool delta_fp32, const double* a, double2* r, double* partials,
                                    unsigned* ticket, double* norms_out, IterCtl* ctl, double* hist,
-                                   int hist_cap, int* /*u_cur*/) {
+                                   int hist_cap, const void* delta_rf) {
   dim3 grid((lv.nx + TX - 1) / TX, (lv.ny + TY - 1) / TY);
-  if (delta_fp32)
-    k_update_residual<float2><<<grid, NT, 0, s>>>(lv, u_in, u_out, p, (const float2*)delta, a, r,
-                                                  partials, ticket, norms_out, ctl, hist, hist_cap);
-  else
-    k_update_residual<double2><<<grid, NT, 0, s>>>(lv, u_in, u_out, p, (const double2*)delta, a,
-                                                   r, partials, ticket, norms_out, ctl, hist,
-                                                   hist_cap);
+  const bool rf = lv.q == NMODES_RF;
+  if (delta_fp32) {
+    if (rf)
+      k_update_residual<float2, true><<<grid, NT, 0, s>>>(lv, u_in, u_out, p, (const float2*)delta,
+                                                          (const float2*)delta_rf, a, r, partials, ticket,
+                                                          norms_out, ctl, hist, hist_cap);
+    else
+      k_update_residual<float2, false><<<grid, NT, 0, s>>>(lv, u_in, u_out, p, (const float2*)delta, nullptr, a, r,
+                                                           partials, ticket, norms_out, ctl, hist, hist_cap);
+  } else {
+    if (rf)
+      k_update_residual<double2, true><<<grid, NT, 0, s>>>(lv, u_in, u_out, p, (const double2*)delta,
+                                                           (const double2*)delta_rf, a, r, partials, ticket,
+                                                           norms_out, ctl, hist, hist_cap);
+    else
+      k_update_residual<double2, false><<<grid, NT, 0, s>>>(lv, u_in, u_out, p, (const double2*)delta, nullptr, a,
+                                                            r, partials, ticket, norms_out, ctl, hist, hist_cap);
+  }
   return cudaGetLastError();
 }
 

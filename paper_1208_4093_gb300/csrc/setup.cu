@@ -18,6 +18,16 @@
 //
 // One CTA per set (grid-stride over sets), FP64 throughout; the FP32 copy for
 // the mixed path is rounded from the FP64 factor.
+//
+// CUT = true factors k^Inner + Delta k of Eq. 15 instead: Delta k adds to each
+// inner node's diagonal block the blocks k_il of the bars to nodes l outside
+// the set, which cancels their stiffness, so the matrix is that of the set's
+// own bars (the set cut free).  The diagonal blocks then sum only the bars whose
+// other end lies in the region; the couplings are inner bars already.  A set
+// clear of the supports floats (rigid motions); the caller marks as
+// constrained, besides the supports, as many DOFs as the set has free rigid
+// motions ("pinned", chosen so that no rigid motion vanishes on them), which
+// makes the matrix nonsingular (see force.cu for the use of its solution).
 #include "hms_internal.cuh"
 
 namespace hms {
@@ -28,19 +38,28 @@ constexpr double SQ3_4 = 0.43301270189221932338;  // sqrt(3)/4
 
 __device__ inline long long pk(int r, int c) { return (long long)r * (r + 1) / 2 + c; }
 
-// 2x2 diagonal block of K at node (i, j): sum over its six bars of (EA/L) e e^T.
-__device__ inline void node_diag(const LatView& lv, int i, int j, double& dxx, double& dxy,
+// 2x2 diagonal block of K at node (i, j): sum over its six bars of (EA/L) e e^T
+// (CUT: only the bars whose other end lies in the region R).
+template <bool CUT>
+__device__ inline void node_diag(const LatView& lv, int i, int j, const Region& R, double& dxx, double& dxy,
                                  double& dyy) {
   const int off = j & 1;
-  const double kE = bar_k(lv, i, j, 0), kW = bar_k(lv, i - 1, j, 0);
-  const double kNE = bar_k(lv, i, j, 1), kSW = bar_k(lv, i - 1 + off, j - 1, 1);
-  const double kNW = bar_k(lv, i, j, 2), kSE = bar_k(lv, i + off, j - 1, 2);
+  auto in = [&](int ii, int jj) {
+    return !CUT || (ii >= R.i0 && ii < R.i0 + R.w && jj >= R.j0 && jj < R.j0 + R.h);
+  };
+  const double kE = in(i + 1, j) ? bar_k(lv, i, j, 0) : 0.0;
+  const double kW = in(i - 1, j) ? bar_k(lv, i - 1, j, 0) : 0.0;
+  const double kNE = in(i + off, j + 1) ? bar_k(lv, i, j, 1) : 0.0;
+  const double kSW = in(i - 1 + off, j - 1) ? bar_k(lv, i - 1 + off, j - 1, 1) : 0.0;
+  const double kNW = in(i - 1 + off, j + 1) ? bar_k(lv, i, j, 2) : 0.0;
+  const double kSE = in(i + off, j - 1) ? bar_k(lv, i + off, j - 1, 2) : 0.0;
   const double sne = kNE + kSW, snw = kNW + kSE;
   dxx = kE + kW + 0.25 * (sne + snw);
   dxy = SQ3_4 * (sne - snw);
   dyy = 0.75 * (sne + snw);
 }
 
+template <bool CUT>
 __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* __restrict__ set_off,
                                                    double* __restrict__ f64, float* __restrict__ f32,
                                                    double* __restrict__ scratch, int* err) {
@@ -70,7 +89,7 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
       for (int il = tid; il < w; il += NT) {
         const int i = i0 + il;
         double dxx, dxy, dyy;
-        node_diag(lv, i, j, dxx, dxy, dyy);
+        node_diag<CUT>(lv, i, j, R, dxx, dxy, dyy);
         S[pk(2 * il, 2 * il)] = dxx;
         S[pk(2 * il + 1, 2 * il)] = dxy;
         S[pk(2 * il + 1, 2 * il + 1)] = dyy;
@@ -195,15 +214,18 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
 }  // namespace
 
 cudaError_t launch_set_factor(cudaStream_t s, const LatView& lv, const long long* set_off,
-                              double* f64, float* f32, double* scratch, int grid, int* err) {
+                              double* f64, float* f32, double* scratch, int grid, int* err, bool cut) {
   const int nb = 2 * region_w_max(lv);
   const size_t smem = 2 * (size_t)((long long)nb * (nb + 1) / 2) * sizeof(double);
-  k_set_factor<<<grid, NT, smem, s>>>(lv, set_off, f64, f32, scratch, err);
+  if (cut) k_set_factor<true><<<grid, NT, smem, s>>>(lv, set_off, f64, f32, scratch, err);
+  else k_set_factor<false><<<grid, NT, smem, s>>>(lv, set_off, f64, f32, scratch, err);
   return cudaGetLastError();
 }
 
 cudaError_t configure_setup(int max_smem) {
-  return set_max_dynamic_smem(k_set_factor, max_smem);
+  cudaError_t e = set_max_dynamic_smem(k_set_factor<false>, max_smem);
+  if (e != cudaSuccess) return e;
+  return set_max_dynamic_smem(k_set_factor<true>, max_smem);
 }
 
 }  // namespace hms

@@ -113,11 +113,15 @@ def test_mode_mask_trajectory_matches_oracle(hms_ctx, mask, precision):
         assert rel(u[0], ref[k - 1]) < (1e-9 if precision == 0 else 1e-4), (mask, k)
 
 
-def test_mode_mask_rejects_bits_above_nine(hms_ctx):
+def test_mode_mask_rejects_bits_above_twelve(hms_ctx):
+    """Bits 0-8: the displacement-controlled modes; 9-11: the force-controlled
+    ones (q = 12, tests/test_gpu_force.py); nothing above."""
     from paper_1208_4093_gb300 import capi
     with pytest.raises(capi.HmsError) as e:
-        capi.hms_problem_create(hms_ctx, 20, 20, 10, 10, mode_mask=0x3FF)
+        capi.hms_problem_create(hms_ctx, 20, 20, 10, 10, mode_mask=0x1FFF)
     assert e.value.status == capi.HMS_ERR_ARG
+    pr = capi.hms_problem_create(hms_ctx, 20, 20, 10, 10, mode_mask=0x3FF)
+    capi.hms_problem_destroy(pr)
 
 
 def test_relax_overlap_overflow_rejected(hms_ctx):
