@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-force-modes", action="store_true",
+                    help="skip the q = 12 solves (force-controlled modes) on the bench workload")
     ap.add_argument("--no-config-eps", action="store_true",
                     help="skip the solves to the configuration's own R1 < 1e-10")
     ap.add_argument("--ncu-case", choices=["fp64", "mixed"], default=None,
@@ -741,6 +743,25 @@ def run_ours(args, rank, world, local_rank):
         nor, _ = nir_golden(TOL_CONFIG)
         config_eps["oracle_iterations"] = nor
 
+    # ---- the force-controlled modes (q = 12, Eqs. 15-18) on the same workload ----
+    force_modes = None
+    if not args.no_force_modes:
+        force_modes = {"tol": TOL, "what": "q = 12 (mode_mask 0xFFF: modes 10-12 of the force-controlled "
+                                           "relaxation added) against the q = 9 solves above"}
+        for prec, name in ((capi.HMS_FP64, "fp64"), (capi.HMS_MIXED, "mixed")):
+            if name == "mixed" and args.no_mixed:
+                continue
+            prf = capi.hms_problem_create(ctx, c.nx, c.ny, c.sx, c.sy, ea=ea, precision=prec, tol=TOL,
+                                          max_iter=5000, mode_mask=0xFFF)
+            msf, _ = timed(prf, 1, 1)
+            force_modes[name] = {"value": msf[0], "unit": "ms", "iterations": int(its.item()),
+                                 "setup_ms": capi.hms_problem_setup_ms(prf),
+                                 "device_bytes": capi.hms_problem_device_bytes(prf)}
+            capi.hms_problem_destroy(prf)
+        force_modes["q9"] = {"fp64": {"value": statistics.median(ms64), "iterations": nit64},
+                             "mixed": ({"value": mixed["value"], "iterations": mixed["iterations"]}
+                                       if mixed else None)}
+
     # ---- the 64 x 64 lattice (16 x 16-node sets, EA = 1), FP64, to R1 < 1e-8 ----
     from workloads import CASES
     c1 = CASES["lattice64_fp64"]
@@ -873,6 +894,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": statistics.median(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * nd,
                 "d2h_bytes_per_step": 8 * nd},
         "serve": serve,
+        "force_modes": force_modes,
         "gpu_launches": launches,
         "clocks": clocks,
         "dofs_per_s": world * nd / (ms_med * 1e-3),

@@ -5,9 +5,11 @@
  * algorithm for the solution of super large-scale sparse linear equations")
  * for the 2-D triangle-lattice truss of its Sec. 3.1 by the paper's
  * iteration: matrix-free residual, displacement-controlled local relaxation
- * of every set (Eqs. 11-14), and the upper-level ("master") correction over
- * q = 9 incremental modes per set (Eqs. 3-10), stopped by the 1-norm relative
- * residual of Eq. 19.  Every step runs in CUDA kernels on one GPU.
+ * of every set (Eqs. 11-14; with hms_options.mode_mask bits 9-11 also the
+ * force-controlled one, Eqs. 15-18), and the upper-level ("master")
+ * correction over q = 9 (or 12) incremental modes per set (Eqs. 3-10),
+ * stopped by the 1-norm relative residual of Eq. 19.  Every step runs in
+ * CUDA kernels on one GPU.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -22,8 +24,9 @@
  * Sets: rectangular node tiles of set_sx x set_sy nodes, the last tile of a
  *   row / column takes the remainder; set index I = Iy*Mx + Ix with
  *   Mx = ceil(nx/set_sx).  Mode m (0-based) of set I is the coarse unknown
- *   9*I + m: translations x, y (Eq. 9), gradients (xi,0), (eta,0), (0,xi),
- *   (0,eta) (Eq. 10), delta, xi*delta, eta*delta (Eqs. 13-14), with
+ *   q*I + m: translations x, y (Eq. 9), gradients (xi,0), (eta,0), (0,xi),
+ *   (0,eta) (Eq. 10), delta, xi*delta, eta*delta (Eqs. 13-14), and with
+ *   q = 12 delta^RF, xi*delta^RF, eta*delta^RF (Eqs. 17-18), with
  *   xi = x - x^(I), eta = y - y^(I) and (x^(I), y^(I)) the centroid of the
  *   set's nodes.
  * Memory: functions taking `mem_kind` accept either host pointers
