@@ -143,6 +143,16 @@ typedef struct {
   int32_t record_history;    /* 1 = keep the (R1, R2, Pi) row of every residual evaluation on
                                 the device for hms_solve's hist output; 0 = record nothing
                                 (no history buffer; hist rows come back as NaN) */
+  int32_t class_factors;     /* 0 = one factor of k^Inner per set (end of Sec. 2.2);
+                                1 = one factor per class of identical sets, for lattices whose
+                                per-set factors would not fit in device memory: with a uniform
+                                EA, sets of the same width and height, parity of the first
+                                row, lattice edges touched and constrained DOFs have the same
+                                k^Inner, so each class is factored once and its sets are
+                                relaxed together, 64 (FP32) or 32 (FP64) right-hand sides per
+                                CTA.  Needs ea = NULL, relax_overlap = 0 and mode_mask bits
+                                9-11 clear.  The increments equal the per-set ones up to
+                                rounding (another order of the sums) */
 } hms_options;
 
 /* Context: one device, one CUDA stream.  device = CUDA ordinal. */

@@ -56,7 +56,8 @@ class Options(ctypes.Structure):
                 ("coarse_solves", ctypes.c_int32), ("batch", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("coarse_factor", ctypes.c_int32), ("relax_threads", ctypes.c_int32),
                 ("relax_copies", ctypes.c_int32), ("relax_overlap", ctypes.c_int32),
-                ("mode_mask", ctypes.c_uint32), ("record_history", ctypes.c_int32)]
+                ("mode_mask", ctypes.c_uint32), ("record_history", ctypes.c_int32),
+                ("class_factors", ctypes.c_int32)]
 
 
 _lib = None
@@ -197,7 +198,7 @@ def hms_last_error(ctx) -> str:
 
 def _desc_opts(nx, ny, set_sx, set_sy, bar_length=1.0, ea=None, ea_uniform=1.0, fixed=None, fix_bottom_edge=1,
                precision=HMS_FP64, tol=1e-8, max_iter=1000, coarse_solves=0, batch=0, profile=0, coarse_factor=0,
-               relax_threads=0, relax_copies=0, relax_overlap=0, mode_mask=0x1FF, record_history=1):
+               relax_threads=0, relax_copies=0, relax_overlap=0, mode_mask=0x1FF, record_history=1, class_factors=0):
     """LatticeDesc and Options structs (plus the arrays they point to, kept alive by the caller)."""
     ea_a = None if ea is None else np.ascontiguousarray(ea, dtype=np.float64)
     fx_a = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
@@ -210,7 +211,7 @@ def _desc_opts(nx, ny, set_sx, set_sy, bar_length=1.0, ea=None, ea_uniform=1.0, 
                     int(set_sx), int(set_sy))
     o = Options(int(precision), float(tol), int(max_iter), int(coarse_solves), int(batch), int(profile),
                 int(coarse_factor), int(relax_threads), int(relax_copies), int(relax_overlap), int(mode_mask),
-                int(record_history))
+                int(record_history), int(class_factors))
     return d, o, (ea_a, fx_a)
 
 
@@ -218,7 +219,7 @@ def hms_problem_create(ctx, nx, ny, set_sx, set_sy, **kw):
     """kw: bar_length, ea (host float64 [3, ny, nx]), ea_uniform, fixed (host uint8
     [ny, nx, 2]), fix_bottom_edge, precision, tol, max_iter, coarse_solves, batch,
     profile, coarse_factor, relax_threads, relax_copies, relax_overlap, mode_mask,
-    record_history."""
+    record_history, class_factors."""
     d, o, keep = _desc_opts(nx, ny, set_sx, set_sy, **kw)
     h = _P()
     _check(ctx, lib().hms_problem_create(ctx, ctypes.byref(d), ctypes.byref(o), ctypes.byref(h)))

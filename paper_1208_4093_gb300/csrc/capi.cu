@@ -1,6 +1,7 @@
 // C ABI of the HMS truss solver: contexts, problem setup, the iteration loop
 // (Fig. 3 of the paper as a device-resident CUDA graph) and the single steps.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -56,9 +57,12 @@ struct hms_problem {
   uint8_t* fix = nullptr;
   double2* rep = nullptr;
   long long* set_off = nullptr;
-  // factors
+  // factors: one per set (set_off), or with cls one per class of identical
+  // sets in the grouped layout of relax_class.cu (plan in cpd)
   double* f64 = nullptr;
   float* f32 = nullptr;
+  bool cls = false;
+  ClassPlanDev cpd;
   // force-controlled relaxation (q = 12): cut-free set factors with pinned DOFs,
   // supports | pins, per-set projection onto the free rigid motions (force.cu)
   double* f64F = nullptr;
@@ -219,6 +223,16 @@ cudaError_t launch_solve_stage(hms_problem* pr, cudaStream_t s, int q, const Ite
                              pr->x, pr->scale, pr->a, pr->cstat, flags, ctl, pr->err);
 }
 
+// The displacement-controlled relaxation of every set (K2), with per-set or
+// class factors.
+cudaError_t launch_relax_main(hms_problem* pr, cudaStream_t s, const IterCtl* ctl) {
+  if (pr->cls)
+    return launch_relax_class(s, pr->lv, pr->cpd, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, ctl,
+                              pr->err, pr->relax_wait0);
+  return launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, ctl, pr->err,
+                      pr->relax_threads, pr->relax_chunks, pr->relax_wait0);
+}
+
 // The force-controlled relaxation of every set (Eqs. 15-17, force.cu) after the
 // displacement-controlled one: r projected, the cut-free solve, delta^RF and
 // the upper-level forces of the modes 10-12 (P[12 I + 9 .. 11]).
@@ -246,8 +260,7 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
                              pr->delta_rf);
   if (e != cudaSuccess) return e;
   mark();
-  e = launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, pr->ctl, pr->err,
-                   pr->relax_threads, pr->relax_chunks, pr->relax_wait0);
+  e = launch_relax_main(pr, s, pr->ctl);
   if (e != cudaSuccess) return e;
   if (lv.q == NMODES_RF) {
     e = launch_force_relax(pr, s, pr->ctl);
@@ -391,6 +404,87 @@ bool choose_band(hms_problem* pr, const hms_options* o, int maxsm) {
   return true;
 }
 
+// The supports of a lattice description, per node (bit 0: x, bit 1: y).
+std::vector<uint8_t> fix_pattern(const hms_lattice_desc* d) {
+  const size_t nn = (size_t)d->nx * d->ny;
+  std::vector<uint8_t> fm(nn, 0);
+  if (d->fixed) {
+    for (size_t n = 0; n < nn; ++n) fm[n] = (uint8_t)((d->fixed[2 * n] ? 1 : 0) | (d->fixed[2 * n + 1] ? 2 : 0));
+  } else if (d->fix_bottom_edge) {
+    for (int i = 0; i < d->nx; ++i) fm[i] = 3;
+  }
+  return fm;
+}
+
+// Classes of sets with the same k^Inner under a uniform bar stiffness (the
+// relaxation with class factors, relax_class.cu): the same width and height,
+// parity of the first row, lattice edges touched and constrained DOFs.  Per
+// class: the offset and shape of its grouped factor and its first set (the one
+// factored); the sets class by class in index order; and batches of ts sets of
+// one class, one CTA each.
+struct ClassPlanHost {
+  std::vector<ClassInfo> info;
+  std::vector<int> rep, sets;
+  std::vector<ClassItem> items;
+  long long fac_elems = 0;
+  int nb8max = 0, hmax = 0;
+  size_t slot_elems = 0;
+};
+void class_plan_build(const LatView& lv, const std::vector<uint8_t>& fix, int ts, ClassPlanHost* P) {
+  std::map<std::array<int, 7>, std::vector<int>> by_key;
+  std::vector<std::vector<int>> members;
+  for (int I = 0; I < lv.M; ++I) {
+    const int i0 = (I % lv.Mx) * lv.sx, j0 = (I / lv.Mx) * lv.sy;
+    const int w = std::min(lv.sx, lv.nx - i0), h = std::min(lv.sy, lv.ny - j0);
+    const std::array<int, 7> key = {w, h, j0 & 1, i0 == 0, i0 + w == lv.nx, j0 == 0, j0 + h == lv.ny};
+    std::vector<int>& ids = by_key[key];
+    int cls = -1;
+    for (int c : ids) {
+      const int R = P->rep[c];
+      const int ri0 = (R % lv.Mx) * lv.sx, rj0 = (R / lv.Mx) * lv.sy;
+      bool same = true;
+      for (int jj = 0; jj < h && same; ++jj)
+        same = std::memcmp(&fix[(size_t)(j0 + jj) * lv.nx + i0], &fix[(size_t)(rj0 + jj) * lv.nx + ri0], w) == 0;
+      if (same) {
+        cls = c;
+        break;
+      }
+    }
+    if (cls < 0) {
+      cls = (int)members.size();
+      members.emplace_back();
+      P->rep.push_back(I);
+      ids.push_back(cls);
+      ClassInfo ci;
+      ci.off = 0;
+      ci.w = w;
+      ci.h = h;
+      P->info.push_back(ci);
+    }
+    members[cls].push_back(I);
+  }
+  for (size_t c = 0; c < members.size(); ++c) {
+    ClassInfo& ci = P->info[c];
+    const int nb = 2 * ci.w;
+    ci.off = P->fac_elems;
+    P->fac_elems += class_factor_size(nb, ci.h);
+    P->nb8max = std::max(P->nb8max, (nb + 7) / 8 * 8);
+    P->hmax = std::max(P->hmax, ci.h);
+    for (int k = 0; k < 4; ++k) P->slot_elems = std::max(P->slot_elems, (size_t)grp_size(k, nb));
+    const int first = (int)P->sets.size();
+    const int cnt = (int)members[c].size();
+    P->sets.insert(P->sets.end(), members[c].begin(), members[c].end());
+    for (int b = 0; b < cnt; b += ts) {
+      ClassItem it;
+      it.cls = (int)c;
+      it.first = first + b;
+      it.count = std::min(ts, cnt - b);
+      it.pad = 0;
+      P->items.push_back(it);
+    }
+  }
+}
+
 // Nested dissection over the set grid (coarse_nd.cu): the plan of fronts, if
 // every front fits the factor kernel's shared memory.
 bool choose_nd(hms_problem* pr, int maxsm) {
@@ -449,6 +543,7 @@ hms_status hms_context_create(int32_t device, hms_context** out) {
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = configure_setup(maxsm);
   if (e == cudaSuccess) e = configure_relax(maxsm);
+  if (e == cudaSuccess) e = configure_relax_class(maxsm);
   if (e == cudaSuccess) e = configure_coarse_assemble(maxsm);
   if (e == cudaSuccess) e = configure_coarse_solve(maxsm);
   if (e == cudaSuccess) e = configure_coarse_factor_cl(maxsm);
@@ -530,6 +625,8 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
   pr->set_off = src->set_off;
   pr->f64 = src->f64;
   pr->f32 = src->f32;
+  pr->cls = src->cls;
+  pr->cpd = src->cpd;
   pr->f64F = src->f64F;
   pr->f32F = src->f32F;
   pr->fixF = src->fixF;
@@ -595,7 +692,9 @@ static cudaError_t alloc_instance(hms_problem* pr) {
     CKI(cudaMemsetAsync(df, 0, nn * eb, s));
   }
   {
-    const size_t ybytes = (size_t)lv.M * relax_y_stride(lv) * (fp32(pr) ? sizeof(float) : sizeof(double));
+    const size_t esz = fp32(pr) ? sizeof(float) : sizeof(double);
+    const size_t ybytes = pr->cls ? (size_t)pr->cpd.nitems * pr->cpd.ystride * esz
+                                  : (size_t)lv.M * relax_y_stride(lv) * esz;
     unsigned char* ys;
     CKI(palloc(pr, &ys, ybytes));
     pr->yscratch = ys;
@@ -767,7 +866,11 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     return fail(c, HMS_ERR_ARG, "the FP64 relaxation takes regions up to 64 nodes wide");
   if ((o->mode_mask >> NMODES_RF) != 0u) return fail(c, HMS_ERR_ARG, "mode_mask has bits above mode 12");
   if (o->record_history != 0 && o->record_history != 1) return fail(c, HMS_ERR_ARG, "record_history must be 0 or 1");
+  if (o->class_factors != 0 && o->class_factors != 1) return fail(c, HMS_ERR_ARG, "class_factors must be 0 or 1");
   const bool force = (o->mode_mask >> NMODES) != 0u;  // modes 10-12: the force-controlled relaxation
+  if (o->class_factors && (d->ea || o->relax_overlap != 0 || force))
+    return fail(c, HMS_ERR_ARG, "class_factors needs a uniform EA (ea = NULL), relax_overlap = 0 and the nine "
+                                "displacement-controlled modes");
   if (force) {
     const int wr = d->nx - ((d->nx + d->set_sx - 1) / d->set_sx - 1) * d->set_sx;
     const int hr = d->ny - ((d->ny + d->set_sy - 1) / d->set_sy - 1) * d->set_sy;
@@ -838,12 +941,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   std::vector<double2> rep_host;   // the sets' representing points
   // ---- lattice description ----
   {
-    std::vector<uint8_t> fm(nn, 0);
-    if (d->fixed) {
-      for (size_t n = 0; n < nn; ++n) fm[n] = (uint8_t)((d->fixed[2 * n] ? 1 : 0) | (d->fixed[2 * n + 1] ? 2 : 0));
-    } else if (d->fix_bottom_edge) {
-      for (int i = 0; i < lv.nx; ++i) fm[i] = 3;
-    }
+    std::vector<uint8_t> fm = fix_pattern(d);
     CKP(salloc(pr, &pr->fix, nn));
     CKP(cudaMemcpy(pr->fix, fm.data(), nn, cudaMemcpyHostToDevice));
     lv.fix = pr->fix;
@@ -874,6 +972,7 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     CKP(cudaMemcpy(pr->kbar, kb.data(), 3 * nn * sizeof(double), cudaMemcpyHostToDevice));
     lv.kbar = pr->kbar;
   }
+  ClassPlanHost cph;  // with class factors
   {
     // representing node of each set: the centroid of its nodes (Eq. 10)
     std::vector<double2> rp(lv.M);
@@ -893,9 +992,36 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     CKP(cudaMemcpy(pr->rep, rp.data(), lv.M * sizeof(double2), cudaMemcpyHostToDevice));
     lv.rep = pr->rep;
     rep_host = rp;
-    CKP(salloc(pr, &pr->set_off, lv.M + 1));
-    CKP(cudaMemcpy(pr->set_off, so.data(), (lv.M + 1) * sizeof(long long), cudaMemcpyHostToDevice));
-    const size_t fsz = (size_t)so[lv.M];
+    size_t fsz = (size_t)so[lv.M];
+    if (o->class_factors) {
+      pr->cls = true;
+      class_plan_build(lv, fix_host, class_sets_per_cta(fp32(pr)), &cph);
+      if (relax_class_smem(cph.slot_elems, cph.nb8max, fp32(pr)) + 1024 > (size_t)maxsm) {
+        hms_problem_destroy(pr);
+        return fail(c, HMS_ERR_ARG, "set tile too large for the class-factor relaxation's shared memory");
+      }
+      ClassPlanDev& cp = pr->cpd;
+      ClassInfo* info;
+      ClassItem* items;
+      int* sets;
+      CKP(salloc(pr, &info, cph.info.size()));
+      CKP(salloc(pr, &items, cph.items.size()));
+      CKP(salloc(pr, &sets, cph.sets.size()));
+      CKP(cudaMemcpy(info, cph.info.data(), cph.info.size() * sizeof(ClassInfo), cudaMemcpyHostToDevice));
+      CKP(cudaMemcpy(items, cph.items.data(), cph.items.size() * sizeof(ClassItem), cudaMemcpyHostToDevice));
+      CKP(cudaMemcpy(sets, cph.sets.data(), cph.sets.size() * sizeof(int), cudaMemcpyHostToDevice));
+      cp.info = info;
+      cp.items = items;
+      cp.sets = sets;
+      cp.nitems = (int)cph.items.size();
+      cp.nb8max = cph.nb8max;
+      cp.slot_elems = cph.slot_elems;
+      cp.ystride = (long long)cph.hmax * cph.nb8max * class_sets_per_cta(fp32(pr));
+      fsz = (size_t)cph.fac_elems;
+    } else {
+      CKP(salloc(pr, &pr->set_off, lv.M + 1));
+      CKP(cudaMemcpy(pr->set_off, so.data(), (lv.M + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+    }
     if (fp32(pr)) {
       CKP(salloc(pr, &pr->f32, fsz));
       CKP(cudaMemsetAsync(pr->f32, 0, fsz * sizeof(float), s));
@@ -937,7 +1063,35 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     const int grid = std::max(1, std::min(lv.M, c->nsm));
     double* scratch = nullptr;
     CKP(cudaMalloc(&scratch, (size_t)grid * b_size(MAX_NB) * sizeof(double)));
-    cudaError_t e = launch_set_factor(s, lv, pr->set_off, pr->f64, pr->f32, scratch, grid, pr->err);
+    cudaError_t e = cudaSuccess;
+    if (pr->cls) {
+      // each class's first set in the standard layout (FP64), then its grouped copy
+      const int nc = (int)cph.rep.size();
+      std::vector<long long> ro(nc + 1, 0);
+      for (int t = 0; t < nc; ++t) ro[t + 1] = ro[t] + set_factor_stride(2 * cph.info[t].w, cph.info[t].h);
+      double* std64 = nullptr;
+      long long* ro_d = nullptr;
+      int* reps_d = nullptr;
+      e = cudaMalloc(&std64, (size_t)ro[nc] * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&ro_d, (nc + 1) * sizeof(long long));
+      if (e == cudaSuccess) e = cudaMalloc(&reps_d, nc * sizeof(int));
+      if (e == cudaSuccess) e = cudaMemcpy(ro_d, ro.data(), (nc + 1) * sizeof(long long), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(reps_d, cph.rep.data(), nc * sizeof(int), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemsetAsync(std64, 0, (size_t)ro[nc] * sizeof(double), s);
+      if (e == cudaSuccess)
+        e = launch_set_factor(s, lv, ro_d, std64, nullptr, scratch, std::max(1, std::min(nc, c->nsm)), pr->err, false,
+                              reps_d, nc);
+      for (int t = 0; t < nc && e == cudaSuccess; ++t)
+        e = launch_group_factor(s, std64 + ro[t], 2 * cph.info[t].w, cph.info[t].h,
+                                pr->f64 ? pr->f64 + cph.info[t].off : nullptr,
+                                pr->f32 ? pr->f32 + cph.info[t].off : nullptr);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      cudaFree(std64);
+      cudaFree(ro_d);
+      cudaFree(reps_d);
+    } else {
+      e = launch_set_factor(s, lv, pr->set_off, pr->f64, pr->f32, scratch, grid, pr->err);
+    }
     if (e == cudaSuccess && force) {
       LatView lvF = lv;  // the cut-free sets with their pinned DOFs marked as constrained
       lvF.fix = pr->fixF;
@@ -964,7 +1118,10 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     hms_problem_destroy(pr);
     return fail(c, HMS_ERR_ARG, "relax_copies = 2 needs the FP64 path and even set widths >= 6");
   }
-  if (o->relax_threads != 0 && o->relax_copies != 0) {
+  if (pr->cls) {
+    pr->relax_threads = 256;  // the class-factor kernel's fixed shape
+    pr->relax_chunks = 1;
+  } else if (o->relax_threads != 0 && o->relax_copies != 0) {
     pr->relax_threads = o->relax_threads;
     pr->relax_chunks = o->relax_copies;
   } else if (o->relax_threads != 0) {
@@ -1129,7 +1286,7 @@ static bool lockstep_applies(int32_t count, hms_problem* const* problems) {
   for (int i = 0; i < count; ++i) {
     const hms_problem* pr = problems[i];
     if (!pr || pr->profile || pr->coarse_fp64 || pr->cluster_factor || pr->two_sided || pr->big_stages <= 0 ||
-        pr->lv.q != NMODES)
+        pr->lv.q != NMODES || pr->cls)
       return false;
     if (pr->precision != problems[0]->precision || pr->nsolve != problems[0]->nsolve) return false;
   }
@@ -1637,8 +1794,7 @@ hms_status hms_relax(hms_problem* pr, const double* r, double* delta, double* P,
   const size_t nn = nnodes(pr), vb = nn * sizeof(double2);
   CKC(c, cudaMemcpyAsync(pr->r, r, vb, kind_in(mem_kind), s));
   CKC(c, launch_mask_u(s, pr->lv, pr->r));
-  CKC(c, launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr, pr->err,
-                      pr->relax_threads, pr->relax_chunks, pr->relax_wait0));
+  CKC(c, launch_relax_main(pr, s, nullptr));
   if (pr->lv.q == NMODES_RF) CKC(c, launch_force_relax(pr, s, nullptr));
   CKC(c, copy_delta_out(pr, pr->delta, delta, mem_kind));
   CKC(c, cudaMemcpyAsync(P, pr->P, pr->n_c * sizeof(double), kind_out(mem_kind), s));
@@ -1774,7 +1930,9 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
   if (o->relax_overlap < 0 || rw > MAX_RX) return false;
   if (o->precision == HMS_FP64 && rw > MAX_SX) return false;
   if ((o->mode_mask >> NMODES_RF) != 0u || (o->record_history != 0 && o->record_history != 1)) return false;
+  if (o->class_factors != 0 && o->class_factors != 1) return false;
   const bool force = (o->mode_mask >> NMODES) != 0u;
+  if (o->class_factors && (d->ea || o->relax_overlap != 0 || force)) return false;
   if (force) {
     const int wr = d->nx - ((d->nx + d->set_sx - 1) / d->set_sx - 1) * d->set_sx;
     const int hr = d->ny - ((d->ny + d->set_sy - 1) / d->set_sy - 1) * d->set_sy;
@@ -1804,15 +1962,29 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
   const size_t nn = (size_t)lv.nx * lv.ny, M = (size_t)lv.M, n_c = (size_t)pr.n_c;
   const size_t esz = fp32(&pr) ? 4 : 8;
   const size_t nband = n_c * (pr.bw + 1);
-  size_t fac = 0;
-  for (int I = 0; I < lv.M; ++I) {
-    const Region R = relax_region(lv, I);
-    fac += (size_t)set_factor_stride(2 * R.w, R.h);
+  size_t fac = 0, ybytes = 0, plan_bytes = 0, setup_bytes = 0;
+  if (o->class_factors) {
+    ClassPlanHost cph;
+    class_plan_build(lv, fix_pattern(d), class_sets_per_cta(fp32(&pr)), &cph);
+    if (relax_class_smem(cph.slot_elems, cph.nb8max, fp32(&pr)) + 1024 > (size_t)maxsm) return false;
+    fac = (size_t)cph.fac_elems;
+    plan_bytes = cph.info.size() * sizeof(ClassInfo) + cph.items.size() * sizeof(ClassItem) + cph.sets.size() * 4;
+    ybytes = cph.items.size() * (size_t)cph.hmax * cph.nb8max * class_sets_per_cta(fp32(&pr)) * esz;
+    const size_t nc = cph.rep.size();
+    for (size_t t = 0; t < nc; ++t) setup_bytes += (size_t)set_factor_stride(2 * cph.info[t].w, cph.info[t].h) * 8;
+    setup_bytes += (nc + 1) * 8 + nc * 4;
+  } else {
+    for (int I = 0; I < lv.M; ++I) {
+      const Region R = relax_region(lv, I);
+      fac += (size_t)set_factor_stride(2 * R.w, R.h);
+    }
+    plan_bytes = (M + 1) * 8;
+    ybytes = M * (size_t)relax_y_stride(lv) * esz;
   }
   const size_t ss = (size_t)slot_size(lv.q);
-  *shared = nn + (d->ea ? 3 * nn * 8 : 0) + M * 16 + (M + 1) * 8 + fac * esz + M * NSLOTS * ss * 8;
+  *shared = nn + (d->ea ? 3 * nn * 8 : 0) + M * 16 + plan_bytes + fac * esz + M * NSLOTS * ss * 8;
   if (force) *shared += fac * esz + nn + 9 * M * 8;  // cut-free factors, supports | pins, projections
-  size_t b = 4 * nn * 16 + nn * 2 * esz + M * (size_t)relax_y_stride(lv) * esz;
+  size_t b = 4 * nn * 16 + nn * 2 * esz + ybytes;
   if (force) b += nn * 16 + nn * 2 * esz;  // r projected, delta^RF
   b += 2 * n_c * 8 + M * NSLOTS * ss * 8 + 3 * nband * 8 + 4 * n_c * 8;
   if (pr.nd) {
@@ -1832,7 +2004,7 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
   b += n_c * 4 + 32 + (size_t)std::max(update_residual_blocks(lv), 1024) * 3 * 8 + 4 + sizeof(IterCtl) + 4 + 32;
   if (o->record_history) b += 3 * ((size_t)o->max_iter + 1) * 8;
   *inst = b;
-  *scratch = (size_t)std::max(1, std::min(lv.M, c->nsm)) * b_size(MAX_NB) * 8;
+  *scratch = (size_t)std::max(1, std::min(lv.M, c->nsm)) * b_size(MAX_NB) * 8 + setup_bytes;
   return true;
 }
 }  // namespace

@@ -152,6 +152,65 @@ __host__ __device__ inline long long bt_row_off(int nb, int c) {
 }
 __host__ __device__ inline long long set_factor_stride(int nb, int h) { return 2 * set_factor_size(nb, h); }
 
+// ---- class factors (relax_class.cu): one factor per class of identical sets,
+// stored "grouped" for the many-right-hand-side solves.  A matrix of kind K
+// maps an input vector (columns) to an output vector (rows); its rows are
+// taken in groups of 8, and group g stores, for each column its rows reach,
+// the 8 values of that column (zero where a row does not reach it).  Kinds:
+// Linv_j (row r: columns 0..r), B_j (row r: columns b_lo(r)..nb-1), Linv_j^T
+// (row c: columns c..nb-1) and B_j^T (row c: columns 0..min(nb-1, c+3)).
+enum GroupKind { GK_LINV = 0, GK_B, GK_LT, GK_BT };
+__host__ __device__ inline void grp_range(int kind, int nb, int g, int& lo, int& hi) {
+  const int r0 = 8 * g, r1 = 8 * g + 8 < nb ? 8 * g + 8 : nb;  // the group's rows [r0, r1)
+  if (kind == GK_LINV) {
+    lo = 0, hi = r1;
+  } else if (kind == GK_B) {
+    lo = b_lo(r0), hi = nb;
+  } else if (kind == GK_LT) {
+    lo = r0, hi = nb;
+  } else {
+    lo = 0, hi = r1 + 3 < nb ? r1 + 3 : nb;
+  }
+}
+// element offset of group g within a grouped matrix
+__host__ __device__ inline long long grp_off(int kind, int nb, int g) {
+  long long o = 0;
+  for (int q = 0; q < g; ++q) {
+    int lo, hi;
+    grp_range(kind, nb, q, lo, hi);
+    o += 8LL * (hi - lo);
+  }
+  return o;
+}
+__host__ __device__ inline long long grp_size(int kind, int nb) { return pad4(grp_off(kind, nb, (nb + 7) / 8)); }
+// a class's grouped factor: the forward ops' matrices (Linv_0, B_1, Linv_1, ...,
+// Linv_{h-1}), then the backward ops' (Linv_{h-1}^T, B_{h-1}^T, ..., B_1^T,
+// Linv_0^T), each in the order the solves use them
+__host__ __device__ inline long long class_op_off(int nb, int h, int o) {
+  const int nm = 2 * h - 1;
+  if (o < nm) return (long long)((o + 1) / 2) * grp_size(GK_LINV, nb) + (long long)(o / 2) * grp_size(GK_B, nb);
+  const int k = o - nm;
+  const long long fwd = (long long)h * grp_size(GK_LINV, nb) + (long long)(h - 1) * grp_size(GK_B, nb);
+  return fwd + (long long)((k + 1) / 2) * grp_size(GK_LT, nb) + (long long)(k / 2) * grp_size(GK_BT, nb);
+}
+__host__ __device__ inline long long class_factor_size(int nb, int h) { return class_op_off(nb, h, 2 * (2 * h - 1)); }
+struct ClassInfo {
+  long long off;  // element offset of the class's grouped factor
+  int w, h;       // set width and height (nodes)
+};
+struct ClassItem {
+  int cls, first, count, pad;  // the sets sets[first .. first + count) of class cls
+};
+struct ClassPlanDev {
+  const ClassInfo* info = nullptr;
+  const ClassItem* items = nullptr;
+  const int* sets = nullptr;  // set indices, grouped by class
+  int nitems = 0;
+  int nb8max = 0;             // rows of a vector panel (largest nb rounded up to 8)
+  size_t slot_elems = 0;      // largest grouped matrix (elements)
+  long long ystride = 0;      // elements of one CTA's forward vectors
+};
+
 // ---- launchers (each returns the launch error) ----
 // residual.cu
 cudaError_t launch_update_residual(cudaStream_t s, const LatView& lv, const double2* u_in,
@@ -171,7 +230,8 @@ cudaError_t launch_residual_noalloc(cudaStream_t s, const LatView& lv, const dou
 // setup.cu (cut = true: the set cut free, i.e. k^Inner + Delta k of Eq. 15, only the
 // set's own bars; lv.fix then marks the constrained and the pinned DOFs)
 cudaError_t launch_set_factor(cudaStream_t s, const LatView& lv, const long long* set_off,
-                              double* f64, float* f32, double* scratch, int grid, int* err, bool cut = false);
+                              double* f64, float* f32, double* scratch, int grid, int* err, bool cut = false,
+                              const int* list = nullptr, int nlist = 0);
 // force.cu: the force-controlled relaxation's projections (Eqs. 16-18).  M: per set the
 // 3 x 3 matrix of the projection onto the rigid motions the set's supports leave free
 // (zero for anchored sets); fixF: supports | pinned DOFs.
@@ -187,6 +247,14 @@ cudaError_t launch_relax(cudaStream_t s, const LatView& lv, const long long* set
                          double* P, void* yscratch, const IterCtl* ctl, int* err, int threads, int chunks,
                          int wait0 = -1);
 size_t relax_smem_bytes(const LatView& lv, bool fp32, int chunks = 1);
+// relax_class.cu: the relaxation with class factors (sets per CTA: 64 FP32, 32 FP64)
+int class_sets_per_cta(bool fp32);
+size_t relax_class_smem(size_t slot_elems, int nb8max, bool fp32);
+cudaError_t launch_group_factor(cudaStream_t s, const double* src, int nb, int h, double* g64, float* g32);
+cudaError_t launch_relax_class(cudaStream_t s, const LatView& lv, const ClassPlanDev& cp, const double* f64,
+                               const float* f32, const double2* r, void* delta, double* P, void* yscratch,
+                               const IterCtl* ctl, int* err, int wait0 = -1);
+cudaError_t configure_relax_class(int max_smem);
 bool relax_chunks_possible(const LatView& lv, bool fp32);
 long long relax_y_stride(const LatView& lv);
 // coarse.cu

@@ -62,14 +62,18 @@ __device__ inline void node_diag(const LatView& lv, int i, int j, const Region& 
 template <bool CUT>
 __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* __restrict__ set_off,
                                                    double* __restrict__ f64, float* __restrict__ f32,
-                                                   double* __restrict__ scratch, int* err) {
+                                                   double* __restrict__ scratch, int* err,
+                                                   const int* __restrict__ list, int nlist) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* Bprev = scratch + (size_t)blockIdx.x * b_size(MAX_NB);
   __shared__ int bad;
   __shared__ double diag0[MAX_NB];
 
-  for (int I = blockIdx.x; I < lv.M; I += gridDim.x) {
+  // every set, or the sets list[0 .. nlist) (factor t at set_off[t])
+  const int nwork = list ? nlist : lv.M;
+  for (int t = blockIdx.x; t < nwork; t += gridDim.x) {
+    const int I = list ? list[t] : t;
     // the set's relaxation region (the set itself without overlap)
     const Region R = relax_region(lv, I);
     const int i0 = R.i0, j0 = R.j0, w = R.w, h = R.h;
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
     const long long npk = pk(nb - 1, nb - 1) + 1;
     double* S = sm;          // packed lower nb x nb
     double* Li = sm + npk;   // packed lower nb x nb
-    const long long base = set_off[I];
+    const long long base = set_off[t];
     const long long tr_base = set_factor_size(nb, h);  // the column-stored copy
     if (tid == 0) bad = 0;
 
@@ -214,11 +218,12 @@ __global__ void __launch_bounds__(NT) k_set_factor(LatView lv, const long long* 
 }  // namespace
 
 cudaError_t launch_set_factor(cudaStream_t s, const LatView& lv, const long long* set_off,
-                              double* f64, float* f32, double* scratch, int grid, int* err, bool cut) {
+                              double* f64, float* f32, double* scratch, int grid, int* err, bool cut,
+                              const int* list, int nlist) {
   const int nb = 2 * region_w_max(lv);
   const size_t smem = 2 * (size_t)((long long)nb * (nb + 1) / 2) * sizeof(double);
-  if (cut) k_set_factor<true><<<grid, NT, smem, s>>>(lv, set_off, f64, f32, scratch, err);
-  else k_set_factor<false><<<grid, NT, smem, s>>>(lv, set_off, f64, f32, scratch, err);
+  if (cut) k_set_factor<true><<<grid, NT, smem, s>>>(lv, set_off, f64, f32, scratch, err, list, nlist);
+  else k_set_factor<false><<<grid, NT, smem, s>>>(lv, set_off, f64, f32, scratch, err, list, nlist);
   return cudaGetLastError();
 }
 
