@@ -95,9 +95,10 @@ struct hms_problem {
   bool cluster_factor = false;  // FP32 factor on a cluster of 4 CTAs (with the block solve)
   bool two_sided = false;       // FP32 two-sided factor and solve on two SMs
   TwoSided ts;
-  bool nd = false;              // nested-dissection factor and solve (coarse_nd.cu)
-  NDPlanHost ndp;
+  bool nd = false;              // nested-dissection factor and solve (coarse_nd.cu) over
+  NDPlanHost ndp;               // the blocks of K_aa (coarse_blocks.cu; no band)
   NDPlanDev ndd;
+  double* blk = nullptr;
   int* dropped = nullptr;
   unsigned long long* cstat = nullptr;  // refinement state of the upper-level solve
   double* partials = nullptr;
@@ -195,7 +196,7 @@ bool fp32(const hms_problem* pr) { return pr->precision == HMS_MIXED; }
 // The factor of Eq. 8 (after the scaled band is built) and its per-block
 // matrices, by the configured variant.
 cudaError_t launch_factor_stage(hms_problem* pr, cudaStream_t s, const IterCtl* ctl) {
-  if (pr->nd) return launch_nd_factor(s, pr->ndp, pr->ndd, (const float*)pr->lrow, pr->bw, pr->dropped, ctl);
+  if (pr->nd) return launch_nd_factor(s, pr->lv, pr->ndp, pr->ndd, pr->blk, pr->scale, pr->dropped, ctl);
   if (pr->two_sided) return launch_coarse_factor_2s(s, pr->n_c, pr->bw, pr->ts, pr->sband, pr->dropped, ctl);
   cudaError_t e = pr->cluster_factor
                       ? launch_coarse_factor_cl(s, pr->n_c, pr->bw, pr->lrow, pr->lcol, pr->dinv, pr->dropped, ctl)
@@ -231,6 +232,26 @@ cudaError_t launch_relax_main(hms_problem* pr, cudaStream_t s, const IterCtl* ct
                               pr->err, pr->relax_wait0);
   return launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, ctl, pr->err,
                       pr->relax_threads, pr->relax_chunks, pr->relax_wait0);
+}
+
+// K_aa from the slots and the scaled system of Eq. 8 (scale, b, x = 0, drop
+// flags): by blocks for nested dissection, else as a band.
+cudaError_t launch_scaled_system(hms_problem* pr, cudaStream_t s, const IterCtl* ctl) {
+  if (pr->nd) {
+    cudaError_t e = launch_blocks_from_slots(s, pr->lv, pr->slots_base, pr->slots_it, pr->blk, ctl);
+    if (e != cudaSuccess) return e;
+    return launch_blk_diag(s, pr->lv, pr->blk, pr->P, pr->scale, pr->b, pr->x, pr->dropped, pr->mode_mask, ctl);
+  }
+  cudaError_t e = launch_coarse_band_from_slots(s, pr->lv, pr->slots_base, pr->slots_it, pr->band, ctl);
+  if (e != cudaSuccess) return e;
+  return launch_coarse_scale(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale,
+                             pr->b, pr->x, pr->dropped, pr->mode_mask, pr->lv.q, ctl);
+}
+// The FP64 refinement residual of Eq. 8, res = b - A x.
+cudaError_t launch_refine_residual(hms_problem* pr, cudaStream_t s, const IterCtl* ctl) {
+  if (pr->nd)
+    return launch_blk_residual(s, pr->lv, pr->blk, pr->scale, pr->dropped, pr->b, pr->x, pr->res, pr->cstat, ctl);
+  return launch_coarse_residual(s, pr->n_c, pr->bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, pr->cstat, ctl);
 }
 
 // The force-controlled relaxation of every set (Eqs. 15-17, force.cu) after the
@@ -270,10 +291,7 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
   e = launch_coarse_slots(s, lv, pr->delta, fp32(pr), false, pr->slots_it, pr->ctl, pr->delta_rf);
   if (e != cudaSuccess) return e;
   mark();
-  e = launch_coarse_band_from_slots(s, lv, pr->slots_base, pr->slots_it, pr->band, pr->ctl);
-  if (e != cudaSuccess) return e;
-  e = launch_coarse_scale(s, pr->n_c, pr->bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale,
-                          pr->b, pr->x, pr->dropped, pr->mode_mask, lv.q, pr->ctl);
+  e = launch_scaled_system(pr, s, pr->ctl);
   if (e != cudaSuccess) return e;
   mark();
   e = launch_factor_stage(pr, s, pr->ctl);
@@ -281,8 +299,7 @@ cudaError_t launch_iteration(hms_problem* pr, cudaStream_t s, int k, cudaEvent_t
   mark();
   for (int q = 0; q < pr->nsolve; ++q) {
     if (q > 0) {
-      e = launch_coarse_residual(s, pr->n_c, pr->bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, pr->cstat,
-                                 pr->ctl);
+      e = launch_refine_residual(pr, s, pr->ctl);
       if (e != cudaSuccess) return e;
       mark();
     }
@@ -704,17 +721,17 @@ static cudaError_t alloc_instance(hms_problem* pr) {
   CKI(palloc(pr, &pr->a, n_c));
   CKI(palloc(pr, &pr->P, n_c));
   CKI(palloc(pr, &pr->slots_it, (size_t)lv.M * NSLOTS * slot_size(lv.q)));
-  CKI(palloc(pr, &pr->band, nband));
-  CKI(palloc(pr, &pr->sband, 2 * nband));
+  if (!pr->nd) {
+    CKI(palloc(pr, &pr->band, nband));
+    CKI(palloc(pr, &pr->sband, 2 * nband));
+  }
   CKI(palloc(pr, &pr->scale, n_c));
   CKI(palloc(pr, &pr->b, n_c));
   CKI(palloc(pr, &pr->x, n_c));
   CKI(palloc(pr, &pr->res, n_c));
   if (pr->nd) {
-    // the scaled band's FP32 row layout (the fronts' input), the plan and the fronts
-    float* lr;
-    CKI(palloc(pr, &lr, nband + 16));
-    pr->lrow = lr;
+    // the blocks of K_aa (the fronts' input), the plan and the fronts
+    CKI(palloc(pr, &pr->blk, coarse_blocks_elems(lv)));
     const NDPlanHost& P = pr->ndp;
     NDPlanDev& D = pr->ndd;
     CKI(palloc(pr, &D.nodes, P.nodes.size()));
@@ -727,6 +744,13 @@ static cudaError_t alloc_instance(hms_problem* pr) {
       CKI(cudaMemcpyAsync(D.maps, P.maps.data(), P.maps.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     CKI(cudaMemcpyAsync(D.lvl_nodes, P.lvl_nodes.data(), P.lvl_nodes.size() * sizeof(int), cudaMemcpyHostToDevice,
                         s));
+    CKI(palloc(pr, &D.bigs, std::max<size_t>(P.bigs.size(), 1)));
+    CKI(palloc(pr, &D.inv, std::max<size_t>(P.inv.size(), 1)));
+    CKI(palloc(pr, &D.dmask, std::max<size_t>(P.max_level_bigs, 1)));
+    if (!P.bigs.empty())
+      CKI(cudaMemcpyAsync(D.bigs, P.bigs.data(), P.bigs.size() * sizeof(NDBig), cudaMemcpyHostToDevice, s));
+    if (!P.inv.empty())
+      CKI(cudaMemcpyAsync(D.inv, P.inv.data(), P.inv.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     CKI(palloc(pr, &D.F, P.f_elems));
     CKI(palloc(pr, &D.W, std::max<size_t>(P.w_elems, 1)));
     CKI(palloc(pr, &D.y, (size_t)n_c));
@@ -1826,11 +1850,13 @@ hms_status hms_coarse_matrix(hms_problem* pr, const double* delta, double* Kaa, 
   cudaStream_t s = c->stream;
   CKC(c, stage_deltas(pr, delta, mem_kind));
   CKC(c, launch_coarse_slots(s, pr->lv, pr->delta, fp32(pr), false, pr->slots_it, nullptr, pr->delta_rf));
-  CKC(c, launch_coarse_band_from_slots(s, pr->lv, pr->slots_base, pr->slots_it, pr->band, nullptr));
+  if (pr->nd) CKC(c, launch_blocks_from_slots(s, pr->lv, pr->slots_base, pr->slots_it, pr->blk, nullptr));
+  else CKC(c, launch_coarse_band_from_slots(s, pr->lv, pr->slots_base, pr->slots_it, pr->band, nullptr));
   double* dense = nullptr;
   const size_t nd = (size_t)pr->n_c * pr->n_c;
   CKC(c, cudaMallocAsync(&dense, nd * sizeof(double), s));
-  cudaError_t e = launch_coarse_dense_from_band(s, pr->n_c, pr->bw, pr->band, dense);
+  cudaError_t e = pr->nd ? launch_dense_from_blocks(s, pr->lv, pr->blk, dense)
+                         : launch_coarse_dense_from_band(s, pr->n_c, pr->bw, pr->band, dense);
   if (e == cudaSuccess) e = cudaMemcpyAsync(Kaa, dense, nd * sizeof(double), kind_out(mem_kind), s);
   cudaFreeAsync(dense, s);
   CKC(c, e);
@@ -1850,16 +1876,20 @@ hms_status hms_coarse_solve(hms_problem* pr, const double* Kaa, const double* P,
   double* dense = nullptr;
   CKC(c, cudaMallocAsync(&dense, nd * sizeof(double), s));
   cudaError_t e = cudaMemcpyAsync(dense, Kaa, nd * sizeof(double), kind_in(mem_kind), s);
-  if (e == cudaSuccess) e = launch_coarse_band_from_dense(s, n, bw, dense, pr->band);
+  if (e == cudaSuccess)
+    e = pr->nd ? launch_blocks_from_dense(s, pr->lv, dense, pr->blk) : launch_coarse_band_from_dense(s, n, bw, dense,
+                                                                                                      pr->band);
   cudaFreeAsync(dense, s);
   CKC(c, e);
   CKC(c, cudaMemcpyAsync(pr->P, P, n * sizeof(double), kind_in(mem_kind), s));
-  CKC(c, launch_coarse_scale(s, n, bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale, pr->b,
-                             pr->x, pr->dropped, pr->mode_mask, pr->lv.q, nullptr));
+  if (pr->nd)
+    CKC(c, launch_blk_diag(s, pr->lv, pr->blk, pr->P, pr->scale, pr->b, pr->x, pr->dropped, pr->mode_mask, nullptr));
+  else
+    CKC(c, launch_coarse_scale(s, n, bw, pr->coarse_fp64, pr->band, pr->P, pr->sband, pr->lrow, pr->scale, pr->b,
+                               pr->x, pr->dropped, pr->mode_mask, pr->lv.q, nullptr));
   CKC(c, launch_factor_stage(pr, s, nullptr));
   for (int q = 0; q < pr->nsolve; ++q) {
-    if (q > 0)
-      CKC(c, launch_coarse_residual(s, n, bw, pr->sband, pr->b, pr->x, pr->dropped, pr->res, pr->cstat, nullptr));
+    if (q > 0) CKC(c, launch_refine_residual(pr, s, nullptr));
     CKC(c, launch_solve_stage(pr, s, q, nullptr));
   }
   CKC(c, cudaMemcpyAsync(a, pr->a, n * sizeof(double), kind_out(mem_kind), s));
@@ -1986,12 +2016,13 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
   if (force) *shared += fac * esz + nn + 9 * M * 8;  // cut-free factors, supports | pins, projections
   size_t b = 4 * nn * 16 + nn * 2 * esz + ybytes;
   if (force) b += nn * 16 + nn * 2 * esz;  // r projected, delta^RF
-  b += 2 * n_c * 8 + M * NSLOTS * ss * 8 + 3 * nband * 8 + 4 * n_c * 8;
+  b += 2 * n_c * 8 + M * NSLOTS * ss * 8 + (pr.nd ? 0 : 3 * nband * 8) + 4 * n_c * 8;
   if (pr.nd) {
     const NDPlanHost& P = pr.ndp;
-    b += (nband + 16) * 4 + P.nodes.size() * sizeof(NDNode) + P.sets.size() * 4 +
-         std::max<size_t>(P.maps.size(), 1) * 4 + P.lvl_nodes.size() * 4 + P.f_elems * 4 +
-         std::max<size_t>(P.w_elems, 1) * 4 + 2 * n_c * 4;
+    b += coarse_blocks_elems(lv) * 8 + P.nodes.size() * sizeof(NDNode) + P.sets.size() * 4 +
+         std::max<size_t>(P.maps.size(), 1) * 4 + P.lvl_nodes.size() * 4 +
+         std::max<size_t>(P.bigs.size(), 1) * sizeof(NDBig) + std::max<size_t>(P.inv.size(), 1) * 4 +
+         std::max<size_t>(P.max_level_bigs, 1) * 4 + P.f_elems * 4 + std::max<size_t>(P.w_elems, 1) * 4 + 2 * n_c * 4;
   } else {
     b += 2 * (nband + 16) * 8 + (size_t)coarse_dinv_size(pr.n_c) * 8;
   }

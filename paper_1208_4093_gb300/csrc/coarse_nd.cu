@@ -23,14 +23,25 @@
 //   back substitution, root first: x_S = L_SS^-T (y_S - L_BS^T x_B) with x_B
 //     from the ancestors.
 //
-// The matrix is the Jacobi-scaled one the band path factors (its FP32 row
-// layout, written by k_coarse_scale_band), so modes dropped in FP64 are unit
-// rows already; the factor and solves run in FP32 and the FP64 refinement of
-// Eq. 8 (k_coarse_residual) is the same as for the band factors.  Every sum
-// runs in a fixed order (children in order, rows in order), so results are
-// the same on every run.
+// The matrix is the Jacobi-scaled one the band path factors, read from the
+// blocks of K_aa (coarse_blocks.cu) with the scale and drop flags of
+// k_blk_diag and rounded to FP32 as the band path rounds it, so modes dropped
+// in FP64 are unit rows already; the factor and solves run in FP32 and the
+// FP64 refinement of Eq. 8 (k_blk_residual) works on the same scaled system.
+//
+// Fronts of at least ND_BIG unknowns (the top levels of large set grids, up to
+// several thousand unknowns) are factored by many CTAs instead: one launch
+// assembles every wide front of a level, then per 32-column panel one launch
+// factors the diagonal blocks, one forms the panels below them and one
+// applies the rank-32 update to the trailing lower triangles in 64 x 64
+// tiles.  Each step does the arithmetic of the one-CTA factor in the same
+// order, so a front gets the same factor either way.
+//
+// Every sum runs in a fixed order (children in order, rows in order), so
+// results are the same on every run.
 #include <algorithm>
 #include <cmath>
+#include <unordered_map>
 #include <vector>
 
 #include "coarse_common.cuh"
@@ -49,16 +60,31 @@ __device__ inline bool nd_done(const IterCtl* ctl) { return ctl && *(volatile co
 // global unknown of front position p: set st[p / nm], mode p % nm (nm modes per set)
 __device__ inline int nd_glob(const int* st, int p, int nm) { return st[p / nm] * nm + p % nm; }
 
-// entry (gi, gj) of the scaled matrix from its FP32 row-layout band
-__device__ inline float nd_a(const float* __restrict__ frow, int bw, int gi, int gj) {
-  if (gi < gj) {
-    const int t = gi;
-    gi = gj;
-    gj = t;
+// Entry (gi, gj) of the scaled matrix, from the blocks of K_aa: 1 on the
+// diagonal, 0 in the rows and columns of dropped modes, else s_hi K s_lo in
+// FP64 (the larger index's scale first) rounded to FP32.
+struct BlkSrc {
+  const double* blk;
+  const double* scale;
+  const int* dropped;
+  int Mx, nm;
+  __device__ float operator()(int gi, int gj) const {
+    if (gi == gj) return 1.f;
+    if (dropped[gi] || dropped[gj]) return 0.f;
+    const int hi = gi > gj ? gi : gj, lo = gi > gj ? gj : gi;
+    const int J = hi / nm, l = hi % nm, I = lo / nm, m = lo % nm;  // J >= I
+    const size_t bs = (size_t)nm * nm;
+    double k;
+    if (J == I) {
+      k = blk[(size_t)I * NBLK * bs + (size_t)l * nm + m];
+    } else {
+      const int b = blk_of(J % Mx - I % Mx, J / Mx - I / Mx);
+      if (b <= 0) return 0.f;
+      k = blk[((size_t)I * NBLK + b) * bs + (size_t)l * nm + m];
+    }
+    return (float)(scale[hi] * k * scale[lo]);
   }
-  const int d = gi - gj;
-  return d <= bw ? frow[(size_t)gi * (bw + 1) + d] : 0.f;
-}
+};
 
 __device__ inline float warp_sum_f(float v) {
 #pragma unroll
@@ -129,7 +155,7 @@ __device__ __forceinline__ void nd_tri_invert(const float (&a)[PB], float (&x)[P
 template <bool SM>
 __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* __restrict__ nodes,
                                                const int* __restrict__ sets, const int* __restrict__ maps,
-                                               const float* __restrict__ frow, int bw, float* __restrict__ F,
+                                               const BlkSrc& src, float* __restrict__ F,
                                                int* __restrict__ dropped, float* sm, int* gidx, int* cpos,
                                                float (&Dinv)[PB][PB + 1], unsigned& dmask) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -153,7 +179,7 @@ __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* _
 #pragma unroll
       for (int u = 0; u < NU; ++u) {
         const int q = q0 + 32 * u;
-        v[u] = (q <= p && q < nS) ? nd_a(frow, bw, gp, gidx[q]) : 0.f;
+        v[u] = (q <= p && q < nS) ? src(gp, gidx[q]) : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < NU; ++u) {
@@ -291,8 +317,8 @@ __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* _
 // shared memory.
 __global__ void __launch_bounds__(NDT) k_nd_factor(const NDNode* __restrict__ nodes, const int* __restrict__ lvl,
                                                    int lbeg, const int* __restrict__ sets,
-                                                   const int* __restrict__ maps, const float* __restrict__ frow,
-                                                   int bw, float* __restrict__ F, int* __restrict__ dropped,
+                                                   const int* __restrict__ maps, BlkSrc src,
+                                                   float* __restrict__ F, int* __restrict__ dropped,
                                                    long long cap, const IterCtl* ctl) {
   if (nd_done(ctl)) return;
   extern __shared__ __align__(16) float ndsm[];
@@ -304,9 +330,164 @@ __global__ void __launch_bounds__(NDT) k_nd_factor(const NDNode* __restrict__ no
   int* gidx = reinterpret_cast<int*>(ndsm + (cap - 2 * nf));
   int* cpos = gidx + nf;
   if (nf * (nf + 1) / 2 + 2 * nf <= cap)
-    nd_factor_body<true>(nd, nodes, sets, maps, frow, bw, F, dropped, ndsm, gidx, cpos, Dinv, dmask);
+    nd_factor_body<true>(nd, nodes, sets, maps, src, F, dropped, ndsm, gidx, cpos, Dinv, dmask);
   else
-    nd_factor_body<false>(nd, nodes, sets, maps, frow, bw, F, dropped, ndsm, gidx, cpos, Dinv, dmask);
+    nd_factor_body<false>(nd, nodes, sets, maps, src, F, dropped, ndsm, gidx, cpos, Dinv, dmask);
+}
+
+// ---------------------------------------------------------------- wide fronts
+// Assembly of the wide fronts of a level: CTA (x, y) takes rows 32x .. 32x+31
+// of front y (one warp per row, lane = column): the original entries of the S
+// columns, then each child's update matrix added at its sets' places, child
+// after child (the order of the one-CTA extend-add).
+__global__ void __launch_bounds__(256) k_ndb_assemble(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                      const int* __restrict__ sets, const int* __restrict__ inv,
+                                                      BlkSrc src, float* __restrict__ F, const IterCtl* ctl) {
+  if (nd_done(ctl)) return;
+  const NDBig bg = bigs[blockIdx.y];
+  const NDNode nd = nodes[bg.node];
+  const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int* st = sets + nd.s_off;
+  float* fg = F + nd.f_off;
+  NDNode ch[2];
+  for (int c = 0; c < nd.nchild; ++c) ch[c] = nodes[nd.child[c]];
+  for (int p = blockIdx.x * 32 + warp; p < nf && p < blockIdx.x * 32 + 32; p += 8) {
+    const int gp = nd_glob(st, p, nm);
+    int kp[2];
+    for (int c = 0; c < nd.nchild; ++c) {
+      const int t = inv[bg.inv_off[c] + p / nm];
+      kp[c] = t < 0 ? -1 : nm * t + p % nm;
+    }
+    for (int q = lane; q <= p; q += 32) {
+      float v = q < nS ? src(gp, nd_glob(st, q, nm)) : 0.f;
+      for (int c = 0; c < nd.nchild; ++c) {
+        if (kp[c] < 0) continue;
+        const int t = inv[bg.inv_off[c] + q / nm];
+        if (t < 0) continue;
+        const int kq = nm * t + q % nm;
+        const int nSc = ch[c].nm * ch[c].ns, nfc = nSc + ch[c].nm * ch[c].nb;
+        const int a = kp[c] > kq ? kp[c] : kq, b = kp[c] > kq ? kq : kp[c];
+        v += F[ch[c].f_off + (size_t)(nSc + a) * nfc + nSc + b];
+      }
+      fg[(size_t)p * nf + q] = v;
+    }
+  }
+}
+
+// Panel step k0, (a): the diagonal block of every wide front with pivots left,
+// one warp each (the one-CTA factor's step (a)).
+__global__ void __launch_bounds__(32) k_ndb_diag(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                 const int* __restrict__ sets, float* __restrict__ F,
+                                                 int* __restrict__ dropped, int* __restrict__ dmask_out, int k0,
+                                                 const IterCtl* ctl) {
+  if (nd_done(ctl)) return;
+  const NDNode nd = nodes[bigs[blockIdx.x].node];
+  const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
+  if (k0 >= nS) return;
+  const int lane = threadIdx.x, kb = min(PB, nS - k0);
+  float* fg = F + nd.f_off;
+  const int* st = sets + nd.s_off;
+  float a[PB], x[PB];
+#pragma unroll
+  for (int c = 0; c < PB; ++c) a[c] = (lane < kb && c <= lane) ? fg[(size_t)(k0 + lane) * nf + k0 + c] : 0.f;
+  const unsigned dm = nd_diag_factor(a, kb, lane);
+  nd_tri_invert(a, x, kb, lane);
+  // inverse[r][lane] = x[r] into the block's place (r >= lane)
+#pragma unroll
+  for (int r = 0; r < PB; ++r)
+    if (r < kb && lane <= r) fg[(size_t)(k0 + r) * nf + k0 + lane] = x[r];
+  for (int c = 0; c < kb; ++c)
+    if ((dm >> c) & 1u) {
+      for (int j = lane; j < k0; j += 32) fg[(size_t)(k0 + c) * nf + j] = 0.f;
+      if (lane == 0) dropped[nd_glob(st, k0 + c, nm)] = 1;
+    }
+  if (lane == 0) dmask_out[blockIdx.x] = (int)dm;
+}
+
+// (b): the panel below the diagonal block, L[i][blk] = F[i][blk] Dinv^T (one
+// warp per row, lane = column); CTA (x, y): rows r0 + 64x .. of front y.
+__global__ void __launch_bounds__(256) k_ndb_panel(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                   float* __restrict__ F, const int* __restrict__ dmask, int k0,
+                                                   const IterCtl* ctl) {
+  if (nd_done(ctl)) return;
+  const NDNode nd = nodes[bigs[blockIdx.y].node];
+  const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
+  if (k0 >= nS) return;
+  const int kb = min(PB, nS - k0), r0 = k0 + kb;
+  const int rbeg = r0 + 64 * blockIdx.x;
+  if (rbeg >= nf) return;
+  __shared__ float Dinv[PB][PB + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* fg = F + nd.f_off;
+  // Dinv[r][c] = inverse[r][c] (lower), zero above
+  for (int e = tid; e < PB * PB; e += 256) {
+    const int r = e / PB, c = e % PB;
+    Dinv[r][c] = (r < kb && c <= r) ? fg[(size_t)(k0 + r) * nf + k0 + c] : 0.f;
+  }
+  __syncthreads();
+  const unsigned dmk = (unsigned)dmask[blockIdx.y];
+  for (int i = rbeg + warp; i < nf && i < rbeg + 64; i += 8) {
+    const float fv = lane < kb ? fg[(size_t)i * nf + k0 + lane] : 0.f;
+    float sacc = 0.f;
+#pragma unroll
+    for (int u = 0; u < PB; ++u) sacc = fmaf(__shfl_sync(0xffffffffu, fv, u), Dinv[lane][u], sacc);
+    if ((dmk >> lane) & 1u) sacc = 0.f;
+    if (lane < kb) fg[(size_t)i * nf + k0 + lane] = sacc;
+  }
+}
+
+// (c): F[i][j] -= sum_u L[i][u] L[j][u] over the trailing lower triangle, in
+// 64 x 64 tiles (CTA x: tile (ti, tj), ti >= tj; y: front), 4 x 4 per thread.
+__global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                    float* __restrict__ F, int k0, const IterCtl* ctl) {
+  if (nd_done(ctl)) return;
+  const NDNode nd = nodes[bigs[blockIdx.y].node];
+  const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
+  if (k0 >= nS) return;
+  const int kb = min(PB, nS - k0), r0 = k0 + kb, m = nf - r0;
+  const int T = (m + 63) / 64;
+  const int t = blockIdx.x;
+  if (t >= T * (T + 1) / 2) return;
+  int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while (ti * (ti + 1) / 2 > t) --ti;
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  const int tj = t - ti * (ti + 1) / 2;
+  __shared__ float La[64][PB + 1], Lb[64][PB + 1];
+  float* fg = F + nd.f_off;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 64 * PB; e += 256) {
+    const int r = e / PB, u = e % PB;
+    const int ia = 64 * ti + r, jb = 64 * tj + r;
+    La[r][u] = (ia < m && u < kb) ? fg[(size_t)(r0 + ia) * nf + k0 + u] : 0.f;
+    Lb[r][u] = (jb < m && u < kb) ? fg[(size_t)(r0 + jb) * nf + k0 + u] : 0.f;
+  }
+  __syncthreads();
+  const int ty = tid / 16, tx = tid % 16;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int u = 0; u < kb; ++u) {
+    float pa[4], pb[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) pa[a] = La[4 * ty + a][u], pb[a] = Lb[4 * tx + a][u];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = 64 * ti + 4 * ty + a;
+    if (i >= m) break;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = 64 * tj + 4 * tx + b;
+      if (j <= i) fg[(size_t)(r0 + i) * nf + r0 + j] -= acc[a][b];
+    }
+  }
 }
 
 // ---------------------------------------------------------------- solves
@@ -354,7 +535,9 @@ constexpr int NDQ = 12;   // columns per lane and pass in the back substitution'
 // partial sums (NDW x nS) and the front's unknown indices (nf ints).  The
 // factor is read where it lies (global, L2-resident): staging it first cost
 // more than the reads themselves, the fronts being small.
-__device__ __host__ inline long long nd_solve_need(long long nS, long long nf) { return nf + NDW * nS + nf; }
+__device__ __host__ inline long long nd_solve_need(long long nS, long long nf) {
+  return nf + (nf > nS ? NDW * nS : 0) + nf;
+}
 
 __global__ void __launch_bounds__(NDT) k_nd_forward(const NDNode* __restrict__ nodes, const int* __restrict__ lvl,
                                                     int lbeg, const int* __restrict__ sets,
@@ -618,15 +801,53 @@ bool nd_plan_build(const LatView& lv, NDPlanHost* P) {
       }
     }
   }
-  // nodes by height: leaves first
+  // nodes by height, leaves first; in a level the one-CTA fronts, then the wide ones
   std::vector<std::vector<int>> byh(H + 1);
   for (int k = 0; k < nn; ++k) byh[hn[k].height].push_back(k);
+  P->level_split.assign(H + 1, 0);
+  P->big_begin.assign(H + 2, 0);
+  P->level_big_ns.assign(H + 1, 0);
+  P->level_big_nf.assign(H + 1, 0);
+  P->bigs.clear();
+  P->inv.clear();
+  P->max_level_bigs = 0;
+  auto nf_of = [&](int k) { return (long long)P->nodes[k].nm * (P->nodes[k].ns + P->nodes[k].nb); };
   for (int h = 0; h <= H; ++h) {
     P->level_begin[h] = (int)P->lvl_nodes.size();
-    P->lvl_nodes.insert(P->lvl_nodes.end(), byh[h].begin(), byh[h].end());
+    for (int k : byh[h])
+      if (nf_of(k) < ND_BIG) P->lvl_nodes.push_back(k);
+    P->level_split[h] = (int)P->lvl_nodes.size();
+    P->big_begin[h] = (int)P->bigs.size();
+    for (int k : byh[h]) {
+      if (nf_of(k) < ND_BIG) continue;
+      P->lvl_nodes.push_back(k);
+      NDBig b{};
+      b.node = k;
+      // per child: place of each of this front's sets in the child's boundary list
+      const HNode& hk = hn[k];
+      for (int c = 0; c < hk.nchild; ++c) {
+        std::unordered_map<int, int> where;
+        const std::vector<int>& cb = hn[hk.child[c]].B;
+        for (size_t q = 0; q < cb.size(); ++q) where[cb[q]] = (int)q;
+        b.inv_off[c] = (int)P->inv.size();
+        for (int J : hk.S) {
+          auto it = where.find(J);
+          P->inv.push_back(it == where.end() ? -1 : it->second);
+        }
+        for (int J : hk.B) {
+          auto it = where.find(J);
+          P->inv.push_back(it == where.end() ? -1 : it->second);
+        }
+      }
+      P->bigs.push_back(b);
+      P->level_big_ns[h] = std::max(P->level_big_ns[h], P->nodes[k].nm * P->nodes[k].ns);
+      P->level_big_nf[h] = std::max(P->level_big_nf[h], (int)nf_of(k));
+    }
     P->max_level_nodes = std::max(P->max_level_nodes, (int)byh[h].size());
+    P->max_level_bigs = std::max(P->max_level_bigs, (int)P->bigs.size() - P->big_begin[h]);
   }
   P->level_begin[H + 1] = (int)P->lvl_nodes.size();
+  P->big_begin[H + 1] = (int)P->bigs.size();
   P->nlevels = H + 1;
   return true;
 }
@@ -649,7 +870,8 @@ bool nd_plan_smem(NDPlanHost* P, int max_smem) {
     for (int k = P->level_begin[h]; k < P->level_begin[h + 1]; ++k) {
       const NDNode& d = P->nodes[P->lvl_nodes[k]];
       const long long nS = (long long)d.nm * d.ns, nf = (long long)d.nm * (d.ns + d.nb);
-      const long long fneed = nd_factor_need(nf, cap);
+      // wide fronts are factored by the panel kernels (static shared memory only)
+      const long long fneed = k < P->level_split[h] ? nd_factor_need(nf, cap) : 0;
       const long long sneed = nd_solve_need(nS, nf);
       if (fneed > cap || sneed > cap) return false;
       nfac = std::max(nfac, fneed);
@@ -661,16 +883,41 @@ bool nd_plan_smem(NDPlanHost* P, int max_smem) {
   return true;
 }
 
-cudaError_t launch_nd_factor(cudaStream_t s, const NDPlanHost& P, const NDPlanDev& D, const float* frow, int bw,
-                             int* dropped, const IterCtl* ctl) {
+cudaError_t launch_nd_factor(cudaStream_t s, const LatView& lv, const NDPlanHost& P, const NDPlanDev& D,
+                             const double* blk, const double* scale, int* dropped, const IterCtl* ctl) {
+  BlkSrc src;
+  src.blk = blk;
+  src.scale = scale;
+  src.dropped = dropped;
+  src.Mx = lv.Mx;
+  src.nm = lv.q;
+  cudaError_t e;
   for (int h = 0; h < P.nlevels; ++h) {
-    const int b = P.level_begin[h], n = P.level_begin[h + 1] - b;
-    if (n <= 0) continue;
-    const size_t smem = P.level_smem_factor[h];
-    k_nd_factor<<<n, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.maps, frow, bw, D.F, dropped,
-                                     (long long)(smem / sizeof(float)), ctl);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    const int b = P.level_begin[h], n = P.level_split[h] - b;
+    if (n > 0) {
+      const size_t smem = P.level_smem_factor[h];
+      k_nd_factor<<<n, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.maps, src, D.F, dropped,
+                                       (long long)(smem / sizeof(float)), ctl);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int nb = P.big_begin[h + 1] - P.big_begin[h];
+    if (nb <= 0) continue;
+    const NDBig* bg = D.bigs + P.big_begin[h];
+    const int maxnf = P.level_big_nf[h];
+    k_ndb_assemble<<<dim3((maxnf + 31) / 32, nb), 256, 0, s>>>(D.nodes, bg, D.sets, D.inv, src, D.F, ctl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int k0 = 0; k0 < P.level_big_ns[h]; k0 += PB) {
+      k_ndb_diag<<<nb, 32, 0, s>>>(D.nodes, bg, D.sets, D.F, dropped, D.dmask, k0, ctl);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      // the largest trailing size over the level's fronts that still have pivots
+      const long long m = (long long)maxnf - k0 - 1;
+      const int rows = (int)((m + 63) / 64);
+      const long long T = (m + 63) / 64;
+      k_ndb_panel<<<dim3(std::max(rows, 1), nb), 256, 0, s>>>(D.nodes, bg, D.F, D.dmask, k0, ctl);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      k_ndb_update<<<dim3((unsigned)std::max(T * (T + 1) / 2, 1LL), nb), 256, 0, s>>>(D.nodes, bg, D.F, k0, ctl);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }

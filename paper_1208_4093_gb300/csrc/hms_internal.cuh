@@ -34,6 +34,18 @@ constexpr int SLOT_SIZE = SLOT_DIM * SLOT_DIM;
 __host__ __device__ inline int slot_dim(int q) { return 2 * q; }
 __host__ __device__ inline int slot_size(int q) { return 4 * q * q; }
 
+// blocks of K_aa kept per set (coarse_blocks.cu): the diagonal block and those
+// of the four later neighbours J > I in row-major set order, K_aa[J][I]
+enum Blk { BLK_SELF = 0, BLK_E, BLK_NW, BLK_N, BLK_NE, NBLK };
+__host__ __device__ inline int blk_dx(int b) { return b == BLK_E || b == BLK_NE ? 1 : (b == BLK_NW ? -1 : 0); }
+__host__ __device__ inline int blk_dy(int b) { return b >= BLK_NW ? 1 : 0; }
+// block index of the later neighbour at offset (dx, dy); 0 if it is none
+__host__ __device__ inline int blk_of(int dx, int dy) {
+  if (dy == 0) return dx == 1 ? BLK_E : 0;
+  if (dy != 1) return 0;
+  return dx == -1 ? BLK_NW : (dx == 0 ? BLK_N : (dx == 1 ? BLK_NE : 0));
+}
+
 // device error flags (bit mask in a device int)
 enum DevErr { DEVERR_NOT_SPD = 1, DEVERR_TIMEOUT = 2, DEVERR_NONFINITE = 4, DEVERR_COARSE = 8 };
 
@@ -389,6 +401,17 @@ cudaError_t configure_setup(int max_smem);
 cudaError_t configure_relax(int max_smem);
 cudaError_t configure_coarse_assemble(int max_smem);
 cudaError_t configure_coarse_solve(int max_smem);
+// coarse_blocks.cu: K_aa by blocks of the set grid (the nested-dissection path)
+size_t coarse_blocks_elems(const LatView& lv);
+cudaError_t launch_blocks_from_slots(cudaStream_t s, const LatView& lv, const double* base, const double* slots,
+                                     double* blk, const IterCtl* ctl);
+cudaError_t launch_blk_diag(cudaStream_t s, const LatView& lv, const double* blk, const double* P, double* scale,
+                            double* b, double* x, int* dropped, unsigned mode_mask, const IterCtl* ctl);
+cudaError_t launch_blk_residual(cudaStream_t s, const LatView& lv, const double* blk, const double* scale,
+                                const int* dropped, const double* b, const double* x, double* res,
+                                unsigned long long* cstat, const IterCtl* ctl);
+cudaError_t launch_blocks_from_dense(cudaStream_t s, const LatView& lv, const double* dense, double* blk);
+cudaError_t launch_dense_from_blocks(cudaStream_t s, const LatView& lv, const double* blk, double* dense);
 // coarse_nd.cu: nested-dissection factor and solve of Eq. 8 over the set grid.
 // A tree node (front): its own sets S and boundary sets B (lists of set
 // indices at s_off: S then B), up to two children whose boundary sets sit at
@@ -402,23 +425,42 @@ struct NDNode {
   int nm, pad;  // modes per set (9 or 12)
   long long f_off, w_off;
 };
+// A wide front (at least ND_BIG unknowns) is factored by many CTAs, panel by
+// panel: its node, and per child the place of each of its sets (S then B) in
+// the child's boundary list (-1 if absent), at inv_off[c].
+constexpr int ND_BIG = 1024;
+struct NDBig {
+  int node;
+  int inv_off[2];
+  int pad;
+};
 struct NDPlanHost {
   std::vector<NDNode> nodes;
-  std::vector<int> sets, maps, lvl_nodes, level_begin;  // nodes by height: leaves first
+  // nodes by height, leaves first; within a level the fronts factored by one
+  // CTA each first, then the wide ones ([level_split[h], level_begin[h + 1]))
+  std::vector<int> sets, maps, lvl_nodes, level_begin, level_split;
+  std::vector<NDBig> bigs;          // the wide fronts, level by level (bigs[k] <-> lvl_nodes[level_split[h] + ...])
+  std::vector<int> big_begin, inv;  // per level: first entry in bigs; inverse child maps
+  std::vector<int> level_big_ns;    // per level: the largest pivot count of its wide fronts (unknowns)
+  std::vector<int> level_big_nf;    // per level: the largest of its wide fronts (unknowns)
   std::vector<size_t> level_smem_factor, level_smem_solve;  // dynamic shared memory per level's launches
-  int nlevels = 0, max_front = 0, max_level_nodes = 0;
+  int nlevels = 0, max_front = 0, max_level_nodes = 0, max_level_bigs = 0;
   size_t f_elems = 0, w_elems = 0;
 };
 struct NDPlanDev {
   NDNode* nodes = nullptr;
   int *sets = nullptr, *maps = nullptr, *lvl_nodes = nullptr;
+  NDBig* bigs = nullptr;
+  int *inv = nullptr, *dmask = nullptr;
   float *F = nullptr, *W = nullptr, *y = nullptr, *xc = nullptr;
 };
 bool nd_plan_build(const LatView& lv, NDPlanHost* P);
 bool nd_plan_smem(NDPlanHost* P, int max_smem);  // false if a front is too large
 cudaError_t configure_coarse_nd(int max_smem);
-cudaError_t launch_nd_factor(cudaStream_t s, const NDPlanHost& P, const NDPlanDev& D, const float* frow, int bw,
-                             int* dropped, const IterCtl* ctl);
+// the scaled matrix (Eq. 8 after Jacobi scaling) comes from the blocks of
+// coarse_blocks.cu with the scale and drop flags of k_blk_diag
+cudaError_t launch_nd_factor(cudaStream_t s, const LatView& lv, const NDPlanHost& P, const NDPlanDev& D,
+                             const double* blk, const double* scale, int* dropped, const IterCtl* ctl);
 cudaError_t launch_nd_solve(cudaStream_t s, int n, const NDPlanHost& P, const NDPlanDev& D, const double* rhs,
                             double* x, const double* scale, double* a_out, const int* dropped,
                             unsigned long long* cstat, int flags, const IterCtl* ctl);

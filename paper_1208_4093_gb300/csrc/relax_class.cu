@@ -132,9 +132,10 @@ __global__ void __launch_bounds__(NTC + 32) k_relax_class(LatView lv, ClassPlanD
   const size_t yrow = (size_t)cp.nb8max * TS;
   const T* fcls = fac + ci.off;
 
-  // this warp's groups (gA, and gB if it is another one)
+  // this warp's groups: w and NG-1-w while w < NG-1-w, the middle group alone
+  // when they coincide, none above (those groups are a lower warp's)
   const int gA = warp, gB = NG - 1 - warp;
-  const int ngrp = producer ? 0 : (gA < NG ? (gB > gA ? 2 : 1) : 0);
+  const int ngrp = producer ? 0 : (gA < gB ? 2 : (gA == gB ? 1 : 0));
   // this lane's sets
   size_t nbase[SPL];
   bool valid[SPL];

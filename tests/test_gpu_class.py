@@ -50,6 +50,9 @@ CASES = [
     ("roller", 30, 26, 6, 6, roller_left),
     ("scattered_supports", 48, 40, 8, 8, pinned_spots),   # supports split classes
     ("one_node_wide", 9, 12, 1, 4, None),
+    # the set shapes of the 22361 x 22361 lattice: 64 x 64-node sets, the
+    # last row and column of sets 25 nodes wide, bottom row clamped
+    ("paper_scale_shapes", 217, 217, 64, 64, None),
 ]
 PRECS = [0, 1]
 
@@ -86,7 +89,7 @@ def test_class_relax_step(hms_ctx, case, prec):
         capi.hms_problem_destroy(pr)
 
 
-@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[5], CASES[6]], ids=lambda c: c[0])
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[5], CASES[6], CASES[8]], ids=lambda c: c[0])
 @pytest.mark.parametrize("prec", PRECS, ids=["fp64", "mixed"])
 def test_class_solve_matches_direct(hms_ctx, case, prec):
     """Whole solves to R1 < 1e-10 against the direct solve (T2 bars), and the

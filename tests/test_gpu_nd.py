@@ -92,12 +92,15 @@ def test_nd_full_solve_and_trajectory(hms_ctx, case, precision):
             capi.hms_problem_destroy(pr)
 
 
-@pytest.mark.parametrize("nx,ny,sx,sy", [(2048, 256, 32, 32), (512, 512, 16, 16), (1600, 96, 16, 24)],
-                         ids=["64x8_sets", "32x32_sets", "100x4_sets"])
+@pytest.mark.parametrize("nx,ny,sx,sy", [(2048, 256, 32, 32), (512, 512, 16, 16), (1600, 96, 16, 24),
+                                         (320, 320, 4, 4), (600, 420, 5, 5)],
+                         ids=["64x8_sets", "32x32_sets", "100x4_sets", "80x80_sets", "120x84_sets"])
 def test_wide_set_grids_accepted_and_exact(hms_ctx, nx, ny, sx, sy):
-    """Set grids far wider than a band window (64, 32 and 100 sets across)
-    are taken by the automatic choice and solved to the direct solution
-    (the oracle's sparse direct solve, O1)."""
+    """Set grids far wider than a band window (64, 32, 100, 80 and 120 sets
+    across) are taken by the automatic choice and solved to the direct
+    solution (the oracle's sparse direct solve, O1).  On the 80 x 80 and 120 x
+    84 set grids the top fronts of the dissection have 1080 to 2000 unknowns,
+    so they are factored by the many-CTA panel kernels."""
     from paper_1208_4093_gb300 import capi
     ea = ea_lognormal(nx, ny, 29)
     tr = truss.Truss(nx, ny, ea)
