@@ -73,6 +73,10 @@ def parse():
                          "of 32 x 32-node sets (the shapes of the paper's Tests 2 and 3), FP64, 4 loadings")
     ap.add_argument("--overlap-sweep", action="store_true",
                     help="time to R1 < 1e-8 against the relaxation region's overlap instead (separate JSON line)")
+    ap.add_argument("--paper-scale", action="store_true",
+                    help="the 22361 x 22361-node (1.0e9 DOF) lattice: setup, time per update, kernel split")
+    ap.add_argument("--paper-updates", type=int, default=8, help="updates timed by --paper-scale")
+    ap.add_argument("--paper-full", action="store_true", help="with --paper-scale: also the whole solve to 1e-10")
     ap.add_argument("--serve", type=int, default=0, metavar="N",
                     help="serve N requests of the serving workload instead (separate JSON line)")
     ap.add_argument("--serve-max-active", type=int, default=8,
@@ -569,6 +573,103 @@ def run_overlap_sweep(args):
                       "rows": rows}))
 
 
+# ---------------------------------------------------------------- paper scale
+def run_paper_scale(args):
+    """The paper's largest test (Sec. 3.2, Test 1: about 10^9 DOFs): a 22361 x
+    22361-node lattice, EA = 1, bottom row clamped, loads Uniform(-1, 1) (seed
+    0, drawn on the device by the same Philox recipe as every other workload),
+    350 x 350 sets of 64 x 64 nodes (the last row and column 25 wide), mixed
+    precision, the sets' factors shared by class (class_factors = 1), the
+    upper level (1.1 M unknowns) by nested dissection of the set grid.
+
+    Reports the setup, device memory, the time per update over
+    --paper-updates updates (CUDA events on the context stream; loads already
+    on the device), R1 after them, the per-kernel split of a profiled run of 3
+    updates with each kernel's HBM traffic per node against the measured copy
+    rate, and with --paper-full the whole solve to the configuration's R1 <
+    1e-10."""
+    import torch
+    from paper_1208_4093_gb300 import capi
+    from workloads import CASES, loads_torch
+    c = CASES["lattice22361_mixed"]
+    nn = c.nx * c.ny
+    ctx = capi.hms_context_create(0)
+    stream = torch.cuda.ExternalStream(capi.hms_context_stream(ctx), device=torch.device("cuda", 0))
+    t0 = time.time()
+    p = loads_torch(c.nx, c.ny, c.seed, device="cuda").reshape(1, -1)
+    gen_s = time.time() - t0
+    u = torch.empty_like(p)
+    its = torch.zeros(1, dtype=torch.int32, device="cuda")
+    K = args.paper_updates
+    out = {"metric": "time per upper-level update and to R1 < 1e-10, paper-scale lattice", "unit": "ms",
+           "config": {"workload": c.name, "nx": c.nx, "ny": c.ny, "dofs": 2 * nn, "sets": [c.sx, c.sy],
+                      "set_grid": [-(-c.nx // c.sx), -(-c.ny // c.sy)], "ea": "1", "supports": "bottom row clamped",
+                      "loads": "Uniform(-1,1) seed 0 (Philox, drawn on the device)", "precision": "mixed",
+                      "class_factors": 1, "upper_level": "nested dissection by blocks"},
+           "load_generation_s": gen_s}
+
+    def timed(pr, nupd, tol):
+        hist = torch.zeros((1, nupd + 1, 3), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        capi.hms_solve(ctx, pr, p, u, hist=hist, iters=its, allow_no_convergence=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        n = int(its.item())
+        h = hist[0, :n + 1, 0].cpu().numpy()
+        return a.elapsed_time(b), n, h
+
+    pr = capi.hms_problem_create(ctx, c.nx, c.ny, c.sx, c.sy, precision=capi.HMS_MIXED, tol=0.0, max_iter=K,
+                                 class_factors=1)
+    try:
+        out["setup_ms"] = capi.hms_problem_setup_ms(pr)
+        out["device_bytes"] = capi.hms_problem_device_bytes(pr)
+        timed(pr, K, 0.0)  # warm-up (first graph launches)
+        ms, n, h = timed(pr, K, 0.0)
+        out["updates_timed"] = n
+        out["ms_per_update"] = ms / max(n, 1)
+        out["r1_history"] = [float(x) for x in h]
+    finally:
+        capi.hms_problem_destroy(pr)
+    # per-kernel split (profile mode: CUDA events around every kernel, no graph)
+    pr = capi.hms_problem_create(ctx, c.nx, c.ny, c.sx, c.sy, precision=capi.HMS_MIXED, tol=0.0, max_iter=3,
+                                 class_factors=1, profile=1)
+    try:
+        capi.hms_solve(ctx, pr, p, u, iters=its, allow_no_convergence=True)
+        kt = capi.hms_kernel_times(pr)
+        n = max(int(its.item()), 1)
+        hbm = peaks()[0]
+        # algorithmic bytes per node of the per-node kernels (uniform EA: no bar array)
+        bytes_per_node = {"update_residual": 16 + 16 + 8 + 16 + 16 + 1, "relax": 16 + 8 + 2 * 8,
+                          "coarse_assemble": 8}
+        split = {}
+        for k, (tms, cnt) in kt.items():
+            e = {"ms_per_update": tms / n, "launches": cnt}
+            if k in bytes_per_node and tms > 0:
+                gbs = bytes_per_node[k] * nn / (tms / n * 1e-3) / 1e9
+                e.update({"bytes_per_node": bytes_per_node[k], "hbm_gbs": gbs, "hbm_frac": gbs / hbm})
+            split[k] = e
+        out["kernel_split"] = split
+        out["kernel_split_note"] = ("profile mode (CUDA events around every kernel, no graph), 3 updates; "
+                                    "update_residual and coarse_assemble are bound by the FP64 pipe, the class "
+                                    "relaxation by the FP32 pipe, the upper level by its chain of fronts")
+    finally:
+        capi.hms_problem_destroy(pr)
+    if args.paper_full:
+        pr = capi.hms_problem_create(ctx, c.nx, c.ny, c.sx, c.sy, precision=capi.HMS_MIXED, tol=c.tol,
+                                     max_iter=6000, class_factors=1)
+        try:
+            ms, n, h = timed(pr, 6000, c.tol)
+            out["full_solve"] = {"tol": c.tol, "ms": ms, "updates": n, "r1_final": float(h[-1]),
+                                 "ms_per_update": ms / max(n, 1),
+                                 "dofs_per_s": 2 * nn / (ms * 1e-3)}
+        finally:
+            capi.hms_problem_destroy(pr)
+    capi.hms_context_destroy(ctx)
+    print(json.dumps(out))
+
+
 # ---------------------------------------------------------------- serving
 def serve_measure(count, max_active):
     """Requests arrive by a Poisson process (mean 200 per second) with
@@ -924,6 +1025,8 @@ def main():
             run_nir_sweep(args)
         elif args.overlap_sweep:
             run_overlap_sweep(args)
+        elif args.paper_scale:
+            run_paper_scale(args)
         elif args.serve:
             run_serve(args)
         elif args.impl == "reference":

@@ -34,6 +34,16 @@ def test_philox_known_answers():
         assert got == out
 
 
+def test_device_load_generator_equals_host():
+    """loads_torch (the generator of the 10^9-DOF workload, run on the device
+    there) draws the same Philox words and maps them the same way: bitwise the
+    loads of `loads`, across chunk boundaries and 64-bit seeds."""
+    torch = pytest.importorskip("torch")
+    from workloads import loads_torch
+    for nx, ny, seed, rhs, chunk in ((37, 29, 0, 0, 500), (64, 64, 5, 3, 1 << 20), (101, 7, 2**33 + 7, 1, 64)):
+        assert np.array_equal(loads(nx, ny, seed, rhs), loads_torch(nx, ny, seed, rhs, chunk=chunk).numpy())
+
+
 def test_load_and_ea_distributions():
     p = loads(300, 200, 5)
     assert p.shape == (200, 300, 2)

@@ -25,7 +25,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "philox4x32_10", "uniform01", "loads", "ea_lognormal", "clamp_bottom",
+    "philox4x32_10", "uniform01", "loads", "loads_torch", "ea_lognormal", "clamp_bottom",
     "LatticeCase", "CASES",
 ]
 
@@ -95,6 +95,43 @@ def loads(nx: int, ny: int, seed: int, rhs: int = 0) -> np.ndarray:
     out[..., 0] = (2.0 * uniform01(w0) - 1.0).reshape(ny, nx)
     out[..., 1] = (2.0 * uniform01(w1) - 1.0).reshape(ny, nx)
     return out
+
+
+def _mulhilo_t(a, m: int):
+    """High and low 32-bit words of a * m (a: int64 tensor of uint32 values,
+    m < 2^32), by 16-bit halves so that no int64 product overflows."""
+    m1, m0 = m >> 16, m & 0xFFFF
+    a1, a0 = a >> 16, a & 0xFFFF
+    mid = a1 * m0 + a0 * m1
+    t = a0 * m0 + ((mid & 0xFFFF) << 16)
+    return a1 * m1 + (mid >> 16) + (t >> 32), t & 0xFFFFFFFF
+
+
+def loads_torch(nx: int, ny: int, seed: int, rhs: int = 0, device="cpu", chunk: int = 1 << 25):
+    """The loads of `loads` (the same Philox4x32-10 draws, bit for bit) as a
+    torch float64 tensor [ny, nx, 2] made on `device`, chunk nodes at a time:
+    for lattices whose loads are too large to draw on the host (10^9 DOFs)."""
+    import torch
+
+    out = torch.empty((ny * nx, 2), dtype=torch.float64, device=device)
+    k0, k1 = seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF
+    inv = 1.0 / 4294967296.0
+    for n0 in range(0, nx * ny, chunk):
+        n = torch.arange(n0, min(n0 + chunk, nx * ny), dtype=torch.int64, device=device)
+        c0, c1 = n & 0xFFFFFFFF, n >> 32
+        c2 = torch.full_like(n, rhs & 0xFFFFFFFF)
+        c3 = torch.full_like(n, TAG_LOAD)
+        a0, a1 = k0, k1
+        for rnd in range(10):
+            if rnd:
+                a0 = (a0 + int(_W0)) & 0xFFFFFFFF
+                a1 = (a1 + int(_W1)) & 0xFFFFFFFF
+            hi0, lo0 = _mulhilo_t(c0, int(_M0))
+            hi1, lo1 = _mulhilo_t(c2, int(_M1))
+            c0, c1, c2, c3 = hi1 ^ c1 ^ a0, lo1, hi0 ^ c3 ^ a1, lo0
+        out[n0:n0 + n.numel(), 0] = 2.0 * ((c0.double() + 0.5) * inv) - 1.0
+        out[n0:n0 + n.numel(), 1] = 2.0 * ((c1.double() + 0.5) * inv) - 1.0
+    return out.view(ny, nx, 2)
 
 
 def ea_lognormal(nx: int, ny: int, seed: int, sigma: float = 0.3) -> np.ndarray:
