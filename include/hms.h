@@ -34,7 +34,10 @@
  *   pointers on the context's device (HMS_MEM_DEVICE, e.g. torch tensors'
  *   data_ptr()).  The library copies every input it keeps; outputs go to
  *   caller-owned buffers.  Calls are ordered on the context's stream and
- *   return after the results are in the caller's buffers.
+ *   return after the results are in the caller's buffers.  Device inputs are
+ *   read on the context's stream: work that produces them on another stream
+ *   must be complete (or ordered before the call by the caller) when the call
+ *   starts; the Python binding waits for torch's current stream.
  * Errors: every function returns an hms_status (0 = HMS_OK, negative = error)
  *   and never throws; hms_last_error() gives a message.  Handles are opaque
  *   and not thread-safe: use one handle from one thread at a time.

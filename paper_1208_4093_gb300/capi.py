@@ -148,6 +148,10 @@ class _Arg:
             else:
                 if not x.is_contiguous():
                     raise ValueError("device tensors must be contiguous")
+                # the library reads and writes on its own stream: work torch has
+                # queued on the tensor (on torch's current stream) must finish first
+                import torch
+                torch.cuda.current_stream(x.device).synchronize()
                 self.ptr, self.kind, self.keep = x.data_ptr(), HMS_MEM_DEVICE, x
                 return
         if x is not None:
