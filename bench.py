@@ -77,6 +77,8 @@ def parse():
                     help="the 22361 x 22361-node (1.0e9 DOF) lattice: setup, time per update, kernel split")
     ap.add_argument("--paper-updates", type=int, default=8, help="updates timed by --paper-scale")
     ap.add_argument("--paper-full", action="store_true", help="with --paper-scale: also the whole solve to 1e-10")
+    ap.add_argument("--no-paper-scale", action="store_true",
+                    help="leave the paper-scale leg (a few updates of the 10^9-DOF lattice) out of the bench line")
     ap.add_argument("--serve", type=int, default=0, metavar="N",
                     help="serve N requests of the serving workload instead (separate JSON line)")
     ap.add_argument("--serve-max-active", type=int, default=8,
@@ -574,7 +576,7 @@ def run_overlap_sweep(args):
 
 
 # ---------------------------------------------------------------- paper scale
-def run_paper_scale(args):
+def paper_scale_measure(updates, full=False, split=True):
     """The paper's largest test (Sec. 3.2, Test 1: about 10^9 DOFs): a 22361 x
     22361-node lattice, EA = 1, bottom row clamped, loads Uniform(-1, 1) (seed
     0, drawn on the device by the same Philox recipe as every other workload),
@@ -582,12 +584,11 @@ def run_paper_scale(args):
     precision, the sets' factors shared by class (class_factors = 1), the
     upper level (1.1 M unknowns) by nested dissection of the set grid.
 
-    Reports the setup, device memory, the time per update over
-    --paper-updates updates (CUDA events on the context stream; loads already
-    on the device), R1 after them, the per-kernel split of a profiled run of 3
+    Returns the setup, device memory, the time per update over `updates`
+    updates (CUDA events on the context stream; loads already on the device),
+    R1 after them, with `split` the per-kernel split of a profiled run of 3
     updates with each kernel's HBM traffic per node against the measured copy
-    rate, and with --paper-full the whole solve to the configuration's R1 <
-    1e-10."""
+    rate, and with `full` the whole solve to the configuration's R1 < 1e-10."""
     import torch
     from paper_1208_4093_gb300 import capi
     from workloads import CASES, loads_torch
@@ -600,7 +601,7 @@ def run_paper_scale(args):
     gen_s = time.time() - t0
     u = torch.empty_like(p)
     its = torch.zeros(1, dtype=torch.int32, device="cuda")
-    K = args.paper_updates
+    K = updates
     out = {"metric": "time per upper-level update and to R1 < 1e-10, paper-scale lattice", "unit": "ms",
            "config": {"workload": c.name, "nx": c.nx, "ny": c.ny, "dofs": 2 * nn, "sets": [c.sx, c.sy],
                       "set_grid": [-(-c.nx // c.sx), -(-c.ny // c.sy)], "ea": "1", "supports": "bottom row clamped",
@@ -634,8 +635,10 @@ def run_paper_scale(args):
         capi.hms_problem_destroy(pr)
     # per-kernel split (profile mode: CUDA events around every kernel, no graph)
     pr = capi.hms_problem_create(ctx, c.nx, c.ny, c.sx, c.sy, precision=capi.HMS_MIXED, tol=0.0, max_iter=3,
-                                 class_factors=1, profile=1)
+                                 class_factors=1, profile=1) if split else None
     try:
+        if pr is None:
+            raise StopIteration
         capi.hms_solve(ctx, pr, p, u, iters=its, allow_no_convergence=True)
         kt = capi.hms_kernel_times(pr)
         n = max(int(its.item()), 1)
@@ -654,9 +657,12 @@ def run_paper_scale(args):
         out["kernel_split_note"] = ("profile mode (CUDA events around every kernel, no graph), 3 updates; "
                                     "update_residual and coarse_assemble are bound by the FP64 pipe, the class "
                                     "relaxation by the FP32 pipe, the upper level by its chain of fronts")
+    except StopIteration:
+        pass
     finally:
-        capi.hms_problem_destroy(pr)
-    if args.paper_full:
+        if pr is not None:
+            capi.hms_problem_destroy(pr)
+    if full:
         pr = capi.hms_problem_create(ctx, c.nx, c.ny, c.sx, c.sy, precision=capi.HMS_MIXED, tol=c.tol,
                                      max_iter=6000, class_factors=1)
         try:
@@ -667,7 +673,13 @@ def run_paper_scale(args):
         finally:
             capi.hms_problem_destroy(pr)
     capi.hms_context_destroy(ctx)
-    print(json.dumps(out))
+    del p, u
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_paper_scale(args):
+    print(json.dumps(paper_scale_measure(args.paper_updates, full=args.paper_full)))
 
 
 # ---------------------------------------------------------------- serving
@@ -949,6 +961,17 @@ def run_ours(args, rank, world, local_rank):
     if args.serve_in_bench > 0 and world == 1:
         serve = serve_measure(args.serve_in_bench, args.serve_max_active)
 
+    # ---- the paper-scale lattice (10^9 DOFs): setup and time per update ----
+    paper = None
+    if not args.no_paper_scale and world == 1:
+        try:
+            paper = paper_scale_measure(4)
+            paper.pop("metric", None)
+            paper["full_solve_note"] = ("the whole solve to R1 < 1e-10 is `bench.py --paper-scale --paper-full` "
+                                        "(minutes; not part of the default line)")
+        except Exception as e:  # e.g. a device with less memory
+            paper = {"skipped": str(e)}
+
     ms_med = statistics.median(ms64)
     if world > 1:
         ms_med = max_over_ranks(max(ms64), dev)
@@ -995,6 +1018,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": statistics.median(e2e), "unit": "ms", "h2d_bytes_per_step": 8 * nd,
                 "d2h_bytes_per_step": 8 * nd},
         "serve": serve,
+        "paper_scale": paper,
         "force_modes": force_modes,
         "gpu_launches": launches,
         "clocks": clocks,
