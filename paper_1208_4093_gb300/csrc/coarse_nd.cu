@@ -438,7 +438,13 @@ __global__ void __launch_bounds__(256) k_ndb_panel(const NDNode* __restrict__ no
 }
 
 // (c): F[i][j] -= sum_u L[i][u] L[j][u] over the trailing lower triangle, in
-// 64 x 64 tiles (CTA x: tile (ti, tj), ti >= tj; y: front), 4 x 4 per thread.
+// UT x UT tiles (CTA x: tile (ti, tj), ti >= tj; y: front).  The tile's two
+// panels are staged transposed (Lt[u][row], rows padded by 4 floats) so that a
+// thread reads its rows as float4s; thread (ty, tx) owns rows {4ty.., UT/2 +
+// 4ty..} and columns {4tx.., UT/2 + 4tx..} (8 x 8 sums).  Each sum runs over u
+// in order from 0, as in the one-CTA factor.
+constexpr int UT = 128;
+constexpr int ULD = UT + 4;
 __global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
                                                     float* __restrict__ F, int k0, const IterCtl* ctl) {
   if (nd_done(ctl)) return;
@@ -446,46 +452,52 @@ __global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ n
   const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
   if (k0 >= nS) return;
   const int kb = min(PB, nS - k0), r0 = k0 + kb, m = nf - r0;
-  const int T = (m + 63) / 64;
+  const int T = (m + UT - 1) / UT;
   const int t = blockIdx.x;
   if (t >= T * (T + 1) / 2) return;
   int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
   while (ti * (ti + 1) / 2 > t) --ti;
   while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
   const int tj = t - ti * (ti + 1) / 2;
-  __shared__ float La[64][PB + 1], Lb[64][PB + 1];
+  __shared__ __align__(16) float La[PB][ULD];
+  __shared__ __align__(16) float Lb[PB][ULD];
   float* fg = F + nd.f_off;
   const int tid = threadIdx.x;
-  for (int e = tid; e < 64 * PB; e += 256) {
+  // stage: element e -> row e / PB, column u = e % PB (a warp reads one row's 32 columns)
+  for (int e = tid; e < UT * PB; e += 256) {
     const int r = e / PB, u = e % PB;
-    const int ia = 64 * ti + r, jb = 64 * tj + r;
-    La[r][u] = (ia < m && u < kb) ? fg[(size_t)(r0 + ia) * nf + k0 + u] : 0.f;
-    Lb[r][u] = (jb < m && u < kb) ? fg[(size_t)(r0 + jb) * nf + k0 + u] : 0.f;
+    const int ia = UT * ti + r, jb = UT * tj + r;
+    La[u][r] = (ia < m && u < kb) ? fg[(size_t)(r0 + ia) * nf + k0 + u] : 0.f;
+    Lb[u][r] = (jb < m && u < kb) ? fg[(size_t)(r0 + jb) * nf + k0 + u] : 0.f;
   }
   __syncthreads();
   const int ty = tid / 16, tx = tid % 16;
-  float acc[4][4];
+  float acc[8][8];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
   for (int u = 0; u < kb; ++u) {
-    float pa[4], pb[4];
+    const float4 a0 = *reinterpret_cast<const float4*>(&La[u][4 * ty]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&La[u][UT / 2 + 4 * ty]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&Lb[u][4 * tx]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&Lb[u][UT / 2 + 4 * tx]);
+    const float pa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float pb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-    for (int a = 0; a < 4; ++a) pa[a] = La[4 * ty + a][u], pb[a] = Lb[4 * tx + a][u];
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
+      for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int i = 64 * ti + 4 * ty + a;
-    if (i >= m) break;
+  for (int a = 0; a < 8; ++a) {
+    const int i = UT * ti + (a < 4 ? 4 * ty + a : UT / 2 + 4 * ty + a - 4);
+    if (i >= m) continue;
+    float* row = fg + (size_t)(r0 + i) * nf + r0;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = 64 * tj + 4 * tx + b;
-      if (j <= i) fg[(size_t)(r0 + i) * nf + r0 + j] -= acc[a][b];
+    for (int b = 0; b < 8; ++b) {
+      const int j = UT * tj + (b < 4 ? 4 * tx + b : UT / 2 + 4 * tx + b - 4);
+      if (j <= i) row[j] -= acc[a][b];
     }
   }
 }
@@ -528,7 +540,7 @@ __global__ void __launch_bounds__(1024) k_nd_solve_begin(int n, const double* __
   }
 }
 
-constexpr int RU = 4;     // rows per warp in flight in the forward solve's row products
+constexpr int RU = 16;    // rows per warp in flight in the forward solve's row products
 constexpr int NDQ = 12;   // columns per lane and pass in the back substitution's first product
 
 // Shared memory of a solve CTA (floats): the front's vector (nf), the warps'
@@ -552,6 +564,8 @@ __global__ void __launch_bounds__(NDT) k_nd_forward(const NDNode* __restrict__ n
   const NDNode nd = nodes[lvl[lbeg + blockIdx.x]];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
+  // a wide front's boundary rows are updated by k_ndb_fwd_rect, after this kernel
+  const int nrow = nf >= ND_BIG ? nS : nf;
   const float* f = F + nd.f_off;
   const int* st = sets + nd.s_off;
   float* fv = ndsm;
@@ -589,16 +603,16 @@ __global__ void __launch_bounds__(NDT) k_nd_forward(const NDNode* __restrict__ n
     const float yl = lane < kb ? yb[lane] : 0.f;
     if (tid < kb) fv[k0 + tid] = yb[tid];
     // rows below: f_i -= L[i][blk] y_blk, RU rows per warp at once
-    for (int i0 = k0 + kb + RU * warp; i0 < nf; i0 += RU * NDW) {
+    for (int i0 = k0 + kb + RU * warp; i0 < nrow; i0 += RU * NDW) {
       float v[RU];
 #pragma unroll
       for (int q = 0; q < RU; ++q) {
         const int i = i0 + q;
-        v[q] = (i < nf && lane < kb) ? Lp[(size_t)i * ld + k0 + lane] * yl : 0.f;
+        v[q] = (i < nrow && lane < kb) ? Lp[(size_t)i * ld + k0 + lane] * yl : 0.f;
       }
 #pragma unroll
       for (int q = 0; q < RU; ++q) v[q] = warp_sum_f(v[q]);
-      if (lane < RU && i0 + lane < nf) {
+      if (lane < RU && i0 + lane < nrow) {
         float mine = v[0];
 #pragma unroll
         for (int q = 1; q < RU; ++q) mine = lane == q ? v[q] : mine;
@@ -640,7 +654,9 @@ __global__ void __launch_bounds__(NDT) k_nd_backward(const NDNode* __restrict__ 
   __syncthreads();
   // t = y_S - L_BS^T x_B: warp w sums the rows k = w, w + NDW, ... (lane: columns
   // lane + 32 q), then the warps' partial sums are added in warp order
-  for (int jb = 0; nB > 0 && jb < nS; jb += 32 * NDQ) {
+  // (a wide front's t was formed by k_ndb_bwd_rect, in the same order, into y)
+  const bool rect = nB > 0 && nf < ND_BIG;
+  for (int jb = 0; rect && jb < nS; jb += 32 * NDQ) {
     float acc[NDQ];
 #pragma unroll
     for (int q = 0; q < NDQ; ++q) acc[q] = 0.f;
@@ -662,7 +678,7 @@ __global__ void __launch_bounds__(NDT) k_nd_backward(const NDNode* __restrict__ 
   __syncthreads();
   for (int j = tid; j < nS; j += NDT) {
     float sacc = y[gidx[j]];
-    if (nB > 0)
+    if (rect)
       for (int w = 0; w < NDW; ++w) sacc -= part[w * nS + j];
     tv[j] = sacc;
   }
@@ -684,9 +700,13 @@ __global__ void __launch_bounds__(NDT) k_nd_backward(const NDNode* __restrict__ 
     if (tid < kb) tv[k0 + tid] = xb[tid];
     // earlier columns: t_j -= sum_r L[k0 + r][j] x_r
     for (int j = tid; j < k0; j += NDT) {
+      float lv[PB];
+#pragma unroll
+      for (int r = 0; r < PB; ++r) lv[r] = r < kb ? Lp[(size_t)(k0 + r) * ld + j] : 0.f;
       float sacc = tv[j];
-#pragma unroll 8
-      for (int r = 0; r < kb; ++r) sacc = fmaf(-Lp[(size_t)(k0 + r) * ld + j], xb[r], sacc);
+#pragma unroll
+      for (int r = 0; r < PB; ++r)
+        if (r < kb) sacc = fmaf(-lv[r], xb[r], sacc);
       tv[j] = sacc;
     }
     __syncthreads();
@@ -699,6 +719,73 @@ __global__ void __launch_bounds__(NDT) k_nd_backward(const NDNode* __restrict__ 
     x[g] = xi;
     a_out[g] = scale[g] * xi;
   }
+}
+
+// Forward solve of a wide front, its boundary rows: W_k -= L[nS+k][blk] y_blk
+// panel by panel, each panel's products summed by the warp tree of
+// k_nd_forward, in its order (so the result is the one-CTA solve's).  CTA
+// (x, y): rows nS + 32x .. + 31 of front y, four per warp.
+__global__ void __launch_bounds__(256) k_ndb_fwd_rect(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                      const int* __restrict__ sets, const float* __restrict__ F,
+                                                      const float* __restrict__ y, float* __restrict__ W,
+                                                      const unsigned long long* cstat, const IterCtl* ctl) {
+  if (nd_done(ctl) || *(volatile const unsigned long long*)&cstat[2]) return;
+  extern __shared__ __align__(16) float ndsm[];  // y_S of the front
+  const NDNode nd = nodes[bigs[blockIdx.y].node];
+  const int nm = nd.nm, nS = nm * nd.ns, nB = nm * nd.nb, nf = nS + nB;
+  const int kbeg = 32 * blockIdx.x;
+  if (kbeg >= nB) return;
+  const int* st = sets + nd.s_off;
+  for (int j = threadIdx.x; j < nS; j += blockDim.x) ndsm[j] = y[nd_glob(st, j, nm)];
+  __syncthreads();
+  const float* f = F + nd.f_off;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = kbeg + warp; k < nB && k < kbeg + 32; k += 8) {
+    const float* row = f + (size_t)(nS + k) * nf;
+    float acc = W[nd.w_off + k];
+    for (int k0 = 0; k0 < nS; k0 += PB) {
+      const int kb = min(PB, nS - k0);
+      const float v = lane < kb ? row[k0 + lane] * ndsm[k0 + lane] : 0.f;
+      acc -= warp_sum_f(v);
+    }
+    if (lane == 0) W[nd.w_off + k] = acc;
+  }
+}
+
+// Back substitution of a wide front, t = y_S - L_BS^T x_B: per column j the
+// NDW partial sums over the boundary rows k = w, w + NDW, ... and their
+// difference from y in w order, as k_nd_backward forms them; written into y.
+// Thread per column (256 per CTA); CTA y: the front.
+__global__ void __launch_bounds__(256) k_ndb_bwd_rect(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                      const int* __restrict__ sets, const float* __restrict__ F,
+                                                      const float* __restrict__ xc, float* __restrict__ y,
+                                                      const unsigned long long* cstat, const IterCtl* ctl) {
+  if (nd_done(ctl) || *(volatile const unsigned long long*)&cstat[2]) return;
+  extern __shared__ __align__(16) float ndsm[];  // x_B of the front
+  const NDNode nd = nodes[bigs[blockIdx.y].node];
+  const int nm = nd.nm, nS = nm * nd.ns, nB = nm * nd.nb, nf = nS + nB;
+  if (nB == 0 || 256 * (int)blockIdx.x >= nS) return;
+  const int* st = sets + nd.s_off;
+  for (int k = threadIdx.x; k < nB; k += blockDim.x) ndsm[k] = xc[nd_glob(st, nS + k, nm)];
+  __syncthreads();
+  const int j = 256 * blockIdx.x + threadIdx.x;
+  if (j >= nS) return;
+  const float* col = F + nd.f_off + (size_t)nS * nf + j;
+  float acc[NDW];
+#pragma unroll
+  for (int w = 0; w < NDW; ++w) acc[w] = 0.f;
+  for (int k0 = 0; k0 < nB; k0 += NDW) {
+#pragma unroll
+    for (int w = 0; w < NDW; ++w) {
+      const int k = k0 + w;
+      if (k < nB) acc[w] = fmaf(col[(size_t)k * nf], ndsm[k], acc[w]);
+    }
+  }
+  const int g = nd_glob(st, j, nm);
+  float sacc = y[g];
+#pragma unroll
+  for (int w = 0; w < NDW; ++w) sacc -= acc[w];
+  y[g] = sacc;
 }
 
 }  // namespace
@@ -808,6 +895,7 @@ bool nd_plan_build(const LatView& lv, NDPlanHost* P) {
   P->big_begin.assign(H + 2, 0);
   P->level_big_ns.assign(H + 1, 0);
   P->level_big_nf.assign(H + 1, 0);
+  P->level_big_nb.assign(H + 1, 0);
   P->bigs.clear();
   P->inv.clear();
   P->max_level_bigs = 0;
@@ -842,6 +930,7 @@ bool nd_plan_build(const LatView& lv, NDPlanHost* P) {
       P->bigs.push_back(b);
       P->level_big_ns[h] = std::max(P->level_big_ns[h], P->nodes[k].nm * P->nodes[k].ns);
       P->level_big_nf[h] = std::max(P->level_big_nf[h], (int)nf_of(k));
+      P->level_big_nb[h] = std::max(P->level_big_nb[h], P->nodes[k].nm * P->nodes[k].nb);
     }
     P->max_level_nodes = std::max(P->max_level_nodes, (int)byh[h].size());
     P->max_level_bigs = std::max(P->max_level_bigs, (int)P->bigs.size() - P->big_begin[h]);
@@ -912,7 +1001,7 @@ cudaError_t launch_nd_factor(cudaStream_t s, const LatView& lv, const NDPlanHost
       // the largest trailing size over the level's fronts that still have pivots
       const long long m = (long long)maxnf - k0 - 1;
       const int rows = (int)((m + 63) / 64);
-      const long long T = (m + 63) / 64;
+      const long long T = (m + UT - 1) / UT;
       k_ndb_panel<<<dim3(std::max(rows, 1), nb), 256, 0, s>>>(D.nodes, bg, D.F, D.dmask, k0, ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       k_ndb_update<<<dim3((unsigned)std::max(T * (T + 1) / 2, 1LL), nb), 256, 0, s>>>(D.nodes, bg, D.F, k0, ctl);
@@ -935,10 +1024,22 @@ cudaError_t launch_nd_solve(cudaStream_t s, int n, const NDPlanHost& P, const ND
     k_nd_forward<<<m, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.maps, D.F, D.W, rhs, dropped, D.y,
                                       (long long)(smem / sizeof(float)), cstat, ctl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int nb = P.big_begin[h + 1] - P.big_begin[h];
+    if (nb > 0 && P.level_big_nb[h] > 0) {
+      k_ndb_fwd_rect<<<dim3((P.level_big_nb[h] + 31) / 32, nb), 256, (size_t)P.level_big_ns[h] * sizeof(float), s>>>(
+          D.nodes, D.bigs + P.big_begin[h], D.sets, D.F, D.y, D.W, cstat, ctl);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
   }
   for (int h = P.nlevels - 1; h >= 0; --h) {
     const int b = P.level_begin[h], m = P.level_begin[h + 1] - b;
     if (m <= 0) continue;
+    const int nb = P.big_begin[h + 1] - P.big_begin[h];
+    if (nb > 0 && P.level_big_nb[h] > 0) {
+      k_ndb_bwd_rect<<<dim3((P.level_big_ns[h] + 255) / 256, nb), 256, (size_t)P.level_big_nb[h] * sizeof(float), s>>>(
+          D.nodes, D.bigs + P.big_begin[h], D.sets, D.F, D.xc, D.y, cstat, ctl);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const size_t smem = P.level_smem_solve[h];
     k_nd_backward<<<m, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.F, D.y, D.xc, dropped, x, scale, a_out,
                                        (long long)(smem / sizeof(float)), cstat, ctl);

@@ -28,8 +28,9 @@
 // rounding, the order of the sums being another.
 //
 // The sums of P_I = V_I^T r_I are formed in FP64 in the backward pass, as each
-// row of delta is produced: per thread over its rows, then over the warps in
-// order.
+// row of delta is produced: per thread over its nodes of the row (xi of a node
+// is the row's xi0 plus L times its column, eta is the row's), then over the
+// rows, then over the warps in order.
 #include <type_traits>
 
 #include "hms_internal.cuh"
@@ -89,8 +90,9 @@ __device__ inline void op_kind(int h, int o, int& kind, int& j) {
   }
 }
 
-// Shared-memory regions (elements of T): NS matrix slots, then two vector
-// panels [nb8max][TS] (or, after the loop, the P partial sums)
+// Shared-memory regions: NS matrix slots and two vector panels [nb8max][TS]
+// (elements of T), then the P partial sums [8 warps][TS][9] (doubles; each
+// thread adds only to its own warp's entries of its own sets)
 struct ClassSmem {
   size_t pan0, pan1, red_bytes_off, total_bytes;
 };
@@ -102,13 +104,13 @@ __host__ __device__ inline ClassSmem class_layout(size_t slot_elems, int nb8max)
   L.pan1 = L.pan0 + (size_t)nb8max * TS;
   const size_t pan_bytes = 2 * (size_t)nb8max * TS * sizeof(T);
   const size_t red_bytes = (size_t)(NTC / 32) * TS * NMODES * sizeof(double);
-  L.red_bytes_off = L.pan0 * sizeof(T);
-  L.total_bytes = L.red_bytes_off + (pan_bytes > red_bytes ? pan_bytes : red_bytes);
+  L.red_bytes_off = (L.pan0 * sizeof(T) + pan_bytes + 15) / 16 * 16;
+  L.total_bytes = L.red_bytes_off + red_bytes;
   return L;
 }
 
 template <typename T, int SPL, int NS>
-__global__ void __launch_bounds__(NTC + 32) k_relax_class(LatView lv, ClassPlanDev cp, const T* __restrict__ fac,
+__global__ void __launch_bounds__(NTC + 32, 1) k_relax_class(LatView lv, ClassPlanDev cp, const T* __restrict__ fac,
                                                          const double2* __restrict__ r, T* __restrict__ delta,
                                                          double* __restrict__ P, T* __restrict__ yglob,
                                                          const IterCtl* ctl, int* err, int wait0) {
@@ -203,11 +205,9 @@ __global__ void __launch_bounds__(NTC + 32) k_relax_class(LatView lv, ClassPlanD
   }
   __syncthreads();
 
-  double pacc[SPL][NMODES];
-#pragma unroll
-  for (int s = 0; s < SPL; ++s)
-#pragma unroll
-    for (int m = 0; m < NMODES; ++m) pacc[s][m] = 0.0;
+  double* red = reinterpret_cast<double*>(smraw + LY.red_bytes_off);  // [8 warps][TS][9]
+  if (!producer)
+    for (int q = 0; q < SPL * NMODES; ++q) red[((size_t)warp * TS + lane * SPL) * NMODES + q] = 0.0;
 
   int o_stop = 0;
   for (int o = 0; o < nops; ++o) {
@@ -249,15 +249,30 @@ __global__ void __launch_bounds__(NTC + 32) k_relax_class(LatView lv, ClassPlanD
         for (int rr = 0; rr < 8; ++rr)
 #pragma unroll
           for (int s = 0; s < SPL; ++s) acc[rr][s] = T(0);
-#pragma unroll 4
+        // column steps, the loads of column c + 1 issued before the products of c
+        T m[8], v[SPL];
+        if (lo < hi) {
+          ld8(mg, m);
+          ldv<T, SPL>(pin + (size_t)lo * TS + lane * SPL, v);
+        }
+#pragma unroll 2
         for (int c = lo; c < hi; ++c) {
-          T m[8], v[SPL];
-          ld8(mg + (size_t)(c - lo) * 8, m);
-          ldv<T, SPL>(pin + (size_t)c * TS + lane * SPL, v);
+          T mn[8], vn[SPL];
+          const bool more = c + 1 < hi;
+          if (more) {
+            ld8(mg + (size_t)(c + 1 - lo) * 8, mn);
+            ldv<T, SPL>(pin + (size_t)(c + 1) * TS + lane * SPL, vn);
+          }
 #pragma unroll
           for (int rr = 0; rr < 8; ++rr)
 #pragma unroll
             for (int s = 0; s < SPL; ++s) acc[rr][s] = fma(m[rr], v[s], acc[rr][s]);
+          if (more) {
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) m[rr] = mn[rr];
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) v[s] = vn[s];
+          }
         }
         // epilogue: rows 8g + rr < nb only
 #pragma unroll
@@ -280,32 +295,44 @@ __global__ void __launch_bounds__(NTC + 32) k_relax_class(LatView lv, ClassPlanD
           if (kind == GK_LINV) stv<T, SPL>(ybase + (size_t)j * yrow + (size_t)row * TS + lane * SPL, out);
         }
         if (kind == GK_LT) {
-          // delta of block row j (lattice row j0 + j) and the P sums of its nodes
+          // delta of block row j (lattice row j0 + j) and the P sums of its
+          // nodes.  On a row, eta is one value and xi = xi0 + L il, so the row's
+          // six sums (r_x, r_y, delta.r and their il-weighted copies) are
+          // formed first and the nine modes from them once per row.
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const int il = 4 * g + t;
-            if (il >= w) break;
+          for (int s = 0; s < SPL; ++s) {
+            if (!valid[s]) continue;
+            double sx = 0.0, sy = 0.0, sd = 0.0, six = 0.0, siy = 0.0, sid = 0.0;
 #pragma unroll
-            for (int s = 0; s < SPL; ++s) {
-              if (!valid[s]) continue;
+            for (int t = 0; t < 4; ++t) {
+              const int il = 4 * g + t;
+              if (il >= w) break;
               T2 dv;
               dv.x = acc[2 * t][s], dv.y = acc[2 * t + 1][s];
               reinterpret_cast<T2*>(delta)[nbase[s] + (size_t)j * lv.nx + il] = dv;
-              const int jg = j0p[s] + j;
-              const double xi = fma(lv.L, xoff[s] + (double)il + 0.5 * (double)(jg & 1), -repx[s]);
-              const double eta = fma(lv.L * SQ3_2, (double)jg, -repy[s]);
               const double2 rc = rv[t][s];
               const double dr = fma((double)dv.x, rc.x, (double)dv.y * rc.y);
-              pacc[s][0] += rc.x;
-              pacc[s][1] += rc.y;
-              pacc[s][2] = fma(xi, rc.x, pacc[s][2]);
-              pacc[s][3] = fma(eta, rc.x, pacc[s][3]);
-              pacc[s][4] = fma(xi, rc.y, pacc[s][4]);
-              pacc[s][5] = fma(eta, rc.y, pacc[s][5]);
-              pacc[s][6] += dr;
-              pacc[s][7] = fma(xi, dr, pacc[s][7]);
-              pacc[s][8] = fma(eta, dr, pacc[s][8]);
+              const double fil = (double)il;
+              sx += rc.x;
+              sy += rc.y;
+              sd += dr;
+              six = fma(fil, rc.x, six);
+              siy = fma(fil, rc.y, siy);
+              sid = fma(fil, dr, sid);
             }
+            const int jg = j0p[s] + j;
+            const double xi0 = fma(lv.L, xoff[s] + 0.5 * (double)(jg & 1), -repx[s]);
+            const double eta = fma(lv.L * SQ3_2, (double)jg, -repy[s]);
+            double* pr = red + ((size_t)warp * TS + lane * SPL + s) * NMODES;
+            pr[0] += sx;
+            pr[1] += sy;
+            pr[2] += fma(xi0, sx, lv.L * six);
+            pr[3] = fma(eta, sx, pr[3]);
+            pr[4] += fma(xi0, sy, lv.L * siy);
+            pr[5] = fma(eta, sy, pr[5]);
+            pr[6] += sd;
+            pr[7] += fma(xi0, sd, lv.L * sid);
+            pr[8] = fma(eta, sd, pr[8]);
           }
         }
       }
@@ -324,13 +351,6 @@ __global__ void __launch_bounds__(NTC + 32) k_relax_class(LatView lv, ClassPlanD
     return;
   }
   // P_I: the warps' partial sums, added in warp order
-  double* red = reinterpret_cast<double*>(smraw + LY.red_bytes_off);  // [8 warps][TS][9]
-  if (!producer) {
-#pragma unroll
-    for (int s = 0; s < SPL; ++s)
-#pragma unroll
-      for (int m = 0; m < NMODES; ++m) red[((size_t)warp * TS + lane * SPL + s) * NMODES + m] = pacc[s][m];
-  }
   __syncthreads();
   for (int q = tid; q < it.count * NMODES; q += NTC + 32) {
     const int ls = q / NMODES, m = q % NMODES;
