@@ -438,13 +438,7 @@ __global__ void __launch_bounds__(256) k_ndb_panel(const NDNode* __restrict__ no
 }
 
 // (c): F[i][j] -= sum_u L[i][u] L[j][u] over the trailing lower triangle, in
-// UT x UT tiles (CTA x: tile (ti, tj), ti >= tj; y: front).  The tile's two
-// panels are staged transposed (Lt[u][row], rows padded by 4 floats) so that a
-// thread reads its rows as float4s; thread (ty, tx) owns rows {4ty.., UT/2 +
-// 4ty..} and columns {4tx.., UT/2 + 4tx..} (8 x 8 sums).  Each sum runs over u
-// in order from 0, as in the one-CTA factor.
-constexpr int UT = 128;
-constexpr int ULD = UT + 4;
+// 64 x 64 tiles (CTA x: tile (ti, tj), ti >= tj; y: front), 4 x 4 per thread.
 __global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
                                                     float* __restrict__ F, int k0, const IterCtl* ctl) {
   if (nd_done(ctl)) return;
@@ -452,52 +446,46 @@ __global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ n
   const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
   if (k0 >= nS) return;
   const int kb = min(PB, nS - k0), r0 = k0 + kb, m = nf - r0;
-  const int T = (m + UT - 1) / UT;
+  const int T = (m + 63) / 64;
   const int t = blockIdx.x;
   if (t >= T * (T + 1) / 2) return;
   int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
   while (ti * (ti + 1) / 2 > t) --ti;
   while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
   const int tj = t - ti * (ti + 1) / 2;
-  __shared__ __align__(16) float La[PB][ULD];
-  __shared__ __align__(16) float Lb[PB][ULD];
+  __shared__ float La[64][PB + 1], Lb[64][PB + 1];
   float* fg = F + nd.f_off;
   const int tid = threadIdx.x;
-  // stage: element e -> row e / PB, column u = e % PB (a warp reads one row's 32 columns)
-  for (int e = tid; e < UT * PB; e += 256) {
+  for (int e = tid; e < 64 * PB; e += 256) {
     const int r = e / PB, u = e % PB;
-    const int ia = UT * ti + r, jb = UT * tj + r;
-    La[u][r] = (ia < m && u < kb) ? fg[(size_t)(r0 + ia) * nf + k0 + u] : 0.f;
-    Lb[u][r] = (jb < m && u < kb) ? fg[(size_t)(r0 + jb) * nf + k0 + u] : 0.f;
+    const int ia = 64 * ti + r, jb = 64 * tj + r;
+    La[r][u] = (ia < m && u < kb) ? fg[(size_t)(r0 + ia) * nf + k0 + u] : 0.f;
+    Lb[r][u] = (jb < m && u < kb) ? fg[(size_t)(r0 + jb) * nf + k0 + u] : 0.f;
   }
   __syncthreads();
   const int ty = tid / 16, tx = tid % 16;
-  float acc[8][8];
+  float acc[4][4];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
   for (int u = 0; u < kb; ++u) {
-    const float4 a0 = *reinterpret_cast<const float4*>(&La[u][4 * ty]);
-    const float4 a1 = *reinterpret_cast<const float4*>(&La[u][UT / 2 + 4 * ty]);
-    const float4 b0 = *reinterpret_cast<const float4*>(&Lb[u][4 * tx]);
-    const float4 b1 = *reinterpret_cast<const float4*>(&Lb[u][UT / 2 + 4 * tx]);
-    const float pa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    const float pb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    float pa[4], pb[4];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < 4; ++a) pa[a] = La[4 * ty + a][u], pb[a] = Lb[4 * tx + a][u];
 #pragma unroll
-      for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
   }
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const int i = UT * ti + (a < 4 ? 4 * ty + a : UT / 2 + 4 * ty + a - 4);
-    if (i >= m) continue;
-    float* row = fg + (size_t)(r0 + i) * nf + r0;
+  for (int a = 0; a < 4; ++a) {
+    const int i = 64 * ti + 4 * ty + a;
+    if (i >= m) break;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int j = UT * tj + (b < 4 ? 4 * tx + b : UT / 2 + 4 * tx + b - 4);
-      if (j <= i) row[j] -= acc[a][b];
+    for (int b = 0; b < 4; ++b) {
+      const int j = 64 * tj + 4 * tx + b;
+      if (j <= i) fg[(size_t)(r0 + i) * nf + r0 + j] -= acc[a][b];
     }
   }
 }
@@ -540,7 +528,9 @@ __global__ void __launch_bounds__(1024) k_nd_solve_begin(int n, const double* __
   }
 }
 
-constexpr int RU = 16;    // rows per warp in flight in the forward solve's row products
+// rows per warp in flight in the forward solve's row products: 4 for the
+// one-CTA fronts (fewer registers, more CTAs per SM), 16 for the wide ones
+constexpr int RU_SMALL = 4, RU_WIDE = 16;
 constexpr int NDQ = 12;   // columns per lane and pass in the back substitution's first product
 
 // Shared memory of a solve CTA (floats): the front's vector (nf), the warps'
@@ -551,6 +541,7 @@ __device__ __host__ inline long long nd_solve_need(long long nS, long long nf) {
   return nf + (nf > nS ? NDW * nS : 0) + nf;
 }
 
+template <int RU>
 __global__ void __launch_bounds__(NDT) k_nd_forward(const NDNode* __restrict__ nodes, const int* __restrict__ lvl,
                                                     int lbeg, const int* __restrict__ sets,
                                                     const int* __restrict__ maps, const float* __restrict__ F,
@@ -627,6 +618,7 @@ __global__ void __launch_bounds__(NDT) k_nd_forward(const NDNode* __restrict__ n
   }
 }
 
+template <int PRE>
 __global__ void __launch_bounds__(NDT) k_nd_backward(const NDNode* __restrict__ nodes, const int* __restrict__ lvl,
                                                      int lbeg, const int* __restrict__ sets,
                                                      const float* __restrict__ F, const float* __restrict__ y,
@@ -699,14 +691,17 @@ __global__ void __launch_bounds__(NDT) k_nd_backward(const NDNode* __restrict__ 
     __syncthreads();
     if (tid < kb) tv[k0 + tid] = xb[tid];
     // earlier columns: t_j -= sum_r L[k0 + r][j] x_r
+    // PRE entries of the column loaded ahead of their products (same order)
     for (int j = tid; j < k0; j += NDT) {
-      float lv[PB];
-#pragma unroll
-      for (int r = 0; r < PB; ++r) lv[r] = r < kb ? Lp[(size_t)(k0 + r) * ld + j] : 0.f;
       float sacc = tv[j];
+      for (int r0 = 0; r0 < kb; r0 += PRE) {
+        float lv[PRE];
 #pragma unroll
-      for (int r = 0; r < PB; ++r)
-        if (r < kb) sacc = fmaf(-lv[r], xb[r], sacc);
+        for (int q = 0; q < PRE; ++q) lv[q] = r0 + q < kb ? Lp[(size_t)(k0 + r0 + q) * ld + j] : 0.f;
+#pragma unroll
+        for (int q = 0; q < PRE; ++q)
+          if (r0 + q < kb) sacc = fmaf(-lv[q], xb[r0 + q], sacc);
+      }
       tv[j] = sacc;
     }
     __syncthreads();
@@ -1001,7 +996,7 @@ cudaError_t launch_nd_factor(cudaStream_t s, const LatView& lv, const NDPlanHost
       // the largest trailing size over the level's fronts that still have pivots
       const long long m = (long long)maxnf - k0 - 1;
       const int rows = (int)((m + 63) / 64);
-      const long long T = (m + UT - 1) / UT;
+      const long long T = (m + 63) / 64;
       k_ndb_panel<<<dim3(std::max(rows, 1), nb), 256, 0, s>>>(D.nodes, bg, D.F, D.dmask, k0, ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       k_ndb_update<<<dim3((unsigned)std::max(T * (T + 1) / 2, 1LL), nb), 256, 0, s>>>(D.nodes, bg, D.F, k0, ctl);
@@ -1021,8 +1016,13 @@ cudaError_t launch_nd_solve(cudaStream_t s, int n, const NDPlanHost& P, const ND
     const int b = P.level_begin[h], m = P.level_begin[h + 1] - b;
     if (m <= 0) continue;
     const size_t smem = P.level_smem_solve[h];
-    k_nd_forward<<<m, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.maps, D.F, D.W, rhs, dropped, D.y,
-                                      (long long)(smem / sizeof(float)), cstat, ctl);
+    const int msmall = P.level_split[h] - b, mwide = m - msmall;
+    if (msmall > 0)
+      k_nd_forward<RU_SMALL><<<msmall, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.maps, D.F, D.W, rhs, dropped,
+                                                      D.y, (long long)(smem / sizeof(float)), cstat, ctl);
+    if (mwide > 0)
+      k_nd_forward<RU_WIDE><<<mwide, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b + msmall, D.sets, D.maps, D.F, D.W, rhs,
+                                                    dropped, D.y, (long long)(smem / sizeof(float)), cstat, ctl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int nb = P.big_begin[h + 1] - P.big_begin[h];
     if (nb > 0 && P.level_big_nb[h] > 0) {
@@ -1041,8 +1041,13 @@ cudaError_t launch_nd_solve(cudaStream_t s, int n, const NDPlanHost& P, const ND
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const size_t smem = P.level_smem_solve[h];
-    k_nd_backward<<<m, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.F, D.y, D.xc, dropped, x, scale, a_out,
-                                       (long long)(smem / sizeof(float)), cstat, ctl);
+    const int msmall = P.level_split[h] - b, mwide = m - msmall;
+    if (msmall > 0)
+      k_nd_backward<8><<<msmall, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.F, D.y, D.xc, dropped, x, scale,
+                                                 a_out, (long long)(smem / sizeof(float)), cstat, ctl);
+    if (mwide > 0)
+      k_nd_backward<PB><<<mwide, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b + msmall, D.sets, D.F, D.y, D.xc, dropped, x,
+                                                 scale, a_out, (long long)(smem / sizeof(float)), cstat, ctl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1051,8 +1056,10 @@ cudaError_t launch_nd_solve(cudaStream_t s, int n, const NDPlanHost& P, const ND
 cudaError_t configure_coarse_nd(int max_smem) {
   cudaError_t e = set_max_dynamic_smem(k_nd_factor, max_smem);
   if (e != cudaSuccess) return e;
-  if ((e = set_max_dynamic_smem(k_nd_forward, max_smem)) != cudaSuccess) return e;
-  return set_max_dynamic_smem(k_nd_backward, max_smem);
+  if ((e = set_max_dynamic_smem(k_nd_forward<RU_SMALL>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_nd_forward<RU_WIDE>, max_smem)) != cudaSuccess) return e;
+  if ((e = set_max_dynamic_smem(k_nd_backward<8>, max_smem)) != cudaSuccess) return e;
+  return set_max_dynamic_smem(k_nd_backward<PB>, max_smem);
 }
 
 }  // namespace hms

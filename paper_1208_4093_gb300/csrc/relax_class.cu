@@ -256,23 +256,24 @@ __global__ void __launch_bounds__(NTC + 32, 1) k_relax_class(LatView lv, ClassPl
           ldv<T, SPL>(pin + (size_t)lo * TS + lane * SPL, v);
         }
 #pragma unroll 2
-        for (int c = lo; c < hi; ++c) {
+        for (int c = lo; c + 1 < hi; ++c) {
           T mn[8], vn[SPL];
-          const bool more = c + 1 < hi;
-          if (more) {
-            ld8(mg + (size_t)(c + 1 - lo) * 8, mn);
-            ldv<T, SPL>(pin + (size_t)(c + 1) * TS + lane * SPL, vn);
-          }
+          ld8(mg + (size_t)(c + 1 - lo) * 8, mn);
+          ldv<T, SPL>(pin + (size_t)(c + 1) * TS + lane * SPL, vn);
 #pragma unroll
           for (int rr = 0; rr < 8; ++rr)
 #pragma unroll
             for (int s = 0; s < SPL; ++s) acc[rr][s] = fma(m[rr], v[s], acc[rr][s]);
-          if (more) {
 #pragma unroll
-            for (int rr = 0; rr < 8; ++rr) m[rr] = mn[rr];
+          for (int rr = 0; rr < 8; ++rr) m[rr] = mn[rr];
 #pragma unroll
-            for (int s = 0; s < SPL; ++s) v[s] = vn[s];
-          }
+          for (int s = 0; s < SPL; ++s) v[s] = vn[s];
+        }
+        if (lo < hi) {
+#pragma unroll
+          for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) acc[rr][s] = fma(m[rr], v[s], acc[rr][s]);
         }
         // epilogue: rows 8g + rr < nb only
 #pragma unroll
