@@ -152,7 +152,7 @@ __device__ __forceinline__ void nd_tri_invert(const float (&a)[PB], float (&x)[P
 // the solves multiply by it); every row below is multiplied by the inverse's
 // transpose (one warp per row); the trailing lower triangle takes the rank-PB
 // update.
-template <bool SM>
+template <bool SM, int NT>
 __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* __restrict__ nodes,
                                                const int* __restrict__ sets, const int* __restrict__ maps,
                                                const BlkSrc& src, float* __restrict__ F,
@@ -167,12 +167,12 @@ __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* _
     else return fg[(size_t)i * nf + j];
   };
   // the global unknown of every front position
-  for (int p = tid; p < nf; p += NDT) gidx[p] = nd_glob(st, p, nm);
+  for (int p = tid; p < nf; p += NT) gidx[p] = nd_glob(st, p, nm);
   __syncthreads();
 
   // ---- assemble: original entries of the S columns, zero B x B (NU loads in flight per lane) ----
   constexpr int NU = 4;
-  for (int p = warp; p < nf; p += NDW) {
+  for (int p = warp; p < nf; p += (NT / 32)) {
     const int gp = gidx[p];
     for (int q0 = lane; q0 <= p; q0 += 32 * NU) {
       float v[NU];
@@ -195,9 +195,9 @@ __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* _
     const int nSc = nm * ch.ns, nbc = nm * ch.nb, nfc = nSc + nbc;
     const float* U = F + ch.f_off + (size_t)nSc * nfc + nSc;
     const int* mp = maps + nd.map_off[c];
-    for (int k = tid; k < nbc; k += NDT) cpos[k] = nm * mp[k / nm] + k % nm;
+    for (int k = tid; k < nbc; k += NT) cpos[k] = nm * mp[k / nm] + k % nm;
     __syncthreads();
-    for (int k = warp; k < nbc; k += NDW) {
+    for (int k = warp; k < nbc; k += (NT / 32)) {
       const int pk = cpos[k];
       const float* Uk = U + (size_t)k * nfc;
       for (int l0 = lane; l0 <= k; l0 += 32 * NU) {
@@ -249,7 +249,7 @@ __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* _
     // (b) the panel below: L[i][blk] = F[i][blk] Dinv^T, one warp per row (lane = column)
     const unsigned dmk = dmask;
     const int r0 = k0 + kb, m = nf - r0;
-    for (int ii = warp; ii < m; ii += NDW) {
+    for (int ii = warp; ii < m; ii += (NT / 32)) {
       const float fv = lane < kb ? at(r0 + ii, k0 + lane) : 0.f;
       float sacc = 0.f;
 #pragma unroll
@@ -264,7 +264,7 @@ __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* _
     // (c) trailing update of the lower triangle below the block, 4 x 4 tiles
     const int T = (m + 3) / 4;
     const int ntile = T * (T + 1) / 2;
-    for (int t = tid; t < ntile; t += NDT) {
+    for (int t = tid; t < ntile; t += NT) {
       int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
       while (ti * (ti + 1) / 2 > t) --ti;
       while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
@@ -307,7 +307,7 @@ __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* _
   }
   if constexpr (SM) {
     // the factored front out to its global copy (the solves and the parent read it there)
-    for (int p = warp; p < nf; p += NDW)
+    for (int p = warp; p < nf; p += (NT / 32))
       for (int q = lane; q <= p; q += 32) fg[(size_t)p * nf + q] = sm[(size_t)p * (p + 1) / 2 + q];
   }
 }
@@ -315,7 +315,8 @@ __device__ __forceinline__ void nd_factor_body(const NDNode& nd, const NDNode* _
 // One CTA per front of a tree level.  cap = the launch's dynamic shared
 // memory in floats: a front whose packed lower triangle fits is factored in
 // shared memory.
-__global__ void __launch_bounds__(NDT) k_nd_factor(const NDNode* __restrict__ nodes, const int* __restrict__ lvl,
+template <int NT>
+__global__ void __launch_bounds__(NT) k_nd_factor(const NDNode* __restrict__ nodes, const int* __restrict__ lvl,
                                                    int lbeg, const int* __restrict__ sets,
                                                    const int* __restrict__ maps, BlkSrc src,
                                                    float* __restrict__ F, int* __restrict__ dropped,
@@ -330,9 +331,9 @@ __global__ void __launch_bounds__(NDT) k_nd_factor(const NDNode* __restrict__ no
   int* gidx = reinterpret_cast<int*>(ndsm + (cap - 2 * nf));
   int* cpos = gidx + nf;
   if (nf * (nf + 1) / 2 + 2 * nf <= cap)
-    nd_factor_body<true>(nd, nodes, sets, maps, src, F, dropped, ndsm, gidx, cpos, Dinv, dmask);
+    nd_factor_body<true, NT>(nd, nodes, sets, maps, src, F, dropped, ndsm, gidx, cpos, Dinv, dmask);
   else
-    nd_factor_body<false>(nd, nodes, sets, maps, src, F, dropped, ndsm, gidx, cpos, Dinv, dmask);
+    nd_factor_body<false, NT>(nd, nodes, sets, maps, src, F, dropped, ndsm, gidx, cpos, Dinv, dmask);
 }
 
 // ---------------------------------------------------------------- wide fronts
@@ -438,9 +439,14 @@ __global__ void __launch_bounds__(256) k_ndb_panel(const NDNode* __restrict__ no
 }
 
 // (c): F[i][j] -= sum_u L[i][u] L[j][u] over the trailing lower triangle, in
-// 64 x 64 tiles (CTA x: tile (ti, tj), ti >= tj; y: front), 4 x 4 per thread.
-__global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
-                                                    float* __restrict__ F, int k0, const IterCtl* ctl) {
+// 64 x 64 tiles (CTA x: tile (ti, tj), ti >= tj; y: front).  64 threads per
+// tile, 8 x 8 sums each (rows {4ty.., 32 + 4ty..}, columns {4tx.., 32 +
+// 4tx..}); the tile's two panels are staged transposed (Lt[u][row]) so that a
+// thread reads its four consecutive rows as one float4.  Each sum runs over u
+// in order from 0, as in the one-CTA factor.
+constexpr int ULD = 68;  // padded row of the transposed panels (16-byte multiple)
+__global__ void __launch_bounds__(64) k_ndb_update(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                   float* __restrict__ F, int k0, const IterCtl* ctl) {
   if (nd_done(ctl)) return;
   const NDNode nd = nodes[bigs[blockIdx.y].node];
   const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
@@ -453,39 +459,49 @@ __global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ n
   while (ti * (ti + 1) / 2 > t) --ti;
   while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
   const int tj = t - ti * (ti + 1) / 2;
-  __shared__ float La[64][PB + 1], Lb[64][PB + 1];
+  __shared__ __align__(16) float La[PB][ULD];
+  __shared__ __align__(16) float Lb[PB][ULD];
   float* fg = F + nd.f_off;
   const int tid = threadIdx.x;
-  for (int e = tid; e < 64 * PB; e += 256) {
-    const int r = e / PB, u = e % PB;
-    const int ia = 64 * ti + r, jb = 64 * tj + r;
-    La[r][u] = (ia < m && u < kb) ? fg[(size_t)(r0 + ia) * nf + k0 + u] : 0.f;
-    Lb[r][u] = (jb < m && u < kb) ? fg[(size_t)(r0 + jb) * nf + k0 + u] : 0.f;
+  {
+    // thread tid stages row tid of each panel (its kb entries, then zeros)
+    const int ia = 64 * ti + tid, jb = 64 * tj + tid;
+    const float* ra = fg + (size_t)(r0 + ia) * nf + k0;
+    const float* rb = fg + (size_t)(r0 + jb) * nf + k0;
+#pragma unroll 8
+    for (int u = 0; u < PB; ++u) {
+      La[u][tid] = (ia < m && u < kb) ? ra[u] : 0.f;
+      Lb[u][tid] = (jb < m && u < kb) ? rb[u] : 0.f;
+    }
   }
   __syncthreads();
-  const int ty = tid / 16, tx = tid % 16;
-  float acc[4][4];
+  const int ty = tid / 8, tx = tid % 8;
+  float acc[8][8];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
   for (int u = 0; u < kb; ++u) {
-    float pa[4], pb[4];
+    const float4 a0 = *reinterpret_cast<const float4*>(&La[u][4 * ty]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&La[u][32 + 4 * ty]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&Lb[u][4 * tx]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&Lb[u][32 + 4 * tx]);
+    const float pa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float pb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-    for (int a = 0; a < 4; ++a) pa[a] = La[4 * ty + a][u], pb[a] = Lb[4 * tx + a][u];
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
+      for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int i = 64 * ti + 4 * ty + a;
-    if (i >= m) break;
+  for (int a = 0; a < 8; ++a) {
+    const int i = 64 * ti + (a < 4 ? 4 * ty + a : 32 + 4 * ty + a - 4);
+    if (i >= m) continue;
+    float* row = fg + (size_t)(r0 + i) * nf + r0;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = 64 * tj + 4 * tx + b;
-      if (j <= i) fg[(size_t)(r0 + i) * nf + r0 + j] -= acc[a][b];
+    for (int b = 0; b < 8; ++b) {
+      const int j = 64 * tj + (b < 4 ? 4 * tx + b : 32 + 4 * tx + b - 4);
+      if (j <= i) row[j] -= acc[a][b];
     }
   }
 }
@@ -980,8 +996,15 @@ cudaError_t launch_nd_factor(cudaStream_t s, const LatView& lv, const NDPlanHost
     const int b = P.level_begin[h], n = P.level_split[h] - b;
     if (n > 0) {
       const size_t smem = P.level_smem_factor[h];
-      k_nd_factor<<<n, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.maps, src, D.F, dropped,
-                                       (long long)(smem / sizeof(float)), ctl);
+      // levels of many small fronts: 256-thread CTAs, so that several fronts
+      // share an SM and one front's serial steps overlap another's (the same
+      // arithmetic either way)
+      if (n >= 256)
+        k_nd_factor<NDT / 2><<<n, NDT / 2, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.maps, src, D.F, dropped,
+                                                      (long long)(smem / sizeof(float)), ctl);
+      else
+        k_nd_factor<NDT><<<n, NDT, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.maps, src, D.F, dropped,
+                                              (long long)(smem / sizeof(float)), ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int nb = P.big_begin[h + 1] - P.big_begin[h];
@@ -999,7 +1022,7 @@ cudaError_t launch_nd_factor(cudaStream_t s, const LatView& lv, const NDPlanHost
       const long long T = (m + 63) / 64;
       k_ndb_panel<<<dim3(std::max(rows, 1), nb), 256, 0, s>>>(D.nodes, bg, D.F, D.dmask, k0, ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      k_ndb_update<<<dim3((unsigned)std::max(T * (T + 1) / 2, 1LL), nb), 256, 0, s>>>(D.nodes, bg, D.F, k0, ctl);
+      k_ndb_update<<<dim3((unsigned)std::max(T * (T + 1) / 2, 1LL), nb), 64, 0, s>>>(D.nodes, bg, D.F, k0, ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }
@@ -1054,7 +1077,9 @@ cudaError_t launch_nd_solve(cudaStream_t s, int n, const NDPlanHost& P, const ND
 }
 
 cudaError_t configure_coarse_nd(int max_smem) {
-  cudaError_t e = set_max_dynamic_smem(k_nd_factor, max_smem);
+  cudaError_t e = set_max_dynamic_smem(k_nd_factor<NDT>, max_smem);
+  if (e != cudaSuccess) return e;
+  e = set_max_dynamic_smem(k_nd_factor<NDT / 2>, max_smem);
   if (e != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_nd_forward<RU_SMALL>, max_smem)) != cudaSuccess) return e;
   if ((e = set_max_dynamic_smem(k_nd_forward<RU_WIDE>, max_smem)) != cudaSuccess) return e;
