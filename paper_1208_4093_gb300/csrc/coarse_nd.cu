@@ -439,14 +439,9 @@ __global__ void __launch_bounds__(256) k_ndb_panel(const NDNode* __restrict__ no
 }
 
 // (c): F[i][j] -= sum_u L[i][u] L[j][u] over the trailing lower triangle, in
-// 64 x 64 tiles (CTA x: tile (ti, tj), ti >= tj; y: front).  64 threads per
-// tile, 8 x 8 sums each (rows {4ty.., 32 + 4ty..}, columns {4tx.., 32 +
-// 4tx..}); the tile's two panels are staged transposed (Lt[u][row]) so that a
-// thread reads its four consecutive rows as one float4.  Each sum runs over u
-// in order from 0, as in the one-CTA factor.
-constexpr int ULD = 68;  // padded row of the transposed panels (16-byte multiple)
-__global__ void __launch_bounds__(64) k_ndb_update(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
-                                                   float* __restrict__ F, int k0, const IterCtl* ctl) {
+// 64 x 64 tiles (CTA x: tile (ti, tj), ti >= tj; y: front), 4 x 4 per thread.
+__global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                    float* __restrict__ F, int k0, const IterCtl* ctl) {
   if (nd_done(ctl)) return;
   const NDNode nd = nodes[bigs[blockIdx.y].node];
   const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
@@ -459,49 +454,39 @@ __global__ void __launch_bounds__(64) k_ndb_update(const NDNode* __restrict__ no
   while (ti * (ti + 1) / 2 > t) --ti;
   while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
   const int tj = t - ti * (ti + 1) / 2;
-  __shared__ __align__(16) float La[PB][ULD];
-  __shared__ __align__(16) float Lb[PB][ULD];
+  __shared__ float La[64][PB + 1], Lb[64][PB + 1];
   float* fg = F + nd.f_off;
   const int tid = threadIdx.x;
-  {
-    // thread tid stages row tid of each panel (its kb entries, then zeros)
-    const int ia = 64 * ti + tid, jb = 64 * tj + tid;
-    const float* ra = fg + (size_t)(r0 + ia) * nf + k0;
-    const float* rb = fg + (size_t)(r0 + jb) * nf + k0;
-#pragma unroll 8
-    for (int u = 0; u < PB; ++u) {
-      La[u][tid] = (ia < m && u < kb) ? ra[u] : 0.f;
-      Lb[u][tid] = (jb < m && u < kb) ? rb[u] : 0.f;
-    }
+  for (int e = tid; e < 64 * PB; e += 256) {
+    const int r = e / PB, u = e % PB;
+    const int ia = 64 * ti + r, jb = 64 * tj + r;
+    La[r][u] = (ia < m && u < kb) ? fg[(size_t)(r0 + ia) * nf + k0 + u] : 0.f;
+    Lb[r][u] = (jb < m && u < kb) ? fg[(size_t)(r0 + jb) * nf + k0 + u] : 0.f;
   }
   __syncthreads();
-  const int ty = tid / 8, tx = tid % 8;
-  float acc[8][8];
+  const int ty = tid / 16, tx = tid % 16;
+  float acc[4][4];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
   for (int u = 0; u < kb; ++u) {
-    const float4 a0 = *reinterpret_cast<const float4*>(&La[u][4 * ty]);
-    const float4 a1 = *reinterpret_cast<const float4*>(&La[u][32 + 4 * ty]);
-    const float4 b0 = *reinterpret_cast<const float4*>(&Lb[u][4 * tx]);
-    const float4 b1 = *reinterpret_cast<const float4*>(&Lb[u][32 + 4 * tx]);
-    const float pa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    const float pb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    float pa[4], pb[4];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < 4; ++a) pa[a] = La[4 * ty + a][u], pb[a] = Lb[4 * tx + a][u];
 #pragma unroll
-      for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
   }
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const int i = 64 * ti + (a < 4 ? 4 * ty + a : 32 + 4 * ty + a - 4);
-    if (i >= m) continue;
-    float* row = fg + (size_t)(r0 + i) * nf + r0;
+  for (int a = 0; a < 4; ++a) {
+    const int i = 64 * ti + 4 * ty + a;
+    if (i >= m) break;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int j = 64 * tj + (b < 4 ? 4 * tx + b : 32 + 4 * tx + b - 4);
-      if (j <= i) row[j] -= acc[a][b];
+    for (int b = 0; b < 4; ++b) {
+      const int j = 64 * tj + 4 * tx + b;
+      if (j <= i) fg[(size_t)(r0 + i) * nf + r0 + j] -= acc[a][b];
     }
   }
 }
@@ -907,14 +892,19 @@ bool nd_plan_build(const LatView& lv, NDPlanHost* P) {
   P->level_big_ns.assign(H + 1, 0);
   P->level_big_nf.assign(H + 1, 0);
   P->level_big_nb.assign(H + 1, 0);
+  P->level_small_nf.assign(H + 1, 0);
   P->bigs.clear();
   P->inv.clear();
   P->max_level_bigs = 0;
   auto nf_of = [&](int k) { return (long long)P->nodes[k].nm * (P->nodes[k].ns + P->nodes[k].nb); };
   for (int h = 0; h <= H; ++h) {
     P->level_begin[h] = (int)P->lvl_nodes.size();
+    P->level_small_nf[h] = 0;
     for (int k : byh[h])
-      if (nf_of(k) < ND_BIG) P->lvl_nodes.push_back(k);
+      if (nf_of(k) < ND_BIG) {
+        P->lvl_nodes.push_back(k);
+        P->level_small_nf[h] = std::max(P->level_small_nf[h], (int)nf_of(k));
+      }
     P->level_split[h] = (int)P->lvl_nodes.size();
     P->big_begin[h] = (int)P->bigs.size();
     for (int k : byh[h]) {
@@ -996,10 +986,10 @@ cudaError_t launch_nd_factor(cudaStream_t s, const LatView& lv, const NDPlanHost
     const int b = P.level_begin[h], n = P.level_split[h] - b;
     if (n > 0) {
       const size_t smem = P.level_smem_factor[h];
-      // levels of many small fronts: 256-thread CTAs, so that several fronts
-      // share an SM and one front's serial steps overlap another's (the same
-      // arithmetic either way)
-      if (n >= 256)
+      // levels of many tiny fronts (at most 200 unknowns): 256-thread CTAs, so
+      // that several fronts share an SM and one front's serial steps overlap
+      // another's (the same arithmetic either way)
+      if (P.level_small_nf[h] <= 200)
         k_nd_factor<NDT / 2><<<n, NDT / 2, smem, s>>>(D.nodes, D.lvl_nodes, b, D.sets, D.maps, src, D.F, dropped,
                                                       (long long)(smem / sizeof(float)), ctl);
       else
@@ -1022,7 +1012,7 @@ cudaError_t launch_nd_factor(cudaStream_t s, const LatView& lv, const NDPlanHost
       const long long T = (m + 63) / 64;
       k_ndb_panel<<<dim3(std::max(rows, 1), nb), 256, 0, s>>>(D.nodes, bg, D.F, D.dmask, k0, ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      k_ndb_update<<<dim3((unsigned)std::max(T * (T + 1) / 2, 1LL), nb), 64, 0, s>>>(D.nodes, bg, D.F, k0, ctl);
+      k_ndb_update<<<dim3((unsigned)std::max(T * (T + 1) / 2, 1LL), nb), 256, 0, s>>>(D.nodes, bg, D.F, k0, ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }

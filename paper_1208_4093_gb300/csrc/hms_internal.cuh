@@ -444,6 +444,7 @@ struct NDPlanHost {
   std::vector<int> level_big_ns;    // per level: the largest pivot count of its wide fronts (unknowns)
   std::vector<int> level_big_nf;    // per level: the largest of its wide fronts (unknowns)
   std::vector<int> level_big_nb;    // per level: the largest boundary of its wide fronts (unknowns)
+  std::vector<int> level_small_nf;  // per level: the largest of its one-CTA fronts (unknowns)
   std::vector<size_t> level_smem_factor, level_smem_solve;  // dynamic shared memory per level's launches
   int nlevels = 0, max_front = 0, max_level_nodes = 0, max_level_bigs = 0;
   size_t f_elems = 0, w_elems = 0;
