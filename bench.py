@@ -621,8 +621,9 @@ def paper_scale_measure(updates, full=False, split=True):
         h = hist[0, :n + 1, 0].cpu().numpy()
         return a.elapsed_time(b), n, h
 
+    # a CUDA graph of K updates: no launches of finished updates in the timed region
     pr = capi.hms_problem_create(ctx, c.nx, c.ny, c.sx, c.sy, precision=capi.HMS_MIXED, tol=0.0, max_iter=K,
-                                 class_factors=1)
+                                 class_factors=1, batch=min(K, 16))
     try:
         out["setup_ms"] = capi.hms_problem_setup_ms(pr)
         out["device_bytes"] = capi.hms_problem_device_bytes(pr)
@@ -648,13 +649,14 @@ def paper_scale_measure(updates, full=False, split=True):
                           "coarse_assemble": 8}
         split = {}
         for k, (tms, cnt) in kt.items():
-            e = {"ms_per_update": tms / n, "launches": cnt}
+            e = {"ms_per_update": tms / n, "ms_per_launch": tms / max(cnt, 1), "launches": cnt}
             if k in bytes_per_node and tms > 0:
-                gbs = bytes_per_node[k] * nn / (tms / n * 1e-3) / 1e9
+                gbs = bytes_per_node[k] * nn / (tms / max(cnt, 1) * 1e-3) / 1e9
                 e.update({"bytes_per_node": bytes_per_node[k], "hbm_gbs": gbs, "hbm_frac": gbs / hbm})
             split[k] = e
         out["kernel_split"] = split
-        out["kernel_split_note"] = ("profile mode (CUDA events around every kernel, no graph), 3 updates; "
+        out["kernel_split_note"] = ("profile mode (CUDA events around every kernel, no graph), 3 updates (the "
+                                    "residual runs once more than the updates); "
                                     "update_residual and coarse_assemble are bound by the FP64 pipe, the class "
                                     "relaxation by the FP32 pipe, the upper level by its chain of fronts")
     except StopIteration:

@@ -751,37 +751,39 @@ __global__ void __launch_bounds__(256) k_ndb_fwd_rect(const NDNode* __restrict__
 // Back substitution of a wide front, t = y_S - L_BS^T x_B: per column j the
 // NDW partial sums over the boundary rows k = w, w + NDW, ... and their
 // difference from y in w order, as k_nd_backward forms them; written into y.
-// Thread per column (256 per CTA); CTA y: the front.
-__global__ void __launch_bounds__(256) k_ndb_bwd_rect(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+// CTA (x, y): columns 32x .. 32x + 31 of front y; warp w forms the partial sum
+// w of every column (lane = column), then warp 0 combines them in order.
+__global__ void __launch_bounds__(NDT) k_ndb_bwd_rect(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
                                                       const int* __restrict__ sets, const float* __restrict__ F,
                                                       const float* __restrict__ xc, float* __restrict__ y,
                                                       const unsigned long long* cstat, const IterCtl* ctl) {
+  static_assert(NDT == 32 * NDW, "one warp per partial sum");
   if (nd_done(ctl) || *(volatile const unsigned long long*)&cstat[2]) return;
   extern __shared__ __align__(16) float ndsm[];  // x_B of the front
+  __shared__ float part[NDW][32];
   const NDNode nd = nodes[bigs[blockIdx.y].node];
   const int nm = nd.nm, nS = nm * nd.ns, nB = nm * nd.nb, nf = nS + nB;
-  if (nB == 0 || 256 * (int)blockIdx.x >= nS) return;
+  if (nB == 0 || 32 * (int)blockIdx.x >= nS) return;
   const int* st = sets + nd.s_off;
   for (int k = threadIdx.x; k < nB; k += blockDim.x) ndsm[k] = xc[nd_glob(st, nS + k, nm)];
   __syncthreads();
-  const int j = 256 * blockIdx.x + threadIdx.x;
-  if (j >= nS) return;
-  const float* col = F + nd.f_off + (size_t)nS * nf + j;
-  float acc[NDW];
-#pragma unroll
-  for (int w = 0; w < NDW; ++w) acc[w] = 0.f;
-  for (int k0 = 0; k0 < nB; k0 += NDW) {
-#pragma unroll
-    for (int w = 0; w < NDW; ++w) {
-      const int k = k0 + w;
-      if (k < nB) acc[w] = fmaf(col[(size_t)k * nf], ndsm[k], acc[w]);
-    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = 32 * blockIdx.x + lane;
+  float acc = 0.f;
+  if (j < nS) {
+    const float* col = F + nd.f_off + (size_t)nS * nf + j;
+#pragma unroll 4
+    for (int k = warp; k < nB; k += NDW) acc = fmaf(col[(size_t)k * nf], ndsm[k], acc);
   }
-  const int g = nd_glob(st, j, nm);
-  float sacc = y[g];
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && j < nS) {
+    const int g = nd_glob(st, j, nm);
+    float sacc = y[g];
 #pragma unroll
-  for (int w = 0; w < NDW; ++w) sacc -= acc[w];
-  y[g] = sacc;
+    for (int w = 0; w < NDW; ++w) sacc -= part[w][lane];
+    y[g] = sacc;
+  }
 }
 
 }  // namespace
@@ -1049,7 +1051,7 @@ cudaError_t launch_nd_solve(cudaStream_t s, int n, const NDPlanHost& P, const ND
     if (m <= 0) continue;
     const int nb = P.big_begin[h + 1] - P.big_begin[h];
     if (nb > 0 && P.level_big_nb[h] > 0) {
-      k_ndb_bwd_rect<<<dim3((P.level_big_ns[h] + 255) / 256, nb), 256, (size_t)P.level_big_nb[h] * sizeof(float), s>>>(
+      k_ndb_bwd_rect<<<dim3((P.level_big_ns[h] + 31) / 32, nb), NDT, (size_t)P.level_big_nb[h] * sizeof(float), s>>>(
           D.nodes, D.bigs + P.big_begin[h], D.sets, D.F, D.xc, D.y, cstat, ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
