@@ -29,13 +29,15 @@
 // in FP64 are unit rows already; the factor and solves run in FP32 and the
 // FP64 refinement of Eq. 8 (k_blk_residual) works on the same scaled system.
 //
-// Fronts of at least ND_BIG unknowns (the top levels of large set grids, up to
-// several thousand unknowns) are factored by many CTAs instead: one launch
-// assembles every wide front of a level, then per 32-column panel one launch
-// factors the diagonal blocks, one forms the panels below them and one
-// applies the rank-32 update to the trailing lower triangles in 64 x 64
-// tiles.  Each step does the arithmetic of the one-CTA factor in the same
-// order, so a front gets the same factor either way.
+// Fronts of at least ND_BIG (300) unknowns (all but the lowest levels of large
+// set grids, up to several thousand unknowns) are factored by many CTAs
+// instead: one launch assembles every wide front of a level, then per
+// 32-column panel one launch factors the diagonal blocks, one forms the panels
+// below them and one applies the rank-32 update to the trailing lower
+// triangles in 64 x 64 tiles.  Their solves hand the rectangular parts (the
+// boundary rows' products) to many-CTA kernels.  Each step does the arithmetic
+// of the one-CTA kernels in the same order, so a front gets the same factor
+// and the same solves either way; the threshold only changes the time.
 //
 // Every sum runs in a fixed order (children in order, rows in order), so
 // results are the same on every run.
@@ -440,6 +442,10 @@ __global__ void __launch_bounds__(256) k_ndb_panel(const NDNode* __restrict__ no
 
 // (c): F[i][j] -= sum_u L[i][u] L[j][u] over the trailing lower triangle, in
 // 64 x 64 tiles (CTA x: tile (ti, tj), ti >= tj; y: front), 4 x 4 per thread.
+// The tile's two panels are staged transposed (Lt[u][row], rows padded to 68
+// floats) so that a thread reads its four rows, and its four columns, as one
+// float4 each.  Each sum runs over u in order from 0, as in the one-CTA factor.
+constexpr int ULD = 68;
 __global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
                                                     float* __restrict__ F, int k0, const IterCtl* ctl) {
   if (nd_done(ctl)) return;
@@ -454,14 +460,15 @@ __global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ n
   while (ti * (ti + 1) / 2 > t) --ti;
   while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
   const int tj = t - ti * (ti + 1) / 2;
-  __shared__ float La[64][PB + 1], Lb[64][PB + 1];
+  __shared__ __align__(16) float La[PB][ULD];
+  __shared__ __align__(16) float Lb[PB][ULD];
   float* fg = F + nd.f_off;
   const int tid = threadIdx.x;
   for (int e = tid; e < 64 * PB; e += 256) {
     const int r = e / PB, u = e % PB;
     const int ia = 64 * ti + r, jb = 64 * tj + r;
-    La[r][u] = (ia < m && u < kb) ? fg[(size_t)(r0 + ia) * nf + k0 + u] : 0.f;
-    Lb[r][u] = (jb < m && u < kb) ? fg[(size_t)(r0 + jb) * nf + k0 + u] : 0.f;
+    La[u][r] = (ia < m && u < kb) ? fg[(size_t)(r0 + ia) * nf + k0 + u] : 0.f;
+    Lb[u][r] = (jb < m && u < kb) ? fg[(size_t)(r0 + jb) * nf + k0 + u] : 0.f;
   }
   __syncthreads();
   const int ty = tid / 16, tx = tid % 16;
@@ -471,9 +478,9 @@ __global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ n
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
   for (int u = 0; u < kb; ++u) {
-    float pa[4], pb[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) pa[a] = La[4 * ty + a][u], pb[a] = Lb[4 * tx + a][u];
+    const float4 qa = *reinterpret_cast<const float4*>(&La[u][4 * ty]);
+    const float4 qb = *reinterpret_cast<const float4*>(&Lb[u][4 * tx]);
+    const float pa[4] = {qa.x, qa.y, qa.z, qa.w}, pb[4] = {qb.x, qb.y, qb.z, qb.w};
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll

@@ -428,7 +428,7 @@ struct NDNode {
 // A wide front (at least ND_BIG unknowns) is factored by many CTAs, panel by
 // panel: its node, and per child the place of each of its sets (S then B) in
 // the child's boundary list (-1 if absent), at inv_off[c].
-constexpr int ND_BIG = 1024;
+constexpr int ND_BIG = 300;
 struct NDBig {
   int node;
   int inv_off[2];

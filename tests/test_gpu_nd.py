@@ -99,7 +99,7 @@ def test_wide_set_grids_accepted_and_exact(hms_ctx, nx, ny, sx, sy):
     """Set grids far wider than a band window (64, 32, 100, 80 and 120 sets
     across) are taken by the automatic choice and solved to the direct
     solution (the oracle's sparse direct solve, O1).  On the 80 x 80 and 120 x
-    84 set grids the top fronts of the dissection have 1080 to 2000 unknowns,
+    84 set grids the upper fronts of the dissection have 300 to 2000 unknowns,
     so they are factored by the many-CTA panel kernels."""
     from paper_1208_4093_gb300 import capi
     ea = ea_lognormal(nx, ny, 29)
