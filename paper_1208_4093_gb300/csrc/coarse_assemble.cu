@@ -67,6 +67,28 @@ __device__ inline void mode_proj(double ex, double ey, double xi, double eta, un
   s[8] = eta * ed;
 }
 
+// mode_proj in the arithmetic AT of the per-bar products (the same formula)
+template <typename AT>
+__device__ inline void mode_proj_t(AT ex, AT ey, AT xi, AT eta, unsigned fm, AT dx, AT dy, AT* s) {
+  const AT fx = (fm & 1u) ? AT(0) : AT(1), fy = (fm & 2u) ? AT(0) : AT(1);
+  const AT ed = ex * dx + ey * dy;
+  s[0] = ex * fx;
+  s[1] = ey * fy;
+  s[2] = ex * xi * fx;
+  s[3] = ex * eta * fx;
+  s[4] = ey * xi * fy;
+  s[5] = ey * eta * fy;
+  s[6] = ed;
+  s[7] = xi * ed;
+  s[8] = eta * ed;
+}
+template <typename AT>
+__device__ inline AT warp_sum_t(AT v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
 struct ListCaps {
   int cap[6], off[6], total;
 };
@@ -87,11 +109,13 @@ __host__ __device__ inline ListCaps list_caps(int w, int h) {
   return c;
 }
 
-// AT: arithmetic of the per-bar products of bars inside the set (double on the
-// FP64 path; float on the mixed path, where delta itself is FP32 and the
-// products only approximate K_aa, which leaves the iteration's fixed point
-// unchanged because P uses the FP64 residual).  Per-thread partial sums are
-// promoted to FP64 before the block reduction.
+// AT: arithmetic of the per-bar products (double on the FP64 path; float on
+// the mixed path, where delta itself is FP32 and the products only
+// approximate K_aa, which leaves the iteration's fixed point unchanged because
+// P uses the FP64 residual).  On the mixed path the interface bars' products,
+// the sums over a slot's bars (in chunks of 16, the chunks added in FP64) and
+// the block reduction of the per-thread sums run in FP32 too; on the FP64
+// path everything is FP64.
 // The kernel body for set I.
 template <typename DT, bool FULL, typename AT>
 __device__ __forceinline__ void slots_body(const LatView lv, const DT* __restrict__ delta, double* __restrict__ slots,
@@ -106,7 +130,8 @@ __device__ __forceinline__ void slots_body(const LatView lv, const DT* __restric
   const ListCaps LC = list_caps(w, h);
   double* out = slots + (size_t)I * NSLOTS * SLOT_SIZE;
 
-  for (int q = tid; q < LC.total * LSTRIDE; q += NT) lists[q] = 0.0;
+  AT* la = reinterpret_cast<AT*>(lists);  // the interface lists, in AT
+  for (int q = tid; q < LC.total * LSTRIDE; q += NT) la[q] = AT(0);
   for (int q = tid; q < NSLOTS * SLOT_SIZE; q += NT) out[q] = 0.0;
   __syncthreads();
 
@@ -261,16 +286,17 @@ __device__ __forceinline__ void slots_body(const LatView lv, const DT* __restric
       fp64_ends(da, db, xa, ya, xb, yb);
       const int Jx = Ix + dxs, Jy = Iy + dys;
       const double2 repJ = lv.rep[Jy * lv.Mx + Jx];
-      double* e = lists + (size_t)(LC.off[slot] + idx) * LSTRIDE;
-      double sa[9], sb[9];
-      mode_proj(ex, ey, xa - repI.x, ya - repI.y, fa, da, sa);
-      mode_proj(ex, ey, xb - repJ.x, yb - repJ.y, fb, db, sb);
+      AT* e = la + (size_t)(LC.off[slot] + idx) * LSTRIDE;
+      AT sa[9], sb[9];
+      mode_proj_t<AT>((AT)ex, (AT)ey, (AT)(xa - repI.x), (AT)(ya - repI.y), fa, (AT)da.x, (AT)da.y, sa);
+      mode_proj_t<AT>((AT)ex, (AT)ey, (AT)(xb - repJ.x), (AT)(yb - repJ.y), fb, (AT)db.x, (AT)db.y, sb);
+      const AT kA = (AT)k;
 #pragma unroll
       for (int m = 0; m < 9; ++m) {
         e[m] = sa[m];
         e[9 + m] = -sb[m];
-        e[18 + m] = k * sa[m];
-        e[27 + m] = -(k * sb[m]);
+        e[18 + m] = kA * sa[m];
+        e[27 + m] = -(kA * sb[m]);
       }
     }
   }
@@ -281,22 +307,23 @@ __device__ __forceinline__ void slots_body(const LatView lv, const DT* __restric
   constexpr int NACC = NREG + NGEN;
   double* red = lists + (size_t)LC.total * LSTRIDE;  // RED_CHUNK x NT
   double* tot = red + RED_CHUNK * NT;                 // NACC CTA totals
+  AT* redA = reinterpret_cast<AT*>(red);
 #pragma unroll
   for (int c0 = 0; c0 < NACC; c0 += RED_CHUNK) {
 #pragma unroll
     for (int q = 0; q < RED_CHUNK; ++q) {
       const int k = c0 + q;
-      if (k < NREG) red[q * NT + tid] = (double)reg[k];
-      else if (k < NACC) red[q * NT + tid] = (double)gen[k - NREG];
+      if (k < NREG) redA[q * NT + tid] = reg[k];
+      else if (k < NACC) redA[q * NT + tid] = gen[k - NREG];
     }
     __syncthreads();
     if (c0 + warp < NACC) {
-      const double* q = red + warp * NT + lane;
-      double v = q[0];
+      const AT* q = redA + warp * NT + lane;
+      AT v = q[0];
 #pragma unroll
       for (int ww = 1; ww < NW; ++ww) v += q[32 * ww];
-      v = warp_sum(v);
-      if (lane == 0) tot[c0 + warp] = v;
+      v = warp_sum_t<AT>(v);
+      if (lane == 0) tot[c0 + warp] = (double)v;
     }
     __syncthreads();
   }
@@ -339,9 +366,17 @@ __device__ __forceinline__ void slots_body(const LatView lv, const DT* __restric
     const int c = p + r;
     const bool dp = (p % 9) >= 6, dc = (c % 9) >= 6;
     if (!FULL && !dp && !dc) continue;
-    const double* e = lists + (size_t)LC.off[slot] * LSTRIDE;
+    const AT* e = la + (size_t)LC.off[slot] * LSTRIDE;
     double v = 0.0;
-    for (int b = 0; b < LC.cap[slot]; ++b, e += LSTRIDE) v = fma(e[18 + p], e[c], v);
+    if constexpr (sizeof(AT) == 8) {
+      for (int b = 0; b < LC.cap[slot]; ++b, e += LSTRIDE) v = fma(e[18 + p], e[c], v);
+    } else {
+      for (int b0 = 0; b0 < LC.cap[slot]; b0 += 16) {
+        AT part = AT(0);
+        for (int b = b0; b < b0 + 16 && b < LC.cap[slot]; ++b, e += LSTRIDE) part = fma(e[18 + p], e[c], part);
+        v += (double)part;
+      }
+    }
     out[slot * SLOT_SIZE + p * SLOT_DIM + c] = v;
     out[slot * SLOT_SIZE + c * SLOT_DIM + p] = v;
   }
