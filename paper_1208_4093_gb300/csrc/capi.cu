@@ -746,7 +746,7 @@ static cudaError_t alloc_instance(hms_problem* pr) {
                         s));
     CKI(palloc(pr, &D.bigs, std::max<size_t>(P.bigs.size(), 1)));
     CKI(palloc(pr, &D.inv, std::max<size_t>(P.inv.size(), 1)));
-    CKI(palloc(pr, &D.dmask, std::max<size_t>(P.max_level_bigs, 1)));
+    CKI(palloc(pr, &D.dmask, 2 * std::max<size_t>(P.max_level_bigs, 1)));
     if (!P.bigs.empty())
       CKI(cudaMemcpyAsync(D.bigs, P.bigs.data(), P.bigs.size() * sizeof(NDBig), cudaMemcpyHostToDevice, s));
     if (!P.inv.empty())
@@ -2022,7 +2022,7 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
     b += coarse_blocks_elems(lv) * 8 + P.nodes.size() * sizeof(NDNode) + P.sets.size() * 4 +
          std::max<size_t>(P.maps.size(), 1) * 4 + P.lvl_nodes.size() * 4 +
          std::max<size_t>(P.bigs.size(), 1) * sizeof(NDBig) + std::max<size_t>(P.inv.size(), 1) * 4 +
-         std::max<size_t>(P.max_level_bigs, 1) * 4 + P.f_elems * 4 + std::max<size_t>(P.w_elems, 1) * 4 + 2 * n_c * 4;
+         2 * std::max<size_t>(P.max_level_bigs, 1) * 4 + P.f_elems * 4 + std::max<size_t>(P.w_elems, 1) * 4 + 2 * n_c * 4;
   } else {
     b += 2 * (nband + 16) * 8 + (size_t)coarse_dinv_size(pr.n_c) * 8;
   }

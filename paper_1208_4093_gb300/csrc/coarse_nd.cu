@@ -31,10 +31,12 @@
 //
 // Fronts of at least ND_BIG (300) unknowns (all but the lowest levels of large
 // set grids, up to several thousand unknowns) are factored by many CTAs
-// instead: one launch assembles every wide front of a level, then per
-// 32-column panel one launch factors the diagonal blocks, one forms the panels
-// below them and one applies the rank-32 update to the trailing lower
-// triangles in 64 x 64 tiles.  Their solves hand the rectangular parts (the
+// instead: one launch assembles every wide front of a level, then per two
+// 32-column panels one launch factors the diagonal blocks (one warp per
+// front), one forms the panels below them and one applies both panels' rank-32
+// updates to the trailing lower triangles in 64 x 64 tiles, so the trailing
+// triangle is read and written once per 64 columns.  Their solves hand the
+// rectangular parts (the
 // boundary rows' products) to many-CTA kernels.  Each step does the arithmetic
 // of the one-CTA kernels in the same order, so a front gets the same factor
 // and the same solves either way; the threshold only changes the time.
@@ -378,81 +380,145 @@ __global__ void __launch_bounds__(256) k_ndb_assemble(const NDNode* __restrict__
   }
 }
 
-// Panel step k0, (a): the diagonal block of every wide front with pivots left,
-// one warp each (the one-CTA factor's step (a)).
-__global__ void __launch_bounds__(32) k_ndb_diag(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
-                                                 const int* __restrict__ sets, float* __restrict__ F,
-                                                 int* __restrict__ dropped, int* __restrict__ dmask_out, int k0,
-                                                 const IterCtl* ctl) {
+// Two 32-column panels per step (A = [k0, k0+32), B = [k0+32, k0+64)), with
+// the arithmetic of two one-panel steps in their order, so that the trailing
+// triangle is read and written once per 64 columns.
+//
+// (a, b) One warp per front: A's diagonal block (factor, inverse, drops), the
+// rows of B below it (L21 = F[B][A] Dinv_A^T), B's diagonal block updated by
+// L21 L21^T, then B's diagonal block (factor, inverse, drops).
+__global__ void __launch_bounds__(32) k_ndb_diag2(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                  const int* __restrict__ sets, float* __restrict__ F,
+                                                  int* __restrict__ dropped, int* __restrict__ dmask_out, int k0,
+                                                  const IterCtl* ctl) {
   if (nd_done(ctl)) return;
   const NDNode nd = nodes[bigs[blockIdx.x].node];
   const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
   if (k0 >= nS) return;
-  const int lane = threadIdx.x, kb = min(PB, nS - k0);
+  __shared__ float DA[PB][PB + 1];
+  __shared__ float L21[PB][PB + 1];
+  const int lane = threadIdx.x, kbA = min(PB, nS - k0), kB = k0 + PB, kbB = min(PB, nS - kB);
   float* fg = F + nd.f_off;
   const int* st = sets + nd.s_off;
   float a[PB], x[PB];
+  // A: the one-panel step (a)
 #pragma unroll
-  for (int c = 0; c < PB; ++c) a[c] = (lane < kb && c <= lane) ? fg[(size_t)(k0 + lane) * nf + k0 + c] : 0.f;
-  const unsigned dm = nd_diag_factor(a, kb, lane);
-  nd_tri_invert(a, x, kb, lane);
-  // inverse[r][lane] = x[r] into the block's place (r >= lane)
+  for (int c = 0; c < PB; ++c) a[c] = (lane < kbA && c <= lane) ? fg[(size_t)(k0 + lane) * nf + k0 + c] : 0.f;
+  const unsigned dmA = nd_diag_factor(a, kbA, lane);
+  nd_tri_invert(a, x, kbA, lane);
 #pragma unroll
-  for (int r = 0; r < PB; ++r)
-    if (r < kb && lane <= r) fg[(size_t)(k0 + r) * nf + k0 + lane] = x[r];
-  for (int c = 0; c < kb; ++c)
-    if ((dm >> c) & 1u) {
+  for (int r = 0; r < PB; ++r) {
+    DA[r][lane] = x[r];
+    if (r < kbA && lane <= r) fg[(size_t)(k0 + r) * nf + k0 + lane] = x[r];
+  }
+  for (int c = 0; c < kbA; ++c)
+    if ((dmA >> c) & 1u) {
       for (int j = lane; j < k0; j += 32) fg[(size_t)(k0 + c) * nf + j] = 0.f;
       if (lane == 0) dropped[nd_glob(st, k0 + c, nm)] = 1;
     }
-  if (lane == 0) dmask_out[blockIdx.x] = (int)dm;
+  unsigned dmB = 0u;
+  __syncwarp();
+  if (kbB > 0) {
+    // B's rows of A's panel (the one-panel step (b) on those rows)
+    for (int r = 0; r < kbB; ++r) {
+      float* row = fg + (size_t)(kB + r) * nf + k0;
+      const float fv = lane < kbA ? row[lane] : 0.f;
+      float sacc = 0.f;
+#pragma unroll
+      for (int u = 0; u < PB; ++u) sacc = fmaf(__shfl_sync(0xffffffffu, fv, u), DA[lane][u], sacc);
+      if ((dmA >> lane) & 1u) sacc = 0.f;
+      L21[r][lane] = lane < kbA ? sacc : 0.f;
+      if (lane < kbA) row[lane] = sacc;
+    }
+    __syncwarp();
+    // B's diagonal block takes A's rank-kbA update (the one-panel step (c) there)
+    for (int i = 0; i < kbB; ++i) {
+      if (lane <= i) {
+        float acc = 0.f;
+        for (int u = 0; u < kbA; ++u) acc = fmaf(L21[i][u], L21[lane][u], acc);
+        fg[(size_t)(kB + i) * nf + kB + lane] -= acc;
+      }
+    }
+    __syncwarp();
+    // B: the one-panel step (a)
+#pragma unroll
+    for (int c = 0; c < PB; ++c) a[c] = (lane < kbB && c <= lane) ? fg[(size_t)(kB + lane) * nf + kB + c] : 0.f;
+    dmB = nd_diag_factor(a, kbB, lane);
+    nd_tri_invert(a, x, kbB, lane);
+#pragma unroll
+    for (int r = 0; r < PB; ++r)
+      if (r < kbB && lane <= r) fg[(size_t)(kB + r) * nf + kB + lane] = x[r];
+    for (int c = 0; c < kbB; ++c)
+      if ((dmB >> c) & 1u) {
+        for (int j = lane; j < kB; j += 32) fg[(size_t)(kB + c) * nf + j] = 0.f;
+        if (lane == 0) dropped[nd_glob(st, kB + c, nm)] = 1;
+      }
+  }
+  if (lane == 0) {
+    dmask_out[2 * blockIdx.x] = (int)dmA;
+    dmask_out[2 * blockIdx.x + 1] = (int)dmB;
+  }
 }
 
-// (b): the panel below the diagonal block, L[i][blk] = F[i][blk] Dinv^T (one
-// warp per row, lane = column); CTA (x, y): rows r0 + 64x .. of front y.
-__global__ void __launch_bounds__(256) k_ndb_panel(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
-                                                   float* __restrict__ F, const int* __restrict__ dmask, int k0,
-                                                   const IterCtl* ctl) {
+// (c) The rows below both panels, one warp per row (lane = column): L[i][A] =
+// F[i][A] Dinv_A^T; F[i][B] takes A's update; L[i][B] = F[i][B] Dinv_B^T.
+// CTA (x, y): rows r0 + 64x .. of front y, r0 = k0 + kbA + kbB.
+__global__ void __launch_bounds__(256) k_ndb_panel2(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                    float* __restrict__ F, const int* __restrict__ dmask, int k0,
+                                                    const IterCtl* ctl) {
   if (nd_done(ctl)) return;
   const NDNode nd = nodes[bigs[blockIdx.y].node];
   const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
   if (k0 >= nS) return;
-  const int kb = min(PB, nS - k0), r0 = k0 + kb;
+  const int kbA = min(PB, nS - k0), kB = k0 + PB, kbB = max(0, min(PB, nS - kB));
+  const int r0 = k0 + kbA + kbB;
   const int rbeg = r0 + 64 * blockIdx.x;
   if (rbeg >= nf) return;
-  __shared__ float Dinv[PB][PB + 1];
+  __shared__ float DA[PB][PB + 1], DB[PB][PB + 1], L21[PB][PB + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* fg = F + nd.f_off;
-  // Dinv[r][c] = inverse[r][c] (lower), zero above
   for (int e = tid; e < PB * PB; e += 256) {
     const int r = e / PB, c = e % PB;
-    Dinv[r][c] = (r < kb && c <= r) ? fg[(size_t)(k0 + r) * nf + k0 + c] : 0.f;
+    DA[r][c] = (r < kbA && c <= r) ? fg[(size_t)(k0 + r) * nf + k0 + c] : 0.f;
+    DB[r][c] = (r < kbB && c <= r) ? fg[(size_t)(kB + r) * nf + kB + c] : 0.f;
+    L21[r][c] = (r < kbB && c < kbA) ? fg[(size_t)(kB + r) * nf + k0 + c] : 0.f;
   }
   __syncthreads();
-  const unsigned dmk = (unsigned)dmask[blockIdx.y];
+  const unsigned dmA = (unsigned)dmask[2 * blockIdx.y], dmB = (unsigned)dmask[2 * blockIdx.y + 1];
   for (int i = rbeg + warp; i < nf && i < rbeg + 64; i += 8) {
-    const float fv = lane < kb ? fg[(size_t)i * nf + k0 + lane] : 0.f;
-    float sacc = 0.f;
+    float* row = fg + (size_t)i * nf;
+    const float fv = lane < kbA ? row[k0 + lane] : 0.f;
+    float sA = 0.f;
 #pragma unroll
-    for (int u = 0; u < PB; ++u) sacc = fmaf(__shfl_sync(0xffffffffu, fv, u), Dinv[lane][u], sacc);
-    if ((dmk >> lane) & 1u) sacc = 0.f;
-    if (lane < kb) fg[(size_t)i * nf + k0 + lane] = sacc;
+    for (int u = 0; u < PB; ++u) sA = fmaf(__shfl_sync(0xffffffffu, fv, u), DA[lane][u], sA);
+    if ((dmA >> lane) & 1u) sA = 0.f;
+    if (lane < kbA) row[k0 + lane] = sA;
+    if (kbB > 0) {
+      float acc = 0.f;
+      for (int u = 0; u < kbA; ++u) acc = fmaf(__shfl_sync(0xffffffffu, sA, u), L21[lane][u], acc);
+      const float fb = lane < kbB ? row[kB + lane] - acc : 0.f;
+      float sB = 0.f;
+#pragma unroll
+      for (int u = 0; u < PB; ++u) sB = fmaf(__shfl_sync(0xffffffffu, fb, u), DB[lane][u], sB);
+      if ((dmB >> lane) & 1u) sB = 0.f;
+      if (lane < kbB) row[kB + lane] = sB;
+    }
   }
 }
 
-// (c): F[i][j] -= sum_u L[i][u] L[j][u] over the trailing lower triangle, in
-// 64 x 64 tiles (CTA x: tile (ti, tj), ti >= tj; y: front), 4 x 4 per thread.
-// The tile's two panels are staged transposed (Lt[u][row], rows padded to 68
-// floats) so that a thread reads its four rows, and its four columns, as one
-// float4 each.  Each sum runs over u in order from 0, as in the one-CTA factor.
-constexpr int ULD = 68;
-__global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
-                                                    float* __restrict__ F, int k0, const IterCtl* ctl) {
+constexpr int ULD = 68;  // padded row of the transposed panels (16-byte multiple)
+
+// (d) The trailing lower triangle below both panels, rows and columns from r0
+// = k0 + kbA + kbB, in 64 x 64 tiles: F[i][j] takes A's rank-kbA update, then
+// B's, each sum over u in order from 0 (the two one-panel updates).
+__global__ void __launch_bounds__(256) k_ndb_update2(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                     float* __restrict__ F, int k0, const IterCtl* ctl) {
   if (nd_done(ctl)) return;
   const NDNode nd = nodes[bigs[blockIdx.y].node];
   const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
   if (k0 >= nS) return;
-  const int kb = min(PB, nS - k0), r0 = k0 + kb, m = nf - r0;
+  const int kbA = min(PB, nS - k0), kB = k0 + PB, kbB = max(0, min(PB, nS - kB));
+  const int r0 = k0 + kbA + kbB, m = nf - r0;
   const int T = (m + 63) / 64;
   const int t = blockIdx.x;
   if (t >= T * (T + 1) / 2) return;
@@ -460,31 +526,41 @@ __global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ n
   while (ti * (ti + 1) / 2 > t) --ti;
   while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
   const int tj = t - ti * (ti + 1) / 2;
-  __shared__ __align__(16) float La[PB][ULD];
-  __shared__ __align__(16) float Lb[PB][ULD];
+  __shared__ __align__(16) float La[2][PB][ULD];
+  __shared__ __align__(16) float Lb[2][PB][ULD];
   float* fg = F + nd.f_off;
   const int tid = threadIdx.x;
-  for (int e = tid; e < 64 * PB; e += 256) {
-    const int r = e / PB, u = e % PB;
+  for (int e = tid; e < 64 * 2 * PB; e += 256) {
+    const int r = e / (2 * PB), q = e % (2 * PB), pnl = q / PB, u = q % PB;
+    const int kbq = pnl == 0 ? kbA : kbB, kq = pnl == 0 ? k0 : kB;
     const int ia = 64 * ti + r, jb = 64 * tj + r;
-    La[u][r] = (ia < m && u < kb) ? fg[(size_t)(r0 + ia) * nf + k0 + u] : 0.f;
-    Lb[u][r] = (jb < m && u < kb) ? fg[(size_t)(r0 + jb) * nf + k0 + u] : 0.f;
+    La[pnl][u][r] = (ia < m && u < kbq) ? fg[(size_t)(r0 + ia) * nf + kq + u] : 0.f;
+    Lb[pnl][u][r] = (jb < m && u < kbq) ? fg[(size_t)(r0 + jb) * nf + kq + u] : 0.f;
   }
   __syncthreads();
   const int ty = tid / 16, tx = tid % 16;
-  float acc[4][4];
+  float acc[4][4], acc2[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  for (int u = 0; u < kb; ++u) {
-    const float4 qa = *reinterpret_cast<const float4*>(&La[u][4 * ty]);
-    const float4 qb = *reinterpret_cast<const float4*>(&Lb[u][4 * tx]);
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f, acc2[a][b] = 0.f;
+  for (int u = 0; u < kbA; ++u) {
+    const float4 qa = *reinterpret_cast<const float4*>(&La[0][u][4 * ty]);
+    const float4 qb = *reinterpret_cast<const float4*>(&Lb[0][u][4 * tx]);
     const float pa[4] = {qa.x, qa.y, qa.z, qa.w}, pb[4] = {qb.x, qb.y, qb.z, qb.w};
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(pa[a], pb[b], acc[a][b]);
+  }
+  for (int u = 0; u < kbB; ++u) {
+    const float4 qa = *reinterpret_cast<const float4*>(&La[1][u][4 * ty]);
+    const float4 qb = *reinterpret_cast<const float4*>(&Lb[1][u][4 * tx]);
+    const float pa[4] = {qa.x, qa.y, qa.z, qa.w}, pb[4] = {qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc2[a][b] = fmaf(pa[a], pb[b], acc2[a][b]);
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
@@ -493,7 +569,12 @@ __global__ void __launch_bounds__(256) k_ndb_update(const NDNode* __restrict__ n
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int j = 64 * tj + 4 * tx + b;
-      if (j <= i) fg[(size_t)(r0 + i) * nf + r0 + j] -= acc[a][b];
+      if (j <= i) {
+        float* f = fg + (size_t)(r0 + i) * nf + r0 + j;
+        float v = *f - acc[a][b];
+        if (kbB > 0) v -= acc2[a][b];
+        *f = v;
+      }
     }
   }
 }
@@ -1012,16 +1093,16 @@ cudaError_t launch_nd_factor(cudaStream_t s, const LatView& lv, const NDPlanHost
     const int maxnf = P.level_big_nf[h];
     k_ndb_assemble<<<dim3((maxnf + 31) / 32, nb), 256, 0, s>>>(D.nodes, bg, D.sets, D.inv, src, D.F, ctl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    for (int k0 = 0; k0 < P.level_big_ns[h]; k0 += PB) {
-      k_ndb_diag<<<nb, 32, 0, s>>>(D.nodes, bg, D.sets, D.F, dropped, D.dmask, k0, ctl);
+    for (int k0 = 0; k0 < P.level_big_ns[h]; k0 += 2 * PB) {
+      k_ndb_diag2<<<nb, 32, 0, s>>>(D.nodes, bg, D.sets, D.F, dropped, D.dmask, k0, ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       // the largest trailing size over the level's fronts that still have pivots
       const long long m = (long long)maxnf - k0 - 1;
       const int rows = (int)((m + 63) / 64);
       const long long T = (m + 63) / 64;
-      k_ndb_panel<<<dim3(std::max(rows, 1), nb), 256, 0, s>>>(D.nodes, bg, D.F, D.dmask, k0, ctl);
+      k_ndb_panel2<<<dim3(std::max(rows, 1), nb), 256, 0, s>>>(D.nodes, bg, D.F, D.dmask, k0, ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      k_ndb_update<<<dim3((unsigned)std::max(T * (T + 1) / 2, 1LL), nb), 256, 0, s>>>(D.nodes, bg, D.F, k0, ctl);
+      k_ndb_update2<<<dim3((unsigned)std::max(T * (T + 1) / 2, 1LL), nb), 256, 0, s>>>(D.nodes, bg, D.F, k0, ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }
