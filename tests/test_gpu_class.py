@@ -156,3 +156,33 @@ def test_class_estimate_equals_allocation(hms_ctx, prec):
     assert held < est < held + 64 * 2**20
     per_set = capi.hms_problem_estimate_bytes(hms_ctx, 200, 150, 32, 32, precision=prec, tol=1e-8, max_iter=100)
     assert est < per_set  # the class factors take far less than one factor per set
+
+
+def test_class_factors_in_batches_and_clones(hms_ctx):
+    """Problems with class factors (and a clone sharing them) solved together
+    by hms_solve_batch equal their solo solves bit for bit, and the automatic
+    engine choice falls back to the stream engine for them."""
+    from paper_1208_4093_gb300 import capi
+    specs = [(100, 80, 16, 16, 0), (131, 70, 32, 16, 1), (100, 80, 16, 16, 2)]
+    prs = []
+    for nx, ny, sx, sy, _ in specs[:2]:
+        prs.append(capi.hms_problem_create(hms_ctx, nx, ny, sx, sy, precision=1, tol=1e-9, max_iter=2000,
+                                           class_factors=1))
+    prs.append(capi.hms_problem_clone(hms_ctx, prs[0]))
+    try:
+        loads_ = [loads(nx, ny, seed).reshape(1, -1) for nx, ny, _, _, seed in specs]
+        outs = [np.empty_like(p) for p in loads_]
+        its = np.zeros(3, np.int32)
+        capi.hms_solve_batch(hms_ctx, prs, loads_, outs, iters=its)
+        for k, pr in enumerate(prs):
+            solo = np.empty_like(loads_[k])
+            it1 = np.zeros(1, np.int32)
+            capi.hms_solve(hms_ctx, pr, loads_[k], solo, iters=it1)
+            assert np.array_equal(solo, outs[k]), k
+            assert int(it1[0]) == int(its[k])
+            nx, ny = specs[k][:2]
+            tr = truss.Truss(nx, ny)
+            assert rel(outs[k][0], direct.cholesky_solve(tr, tr.free * loads_[k][0])) < 1e-8
+    finally:
+        for pr in prs:
+            capi.hms_problem_destroy(pr)
