@@ -384,43 +384,50 @@ __global__ void __launch_bounds__(256) k_ndb_assemble(const NDNode* __restrict__
 // the arithmetic of two one-panel steps in their order, so that the trailing
 // triangle is read and written once per 64 columns.
 //
-// (a, b) One warp per front: A's diagonal block (factor, inverse, drops), the
-// rows of B below it (L21 = F[B][A] Dinv_A^T), B's diagonal block updated by
-// L21 L21^T, then B's diagonal block (factor, inverse, drops).
-__global__ void __launch_bounds__(32) k_ndb_diag2(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
-                                                  const int* __restrict__ sets, float* __restrict__ F,
-                                                  int* __restrict__ dropped, int* __restrict__ dmask_out, int k0,
-                                                  const IterCtl* ctl) {
+// (a, b) One CTA of 8 warps per front: warp 0 factors A's diagonal block
+// (factor, inverse, drops); all warps form the rows of B below it (L21 =
+// F[B][A] Dinv_A^T, a warp per row) and update B's diagonal block by L21
+// L21^T (a thread per entry); warp 0 factors B's diagonal block.
+__global__ void __launch_bounds__(256) k_ndb_diag2(const NDNode* __restrict__ nodes, const NDBig* __restrict__ bigs,
+                                                   const int* __restrict__ sets, float* __restrict__ F,
+                                                   int* __restrict__ dropped, int* __restrict__ dmask_out, int k0,
+                                                   const IterCtl* ctl) {
   if (nd_done(ctl)) return;
   const NDNode nd = nodes[bigs[blockIdx.x].node];
   const int nm = nd.nm, nS = nm * nd.ns, nf = nm * (nd.ns + nd.nb);
   if (k0 >= nS) return;
   __shared__ float DA[PB][PB + 1];
   __shared__ float L21[PB][PB + 1];
-  const int lane = threadIdx.x, kbA = min(PB, nS - k0), kB = k0 + PB, kbB = min(PB, nS - kB);
+  __shared__ unsigned dmAs;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int kbA = min(PB, nS - k0), kB = k0 + PB, kbB = min(PB, nS - kB);
   float* fg = F + nd.f_off;
   const int* st = sets + nd.s_off;
-  float a[PB], x[PB];
-  // A: the one-panel step (a)
+  if (warp == 0) {
+    // A: the one-panel step (a)
+    float a[PB], x[PB];
 #pragma unroll
-  for (int c = 0; c < PB; ++c) a[c] = (lane < kbA && c <= lane) ? fg[(size_t)(k0 + lane) * nf + k0 + c] : 0.f;
-  const unsigned dmA = nd_diag_factor(a, kbA, lane);
-  nd_tri_invert(a, x, kbA, lane);
+    for (int c = 0; c < PB; ++c) a[c] = (lane < kbA && c <= lane) ? fg[(size_t)(k0 + lane) * nf + k0 + c] : 0.f;
+    const unsigned dm = nd_diag_factor(a, kbA, lane);
+    nd_tri_invert(a, x, kbA, lane);
 #pragma unroll
-  for (int r = 0; r < PB; ++r) {
-    DA[r][lane] = x[r];
-    if (r < kbA && lane <= r) fg[(size_t)(k0 + r) * nf + k0 + lane] = x[r];
-  }
-  for (int c = 0; c < kbA; ++c)
-    if ((dmA >> c) & 1u) {
-      for (int j = lane; j < k0; j += 32) fg[(size_t)(k0 + c) * nf + j] = 0.f;
-      if (lane == 0) dropped[nd_glob(st, k0 + c, nm)] = 1;
+    for (int r = 0; r < PB; ++r) {
+      DA[r][lane] = x[r];
+      if (r < kbA && lane <= r) fg[(size_t)(k0 + r) * nf + k0 + lane] = x[r];
     }
+    for (int c = 0; c < kbA; ++c)
+      if ((dm >> c) & 1u) {
+        for (int jj = lane; jj < k0; jj += 32) fg[(size_t)(k0 + c) * nf + jj] = 0.f;
+        if (lane == 0) dropped[nd_glob(st, k0 + c, nm)] = 1;
+      }
+    if (lane == 0) dmAs = dm;
+  }
+  __syncthreads();
+  const unsigned dmA = dmAs;
   unsigned dmB = 0u;
-  __syncwarp();
   if (kbB > 0) {
     // B's rows of A's panel (the one-panel step (b) on those rows)
-    for (int r = 0; r < kbB; ++r) {
+    for (int r = warp; r < kbB; r += 8) {
       float* row = fg + (size_t)(kB + r) * nf + k0;
       const float fv = lane < kbA ? row[lane] : 0.f;
       float sacc = 0.f;
@@ -430,31 +437,35 @@ __global__ void __launch_bounds__(32) k_ndb_diag2(const NDNode* __restrict__ nod
       L21[r][lane] = lane < kbA ? sacc : 0.f;
       if (lane < kbA) row[lane] = sacc;
     }
-    __syncwarp();
+    __syncthreads();
     // B's diagonal block takes A's rank-kbA update (the one-panel step (c) there)
-    for (int i = 0; i < kbB; ++i) {
-      if (lane <= i) {
+    for (int e = tid; e < PB * PB; e += 256) {
+      const int i = e / PB, jj = e % PB;
+      if (i < kbB && jj <= i) {
         float acc = 0.f;
-        for (int u = 0; u < kbA; ++u) acc = fmaf(L21[i][u], L21[lane][u], acc);
-        fg[(size_t)(kB + i) * nf + kB + lane] -= acc;
+        for (int u = 0; u < kbA; ++u) acc = fmaf(L21[i][u], L21[jj][u], acc);
+        fg[(size_t)(kB + i) * nf + kB + jj] -= acc;
       }
     }
-    __syncwarp();
-    // B: the one-panel step (a)
+    __syncthreads();
+    if (warp == 0) {
+      // B: the one-panel step (a)
+      float a[PB], x[PB];
 #pragma unroll
-    for (int c = 0; c < PB; ++c) a[c] = (lane < kbB && c <= lane) ? fg[(size_t)(kB + lane) * nf + kB + c] : 0.f;
-    dmB = nd_diag_factor(a, kbB, lane);
-    nd_tri_invert(a, x, kbB, lane);
+      for (int c = 0; c < PB; ++c) a[c] = (lane < kbB && c <= lane) ? fg[(size_t)(kB + lane) * nf + kB + c] : 0.f;
+      dmB = nd_diag_factor(a, kbB, lane);
+      nd_tri_invert(a, x, kbB, lane);
 #pragma unroll
-    for (int r = 0; r < PB; ++r)
-      if (r < kbB && lane <= r) fg[(size_t)(kB + r) * nf + kB + lane] = x[r];
-    for (int c = 0; c < kbB; ++c)
-      if ((dmB >> c) & 1u) {
-        for (int j = lane; j < kB; j += 32) fg[(size_t)(kB + c) * nf + j] = 0.f;
-        if (lane == 0) dropped[nd_glob(st, kB + c, nm)] = 1;
-      }
+      for (int r = 0; r < PB; ++r)
+        if (r < kbB && lane <= r) fg[(size_t)(kB + r) * nf + kB + lane] = x[r];
+      for (int c = 0; c < kbB; ++c)
+        if ((dmB >> c) & 1u) {
+          for (int jj = lane; jj < kB; jj += 32) fg[(size_t)(kB + c) * nf + jj] = 0.f;
+          if (lane == 0) dropped[nd_glob(st, kB + c, nm)] = 1;
+        }
+    }
   }
-  if (lane == 0) {
+  if (tid == 0) {
     dmask_out[2 * blockIdx.x] = (int)dmA;
     dmask_out[2 * blockIdx.x + 1] = (int)dmB;
   }
@@ -1094,7 +1105,7 @@ cudaError_t launch_nd_factor(cudaStream_t s, const LatView& lv, const NDPlanHost
     k_ndb_assemble<<<dim3((maxnf + 31) / 32, nb), 256, 0, s>>>(D.nodes, bg, D.sets, D.inv, src, D.F, ctl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     for (int k0 = 0; k0 < P.level_big_ns[h]; k0 += 2 * PB) {
-      k_ndb_diag2<<<nb, 32, 0, s>>>(D.nodes, bg, D.sets, D.F, dropped, D.dmask, k0, ctl);
+      k_ndb_diag2<<<nb, 256, 0, s>>>(D.nodes, bg, D.sets, D.F, dropped, D.dmask, k0, ctl);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       // the largest trailing size over the level's fronts that still have pivots
       const long long m = (long long)maxnf - k0 - 1;
