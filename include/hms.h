@@ -104,11 +104,14 @@ typedef struct {
                                 4 = FP32 on one SM, 5 = FP32 two-sided: top and bottom
                                 segments eliminated at once on two SMs, then the
                                 separator between them, 6 = FP32 nested dissection of
-                                the set grid: boxes of sets cut by a middle column or
+                                the set grid over K_aa kept as 9 x 9 blocks per set
+                                pair (no band): boxes of sets cut by a middle column or
                                 row of sets, the fronts of one level of the tree
-                                factored at once, one CTA each (set grids of any
-                                width; auto takes it where no band factor fits,
-                                e.g. more than about 22 sets across) */
+                                factored at once, one CTA each, fronts of 300 or more
+                                unknowns by many CTAs (set grids of any width, up to
+                                the 350 x 350 sets of a 1e9-DOF lattice; auto takes it
+                                where no band factor fits, e.g. more than about 22
+                                sets across) */
   int32_t relax_threads;     /* compute threads per CTA of the relaxation (Eqs. 11-13; one more
                                 warp issues its copies): 64, 128 or 256, or
                                 0 = autotuned: the first problem of a set-tile shape and
