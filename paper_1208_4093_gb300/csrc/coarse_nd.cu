@@ -541,15 +541,38 @@ __global__ void __launch_bounds__(256) k_ndb_update2(const NDNode* __restrict__ 
   __shared__ __align__(16) float Lb[2][PB][ULD];
   float* fg = F + nd.f_off;
   const int tid = threadIdx.x;
-  for (int e = tid; e < 64 * 2 * PB; e += 256) {
-    const int r = e / (2 * PB), q = e % (2 * PB), pnl = q / PB, u = q % PB;
-    const int kbq = pnl == 0 ? kbA : kbB, kq = pnl == 0 ? k0 : kB;
-    const int ia = 64 * ti + r, jb = 64 * tj + r;
-    La[pnl][u][r] = (ia < m && u < kbq) ? fg[(size_t)(r0 + ia) * nf + kq + u] : 0.f;
-    Lb[pnl][u][r] = (jb < m && u < kbq) ? fg[(size_t)(r0 + jb) * nf + kq + u] : 0.f;
+  {
+    // all the tile's loads issued before the shared-memory stores (latency)
+    constexpr int NE = 64 * 2 * PB / 256;
+    float va[NE], vb[NE];
+#pragma unroll
+    for (int q0 = 0; q0 < NE; ++q0) {
+      const int e = tid + 256 * q0;
+      const int r = e / (2 * PB), q = e % (2 * PB), pnl = q / PB, u = q % PB;
+      const int kbq = pnl == 0 ? kbA : kbB, kq = pnl == 0 ? k0 : kB;
+      const int ia = 64 * ti + r, jb = 64 * tj + r;
+      va[q0] = (ia < m && u < kbq) ? fg[(size_t)(r0 + ia) * nf + kq + u] : 0.f;
+      vb[q0] = (jb < m && u < kbq) ? fg[(size_t)(r0 + jb) * nf + kq + u] : 0.f;
+    }
+#pragma unroll
+    for (int q0 = 0; q0 < NE; ++q0) {
+      const int e = tid + 256 * q0;
+      const int r = e / (2 * PB), q = e % (2 * PB), pnl = q / PB, u = q % PB;
+      La[pnl][u][r] = va[q0];
+      Lb[pnl][u][r] = vb[q0];
+    }
   }
   __syncthreads();
   const int ty = tid / 16, tx = tid % 16;
+  // this thread's 4 x 4 entries of F, fetched before the products (latency)
+  float cur[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = 64 * ti + 4 * ty + a, j = 64 * tj + 4 * tx + b;
+      cur[a][b] = (i < m && j <= i) ? fg[(size_t)(r0 + i) * nf + r0 + j] : 0.f;
+    }
   float acc[4][4], acc2[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -581,10 +604,9 @@ __global__ void __launch_bounds__(256) k_ndb_update2(const NDNode* __restrict__ 
     for (int b = 0; b < 4; ++b) {
       const int j = 64 * tj + 4 * tx + b;
       if (j <= i) {
-        float* f = fg + (size_t)(r0 + i) * nf + r0 + j;
-        float v = *f - acc[a][b];
+        float v = cur[a][b] - acc[a][b];
         if (kbB > 0) v -= acc2[a][b];
-        *f = v;
+        fg[(size_t)(r0 + i) * nf + r0 + j] = v;
       }
     }
   }
