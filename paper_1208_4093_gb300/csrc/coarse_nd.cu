@@ -496,9 +496,21 @@ __global__ void __launch_bounds__(256) k_ndb_panel2(const NDNode* __restrict__ n
   }
   __syncthreads();
   const unsigned dmA = (unsigned)dmask[2 * blockIdx.y], dmB = (unsigned)dmask[2 * blockIdx.y + 1];
-  for (int i = rbeg + warp; i < nf && i < rbeg + 64; i += 8) {
+  // this warp's eight rows, their entries of both panels loaded first (latency)
+  float fa[8], fbv[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int i = rbeg + warp + 8 * q;
+    const bool in = i < nf;
+    fa[q] = (in && lane < kbA) ? fg[(size_t)i * nf + k0 + lane] : 0.f;
+    fbv[q] = (in && lane < kbB) ? fg[(size_t)i * nf + kB + lane] : 0.f;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int i = rbeg + warp + 8 * q;
+    if (i >= nf) break;
     float* row = fg + (size_t)i * nf;
-    const float fv = lane < kbA ? row[k0 + lane] : 0.f;
+    const float fv = fa[q];
     float sA = 0.f;
 #pragma unroll
     for (int u = 0; u < PB; ++u) sA = fmaf(__shfl_sync(0xffffffffu, fv, u), DA[lane][u], sA);
@@ -507,7 +519,7 @@ __global__ void __launch_bounds__(256) k_ndb_panel2(const NDNode* __restrict__ n
     if (kbB > 0) {
       float acc = 0.f;
       for (int u = 0; u < kbA; ++u) acc = fmaf(__shfl_sync(0xffffffffu, sA, u), L21[lane][u], acc);
-      const float fb = lane < kbB ? row[kB + lane] - acc : 0.f;
+      const float fb = lane < kbB ? fbv[q] - acc : 0.f;
       float sB = 0.f;
 #pragma unroll
       for (int u = 0; u < PB; ++u) sB = fmaf(__shfl_sync(0xffffffffu, fb, u), DB[lane][u], sB);
