@@ -70,8 +70,10 @@ __device__ inline double2 apply_update(const LatView& lv, double2 v, int i, int 
   const int I = set_of(lv, i, j);
   const double* aI = a + (size_t)lv.q * I;
   const double2 c = lv.rep[I];
-  const double xi = node_x(lv, i, j) - c.x;
-  const double eta = node_y(lv, j) - c.y;
+  // xi = x - x^(I), eta = y - y^(I) as one FMA each (the half-column offset of odd
+  // rows added to i exactly)
+  const double xi = fma(lv.L, (double)i + ((j & 1) ? 0.5 : 0.0), -c.x);
+  const double eta = fma(lv.L * SQ3_2, (double)j, -c.y);
   const double2 d = load_delta(delta, n);
   const unsigned fm = lv.fix[n];
   const double cd = fma(__ldg(aI + 8), eta, fma(__ldg(aI + 7), xi, __ldg(aI + 6)));
