@@ -355,27 +355,65 @@ __global__ void __launch_bounds__(256) k_ndb_assemble(const NDNode* __restrict__
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int* st = sets + nd.s_off;
   float* fg = F + nd.f_off;
-  NDNode ch[2];
-  for (int c = 0; c < nd.nchild; ++c) ch[c] = nodes[nd.child[c]];
+  // the children's front shapes (at most two; indices fixed at compile time so
+  // that they stay in registers)
+  long long cf_off[2] = {0, 0};
+  int cnS[2] = {0, 0}, cnf[2] = {0, 0};
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+    if (c < nd.nchild) {
+      const NDNode chn = nodes[nd.child[c]];
+      cf_off[c] = chn.f_off;
+      cnS[c] = chn.nm * chn.ns;
+      cnf[c] = cnS[c] + chn.nm * chn.nb;
+    }
   for (int p = blockIdx.x * 32 + warp; p < nf && p < blockIdx.x * 32 + 32; p += 8) {
     const int gp = nd_glob(st, p, nm);
-    int kp[2];
-    for (int c = 0; c < nd.nchild; ++c) {
-      const int t = inv[bg.inv_off[c] + p / nm];
-      kp[c] = t < 0 ? -1 : nm * t + p % nm;
-    }
-    for (int q = lane; q <= p; q += 32) {
-      float v = q < nS ? src(gp, nd_glob(st, q, nm)) : 0.f;
-      for (int c = 0; c < nd.nchild; ++c) {
-        if (kp[c] < 0) continue;
-        const int t = inv[bg.inv_off[c] + q / nm];
-        if (t < 0) continue;
-        const int kq = nm * t + q % nm;
-        const int nSc = ch[c].nm * ch[c].ns, nfc = nSc + ch[c].nm * ch[c].nb;
-        const int a = kp[c] > kq ? kp[c] : kq, b = kp[c] > kq ? kq : kp[c];
-        v += F[ch[c].f_off + (size_t)(nSc + a) * nfc + nSc + b];
+    int kp[2] = {-1, -1};
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      if (c < nd.nchild) {
+        const int t = inv[bg.inv_off[c] + p / nm];
+        kp[c] = t < 0 ? -1 : nm * t + p % nm;
       }
-      fg[(size_t)p * nf + q] = v;
+    // AU columns per lane at a time: their loads are independent, so they are
+    // all issued before the stores (the same value per entry, added in the
+    // same order)
+    constexpr int AU = 4;
+    for (int q0 = lane; q0 <= p; q0 += 32 * AU) {
+      float v[AU];
+#pragma unroll
+      for (int k = 0; k < AU; ++k) {
+        const int q = q0 + 32 * k;
+        v[k] = (q <= p && q < nS) ? src(gp, nd_glob(st, q, nm)) : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (c >= nd.nchild || kp[c] < 0) continue;
+        const int nSc = cnS[c], nfc = cnf[c];
+        float add[AU];
+#pragma unroll
+        for (int k = 0; k < AU; ++k) {
+          const int q = q0 + 32 * k;
+          add[k] = 0.f;
+          const int t = q <= p ? inv[bg.inv_off[c] + q / nm] : -1;
+          if (t >= 0) {
+            const int kq = nm * t + q % nm;
+            const int a = kp[c] > kq ? kp[c] : kq, b = kp[c] > kq ? kq : kp[c];
+            add[k] = F[cf_off[c] + (size_t)(nSc + a) * nfc + nSc + b];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < AU; ++k) {
+          const int q = q0 + 32 * k;
+          if (q <= p && inv[bg.inv_off[c] + q / nm] >= 0) v[k] += add[k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < AU; ++k) {
+        const int q = q0 + 32 * k;
+        if (q <= p) fg[(size_t)p * nf + q] = v[k];
+      }
     }
   }
 }
