@@ -159,6 +159,21 @@ typedef struct {
                                 CTA.  Needs ea = NULL, relax_overlap = 0 and mode_mask bits
                                 9-11 clear.  The increments equal the per-set ones up to
                                 rounding (another order of the sums) */
+  int32_t relax_balance;     /* schedule of the relaxation with per-set factors:
+                                1 = one CTA per set (sets in waves of the SM count);
+                                2 = balanced: one persistent CTA per SM (cooperative
+                                launch), each running an equal share of all sets'
+                                substitution steps, a set cut between two CTAs at a step
+                                whose state is in device memory (McNaughton's wrap-around
+                                rule: the first CTA runs the set's head first, the second
+                                its tail last, after a bounded wait on a per-set flag).
+                                Needs more sets than SMs, none costing more than an SM's
+                                share, relax_threads 0 or 256, relax_copies 0 or 1,
+                                relax_overlap = 0 and class_factors = 0 (else
+                                HMS_ERR_ARG);
+                                0 = with relax_threads = 0 timed together with the CTA
+                                sizes where it applies, else 1.  Results are bitwise the
+                                same either way */
 } hms_options;
 
 /* Context: one device, one CUDA stream.  device = CUDA ordinal. */
@@ -194,6 +209,8 @@ double hms_problem_setup_ms(const hms_problem* pr);
  * or the autotuned choice). */
 int32_t hms_problem_relax_threads(const hms_problem* pr);
 int32_t hms_problem_relax_copies(const hms_problem* pr);
+/* 1 if the relaxation of pr runs on the balanced schedule (relax_balance). */
+int32_t hms_problem_relax_balanced(const hms_problem* pr);
 
 /* The whole iteration (Fig. 3) for nrhs load vectors, each from u0 (NULL =
  * zero): loads [nrhs][2*nx*ny], u0 and u_out likewise.  hist (nullable)

@@ -57,7 +57,7 @@ class Options(ctypes.Structure):
                 ("coarse_factor", ctypes.c_int32), ("relax_threads", ctypes.c_int32),
                 ("relax_copies", ctypes.c_int32), ("relax_overlap", ctypes.c_int32),
                 ("mode_mask", ctypes.c_uint32), ("record_history", ctypes.c_int32),
-                ("class_factors", ctypes.c_int32)]
+                ("class_factors", ctypes.c_int32), ("relax_balance", ctypes.c_int32)]
 
 
 _lib = None
@@ -89,6 +89,7 @@ def lib():
         "hms_problem_setup_ms": (ctypes.c_double, [_P]),
         "hms_problem_relax_threads": (ctypes.c_int32, [_P]),
         "hms_problem_relax_copies": (ctypes.c_int32, [_P]),
+        "hms_problem_relax_balanced": (ctypes.c_int32, [_P]),
         "hms_solve": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, ctypes.c_int32]),
         "hms_kernel_times": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
         "hms_residual": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32]),
@@ -131,7 +132,7 @@ def exported_symbols():
             "hms_server_destroy", "hms_server_submit", "hms_server_step", "hms_server_take", "hms_problem_clone",
             "hms_problem_relax_threads", "hms_context_set_batch_mode", "hms_problem_relax_copies",
             "hms_reactions", "hms_problem_refine_cap_hits", "hms_problem_set_relax_wait_limit",
-            "hms_measure_fp64_rate", "hms_relax_force"]
+            "hms_measure_fp64_rate", "hms_relax_force", "hms_problem_relax_balanced"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -202,7 +203,8 @@ def hms_last_error(ctx) -> str:
 
 def _desc_opts(nx, ny, set_sx, set_sy, bar_length=1.0, ea=None, ea_uniform=1.0, fixed=None, fix_bottom_edge=1,
                precision=HMS_FP64, tol=1e-8, max_iter=1000, coarse_solves=0, batch=0, profile=0, coarse_factor=0,
-               relax_threads=0, relax_copies=0, relax_overlap=0, mode_mask=0x1FF, record_history=1, class_factors=0):
+               relax_threads=0, relax_copies=0, relax_overlap=0, mode_mask=0x1FF, record_history=1, class_factors=0,
+               relax_balance=0):
     """LatticeDesc and Options structs (plus the arrays they point to, kept alive by the caller)."""
     ea_a = None if ea is None else np.ascontiguousarray(ea, dtype=np.float64)
     fx_a = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
@@ -215,7 +217,7 @@ def _desc_opts(nx, ny, set_sx, set_sy, bar_length=1.0, ea=None, ea_uniform=1.0, 
                     int(set_sx), int(set_sy))
     o = Options(int(precision), float(tol), int(max_iter), int(coarse_solves), int(batch), int(profile),
                 int(coarse_factor), int(relax_threads), int(relax_copies), int(relax_overlap), int(mode_mask),
-                int(record_history), int(class_factors))
+                int(record_history), int(class_factors), int(relax_balance))
     return d, o, (ea_a, fx_a)
 
 
@@ -223,7 +225,7 @@ def hms_problem_create(ctx, nx, ny, set_sx, set_sy, **kw):
     """kw: bar_length, ea (host float64 [3, ny, nx]), ea_uniform, fixed (host uint8
     [ny, nx, 2]), fix_bottom_edge, precision, tol, max_iter, coarse_solves, batch,
     profile, coarse_factor, relax_threads, relax_copies, relax_overlap, mode_mask,
-    record_history, class_factors."""
+    record_history, class_factors, relax_balance."""
     d, o, keep = _desc_opts(nx, ny, set_sx, set_sy, **kw)
     h = _P()
     _check(ctx, lib().hms_problem_create(ctx, ctypes.byref(d), ctypes.byref(o), ctypes.byref(h)))
@@ -259,6 +261,10 @@ def hms_problem_relax_threads(pr) -> int:
 
 def hms_problem_relax_copies(pr) -> int:
     return int(lib().hms_problem_relax_copies(pr))
+
+
+def hms_problem_relax_balanced(pr) -> int:
+    return int(lib().hms_problem_relax_balanced(pr))
 
 
 def hms_solve(ctx, pr, loads, u_out, u0=None, hist=None, iters=None, allow_no_convergence=False):

@@ -23,8 +23,9 @@ struct hms_context {
   cudaStream_t stream = nullptr;
   std::vector<cudaStream_t> pool;  // streams of hms_solve_batch, created on first use
   std::string err;
-  // relaxation CTA size picked by timing, per (set width, set height, precision)
-  std::map<std::tuple<int, int, int, int>, int> relax_tuned;  // (set w, set h, precision, copies, overlap)
+  // relaxation launch shape picked by timing, per (set width, set height,
+  // precision and copies, overlap, set count where the balanced schedule applies)
+  std::map<std::tuple<int, int, int, int, int>, int> relax_tuned;
   int batch_mode = HMS_BATCH_AUTO;
 };
 
@@ -49,6 +50,12 @@ struct hms_problem {
   double tol = 1e-8;
   int relax_threads = 256;   // CTA size of the relaxation
   int relax_chunks = 1;      // bulk copies per factor matrix in the relaxation (2: half the shared memory)
+  // the relaxation on a balanced schedule (one persistent CTA per SM; relax.cu)
+  bool relax_sched = false;
+  int sched_grid = 0;
+  RelaxSeg* sched_segs = nullptr;
+  int* sched_cta = nullptr;
+  int* sched_flags = nullptr;  // per set; per instance, as clones run at the same time
   int n_c = 0, bw = 0;
   size_t bytes = 0;
   std::vector<void*> allocs;
@@ -230,6 +237,10 @@ cudaError_t launch_relax_main(hms_problem* pr, cudaStream_t s, const IterCtl* ct
   if (pr->cls)
     return launch_relax_class(s, pr->lv, pr->cpd, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, ctl,
                               pr->err, pr->relax_wait0);
+  if (pr->relax_sched)
+    return launch_relax_sched(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, ctl,
+                              pr->err, pr->sched_segs, pr->sched_cta, pr->sched_flags, pr->sched_grid,
+                              pr->relax_wait0);
   return launch_relax(s, pr->lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, ctl, pr->err,
                       pr->relax_threads, pr->relax_chunks, pr->relax_wait0);
 }
@@ -345,8 +356,12 @@ hms_status check_dev_err(hms_problem* pr) {
   CKC(pr->ctx, cudaMemcpyAsync(&herr, pr->err, sizeof(int), cudaMemcpyDeviceToHost, pr->ctx->stream));
   CKC(pr->ctx, cudaStreamSynchronize(pr->ctx->stream));
   if (herr) {
-    // reported once: the next call starts from a clear flag
+    // reported once: the next call starts from a clear flag, and from clear
+    // set flags of the balanced relaxation (an aborted launch may leave a
+    // head's flag raised with its tail never run)
     CKC(pr->ctx, cudaMemsetAsync(pr->err, 0, sizeof(int), pr->ctx->stream));
+    if (pr->sched_flags)
+      CKC(pr->ctx, cudaMemsetAsync(pr->sched_flags, 0, (size_t)pr->lv.M * sizeof(int), pr->ctx->stream));
     CKC(pr->ctx, cudaStreamSynchronize(pr->ctx->stream));
   }
   if (herr & DEVERR_NOT_SPD) return fail(pr->ctx, HMS_ERR_NOT_SPD, "non-positive pivot in a local factorisation");
@@ -601,6 +616,7 @@ void hms_problem_destroy(hms_problem* pr) {
 }
 
 static cudaError_t alloc_instance(hms_problem* pr);
+static cudaError_t setup_relax_sched(hms_problem* pr, bool* ok);
 
 hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
   if (!src || !out) return HMS_ERR_ARG;
@@ -628,6 +644,7 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
   pr->cluster_factor = src->cluster_factor;
   pr->relax_threads = src->relax_threads;
   pr->relax_chunks = src->relax_chunks;
+  pr->relax_sched = src->relax_sched;
   pr->two_sided = src->two_sided;
   pr->nd = src->nd;
   pr->ndp = src->ndp;
@@ -650,6 +667,11 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
   pr->Mforce = src->Mforce;
   pr->slots_base = src->slots_base;
   cudaError_t e = alloc_instance(pr);
+  if (e == cudaSuccess && pr->relax_sched) {
+    bool ok = false;  // the clone's own flags (same plan)
+    e = setup_relax_sched(pr, &ok);
+    if (e == cudaSuccess && !ok) e = cudaErrorInvalidValue;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     const hms_status st = fail(c, e == cudaErrorMemoryAllocation ? HMS_ERR_OOM : HMS_ERR_CUDA,
@@ -671,6 +693,7 @@ hms_status hms_problem_clone(hms_problem* src, hms_problem** out) {
 size_t hms_problem_device_bytes(const hms_problem* pr) { return pr ? pr->bytes : 0; }
 int32_t hms_problem_relax_threads(const hms_problem* pr) { return pr ? pr->relax_threads : 0; }
 int32_t hms_problem_relax_copies(const hms_problem* pr) { return pr ? pr->relax_chunks : 0; }
+int32_t hms_problem_relax_balanced(const hms_problem* pr) { return pr && pr->relax_sched ? 1 : 0; }
 double hms_problem_setup_ms(const hms_problem* pr) { return pr ? (double)pr->setup_ms : 0.0; }
 
 // The per-instance buffers of a problem whose configuration (lv, n_c, bw,
@@ -804,21 +827,61 @@ static cudaError_t alloc_instance(hms_problem* pr) {
   return cudaSuccess;
 }
 
-// Relaxation CTA size by timing: the first problem of a (set width, set
+// The balanced relaxation schedule for this problem (relax.cu): the plan, its
+// device copy and the per-set flags (per instance: clones run at the same
+// time).  *ok = false where the schedule does not apply.
+static cudaError_t setup_relax_sched(hms_problem* pr, bool* ok) {
+  *ok = false;
+  if (pr->cls) return cudaSuccess;
+  int grid = 0;
+  cudaError_t e = relax_sched_grid(pr->lv, fp32(pr), &grid);
+  if (e != cudaSuccess || grid == 0) return e;
+  std::vector<RelaxSeg> segs;
+  std::vector<int> cta;
+  if (!relax_sched_plan(pr->lv, grid, segs, cta)) return cudaSuccess;
+  cudaStream_t s = pr->ctx->stream;
+  if (!pr->sched_segs) {
+    if ((e = palloc(pr, &pr->sched_segs, segs.size())) != cudaSuccess) return e;
+    if ((e = palloc(pr, &pr->sched_cta, cta.size())) != cudaSuccess) return e;
+    if ((e = palloc(pr, &pr->sched_flags, (size_t)pr->lv.M)) != cudaSuccess) return e;
+  }
+  if ((e = cudaMemcpyAsync(pr->sched_segs, segs.data(), segs.size() * sizeof(RelaxSeg), cudaMemcpyHostToDevice,
+                           s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(pr->sched_cta, cta.data(), cta.size() * sizeof(int), cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(pr->sched_flags, 0, (size_t)pr->lv.M * sizeof(int), s)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;  // the host vectors go out of scope
+  pr->sched_grid = grid;
+  *ok = true;
+  return cudaSuccess;
+}
+
+// Relaxation launch shape by timing: the first problem of a (set width, set
 // height, precision) on a context times one warm-up and three timed launches
-// of each size on its own factors (r = 0; the kernel's time does not depend
-// on the values) and the context keeps the fastest for that shape.  The sizes
+// of each CTA size, copies per matrix and, where it applies, the balanced
+// schedule on its own factors (r = 0; the kernel's time does not depend on the
+// values) and the context keeps the fastest for that shape.  All candidates
 // give bitwise the same results, so the choice only changes the time.
-static cudaError_t autotune_relax(hms_problem* pr, int copies) {
+static cudaError_t autotune_relax(hms_problem* pr, int copies, bool try_sched) {
   hms_context* c = pr->ctx;
   const LatView& lv = pr->lv;
+  bool sched_ok = false;
+  if (try_sched && (copies == 0 || copies == 1)) {
+    cudaError_t e = setup_relax_sched(pr, &sched_ok);
+    if (e != cudaSuccess) return e;
+  }
   // the relaxation region's overlap changes the factors' shapes and rules out
-  // two copies per matrix, so it is part of the key
-  const auto key = std::make_tuple(std::min(lv.sx, lv.nx), std::min(lv.sy, lv.ny), pr->precision * 10 + copies, lv.ov);
+  // two copies per matrix, so it is part of the key; so is the set count
+  // where the balanced schedule applies (its gain depends on it)
+  const auto key = std::make_tuple(std::min(lv.sx, lv.nx), std::min(lv.sy, lv.ny), pr->precision * 10 + copies,
+                                   lv.ov, sched_ok ? lv.M : 0);
   const auto it = c->relax_tuned.find(key);
   if (it != c->relax_tuned.end()) {
-    pr->relax_threads = it->second / 10;
+    pr->relax_threads = (it->second % 10000) / 10;
     pr->relax_chunks = it->second % 10;
+    pr->relax_sched = it->second >= 10000;
     return cudaSuccess;
   }
   cudaStream_t s = c->stream;
@@ -832,12 +895,17 @@ static cudaError_t autotune_relax(hms_problem* pr, int copies) {
   }
   // candidates, each timed in two rounds (the smaller time counts) after a
   // warm-up, so that clocks ramping up from idle do not favour later ones
+  // (threads, copies); copies 0 = the balanced schedule (256 threads, one copy)
   std::vector<std::pair<int, int>> cand;
   const int max_nc = copies != 0 ? copies : (relax_chunks_possible(lv, fp32(pr)) ? 2 : 1);
   for (int nc = copies != 0 ? copies : 1; nc <= max_nc; ++nc)
     for (int nt : {64, 128, 256}) cand.push_back({nt, nc});
+  if (sched_ok) cand.push_back({256, 0});
   std::vector<float> tbest(cand.size(), 1e30f);
   auto run = [&](int nt, int nc) {
+    if (nc == 0)
+      return launch_relax_sched(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch,
+                                nullptr, pr->err, pr->sched_segs, pr->sched_cta, pr->sched_flags, pr->sched_grid);
     return launch_relax(s, lv, pr->set_off, pr->f64, pr->f32, pr->r, pr->delta, pr->P, pr->yscratch, nullptr,
                         pr->err, nt, nc);
   };
@@ -861,8 +929,9 @@ static cudaError_t autotune_relax(hms_problem* pr, int copies) {
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return e;
   pr->relax_threads = best_nt;
-  pr->relax_chunks = best_nc;
-  c->relax_tuned[key] = best_nt * 10 + best_nc;
+  pr->relax_chunks = best_nc == 0 ? 1 : best_nc;
+  pr->relax_sched = best_nc == 0;
+  c->relax_tuned[key] = (pr->relax_sched ? 10000 : 0) + best_nt * 10 + pr->relax_chunks;
   return cudaSuccess;
 }
 
@@ -882,6 +951,10 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (o->relax_threads != 0 && o->relax_threads != 64 && o->relax_threads != 128 && o->relax_threads != 256)
     return fail(c, HMS_ERR_ARG, "relax_threads must be 0, 64, 128 or 256");
   if (o->relax_copies < 0 || o->relax_copies > 2) return fail(c, HMS_ERR_ARG, "relax_copies must be 0, 1 or 2");
+  if (o->relax_balance < 0 || o->relax_balance > 2) return fail(c, HMS_ERR_ARG, "relax_balance must be 0, 1 or 2");
+  if (o->relax_balance == 2 && ((o->relax_threads != 0 && o->relax_threads != 256) || o->relax_copies == 2 ||
+                                o->relax_overlap != 0 || o->class_factors != 0))
+    return fail(c, HMS_ERR_ARG, "relax_balance = 2 runs 256 threads, one copy per matrix, no overlap, per-set factors");
   // the region width in 64 bits: set_sx + 2 relax_overlap may exceed INT_MAX
   const long long rw = std::min((long long)d->nx, (long long)d->set_sx + 2LL * (long long)o->relax_overlap);
   if (o->relax_overlap < 0 || rw > MAX_RX)
@@ -1145,6 +1218,17 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
   if (pr->cls) {
     pr->relax_threads = 256;  // the class-factor kernel's fixed shape
     pr->relax_chunks = 1;
+  } else if (o->relax_balance == 2) {
+    bool ok = false;
+    CKP(setup_relax_sched(pr, &ok));
+    if (!ok) {
+      hms_problem_destroy(pr);
+      return fail(c, HMS_ERR_ARG, "relax_balance = 2: the balanced schedule does not apply (more sets than SMs, "
+                                  "none costing more than an SM's share)");
+    }
+    pr->relax_sched = true;
+    pr->relax_threads = 256;
+    pr->relax_chunks = 1;
   } else if (o->relax_threads != 0 && o->relax_copies != 0) {
     pr->relax_threads = o->relax_threads;
     pr->relax_chunks = o->relax_copies;
@@ -1152,10 +1236,16 @@ hms_status hms_problem_create(hms_context* c, const hms_lattice_desc* d, const h
     pr->relax_threads = o->relax_threads;
     pr->relax_chunks = 1;
   } else {
-    CKP(autotune_relax(pr, o->relax_copies));
+    CKP(autotune_relax(pr, o->relax_copies, o->relax_balance == 0));
   }
   if (!pr->profile) {
     hms_status st = build_graph(pr);
+    if (st != HMS_OK && pr->relax_sched && o->relax_balance == 0) {
+      // a cooperative launch the graph would not take: one CTA per set
+      cudaGetLastError();
+      pr->relax_sched = false;
+      st = build_graph(pr);
+    }
     if (st != HMS_OK) {
       hms_problem_destroy(pr);
       return st;
@@ -1961,6 +2051,7 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
   if (o->precision == HMS_FP64 && rw > MAX_SX) return false;
   if ((o->mode_mask >> NMODES_RF) != 0u || (o->record_history != 0 && o->record_history != 1)) return false;
   if (o->class_factors != 0 && o->class_factors != 1) return false;
+  if (o->relax_balance < 0 || o->relax_balance > 2) return false;
   const bool force = (o->mode_mask >> NMODES) != 0u;
   if (o->class_factors && (d->ea || o->relax_overlap != 0 || force)) return false;
   if (force) {
@@ -2034,6 +2125,8 @@ bool estimate_parts(hms_context* c, const hms_lattice_desc* d, const hms_options
     }
   b += n_c * 4 + 32 + (size_t)std::max(update_residual_blocks(lv), 1024) * 3 * 8 + 4 + sizeof(IterCtl) + 4 + 32;
   if (o->record_history) b += 3 * ((size_t)o->max_iter + 1) * 8;
+  if (!o->class_factors && o->relax_overlap == 0 && o->relax_balance != 1 && lv.M > c->nsm)
+    b += ((size_t)lv.M + 2 * c->nsm) * sizeof(RelaxSeg) + ((size_t)c->nsm + 1) * 4 + (size_t)lv.M * 4;  // schedule
   *inst = b;
   *scratch = (size_t)std::max(1, std::min(lv.M, c->nsm)) * b_size(MAX_NB) * 8 + setup_bytes;
   return true;

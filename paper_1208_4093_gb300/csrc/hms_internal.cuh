@@ -269,6 +269,26 @@ cudaError_t launch_relax_class(cudaStream_t s, const LatView& lv, const ClassPla
 cudaError_t configure_relax_class(int max_smem);
 bool relax_chunks_possible(const LatView& lv, bool fp32);
 long long relax_y_stride(const LatView& lv);
+// The relaxation on a balanced schedule (relax.cu): one persistent CTA per SM,
+// each running an equal share of all sets' substitution steps.  Segment =
+// ops [o0, o1) of set I (op o: matrix o of the forward pass, o < 2h - 1, then
+// the backward pass's matrices in reverse).  cta[g] .. cta[g + 1] - 1 index
+// CTA g's segments in the order it runs them.
+struct RelaxSeg {
+  int I, o0, o1, pad;
+};
+// Plans the schedule over `grid` CTAs; false where it does not apply (an
+// extended relaxation region, no more sets than CTAs, or a set costing more
+// than one CTA's share).  est_balance (optional): the busiest CTA's cost over
+// the mean, and the same for one CTA per set in waves of `grid`.
+bool relax_sched_plan(const LatView& lv, int grid, std::vector<RelaxSeg>& segs, std::vector<int>& cta,
+                      double* est_sched = nullptr, double* est_waves = nullptr);
+// CTAs of the balanced relaxation on this device (SMs x resident CTAs, 0 if none fits).
+cudaError_t relax_sched_grid(const LatView& lv, bool fp32, int* grid);
+cudaError_t launch_relax_sched(cudaStream_t s, const LatView& lv, const long long* set_off, const double* f64,
+                               const float* f32, const double2* r, void* delta, double* P, void* yscratch,
+                               const IterCtl* ctl, int* err, const RelaxSeg* segs, const int* cta, int* flags,
+                               int grid, int wait0 = -1);
 // coarse.cu
 cudaError_t launch_coarse_slots(cudaStream_t s, const LatView& lv, const void* delta, bool delta_fp32,
                                 bool full, double* slots, const IterCtl* ctl, const void* delta_rf = nullptr);

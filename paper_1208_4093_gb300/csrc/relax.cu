@@ -43,6 +43,8 @@
 // whatever NT and NC are (the P sums over 256 virtual lanes), so the results
 // are bitwise the same for every choice, and the problem setup may pick them
 // by timing (relax_threads = 0).
+#include <algorithm>
+#include <cmath>
 #include <type_traits>
 
 #include "hms_internal.cuh"
@@ -546,6 +548,289 @@ __global__ void __launch_bounds__(NT + 32) kb_relax(const BatchProb* __restrict_
                         q.err, it.bx, -1);
 }
 
+// ---------------------------------------------------------------------------
+// The same relaxation on a balanced schedule.  One CTA per set leaves the last
+// wave partly idle when the set count is not a multiple of the SM count (256
+// sets of 64 x 64 nodes on 152 SMs: two waves, the second on 104 SMs, so the
+// SMs are busy 84 % of the kernel's time).  Here one persistent CTA per SM runs
+// an equal share of the whole job: the sets' op sequences, laid end to end
+// and weighted by their matrix entries, are cut into `grid` equal parts, each
+// cut moved to the nearest step boundary after a Linv_j (forward) or Linv_j^T
+// (backward) product, where the substitution's state is in global memory
+// (y_j in the y scratch, x_j in delta).  A set cut between CTAs g-1 and g has
+// its first part (the head) run FIRST by CTA g-1 and its second part (the
+// tail) run LAST by CTA g: McNaughton's wrap-around rule, with each CTA
+// running head, whole sets, tail.  With every set's cost C at most the share
+// T, the head ends at a and the tail starts at T - b >= a (a + b = C), so in a
+// balanced run the tail never waits.  The head's CTA releases a per-set flag
+// once its part is written; the tail's CTA acquires it (bounded wait) before
+// reading the state, and resets it when the set is done.  The CTAs are
+// co-resident (cooperative launch) and every head is its CTA's first segment,
+// which waits for nothing, so every wait ends.  Each op's arithmetic and the
+// P sums are those of relax_body with one copy per matrix, so the results are
+// bitwise the same as k_relax's.
+
+__device__ inline int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ inline void st_release_gpu(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Bounded wait (about a second) for a set's flag; false if it gave up.
+__device__ inline bool set_flag_wait(const int* p) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (ld_acquire_gpu(p) != 0) return true;
+    __nanosleep(256);
+  }
+  return false;
+}
+
+template <typename T>
+struct SetGeo {
+  int I, i0, j0, w, h, nb, nbr, nmat, nops;
+  const T* f;   // the factor stored by rows
+  const T* ft;  // the copy stored by columns
+  T* yg;        // the set's y scratch
+};
+template <typename T>
+__device__ inline SetGeo<T> set_geo(const LatView& lv, const long long* set_off, const T* fac, T* yglob,
+                                    long long ystride, int I) {
+  SetGeo<T> G;
+  G.I = I;
+  G.i0 = (I % lv.Mx) * lv.sx;
+  G.j0 = (I / lv.Mx) * lv.sy;
+  G.w = min(lv.sx, lv.nx - G.i0);
+  G.h = min(lv.sy, lv.ny - G.j0);
+  G.nb = 2 * G.w;
+  G.nbr = y_row(G.nb);
+  G.nmat = 2 * G.h - 1;
+  G.nops = 2 * G.nmat;
+  G.f = fac + set_off[I];
+  G.ft = G.f + set_factor_size(G.nb, G.h);
+  G.yg = yglob + (size_t)I * ystride;
+  return G;
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT + 32, 1)
+    k_relax_sched(const LatView lv, const long long* __restrict__ set_off, const T* __restrict__ fac,
+                  const double2* __restrict__ r, T* __restrict__ delta, double* __restrict__ P,
+                  T* __restrict__ yglob, long long ystride, const IterCtl* ctl, int* err,
+                  const RelaxSeg* __restrict__ segs, const int* __restrict__ cta_seg, int* flags, int wait0) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint64_t bars[NSLOT];
+  __shared__ double pred[(VL / 32) * NMODES];
+  if (ctl && *(volatile const int*)&ctl->done) return;
+
+  using T2 = typename Vec2<T>::type;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const bool producer = tid >= NT;
+  const int sg0 = cta_seg[blockIdx.x], sg1 = cta_seg[blockIdx.x + 1];
+  if (sg0 >= sg1) return;
+  // one slot layout for every set: that of the widest
+  const RelaxSmem LY = relax_layout<T, 1>(2 * min(lv.sx, lv.nx));
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* ycur = sm + LY.ycur_off;
+  T* zbuf = sm + LY.z_off;
+  T* wbuf = sm + LY.w_off;
+  T* xbuf = sm + LY.x_off;
+  const double* rg = reinterpret_cast<const double*>(r);
+
+  // ---- the producer's cursor over this CTA's ops (thread NT only) ----
+  int total = 0, issued = 0, psg = sg0, po = 0;
+  bool pfail = false;
+  SetGeo<T> PG{};
+  auto enter = [&](int sg) {
+    // a tail's copies (y rows of the backward pass) read what the head's CTA wrote
+    PG = set_geo<T>(lv, set_off, fac, yglob, ystride, segs[sg].I);
+    po = segs[sg].o0;
+    if (po > 0) {
+      if (!set_flag_wait(&flags[PG.I])) pfail = true;
+      fence_proxy_async_global();
+    }
+  };
+  auto issue_next = [&]() {
+    const int o = po, slot = issued % NSLOT;
+    const int k = o < PG.nmat ? o : 2 * PG.nmat - 1 - o;
+    const bool fwd = o < PG.nmat;
+    const int kind = (k & 1) ? (fwd ? 1 : 3) : (fwd ? 0 : 2);
+    uint64_t* bar = &bars[slot];
+    const T* src = (fwd ? PG.f : PG.ft) + mat_off(PG.nb, k);
+    T* dst = sm + (size_t)slot * LY.slot_elems;
+    const int jv = (k + 1) / 2;
+    const void* vsrc = fwd ? (const void*)(rg + 2 * ((size_t)(PG.j0 + jv) * lv.nx + PG.i0))
+                           : (const void*)(PG.yg + (size_t)(jv - 1) * PG.nbr);
+    const uint32_t vbytes = (k & 1) ? (uint32_t)(fwd ? PG.nb * sizeof(double) : PG.nbr * sizeof(T)) : 0u;
+    T* vdst = sm + LY.vec_off + (size_t)slot * LY.vec_elems;
+    fence_proxy_async_smem();
+    if (!fwd && (k & 1)) fence_proxy_async_global();
+    const uint32_t bytes = (uint32_t)(kind_size(kind, PG.nb) * sizeof(T));
+    mbar_arrive_expect_tx(bar, bytes + vbytes);
+    bulk_g2s(dst, src, bytes, bar);
+    if (vbytes) bulk_g2s(vdst, vsrc, vbytes, bar);
+    ++issued;
+    if (++po == segs[psg].o1 && ++psg < sg1) enter(psg);
+  };
+
+  if (tid == 0) {
+    for (int k = 0; k < NSLOT; ++k) mbar_init(&bars[k], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == NT) {
+    for (int sg = sg0; sg < sg1; ++sg) total += segs[sg].o1 - segs[sg].o0;
+    enter(sg0);
+    for (int k = 0; k < NSLOT - 1 && issued < total && !pfail; ++k) issue_next();
+  }
+
+  int gop = 0;  // ops of this CTA consumed so far (slot gop % NSLOT)
+  bool aborted = false;
+  for (int sg = sg0; sg < sg1; ++sg) {
+    const RelaxSeg S = segs[sg];
+    const SetGeo<T> G = set_geo<T>(lv, set_off, fac, yglob, ystride, S.I);
+    // ---- the state the segment starts from ----
+    bool bad = tid == NT && pfail;
+    if (S.o0 > 0 && tid == 0) bad = !set_flag_wait(&flags[S.I]);
+    if (__syncthreads_or(bad)) {
+      aborted = true;
+      break;
+    }
+    if (!producer) {
+      if (S.o0 == 0) {
+        const size_t rowbase0 = 2 * ((size_t)G.j0 * lv.nx + G.i0);  // z = r_0
+        for (int t = tid; t < G.nb; t += NT) zbuf[t] = (T)rg[rowbase0 + t];
+      } else if (S.o0 <= G.nmat) {
+        const T* ys = G.yg + (size_t)((S.o0 - 1) / 2) * G.nbr;  // y_j after Linv_j
+        for (int t = tid; t < G.nb; t += NT) ycur[t] = __ldcg(ys + t);
+      } else {
+        const int j = (2 * G.nmat - S.o0) / 2;  // x_j after Linv_j^T, in delta
+        const T* xs = delta + 2 * ((size_t)(G.j0 + j) * lv.nx + G.i0);
+        for (int t = tid; t < G.nb; t += NT) xbuf[t] = __ldcg(xs + t);
+      }
+    }
+    __syncthreads();
+    const int nb = G.nb, pb = nb / 2;
+    for (int o = S.o0; o < S.o1; ++o, ++gop) {
+      const uint32_t tries = (gop == 0 && wait0 >= 0) ? (uint32_t)wait0 : MBAR_WAIT_TRIES;
+      const bool late = !producer && !mbar_wait_bounded(&bars[gop % NSLOT], (uint32_t)((gop / NSLOT) & 1), tries);
+      if (producer) {
+        // the slot of op gop - 1 is free since the barrier that ended it
+        if (tid == NT && issued < total && !pfail) issue_next();
+        if (__syncthreads_or(tid == NT && pfail)) {
+          aborted = true;
+          break;
+        }
+        continue;
+      }
+      const T* M = sm + (size_t)(gop % NSLOT) * LY.slot_elems;
+      const T* vstage = sm + LY.vec_off + (size_t)(gop % NSLOT) * LY.vec_elems;
+      const int k = o < G.nmat ? o : 2 * G.nmat - 1 - o;
+      const bool is_b = (k & 1) != 0;
+      const int j = is_b ? (k + 1) / 2 : k / 2;
+      constexpr int GR = 4, CH = sizeof(T) == 8 ? 1 : 2;
+      if (o < G.nmat) {
+        if (is_b) {
+          const double* rj = reinterpret_cast<const double*>(vstage);
+          rows_times<NT, T, GR, CH, ROW_B>(
+              M, ycur, nb, 0, pb, 0, nb, 0, [&](int row) { return (T)rj[row]; },
+              [&](int row, T s, T pre) { zbuf[row] = pre - s; });
+        } else {
+          T* yj = G.yg + (size_t)j * G.nbr;
+          rows_times<NT, T, GR, CH, ROW_LINV>(
+              M, zbuf, nb, 0, pb, 0, nb, 0, [](int) { return T(0); },
+              [&](int row, T s, T) {
+                ycur[row] = s;
+                yj[row] = s;
+              });
+        }
+      } else {
+        if (!is_b) {
+          const T* wv = (j == G.h - 1) ? ycur : wbuf;
+          T* drow = delta + 2 * ((size_t)(G.j0 + j) * lv.nx + G.i0);
+          rows_times<NT, T, GR, CH, ROW_LT>(
+              M, wv, nb, 0, pb, 0, nb, 0, [](int) { return T(0); },
+              [&](int row, T s, T) {
+                xbuf[row] = s;
+                drow[row] = s;
+              });
+        } else {
+          const T* yp = vstage;
+          rows_times<NT, T, GR, CH, ROW_BT>(
+              M, xbuf, nb, 0, pb, 0, nb, 0, [&](int row) { return yp[row]; },
+              [&](int row, T s, T pre) { wbuf[row] = pre - s; });
+        }
+      }
+      if (__syncthreads_or(late)) {
+        aborted = true;
+        break;
+      }
+    }
+    if (aborted) break;
+    if (S.o1 < G.nops) {
+      // head done: its y rows and delta rows (ordered by the barrier above) go
+      // out before the flag
+      if (tid == 0) {
+        __threadfence();
+        st_release_gpu(&flags[S.I], 1);
+      }
+      continue;
+    }
+    if (S.o0 > 0 && tid == 0) flags[S.I] = 0;  // both waits on it are past
+    if (P == nullptr) continue;
+    // P = V^T r (Eq. 7), as in relax_body (delta partly written by another CTA: read from L2)
+    __syncthreads();
+    const double2 rep = lv.rep[S.I];
+    const T2* d2 = reinterpret_cast<const T2*>(delta);
+    const int w = G.w, h = G.h, i0 = G.i0, j0 = G.j0;
+    for (int vbase = 0; vbase < VL && !producer; vbase += NT) {
+      const int v = vbase + tid;
+      if (v >= VL) break;
+      double pacc[NMODES];
+#pragma unroll
+      for (int m = 0; m < NMODES; ++m) pacc[m] = 0.0;
+      for (int node = v; node < w * h; node += VL) {
+        const int jj = node / w, il = node - jj * w;
+        const int jn = j0 + jj;
+        const size_t nidx = (size_t)jn * lv.nx + i0 + il;
+        const double2 rv = r[nidx];
+        const T2 dv = __ldcg(d2 + nidx);
+        const double xi = fma(lv.L, (double)(i0 + il) + 0.5 * (double)(jn & 1), -rep.x);
+        const double eta = fma(lv.L * SQ3_2, (double)jn, -rep.y);
+        const double dr = fma((double)dv.x, rv.x, (double)dv.y * rv.y);
+        pacc[0] += rv.x;
+        pacc[1] += rv.y;
+        pacc[2] = fma(xi, rv.x, pacc[2]);
+        pacc[3] = fma(eta, rv.x, pacc[3]);
+        pacc[4] = fma(xi, rv.y, pacc[4]);
+        pacc[5] = fma(eta, rv.y, pacc[5]);
+        pacc[6] += dr;
+        pacc[7] = fma(xi, dr, pacc[7]);
+        pacc[8] = fma(eta, dr, pacc[8]);
+      }
+#pragma unroll
+      for (int m = 0; m < NMODES; ++m) {
+        const double sm2 = warp_sum_d(pacc[m]);
+        if (lane == 0) pred[(v >> 5) * NMODES + m] = sm2;
+      }
+    }
+    __syncthreads();
+    if (tid < NMODES) {
+      double sum = 0.0;
+      for (int ww = 0; ww < VL / 32; ++ww) sum += pred[ww * NMODES + tid];
+      P[(size_t)lv.q * S.I + tid] = sum;
+    }
+  }
+  if (aborted) {
+    // the copies still in flight (ops gop .. issued - 1) land before the CTA exits
+    if (tid == NT) {
+      for (int k = gop; k < issued; ++k) mbar_wait_bounded(&bars[k % NSLOT], (uint32_t)((k / NSLOT) & 1));
+      atomicOr(err, (int)DEVERR_TIMEOUT);
+    }
+  }
+}
+
 }  // namespace
 
 size_t relax_smem_bytes(const LatView& lv, bool fp32, int chunks) {
@@ -565,6 +850,137 @@ bool relax_chunks_possible(const LatView& lv, bool fp32) {
 }
 
 long long relax_y_stride(const LatView& lv) { return y_stride(lv); }
+
+// Cost of op o of a set (nb DOFs per row, nmat matrices per pass): its matrix
+// entries (one FMA each) plus a per-op share for the reduction and barrier.
+static double op_cost(int nb, int nmat, int o) {
+  const int k = o < nmat ? o : 2 * nmat - 1 - o;
+  const double e = (k & 1) ? (double)b_row_off(nb, nb) : (double)linv_row_off(nb);
+  return e + 8.0 * nb;
+}
+
+bool relax_sched_plan(const LatView& lv, int grid, std::vector<RelaxSeg>& segs, std::vector<int>& cta,
+                      double* est_sched, double* est_waves) {
+  segs.clear();
+  cta.clear();
+  if (lv.ov != 0 || grid < 2 || lv.M <= grid) return false;
+  // per set: the cost at each op boundary
+  std::vector<std::vector<double>> pre(lv.M);
+  std::vector<double> start(lv.M + 1, 0.0);
+  double cmax = 0.0;
+  for (int I = 0; I < lv.M; ++I) {
+    const int i0 = (I % lv.Mx) * lv.sx, j0 = (I / lv.Mx) * lv.sy;
+    const int w = std::min(lv.sx, lv.nx - i0), h = std::min(lv.sy, lv.ny - j0);
+    const int nb = 2 * w, nmat = 2 * h - 1, nops = 2 * nmat;
+    std::vector<double>& c = pre[I];
+    c.assign(nops + 1, 0.0);
+    for (int o = 0; o < nops; ++o) c[o + 1] = c[o] + op_cost(nb, nmat, o);
+    c[nops] += 12.0 * w * h;  // the P sums
+    start[I + 1] = start[I] + c[nops];
+    cmax = std::max(cmax, c[nops]);
+  }
+  const double total = start[lv.M], share = total / grid;
+  if (cmax > share) return false;
+  // set I: head [0, cut) on CTA hd[I], tail [cut, nops) on CTA hd[I] + 1;
+  // cut = nops: the whole set on hd[I]; cut = 0: the whole set on hd[I] + 1
+  std::vector<int> hd(lv.M), cut(lv.M);
+  for (int I = 0; I < lv.M; ++I) {
+    const std::vector<double>& c = pre[I];
+    const int nops = (int)c.size() - 1, nmat = nops / 2;
+    int g = (int)(start[I] / share);
+    g = std::min(g, grid - 1);
+    hd[I] = g;
+    cut[I] = nops;
+    const double x = (g + 1) * share;  // the next CTA's boundary
+    if (g + 1 < grid && x < start[I + 1]) {
+      // the valid cut (after a Linv_j or a Linv_j^T product) nearest to x
+      int best = 0;
+      double bd = std::fabs(start[I] - x);
+      for (int o = 1; o <= nops; ++o) {
+        const bool ok = o == nops || ((o & 1) && o <= nmat) || (!(o & 1) && o > nmat);
+        if (!ok) continue;
+        const double d = std::fabs(start[I] + c[o] - x);
+        if (d < bd) bd = d, best = o;
+      }
+      cut[I] = best;
+    }
+  }
+  // per CTA: the head it runs first, its whole sets, the tail it runs last
+  std::vector<std::vector<RelaxSeg>> head(grid), mid(grid), tail(grid);
+  for (int I = 0; I < lv.M; ++I) {
+    const int nops = (int)pre[I].size() - 1, g = hd[I];
+    if (cut[I] == nops) mid[g].push_back({I, 0, nops, 0});
+    else if (cut[I] == 0) mid[g + 1].push_back({I, 0, nops, 0});
+    else {
+      head[g].push_back({I, 0, cut[I], 0});
+      tail[g + 1].push_back({I, cut[I], nops, 0});
+    }
+  }
+  cta.push_back(0);
+  double busiest = 0.0;
+  for (int g = 0; g < grid; ++g) {
+    if (head[g].size() > 1 || tail[g].size() > 1) {
+      segs.clear();
+      cta.clear();
+      return false;
+    }
+    double cost = 0.0;
+    for (auto* v : {&head[g], &mid[g], &tail[g]})
+      for (const RelaxSeg& sg : *v) {
+        segs.push_back(sg);
+        cost += pre[sg.I][sg.o1] - pre[sg.I][sg.o0];
+      }
+    busiest = std::max(busiest, cost);
+    cta.push_back((int)segs.size());
+  }
+  if (est_sched) *est_sched = busiest / share;
+  if (est_waves) {
+    // one CTA per set in order, `grid` at a time: the busiest SM's cost
+    std::vector<double> load(grid, 0.0);
+    for (int I = 0; I < lv.M; ++I) load[I % grid] += start[I + 1] - start[I];
+    *est_waves = *std::max_element(load.begin(), load.end()) / share;
+  }
+  return true;
+}
+
+cudaError_t relax_sched_grid(const LatView& lv, bool fp32, int* grid) {
+  *grid = 0;
+  int dev = 0, nsm = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const size_t smem = relax_smem_bytes(lv, fp32, 1);
+  e = fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_relax_sched<float, 256>, 256 + 32, smem)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_relax_sched<double, 256>, 256 + 32, smem);
+  if (e != cudaSuccess) return e;
+  *grid = nsm * std::min(per, 1);
+  return cudaSuccess;
+}
+
+cudaError_t launch_relax_sched(cudaStream_t s, const LatView& lv, const long long* set_off, const double* f64,
+                               const float* f32, const double2* r, void* delta, double* P, void* yscratch,
+                               const IterCtl* ctl, int* err, const RelaxSeg* segs, const int* cta, int* flags,
+                               int grid, int wait0) {
+  const bool fp32 = (f32 != nullptr);
+  const size_t smem = relax_smem_bytes(lv, fp32, 1);
+  const long long ys = relax_y_stride(lv);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(256 + 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  // every CTA resident at once: a tail's CTA may wait for a head's
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (fp32)
+    return cudaLaunchKernelEx(&cfg, k_relax_sched<float, 256>, lv, set_off, f32, r, (float*)delta, P,
+                              (float*)yscratch, ys, ctl, err, segs, cta, flags, wait0);
+  return cudaLaunchKernelEx(&cfg, k_relax_sched<double, 256>, lv, set_off, f64, r, (double*)delta, P,
+                            (double*)yscratch, ys, ctl, err, segs, cta, flags, wait0);
+}
 
 template <int NC, class F>
 static cudaError_t dispatch_nt(int threads, F go) {
@@ -632,6 +1048,8 @@ cudaError_t configure_relax(int max_smem) {
   HMS_RELAX_ATTR((kb_relax<double, 64, 2>))
   HMS_RELAX_ATTR((kb_relax<double, 128, 2>))
   HMS_RELAX_ATTR((kb_relax<double, 256, 2>))
+  HMS_RELAX_ATTR((k_relax_sched<float, 256>))
+  HMS_RELAX_ATTR((k_relax_sched<double, 256>))
 #undef HMS_RELAX_ATTR
   return cudaSuccess;
 }
