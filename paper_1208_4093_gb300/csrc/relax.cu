@@ -165,15 +165,44 @@ __device__ inline void pair_dot(const T* __restrict__ pA, int loA, int lenA, con
     // FP64: one walk with the row chosen per entry.  Every lane of a warp then
     // runs the same number of FMAs (len is nearly the same for every pair),
     // which matters where a warp's FMA holds the FP64 pipe whatever its
-    // active lanes.
-    for (int t = g; t < len; t += G) {
-      const bool inA = t < lenA;
-      const T* mp = inA ? pA + t : pB + (t - lenA);
-      const T* vp = inA ? v + (loA + t) : v + (loB + t - lenA);
-      T c = inA ? a[0] : b[0];
-      c = fma(*mp, *vp, c);
-      if (inA) a[0] = c;
-      else b[0] = c;
+    // active lanes.  The walk keeps one running sum and, where its index
+    // passes lenA, moves that sum to row A's and starts row B's from zero (so
+    // no select sits between two FMAs of the chain); the next entry's two
+    // operands are loaded before this entry's FMA, so the shared-memory
+    // latency overlaps the chain.
+    if (g < len) {
+      bool inA = g < lenA;
+      const T* mb = inA ? pA : pB - lenA;  // entry t of the walk: mb[t] * xb[t]
+      const T* xb = inA ? v + loA : v + (loB - lenA);
+      T m = mb[g], x = xb[g];
+      T acc = T(0), accA = T(0);
+      for (int t = g; t < len; t += G) {
+        const int tn = t + G;
+        const bool cross = inA && tn >= lenA;  // entry tn is this thread's first of row B
+        if (cross) {
+          mb = pB - lenA;
+          xb = v + (loB - lenA);
+        }
+        T mn = T(0), xn = T(0);
+        if (tn < len) {
+          mn = mb[tn];
+          xn = xb[tn];
+        }
+        acc = fma(m, x, acc);
+        if (cross) {
+          accA = acc;
+          acc = T(0);
+          inA = false;
+        }
+        m = mn;
+        x = xn;
+      }
+      if (inA) {
+        a[0] = acc;
+      } else {
+        a[0] = accA;
+        b[0] = acc;
+      }
     }
   } else {
     // FP32: row A's part and row B's part as two plain loops (no per-entry
