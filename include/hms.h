@@ -211,6 +211,20 @@ int32_t hms_problem_relax_threads(const hms_problem* pr);
 int32_t hms_problem_relax_copies(const hms_problem* pr);
 /* 1 if the relaxation of pr runs on the balanced schedule (relax_balance). */
 int32_t hms_problem_relax_balanced(const hms_problem* pr);
+/* The balanced relaxation schedule (relax_balance) of a lattice's sets over
+ * `ctas` persistent CTAs (one per SM), computed on the host; no device is
+ * needed.  It is the plan hms_problem_create makes on a device with that many
+ * SMs for set tiles of set_sx x set_sy nodes (no overlap).  A set of h rows
+ * has 2(2h - 1) ops: op o < 2h - 1 applies matrix o of the forward
+ * substitution (Linv_0, B_1, Linv_1, ...), the rest the back substitution's
+ * matrices in reverse order.  Output, host memory: segs_out[3 k .. 3 k + 2] =
+ * (set index, first op, end op) of segment k; CTA g runs segments
+ * cta_out[g] .. cta_out[g + 1] - 1 in that order (cta_out: ctas + 1 int32).
+ * Returns the segment count, 0 if the schedule does not apply (no more sets
+ * than CTAs, or a set costing more than one CTA's share), -1 for bad
+ * arguments or cap (segments segs_out holds) too small. */
+int32_t hms_relax_schedule(int32_t nx, int32_t ny, int32_t set_sx, int32_t set_sy, int32_t ctas,
+                           int32_t* segs_out, int32_t cap, int32_t* cta_out);
 
 /* The whole iteration (Fig. 3) for nrhs load vectors, each from u0 (NULL =
  * zero): loads [nrhs][2*nx*ny], u0 and u_out likewise.  hist (nullable)

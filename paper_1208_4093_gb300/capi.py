@@ -90,6 +90,8 @@ def lib():
         "hms_problem_relax_threads": (ctypes.c_int32, [_P]),
         "hms_problem_relax_copies": (ctypes.c_int32, [_P]),
         "hms_problem_relax_balanced": (ctypes.c_int32, [_P]),
+        "hms_relax_schedule": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32, _P, ctypes.c_int32, _P]),
         "hms_solve": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, ctypes.c_int32]),
         "hms_kernel_times": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
         "hms_residual": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32]),
@@ -132,7 +134,7 @@ def exported_symbols():
             "hms_server_destroy", "hms_server_submit", "hms_server_step", "hms_server_take", "hms_problem_clone",
             "hms_problem_relax_threads", "hms_context_set_batch_mode", "hms_problem_relax_copies",
             "hms_reactions", "hms_problem_refine_cap_hits", "hms_problem_set_relax_wait_limit",
-            "hms_measure_fp64_rate", "hms_relax_force", "hms_problem_relax_balanced"]
+            "hms_measure_fp64_rate", "hms_relax_force", "hms_problem_relax_balanced", "hms_relax_schedule"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -265,6 +267,20 @@ def hms_problem_relax_copies(pr) -> int:
 
 def hms_problem_relax_balanced(pr) -> int:
     return int(lib().hms_problem_relax_balanced(pr))
+
+
+def hms_relax_schedule(nx, ny, set_sx, set_sy, ctas):
+    """The balanced relaxation schedule over `ctas` CTAs (host only): (segments
+    [k, 3] of (set, first op, end op), CTA offsets [ctas + 1]), or None where
+    it does not apply."""
+    cap = 4 * (-(-nx // set_sx)) * (-(-ny // set_sy)) + 2 * ctas + 4
+    segs = np.zeros((cap, 3), np.int32)
+    cta = np.zeros(ctas + 1, np.int32)
+    n = lib().hms_relax_schedule(int(nx), int(ny), int(set_sx), int(set_sy), int(ctas), segs.ctypes.data, cap,
+                                 cta.ctypes.data)
+    if n < 0:
+        raise HmsError(HMS_ERR_ARG, "hms_relax_schedule: bad arguments")
+    return None if n == 0 else (segs[:n].copy(), cta)
 
 
 def hms_solve(ctx, pr, loads, u_out, u0=None, hist=None, iters=None, allow_no_convergence=False):

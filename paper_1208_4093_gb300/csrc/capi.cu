@@ -694,6 +694,33 @@ size_t hms_problem_device_bytes(const hms_problem* pr) { return pr ? pr->bytes :
 int32_t hms_problem_relax_threads(const hms_problem* pr) { return pr ? pr->relax_threads : 0; }
 int32_t hms_problem_relax_copies(const hms_problem* pr) { return pr ? pr->relax_chunks : 0; }
 int32_t hms_problem_relax_balanced(const hms_problem* pr) { return pr && pr->relax_sched ? 1 : 0; }
+
+int32_t hms_relax_schedule(int32_t nx, int32_t ny, int32_t set_sx, int32_t set_sy, int32_t ctas,
+                           int32_t* segs_out, int32_t cap, int32_t* cta_out) {
+  if (nx < 2 || ny < 2 || set_sx < 1 || set_sx > MAX_SX || set_sy < 1 || ctas < 1 || cap < 0 || !cta_out)
+    return -1;
+  LatView lv{};
+  lv.nx = nx;
+  lv.ny = ny;
+  lv.sx = set_sx;
+  lv.sy = set_sy;
+  lv.Mx = (nx + set_sx - 1) / set_sx;
+  lv.My = (ny + set_sy - 1) / set_sy;
+  if ((long long)lv.Mx * lv.My > (1LL << 30)) return -1;
+  lv.M = lv.Mx * lv.My;
+  lv.ov = 0;
+  std::vector<RelaxSeg> segs;
+  std::vector<int> cta;
+  if (!relax_sched_plan(lv, ctas, segs, cta)) return 0;
+  if ((long long)segs.size() > cap || !segs_out) return -1;
+  for (size_t k = 0; k < segs.size(); ++k) {
+    segs_out[3 * k] = segs[k].I;
+    segs_out[3 * k + 1] = segs[k].o0;
+    segs_out[3 * k + 2] = segs[k].o1;
+  }
+  for (size_t g = 0; g < cta.size(); ++g) cta_out[g] = cta[g];
+  return (int32_t)segs.size();
+}
 double hms_problem_setup_ms(const hms_problem* pr) { return pr ? (double)pr->setup_ms : 0.0; }
 
 // The per-instance buffers of a problem whose configuration (lv, n_c, bw,
