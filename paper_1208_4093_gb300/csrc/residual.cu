@@ -11,6 +11,19 @@
 // reduces the per-CTA sums in CTA order (deterministic), turns them into the
 // relative residuals of Eq. 19 and the energy Pi = 1/2 u.K.u - u.p =
 // -1/2 u.(p + r) of Eq. 2, and decides convergence.
+//
+// In the mixed form (FP32 delta) the increment V a of Eq. 3 is formed in FP32
+// and added to the FP64 u: the coefficients of the tile's sets are rounded to
+// FP32 once per CTA (with the set's representative point as an offset, so
+// that xi and eta are small numbers), and a staged node then costs 4 FP64
+// operations (two conversions, two adds) instead of about 17.  The increment
+// carries an FP32 rounding error of its own size times ~1e-7, like the FP32
+// relaxation's delta it multiplies; the residual that decides convergence
+// stays FP64, so the iteration still converges to the FP64 solution (later
+// updates correct what an update got wrong).  The FP64 form and the
+// force-controlled modes keep the FP64 increment.
+#include <type_traits>
+
 #include "hms_internal.cuh"
 
 namespace hms {
@@ -88,6 +101,32 @@ __device__ inline double2 apply_update(const LatView& lv, double2 v, int i, int 
   return v;
 }
 
+// FP32 increment of the mixed form: the sets a tile's staged nodes (the tile
+// and its one-node halo) can fall in, at most F32SETS of them.
+constexpr int F32SETS = 32;
+constexpr int F32STRIDE = 12;  // a_0 .. a_8, the offsets ox, oy, pad
+__host__ __device__ inline bool f32_increment_fits(int sx, int sy) {
+  // set columns a span of TX + 2 nodes can touch, times set rows of TY + 2
+  return ((TX + 2 + sx - 1) / sx + 1) * ((TY + 2 + sy - 1) / sy + 1) <= F32SETS;
+}
+
+// Eq. 3 at node (i, j) with the FP32 coefficients f of its set (origin i0s, j0s):
+// xi = L (i - i0s + (j odd ? 1/2 : 0)) + ox, eta = L sqrt3/2 (j - j0s) + oy
+// with ox = L i0s - x^(I), oy = L sqrt3/2 j0s - y^(I) rounded to FP32.
+__device__ inline double2 apply_update_f32(const LatView& lv, double2 v, int i, int j, int i0s, int j0s,
+                                           const float* f, const float2* delta) {
+  const size_t n = (size_t)j * lv.nx + i;
+  const float L = (float)lv.L;
+  const float xi = fmaf(L, (float)(i - i0s) + ((j & 1) ? 0.5f : 0.0f), f[9]);
+  const float eta = fmaf(L * (float)SQ3_2, (float)(j - j0s), f[10]);
+  const float2 d = delta[n];
+  const unsigned fm = lv.fix[n];
+  const float cd = fmaf(f[8], eta, fmaf(f[7], xi, f[6]));
+  if (!(fm & 1u)) v.x += (double)fmaf(cd, d.x, fmaf(f[3], eta, fmaf(f[2], xi, f[0])));
+  if (!(fm & 2u)) v.y += (double)fmaf(cd, d.y, fmaf(f[5], eta, fmaf(f[4], xi, f[1])));
+  return v;
+}
+
 // The kernel body for tile (bx, by) of a gx x gy grid (the whole lattice).
 template <typename DT, bool RF = false>
 __device__ __forceinline__ void update_residual_body(
@@ -108,13 +147,48 @@ __device__ __forceinline__ void update_residual_body(
   const int i0 = bx * TX, j0 = by * TY;
   const int tid = threadIdx.x;
 
+  constexpr bool MIXED = std::is_same<DT, float2>::value && !RF;
+  __shared__ float fa[MIXED ? F32SETS * F32STRIDE : 1];
+  const bool f32inc = MIXED && upd && f32_increment_fits(lv.sx, lv.sy);
+  // the sets of the staged nodes: columns scx0.., rows scy0.. (nscx across)
+  const int scx0 = max(i0 - 1, 0) / lv.sx, scy0 = max(j0 - 1, 0) / lv.sy;
+  const int nscx = min(i0 + TX, lv.nx - 1) / lv.sx - scx0 + 1;
+  if (f32inc) {
+    const int nscy = min(j0 + TY, lv.ny - 1) / lv.sy - scy0 + 1;
+    for (int q = tid; q < nscx * nscy * F32STRIDE; q += NT) {
+      const int sl = q / F32STRIDE, m = q - sl * F32STRIDE;
+      const int Ix = scx0 + sl % nscx, Iy = scy0 + sl / nscx;
+      const int I = Iy * lv.Mx + Ix;
+      float v = 0.0f;
+      if (m < NMODES) {
+        v = (float)__ldg(a + (size_t)lv.q * I + m);
+      } else if (m == 9) {
+        v = (float)fma(lv.L, (double)(Ix * lv.sx), -lv.rep[I].x);
+      } else if (m == 10) {
+        v = (float)fma(lv.L * SQ3_2, (double)(Iy * lv.sy), -lv.rep[I].y);
+      }
+      fa[q] = v;
+    }
+    __syncthreads();
+  }
+
   for (int idx = tid; idx < (TX + 2) * (TY + 2); idx += NT) {
     const int lx = idx % (TX + 2), ly = idx / (TX + 2);
     const int i = i0 + lx - 1, j = j0 + ly - 1;
     double2 v = make_double2(0.0, 0.0);
     if (i >= 0 && i < lv.nx && j >= 0 && j < lv.ny) {
       v = u_in[(size_t)j * lv.nx + i];
-      if (upd) v = apply_update<DT, RF>(lv, v, i, j, delta, delta_rf, a);
+      if constexpr (MIXED) {
+        if (f32inc) {
+          const int Ix = i / lv.sx, Iy = j / lv.sy;
+          const float* f = fa + ((Iy - scy0) * nscx + (Ix - scx0)) * F32STRIDE;
+          v = apply_update_f32(lv, v, i, j, Ix * lv.sx, Iy * lv.sy, f, reinterpret_cast<const float2*>(delta));
+        } else if (upd) {
+          v = apply_update<DT, RF>(lv, v, i, j, delta, delta_rf, a);
+        }
+      } else if (upd) {
+        v = apply_update<DT, RF>(lv, v, i, j, delta, delta_rf, a);
+      }
     }
     U[ly][lx] = v;
   }
