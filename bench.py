@@ -140,15 +140,22 @@ def residual_work(c, fp32):
 # FP64 pipe whatever its flops: 37 for the six bar forces, r and the three norm
 # terms, plus 17 for the upper-level update u += V a of each staged node (node
 # position, xi and eta, the mode sums; int-to-double conversions not counted),
-# of which a 32 x 8 tile stages (34 x 10) / (32 x 8) = 1.33 per node.
+# of which a 32 x 8 tile stages (34 x 10) / (32 x 8) = 1.33 per node.  The
+# mixed form forms the increment in FP32 and spends 4 FP64 instructions per
+# staged node on it (two conversions, two adds).
 RESIDUAL_FP64_INSTR_PER_NODE = 37 + 17 * (34 * 10) / (32 * 8)
+RESIDUAL_FP64_INSTR_PER_NODE_MIXED = 37 + 4 * (34 * 10) / (32 * 8)
 
 
-def residual_fp64_frac(c, avg_ms, n_sm, sm_mhz):
+def residual_fp64_instr(fp32):
+    return RESIDUAL_FP64_INSTR_PER_NODE_MIXED if fp32 else RESIDUAL_FP64_INSTR_PER_NODE
+
+
+def residual_fp64_frac(c, avg_ms, n_sm, sm_mhz, fp32=False):
     """Share of the FP64 pipe's instruction slots (SMs x DFMA lanes x clock)
     the update/residual kernel's FP64 instructions fill."""
     slots = n_sm * FP64_LANES_PER_SM_CLK * sm_mhz * 1e6 * avg_ms * 1e-3
-    return c.nx * c.ny * RESIDUAL_FP64_INSTR_PER_NODE / slots
+    return c.nx * c.ny * residual_fp64_instr(fp32) / slots
 
 
 def src_sha(name):
@@ -947,8 +954,8 @@ def run_ours(args, rank, world, local_rank):
         roof["update_residual"] = {"avg_launch_ms": ravg, "hbm_gbs": rb / (ravg * 1e-3) / 1e9,
                                    "hbm_frac": rb / (ravg * 1e-3) / 1e9 / hbm_peak,
                                    "bound": "alu (FP64 pipe)",
-                                   "fp64_instr_per_node": RESIDUAL_FP64_INSTR_PER_NODE,
-                                   "fp64_frac": residual_fp64_frac(c, ravg, n_sm1, mhz1)}
+                                   "fp64_instr_per_node": residual_fp64_instr(fp32),
+                                   "fp64_frac": residual_fp64_frac(c, ravg, n_sm1, mhz1, fp32)}
         roof["kernel_ms"] = {k: v[0] for k, v in kt.items()}
         roof["kernel_launches"] = {k: v[1] for k, v in kt.items()}
         rooflines[name] = roof
