@@ -66,7 +66,8 @@ typedef int32_t hms_status;
 #define HMS_MEM_DEVICE 1
 
 #define HMS_FP64 0   /* every step in FP64 (the plain form) */
-#define HMS_MIXED 1  /* FP32 local relaxation; FP64 residual, master correction, norms */
+#define HMS_MIXED 1  /* FP32 local relaxation, K_aa bar products and increment V a;
+                        FP64 residual, u, master correction, norms */
 
 typedef struct hms_context hms_context;
 typedef struct hms_problem hms_problem;
@@ -314,7 +315,11 @@ hms_status hms_reactions(hms_problem* pr, const double* u, double* f_out, int32_
 /* Steps a2 + a1 (Eq. 3 then Eq. 1): u_out = u + V a with modes built from
  * delta [2*nx*ny] (q = 12: [2][2*nx*ny], delta then delta^RF) and
  * coefficients a [q*M] (set-major, q per set), then r = p - K u_out and the
- * sums of hms_residual.  u_out may not alias u. */
+ * sums of hms_residual.  u_out may not alias u.  For HMS_MIXED problems with
+ * q = 9 delta is rounded to FP32 and the increment V a is formed in FP32
+ * (coefficients and the node's offsets from its set's representative point
+ * rounded to FP32), then added to the FP64 u; r is exact for the u_out
+ * written. */
 hms_status hms_update_residual(hms_problem* pr, const double* p, const double* u,
                                const double* delta, const double* a, double* u_out,
                                double* r, double* norms, int32_t mem_kind);
