@@ -318,8 +318,10 @@ hms_status hms_reactions(hms_problem* pr, const double* u, double* f_out, int32_
  * sums of hms_residual.  u_out may not alias u.  For HMS_MIXED problems with
  * q = 9 delta is rounded to FP32 and the increment V a is formed in FP32
  * (coefficients and the node's offsets from its set's representative point
- * rounded to FP32), then added to the FP64 u; r is exact for the u_out
- * written. */
+ * rounded to FP32), then added to the FP64 u, wherever a 34 x 10-node block
+ * (a 32 x 8 tile and its halo) touches at most 32 sets (set tiles of 8 x 8
+ * nodes and larger; smaller ones keep the FP64 increment); r is exact for
+ * the u_out written. */
 hms_status hms_update_residual(hms_problem* pr, const double* p, const double* u,
                                const double* delta, const double* a, double* u_out,
                                double* r, double* norms, int32_t mem_kind);
