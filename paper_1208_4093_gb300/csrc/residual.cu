@@ -17,7 +17,7 @@
 // FP32 once per CTA (with the set's representative point as an offset, so
 // that xi and eta are small numbers), and a staged node then costs 4 FP64
 // operations (two conversions, two adds) instead of about 17.  The increment
-// carries an FP32 rounding error of its own size times ~1e-7, like the FP32
+// carries FP32 rounding errors of about 1e-7 of its terms' size, like the FP32
 // relaxation's delta it multiplies; the residual that decides convergence
 // stays FP64, so the iteration still converges to the FP64 solution (later
 // updates correct what an update got wrong).  The FP64 form and the
