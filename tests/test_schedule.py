@@ -113,3 +113,84 @@ def test_schedule_does_not_apply():
         capi.hms_relax_schedule(1, 64, 16, 16, 152)
     with pytest.raises(capi.HmsError):
         capi.hms_relax_schedule(64, 64, 65, 16, 152)
+
+
+def test_schedule_handoff_reproduces_the_substitution():
+    """Run every set's block substitution (Eq. 12's local solve, k^Inner = L L^T
+    with L block bidiagonal by lattice rows) op by op in the plan's segments, a
+    cut set's tail starting only from what the head left in device memory: y_j
+    after a forward Linv_j product (o0 <= 2h - 1), x_j (the set's delta row j)
+    after a backward Linv_j^T product.  Every set must get k^Inner^-1 r_I."""
+    import numpy as np
+    from oracle import truss
+    from paper_1208_4093_gb300 import capi
+    nx, ny, sx, sy, ctas = 20, 16, 4, 4, 6
+    segs, cta = capi.hms_relax_schedule(nx, ny, sx, sy, ctas)
+    K = truss.assemble_K(nx, ny).toarray()
+    free = truss.free_mask(nx, ny)
+    mx = -(-nx // sx)
+    rng = np.random.default_rng(3)
+    r = free * rng.standard_normal(2 * nx * ny)
+    state = {}
+
+    def setup(I):
+        i0, j0 = (I % mx) * sx, (I // mx) * sy
+        w, h = min(sx, nx - i0), min(sy, ny - j0)
+        nb = 2 * w
+        idx = np.array([2 * ((j0 + jl) * nx + i0 + il) + d for jl in range(h) for il in range(w) for d in range(2)])
+        k = K[np.ix_(idx, idx)].copy()
+        fx = ~free[idx]
+        k[fx, :] = 0.0
+        k[:, fx] = 0.0
+        k[fx, fx] = 1.0
+        L = np.linalg.cholesky(k)
+        blk = lambda a, b: L[a * nb:(a + 1) * nb, b * nb:(b + 1) * nb]
+        return dict(h=h, nb=nb, idx=idx, k=k, Linv=[np.linalg.inv(blk(j, j)) for j in range(h)],
+                    B=[None] + [blk(j, j - 1) for j in range(1, h)], rr=r[idx].reshape(h, nb),
+                    y=np.zeros((h, nb)), x=np.zeros((h, nb)))
+
+    def run(I, o0, o1):
+        s = state.setdefault(I, setup(I))
+        h, nmat = s["h"], 2 * s["h"] - 1
+        # the state a segment starts from: only what device memory holds
+        if o0 == 0:
+            z = s["rr"][0].copy()
+        elif o0 <= nmat:
+            ycur = s["y"][(o0 - 1) // 2].copy()
+        else:
+            xbuf = s["x"][(2 * nmat - o0) // 2].copy()
+        for o in range(o0, o1):
+            k = o if o < nmat else 2 * nmat - 1 - o
+            if o < nmat and k % 2 == 1:          # z = r_j - B_j y_{j-1}
+                j = (k + 1) // 2
+                z = s["rr"][j] - s["B"][j] @ ycur
+            elif o < nmat:                        # y_j = Linv_j z
+                j = k // 2
+                ycur = s["Linv"][j] @ z
+                s["y"][j] = ycur
+            elif k % 2 == 0:                      # x_j = Linv_j^T w
+                j = k // 2
+                wv = ycur if j == h - 1 else wbuf
+                xbuf = s["Linv"][j].T @ wv
+                s["x"][j] = xbuf
+            else:                                 # w = y_{j-1} - B_j^T x_j
+                j = (k + 1) // 2
+                wbuf = s["y"][j - 1] - s["B"][j].T @ xbuf
+        # (locals of a segment end with it: the next segment of the same set
+        # is a tail on another CTA)
+
+    heads = [tuple(int(v) for v in segs[cta[g]]) for g in range(ctas)]
+    done = set()
+    for I, o0, o1 in heads:          # heads wait for nothing
+        if o1 < 2 * (2 * state.setdefault(I, setup(I))["h"] - 1):
+            run(I, o0, o1)
+            done.add((I, o0))
+    for g in range(ctas):            # then each CTA's whole sets and tail, in its order
+        for k in range(cta[g], cta[g + 1]):
+            I, o0, o1 = (int(v) for v in segs[k])
+            if (I, o0) not in done:
+                run(I, o0, o1)
+    for I, s in state.items():
+        want = np.linalg.solve(s["k"], r[s["idx"]])
+        assert np.allclose(s["x"].reshape(-1), want, rtol=0, atol=1e-10 * np.abs(want).max()), I
+    assert len(state) == (-(-nx // sx)) * (-(-ny // sy))
