@@ -226,6 +226,15 @@ int32_t hms_problem_relax_balanced(const hms_problem* pr);
  * arguments or cap (segments segs_out holds) too small. */
 int32_t hms_relax_schedule(int32_t nx, int32_t ny, int32_t set_sx, int32_t set_sy, int32_t ctas,
                            int32_t* segs_out, int32_t cap, int32_t* cta_out);
+/* The classes of identical sets that class_factors = 1 factors once each,
+ * computed on the host; no device is needed.  With a uniform EA two sets have
+ * the same k^Inner (Eq. 12) when they agree in width, height, parity of the
+ * first row, the lattice edges they touch and their constrained DOFs.
+ * class_out (host, cap >= set count int32) receives each set's class in set
+ * order (row-major over the set grid), the classes numbered by first
+ * appearance.  Returns the class count; -1 for bad arguments, cap too small,
+ * or a per-bar EA (d->ea != NULL: no two sets need share a matrix). */
+int32_t hms_set_classes(const hms_lattice_desc* d, int32_t* class_out, int32_t cap);
 
 /* The whole iteration (Fig. 3) for nrhs load vectors, each from u0 (NULL =
  * zero): loads [nrhs][2*nx*ny], u0 and u_out likewise.  hist (nullable)

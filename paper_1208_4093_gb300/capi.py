@@ -92,6 +92,7 @@ def lib():
         "hms_problem_relax_balanced": (ctypes.c_int32, [_P]),
         "hms_relax_schedule": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                 ctypes.c_int32, _P, ctypes.c_int32, _P]),
+        "hms_set_classes": (ctypes.c_int32, [ctypes.POINTER(LatticeDesc), _P, ctypes.c_int32]),
         "hms_solve": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, ctypes.c_int32]),
         "hms_kernel_times": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
         "hms_residual": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32]),
@@ -134,7 +135,8 @@ def exported_symbols():
             "hms_server_destroy", "hms_server_submit", "hms_server_step", "hms_server_take", "hms_problem_clone",
             "hms_problem_relax_threads", "hms_context_set_batch_mode", "hms_problem_relax_copies",
             "hms_reactions", "hms_problem_refine_cap_hits", "hms_problem_set_relax_wait_limit",
-            "hms_measure_fp64_rate", "hms_relax_force", "hms_problem_relax_balanced", "hms_relax_schedule"]
+            "hms_measure_fp64_rate", "hms_relax_force", "hms_problem_relax_balanced", "hms_relax_schedule",
+            "hms_set_classes"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -267,6 +269,18 @@ def hms_problem_relax_copies(pr) -> int:
 
 def hms_problem_relax_balanced(pr) -> int:
     return int(lib().hms_problem_relax_balanced(pr))
+
+
+def hms_set_classes(nx, ny, set_sx, set_sy, fixed=None, fix_bottom_edge=1):
+    """Class of every set (row-major over the set grid) that class_factors = 1
+    would share one factor across (host only): (classes [M], class count)."""
+    d, _, keep = _desc_opts(nx, ny, set_sx, set_sy, fixed=fixed, fix_bottom_edge=fix_bottom_edge)
+    m = (-(-nx // set_sx)) * (-(-ny // set_sy))
+    out = np.zeros(m, np.int32)
+    n = lib().hms_set_classes(ctypes.byref(d), out.ctypes.data, m)
+    if n < 0:
+        raise HmsError(HMS_ERR_ARG, "hms_set_classes: bad arguments")
+    return out, int(n)
 
 
 def hms_relax_schedule(nx, ny, set_sx, set_sy, ctas):

@@ -695,6 +695,24 @@ int32_t hms_problem_relax_threads(const hms_problem* pr) { return pr ? pr->relax
 int32_t hms_problem_relax_copies(const hms_problem* pr) { return pr ? pr->relax_chunks : 0; }
 int32_t hms_problem_relax_balanced(const hms_problem* pr) { return pr && pr->relax_sched ? 1 : 0; }
 
+int32_t hms_set_classes(const hms_lattice_desc* d, int32_t* class_out, int32_t cap) {
+  if (!d || !class_out || d->ea || d->nx < 2 || d->ny < 2 || d->set_sx < 1 || d->set_sx > MAX_SX || d->set_sy < 1)
+    return -1;
+  LatView lv{};
+  lv.nx = d->nx;
+  lv.ny = d->ny;
+  lv.sx = d->set_sx;
+  lv.sy = d->set_sy;
+  lv.Mx = (lv.nx + lv.sx - 1) / lv.sx;
+  lv.My = (lv.ny + lv.sy - 1) / lv.sy;
+  if ((long long)lv.Mx * lv.My > cap) return -1;
+  lv.M = lv.Mx * lv.My;
+  ClassPlanHost P;
+  class_plan_build(lv, fix_pattern(d), 1, &P);  // one set per item
+  for (const ClassItem& it : P.items) class_out[P.sets[it.first]] = it.cls;
+  return (int32_t)P.info.size();
+}
+
 int32_t hms_relax_schedule(int32_t nx, int32_t ny, int32_t set_sx, int32_t set_sy, int32_t ctas,
                            int32_t* segs_out, int32_t cap, int32_t* cta_out) {
   if (nx < 2 || ny < 2 || set_sx < 1 || set_sx > MAX_SX || set_sy < 1 || ctas < 1 || cap < 0 || !cta_out)
