@@ -235,6 +235,17 @@ int32_t hms_relax_schedule(int32_t nx, int32_t ny, int32_t set_sx, int32_t set_s
  * appearance.  Returns the class count; -1 for bad arguments, cap too small,
  * or a per-bar EA (d->ea != NULL: no two sets need share a matrix). */
 int32_t hms_set_classes(const hms_lattice_desc* d, int32_t* class_out, int32_t cap);
+/* The nested-dissection plan of the upper level (Eq. 8; coarse_factor = 6)
+ * for a grid of mx x my sets, computed on the host; no device is needed.
+ * Node k eliminates the unknowns of its sets S_k and couples to its boundary
+ * sets B_k, which lie on its ancestors' separators; children come before
+ * their parents, the root last.  nodes_out[6 k .. 6 k + 5] = (|S_k|, |B_k|,
+ * first entry in sets_out, child count, child 0, child 1; -1 for no child);
+ * sets_out holds S_k then B_k (set indices, row-major over the set grid)
+ * node by node.  Returns the node count; -1 for bad arguments or caps
+ * (nodes_out holds 6 node_cap int32, sets_out sets_cap) too small. */
+int32_t hms_nd_plan(int32_t mx, int32_t my, int32_t* nodes_out, int32_t node_cap, int32_t* sets_out,
+                    int32_t sets_cap);
 
 /* The whole iteration (Fig. 3) for nrhs load vectors, each from u0 (NULL =
  * zero): loads [nrhs][2*nx*ny], u0 and u_out likewise.  hist (nullable)

@@ -93,6 +93,7 @@ def lib():
         "hms_relax_schedule": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                 ctypes.c_int32, _P, ctypes.c_int32, _P]),
         "hms_set_classes": (ctypes.c_int32, [ctypes.POINTER(LatticeDesc), _P, ctypes.c_int32]),
+        "hms_nd_plan": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_int32]),
         "hms_solve": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, ctypes.c_int32]),
         "hms_kernel_times": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32]),
         "hms_residual": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32]),
@@ -136,7 +137,7 @@ def exported_symbols():
             "hms_problem_relax_threads", "hms_context_set_batch_mode", "hms_problem_relax_copies",
             "hms_reactions", "hms_problem_refine_cap_hits", "hms_problem_set_relax_wait_limit",
             "hms_measure_fp64_rate", "hms_relax_force", "hms_problem_relax_balanced", "hms_relax_schedule",
-            "hms_set_classes"]
+            "hms_set_classes", "hms_nd_plan"]
 
 
 # ---------------------------------------------------------------- marshalling
@@ -281,6 +282,24 @@ def hms_set_classes(nx, ny, set_sx, set_sy, fixed=None, fix_bottom_edge=1):
     if n < 0:
         raise HmsError(HMS_ERR_ARG, "hms_set_classes: bad arguments")
     return out, int(n)
+
+
+def hms_nd_plan(mx, my):
+    """The upper level's nested-dissection plan for mx x my sets (host only):
+    a list of nodes, children before parents, each a dict with S (sets it
+    eliminates), B (its boundary sets) and children (node indices)."""
+    m = mx * my
+    cap_n, cap_s = 4 * m + 8, 64 * m + 64
+    nodes = np.zeros((cap_n, 6), np.int32)
+    sets = np.zeros(cap_s, np.int32)
+    n = lib().hms_nd_plan(int(mx), int(my), nodes.ctypes.data, cap_n, sets.ctypes.data, cap_s)
+    if n < 0:
+        raise HmsError(HMS_ERR_ARG, "hms_nd_plan: bad arguments")
+    out = []
+    for ns, nb, off, nch, c0, c1 in nodes[:n].tolist():
+        out.append({"S": sets[off:off + ns].tolist(), "B": sets[off + ns:off + ns + nb].tolist(),
+                    "children": [c for c in (c0, c1)[:nch]]})
+    return out
 
 
 def hms_relax_schedule(nx, ny, set_sx, set_sy, ctas):

@@ -713,6 +713,30 @@ int32_t hms_set_classes(const hms_lattice_desc* d, int32_t* class_out, int32_t c
   return (int32_t)P.info.size();
 }
 
+int32_t hms_nd_plan(int32_t mx, int32_t my, int32_t* nodes_out, int32_t node_cap, int32_t* sets_out,
+                    int32_t sets_cap) {
+  if (mx < 1 || my < 1 || (long long)mx * my > (1LL << 24) || !nodes_out || !sets_out) return -1;
+  LatView lv{};
+  lv.Mx = mx;
+  lv.My = my;
+  lv.M = mx * my;
+  NDPlanHost P;
+  if (!nd_plan_build(lv, &P)) return -1;
+  if ((long long)P.nodes.size() > node_cap || (long long)P.sets.size() > sets_cap) return -1;
+  for (size_t k = 0; k < P.nodes.size(); ++k) {
+    const NDNode& d = P.nodes[k];
+    int32_t* o = nodes_out + 6 * k;
+    o[0] = d.ns;
+    o[1] = d.nb;
+    o[2] = d.s_off;
+    o[3] = d.nchild;
+    o[4] = d.nchild > 0 ? d.child[0] : -1;
+    o[5] = d.nchild > 1 ? d.child[1] : -1;
+  }
+  for (size_t q = 0; q < P.sets.size(); ++q) sets_out[q] = P.sets[q];
+  return (int32_t)P.nodes.size();
+}
+
 int32_t hms_relax_schedule(int32_t nx, int32_t ny, int32_t set_sx, int32_t set_sy, int32_t ctas,
                            int32_t* segs_out, int32_t cap, int32_t* cta_out) {
   if (nx < 2 || ny < 2 || set_sx < 1 || set_sx > MAX_SX || set_sy < 1 || ctas < 1 || cap < 0 || !cta_out)
