@@ -212,7 +212,8 @@ int32_t hms_problem_relax_threads(const hms_problem* pr);
 int32_t hms_problem_relax_copies(const hms_problem* pr);
 /* 1 if the relaxation of pr runs on the balanced schedule (relax_balance). */
 int32_t hms_problem_relax_balanced(const hms_problem* pr);
-/* The balanced relaxation schedule (relax_balance) of a lattice's sets over
+/* No counterpart in the paper (a launch plan of the relaxation of Eqs. 12-13):
+ * the balanced relaxation schedule (relax_balance) of a lattice's sets over
  * `ctas` persistent CTAs (one per SM), computed on the host; no device is
  * needed.  It is the plan hms_problem_create makes on a device with that many
  * SMs for set tiles of set_sx x set_sy nodes (no overlap).  A set of h rows
