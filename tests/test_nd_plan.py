@@ -127,3 +127,29 @@ def test_nd_plan_factor_solves_a_set_grid_system(mx, my, q):
     x = multifrontal_solve(A, rhs, nodes, q)
     want = np.linalg.solve(A, rhs)
     assert np.linalg.norm(x - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_planted_plan_mistakes_are_caught():
+    """A plan with one boundary set missing from a leaf's front no longer
+    solves the system: the multifrontal check is not vacuous."""
+    import copy
+    mx, my, q = 7, 5, 2
+    nodes, _, _ = plan(mx, my)
+    rng = np.random.default_rng(1)
+    M = mx * my
+    A = np.zeros((M * q, M * q))
+    for I in range(M):
+        for J in neighbours(I, mx, my) + [I]:
+            if J >= I:
+                blk = rng.standard_normal((q, q))
+                A[I * q:(I + 1) * q, J * q:(J + 1) * q] = blk + (blk.T if J == I else 0)
+                A[J * q:(J + 1) * q, I * q:(I + 1) * q] = A[I * q:(I + 1) * q, J * q:(J + 1) * q].T
+    A += np.diag(np.abs(A).sum(axis=1) + 1.0)
+    rhs = rng.standard_normal(M * q)
+    want = np.linalg.solve(A, rhs)
+    # a leaf's boundary loses a set (its coupling to that set is dropped)
+    bad = copy.deepcopy(nodes)
+    k = next(i for i, n in enumerate(bad) if not n["children"] and len(n["B"]) > 1)
+    bad[k]["B"] = bad[k]["B"][1:]
+    x = multifrontal_solve(A, rhs, bad, q)
+    assert np.linalg.norm(x - want) > 1e-6 * np.linalg.norm(want)
